@@ -1,0 +1,276 @@
+"""FP64 CPU oracle for cascading-smoother multigrid -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The library under
+``paper_2606_12577_gb300`` never does, and the two share no code: the only
+thing both sides consume is the seeded input module ``problems``.
+
+The arithmetic lives in ``cs_oracle.c`` (plain C loops over CSR matrices,
+one function per step of the paper; see its header for the citations).  This
+file compiles it with gcc on first use, marshals numpy arrays through ctypes,
+and implements the paper's reporting metrics (rho, eta, C_d) in numpy.
+
+Parity pins: see ``tests/test_oracle_pins.py`` (Table 1, Fourier closed
+forms, brute-force dense least squares, monotonicity, propagators, V-cycle
+symmetry, Galerkin stencils, special cases, convergence).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cs_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libcs_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+KINDS = {"additive": 0, "multiplicative": 1}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction so that
+    x86 and Arm hosts round identically)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(build())
+        P, I, D, L = C.c_void_p, C.c_int, C.c_double, C.c_int64
+        sig = {
+            "ora_hier_create": (P, [I, P, I, P, P, I, I, I, I, I]),
+            "ora_hier_free": (None, [P]),
+            "ora_hier_nlev": (I, [P]),
+            "ora_hier_dims": (None, [P, I, P]),
+            "ora_hier_nnz": (L, [P, I]),
+            "ora_hier_csr": (None, [P, I, P, P, P]),
+            "ora_hier_nblocks": (I, [P, I]),
+            "ora_hier_blocks": (None, [P, I, P, P, P]),
+            "ora_casc_create": (P, [P, I, I, I, I]),
+            "ora_casc_empty": (P, [P, I, I]),
+            "ora_casc_free": (None, [P]),
+            "ora_casc_nlev": (I, [P]),
+            "ora_casc_lamsize": (L, [P, I]),
+            "ora_casc_lambda": (None, [P, I, P]),
+            "ora_casc_set_lambda": (None, [P, I, P]),
+            "ora_casc_efrob": (None, [P, I, P]),
+            "ora_residual": (None, [P, I, P, P, P]),
+            "ora_smooth": (None, [P, P, I, I, P, P]),
+            "ora_restrict": (None, [P, I, P, P]),
+            "ora_prolong_correct": (None, [P, I, P, P]),
+            "ora_coarse_solve": (None, [P, P, P]),
+            "ora_vcycle": (None, [P, P, I, I, I, P, P]),
+            "ora_solve": (I, [P, P, I, I, I, I, D, I, I, P, P, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Hierarchy:
+    """Geometric hierarchy (Sec. 2.4): even-index node coarsening until the
+    largest side is <= coarse_max, bilinear/trilinear P, Galerkin
+    A_2h = R A_h P with R = 2^{-d} P^T (rscale_mode=1: R = P^T)."""
+
+    def __init__(self, A, bs: int = 1, coarse_max: int = 4, max_levels: int = 0, rscale_mode: int = 0):
+        lib = _load()
+        self.dim = A.dim
+        self.bs = bs
+        n3 = np.asarray(A.n, dtype=np.int32)
+        off = np.ascontiguousarray(A.offsets_array(), dtype=np.int32)
+        coeff = _f64(A.coeff)
+        self._h = lib.ora_hier_create(A.dim, _ptr(n3), A.nst, _ptr(off), _ptr(coeff), int(A.periodic),
+                                      bs, coarse_max, max_levels, rscale_mode)
+        if not self._h:
+            raise RuntimeError("oracle hierarchy creation failed")
+        self.nlev = lib.ora_hier_nlev(self._h)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.ora_hier_free(self._h)
+            self._h = None
+
+    def dims(self, l: int):
+        out = np.zeros(3, dtype=np.int32)
+        _lib.ora_hier_dims(self._h, l, _ptr(out))
+        return tuple(int(v) for v in out)
+
+    def N(self, l: int) -> int:
+        d = self.dims(l)
+        return d[0] * d[1] * d[2]
+
+    def csr(self, l: int):
+        """(rowptr, colind, values) of the level-l operator."""
+        N = self.N(l)
+        nnz = _lib.ora_hier_nnz(self._h, l)
+        rp = np.zeros(N + 1, dtype=np.int64)
+        ci = np.zeros(nnz, dtype=np.int32)
+        v = np.zeros(nnz, dtype=np.float64)
+        _lib.ora_hier_csr(self._h, l, _ptr(rp), _ptr(ci), _ptr(v))
+        return rp, ci, v
+
+    def dense(self, l: int) -> np.ndarray:
+        rp, ci, v = self.csr(l)
+        N = len(rp) - 1
+        M = np.zeros((N, N))
+        for i in range(N):
+            M[i, ci[rp[i]:rp[i + 1]]] += v[rp[i]:rp[i + 1]]
+        return M
+
+    def blocks(self, l: int):
+        """(bptr, members, parity) of the level-l block partition."""
+        nb = _lib.ora_hier_nblocks(self._h, l)
+        bptr = np.zeros(nb + 1, dtype=np.int32)
+        bidx = np.zeros(self.N(l), dtype=np.int32)
+        bpar = np.zeros(nb, dtype=np.int32)
+        _lib.ora_hier_blocks(self._h, l, _ptr(bptr), _ptr(bidx), _ptr(bpar))
+        return bptr, bidx, bpar
+
+    def colours(self, l: int) -> np.ndarray:
+        """Red-black colour id (0 = red) of every unknown on level l."""
+        bptr, bidx, bpar = self.blocks(l)
+        out = np.zeros(self.N(l), dtype=np.int8)
+        for b in range(len(bpar)):
+            out[bidx[bptr[b]:bptr[b + 1]]] = bpar[b]
+        return out
+
+    # ---- single steps of Algorithm 1
+    def residual(self, l, b, x):
+        r = np.zeros(self.N(l))
+        _lib.ora_residual(self._h, l, _ptr(_f64(b)), _ptr(_f64(x)), _ptr(r))
+        return r
+
+    def restrict(self, l, r):
+        rc = np.zeros(self.N(l + 1))
+        _lib.ora_restrict(self._h, l, _ptr(_f64(r)), _ptr(rc))
+        return rc
+
+    def prolong_correct(self, l, xc, x):
+        x = _f64(x).copy()
+        _lib.ora_prolong_correct(self._h, l, _ptr(_f64(xc)), _ptr(x))
+        return x
+
+    def coarse_solve(self, b):
+        x = np.zeros(self.N(self.nlev - 1))
+        _lib.ora_coarse_solve(self._h, _ptr(_f64(b)), _ptr(x))
+        return x
+
+
+class Cascade:
+    """Cascading smoothers on every smoothing level of a hierarchy
+    (Algorithm 2; SM Algorithm for kind='multiplicative', red-black)."""
+
+    def __init__(self, hier: Hierarchy, kind: str = "additive", nu: int = 3, prescale: bool = True,
+                 alpha: int = 0, _empty: bool = False):
+        self.hier = hier
+        self.kind = kind
+        self.nu = nu
+        self.ncol = 2 if kind == "multiplicative" else 1
+        if _empty:
+            self._c = _lib.ora_casc_empty(hier._h, KINDS[kind], nu)
+        else:
+            self._c = _lib.ora_casc_create(hier._h, KINDS[kind], nu, int(prescale), alpha)
+        if not self._c:
+            raise RuntimeError("oracle cascade setup failed (non-positive diagonal under prescaling?)")
+        self.nlev = _lib.ora_casc_nlev(self._c)
+
+    @classmethod
+    def empty(cls, hier, kind="additive", nu=1):
+        return cls(hier, kind, nu, _empty=True)
+
+    def __del__(self):
+        if getattr(self, "_c", None) and _lib is not None:
+            _lib.ora_casc_free(self._c)
+            self._c = None
+
+    def lamsize(self, l: int) -> int:
+        return int(_lib.ora_casc_lamsize(self._c, l))
+
+    def lam(self, l: int) -> np.ndarray:
+        """Lambda_{l'} on hierarchy level l as [nu, lamsize]: block b's
+        n_b x n_b matrix row-major at its offset (point blocks: one value per
+        unknown).  Multiplicative: Lambda_{l',k} sits on the blocks of colour k."""
+        out = np.zeros((self.nu, self.lamsize(l)))
+        _lib.ora_casc_lambda(self._c, l, _ptr(out))
+        return out
+
+    def set_lam(self, l: int, lam: np.ndarray):
+        lam = _f64(lam).reshape(self.nu, self.lamsize(l))
+        _lib.ora_casc_set_lambda(self._c, l, _ptr(lam))
+
+    def efrob(self, l: int) -> np.ndarray:
+        """||E~||_F after each setup step (prescaled space), starting with E_0 = I."""
+        out = np.zeros(self.nu * self.ncol + 1)
+        _lib.ora_casc_efrob(self._c, l, _ptr(out))
+        return out
+
+
+def smooth(h: Hierarchy, c: Cascade, l: int, b, x, reverse: bool = False) -> np.ndarray:
+    x = _f64(x).copy()
+    _lib.ora_smooth(h._h, c._c, l, int(reverse), _ptr(_f64(b)), _ptr(x))
+    return x
+
+
+def vcycle(h: Hierarchy, c: Cascade, b, x=None, mu_pre: int = 1, mu_post: int = 1, rf: bool = True) -> np.ndarray:
+    x = np.zeros(h.N(0)) if x is None else _f64(x).copy()
+    _lib.ora_vcycle(h._h, c._c, mu_pre, mu_post, int(rf), _ptr(_f64(b)), _ptr(x))
+    return x
+
+
+def solve(h: Hierarchy, c: Cascade, b, x=None, method: str = "stationary", mu_pre: int = 1,
+          mu_post: int = 1, rf: bool = True, tol: float = 1e-10, maxit: int = 100, restart: int = 30):
+    """Returns (x, iterations or -1, history, final relative true residual)."""
+    x = np.zeros(h.N(0)) if x is None else _f64(x).copy()
+    hist = np.zeros(2 * maxit + 4)
+    nh = C.c_int(0)
+    fin = C.c_double(0.0)
+    it = _lib.ora_solve(h._h, c._c, 0 if method == "stationary" else 1, mu_pre, mu_post, int(rf), tol,
+                        maxit, restart, _ptr(_f64(b)), _ptr(x), _ptr(hist), C.byref(nh), C.byref(fin))
+    return x, int(it), hist[: nh.value].copy(), float(fin.value)
+
+
+# ---------------------------------------------------------------- metrics
+def rho_from_history(r) -> float:
+    """Convergence rate by least-squares regression of log r_i on i
+    (Sec. 3.1 footnote)."""
+    r = np.asarray(r, dtype=np.float64)
+    r = r[r > 0]
+    i = np.arange(len(r), dtype=np.float64)
+    slope = np.polyfit(i, np.log(r), 1)[0]
+    return float(np.exp(slope))
+
+
+def eta(rho: float) -> float:
+    """eta = log 0.1 / log rho (eq. eta)."""
+    return float(np.log(0.1) / np.log(rho))
+
+
+def cost_cd(d: int, nu: int, eta_value: float) -> float:
+    """C_d(nu, eta) = eta (1 + (2 nu + 1) / (1 - 2^{-d})) (eq. cost)."""
+    return float(eta_value * (1.0 + (2 * nu + 1) / (1.0 - 2.0 ** (-d))))

@@ -1,0 +1,213 @@
+"""Seeded synthetic problem generators shared by the oracle and the CUDA path.
+
+This module only builds inputs: structured-grid operators ``A`` in stencil
+form (the discretisation the method is applied to, Sec. 2 "block-partitioned
+Ax = b" and Sec. 3.3.1 "finite difference Poisson") and right-hand sides.  It
+holds none of the cascading-smoother arithmetic (no setup, no smoothing, no
+transfers): the oracle under ``oracle/`` and the CUDA library each implement
+that on their own.
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014), used as a counter-based
+generator: draw k of stream ``seed`` is ``mix(seed*G + (k+1)*G)`` with
+``G = 0x9E3779B97F4A7C15``; the top 53 bits give a uniform double in [0, 1).
+
+Layout of a structured operator (``Stencil``):
+  * unknowns are the interior nodes of a ``nx x ny x nz`` grid (``nz = 1`` in
+    2D), numbered ``i = ix + nx*(iy + ny*iz)`` (x fastest);
+  * ``offsets[s] = (dx, dy, dz)`` with entries in {-1, 0, 1};
+  * ``coeff[s, i]`` couples unknown ``i`` to the node at ``i + offsets[s]``;
+    it is zero where that node is a (homogeneous) Dirichlet boundary node,
+    so boundary nodes are eliminated and are not unknowns;
+  * with ``periodic=True`` neighbours wrap around instead (used only to pin
+    the setup against the constant-coefficient values of Table 1).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Tuple
+
+import numpy as np
+
+_G = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, count: int, start: int = 0) -> np.ndarray:
+    """Return ``count`` SplitMix64 outputs (uint64) of stream ``seed``,
+    beginning at draw ``start``."""
+    with np.errstate(over="ignore"):
+        k = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+        z = np.uint64(seed) * _G + k * _G
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, count: int, start: int = 0) -> np.ndarray:
+    """Uniform doubles in [0, 1) with 53 random bits."""
+    return (splitmix64(seed, count, start) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def uniform(seed: int, count: int, lo: float = -1.0, hi: float = 1.0, start: int = 0) -> np.ndarray:
+    return lo + (hi - lo) * uniform01(seed, count, start)
+
+
+@dataclass
+class Stencil:
+    """A structured-grid operator in stencil (SoA) form; see module doc."""
+
+    dim: int
+    n: Tuple[int, int, int]
+    offsets: List[Tuple[int, int, int]]
+    coeff: np.ndarray  # float64 [nst, N]
+    periodic: bool = False
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def N(self) -> int:
+        return int(self.n[0] * self.n[1] * self.n[2])
+
+    @property
+    def nst(self) -> int:
+        return len(self.offsets)
+
+    def offsets_array(self) -> np.ndarray:
+        return np.asarray(self.offsets, dtype=np.int32).reshape(-1, 3)
+
+
+def _grid_coords(n):
+    nx, ny, nz = n
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return ix.ravel(), iy.ravel(), iz.ravel()
+
+
+def _inside(n, ix, iy, iz, off):
+    jx, jy, jz = ix + off[0], iy + off[1], iz + off[2]
+    return (jx >= 0) & (jx < n[0]) & (jy >= 0) & (jy < n[1]) & (jz >= 0) & (jz < n[2])
+
+
+def _star_offsets(dim):
+    offs = [(0, 0, 0)]
+    for d in range(dim):
+        for sgn in (-1, 1):
+            o = [0, 0, 0]
+            o[d] = sgn
+            offs.append(tuple(o))
+    return offs
+
+
+def poisson(dim: int, n: int, periodic: bool = False, h: float | None = None) -> Stencil:
+    """Second-order FD negative Laplacian on an ``n^dim`` interior-node grid
+    (5-point in 2D, 7-point in 3D, diagonal ``2d/h^2``; Sec. 3.3.1).
+
+    Dirichlet: ``h = 1/(n+1)`` and couplings to boundary nodes are zero.
+    Periodic: ``h = 1/n`` and every row carries the full stencil."""
+    if dim not in (2, 3):
+        raise ValueError("dim must be 2 or 3")
+    shape = (n, n, n if dim == 3 else 1)
+    if h is None:
+        h = 1.0 / n if periodic else 1.0 / (n + 1)
+    offs = _star_offsets(dim)
+    N = shape[0] * shape[1] * shape[2]
+    coeff = np.zeros((len(offs), N), dtype=np.float64)
+    ix, iy, iz = _grid_coords(shape)
+    inv_h2 = 1.0 / (h * h)
+    for s, o in enumerate(offs):
+        if o == (0, 0, 0):
+            coeff[s] = 2 * dim * inv_h2
+        else:
+            coeff[s] = -inv_h2 if periodic else np.where(_inside(shape, ix, iy, iz, o), -inv_h2, 0.0)
+    return Stencil(dim, shape, offs, coeff, periodic, name=f"poisson{dim}d_{n}")
+
+
+def variable_poisson(mu_cells: np.ndarray, h: float | None = None) -> Stencil:
+    """Cell-coefficient FD/FV operator ``-div(mu grad u)`` on interior nodes
+    (5-point in 2D, 7-point in 3D), homogeneous Dirichlet.
+
+    ``mu_cells`` has shape ``(n+1,)*dim`` (cells between nodes, C order
+    ``[cz,] cy, cx``).  The coefficient of the edge joining two nodes is the
+    arithmetic mean of the ``2^(dim-1)`` cells sharing that edge."""
+    dim = mu_cells.ndim
+    n1 = mu_cells.shape[-1]
+    n = n1 - 1
+    if h is None:
+        h = 1.0 / n1
+    inv_h2 = 1.0 / (h * h)
+    shape = (n, n, n if dim == 3 else 1)
+    offs = _star_offsets(dim)
+    N = shape[0] * shape[1] * shape[2]
+    ix, iy, iz = _grid_coords(shape)
+    # node (ix,iy[,iz]) in 0-based interior numbering sits at 1-based node
+    # index ix+1; cell c lies between nodes c and c+1 (1-based node indices).
+    mu = mu_cells if dim == 3 else mu_cells[None, :, :]
+
+    def edge(axis, sgn):
+        # coefficient of the edge from node p to node p + sgn*e_axis
+        X, Y, Z = ix + 1, iy + 1, iz + 1  # 1-based node coordinates
+        lo = [X, Y, Z]
+        lo = [a.copy() for a in lo]
+        lo[axis] = lo[axis] + (0 if sgn > 0 else -1)  # cell index along axis
+        others = [a for a in range(dim) if a != axis]
+        tot = np.zeros(N)
+        cnt = 0
+        for a in (-1, 0):
+            for b in ((-1, 0) if dim == 3 else (0,)):
+                c = [lo[0].copy(), lo[1].copy(), lo[2].copy()]
+                c[others[0]] = c[others[0]] + a
+                if dim == 3:
+                    c[others[1]] = c[others[1]] + b
+                if dim == 2:
+                    tot += mu[0, c[1], c[0]]
+                else:
+                    tot += mu[c[2], c[1], c[0]]
+                cnt += 1
+        return tot / cnt
+
+    coeff = np.zeros((len(offs), N), dtype=np.float64)
+    diag = np.zeros(N)
+    for s, o in enumerate(offs):
+        if o == (0, 0, 0):
+            continue
+        axis = int(np.nonzero(o)[0][0])
+        sgn = o[axis]
+        w = edge(axis, sgn) * inv_h2
+        diag += w
+        coeff[s] = np.where(_inside(shape, ix, iy, iz, o), -w, 0.0)
+    coeff[0] = diag
+    return Stencil(dim, shape, offs, coeff, False, name=f"varpoisson{dim}d_{n}")
+
+
+def random_coefficients(dim: int, n: int, seed: int, lo: float = -2.0, hi: float = 2.0) -> np.ndarray:
+    """i.i.d. log-uniform cell coefficients ``10^U[lo,hi]`` on ``(n+1)^dim``
+    cells (a small variable-coefficient test case)."""
+    shape = (n + 1,) * dim
+    u = uniform(seed, int(np.prod(shape)), lo, hi)
+    return (10.0 ** u).reshape(shape)
+
+
+def rhs(N: int, seed: int, nrhs: int = 1) -> np.ndarray:
+    """Right-hand side with i.i.d. entries ~ U[-1, 1] (Sec. 3.1 footnote).
+    Shape ``(N,)`` for one RHS, else ``(N, nrhs)`` (RHS-contiguous)."""
+    v = uniform(seed, N * nrhs, -1.0, 1.0)
+    return v if nrhs == 1 else v.reshape(N, nrhs)
+
+
+def config_seed(config: int, problem: int = 0) -> int:
+    """Seed of problem ``problem`` of workload ``config`` (run seed 0)."""
+    return 1000 * config + problem
+
+
+def poisson2d_64() -> Tuple[Stencil, np.ndarray]:
+    """2D Poisson, 5-point FD on a 64x64 interior grid, Dirichlet; RHS ~ U[-1,1]."""
+    A = poisson(2, 64)
+    return A, rhs(A.N, config_seed(1))
+
+
+def poisson3d(n: int = 256) -> Tuple[Stencil, np.ndarray]:
+    """3D Poisson, 7-point FD on an n^3 interior grid, Dirichlet; RHS ~ U[-1,1]."""
+    A = poisson(3, n)
+    return A, rhs(A.N, config_seed(2))

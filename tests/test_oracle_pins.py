@@ -1,0 +1,459 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (Table 1), closed forms (Fourier symbols, the known Galerkin
+stencil), brute-force dense least squares, invariants (monotonicity,
+propagators, V-cycle symmetry, scale invariance, fixed points) and special
+cases (damped Jacobi, red-black Gauss-Seidel, direct solves).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import problems
+from tests import dense_ref
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1.txt")
+
+
+def _table1():
+    rows = []
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            t = line.split()
+            rows.append((t[0], int(t[1]), int(t[2]), [float(v) for v in t[3:]]))
+    return rows
+
+
+@pytest.fixture(scope="module")
+def periodic_lams():
+    """lambda_l = Lambda_l * diag(A) on periodic Poisson grids of side >= 4 nu
+    (16^2 and 16^3), additive and red-black multiplicative, nu = 4."""
+    out = {}
+    for dim in (2, 3):
+        A = problems.poisson(dim, 16, periodic=True)
+        h = oracle.Hierarchy(A)
+        assert h.nlev == 1
+        col = h.colours(0)
+        for kind in ("additive", "multiplicative"):
+            c = oracle.Cascade(h, kind, nu=4)
+            lam = c.lam(0) * A.coeff[0][None, :]
+            out[(kind, dim)] = (lam, col)
+    return out
+
+
+# ---------------------------------------------------------------- Table 1
+@pytest.mark.parametrize("row", _table1(), ids=lambda r: f"{r[0]}-{r[1]}d-l{r[2]}")
+def test_table1(periodic_lams, row):
+    kind, dim, l, vals = row
+    lam, col = periodic_lams[(kind, dim)]
+    if kind == "additive":
+        v = lam[l - 1]
+        assert np.ptp(v) < 1e-12, "periodic constant stencil must give a scaled identity"
+        assert round(float(v[0]), 2) == pytest.approx(vals[0], abs=1e-9)
+    else:
+        for k, expect in enumerate(vals):
+            v = lam[l - 1][col == k]
+            assert np.ptp(v) < 1e-12
+            assert round(float(v[0]), 2) == pytest.approx(expect, abs=1e-9)
+
+
+def _fourier_additive(dim, n, nu):
+    """lambda_l for periodic Poisson from the Fourier symbol of the prescaled
+    operator a(theta) = 1 - (1/d) sum cos(theta_j): the Frobenius norm over
+    a periodic grid is n^d times the mean of |symbol|^2 over the discrete
+    frequencies, so lambda_l = <a e^2> / <a^2 e^2> with e = prod(1 - lambda_k a)."""
+    th = 2 * np.pi * np.arange(n) / n
+    grids = np.meshgrid(*([th] * dim), indexing="ij")
+    a = 1.0 - sum(np.cos(g) for g in grids) / dim
+    e = np.ones_like(a)
+    lams = []
+    for _ in range(nu):
+        lam = np.mean(a * e * e) / np.mean(a * a * e * e)
+        lams.append(lam)
+        e = e * (1.0 - lam * a)
+    return np.array(lams)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_additive_fourier_closed_form(periodic_lams, dim):
+    lam, _ = periodic_lams[("additive", dim)]
+    expect = _fourier_additive(dim, 16, 4)
+    np.testing.assert_allclose(lam[:, 0], expect, rtol=1e-12)
+    # first level: the optimal Jacobi damping 4/5 (2D), 6/7 (3D) (Sec. 3.3.1)
+    assert lam[0, 0] == pytest.approx(4 / 5 if dim == 2 else 6 / 7, rel=1e-13)
+    # second level closed forms 6/7 (2D), 15/17 (3D)
+    assert lam[1, 0] == pytest.approx(6 / 7 if dim == 2 else 15 / 17, rel=1e-12)
+
+
+# ------------------------------------------------ brute-force dense setup
+def _small_problem(dim, n, seed):
+    mu = problems.random_coefficients(dim, n, seed)
+    return problems.variable_poisson(mu)
+
+
+CASES = [
+    (2, 7, 1, "additive", 3),
+    (2, 7, 1, "multiplicative", 3),
+    (2, 6, 2, "additive", 2),
+    (2, 6, 2, "multiplicative", 2),
+    (2, 7, 3, "additive", 2),
+    (3, 4, 1, "additive", 2),
+    (3, 4, 1, "multiplicative", 2),
+    (3, 4, 2, "additive", 2),
+]
+
+
+@pytest.mark.parametrize("dim,n,bs,kind,nu", CASES)
+def test_setup_matches_dense_lstsq(dim, n, bs, kind, nu):
+    A = _small_problem(dim, n, seed=11 + n + bs)
+    h = oracle.Hierarchy(A, bs=bs, max_levels=1)
+    c = oracle.Cascade(h, kind, nu=nu)
+    Ad = dense_ref.dense_from_stencil(A)
+    blocks, par = dense_ref.block_partition(A.n, dim, bs)
+    bptr, bidx, bpar = h.blocks(0)
+    # block partition and colours bit-exact
+    assert len(blocks) == len(bptr) - 1
+    for b, m in enumerate(blocks):
+        assert np.array_equal(bidx[bptr[b]:bptr[b + 1]], m)
+    assert np.array_equal(bpar, par)
+    lam_t, lam_u, Es = dense_ref.dense_cascade(Ad, blocks, par, kind, nu)
+    lam = c.lam(0)
+    ncol = 2 if kind == "multiplicative" else 1
+    for l in range(nu):
+        for b, rows in enumerate(blocks):
+            k = par[b] if ncol == 2 else 0
+            nb = len(rows)
+            got = lam[l, int(np.sum([len(r) ** 2 for r in blocks[:b]])):][: nb * nb].reshape(nb, nb)
+            ref = lam_u[l][k][np.ix_(rows, rows)]
+            np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
+    # Frobenius norms of E after each step agree and never increase (Lambda = 0 is feasible)
+    ef = c.efrob(0)
+    dense_norms = np.array([np.linalg.norm(E) for E in Es])
+    np.testing.assert_allclose(ef, dense_norms, rtol=1e-10)
+    assert np.all(np.diff(ef) <= 1e-12 * ef[:-1])
+
+
+@pytest.mark.parametrize("kind", ["additive", "multiplicative"])
+def test_first_order_optimality_and_perturbation(kind):
+    """(E_b - Lam_b R_b) R_b^T = 0, and random perturbations of any block
+    never lower ||(I - Lam A~) E~||_F."""
+    rng = np.random.default_rng(5)
+    A = _small_problem(2, 6, seed=3)
+    h = oracle.Hierarchy(A, bs=2, max_levels=1)
+    c = oracle.Cascade(h, kind, nu=2)
+    Ad = dense_ref.dense_from_stencil(A)
+    w = 1.0 / np.sqrt(np.diag(Ad))
+    At = w[:, None] * Ad * w[None, :]
+    blocks, par = dense_ref.block_partition(A.n, 2, 2)
+    lam = c.lam(0)
+    offs = np.cumsum([0] + [len(r) ** 2 for r in blocks])
+    E = np.eye(A.N)
+    ncol = 2 if kind == "multiplicative" else 1
+    for l in range(2):
+        for k in range(ncol):
+            AE = At @ E
+            Lt = np.zeros_like(E)
+            for b, rows in enumerate(blocks):
+                if ncol == 2 and par[b] != k:
+                    continue
+                nb = len(rows)
+                Lt[np.ix_(rows, rows)] = lam[l, offs[b]:offs[b + 1]].reshape(nb, nb) / np.outer(w[rows], w[rows])
+            sel = np.zeros(A.N, bool)
+            for b, rows in enumerate(blocks):
+                if ncol == 1 or par[b] == k:
+                    sel[rows] = True
+            F = E - Lt @ AE
+            F[~sel] = E[~sel]
+            for b, rows in enumerate(blocks):
+                if ncol == 2 and par[b] != k:
+                    continue
+                grad = F[rows] @ AE[rows].T
+                assert np.abs(grad).max() <= 1e-11 * max(1.0, np.abs(F[rows]).max() * np.abs(AE[rows]).max())
+            base = np.linalg.norm(F)
+            for _ in range(5):
+                P = Lt + 1e-3 * rng.standard_normal(Lt.shape) * (Lt != 0)
+                Fp = E - P @ AE
+                Fp[~sel] = E[~sel]
+                assert np.linalg.norm(Fp) >= base * (1 - 1e-14)
+            E = F
+
+
+def test_truncation_matches_dense():
+    A = _small_problem(2, 7, seed=21)
+    h = oracle.Hierarchy(A, max_levels=1)
+    Ad = dense_ref.dense_from_stencil(A)
+    blocks, par = dense_ref.block_partition(A.n, 2, 1)
+    for alpha in (3, 5):
+        c = oracle.Cascade(h, "additive", nu=3, alpha=alpha)
+        _, lam_u, _ = dense_ref.dense_cascade(Ad, blocks, par, "additive", 3, alpha=alpha)
+        lam = c.lam(0)
+        for l in range(3):
+            np.testing.assert_allclose(lam[l], np.diag(lam_u[l][0]), rtol=1e-9)
+    # alpha larger than any fill-in equals the exact cascade
+    c_big = oracle.Cascade(h, "additive", nu=3, alpha=1000)
+    c_ex = oracle.Cascade(h, "additive", nu=3)
+    np.testing.assert_array_equal(c_big.lam(0), c_ex.lam(0))
+
+
+def test_scale_invariance_of_setup():
+    """Prescaling makes Lambda(cA) = Lambda(A)/c and
+    Lambda(DAD) = D^-1 Lambda(A) D^-1 (Sec. 2.3, footnote)."""
+    A = _small_problem(2, 6, seed=8)
+    h = oracle.Hierarchy(A, max_levels=1)
+    lam = oracle.Cascade(h, "multiplicative", nu=3).lam(0)
+    A2 = problems.Stencil(A.dim, A.n, A.offsets, 7.5 * A.coeff)
+    lam2 = oracle.Cascade(oracle.Hierarchy(A2, max_levels=1), "multiplicative", nu=3).lam(0)
+    np.testing.assert_allclose(lam2, lam / 7.5, rtol=1e-12)
+    d = 10.0 ** problems.uniform(77, A.N, -1, 1)
+    Ad = dense_ref.dense_from_stencil(A)
+    coeff = np.zeros_like(A.coeff)
+    nx = A.n[0]
+    for s, (dx, dy, _) in enumerate(A.offsets):
+        for i in range(A.N):
+            ix, iy = i % nx, i // nx
+            jx, jy = ix + dx, iy + dy
+            if 0 <= jx < nx and 0 <= jy < A.n[1]:
+                coeff[s, i] = d[i] * A.coeff[s, i] * d[jx + nx * jy]
+    A3 = problems.Stencil(A.dim, A.n, A.offsets, coeff)
+    lam3 = oracle.Cascade(oracle.Hierarchy(A3, max_levels=1), "multiplicative", nu=3).lam(0)
+    np.testing.assert_allclose(lam3, lam / (d * d)[None, :], rtol=1e-11)
+    del Ad
+
+
+# ------------------------------------------------------------ smoothers
+def _dense_lams(c, h, blocks, l=0):
+    lam = c.lam(l)
+    N = h.N(l)
+    offs = np.cumsum([0] + [len(r) ** 2 for r in blocks])
+    out = []
+    for s in range(c.nu):
+        L = np.zeros((N, N))
+        for b, rows in enumerate(blocks):
+            nb = len(rows)
+            L[np.ix_(rows, rows)] = lam[s, offs[b]:offs[b + 1]].reshape(nb, nb)
+        out.append(L)
+    return out
+
+
+@pytest.mark.parametrize("kind,bs", [("additive", 1), ("additive", 2), ("multiplicative", 1), ("multiplicative", 2)])
+def test_smoother_propagators(kind, bs):
+    """forward: x0 -> (I - L_nu A)...(I - L_1 A) x0 for b = 0; reverse:
+    (I - L_1^T A)...(I - L_nu^T A) x0 (SM Sec. 3); multiplicative factors are
+    flattened over colours.  The exact solution is a fixed point."""
+    A = _small_problem(2, 6, seed=31)
+    h = oracle.Hierarchy(A, bs=bs, max_levels=1)
+    c = oracle.Cascade(h, kind, nu=3)
+    Ad = dense_ref.dense_from_stencil(A)
+    blocks, par = dense_ref.block_partition(A.n, 2, bs)
+    Ls = _dense_lams(c, h, blocks)
+    factors = []
+    for s in range(3):
+        if kind == "additive":
+            factors.append(Ls[s])
+        else:
+            for k in range(2):
+                mask = np.zeros(A.N)
+                for b, rows in enumerate(blocks):
+                    if par[b] == k:
+                        mask[rows] = 1.0
+                factors.append(Ls[s] * mask[:, None])
+    I = np.eye(A.N)
+    Mf = I.copy()
+    for F in factors:
+        Mf = (I - F @ Ad) @ Mf
+    Mr = I.copy()
+    for F in reversed(factors):
+        Mr = (I - F.T @ Ad) @ Mr
+    x0 = problems.uniform(4, A.N)
+    zero = np.zeros(A.N)
+    np.testing.assert_allclose(oracle.smooth(h, c, 0, zero, x0), Mf @ x0, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(oracle.smooth(h, c, 0, zero, x0, reverse=True), Mr @ x0, rtol=1e-12, atol=1e-13)
+    xs = problems.uniform(5, A.N)
+    b = Ad @ xs
+    np.testing.assert_allclose(oracle.smooth(h, c, 0, b, xs), xs, rtol=1e-12)
+    np.testing.assert_allclose(oracle.smooth(h, c, 0, b, xs, reverse=True), xs, rtol=1e-12)
+
+
+def test_damped_jacobi_and_redblack_gs():
+    """Lambda = omega blockdiag(A)^-1 reproduces damped Jacobi (Sec. 2) and,
+    with colours, red-black Gauss-Seidel (Sec. 2.2)."""
+    A = _small_problem(2, 8, seed=41)
+    h = oracle.Hierarchy(A, max_levels=1)
+    Ad = dense_ref.dense_from_stencil(A)
+    D = np.diag(Ad)
+    b = problems.uniform(6, A.N)
+    x0 = problems.uniform(7, A.N)
+    om = 0.8
+    cj = oracle.Cascade.empty(h, "additive", nu=3)
+    cj.set_lam(0, np.tile(om / D, (3, 1)))
+    x = x0.copy()
+    for _ in range(3):
+        x = x - om * (Ad @ x - b) / D
+    np.testing.assert_allclose(oracle.smooth(h, cj, 0, b, x0), x, rtol=1e-12)
+    cg = oracle.Cascade.empty(h, "multiplicative", nu=2)
+    cg.set_lam(0, np.tile(1.0 / D, (2, 1)))
+    col = h.colours(0)
+    x = x0.copy()
+    for _ in range(2):
+        for k in (0, 1):
+            for i in np.nonzero(col == k)[0]:  # in-place sweep over one colour
+                x[i] += (b[i] - Ad[i] @ x) / D[i]
+    np.testing.assert_allclose(oracle.smooth(h, cg, 0, b, x0), x, rtol=1e-12)
+
+
+# ----------------------------------------------------- hierarchy and cycle
+@pytest.mark.parametrize("dim,n", [(2, 8), (2, 9), (3, 6), (3, 5)])
+def test_galerkin_matches_dense_rap(dim, n):
+    A = _small_problem(dim, n, seed=51 + n)
+    h = oracle.Hierarchy(A, max_levels=2)
+    assert h.nlev == 2
+    nc = tuple(v // 2 for v in A.n[:dim]) + ((1,) if dim == 2 else ())
+    assert h.dims(1) == nc
+    P = dense_ref.prolongation(A.n, dim)
+    Ad = dense_ref.dense_from_stencil(A)
+    Ac = (P.T @ Ad @ P) / 2 ** dim
+    np.testing.assert_allclose(h.dense(1), Ac, rtol=1e-12, atol=1e-12 * np.abs(Ac).max())
+    # restriction and prolongation steps
+    r = problems.uniform(9, A.N)
+    np.testing.assert_allclose(h.restrict(0, r), P.T @ r / 2 ** dim, rtol=1e-13, atol=1e-15)
+    xc = problems.uniform(10, Ac.shape[0])
+    x = problems.uniform(12, A.N)
+    np.testing.assert_allclose(h.prolong_correct(0, xc, x), x - P @ xc, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_galerkin_poisson_stencil_closed_form(dim):
+    """Bilinear / trilinear Galerkin coarsening of the 5-/7-point Laplacian
+    gives a 9-/27-point operator (SM Sec. 4.1) whose interior stencil is the
+    tensor form  (1/(2h)^2) * sum_j [T_j x M x M]  with the 1D coarse
+    stiffness T = (1/2)[-1 2 -1]... written out as products of the 1D
+    Galerkin pieces of the second difference (K) and of the identity (M)."""
+    n = 16 if dim == 2 else 8
+    A = problems.poisson(dim, n)
+    h = oracle.Hierarchy(A, max_levels=2)
+    hh = 1.0 / (n + 1)
+    # 1D pieces: R = P^T/2 applied to the fine 1D second difference (1/h^2)[-1 2 -1]
+    # and to the fine identity give K = (1/(4h^2))[-1 2 -1] and M = [1/8 3/4 1/8].
+    K = np.array([-1.0, 2.0, -1.0]) / (4 * hh * hh)
+    M = np.array([1 / 8, 3 / 4, 1 / 8])
+    if dim == 2:
+        st = np.einsum("i,j->ji", K, M) + np.einsum("i,j->ji", M, K)
+    else:
+        st = (np.einsum("i,j,k->kji", K, M, M) + np.einsum("i,j,k->kji", M, K, M)
+              + np.einsum("i,j,k->kji", M, M, K))
+    Ac = h.dense(1)
+    nc = h.dims(1)
+    c = [v // 2 for v in nc[:dim]]
+    ic = c[0] + nc[0] * (c[1] + nc[1] * (c[2] if dim == 3 else 0))
+    for idx in np.ndindex(*([3] * dim)):
+        d = [i - 1 for i in idx[::-1]]  # (dx, dy[, dz])
+        jc = (c[0] + d[0]) + nc[0] * ((c[1] + d[1]) + nc[1] * ((c[2] + d[2]) if dim == 3 else 0))
+        assert Ac[ic, jc] == pytest.approx(st[idx], rel=1e-12, abs=1e-9)
+    assert np.count_nonzero(np.abs(Ac[ic]) > 0) == 3 ** dim
+
+
+def test_hierarchy_dims_and_colours():
+    A = problems.poisson(2, 64)
+    h = oracle.Hierarchy(A)
+    assert [h.dims(l)[0] for l in range(h.nlev)] == [64, 32, 16, 8, 4]
+    h = oracle.Hierarchy(problems.poisson(2, 37))
+    assert [h.dims(l)[0] for l in range(h.nlev)] == [37, 18, 9, 4]
+    h = oracle.Hierarchy(problems.poisson(3, 9))
+    assert [h.dims(l) for l in range(h.nlev)] == [(9, 9, 9), (4, 4, 4)]
+    col = h.colours(0)
+    ix, iy, iz = np.meshgrid(np.arange(9), np.arange(9), np.arange(9), indexing="ij")
+    expect = ((ix + 1) + (iy + 1) + (iz + 1)) % 2
+    assert np.array_equal(col, expect.transpose(2, 1, 0).ravel())
+
+
+def test_coarse_solve_is_direct():
+    A = _small_problem(2, 4, seed=61)
+    h = oracle.Hierarchy(A)
+    assert h.nlev == 1
+    b = problems.uniform(13, A.N)
+    np.testing.assert_allclose(h.coarse_solve(b), np.linalg.solve(dense_ref.dense_from_stencil(A), b), rtol=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["additive", "multiplicative"])
+def test_vcycle_symmetry_rf(kind):
+    """RF gives V = V^T for symmetric A (SM Sec. 3); FF in general does not."""
+    A = _small_problem(2, 12, seed=71)
+    h = oracle.Hierarchy(A)
+    c = oracle.Cascade(h, kind, nu=2)
+    N = A.N
+    Vrf = np.zeros((N, N))
+    Vff = np.zeros((N, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        Vrf[:, j] = oracle.vcycle(h, c, e, rf=True)
+        Vff[:, j] = oracle.vcycle(h, c, e, rf=False)
+    scale = np.abs(Vrf).max()
+    assert np.abs(Vrf - Vrf.T).max() <= 1e-13 * scale * 10
+    assert np.abs(Vff - Vff.T).max() > 1e-6 * scale
+
+
+def test_restriction_scale_invariance():
+    """R = P^T (Alg. 1 as printed) and R = 2^{-d} P^T (SM Sec. 4.1) give the
+    same V-cycle iterates, since Lambda(cA) = Lambda(A)/c."""
+    A = _small_problem(2, 16, seed=81)
+    b = problems.rhs(A.N, 14)
+    xs = []
+    for mode in (0, 1):
+        h = oracle.Hierarchy(A, rscale_mode=mode)
+        c = oracle.Cascade(h, "multiplicative", nu=2)
+        x = oracle.vcycle(h, c, b, mu_pre=2, mu_post=2, rf=True)
+        xs.append(oracle.vcycle(h, c, b, x, mu_pre=2, mu_post=2, rf=True))
+    np.testing.assert_allclose(xs[0], xs[1], rtol=1e-11, atol=1e-14 * np.abs(xs[0]).max())
+
+
+@pytest.mark.parametrize("dim,n,kind,method", [
+    (2, 31, "additive", "stationary"), (2, 31, "multiplicative", "gmres"),
+    (3, 15, "additive", "gmres"), (3, 15, "multiplicative", "stationary")])
+def test_manufactured_convergence(dim, n, kind, method):
+    A = problems.poisson(dim, n)
+    h = oracle.Hierarchy(A)
+    c = oracle.Cascade(h, kind, nu=3)
+    xs = problems.uniform(15, A.N)
+    Ad = None
+    # b = A x* by the stencil definition (independent of the oracle's CSR)
+    b = np.zeros(A.N)
+    nx, ny, nz = A.n
+    X = xs.reshape(nz, ny, nx)
+    for s, (dx, dy, dz) in enumerate(A.offsets):
+        sh = np.zeros_like(X)
+        src = X[max(dz, 0):nz + min(dz, 0), max(dy, 0):ny + min(dy, 0), max(dx, 0):nx + min(dx, 0)]
+        sh[max(-dz, 0):nz + min(-dz, 0), max(-dy, 0):ny + min(-dy, 0), max(-dx, 0):nx + min(-dx, 0)] = src
+        b += A.coeff[s] * sh.ravel()
+    x, it, hist, fin = oracle.solve(h, c, b, method=method, mu_pre=1, mu_post=1, rf=True, tol=1e-10)
+    assert it > 0 and fin <= 1e-10
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-8
+    rho = oracle.rho_from_history(hist)
+    assert rho < 0.2
+    del Ad
+
+
+def test_gmres_finite_termination():
+    A = _small_problem(2, 3, seed=91)
+    h = oracle.Hierarchy(A, max_levels=1)
+    c = oracle.Cascade(h, "additive", nu=1)
+    b = problems.uniform(16, A.N)
+    # single-level hierarchy: V is the direct solve, so GMRES ends after one step
+    x, it, hist, fin = oracle.solve(h, c, b, method="gmres", tol=1e-12)
+    assert it == 1 and fin < 1e-12
+
+
+def test_metrics():
+    r = 0.3 ** np.arange(8) * 2.0
+    assert oracle.rho_from_history(r) == pytest.approx(0.3, rel=1e-12)
+    assert oracle.eta(0.1) == pytest.approx(1.0)
+    assert oracle.eta(0.01) == pytest.approx(0.5)
+    # C_d(nu, eta) = eta (1 + (2 nu + 1) / (1 - 2^-d)) (eq. cost)
+    assert oracle.cost_cd(2, 1, 1.0) == pytest.approx(1 + 3 / 0.75)
+    assert oracle.cost_cd(3, 2, 0.5) == pytest.approx(0.5 * (1 + 5 / 0.875))
