@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Time to 1e-10 relative residual for cascading-smoother multigrid.
+
+Workload (default): 3D Poisson, 7-point FD on a 256^3 interior grid,
+homogeneous Dirichlet, RHS ~ U[-1,1] (seeded); Galerkin hierarchy down to
+4^3; additive cascade of depth 3; V(2,2) with reverse pre- / forward
+post-smoothing.  One step = setup_hierarchy + setup_cascade + solve from
+x = 0 until ||b - A x|| / ||b|| <= 1e-10, inputs resident in HBM.
+
+The chosen form (``value``) runs the cycle in FP32 inside FP64 iterative
+refinement; the plain FP64 form (stationary V-cycle iteration) is timed
+beside it.  Also reported: the sweep kernel's achieved HBM bandwidth
+against the measured copy peak, the same step end to end through the C ABI
+with host buffers, and the FP64 CPU oracle on a bounded sample.
+
+``--impl reference`` times the oracle alone (the baseline arm).
+Multi-GPU (torchrun): independent replicas, one problem per rank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-10 residual & smoother GB/s vs HBM peak: chosen vs plain FP64"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+FALLBACK_HBM = 6800.0
+
+
+def args_():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=256, help="interior nodes per side")
+    p.add_argument("--kind", default="additive", choices=["additive", "multiplicative"])
+    p.add_argument("--nu", type=int, default=3)
+    p.add_argument("--mu", type=int, default=2)
+    p.add_argument("--order", default="RF")
+    p.add_argument("--cpu-n", type=int, default=64, help="side of the oracle's bounded sample")
+    p.add_argument("--no-extras", action="store_true", help="time the chosen form only")
+    return p.parse_args()
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2606_12577_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    try:
+        with open(PEAKS) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            t = [v.strip() for v in line.split(",")]
+            if len(t) >= 9:
+                rows.append(t)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------- the oracle
+def oracle_step(n, kind, nu, mu, order):
+    import oracle
+    import problems
+    A, b = problems.poisson3d(n)
+    t0 = time.perf_counter()
+    h = oracle.Hierarchy(A)
+    c = oracle.Cascade(h, kind, nu=nu)
+    x, it, hist, fin = oracle.solve(h, c, b, method="stationary", mu_pre=mu, mu_post=mu, rf=order == "RF",
+                                    tol=1e-10)
+    dt = time.perf_counter() - t0
+    return dt, it, fin
+
+
+def cpu_baseline(a, n_full):
+    dt, it, fin = oracle_step(a.cpu_n, a.kind, a.nu, a.mu, a.order)
+    scale = (n_full / a.cpu_n) ** 3
+    return {"value": dt * 1e3 * scale, "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, same problem family at {a.cpu_n}^3 (setup + stationary solve, "
+                      f"{it} cycles, {dt:.2f} s), scaled by N_full/N_sample = {scale:.0f} (O(N) method)"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = config(a)
+    for _ in range(a.warmup):
+        oracle_step(a.cpu_n, a.kind, a.nu, a.mu, a.order)
+    ts = []
+    for _ in range(a.steps):
+        dt, it, fin = oracle_step(a.cpu_n, a.kind, a.nu, a.mu, a.order)
+        ts.append(dt)
+    scale = (a.n / a.cpu_n) ** 3
+    v = statistics.mean(ts) * 1e3 * scale
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: the FP64 oracle on the same problem at {a.cpu_n}^3 "
+                                       f"(setup + stationary solve to 1e-10), time scaled by {scale:.0f} = N ratio"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config(a):
+    return {"workload": f"3D Poisson 7-point FD {a.n}^3 interior, Dirichlet, RHS U[-1,1] seed 2002; "
+                        f"{a.kind} cascade nu={a.nu}, V({a.mu},{a.mu}) {a.order}, Galerkin to 4^3, "
+                        f"setup + solve to 1e-10",
+            "global_batch": 1, "unknowns": a.n ** 3, "parallelism": f"replicas x{a.gpus}",
+            "l2": "inputs larger than L2 (A alone is 0.94 GB)"}
+
+
+# ------------------------------------------------------------------- ours
+def main():
+    a = args_()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import __graft_entry__ as ge
+    if rank == 0:
+        ge.build()
+    if world > 1:
+        dist.barrier()
+    ge.build()
+    import paper_2606_12577_gb300 as cmg
+    import problems
+
+    A, b = problems.poisson3d(a.n)
+    coeff = torch.tensor(A.coeff, dtype=torch.float64, device=dev)
+    bd = torch.tensor(b, dtype=torch.float64, device=dev)
+    mu = a.mu
+
+    def step(precision, method, lowp, out=None):
+        h = cmg.setup_hierarchy(A.dim, A.n, A.offsets, coeff)
+        c = cmg.setup_cascade(h, a.kind, nu=a.nu, lowp=lowp)
+        x = torch.zeros(A.N, dtype=torch.float64, device=dev)
+        info = cmg.solve(h, c, bd, x, method=method, precision=precision, tol=1e-10, mu_pre=mu, mu_post=mu,
+                         order=a.order)
+        if out is not None:
+            out.append(info)
+        return h, c, x
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        barrier()
+        torch.cuda.synchronize()
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    infos = []
+    # ---- chosen form: FP32 cycle in FP64 iterative refinement
+    for _ in range(a.warmup):
+        step("fp32", "refine", True)
+    clk = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = cmg.kernel_launches()
+    clk.start()
+    ms = timed(lambda: step("fp32", "refine", True, infos), a.steps, 0)
+    clocks = clk.stop()
+    launches = cmg.kernel_launches() - l0
+    it_chosen = infos[-1].iterations
+    res_chosen = infos[-1].final_rel_residual
+
+    result = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+              "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+              "dtype": "f32 cycle + f64 refinement", "data": "synthetic", "config": config(a),
+              "iterations": it_chosen, "final_rel_residual": res_chosen, "gpu_launches": launches,
+              "clocks": clocks, "solves_per_s_all_gpus": world * 1e3 / ms}
+
+    if not a.no_extras:
+        # split: setup vs solve (events around each phase, one extra run)
+        torch.cuda.synchronize()
+        s = torch.cuda.current_stream()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(s)
+        h = cmg.setup_hierarchy(A.dim, A.n, A.offsets, coeff)
+        c = cmg.setup_cascade(h, a.kind, nu=a.nu, lowp=True)
+        ev[1].record(s)
+        x = torch.zeros(A.N, dtype=torch.float64, device=dev)
+        cmg.solve(h, c, bd, x, method="refine", precision="fp32", tol=1e-10, mu_pre=mu, mu_post=mu, order=a.order)
+        ev[2].record(s)
+        torch.cuda.synchronize()
+        result["setup_ms"] = ev[0].elapsed_time(ev[1])
+        result["solve_ms"] = ev[1].elapsed_time(ev[2])
+        # ---- roofline of the sweep kernel (FP32 additive step, finest level)
+        N = A.N
+        lvl = cmg.query_level(h, 0)
+        nst = lvl["nst"]
+        xb = [torch.rand(N, device=dev, dtype=torch.float32) for _ in range(2)]
+        b32 = torch.rand(N, device=dev, dtype=torch.float32)
+        reps = 20
+        for k in range(3):
+            cmg.sweep(h, c, 0, k % a.nu, b32, xb[k % 2], xb[(k + 1) % 2], colour=-1 if a.kind == "additive" else 0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for k in range(reps):
+            cmg.sweep(h, c, 0, k % a.nu, b32, xb[k % 2], xb[(k + 1) % 2], colour=-1 if a.kind == "additive" else 0)
+        e1.record(s)
+        torch.cuda.synchronize()
+        t_sweep = e0.elapsed_time(e1) / reps * 1e-3
+        bytes_sweep = (nst + 4) * 4 * N  # A (nst), Lambda, b, x read, x written: FP32
+        peak, src = peaks()
+        achieved = bytes_sweep / t_sweep / 1e9
+        traffic = None
+        try:
+            with open(TRAFFIC) as f:
+                tr = json.load(f)
+            if tr.get("csrc_hash") == csrc_hash() and tr.get("n") == a.n:
+                traffic = tr["sweep_fp32_bytes_per_launch"]
+        except Exception:
+            traffic = None
+        result["roofline"] = {"bound": "hbm", "kernel": "k_sweep<3,STAR,float> (additive step, finest level)",
+                              "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                              "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+                              "traffic": traffic, "algorithmic_bytes_per_launch": bytes_sweep,
+                              "launch_ms": t_sweep * 1e3}
+        result["smoother_gbs"] = achieved
+        del h, c, x
+        torch.cuda.empty_cache()
+        # ---- plain FP64 path (stationary V-cycle iteration)
+        pinfo = []
+        ms64 = timed(lambda: step("fp64", "stationary", False, pinfo), max(2, a.steps // 2), 1)
+        result["plain_fp64"] = {"ms_per_step": ms64, "iterations": pinfo[-1].iterations,
+                                "final_rel_residual": pinfo[-1].final_rel_residual,
+                                "speedup_chosen_vs_plain": ms64 / ms}
+        # ---- end to end through the C ABI with host buffers (pinned)
+        pin_coeff = torch.tensor(A.coeff, dtype=torch.float64).pin_memory()
+        pin_b = torch.tensor(b, dtype=torch.float64).pin_memory()
+        pin_x = torch.zeros(A.N, dtype=torch.float64).pin_memory()
+        cn = pin_coeff.numpy()
+
+        def e2e_step():
+            h2 = cmg.setup_hierarchy(A.dim, A.n, A.offsets, cn)
+            c2 = cmg.setup_cascade(h2, a.kind, nu=a.nu, lowp=True)
+            pin_x.zero_()
+            cmg.solve(h2, c2, pin_b, pin_x, method="refine", precision="fp32", tol=1e-10, mu_pre=mu, mu_post=mu,
+                      order=a.order, host_buffers=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        ne = max(2, a.steps // 2)
+        for _ in range(ne):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / ne
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        result["e2e"] = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(A.coeff.nbytes + 2 * 8 * A.N),
+                         "d2h_bytes_per_step": int(8 * A.N)}
+        if rank == 0 and world == 1:
+            result["cpu_baseline"] = cpu_baseline(a, a.n)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * cascade_mg.h -- C ABI of the GB300 (sm_103a) cascading-smoother multigrid
+ * library.
+ *
+ * The library solves A x = b for an operator given on a structured 2D/3D
+ * grid of interior nodes (homogeneous Dirichlet boundary nodes eliminated),
+ * with a geometric V-cycle (Algorithm 1) whose smoother is a cascading
+ * smoother (Sec. 2): an ordered sequence of block-diagonal steps
+ *     x_l = x_{l-1} - Lambda_l (A x_{l-1} - b),   l = 1..nu      (eq. fwda)
+ * (multiplicative form: one step per colour, eq. fwdm), each Lambda_l the
+ * block-diagonal minimiser of || (I - Lambda A) E_{l-1} ||_F (Sec. 2.1-2.2,
+ * Algorithm 2), built on the prescaled operator W A W, W = diag(A_ii^-1/2)
+ * (Sec. 2.3.1).
+ *
+ * Conventions for every entry point:
+ *   - Return value: CS_OK (0) or a negative cs_status; on error
+ *     cs_last_error() returns a message (thread-local, valid until the next
+ *     call on the same thread).  No C++ exception crosses this boundary.
+ *   - Vectors are FP64, one value per interior node, node (ix,iy,iz) at index
+ *     ix + nx*(iy + ny*iz) (x fastest).  Unless a call says otherwise they
+ *     are DEVICE pointers owned by the caller.
+ *   - Handles own all their device memory (allocated at setup); the cycle and
+ *     solve calls allocate nothing.  A handle may be used by one host thread
+ *     at a time.  A cascade refers to its hierarchy, which must outlive it.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t; NULL = the
+ *     legacy default stream), except where a call returns host data (exports,
+ *     cs_solve's info): those synchronise the stream before returning.
+ */
+#ifndef CASCADE_MG_H
+#define CASCADE_MG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int cs_status;
+enum {
+    CS_OK = 0,
+    CS_ERR_ARG = -1,         /* invalid argument (null pointer, bad size, non-positive diagonal) */
+    CS_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+    CS_ERR_NOMEM = -3,       /* device allocation failed */
+    CS_ERR_SINGULAR = -4,    /* the coarsest-level matrix could not be factorised */
+    CS_ERR_DIVERGED = -5,    /* residual became non-finite or grew > 1e3 x its start */
+    CS_ERR_TIMEOUT = -6,     /* a bounded device-side wait expired */
+    CS_ERR_UNSUPPORTED = -7, /* option not implemented for this operator */
+    CS_ERR_NOTCONV = -8      /* maxit reached before the tolerance */
+};
+
+typedef void *cs_stream; /* cudaStream_t */
+typedef struct cs_hierarchy cs_hierarchy;
+typedef struct cs_cascade cs_cascade;
+
+/* ------------------------------------------------------------- operator */
+/* A structured-grid operator in stencil form (Sec. 2: the block-partitioned
+ * A x = b; Sec. 3.3.1: FD Poisson).  coeff[s*N + i] couples unknown i to the
+ * node at i + off[s]; it must be zero where that node lies outside the grid
+ * (a Dirichlet node).  Offsets are in {-1,0,1}^dim and (0,0,0) must be
+ * present.  With periodic != 0 neighbours wrap around (accepted by
+ * cs_setup_hierarchy only with max_levels == 1: used to check the setup
+ * against the constant-coefficient coefficients of Table 1). */
+typedef struct {
+    int dim;           /* 2 or 3 */
+    int n[3];          /* interior nodes per side; n[2] = 1 when dim == 2 */
+    int nst;           /* stencil entries, 1..27 */
+    int off[27][3];    /* (dx, dy, dz) of entry s */
+    const double *coeff; /* [nst][N], N = n[0]*n[1]*n[2]; device, or host if coeff_on_host */
+    int coeff_on_host; /* 1: coeff is a host pointer (copied during setup) */
+    int periodic;
+} cs_stencil;
+
+/* ------------------------------------------------------------ hierarchy */
+typedef struct {
+    int coarse_max; /* stop coarsening when every side is <= coarse_max (default 4) */
+    int max_levels; /* 0 = no limit */
+    int block;      /* block edge in nodes (1 = point blocks; >1 unsupported for now) */
+} cs_hierarchy_opts;
+
+/* Geometric hierarchy (Sec. 2.4): coarse interior nodes are the fine nodes
+ * with even 1-based index on every axis (so n -> floor(n/2)); interpolation
+ * P is bilinear/trilinear on that node set and the coarse operator is the
+ * Galerkin product A_2h = R A_h P with R = 2^-dim P^T (SM Sec. 4.1), a
+ * 9-point (2D) / 27-point (3D) stencil.  The coarsest operator is factorised
+ * densely in FP64 for the bottom-level direct solve (Algorithm 1).
+ * A0: the finest operator (its coefficients are copied).  opts may be NULL
+ * (defaults).  On success *out receives a handle that cs_destroy_hierarchy
+ * frees.  Errors: CS_ERR_ARG (bad stencil), CS_ERR_NOMEM, CS_ERR_SINGULAR,
+ * CS_ERR_CUDA, CS_ERR_UNSUPPORTED (block > 1). */
+cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts, cs_stream stream,
+                             cs_hierarchy **out);
+
+/* -------------------------------------------------------------- cascade */
+enum { CS_ADDITIVE = 0, CS_MULTIPLICATIVE = 1 };
+enum { CS_FP64 = 0, CS_FP32 = 1 };
+
+typedef struct {
+    int kind;      /* CS_ADDITIVE (Sec. 2.1) or CS_MULTIPLICATIVE (Sec. 2.2, red-black) */
+    int nu;        /* depth, 1..8 */
+    int prescale;  /* 1: elliptic prescaling W = diag(A_ii^-1/2) (Sec. 2.3.1); 0: none */
+    int alpha;     /* residual truncation (Algorithm 2); 0 = none (only 0 supported) */
+    int lowp;      /* 1: also keep FP32 copies of the level operators and Lambda for
+                      CS_FP32 cycles (iterative refinement) */
+} cs_cascade_opts;
+
+/* Build the cascade (Lambda_l, l = 1..nu; multiplicative: Lambda_{l,k},
+ * k = red, black) on every level that has a smoother (all but the
+ * coarsest), by the per-block least-squares problems of Algorithm 2 / the
+ * SM algorithm in FP64 on the device.  Red = nodes with an even 1-based
+ * index sum.  Multiplicative steps read the residual E_{l,k-1} of the
+ * previous colour (snapshot semantics, exact also where red-black is not a
+ * graph colouring, e.g. on 27-point Galerkin levels).
+ * Errors: CS_ERR_ARG (nu out of range, non-positive diagonal under
+ * prescaling), CS_ERR_NOMEM, CS_ERR_UNSUPPORTED (alpha > 0, periodic wrap
+ * that aliases the fill-in: side <= 2 * fill radius), CS_ERR_CUDA. */
+cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *opts, cs_stream stream,
+                           cs_cascade **out);
+
+/* --------------------------------------------------------------- cycles */
+enum { CS_FF = 0, CS_RF = 1 };
+
+typedef struct {
+    int mu_pre;    /* applications of the cascade before the coarse correction */
+    int mu_post;   /* ... and after */
+    int order;     /* CS_RF: reverse pre-smoother, forward post (symmetric V, SM Sec. 3);
+                      CS_FF: forward both (Sec. 2.4) */
+    int precision; /* CS_FP64, or CS_FP32 (needs lowp; coarsest solve stays FP64) */
+} cs_vcycle_opts;
+
+/* One V-cycle (Algorithm 1) on the finest level: x <- V(x, b), i.e.
+ * x + V0 (b - A x) with V0 the zero-initial-guess cycle.  b, x: device,
+ * N doubles each; x is read and overwritten. */
+cs_status cs_vcycle(const cs_hierarchy *h, cs_cascade *c, const cs_vcycle_opts *opts, const double *b,
+                    double *x, cs_stream stream);
+
+/* ---------------------------------------------------------- level steps */
+/* One application of the depth-nu cascade on `level` (forward: eq. fwda /
+ * fwdm; reverse != 0: the reverse application eq. fwdar / fwdmr, read as
+ * Lambda_{nu-l+1}^T with the colour order reversed).  b, x: device vectors
+ * of that level (N_level doubles); x is updated in place. */
+cs_status cs_smooth(const cs_hierarchy *h, cs_cascade *c, int level, int reverse, const double *b,
+                    double *x, cs_stream stream);
+
+/* One cascade step on `level` (a single kernel launch):
+ *     out = x - Lambda_{step+1[, colour]} (A x - b)
+ * over every node (colour = -1, additive step of eq. fwda) or over the nodes
+ * of one colour (colour = 0 red / 1 black, eq. fwdm; other nodes are copied
+ * to out unless out == x).  precision CS_FP64: b, x, out are double
+ * vectors; CS_FP32: float vectors (needs lowp).  out == x is allowed only
+ * for a colour step on a 5/7-point level (red-black is then a graph
+ * colouring); otherwise out must not alias x. */
+cs_status cs_sweep(const cs_hierarchy *h, cs_cascade *c, int level, int step, int colour, int precision,
+                   const void *b, const void *x, void *out, cs_stream stream);
+
+/* rc = R (A x - b) on `level` (Algorithm 1's restricted residual; R =
+ * 2^-dim P^T).  rc has N_{level+1} doubles. */
+cs_status cs_residual_restrict(const cs_hierarchy *h, int level, const double *b, const double *x,
+                               double *rc, cs_stream stream);
+
+/* x <- x - P xc on `level` (Algorithm 1's interpolate-and-correct). */
+cs_status cs_prolong_correct(const cs_hierarchy *h, int level, const double *xc, double *x,
+                             cs_stream stream);
+
+/* x = A_c^-1 b on the coarsest level (bottom-level direct solve, FP64). */
+cs_status cs_coarse_solve(const cs_hierarchy *h, const double *b, double *x, cs_stream stream);
+
+/* r = b - A x on `level`; if norm2 != NULL, *norm2 (HOST) receives ||r||_2
+ * (the call then synchronises). */
+cs_status cs_residual(const cs_hierarchy *h, int level, const double *b, const double *x, double *r,
+                      double *norm2, cs_stream stream);
+
+/* ---------------------------------------------------------------- solve */
+enum { CS_STATIONARY = 0, CS_GMRES = 1, CS_REFINE = 2 };
+
+typedef struct {
+    int method;      /* CS_STATIONARY: x <- V(x,b); CS_GMRES: left-preconditioned
+                        restarted GMRES with V0 (Sec. 3.1); CS_REFINE: FP64 iterative
+                        refinement x += V0(b - A x) with the cycle in cycle.precision */
+    int restart;     /* GMRES restart length (default 30) */
+    int maxit;       /* maximum V-cycle applications (default 100) */
+    double tol;      /* stop when ||b - A x||_2 / ||b||_2 <= tol (default 1e-10) */
+    cs_vcycle_opts cycle;
+    int host_buffers; /* 1: b and x are HOST pointers; copies happen inside the call */
+    double *hist;    /* optional host array: relative residual per iteration (true residual
+                        for stationary/refine, preconditioned estimate for GMRES) */
+    int hist_cap;
+} cs_solve_opts;
+
+typedef struct {
+    int iterations;        /* V-cycle applications in the iteration (GMRES: Arnoldi steps) */
+    int converged;         /* 1 if the tolerance was met */
+    double final_rel_residual; /* ||b - A x||_2 / ||b||_2 in FP64 */
+    int nhist;             /* entries written to opts->hist */
+} cs_solve_info;
+
+/* Solve A x = b from the given initial x (0 for the paper's convention).
+ * Synchronises the stream before returning (info is host data).
+ * Errors: CS_ERR_NOTCONV (maxit reached; x holds the last iterate),
+ * CS_ERR_DIVERGED, CS_ERR_ARG, CS_ERR_CUDA. */
+cs_status cs_solve(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *opts, const double *b,
+                   double *x, cs_solve_info *info, cs_stream stream);
+
+/* -------------------------------------------------------------- queries */
+typedef struct {
+    int dim;
+    int n[3];
+    int64_t N;
+    int nst;          /* stencil entries stored for this level */
+    int off[27][3];   /* their offsets */
+    int nlevels;      /* levels in the hierarchy */
+} cs_level_info;
+
+cs_status cs_query_level(const cs_hierarchy *h, int level, cs_level_info *info);
+/* Copy the level operator to HOST memory: [nst][N] doubles, offsets as in
+ * cs_query_level (zero where the neighbour lies outside the grid). */
+cs_status cs_export_operator(const cs_hierarchy *h, int level, double *host_coeff);
+/* Red-black colour id of every node of `level` (0 = red) into HOST memory. */
+cs_status cs_export_colours(const cs_hierarchy *h, int level, int8_t *host_colour);
+/* Copy Lambda of `level` to HOST memory: [nu][N] doubles (point blocks; the
+ * multiplicative Lambda_{l,k} occupy the nodes of colour k). */
+cs_status cs_export_lambda(const cs_cascade *c, int level, double *host_lambda);
+/* Number of device bytes the handle holds. */
+int64_t cs_hierarchy_bytes(const cs_hierarchy *h);
+int64_t cs_cascade_bytes(const cs_cascade *c);
+
+/* Kernel launches issued by this library in this process so far (a replay
+ * of a captured cycle counts each of its kernels). */
+int64_t cs_kernel_launches(void);
+const char *cs_last_error(void);
+void cs_destroy_hierarchy(cs_hierarchy *h);
+void cs_destroy_cascade(cs_cascade *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CASCADE_MG_H */

@@ -1,0 +1,287 @@
+"""Cascading-smoother geometric multigrid on GB300 (sm_103a).
+
+Python binding of the C ABI declared in ``include/cascade_mg.h``: the same
+entry points (``setup_hierarchy``, ``setup_cascade``, ``vcycle``, ``solve``,
+``smooth``, ``residual_restrict``, ``prolong_correct``, ``coarse_solve``,
+``residual`` and the exports), marshalling torch CUDA tensors (device
+memory) and streams into plain pointers.  All arithmetic runs in the CUDA
+kernels of ``libcascade_mg.so``; when the library is missing every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _capi
+from ._capi import CascadeError
+
+__all__ = ["setup_hierarchy", "setup_cascade", "vcycle", "solve", "smooth", "sweep", "residual_restrict",
+           "prolong_correct", "coarse_solve", "residual", "query_level", "export_operator", "export_colours",
+           "export_lambda", "kernel_launches", "Hierarchy", "Cascade", "SolveInfo", "CascadeError"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    if stream is None:
+        torch = _torch()
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, n=None, name="tensor"):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Hierarchy:
+    """Handle of a geometric hierarchy (owns its device memory)."""
+
+    def __init__(self, ptr, dim):
+        self._p = ptr
+        self.dim = dim
+        self._infos = {}
+        lvl = self.level_info(0)
+        self.nlevels = lvl["nlevels"]
+
+    @property
+    def ptr(self):
+        return self._p
+
+    def level_info(self, level):
+        if level not in self._infos:
+            info = _capi.cs_level_info()
+            _capi.check(_capi.lib().cs_query_level(self._p, level, C.byref(info)), "cs_query_level")
+            self._infos[level] = {
+                "dim": info.dim, "n": tuple(info.n), "N": int(info.N), "nst": info.nst,
+                "offsets": [tuple(info.off[s]) for s in range(info.nst)], "nlevels": info.nlevels}
+        return self._infos[level]
+
+    def N(self, level=0):
+        return self.level_info(level)["N"]
+
+    def nbytes(self):
+        return int(_capi.lib().cs_hierarchy_bytes(self._p))
+
+    def __del__(self):
+        if getattr(self, "_p", None) and _capi._lib is not None:
+            _capi._lib.cs_destroy_hierarchy(self._p)
+            self._p = None
+
+
+class Cascade:
+    """Handle of a cascade built on a hierarchy (keeps the hierarchy alive)."""
+
+    def __init__(self, ptr, hier, kind, nu, lowp):
+        self._p = ptr
+        self.hier = hier
+        self.kind = kind
+        self.nu = nu
+        self.lowp = lowp
+
+    @property
+    def ptr(self):
+        return self._p
+
+    def nbytes(self):
+        return int(_capi.lib().cs_cascade_bytes(self._p))
+
+    def __del__(self):
+        if getattr(self, "_p", None) and _capi._lib is not None:
+            _capi._lib.cs_destroy_cascade(self._p)
+            self._p = None
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    iterations: int
+    converged: bool
+    final_rel_residual: float
+    history: np.ndarray
+
+
+def setup_hierarchy(dim, n, offsets, coeff, periodic=False, coarse_max=4, max_levels=0, block=1, stream=None):
+    """Build the hierarchy of the structured operator given by ``offsets``
+    (list of (dx,dy,dz)) and ``coeff`` ([nst, N] float64: a CUDA tensor, or a
+    host numpy array copied during the call)."""
+    st = _capi.cs_stencil()
+    st.dim = dim
+    nn = list(n) + [1] * (3 - len(n))
+    for d in range(3):
+        st.n[d] = int(nn[d])
+    st.nst = len(offsets)
+    for s, o in enumerate(offsets):
+        for d in range(3):
+            st.off[s][d] = int(o[d])
+    keep = coeff
+    if isinstance(coeff, np.ndarray):
+        keep = np.ascontiguousarray(coeff, dtype=np.float64)
+        st.coeff = keep.ctypes.data_as(C.c_void_p)
+        st.coeff_on_host = 1
+    else:
+        st.coeff = _dev_ptr(coeff, name="coeff").value
+        st.coeff_on_host = 0
+    st.periodic = int(bool(periodic))
+    opts = _capi.cs_hierarchy_opts(coarse_max, max_levels, block)
+    out = C.c_void_p()
+    _capi.check(_capi.lib().cs_setup_hierarchy(C.byref(st), C.byref(opts), _stream(stream), C.byref(out)),
+                "cs_setup_hierarchy")
+    del keep
+    return Hierarchy(out.value, dim)
+
+
+def setup_cascade(h: Hierarchy, kind="additive", nu=3, prescale=True, alpha=0, lowp=False, stream=None):
+    k = _capi.CS_MULTIPLICATIVE if kind == "multiplicative" else _capi.CS_ADDITIVE
+    opts = _capi.cs_cascade_opts(k, nu, int(prescale), alpha, int(lowp))
+    out = C.c_void_p()
+    _capi.check(_capi.lib().cs_setup_cascade(h.ptr, C.byref(opts), _stream(stream), C.byref(out)),
+                "cs_setup_cascade")
+    return Cascade(out.value, h, kind, nu, lowp)
+
+
+def _cycle_opts(mu_pre, mu_post, order, precision):
+    return _capi.cs_vcycle_opts(mu_pre, mu_post, _capi.CS_RF if order.upper() == "RF" else _capi.CS_FF,
+                                _capi.CS_FP32 if precision == "fp32" else _capi.CS_FP64)
+
+
+def vcycle(h, c, b, x, mu_pre=1, mu_post=1, order="RF", precision="fp64", stream=None):
+    """x <- V(x, b) in place (Algorithm 1)."""
+    N = h.N(0)
+    o = _cycle_opts(mu_pre, mu_post, order, precision)
+    _capi.check(_capi.lib().cs_vcycle(h.ptr, c.ptr, C.byref(o), _dev_ptr(b, N, "b"), _dev_ptr(x, N, "x"),
+                                      _stream(stream)), "cs_vcycle")
+
+
+def smooth(h, c, level, b, x, reverse=False, stream=None):
+    N = h.N(level)
+    _capi.check(_capi.lib().cs_smooth(h.ptr, c.ptr, level, int(reverse), _dev_ptr(b, N, "b"), _dev_ptr(x, N, "x"),
+                                      _stream(stream)), "cs_smooth")
+
+
+def sweep(h, c, level, step, b, x, out, colour=-1, stream=None):
+    """One cascade step (one kernel): out = x - Lambda_{step+1[,colour]} (A x - b).
+    float64 tensors run the FP64 kernel, float32 tensors the FP32 one (lowp)."""
+    torch = _torch()
+    N = h.N(level)
+    ts = (b, x, out)
+    if any((not isinstance(t, torch.Tensor)) or (not t.is_cuda) or (not t.is_contiguous()) or t.numel() != N
+           for t in ts):
+        raise ValueError(f"b, x, out must be contiguous CUDA tensors of {N} values")
+    if all(t.dtype == torch.float32 for t in ts):
+        prec = _capi.CS_FP32
+    elif all(t.dtype == torch.float64 for t in ts):
+        prec = _capi.CS_FP64
+    else:
+        raise TypeError("b, x, out must all be float64 or all float32")
+    _capi.check(_capi.lib().cs_sweep(h.ptr, c.ptr, level, step, colour, prec, C.c_void_p(b.data_ptr()),
+                                     C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), _stream(stream)),
+                "cs_sweep")
+
+
+def kernel_launches() -> int:
+    """Kernel launches issued by the library in this process so far."""
+    return int(_capi.lib().cs_kernel_launches())
+
+
+def residual_restrict(h, level, b, x, rc, stream=None):
+    N, Nc = h.N(level), h.N(level + 1)
+    _capi.check(_capi.lib().cs_residual_restrict(h.ptr, level, _dev_ptr(b, N, "b"), _dev_ptr(x, N, "x"),
+                                                 _dev_ptr(rc, Nc, "rc"), _stream(stream)), "cs_residual_restrict")
+
+
+def prolong_correct(h, level, xc, x, stream=None):
+    N, Nc = h.N(level), h.N(level + 1)
+    _capi.check(_capi.lib().cs_prolong_correct(h.ptr, level, _dev_ptr(xc, Nc, "xc"), _dev_ptr(x, N, "x"),
+                                               _stream(stream)), "cs_prolong_correct")
+
+
+def coarse_solve(h, b, x, stream=None):
+    N = h.N(h.nlevels - 1)
+    _capi.check(_capi.lib().cs_coarse_solve(h.ptr, _dev_ptr(b, N, "b"), _dev_ptr(x, N, "x"), _stream(stream)),
+                "cs_coarse_solve")
+
+
+def residual(h, level, b, x, r, norm=False, stream=None):
+    """r = b - A x on ``level``; returns ||r||_2 when norm=True."""
+    N = h.N(level)
+    nrm = C.c_double(0.0)
+    _capi.check(_capi.lib().cs_residual(h.ptr, level, _dev_ptr(b, N, "b"), _dev_ptr(x, N, "x"), _dev_ptr(r, N, "r"),
+                                        C.byref(nrm) if norm else None, _stream(stream)), "cs_residual")
+    return float(nrm.value) if norm else None
+
+
+_METHODS = {"stationary": _capi.CS_STATIONARY, "gmres": _capi.CS_GMRES, "refine": _capi.CS_REFINE}
+
+
+def solve(h, c, b, x, method="stationary", tol=1e-10, maxit=100, restart=30, mu_pre=1, mu_post=1, order="RF",
+          precision="fp64", host_buffers=False, raise_on_error=True, stream=None) -> SolveInfo:
+    """Solve A x = b from the initial x (in place).  With host_buffers=True,
+    b and x are host float64 arrays (numpy or CPU tensors; pinned memory is
+    fastest) and the host<->device copies happen inside the call."""
+    N = h.N(0)
+    hist = np.zeros(4 * maxit + 8)
+    o = _capi.cs_solve_opts(_METHODS[method], restart, maxit, tol, _cycle_opts(mu_pre, mu_post, order, precision),
+                            int(host_buffers), hist.ctypes.data_as(C.POINTER(C.c_double)), len(hist))
+    if host_buffers:
+        bp, xp = _host_ptr(b, N, "b"), _host_ptr(x, N, "x")
+    else:
+        bp, xp = _dev_ptr(b, N, "b"), _dev_ptr(x, N, "x")
+    info = _capi.cs_solve_info()
+    st = _capi.lib().cs_solve(h.ptr, c.ptr, C.byref(o), bp, xp, C.byref(info), _stream(stream))
+    if raise_on_error and st not in (_capi.CS_OK,):
+        _capi.check(st, "cs_solve")
+    return SolveInfo(st, info.iterations, bool(info.converged), info.final_rel_residual, hist[: info.nhist].copy())
+
+
+def _host_ptr(a, n, name):
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != n:
+            raise TypeError(f"{name} must be a contiguous float64 array of {n} values")
+        return a.ctypes.data_as(C.c_void_p)
+    torch = _torch()
+    if isinstance(a, torch.Tensor) and not a.is_cuda:
+        if a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != n:
+            raise TypeError(f"{name} must be a contiguous float64 tensor of {n} values")
+        return C.c_void_p(a.data_ptr())
+    raise TypeError(f"{name} must be a host array")
+
+
+def query_level(h, level):
+    return h.level_info(level)
+
+
+def export_operator(h, level):
+    """(offsets, coeff [nst, N]) of ``level`` as host arrays."""
+    info = h.level_info(level)
+    out = np.zeros((info["nst"], info["N"]))
+    _capi.check(_capi.lib().cs_export_operator(h.ptr, level, out.ctypes.data_as(C.c_void_p)), "cs_export_operator")
+    return info["offsets"], out
+
+
+def export_colours(h, level):
+    out = np.zeros(h.N(level), dtype=np.int8)
+    _capi.check(_capi.lib().cs_export_colours(h.ptr, level, out.ctypes.data_as(C.c_void_p)), "cs_export_colours")
+    return out
+
+
+def export_lambda(c, level):
+    out = np.zeros((c.nu, c.hier.N(level)))
+    _capi.check(_capi.lib().cs_export_lambda(c.ptr, level, out.ctypes.data_as(C.c_void_p)), "cs_export_lambda")
+    return out

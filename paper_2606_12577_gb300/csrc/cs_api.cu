@@ -1,0 +1,772 @@
+// C ABI of the cascading-smoother multigrid library (see
+// include/cascade_mg.h): handle management, the V-cycle of Algorithm 1
+// enqueued level by level and captured once into a CUDA graph, and the solve
+// drivers (stationary iteration, FP64 iterative refinement around an FP32
+// cycle, and left-preconditioned restarted GMRES as in Sec. 3.1).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "cs_internal.cuh"
+
+namespace csx {
+
+static thread_local std::string g_err;
+std::atomic<int64_t> g_launches{0};
+
+void set_error(const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+cs_status cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+    set_error("CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file, line);
+    return e == cudaErrorMemoryAllocation ? CS_ERR_NOMEM : CS_ERR_CUDA;
+}
+
+cs_status dalloc(void **p, size_t bytes, int64_t *acct) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        *p = nullptr;
+        return CS_ERR_NOMEM;
+    }
+    if (acct) *acct += (int64_t)bytes;
+    return CS_OK;
+}
+
+static bool is_star_offset(int dim, const int *o) {
+    int nz = (o[0] != 0) + (o[1] != 0) + (o[2] != 0);
+    if (dim == 2 && o[2] != 0) return false;
+    return nz <= 1;
+}
+static int star_slot(const int *o) {
+    if (o[0] == -1) return 1;
+    if (o[0] == 1) return 2;
+    if (o[1] == -1) return 3;
+    if (o[1] == 1) return 4;
+    if (o[2] == -1) return 5;
+    if (o[2] == 1) return 6;
+    return 0;
+}
+static int box_slot(int dim, const int *o) { return (o[0] + 1) + 3 * (o[1] + 1) + (dim == 3 ? 9 * (o[2] + 1) : 0); }
+
+static void fill_offsets(Level &L) {
+    for (int s = 0; s < L.nst; ++s) {
+        int *o = L.off[s];
+        o[0] = o[1] = o[2] = 0;
+        if (L.kind == STAR) {
+            if (s == 1) o[0] = -1;
+            else if (s == 2) o[0] = 1;
+            else if (s == 3) o[1] = -1;
+            else if (s == 4) o[1] = 1;
+            else if (s == 5) o[2] = -1;
+            else if (s == 6) o[2] = 1;
+        } else {
+            o[0] = s % 3 - 1;
+            o[1] = (s / 3) % 3 - 1;
+            o[2] = L.g.dim == 3 ? s / 9 - 1 : 0;
+        }
+    }
+}
+
+// --------------------------------------------------------------- V-cycle
+template <typename T>
+struct View {
+    const T *A;
+    const T *lam;
+    T *b, *x, *t;
+};
+
+template <typename T>
+static View<T> view(const cs_hierarchy *h, const cs_cascade *c, int l);
+template <>
+View<double> view<double>(const cs_hierarchy *h, const cs_cascade *c, int l) {
+    const Level &L = h->lev[l];
+    return {L.A, l < c->nlev ? c->lam[l] : nullptr, L.b, L.x, L.t};
+}
+template <>
+View<float> view<float>(const cs_hierarchy *, const cs_cascade *c, int l) {
+    const LowLevel &L = c->lo[l];
+    return {L.A, L.lam, L.b, L.x, L.t};
+}
+
+static bool inplace_colours(const cs_cascade *c, const Level &L) {
+    // red-black is a graph colouring of a STAR stencil: colour-k updates read
+    // only the other colour, so they may overwrite x in place
+    return c->kind == CS_MULTIPLICATIVE && L.kind == STAR;
+}
+
+// one application of the cascade on level l; `cur` is the buffer holding the
+// iterate (updated); `xzero` marks an all-zero iterate (cleared on return)
+template <typename T>
+static cs_status smooth_apply(const cs_hierarchy *h, const cs_cascade *c, int l, const View<T> &v, const T *b,
+                              T *&cur, T *other, bool reverse, bool &xzero, cudaStream_t s) {
+    const Level &L = h->lev[l];
+    const int64_t N = L.g.N;
+    const bool inpl = inplace_colours(c, L);
+    for (int step = 0; step < c->nu; ++step) {
+        int lv = reverse ? c->nu - 1 - step : step;
+        for (int kk = 0; kk < c->ncol; ++kk) {
+            int k = reverse ? c->ncol - 1 - kk : kk;
+            int colour = c->ncol == 2 ? k : -1;
+            const T *lam = v.lam + (int64_t)lv * N;
+            if (inpl) {
+                CSX_TRY(launch_sweep<T>(L, v.A, lam, b, cur, cur, colour, xzero, s));
+            } else {  // snapshot semantics: read cur, write the other buffer
+                CSX_TRY(launch_sweep<T>(L, v.A, lam, b, cur, other, colour, xzero, s));
+                std::swap(cur, other);
+            }
+            xzero = false;
+        }
+    }
+    return CS_OK;
+}
+
+template <typename T>
+static int out_of_place_steps(const cs_cascade *c, const Level &L) {
+    return inplace_colours(c, L) ? 0 : c->nu * c->ncol;
+}
+
+template <typename T>
+static cs_status coarse_solve_t(const cs_hierarchy *h, const T *b, T *x, cudaStream_t s);
+template <>
+cs_status coarse_solve_t<double>(const cs_hierarchy *h, const double *b, double *x, cudaStream_t s) {
+    return launch_coarse_solve(h, b, x, s);
+}
+template <>
+cs_status coarse_solve_t<float>(const cs_hierarchy *h, const float *b, float *x, cudaStream_t s) {
+    return launch_coarse_solve32(h, b, x, s);
+}
+
+// zero-initial-guess cycle on level l: reads v.b, leaves the result in v.x
+template <typename T>
+static cs_status v0_enqueue(const cs_hierarchy *h, const cs_cascade *c, int l, int order, int mu_pre, int mu_post,
+                            cudaStream_t s) {
+    View<T> v = view<T>(h, c, l);
+    if (l == h->nlev - 1) return coarse_solve_t<T>(h, v.b, v.x, s);
+    const Level &L = h->lev[l];
+    const Level &Lc = h->lev[l + 1];
+    View<T> vc = view<T>(h, c, l + 1);
+    T *cur = v.x, *other = v.t;
+    bool xzero = true;
+    for (int m = 0; m < mu_pre; ++m)
+        CSX_TRY(smooth_apply<T>(h, c, l, v, v.b, cur, other, order == CS_RF, xzero, s));
+    if (xzero) {
+        CSX_CUDA(cudaMemsetAsync(cur, 0, sizeof(T) * L.g.N, s));
+        xzero = false;
+    }
+    CSX_TRY(launch_residual_restrict<T>(L, Lc, v.A, v.b, cur, vc.b, s));
+    CSX_TRY(v0_enqueue<T>(h, c, l + 1, order, mu_pre, mu_post, s));
+    int P = mu_post * out_of_place_steps<T>(c, L);
+    T *out = (P % 2 == 0) ? v.x : v.t;
+    CSX_TRY(launch_prolong_correct<T>(L, Lc, vc.x, cur, out, s));
+    cur = out;
+    other = (out == v.x) ? v.t : v.x;
+    for (int m = 0; m < mu_post; ++m)
+        CSX_TRY(smooth_apply<T>(h, c, l, v, v.b, cur, other, false, xzero, s));
+    if (cur != v.x) {
+        set_error("internal: V-cycle result not in place");
+        return CS_ERR_ARG;
+    }
+    return CS_OK;
+}
+
+// Launch the captured zero-guess cycle for these options (capturing it on
+// first use): reads level-0 b (FP64 or FP32 state), writes level-0 x.
+static cs_status run_v0(const cs_hierarchy *h, cs_cascade *c, const cs_vcycle_opts &o, cudaStream_t s) {
+    for (auto &g : c->graphs)
+        if (g.prec == o.precision && g.order == o.order && g.mu_pre == o.mu_pre && g.mu_post == o.mu_post) {
+            CSX_CUDA(cudaGraphLaunch(g.exec, s));
+            count_launch(g.kernels);
+            return CS_OK;
+        }
+    // capture after the work already queued on s (the capture stream is separate)
+    cudaStream_t cs = c->capture_stream;
+    CSX_CUDA(cudaStreamSynchronize(s));
+    CSX_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = g_launches.load();
+    cs_status rc = o.precision == CS_FP32 ? v0_enqueue<float>(h, c, 0, o.order, o.mu_pre, o.mu_post, cs)
+                                          : v0_enqueue<double>(h, c, 0, o.order, o.mu_pre, o.mu_post, cs);
+    const int64_t kernels = g_launches.load() - before;  // recorded, not executed
+    g_launches.fetch_sub(kernels);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (rc != CS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+    c->graphs.push_back({o.precision, o.order, o.mu_pre, o.mu_post, exec, kernels});
+    CSX_CUDA(cudaGraphLaunch(exec, s));
+    count_launch(kernels);
+    return CS_OK;
+}
+
+static cs_status check_cycle_opts(const cs_hierarchy *h, const cs_cascade *c, const cs_vcycle_opts *o) {
+    if (!o || o->mu_pre < 0 || o->mu_post < 0 || o->mu_pre > 16 || o->mu_post > 16 ||
+        (o->order != CS_RF && o->order != CS_FF) || (o->precision != CS_FP64 && o->precision != CS_FP32)) {
+        set_error("invalid V-cycle options");
+        return CS_ERR_ARG;
+    }
+    if (o->precision == CS_FP32 && !c->lowp) {
+        set_error("FP32 cycles need a cascade built with lowp = 1");
+        return CS_ERR_ARG;
+    }
+    if (h->cn == 0) {
+        set_error("the hierarchy has no coarsest-level factorisation (periodic, or coarsest level too large)");
+        return CS_ERR_UNSUPPORTED;
+    }
+    return CS_OK;
+}
+
+static double host_sum(const cs_hierarchy *h, int nred, cudaStream_t s, cs_status *rc) {
+    *rc = launch_finish_sum(h->red, nred, s);
+    if (*rc != CS_OK) return 0.0;
+    cudaError_t e = cudaMemcpyAsync(h->red_host, h->red + nred, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        *rc = cuda_fail(e, "reduction readback", __FILE__, __LINE__);
+        return 0.0;
+    }
+    return h->red_host[0];
+}
+
+static int residual_blocks(const Level &L) {
+    dim3 g = node_grid(L.g);
+    return (int)(g.x * g.y * g.z);
+}
+
+}  // namespace csx
+
+using namespace csx;
+
+extern "C" {
+
+const char *cs_last_error(void) { return g_err.c_str(); }
+
+cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts_in, cs_stream stream,
+                             cs_hierarchy **out) {
+    if (!A0 || !out) { set_error("null argument"); return CS_ERR_ARG; }
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    cs_hierarchy_opts opts{4, 0, 1};
+    if (opts_in) opts = *opts_in;
+    if (opts.coarse_max <= 0) opts.coarse_max = 4;
+    if (opts.block == 0) opts.block = 1;
+    int dim = A0->dim;
+    if (dim != 2 && dim != 3) { set_error("dim must be 2 or 3"); return CS_ERR_ARG; }
+    int n[3] = {A0->n[0], A0->n[1], dim == 3 ? A0->n[2] : 1};
+    if (n[0] < 1 || n[1] < 1 || n[2] < 1 || (dim == 2 && A0->n[2] > 1)) { set_error("bad grid size"); return CS_ERR_ARG; }
+    if ((int64_t)n[0] * n[1] * n[2] > (int64_t)1 << 31) { set_error("grid too large (N must fit in 31 bits)"); return CS_ERR_ARG; }
+    if (A0->nst < 1 || A0->nst > 27 || !A0->coeff) { set_error("bad stencil"); return CS_ERR_ARG; }
+    if (opts.block != 1) { set_error("only point blocks (block = 1) are implemented"); return CS_ERR_UNSUPPORTED; }
+    bool star = true, centre = false;
+    bool seen[27] = {false};
+    for (int s2 = 0; s2 < A0->nst; ++s2) {
+        const int *o = A0->off[s2];
+        for (int d = 0; d < 3; ++d)
+            if (o[d] < -1 || o[d] > 1) { set_error("stencil offsets must lie in {-1,0,1}"); return CS_ERR_ARG; }
+        if (dim == 2 && o[2] != 0) { set_error("2D stencil with a z offset"); return CS_ERR_ARG; }
+        int b = box_slot(dim, o);
+        if (seen[b]) { set_error("duplicate stencil offset"); return CS_ERR_ARG; }
+        seen[b] = true;
+        if (o[0] == 0 && o[1] == 0 && o[2] == 0) centre = true;
+        if (!is_star_offset(dim, o)) star = false;
+    }
+    if (!centre) { set_error("stencil needs the (0,0,0) entry"); return CS_ERR_ARG; }
+    if (A0->periodic && opts.max_levels != 1) {
+        set_error("periodic operators are accepted only with max_levels = 1");
+        return CS_ERR_UNSUPPORTED;
+    }
+
+    cs_hierarchy *h = new cs_hierarchy();
+    h->dim = dim;
+    h->periodic = A0->periodic != 0;
+    cs_status rc = CS_OK;
+    {
+        Level L0;
+        L0.g = make_grid(dim, n[0], n[1], n[2]);
+        L0.kind = star ? STAR : BOX;
+        L0.nst = star ? 2 * dim + 1 : (dim == 3 ? 27 : 9);
+        fill_offsets(L0);
+        if ((rc = dalloc_t(&L0.A, (size_t)L0.nst * L0.g.N, &h->bytes)) != CS_OK) goto fail_nolevel;
+        h->lev.push_back(L0);
+        Level &L = h->lev[0];
+        cudaError_t e = cudaMemsetAsync(L.A, 0, sizeof(double) * L.nst * L.g.N, s);
+        for (int s2 = 0; s2 < A0->nst && e == cudaSuccess; ++s2) {
+            int slot = star ? star_slot(A0->off[s2]) : box_slot(dim, A0->off[s2]);
+            e = cudaMemcpyAsync(L.A + (int64_t)slot * L.g.N, A0->coeff + (int64_t)s2 * L.g.N, sizeof(double) * L.g.N,
+                                A0->coeff_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
+        }
+        if (A0->coeff_on_host && e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "copy operator", __FILE__, __LINE__); goto fail; }
+    }
+    while (!h->periodic && (opts.max_levels <= 0 || (int)h->lev.size() < opts.max_levels)) {
+        const Level &F = h->lev.back();
+        int mx = std::max(F.g.nx, std::max(F.g.ny, dim == 3 ? F.g.nz : 0));
+        int mn = std::min(F.g.nx, std::min(F.g.ny, dim == 3 ? F.g.nz : F.g.ny));
+        if (mx <= opts.coarse_max || mn < 2) break;
+        Level C;
+        C.g = make_grid(dim, F.g.nx / 2, F.g.ny / 2, dim == 3 ? F.g.nz / 2 : 1);
+        C.kind = BOX;
+        C.nst = dim == 3 ? 27 : 9;
+        fill_offsets(C);
+        if ((rc = dalloc_t(&C.A, (size_t)C.nst * C.g.N, &h->bytes)) != CS_OK) goto fail;
+        h->lev.push_back(C);
+        if ((rc = galerkin_level(h->lev[h->lev.size() - 2], h->lev.back(), s)) != CS_OK) goto fail;
+    }
+    h->nlev = (int)h->lev.size();
+    for (auto &L : h->lev) {
+        if ((rc = dalloc_t(&L.b, L.g.N, &h->bytes)) != CS_OK) goto fail;
+        if ((rc = dalloc_t(&L.x, L.g.N, &h->bytes)) != CS_OK) goto fail;
+        if ((rc = dalloc_t(&L.t, L.g.N, &h->bytes)) != CS_OK) goto fail;
+    }
+    {
+        int nred = std::max(residual_blocks(h->lev[0]), NRED);
+        if ((rc = dalloc_t(&h->red, (size_t)nred + 8, &h->bytes)) != CS_OK) goto fail;
+        cudaError_t e = cudaMallocHost(&h->red_host, 64 * sizeof(double));
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMallocHost", __FILE__, __LINE__); goto fail; }
+        if ((rc = dalloc_t(&h->hb, h->lev[0].g.N, &h->bytes)) != CS_OK) goto fail;
+        if ((rc = dalloc_t(&h->hx, h->lev[0].g.N, &h->bytes)) != CS_OK) goto fail;
+    }
+    if (!h->periodic && h->lev.back().g.N <= 4096) {
+        if ((rc = coarse_factor(h, s)) != CS_OK) goto fail;
+    }
+    {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "hierarchy setup", __FILE__, __LINE__); goto fail; }
+    }
+    *out = h;
+    return CS_OK;
+fail:
+fail_nolevel:
+    cs_destroy_hierarchy(h);
+    return rc;
+}
+
+void cs_destroy_hierarchy(cs_hierarchy *h) {
+    if (!h) return;
+    for (auto &L : h->lev) { cudaFree(L.A); cudaFree(L.b); cudaFree(L.x); cudaFree(L.t); }
+    cudaFree(h->cinv); cudaFree(h->red); cudaFree(h->hb); cudaFree(h->hx); cudaFree(h->fine_r);
+    if (h->red_host) cudaFreeHost(h->red_host);
+    delete h;
+}
+
+int64_t cs_hierarchy_bytes(const cs_hierarchy *h) { return h ? h->bytes : 0; }
+int64_t cs_cascade_bytes(const cs_cascade *c) { return c ? c->bytes : 0; }
+
+cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream stream, cs_cascade **out) {
+    if (!h || !o || !out) { set_error("null argument"); return CS_ERR_ARG; }
+    *out = nullptr;
+    if (o->kind != CS_ADDITIVE && o->kind != CS_MULTIPLICATIVE) { set_error("bad cascade kind"); return CS_ERR_ARG; }
+    if (o->nu < 1 || o->nu > 8) { set_error("nu must be in 1..8"); return CS_ERR_ARG; }
+    if (o->alpha != 0) { set_error("residual truncation (alpha > 0) is not implemented"); return CS_ERR_UNSUPPORTED; }
+    cudaStream_t s = (cudaStream_t)stream;
+    cs_cascade *c = new cs_cascade();
+    c->h = h;
+    c->kind = o->kind;
+    c->nu = o->nu;
+    c->ncol = o->kind == CS_MULTIPLICATIVE ? 2 : 1;
+    c->nlev = h->nlev > 1 ? h->nlev - 1 : 1;
+    c->lowp = o->lowp != 0;
+    cs_status rc = CS_OK;
+    int64_t peak = 0;
+    c->lam.assign(c->nlev, nullptr);
+    for (int l = 0; l < c->nlev; ++l) {
+        const int64_t N = h->lev[l].g.N;
+        if ((rc = dalloc_t(&c->lam[l], (size_t)c->nu * N, &c->bytes)) != CS_OK) goto fail;
+        if ((rc = cascade_setup_level(h, l, c->kind, c->nu, o->prescale, c->lam[l], s, &peak)) != CS_OK) goto fail;
+    }
+    if (c->lowp) {
+        c->lo.resize(h->nlev);
+        for (int l = 0; l < h->nlev; ++l) {
+            const Level &L = h->lev[l];
+            LowLevel &lo = c->lo[l];
+            const int64_t N = L.g.N;
+            if ((rc = dalloc_t(&lo.A, (size_t)L.nst * N, &c->bytes)) != CS_OK) goto fail;
+            if ((rc = launch_copy_d2f((int64_t)L.nst * N, L.A, lo.A, s)) != CS_OK) goto fail;
+            if (l < c->nlev) {
+                if ((rc = dalloc_t(&lo.lam, (size_t)c->nu * N, &c->bytes)) != CS_OK) goto fail;
+                if ((rc = launch_copy_d2f((int64_t)c->nu * N, c->lam[l], lo.lam, s)) != CS_OK) goto fail;
+            }
+            if ((rc = dalloc_t(&lo.b, N, &c->bytes)) != CS_OK) goto fail;
+            if ((rc = dalloc_t(&lo.x, N, &c->bytes)) != CS_OK) goto fail;
+            if ((rc = dalloc_t(&lo.t, N, &c->bytes)) != CS_OK) goto fail;
+        }
+    }
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cascade setup", __FILE__, __LINE__); goto fail; }
+    }
+    *out = c;
+    return CS_OK;
+fail:
+    cs_destroy_cascade(c);
+    return rc;
+}
+
+void cs_destroy_cascade(cs_cascade *c) {
+    if (!c) return;
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    for (double *p : c->lam) cudaFree(p);
+    for (auto &lo : c->lo) { cudaFree(lo.A); cudaFree(lo.lam); cudaFree(lo.b); cudaFree(lo.x); cudaFree(lo.t); }
+    cudaFree(c->fine_b32); cudaFree(c->fine_x32); cudaFree(c->gm_V); cudaFree(c->gm_h);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    delete c;
+}
+
+cs_status cs_vcycle(const cs_hierarchy *h, cs_cascade *c, const cs_vcycle_opts *o, const double *b, double *x,
+                    cs_stream stream) {
+    if (!h || !c || !b || !x) { set_error("null argument"); return CS_ERR_ARG; }
+    CSX_TRY(check_cycle_opts(h, c, o));
+    cudaStream_t s = (cudaStream_t)stream;
+    const Level &L = h->lev[0];
+    if (o->precision == CS_FP32) {
+        CSX_TRY(launch_residual64(L, L.A, b, x, nullptr, c->lo[0].b, nullptr, 0, s));
+        CSX_TRY(run_v0(h, c, *o, s));
+        CSX_TRY(launch_axpy_f32(L.g.N, c->lo[0].x, x, s));
+    } else {
+        CSX_TRY(launch_residual64(L, L.A, b, x, L.b, nullptr, nullptr, 0, s));
+        CSX_TRY(run_v0(h, c, *o, s));
+        CSX_TRY(launch_add64(L.g.N, L.x, x, s));
+    }
+    return CS_OK;
+}
+
+cs_status cs_smooth(const cs_hierarchy *h, cs_cascade *c, int level, int reverse, const double *b, double *x,
+                    cs_stream stream) {
+    if (!h || !c || !b || !x) { set_error("null argument"); return CS_ERR_ARG; }
+    if (level < 0 || level >= c->nlev) { set_error("level %d has no smoother", level); return CS_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    View<double> v = view<double>(h, c, level);
+    double *cur = x, *other = h->lev[level].t;
+    bool xzero = false;
+    CSX_TRY(smooth_apply<double>(h, c, level, v, b, cur, other, reverse != 0, xzero, s));
+    if (cur != x) CSX_CUDA(cudaMemcpyAsync(x, cur, sizeof(double) * h->lev[level].g.N, cudaMemcpyDeviceToDevice, s));
+    return CS_OK;
+}
+
+cs_status cs_sweep(const cs_hierarchy *h, cs_cascade *c, int level, int step, int colour, int precision,
+                   const void *b, const void *x, void *out, cs_stream stream) {
+    if (!h || !c || !b || !x || !out) { set_error("null argument"); return CS_ERR_ARG; }
+    if (level < 0 || level >= c->nlev) { set_error("level %d has no smoother", level); return CS_ERR_ARG; }
+    if (step < 0 || step >= c->nu) { set_error("step out of range"); return CS_ERR_ARG; }
+    if (colour < -1 || colour > 1 || (colour >= 0 && c->ncol != 2) || (colour < 0 && c->ncol != 1)) {
+        set_error("colour does not match the cascade kind");
+        return CS_ERR_ARG;
+    }
+    const Level &L = h->lev[level];
+    if (out == x && !(colour >= 0 && L.kind == STAR)) {
+        set_error("out may alias x only for a colour step on a 5/7-point level");
+        return CS_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = L.g.N;
+    if (precision == CS_FP32) {
+        if (!c->lowp) { set_error("FP32 steps need lowp"); return CS_ERR_ARG; }
+        const LowLevel &lo = c->lo[level];
+        return launch_sweep<float>(L, lo.A, lo.lam + (int64_t)step * N, (const float *)b, (const float *)x,
+                                   (float *)out, colour, false, s);
+    }
+    if (precision != CS_FP64) { set_error("bad precision"); return CS_ERR_ARG; }
+    return launch_sweep<double>(L, L.A, c->lam[level] + (int64_t)step * N, (const double *)b, (const double *)x,
+                                (double *)out, colour, false, s);
+}
+
+int64_t cs_kernel_launches(void) { return g_launches.load(); }
+
+cs_status cs_residual_restrict(const cs_hierarchy *h, int level, const double *b, const double *x, double *rc,
+                               cs_stream stream) {
+    if (!h || !b || !x || !rc) { set_error("null argument"); return CS_ERR_ARG; }
+    if (level < 0 || level + 1 >= h->nlev) { set_error("level %d has no coarser level", level); return CS_ERR_ARG; }
+    return launch_residual_restrict<double>(h->lev[level], h->lev[level + 1], h->lev[level].A, b, x, rc,
+                                            (cudaStream_t)stream);
+}
+
+cs_status cs_prolong_correct(const cs_hierarchy *h, int level, const double *xc, double *x, cs_stream stream) {
+    if (!h || !xc || !x) { set_error("null argument"); return CS_ERR_ARG; }
+    if (level < 0 || level + 1 >= h->nlev) { set_error("level %d has no coarser level", level); return CS_ERR_ARG; }
+    return launch_prolong_correct<double>(h->lev[level], h->lev[level + 1], xc, x, x, (cudaStream_t)stream);
+}
+
+cs_status cs_coarse_solve(const cs_hierarchy *h, const double *b, double *x, cs_stream stream) {
+    if (!h || !b || !x) { set_error("null argument"); return CS_ERR_ARG; }
+    if (h->cn == 0) { set_error("no coarsest-level factorisation"); return CS_ERR_UNSUPPORTED; }
+    return launch_coarse_solve(h, b, x, (cudaStream_t)stream);
+}
+
+cs_status cs_residual(const cs_hierarchy *h, int level, const double *b, const double *x, double *r, double *norm2,
+                      cs_stream stream) {
+    if (!h || !b || !x || !r) { set_error("null argument"); return CS_ERR_ARG; }
+    if (level < 0 || level >= h->nlev) { set_error("bad level"); return CS_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Level &L = h->lev[level];
+    int nred = residual_blocks(L);
+    bool want = norm2 != nullptr && level == 0;
+    CSX_TRY(launch_residual64(L, L.A, b, x, r, nullptr, want ? h->red : nullptr, nred, s));
+    if (norm2) {
+        if (level != 0) {
+            CSX_TRY(launch_dot(L.g.N, r, r, h->red, NRED, s));
+            nred = NRED;
+            cudaError_t e = cudaMemcpyAsync(h->red_host, h->red + nred, sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_fail(e, "norm readback", __FILE__, __LINE__);
+            *norm2 = std::sqrt(h->red_host[0]);
+        } else {
+            cs_status rc;
+            double v = host_sum(h, nred, s, &rc);
+            if (rc != CS_OK) return rc;
+            *norm2 = std::sqrt(v);
+        }
+    }
+    return CS_OK;
+}
+
+static cs_status gmres(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *o, const double *b, double *x,
+                       double nb, cs_solve_info *info, cudaStream_t s);
+
+cs_status cs_solve(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *o_in, const double *b_in, double *x_in,
+                   cs_solve_info *info, cs_stream stream) {
+    if (!h || !c || !o_in || !b_in || !x_in) { set_error("null argument"); return CS_ERR_ARG; }
+    cs_solve_opts o = *o_in;
+    if (o.maxit <= 0) o.maxit = 100;
+    if (o.tol <= 0) o.tol = 1e-10;
+    if (o.restart <= 0) o.restart = 30;
+    CSX_TRY(check_cycle_opts(h, c, &o.cycle));
+    if (o.method != CS_STATIONARY && o.method != CS_GMRES && o.method != CS_REFINE) {
+        set_error("bad solve method");
+        return CS_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Level &L = h->lev[0];
+    const int64_t N = L.g.N;
+    const double *b = b_in;
+    double *x = x_in;
+    if (o.host_buffers) {
+        CSX_CUDA(cudaMemcpyAsync(h->hb, b_in, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+        CSX_CUDA(cudaMemcpyAsync(h->hx, x_in, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+        b = h->hb;
+        x = h->hx;
+    }
+    cs_solve_info inf{0, 0, 0.0, 0};
+    cs_status rc = CS_OK;
+    // ||b||
+    CSX_TRY(launch_dot(N, b, b, h->red, NRED, s));
+    CSX_CUDA(cudaMemcpyAsync(h->red_host, h->red + NRED, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CSX_CUDA(cudaStreamSynchronize(s));
+    double nb = std::sqrt(h->red_host[0]);
+    if (nb == 0.0) {
+        CSX_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * N, s));
+        inf.converged = 1;
+    } else if (o.method == CS_GMRES) {
+        rc = gmres(h, c, &o, b, x, nb, &inf, s);
+    } else {
+        const bool lowp = o.cycle.precision == CS_FP32;
+        const int nred = residual_blocks(L);
+        float *r32 = lowp ? c->lo[0].b : nullptr;
+        double *r64 = lowp ? nullptr : L.b;
+        CSX_TRY(launch_residual64(L, L.A, b, x, r64, r32, h->red, nred, s));
+        double rel = std::sqrt(host_sum(h, nred, s, &rc)) / nb;
+        if (rc != CS_OK) return rc;
+        const double rel0 = rel;
+        if (o.hist && inf.nhist < o.hist_cap) o.hist[inf.nhist++] = rel;
+        while (rel > o.tol && inf.iterations < o.maxit) {
+            CSX_TRY(run_v0(h, c, o.cycle, s));
+            if (lowp) CSX_TRY(launch_axpy_f32(N, c->lo[0].x, x, s));
+            else CSX_TRY(launch_add64(N, L.x, x, s));
+            ++inf.iterations;
+            CSX_TRY(launch_residual64(L, L.A, b, x, r64, r32, h->red, nred, s));
+            rel = std::sqrt(host_sum(h, nred, s, &rc)) / nb;
+            if (rc != CS_OK) return rc;
+            if (o.hist && inf.nhist < o.hist_cap) o.hist[inf.nhist++] = rel;
+            if (!std::isfinite(rel) || rel > 1e3 * std::max(rel0, 1.0)) {
+                set_error("iteration diverged (relative residual %g)", rel);
+                rc = CS_ERR_DIVERGED;
+                break;
+            }
+        }
+        inf.final_rel_residual = rel;
+        inf.converged = rel <= o.tol;
+        if (rc == CS_OK && !inf.converged) {
+            set_error("not converged after %d iterations (relative residual %g)", inf.iterations, rel);
+            rc = CS_ERR_NOTCONV;
+        }
+    }
+    if (o.host_buffers) {
+        CSX_CUDA(cudaMemcpyAsync(x_in, x, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+        CSX_CUDA(cudaStreamSynchronize(s));
+    }
+    if (info) *info = inf;
+    return rc;
+}
+
+// Left-preconditioned restarted GMRES with M = V0 (the zero-initial-guess
+// cycle), modified Gram-Schmidt and Givens rotations; the small Hessenberg
+// problem is solved on the host.  Stops on the true relative residual.
+static cs_status gmres(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *o, const double *b, double *x,
+                       double nb, cs_solve_info *inf, cudaStream_t s) {
+    const Level &L = h->lev[0];
+    const int64_t N = L.g.N;
+    const int m = o->restart;
+    const bool lowp = o->cycle.precision == CS_FP32;
+    if (c->gm_restart < m) {
+        cudaFree(c->gm_V); cudaFree(c->gm_h);
+        c->gm_V = nullptr; c->gm_h = nullptr;
+        CSX_TRY(dalloc_t(&c->gm_V, (size_t)(m + 1) * N, &c->bytes));
+        CSX_TRY(dalloc_t(&c->gm_h, (size_t)(m + 2) * 2, &c->bytes));
+        c->gm_restart = m;
+    }
+    double *V = c->gm_V, *hd = c->gm_h;
+    double *z = L.x;  // cycle output (FP64 path) / converted output (FP32 path)
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), hh(m + 2);
+    auto precond = [&](const double *rhs_dev) -> cs_status {
+        // z = V0(rhs): rhs is in L.b (FP64) already, or converted for FP32
+        if (lowp) {
+            CSX_TRY(launch_copy_d2f(N, rhs_dev, c->lo[0].b, s));
+            CSX_TRY(run_v0(h, c, o->cycle, s));
+            CSX_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * N, s));
+            CSX_TRY(launch_axpy_f32(N, c->lo[0].x, z, s));
+        } else {
+            if (rhs_dev != L.b) CSX_CUDA(cudaMemcpyAsync(L.b, rhs_dev, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+            CSX_TRY(run_v0(h, c, o->cycle, s));
+        }
+        return CS_OK;
+    };
+    auto dot_to = [&](const double *a, const double *bb, double *dst) -> cs_status {
+        CSX_TRY(launch_dot(N, a, bb, h->red, NRED, s));
+        CSX_CUDA(cudaMemcpyAsync(dst, h->red + NRED, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        return CS_OK;
+    };
+    // ||M b||
+    CSX_TRY(precond(b));
+    CSX_TRY(dot_to(z, z, hd));
+    CSX_CUDA(cudaMemcpyAsync(hh.data(), hd, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CSX_CUDA(cudaStreamSynchronize(s));
+    const double nmb = std::sqrt(hh[0]);
+    const int nred = residual_blocks(L);
+    double rel = 1.0;
+    cs_status rc = CS_OK;
+    for (;;) {
+        CSX_TRY(launch_residual64(L, L.A, b, x, L.t, nullptr, h->red, nred, s));
+        rel = std::sqrt(host_sum(h, nred, s, &rc)) / nb;
+        if (rc != CS_OK) return rc;
+        if (!std::isfinite(rel)) { set_error("GMRES diverged"); return CS_ERR_DIVERGED; }
+        if (rel <= o->tol || inf->iterations >= o->maxit) break;
+        CSX_TRY(precond(L.t));
+        CSX_TRY(dot_to(z, z, hd));
+        CSX_TRY(launch_scale_dev(N, hd, V, z, s));
+        CSX_CUDA(cudaMemcpyAsync(hh.data(), hd, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CSX_CUDA(cudaStreamSynchronize(s));
+        double beta = std::sqrt(hh[0]);
+        if (inf->nhist == 0 && o->hist && inf->nhist < o->hist_cap) o->hist[inf->nhist++] = beta / nmb;
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int j;
+        for (j = 0; j < m && inf->iterations < o->maxit; ++j) {
+            CSX_TRY(launch_matvec64(L, L.A, V + (int64_t)j * N, L.b, s));
+            CSX_TRY(precond(L.b));
+            ++inf->iterations;
+            for (int i = 0; i <= j; ++i) {
+                CSX_TRY(dot_to(z, V + (int64_t)i * N, hd + i));
+                CSX_TRY(launch_axpy_dev(N, hd + i, -1.0, V + (int64_t)i * N, z, s));
+            }
+            CSX_TRY(dot_to(z, z, hd + j + 1));
+            CSX_CUDA(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+            CSX_CUDA(cudaStreamSynchronize(s));
+            double hn = std::sqrt(hh[j + 1]);
+            if (hn > 0.0) CSX_TRY(launch_scale_dev(N, hd + j + 1, V + (int64_t)(j + 1) * N, z, s));
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i];
+            H[(size_t)(j + 1) * m + j] = hn;
+            for (int i = 0; i < j; ++i) {
+                double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+            }
+            double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+            double d = std::sqrt(a * a + bb * bb);
+            cs[j] = d > 0 ? a / d : 1.0;
+            sn[j] = d > 0 ? bb / d : 0.0;
+            H[(size_t)j * m + j] = d;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            if (o->hist && inf->nhist < o->hist_cap) o->hist[inf->nhist++] = std::fabs(g[j + 1]) / nmb;
+            if (std::fabs(g[j + 1]) <= o->tol * nmb || hn == 0.0) { ++j; break; }
+        }
+        for (int i = j - 1; i >= 0; --i) {
+            double sum = g[i];
+            for (int k = i + 1; k < j; ++k) sum -= H[(size_t)i * m + k] * y[k];
+            y[i] = sum / H[(size_t)i * m + i];
+        }
+        CSX_CUDA(cudaMemcpyAsync(hd, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
+        CSX_TRY(launch_axpy_multi(N, j, hd, V, x, s));
+        CSX_CUDA(cudaStreamSynchronize(s));  // y is a host buffer reused next restart
+    }
+    inf->final_rel_residual = rel;
+    inf->converged = rel <= o->tol;
+    if (!inf->converged) {
+        set_error("GMRES not converged after %d iterations (relative residual %g)", inf->iterations, rel);
+        return CS_ERR_NOTCONV;
+    }
+    return CS_OK;
+}
+
+cs_status cs_query_level(const cs_hierarchy *h, int level, cs_level_info *info) {
+    if (!h || !info) { set_error("null argument"); return CS_ERR_ARG; }
+    if (level < 0 || level >= h->nlev) { set_error("bad level"); return CS_ERR_ARG; }
+    const Level &L = h->lev[level];
+    info->dim = L.g.dim;
+    info->n[0] = L.g.nx; info->n[1] = L.g.ny; info->n[2] = L.g.nz;
+    info->N = L.g.N;
+    info->nst = L.nst;
+    for (int s = 0; s < 27; ++s)
+        for (int d = 0; d < 3; ++d) info->off[s][d] = s < L.nst ? L.off[s][d] : 0;
+    info->nlevels = h->nlev;
+    return CS_OK;
+}
+
+cs_status cs_export_operator(const cs_hierarchy *h, int level, double *host) {
+    if (!h || !host) { set_error("null argument"); return CS_ERR_ARG; }
+    if (level < 0 || level >= h->nlev) { set_error("bad level"); return CS_ERR_ARG; }
+    const Level &L = h->lev[level];
+    CSX_CUDA(cudaDeviceSynchronize());
+    CSX_CUDA(cudaMemcpy(host, L.A, sizeof(double) * L.nst * L.g.N, cudaMemcpyDeviceToHost));
+    return CS_OK;
+}
+
+cs_status cs_export_colours(const cs_hierarchy *h, int level, int8_t *host) {
+    if (!h || !host) { set_error("null argument"); return CS_ERR_ARG; }
+    if (level < 0 || level >= h->nlev) { set_error("bad level"); return CS_ERR_ARG; }
+    const Grid &g = h->lev[level].g;
+    for (int iz = 0; iz < g.nz; ++iz)
+        for (int iy = 0; iy < g.ny; ++iy)
+            for (int ix = 0; ix < g.nx; ++ix)
+                host[ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz)] =
+                    (int8_t)(((ix + 1) + (iy + 1) + (g.dim == 3 ? iz + 1 : 0)) & 1);
+    return CS_OK;
+}
+
+cs_status cs_export_lambda(const cs_cascade *c, int level, double *host) {
+    if (!c || !host) { set_error("null argument"); return CS_ERR_ARG; }
+    if (level < 0 || level >= c->nlev) { set_error("bad level"); return CS_ERR_ARG; }
+    CSX_CUDA(cudaDeviceSynchronize());
+    CSX_CUDA(cudaMemcpy(host, c->lam[level], sizeof(double) * c->nu * c->h->lev[level].g.N, cudaMemcpyDeviceToHost));
+    return CS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+// Internal declarations of the cascading-smoother multigrid library.
+// Device data layout (HBM):
+//   * every level stores its operator as structure-of-arrays stencil
+//     coefficients A[s*N + i] (no index arrays: columns are implicit in the
+//     structured grid); the canonical stencil of a level is either STAR
+//     (2*dim+1 entries: C,-x,+x,-y,+y[,-z,+z]) or BOX (3^dim entries,
+//     s = (dx+1) + 3(dy+1) + 9(dz+1));
+//   * Lambda of a point-block cascade is one FP64 value per node per step,
+//     lam[l*N + i]; FP32 copies sit beside it for low-precision cycles;
+//   * vectors are contiguous N-arrays in natural (x fastest) order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cascade_mg.h"
+
+namespace csx {
+
+enum StencilKind { STAR = 0, BOX = 1 };
+
+struct Grid {
+    int dim;
+    int nx, ny, nz;
+    int64_t N;
+};
+
+struct Level {
+    Grid g;
+    int kind = STAR;
+    int nst = 0;
+    int off[27][3];
+    double *A = nullptr;  // [nst][N]
+    // work vectors (FP64): b (rhs), x (iterate), t (ping-pong)
+    double *b = nullptr, *x = nullptr, *t = nullptr;
+};
+
+struct LowLevel {   // FP32 state of one level (owned by a cascade)
+    float *A = nullptr;    // [nst][N]
+    float *lam = nullptr;  // [nu][N]
+    float *b = nullptr, *x = nullptr, *t = nullptr;
+};
+
+}  // namespace csx
+
+struct cs_hierarchy {
+    int dim = 0;
+    int nlev = 0;
+    bool periodic = false;
+    std::vector<csx::Level> lev;
+    int cn = 0;                 // coarsest size
+    double *cinv = nullptr;     // dense inverse of the coarsest operator, row-major
+    double *fine_r = nullptr;   // FP64 residual scratch, finest level
+    double *red = nullptr;      // reduction partials
+    double *red_host = nullptr; // pinned host mirror of the reduction result
+    double *hb = nullptr, *hx = nullptr; // device copies for host-buffer solves
+    int64_t bytes = 0;
+};
+
+struct cs_cascade {
+    cs_hierarchy *h = nullptr;
+    int kind = CS_ADDITIVE;
+    int nu = 1;
+    int ncol = 1;
+    int nlev = 0;               // smoothing levels
+    bool lowp = false;
+    std::vector<double *> lam;  // per level [nu][N]
+    std::vector<csx::LowLevel> lo;
+    float *fine_b32 = nullptr, *fine_x32 = nullptr;
+    // captured zero-initial-guess V-cycles, keyed by (precision, order, mu)
+    struct Graph {
+        int prec, order, mu_pre, mu_post;
+        cudaGraphExec_t exec;
+        int64_t kernels;
+    };
+    std::vector<Graph> graphs;
+    cudaStream_t capture_stream = nullptr;
+    // GMRES workspace (lazily allocated at first GMRES solve)
+    int gm_restart = 0;
+    double *gm_V = nullptr, *gm_h = nullptr;
+    int64_t bytes = 0;
+};
+
+namespace csx {
+
+// error handling ----------------------------------------------------------
+void set_error(const char *fmt, ...);
+cs_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define CSX_CUDA(call)                                                  \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return csx::cuda_fail(_e, #call, __FILE__, __LINE__); \
+    } while (0)
+#define CSX_TRY(call)                                                   \
+    do {                                                                \
+        cs_status _s = (call);                                          \
+        if (_s != CS_OK) return _s;                                     \
+    } while (0)
+
+extern std::atomic<int64_t> g_launches;
+inline void count_launch(int64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+cs_status dalloc(void **p, size_t bytes, int64_t *acct);
+template <typename T>
+cs_status dalloc_t(T **p, size_t count, int64_t *acct) {
+    return dalloc(reinterpret_cast<void **>(p), count * sizeof(T), acct);
+}
+
+inline Grid make_grid(int dim, int nx, int ny, int nz) {
+    Grid g;
+    g.dim = dim; g.nx = nx; g.ny = ny; g.nz = dim == 3 ? nz : 1;
+    g.N = (int64_t)g.nx * g.ny * g.nz;
+    return g;
+}
+
+// launch geometry: one thread per node, x fastest
+constexpr int TBX = 64, TBY = 4;
+inline dim3 node_grid(const Grid &g) {
+    return dim3((unsigned)((g.nx + TBX - 1) / TBX), (unsigned)((g.ny + TBY - 1) / TBY), (unsigned)g.nz);
+}
+inline dim3 node_block() { return dim3(TBX, TBY, 1); }
+
+// ---- stencil kernels (cs_stencil.cu)
+// out = x - lam_l (A x - b) over all nodes (additive step), or over colour
+// `colour` only (multiplicative step; other nodes copied when out != x).
+template <typename T>
+cs_status launch_sweep(const Level &L, const T *A, const T *lam, const T *b, const T *x, T *out,
+                       int colour, bool x_is_zero, cudaStream_t s);
+template <typename T>
+cs_status launch_residual_restrict(const Level &f, const Level &c, const T *A, const T *b, const T *x,
+                                   T *rc, cudaStream_t s);
+template <typename T>
+cs_status launch_prolong_correct(const Level &f, const Level &c, const T *xc, const T *x, T *xo,
+                                 cudaStream_t s);
+// r = b - A x (FP64) with FP64 or FP32-stored coefficients; optional FP32
+// copy of r and per-block partial sums of r^2 into red (nblocks entries).
+cs_status launch_residual64(const Level &L, const double *A, const double *b, const double *x,
+                            double *r, float *r32, double *red, int nred, cudaStream_t s);
+cs_status launch_coarse_solve(const cs_hierarchy *h, const double *b, double *x, cudaStream_t s);
+cs_status launch_coarse_solve32(const cs_hierarchy *h, const float *b, float *x, cudaStream_t s);
+cs_status launch_axpy_f32(int64_t N, const float *d, double *x, cudaStream_t s);  // x += d
+cs_status launch_copy_d2f(int64_t N, const double *a, float *o, cudaStream_t s);
+// sum of red[0..nred) into red[nred] (one block, fixed order)
+cs_status launch_finish_sum(double *red, int nred, cudaStream_t s);
+cs_status launch_dot(int64_t N, const double *a, const double *b, double *red, int nred, cudaStream_t s);
+cs_status launch_axpy_dev(int64_t N, const double *alpha, double sign, const double *x, double *y,
+                          cudaStream_t s);  // y += sign * (*alpha) * x
+cs_status launch_scale_dev(int64_t N, const double *num, double *y, const double *x, cudaStream_t s); // y = x / *num
+cs_status launch_matvec64(const Level &L, const double *A, const double *x, double *y, cudaStream_t s);
+cs_status launch_add64(int64_t N, const double *d, double *x, cudaStream_t s);  // x += d
+cs_status launch_axpy_multi(int64_t N, int m, const double *alpha, const double *V, double *y, cudaStream_t s);
+constexpr int NRED = 1024;  // partial sums of a reduction
+
+// ---- setup kernels (cs_setup.cu)
+cs_status galerkin_level(const Level &f, Level &c, cudaStream_t s);
+cs_status coarse_factor(cs_hierarchy *h, cudaStream_t s);
+cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, double *lam,
+                              cudaStream_t s, int64_t *peak_bytes);
+
+}  // namespace csx

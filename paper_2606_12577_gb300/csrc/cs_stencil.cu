@@ -1,0 +1,440 @@
+// Stencil kernels of the V-cycle: cascade sweeps (eq. fwda / fwdm and their
+// reverse forms), the restricted residual and the interpolated correction of
+// Algorithm 1, the bottom-level solve, and FP64 reductions.
+//
+// One thread per node; x fastest across a warp so that every coefficient
+// array A[s][.] is streamed with coalesced loads, and the neighbour reads of
+// x hit L1/L2.  These kernels are HBM-bound in FP32 (bytes per node per
+// additive step: nst*sizeof(T) + 4*sizeof(T) for A, Lambda, b, x read, x
+// written).
+#include <cstdio>
+
+#include "cs_internal.cuh"
+
+namespace csx {
+
+// canonical stencil offsets -------------------------------------------------
+template <int DIM, int KIND>
+struct Sten {
+    static constexpr int NST = KIND == STAR ? 2 * DIM + 1 : (DIM == 3 ? 27 : 9);
+    static __host__ __device__ __forceinline__ void off(int s, int &dx, int &dy, int &dz) {
+        if (KIND == STAR) {
+            dx = dy = dz = 0;
+            if (s == 1) dx = -1;
+            else if (s == 2) dx = 1;
+            else if (s == 3) dy = -1;
+            else if (s == 4) dy = 1;
+            else if (s == 5) dz = -1;
+            else if (s == 6) dz = 1;
+        } else {
+            dx = s % 3 - 1;
+            dy = (s / 3) % 3 - 1;
+            dz = DIM == 3 ? s / 9 - 1 : 0;
+        }
+    }
+};
+
+template <typename T> struct AccT { using type = T; };
+
+__device__ __forceinline__ int node_colour(int dim, int ix, int iy, int iz) {
+    return ((ix + 1) + (iy + 1) + (dim == 3 ? iz + 1 : 0)) & 1;
+}
+
+// (A x)_i at node (ix,iy,iz); neighbours outside the grid contribute nothing
+template <int DIM, int KIND, typename T>
+__device__ __forceinline__ T apply_row(const Grid &g, const T *__restrict__ A, const T *x, int ix, int iy, int iz,
+                                       int64_t i) {
+    using S = Sten<DIM, KIND>;
+    T ax = T(0);
+#pragma unroll
+    for (int s = 0; s < S::NST; ++s) {
+        int dx, dy, dz;
+        S::off(s, dx, dy, dz);
+        bool in = (unsigned)(ix + dx) < (unsigned)g.nx && (unsigned)(iy + dy) < (unsigned)g.ny &&
+                  (DIM == 2 || (unsigned)(iz + dz) < (unsigned)g.nz);
+        T a = A[(int64_t)s * g.N + i];
+        T xv = in ? x[i + dx + (int64_t)g.nx * (dy + (int64_t)g.ny * dz)] : T(0);
+        ax = fma(a, xv, ax);
+    }
+    return ax;
+}
+
+// Cascade step: out_i = x_i - lam_i ((A x)_i - b_i).
+// COL < 0: every node (additive step, out != x).
+// COL >= 0: only nodes of colour `colour`; the others keep x (copied when
+// out != x, i.e. snapshot semantics for non-graph colourings).
+template <int DIM, int KIND, typename T, bool COLOURED>
+__global__ void __launch_bounds__(TBX *TBY) k_sweep(Grid g, const T *__restrict__ A, const T *__restrict__ lam,
+                                                     const T *__restrict__ b, const T *x, T *out, int colour,
+                                                     int xzero) {
+    int ix = blockIdx.x * TBX + threadIdx.x;
+    int iy = blockIdx.y * TBY + threadIdx.y;
+    int iz = blockIdx.z;
+    if (ix >= g.nx || iy >= g.ny) return;
+    int64_t i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
+    if (COLOURED) {
+        if (node_colour(DIM, ix, iy, iz) != colour) {
+            if (xzero) out[i] = T(0);
+            else if (out != x) out[i] = x[i];
+            return;
+        }
+    }
+    T r;
+    T xi;
+    if (xzero) {
+        r = -b[i];
+        xi = T(0);
+    } else {
+        r = apply_row<DIM, KIND, T>(g, A, x, ix, iy, iz, i) - b[i];
+        xi = x[i];
+    }
+    out[i] = xi - lam[i] * r;
+}
+
+template <typename T, bool COLOURED>
+static cs_status sweep_dispatch(const Level &L, const T *A, const T *lam, const T *b, const T *x, T *out,
+                                int colour, bool xzero, cudaStream_t s) {
+    dim3 gr = node_grid(L.g), bl = node_block();
+    int xz = xzero ? 1 : 0;
+    if (L.g.dim == 2) {
+        if (L.kind == STAR) k_sweep<2, STAR, T, COLOURED><<<gr, bl, 0, s>>>(L.g, A, lam, b, x, out, colour, xz);
+        else k_sweep<2, BOX, T, COLOURED><<<gr, bl, 0, s>>>(L.g, A, lam, b, x, out, colour, xz);
+    } else {
+        if (L.kind == STAR) k_sweep<3, STAR, T, COLOURED><<<gr, bl, 0, s>>>(L.g, A, lam, b, x, out, colour, xz);
+        else k_sweep<3, BOX, T, COLOURED><<<gr, bl, 0, s>>>(L.g, A, lam, b, x, out, colour, xz);
+    }
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+
+template <typename T>
+cs_status launch_sweep(const Level &L, const T *A, const T *lam, const T *b, const T *x, T *out, int colour,
+                       bool x_is_zero, cudaStream_t s) {
+    if (colour < 0) return sweep_dispatch<T, false>(L, A, lam, b, x, out, -1, x_is_zero, s);
+    return sweep_dispatch<T, true>(L, A, lam, b, x, out, colour, x_is_zero, s);
+}
+template cs_status launch_sweep<double>(const Level &, const double *, const double *, const double *,
+                                        const double *, double *, int, bool, cudaStream_t);
+template cs_status launch_sweep<float>(const Level &, const float *, const float *, const float *, const float *,
+                                       float *, int, bool, cudaStream_t);
+
+// rc_I = 2^-dim sum_f P_{f,I} (A x - b)_f.  Coarse node I sits on fine node
+// 2I+1 (0-based); its fine neighbours 2I+1+d (d in {-1,0,1}) carry weight
+// 1/2 per nonzero component of d (bilinear / trilinear interpolation).
+template <int DIM, int KIND, typename T>
+__global__ void __launch_bounds__(TBX *TBY) k_res_restrict(Grid gf, Grid gc, const T *__restrict__ A,
+                                                            const T *__restrict__ b, const T *__restrict__ x,
+                                                            T *__restrict__ rc) {
+    int cx = blockIdx.x * TBX + threadIdx.x;
+    int cy = blockIdx.y * TBY + threadIdx.y;
+    int cz = blockIdx.z;
+    if (cx >= gc.nx || cy >= gc.ny) return;
+    T acc = T(0);
+    const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz) {
+        int fz = DIM == 3 ? 2 * cz + 1 + dz : 0;
+        if (DIM == 3 && fz >= gf.nz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            int fy = 2 * cy + 1 + dy;
+            if (fy >= gf.ny) continue;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                int fx = 2 * cx + 1 + dx;
+                if (fx >= gf.nx) continue;
+                T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+                int64_t f = fx + (int64_t)gf.nx * (fy + (int64_t)gf.ny * fz);
+                T r = apply_row<DIM, KIND, T>(gf, A, x, fx, fy, fz, f) - b[f];
+                acc = fma(w, r, acc);
+            }
+        }
+    }
+    rc[cx + (int64_t)gc.nx * (cy + (int64_t)gc.ny * cz)] = acc * T(DIM == 3 ? 0.125 : 0.25);
+}
+
+template <typename T>
+cs_status launch_residual_restrict(const Level &f, const Level &c, const T *A, const T *b, const T *x, T *rc,
+                                   cudaStream_t s) {
+    dim3 gr = node_grid(c.g), bl = node_block();
+    if (f.g.dim == 2) {
+        if (f.kind == STAR) k_res_restrict<2, STAR, T><<<gr, bl, 0, s>>>(f.g, c.g, A, b, x, rc);
+        else k_res_restrict<2, BOX, T><<<gr, bl, 0, s>>>(f.g, c.g, A, b, x, rc);
+    } else {
+        if (f.kind == STAR) k_res_restrict<3, STAR, T><<<gr, bl, 0, s>>>(f.g, c.g, A, b, x, rc);
+        else k_res_restrict<3, BOX, T><<<gr, bl, 0, s>>>(f.g, c.g, A, b, x, rc);
+    }
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+template cs_status launch_residual_restrict<double>(const Level &, const Level &, const double *, const double *,
+                                                    const double *, double *, cudaStream_t);
+template cs_status launch_residual_restrict<float>(const Level &, const Level &, const float *, const float *,
+                                                   const float *, float *, cudaStream_t);
+
+// 1D interpolation weights of fine node f (0-based) from coarse nodes: an
+// odd f coincides with coarse (f-1)/2; an even f takes half of coarse f/2-1
+// and f/2 (those inside the coarse grid).
+__device__ __forceinline__ int p1d(int f, int nc, int *c, float *w) {
+    if (f & 1) {
+        c[0] = (f - 1) >> 1; w[0] = 1.f;
+        return 1;
+    }
+    int k = 0, lo = (f >> 1) - 1, hi = f >> 1;
+    if (lo >= 0) { c[k] = lo; w[k] = 0.5f; ++k; }
+    if (hi < nc) { c[k] = hi; w[k] = 0.5f; ++k; }
+    return k;
+}
+
+// xo_f = x_f - sum_I P_{f,I} xc_I
+template <int DIM, typename T>
+__global__ void __launch_bounds__(TBX *TBY) k_prolong(Grid gf, Grid gc, const T *__restrict__ xc, const T *x,
+                                                       T *xo) {
+    int fx = blockIdx.x * TBX + threadIdx.x;
+    int fy = blockIdx.y * TBY + threadIdx.y;
+    int fz = blockIdx.z;
+    if (fx >= gf.nx || fy >= gf.ny) return;
+    int cxs[2], cys[2], czs[2];
+    float wx[2], wy[2], wz[2];
+    int kx = p1d(fx, gc.nx, cxs, wx);
+    int ky = p1d(fy, gc.ny, cys, wy);
+    int kz = 1;
+    czs[0] = 0; wz[0] = 1.f;
+    if (DIM == 3) kz = p1d(fz, gc.nz, czs, wz);
+    T acc = T(0);
+    for (int c = 0; c < kz; ++c)
+        for (int bb = 0; bb < ky; ++bb)
+            for (int a = 0; a < kx; ++a)
+                acc = fma(T(wx[a] * wy[bb] * wz[c]), xc[cxs[a] + (int64_t)gc.nx * (cys[bb] + (int64_t)gc.ny * czs[c])],
+                          acc);
+    int64_t f = fx + (int64_t)gf.nx * (fy + (int64_t)gf.ny * fz);
+    xo[f] = x[f] - acc;
+}
+
+template <typename T>
+cs_status launch_prolong_correct(const Level &f, const Level &c, const T *xc, const T *x, T *xo, cudaStream_t s) {
+    dim3 gr = node_grid(f.g), bl = node_block();
+    if (f.g.dim == 2) k_prolong<2, T><<<gr, bl, 0, s>>>(f.g, c.g, xc, x, xo);
+    else k_prolong<3, T><<<gr, bl, 0, s>>>(f.g, c.g, xc, x, xo);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+template cs_status launch_prolong_correct<double>(const Level &, const Level &, const double *, const double *,
+                                                  double *, cudaStream_t);
+template cs_status launch_prolong_correct<float>(const Level &, const Level &, const float *, const float *,
+                                                 float *, cudaStream_t);
+
+// block-wide deterministic sum (fixed tree order)
+__device__ __forceinline__ double block_sum(double v, double *sm) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
+    int warp = (threadIdx.x + threadIdx.y * blockDim.x) >> 5;
+    int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < nw ? sm[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    return t;
+}
+
+// r = b - A x in FP64; per-block partial sums of r^2 into red[block id]
+template <int DIM, int KIND>
+__global__ void __launch_bounds__(TBX *TBY) k_residual64(Grid g, const double *__restrict__ A,
+                                                          const double *__restrict__ b, const double *__restrict__ x,
+                                                          double *__restrict__ r, float *__restrict__ r32,
+                                                          double *__restrict__ red) {
+    __shared__ double sm[32];
+    int ix = blockIdx.x * TBX + threadIdx.x;
+    int iy = blockIdx.y * TBY + threadIdx.y;
+    int iz = blockIdx.z;
+    double v = 0.0;
+    if (ix < g.nx && iy < g.ny) {
+        int64_t i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
+        v = b[i] - apply_row<DIM, KIND, double>(g, A, x, ix, iy, iz, i);
+        if (r) r[i] = v;
+        if (r32) r32[i] = (float)v;
+    }
+    if (red) {
+        double t = block_sum(v * v, sm);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            red[blockIdx.x + gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z)] = t;
+    }
+}
+
+cs_status launch_residual64(const Level &L, const double *A, const double *b, const double *x, double *r,
+                            float *r32, double *red, int nred, cudaStream_t s) {
+    dim3 gr = node_grid(L.g), bl = node_block();
+    if (red && (int64_t)gr.x * gr.y * gr.z != nred) {
+        set_error("internal: reduction size mismatch");
+        return CS_ERR_ARG;
+    }
+    if (L.g.dim == 2) {
+        if (L.kind == STAR) k_residual64<2, STAR><<<gr, bl, 0, s>>>(L.g, A, b, x, r, r32, red);
+        else k_residual64<2, BOX><<<gr, bl, 0, s>>>(L.g, A, b, x, r, r32, red);
+    } else {
+        if (L.kind == STAR) k_residual64<3, STAR><<<gr, bl, 0, s>>>(L.g, A, b, x, r, r32, red);
+        else k_residual64<3, BOX><<<gr, bl, 0, s>>>(L.g, A, b, x, r, r32, red);
+    }
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+
+__global__ void k_finish_sum(double *red, int n) {
+    __shared__ double sm[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += red[i];
+    double t = block_sum(v, sm);
+    if (threadIdx.x == 0) red[n] = t;
+}
+cs_status launch_finish_sum(double *red, int nred, cudaStream_t s) {
+    k_finish_sum<<<1, 1024, 0, s>>>(red, nred);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+
+__global__ void k_dot(int64_t N, const double *__restrict__ a, const double *__restrict__ b, double *red) {
+    __shared__ double sm[32];
+    double v = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        v = fma(a[i], b[i], v);
+    double t = block_sum(v, sm);
+    if (threadIdx.x == 0) red[blockIdx.x] = t;
+}
+cs_status launch_dot(int64_t N, const double *a, const double *b, double *red, int nred, cudaStream_t s) {
+    k_dot<<<nred, 256, 0, s>>>(N, a, b, red);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return launch_finish_sum(red, nred, s);
+}
+
+__global__ void k_axpy_dev(int64_t N, const double *alpha, double sign, const double *__restrict__ x,
+                           double *__restrict__ y) {
+    double a = sign * *alpha;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = fma(a, x[i], y[i]);
+}
+cs_status launch_axpy_dev(int64_t N, const double *alpha, double sign, const double *x, double *y, cudaStream_t s) {
+    k_axpy_dev<<<1216, 256, 0, s>>>(N, alpha, sign, x, y);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+__global__ void k_scale_dev(int64_t N, const double *num, double *y, const double *__restrict__ x) {
+    double inv = 1.0 / sqrt(*num);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = x[i] * inv;
+}
+// y = x / sqrt(*num)
+cs_status launch_scale_dev(int64_t N, const double *num, double *y, const double *x, cudaStream_t s) {
+    k_scale_dev<<<1216, 256, 0, s>>>(N, num, y, x);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+
+__global__ void k_axpy_f32(int64_t N, const float *__restrict__ d, double *__restrict__ x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += (double)d[i];
+}
+cs_status launch_axpy_f32(int64_t N, const float *d, double *x, cudaStream_t s) {
+    k_axpy_f32<<<1216, 256, 0, s>>>(N, d, x);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+__global__ void k_d2f(int64_t N, const double *__restrict__ a, float *__restrict__ o) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        o[i] = (float)a[i];
+}
+cs_status launch_copy_d2f(int64_t N, const double *a, float *o, cudaStream_t s) {
+    k_d2f<<<1216, 256, 0, s>>>(N, a, o);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+
+// y = A x (FP64)
+template <int DIM, int KIND>
+__global__ void __launch_bounds__(TBX *TBY) k_matvec64(Grid g, const double *__restrict__ A,
+                                                        const double *__restrict__ x, double *__restrict__ y) {
+    int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
+    if (ix >= g.nx || iy >= g.ny) return;
+    int64_t i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
+    y[i] = apply_row<DIM, KIND, double>(g, A, x, ix, iy, iz, i);
+}
+cs_status launch_matvec64(const Level &L, const double *A, const double *x, double *y, cudaStream_t s) {
+    dim3 gr = node_grid(L.g), bl = node_block();
+    if (L.g.dim == 2) {
+        if (L.kind == STAR) k_matvec64<2, STAR><<<gr, bl, 0, s>>>(L.g, A, x, y);
+        else k_matvec64<2, BOX><<<gr, bl, 0, s>>>(L.g, A, x, y);
+    } else {
+        if (L.kind == STAR) k_matvec64<3, STAR><<<gr, bl, 0, s>>>(L.g, A, x, y);
+        else k_matvec64<3, BOX><<<gr, bl, 0, s>>>(L.g, A, x, y);
+    }
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+
+__global__ void k_add64(int64_t N, const double *__restrict__ d, double *__restrict__ x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += d[i];
+}
+cs_status launch_add64(int64_t N, const double *d, double *x, cudaStream_t s) {
+    k_add64<<<1216, 256, 0, s>>>(N, d, x);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+
+// y += alpha_host * x with alpha from device memory slot
+__global__ void k_axpy_vec(int64_t N, int m, const double *__restrict__ alpha, const double *__restrict__ V,
+                           double *__restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = y[i];
+        for (int k = 0; k < m; ++k) s = fma(alpha[k], V[(int64_t)k * N + i], s);
+        y[i] = s;
+    }
+}
+// y += sum_k alpha[k] V[k]  (alpha: device array of m values)
+cs_status launch_axpy_multi(int64_t N, int m, const double *alpha, const double *V, double *y, cudaStream_t s) {
+    k_axpy_vec<<<1216, 256, 0, s>>>(N, m, alpha, V, y);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+
+// x = Cinv b (bottom-level direct solve with the inverse formed at setup):
+// one warp per row, FP64
+template <typename T>
+__global__ void k_coarse_solve(int n, const double *__restrict__ Cinv, const T *__restrict__ b, T *__restrict__ x) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s = fma(Cinv[(int64_t)warp * n + j], (double)b[j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) x[warp] = (T)s;
+}
+cs_status launch_coarse_solve(const cs_hierarchy *h, const double *b, double *x, cudaStream_t s) {
+    int threads = 256, blocks = (h->cn * 32 + threads - 1) / threads;
+    k_coarse_solve<double><<<blocks, threads, 0, s>>>(h->cn, h->cinv, b, x);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+cs_status launch_coarse_solve32(const cs_hierarchy *h, const float *b, float *x, cudaStream_t s) {
+    int threads = 256, blocks = (h->cn * 32 + threads - 1) / threads;
+    k_coarse_solve<float><<<blocks, threads, 0, s>>>(h->cn, h->cinv, b, x);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+
+}  // namespace csx
