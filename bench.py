@@ -51,6 +51,8 @@ def args_():
     p.add_argument("--order", default="RF")
     p.add_argument("--cpu-n", type=int, default=64, help="side of the oracle's bounded sample")
     p.add_argument("--no-extras", action="store_true", help="time the chosen form only")
+    p.add_argument("--profile", default="", choices=["", "setup", "step"],
+                   help="run one untimed setup (or setup + solve) and exit: the case ncu captures")
     return p.parse_args()
 
 
@@ -240,6 +242,17 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
         return ms
+
+    if a.profile:
+        h = cmg.setup_hierarchy(A.dim, A.n, A.offsets, coeff)
+        c = cmg.setup_cascade(h, a.kind, nu=a.nu, lowp=True)
+        if a.profile == "step":
+            x = torch.zeros(A.N, dtype=torch.float64, device=dev)
+            cmg.solve(h, c, bd, x, method="refine", precision="fp32", tol=1e-10, mu_pre=mu, mu_post=mu,
+                      order=a.order)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": a.profile, "n": a.n, "launches": cmg.kernel_launches()}), flush=True)
+        return
 
     infos = []
     # ---- chosen form: FP32 cycle in FP64 iterative refinement

@@ -110,7 +110,7 @@ static bool inplace_colours(const cs_cascade *c, const Level &L) {
 // iterate (updated); `xzero` marks an all-zero iterate (cleared on return)
 template <typename T>
 static cs_status smooth_apply(const cs_hierarchy *h, const cs_cascade *c, int l, const View<T> &v, const T *b,
-                              T *&cur, T *other, bool reverse, bool &xzero, cudaStream_t s) {
+                              T *&cur, T *&other, bool reverse, bool &xzero, cudaStream_t s) {
     const Level &L = h->lev[l];
     const int64_t N = L.g.N;
     const bool inpl = inplace_colours(c, L);
@@ -271,7 +271,7 @@ cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts
     if (dim != 2 && dim != 3) { set_error("dim must be 2 or 3"); return CS_ERR_ARG; }
     int n[3] = {A0->n[0], A0->n[1], dim == 3 ? A0->n[2] : 1};
     if (n[0] < 1 || n[1] < 1 || n[2] < 1 || (dim == 2 && A0->n[2] > 1)) { set_error("bad grid size"); return CS_ERR_ARG; }
-    if ((int64_t)n[0] * n[1] * n[2] > (int64_t)1 << 31) { set_error("grid too large (N must fit in 31 bits)"); return CS_ERR_ARG; }
+    if ((int64_t)n[0] * n[1] * n[2] >= (int64_t)1 << 31) { set_error("grid too large (N must fit in 31 bits)"); return CS_ERR_ARG; }
     if (A0->nst < 1 || A0->nst > 27 || !A0->coeff) { set_error("bad stencil"); return CS_ERR_ARG; }
     if (opts.block != 1) { set_error("only point blocks (block = 1) are implemented"); return CS_ERR_UNSUPPORTED; }
     bool star = true, centre = false;

@@ -48,73 +48,81 @@ struct StenS {
 };
 
 // ------------------------------------------------------------ Galerkin RAP
-__device__ __forceinline__ int p1d_s(int f, int nc, int *c, double *w) {
-    if (f & 1) { c[0] = (f - 1) >> 1; w[0] = 1.0; return 1; }
-    int k = 0, lo = (f >> 1) - 1, hi = f >> 1;
-    if (lo >= 0) { c[k] = lo; w[k] = 0.5; ++k; }
-    if (hi < nc) { c[k] = hi; w[k] = 0.5; ++k; }
-    return k;
-}
+// 1D interpolation weight between fine node 2J+1+u and coarse node J:
+// 1 at u = 0, 1/2 at u = +-1, else 0.
+__host__ __device__ constexpr double pw(int u) { return u == 0 ? 1.0 : ((u == 1 || u == -1) ? 0.5 : 0.0); }
 
-// Ac_{I, I+dJ} = 2^-dim sum_{i,j} P_{i,I} A_{i,j} P_{j,I+dJ}; the result is
-// stored as a BOX stencil (dJ in {-1,0,1}^dim).
+// Ac_{I, I+dJ} = 2^-dim sum_{f,j} P_{f,I} A_{f,j} P_{j,I+dJ}, stored as a BOX
+// stencil (dJ in {-1,0,1}^dim).  With f = 2I+1+d and j = f+s, A_s(f) enters
+// entry dJ with weight prod_k pw(d_k) pw(d_k + s_k - 2 dJ_k); per axis
+// u = d_k + s_k in [-2, 2] selects one coarse neighbour (u even) or two with
+// weight 1/2 (u odd).  The 3^dim accumulators of a thread live in shared
+// memory (registers would need dynamic indexing).  Couplings to nodes
+// outside the grid are zero coefficients; fine nodes beyond the upper edge
+// are skipped; entries whose coarse neighbour lies outside are set to zero.
 template <int DIM, int KIND>
-__global__ void k_galerkin(Grid gf, Grid gc, const double *__restrict__ Af, double *__restrict__ Ac) {
+__global__ void __launch_bounds__(TBX *TBY) k_galerkin(Grid gf, Grid gc, const double *__restrict__ Af,
+                                                        double *__restrict__ Ac) {
     using S = StenS<DIM, KIND>;
     constexpr int NC = DIM == 3 ? 27 : 9;
-    int cx = blockIdx.x * TBX + threadIdx.x, cy = blockIdx.y * TBY + threadIdx.y, cz = blockIdx.z;
-    if (cx >= gc.nx || cy >= gc.ny) return;
-    double acc[NC];
+    extern __shared__ double acc_sm[];  // [NC][TBX*TBY]
+    const int tid = threadIdx.x + TBX * threadIdx.y;
+    double *acc = acc_sm + tid;
 #pragma unroll
-    for (int t = 0; t < NC; ++t) acc[t] = 0.0;
-    const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
-    for (int ez = zlo; ez <= zhi; ++ez) {
-        int fz = DIM == 3 ? 2 * cz + 1 + ez : 0;
-        if (DIM == 3 && fz >= gf.nz) continue;
-        for (int ey = -1; ey <= 1; ++ey) {
-            int fy = 2 * cy + 1 + ey;
-            if (fy >= gf.ny) continue;
-            for (int ex = -1; ex <= 1; ++ex) {
-                int fx = 2 * cx + 1 + ex;
-                if (fx >= gf.nx) continue;
-                double wr = (ex ? 0.5 : 1.0) * (ey ? 0.5 : 1.0) * (ez ? 0.5 : 1.0);
-                int64_t fi = fx + (int64_t)gf.nx * (fy + (int64_t)gf.ny * fz);
-                for (int s = 0; s < S::NST; ++s) {
-                    int dx, dy, dz;
-                    S::off(s, dx, dy, dz);
-                    int jx = fx + dx, jy = fy + dy, jz = fz + dz;
-                    if (jx < 0 || jx >= gf.nx || jy < 0 || jy >= gf.ny) continue;
-                    if (DIM == 3 && (jz < 0 || jz >= gf.nz)) continue;
-                    double a = wr * Af[(int64_t)s * gf.N + fi];
-                    int Jx[2], Jy[2], Jz[2];
-                    double wx[2], wy[2], wz[2];
-                    int kx = p1d_s(jx, gc.nx, Jx, wx), ky = p1d_s(jy, gc.ny, Jy, wy), kz = 1;
-                    Jz[0] = cz; wz[0] = 1.0;
-                    if (DIM == 3) kz = p1d_s(jz, gc.nz, Jz, wz);
-                    for (int c = 0; c < kz; ++c)
-                        for (int b = 0; b < ky; ++b)
-                            for (int q = 0; q < kx; ++q) {
-                                int t = (Jx[q] - cx + 1) + 3 * (Jy[b] - cy + 1) + (DIM == 3 ? 9 * (Jz[c] - cz + 1) : 0);
-                                acc[t] += a * wx[q] * wy[b] * wz[c];
-                            }
-                }
-            }
+    for (int t = 0; t < NC; ++t) acc[t * TBX * TBY] = 0.0;
+    const int cx = blockIdx.x * TBX + threadIdx.x, cy = blockIdx.y * TBY + threadIdx.y, cz = blockIdx.z;
+    if (cx >= gc.nx || cy >= gc.ny) return;
+    for (int e = 0; e < NC; ++e) {
+        const int ex = e % 3 - 1, ey = (e / 3) % 3 - 1, ez = DIM == 3 ? e / 9 - 1 : 0;
+        const int fx = 2 * cx + 1 + ex, fy = 2 * cy + 1 + ey, fz = DIM == 3 ? 2 * cz + 1 + ez : 0;
+        if (fx >= gf.nx || fy >= gf.ny || (DIM == 3 && fz >= gf.nz)) continue;
+        const int64_t fi = fx + (int64_t)gf.nx * (fy + (int64_t)gf.ny * fz);
+        const double wr = pw(ex) * pw(ey) * pw(ez);
+#pragma unroll
+        for (int s = 0; s < S::NST; ++s) {
+            int dx, dy, dz;
+            S::off(s, dx, dy, dz);
+            const double a = wr * Af[(int64_t)s * gf.N + fi];
+            // per axis: target offsets j0 (weight w0) and, for odd u, j0+1
+            const int ux = ex + dx, uy = ey + dy, uz = ez + dz;
+            const int jx0 = (ux - 1) >> 1, jy0 = (uy - 1) >> 1, jz0 = (uz - 1) >> 1;  // floor((u-1)/2)
+            const int nxj = (ux & 1) ? 2 : 1, nyj = (uy & 1) ? 2 : 1, nzj = DIM == 3 ? ((uz & 1) ? 2 : 1) : 1;
+            const int bx = (ux & 1) ? jx0 : ux >> 1, by = (uy & 1) ? jy0 : uy >> 1, bz = (uz & 1) ? jz0 : uz >> 1;
+            const double wx = (ux & 1) ? 0.5 : 1.0, wy = (uy & 1) ? 0.5 : 1.0, wz = (DIM == 3 && (uz & 1)) ? 0.5 : 1.0;
+            const double awx = a * wx * wy * wz;
+            for (int kz = 0; kz < nzj; ++kz)
+                for (int ky = 0; ky < nyj; ++ky)
+                    for (int kx = 0; kx < nxj; ++kx) {
+                        const int t = (bx + kx + 1) + 3 * (by + ky + 1) + (DIM == 3 ? 9 * (bz + kz + 1) : 0);
+                        acc[t * TBX * TBY] += awx;
+                    }
         }
     }
-    int64_t ci = cx + (int64_t)gc.nx * (cy + (int64_t)gc.ny * cz);
+    const int64_t ci = cx + (int64_t)gc.nx * (cy + (int64_t)gc.ny * cz);
     const double sc = DIM == 3 ? 0.125 : 0.25;
 #pragma unroll
-    for (int t = 0; t < NC; ++t) Ac[(int64_t)t * gc.N + ci] = sc * acc[t];
+    for (int t = 0; t < NC; ++t) {
+        const int jx = cx + t % 3 - 1, jy = cy + (t / 3) % 3 - 1, jz = DIM == 3 ? cz + t / 9 - 1 : 0;
+        const bool in = jx >= 0 && jx < gc.nx && jy >= 0 && jy < gc.ny && (DIM == 2 || (jz >= 0 && jz < gc.nz));
+        Ac[(int64_t)t * gc.N + ci] = in ? sc * acc[t * TBX * TBY] : 0.0;
+    }
 }
 
 cs_status galerkin_level(const Level &f, Level &c, cudaStream_t s) {
     dim3 gr = node_grid(c.g), bl = node_block();
+    const size_t sm2 = sizeof(double) * 9 * TBX * TBY, sm3 = sizeof(double) * 27 * TBX * TBY;
     if (f.g.dim == 2) {
-        if (f.kind == STAR) k_galerkin<2, STAR><<<gr, bl, 0, s>>>(f.g, c.g, f.A, c.A);
-        else k_galerkin<2, BOX><<<gr, bl, 0, s>>>(f.g, c.g, f.A, c.A);
+        if (f.kind == STAR) k_galerkin<2, STAR><<<gr, bl, sm2, s>>>(f.g, c.g, f.A, c.A);
+        else k_galerkin<2, BOX><<<gr, bl, sm2, s>>>(f.g, c.g, f.A, c.A);
     } else {
-        if (f.kind == STAR) k_galerkin<3, STAR><<<gr, bl, 0, s>>>(f.g, c.g, f.A, c.A);
-        else k_galerkin<3, BOX><<<gr, bl, 0, s>>>(f.g, c.g, f.A, c.A);
+        static bool attr = false;  // 27 x 256 doubles = 54 KB exceeds the default 48 KB
+        if (!attr) {
+            CSX_CUDA(cudaFuncSetAttribute(k_galerkin<3, STAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+            CSX_CUDA(cudaFuncSetAttribute(k_galerkin<3, BOX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+            attr = true;
+        }
+        if (f.kind == STAR) k_galerkin<3, STAR><<<gr, bl, sm3, s>>>(f.g, c.g, f.A, c.A);
+        else k_galerkin<3, BOX><<<gr, bl, sm3, s>>>(f.g, c.g, f.A, c.A);
     }
     CSX_CUDA(cudaGetLastError());
     count_launch();
@@ -324,31 +332,41 @@ __global__ void k_fill(int64_t n, double *p, double v) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
 
-// One setup step (l, k): see the file header.  pairs[o'*NST + s] is the
-// index in O_cur of o' - offset(s), or -1; cur_of[o'] is the index of o' in
-// O_cur or -1.
-template <int DIM, int KIND>
-__global__ void __launch_bounds__(TBX *TBY) k_setup_step(Grid g, int periodic, const double *__restrict__ At,
+// One setup step (l, k) over rows and a chunk of output offsets o'.
+// Per o' the host supplies (uniform across a warp): mask[o'] with bit s set
+// when o' - off(s) is in O_cur, its index cidx[o'*NST + s], and cur_of[o']
+// (index of o' in O_cur or -1).  Neighbours outside the grid carry a zero
+// prescaled coefficient, so they are read at the row itself (no branch).
+// nchunks == 1: the thread finishes the row (lambda, residual update);
+// otherwise partial <E_i,R_i>, <R_i,R_i> go to part[q*N + i] and
+// k_setup_finish completes the row.  LAST: the final step of the cascade,
+// where E_nu is not needed -- R is neither stored nor used to update E.
+template <int DIM, int KIND, bool LAST>
+__global__ void __launch_bounds__(TBX *TBY) k_setup_rows(Grid g, int periodic, const double *__restrict__ At,
                                                           const double *__restrict__ w, const double *__restrict__ Ecur,
-                                                          double *__restrict__ Enxt, int nnxt,
-                                                          const int *__restrict__ pairs, const int *__restrict__ cur_of,
-                                                          int colour, double *__restrict__ lam) {
+                                                          double *__restrict__ Enxt, int nnxt, int chunk, int nchunks,
+                                                          const unsigned *__restrict__ mask, const int *__restrict__ cidx,
+                                                          const int *__restrict__ cur_of, int colour,
+                                                          double *__restrict__ lam, double2 *__restrict__ part) {
     using S = StenS<DIM, KIND>;
     constexpr int NST = S::NST;
-    int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
+    const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y;
+    const int iz = (int)(blockIdx.z % (unsigned)g.nz), q = (int)(blockIdx.z / (unsigned)g.nz);
     if (ix >= g.nx || iy >= g.ny) return;
     const int64_t N = g.N;
-    int64_t i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
-    bool active = colour < 0 || ((((ix + 1) + (iy + 1) + (DIM == 3 ? iz + 1 : 0)) & 1) == colour);
+    const int i = ix + g.nx * (iy + g.ny * iz);
+    const int o0 = q * chunk, o1 = min(nnxt, o0 + chunk);
+    const bool active = colour < 0 || ((((ix + 1) + (iy + 1) + (DIM == 3 ? iz + 1 : 0)) & 1) == colour);
     if (!active) {
-        for (int o = 0; o < nnxt; ++o) {
-            int c = __ldg(cur_of + o);
-            Enxt[(int64_t)o * N + i] = c >= 0 ? Ecur[(int64_t)c * N + i] : 0.0;
-        }
+        if (!LAST)
+            for (int o = o0; o < o1; ++o) {
+                int c = __ldg(cur_of + o);
+                Enxt[(int64_t)o * N + i] = c >= 0 ? Ecur[(int64_t)c * N + i] : 0.0;
+            }
         return;
     }
     double a[NST];
-    int64_t nb[NST];
+    int nb[NST];
 #pragma unroll
     for (int s = 0; s < NST; ++s) {
         int dx, dy, dz;
@@ -361,33 +379,85 @@ __global__ void __launch_bounds__(TBX *TBY) k_setup_step(Grid g, int periodic, c
         } else {
             in = jx >= 0 && jx < g.nx && jy >= 0 && jy < g.ny && (DIM == 2 || (jz >= 0 && jz < g.nz));
         }
-        nb[s] = in ? jx + (int64_t)g.nx * (jy + (int64_t)g.ny * jz) : -1;
-        a[s] = At[(int64_t)s * N + i];
+        nb[s] = in ? jx + g.nx * (jy + g.ny * jz) : i;
+        a[s] = in ? At[(int64_t)s * N + i] : 0.0;
     }
     double num = 0.0, den = 0.0;
-    for (int o = 0; o < nnxt; ++o) {
+    for (int o = o0; o < o1; ++o) {
+        const unsigned m = __ldg(mask + o);
+        const int *co = cidx + o * NST;
         double r = 0.0;
 #pragma unroll
-        for (int s = 0; s < NST; ++s) {
-            int c = __ldg(pairs + o * NST + s);
-            if (c >= 0 && nb[s] >= 0) r = fma(a[s], Ecur[(int64_t)c * N + nb[s]], r);
-        }
-        int c0 = __ldg(cur_of + o);
-        double e = c0 >= 0 ? Ecur[(int64_t)c0 * N + i] : 0.0;
-        num = fma(e, r, num);
+        for (int s = 0; s < NST; ++s)
+            if (m & (1u << s)) r = fma(a[s], Ecur[(int64_t)__ldg(co + s) * N + nb[s]], r);
+        const int c0 = __ldg(cur_of + o);
+        if (c0 >= 0) num = fma(Ecur[(int64_t)c0 * N + i], r, num);
         den = fma(r, r, den);
-        Enxt[(int64_t)o * N + i] = r;
+        if (!LAST) Enxt[(int64_t)o * N + i] = r;
+    }
+    if (nchunks > 1) {
+        part[(int64_t)q * N + i] = make_double2(num, den);
+        return;
     }
     // normal equations of the 1 x 1 least-squares problem; a zero row R_i
     // (pivot <= 1e-14 tr(G) = 0) gives the minimum-norm solution 0
-    double lt = den > 0.0 ? num / den : 0.0;
-    for (int o = 0; o < nnxt; ++o) {
-        int c0 = __ldg(cur_of + o);
-        double e = c0 >= 0 ? Ecur[(int64_t)c0 * N + i] : 0.0;
+    const double lt = den > 0.0 ? num / den : 0.0;
+    if (!LAST)
+        for (int o = o0; o < o1; ++o) {
+            const int c0 = __ldg(cur_of + o);
+            const double e = c0 >= 0 ? Ecur[(int64_t)c0 * N + i] : 0.0;
+            Enxt[(int64_t)o * N + i] = e - lt * Enxt[(int64_t)o * N + i];
+        }
+    const double wi = w[i];
+    lam[i] = wi * lt * wi;
+}
+
+// Completes rows processed in several chunks: sums the partial inner
+// products in chunk order, forms lambda and (unless LAST) updates this
+// chunk's entries of E.
+template <int DIM, bool LAST>
+__global__ void __launch_bounds__(TBX *TBY) k_setup_finish(Grid g, const double *__restrict__ w,
+                                                            const double *__restrict__ Ecur, double *__restrict__ Enxt,
+                                                            int nnxt, int chunk, int nchunks,
+                                                            const int *__restrict__ cur_of, int colour,
+                                                            double *__restrict__ lam, const double2 *__restrict__ part) {
+    const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y;
+    const int iz = (int)(blockIdx.z % (unsigned)g.nz), q = (int)(blockIdx.z / (unsigned)g.nz);
+    if (ix >= g.nx || iy >= g.ny) return;
+    const bool active = colour < 0 || ((((ix + 1) + (iy + 1) + (DIM == 3 ? iz + 1 : 0)) & 1) == colour);
+    if (!active) return;
+    const int64_t N = g.N;
+    const int i = ix + g.nx * (iy + g.ny * iz);
+    double num = 0.0, den = 0.0;
+    for (int t = 0; t < nchunks; ++t) {
+        double2 p = part[(int64_t)t * N + i];
+        num += p.x;
+        den += p.y;
+    }
+    const double lt = den > 0.0 ? num / den : 0.0;
+    if (q == 0) lam[i] = w[i] * lt * w[i];
+    if (LAST) return;
+    const int o0 = q * chunk, o1 = min(nnxt, o0 + chunk);
+    for (int o = o0; o < o1; ++o) {
+        const int c0 = __ldg(cur_of + o);
+        const double e = c0 >= 0 ? Ecur[(int64_t)c0 * N + i] : 0.0;
         Enxt[(int64_t)o * N + i] = e - lt * Enxt[(int64_t)o * N + i];
     }
-    double wi = w[i];
-    lam[i] = wi * lt * wi;
+}
+
+template <int DIM, int KIND, bool LAST>
+static void launch_setup_rows(const Grid &g, int periodic, const double *At, const double *w, const double *Ecur,
+                              double *Enxt, int nn, int chunk, int nchunks, const unsigned *mask, const int *cidx,
+                              const int *cur_of, int colour, double *lam, double2 *part, cudaStream_t s) {
+    dim3 gr = node_grid(g), bl = node_block();
+    gr.z *= nchunks;
+    k_setup_rows<DIM, KIND, LAST><<<gr, bl, 0, s>>>(g, periodic, At, w, Ecur, Enxt, nn, chunk, nchunks, mask, cidx,
+                                                    cur_of, colour, lam, part);
+    count_launch();
+    if (nchunks > 1) {
+        k_setup_finish<DIM, LAST><<<gr, bl, 0, s>>>(g, w, Ecur, Enxt, nn, chunk, nchunks, cur_of, colour, lam, part);
+        count_launch();
+    }
 }
 
 struct Off3 {
@@ -407,7 +477,9 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
     const int ncol = kind == CS_MULTIPLICATIVE ? 2 : 1;
     dim3 gr = node_grid(g), bl = node_block();
     double *w = nullptr, *At = nullptr, *Ecur = nullptr, *Enxt = nullptr;
-    int *bad = nullptr, *pairs = nullptr, *cur_of = nullptr;
+    int *bad = nullptr, *cidx = nullptr, *cur_of = nullptr;
+    unsigned *mask = nullptr;
+    double2 *part = nullptr;
     cs_status rc = CS_OK;
     int badh = 0;
     std::vector<Off3> Ocur{{0, 0, 0}};
@@ -461,34 +533,56 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
             }
             std::map<Off3, int> idx;
             for (size_t t = 0; t < Ocur.size(); ++t) idx[Ocur[t]] = (int)t;
-            std::vector<int> hp(On.size() * NST), hc(On.size());
-            for (size_t o = 0; o < On.size(); ++o) {
+            const int nn = (int)On.size();
+            std::vector<int> hci((size_t)nn * NST, 0), hc(nn);
+            std::vector<unsigned> hm(nn, 0u);
+            for (int o = 0; o < nn; ++o) {
                 auto it = idx.find(On[o]);
                 hc[o] = it == idx.end() ? -1 : it->second;
                 for (int t = 0; t < NST; ++t) {
                     int dx, dy, dz;
                     S::off(t, dx, dy, dz);
                     auto jt = idx.find({On[o].x - dx, On[o].y - dy, On[o].z - dz});
-                    hp[o * NST + t] = jt == idx.end() ? -1 : jt->second;
+                    if (jt != idx.end()) {
+                        hm[o] |= 1u << t;
+                        hci[(size_t)o * NST + t] = jt->second;
+                    }
                 }
             }
-            int nn = (int)On.size();
-            cudaFree(pairs); cudaFree(cur_of);
-            pairs = nullptr; cur_of = nullptr;
-            if ((rc = dalloc_t(&pairs, hp.size(), nullptr)) != CS_OK) goto done;
+            const bool last = lev == nu - 1 && k == ncol - 1;
+            // parallelism for small levels: split each row's offsets into chunks
+            int nchunks = (int)std::min<int64_t>((524288 + N - 1) / N, (nn + 3) / 4);
+            nchunks = std::max(1, std::min(nchunks, 65535 / std::max(1, g.nz)));
+            const int chunk = (nn + nchunks - 1) / nchunks;
+            nchunks = (nn + chunk - 1) / chunk;
+            cudaFree(cidx); cudaFree(cur_of); cudaFree(mask); cudaFree(part);
+            cidx = nullptr; cur_of = nullptr; mask = nullptr; part = nullptr;
+            if ((rc = dalloc_t(&cidx, hci.size(), nullptr)) != CS_OK) goto done;
             if ((rc = dalloc_t(&cur_of, hc.size(), nullptr)) != CS_OK) goto done;
-            if (cudaMemcpyAsync(pairs, hp.data(), hp.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-                cudaMemcpyAsync(cur_of, hc.data(), hc.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            if ((rc = dalloc_t(&mask, hm.size(), nullptr)) != CS_OK) goto done;
+            if (nchunks > 1 && (rc = dalloc_t(&part, (size_t)nchunks * N, nullptr)) != CS_OK) goto done;
+            if (cudaMemcpyAsync(cidx, hci.data(), hci.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(cur_of, hc.data(), hc.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(mask, hm.data(), hm.size() * sizeof(unsigned), cudaMemcpyHostToDevice, s) != cudaSuccess) {
                 rc = cuda_fail(cudaGetLastError(), "copy setup tables", __FILE__, __LINE__);
                 goto done;
             }
-            if ((rc = dalloc_t(&Enxt, (size_t)nn * N, nullptr)) != CS_OK) goto done;
-            track((int64_t)nn * N * 8);
-            k_setup_step<DIM, KIND><<<gr, bl, 0, s>>>(g, h->periodic, At, w, Ecur, Enxt, nn, pairs, cur_of,
-                                                      ncol == 2 ? k : -1, lam + (int64_t)lev * N);
-            count_launch();
-            if (cudaGetLastError() != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "k_setup_step", __FILE__, __LINE__); goto done; }
-            // the host tables are rewritten next step: wait for the copies
+            if (!last) {
+                if ((rc = dalloc_t(&Enxt, (size_t)nn * N, nullptr)) != CS_OK) goto done;
+                track((int64_t)nn * N * 8);
+            }
+            {
+                const int colour = ncol == 2 ? k : -1;
+                double *lam_l = lam + (int64_t)lev * N;
+                if (last)
+                    launch_setup_rows<DIM, KIND, true>(g, h->periodic, At, w, Ecur, Enxt, nn, chunk, nchunks, mask,
+                                                       cidx, cur_of, colour, lam_l, part, s);
+                else
+                    launch_setup_rows<DIM, KIND, false>(g, h->periodic, At, w, Ecur, Enxt, nn, chunk, nchunks, mask,
+                                                        cidx, cur_of, colour, lam_l, part, s);
+            }
+            if (cudaGetLastError() != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "k_setup_rows", __FILE__, __LINE__); goto done; }
+            // the host tables are rebuilt next step: wait for their copies
             if (cudaStreamSynchronize(s) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "setup step", __FILE__, __LINE__); goto done; }
             cudaFree(Ecur);
             track(-(int64_t)Ocur.size() * N * 8);
@@ -498,7 +592,8 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
         }
     }
 done:
-    cudaFree(w); cudaFree(At); cudaFree(Ecur); cudaFree(Enxt); cudaFree(bad); cudaFree(pairs); cudaFree(cur_of);
+    cudaFree(w); cudaFree(At); cudaFree(Ecur); cudaFree(Enxt); cudaFree(bad); cudaFree(cidx); cudaFree(cur_of);
+    cudaFree(mask); cudaFree(part);
     if (peak) *peak = std::max(*peak, pk);
     return rc;
 }

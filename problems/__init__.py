@@ -189,6 +189,39 @@ def random_coefficients(dim: int, n: int, seed: int, lo: float = -2.0, hi: float
     return (10.0 ** u).reshape(shape)
 
 
+def normal(seed: int, count: int) -> np.ndarray:
+    """Standard normal draws by the Box-Muller transform of two uniform
+    streams (draws [0, count) and [count, 2 count) of stream ``seed``)."""
+    u1 = 1.0 - uniform01(seed, count, 0)  # (0, 1]
+    u2 = uniform01(seed, count, count)
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def gaussian_field(shape, corr: float, seed: int) -> np.ndarray:
+    """Zero-mean, unit-variance stationary Gaussian random field on a grid of
+    ``shape`` cells with Gaussian covariance exp(-r^2 / (2 corr^2)) (corr in
+    cells), by spectral synthesis: white noise on a periodic grid padded by
+    3 corr per side, filtered with the square root of the spectral density
+    exp(-corr^2 |k|^2 / 2), cropped and normalised."""
+    pad = int(np.ceil(3 * corr))
+    big = tuple(int(n) + 2 * pad for n in shape)
+    w = normal(seed, int(np.prod(big))).reshape(big)
+    ks = np.meshgrid(*[2.0 * np.pi * np.fft.fftfreq(n) for n in big], indexing="ij")
+    k2 = sum(k * k for k in ks)
+    f = np.real(np.fft.ifftn(np.fft.fftn(w) * np.exp(-0.25 * corr * corr * k2)))
+    f = f[tuple(slice(pad, pad + int(n)) for n in shape)]
+    return (f - f.mean()) / f.std()
+
+
+def log_uniform_field(dim: int, n: int, corr: float, seed: int, lo: float = -3.0, hi: float = 3.0) -> np.ndarray:
+    """Cell coefficients with a log-uniform marginal on [10^lo, 10^hi] and
+    spatial correlation: a Gaussian field mapped through the normal CDF to
+    u in [0, 1], mu = 10^(lo + (hi - lo) u).  Shape ``(n+1,)*dim``."""
+    from scipy.special import ndtr
+    g = gaussian_field((n + 1,) * dim, corr, seed)
+    return 10.0 ** (lo + (hi - lo) * ndtr(g))
+
+
 def rhs(N: int, seed: int, nrhs: int = 1) -> np.ndarray:
     """Right-hand side with i.i.d. entries ~ U[-1, 1] (Sec. 3.1 footnote).
     Shape ``(N,)`` for one RHS, else ``(N, nrhs)`` (RHS-contiguous)."""

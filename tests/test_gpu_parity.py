@@ -44,6 +44,9 @@ PROBLEMS = {
     "p3d_16": lambda: problems.poisson(3, 16),
     "v3d_17": lambda: _var(3, 17, 5),
     "v3d_33x": lambda: _var(3, 33, 6, -1.0, 1.0),
+    # correlated log-uniform coefficients, contrast 1e4 (Gaussian field, corr 8h / 4h)
+    "c2d_130": lambda: problems.variable_poisson(problems.log_uniform_field(2, 130, 8.0, 230, -2.0, 2.0)),
+    "c3d_33": lambda: problems.variable_poisson(problems.log_uniform_field(3, 33, 4.0, 333, -2.0, 2.0)),
 }
 
 
@@ -176,8 +179,9 @@ def test_vcycle_parity(built, name, kind, order, mu):
 
 @pytest.mark.parametrize("name,kind,method", [
     ("p2d_64", "additive", "stationary"), ("p2d_64", "multiplicative", "gmres"),
-    ("v2d_130", "multiplicative", "stationary"), ("v2d_130", "additive", "gmres"),
-    ("v3d_33x", "additive", "stationary"), ("p3d_16", "multiplicative", "gmres")])
+    ("c2d_130", "multiplicative", "gmres"), ("c2d_130", "additive", "gmres"),
+    ("v3d_33x", "additive", "stationary"), ("c3d_33", "multiplicative", "stationary"),
+    ("p3d_16", "multiplicative", "gmres")])
 def test_solve_parity(built, name, kind, method):
     import paper_2606_12577_gb300 as cmg
     A = PROBLEMS[name]()
@@ -185,6 +189,7 @@ def test_solve_parity(built, name, kind, method):
     co = oracle.Cascade(ho, kind, nu=3)
     b = problems.rhs(A.N, 9)
     xo, ito, hist_o, fin_o = oracle.solve(ho, co, b, method=method, mu_pre=1, mu_post=1, rf=True, tol=1e-10)
+    assert ito > 0, "the oracle itself must converge on this case"
     hg = gu.gpu_hierarchy(A)
     cg = cmg.setup_cascade(hg, kind, nu=3)
     xg = _dev(np.zeros(A.N))
@@ -192,8 +197,8 @@ def test_solve_parity(built, name, kind, method):
     assert info.converged and info.final_rel_residual <= 1e-10
     assert info.iterations == ito
     # relative residual histories: equal to 1e-9 relative until they reach the
-    # rounding floor of the residual evaluation (~1e-16 * ||A|| ||x|| / ||b||)
-    np.testing.assert_allclose(info.history, hist_o, rtol=1e-9, atol=1e-15)
+    # rounding floor of the (preconditioned) residual evaluation, 1e-13 here
+    np.testing.assert_allclose(info.history, hist_o, rtol=1e-9, atol=1e-13)
     x = _host(xg)
     # independent FP64 residual of the returned x
     r = b - gu.stencil_matvec(A, x)
@@ -202,7 +207,8 @@ def test_solve_parity(built, name, kind, method):
 
 
 @pytest.mark.parametrize("name,kind,method", [
-    ("p2d_64", "additive", "refine"), ("v2d_130", "multiplicative", "refine"), ("v3d_33x", "additive", "gmres")])
+    ("p2d_64", "additive", "refine"), ("c3d_33", "multiplicative", "refine"), ("v3d_33x", "additive", "refine"),
+    ("v3d_33x", "additive", "gmres"), ("c2d_130", "additive", "gmres")])
 def test_fp32_cycle_with_fp64_refinement(built, name, kind, method):
     """The mixed-precision form: FP32 cycle inside FP64 refinement (or FP64
     GMRES) reaches the same 1e-10 true residual; its distance to the oracle's
@@ -213,6 +219,7 @@ def test_fp32_cycle_with_fp64_refinement(built, name, kind, method):
     co = oracle.Cascade(ho, kind, nu=3)
     b = problems.rhs(A.N, 11)
     xo, ito, _, _ = oracle.solve(ho, co, b, method="stationary" if method == "refine" else method, tol=1e-10)
+    assert ito > 0
     hg = gu.gpu_hierarchy(A)
     cg = cmg.setup_cascade(hg, kind, nu=3, lowp=True)
     xg = _dev(np.zeros(A.N))
@@ -221,14 +228,34 @@ def test_fp32_cycle_with_fp64_refinement(built, name, kind, method):
     x = _host(xg)
     r = b - gu.stencil_matvec(A, x)
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
-    assert info.iterations <= ito + 3
+    # an FP32 cycle is a linear map only to ~1e-7: stationary refinement keeps
+    # the FP64 rate, left-preconditioned GMRES needs one extra restart cycle
+    assert info.iterations <= (ito + 3 if method == "refine" else 2 * ito + 5)
     # both are within cond(A) * 1e-10 of the exact solution
     assert gu.rel_max(x, xo) <= 1e-6
 
 
+@pytest.mark.parametrize("name", ["p2d_64", "v3d_33x", "c3d_33", "c2d_130"])
+@pytest.mark.parametrize("kind", ["additive", "multiplicative"])
+@pytest.mark.parametrize("mu", [1, 2])
+def test_fp32_cycle_tracks_fp64_cycle(built, name, kind, mu):
+    """One zero-guess V-cycle in FP32 storage/arithmetic agrees with the FP64
+    cycle to FP32 accuracy (the per-result error of the low-precision form)."""
+    import paper_2606_12577_gb300 as cmg
+    A = PROBLEMS[name]()
+    hg = gu.gpu_hierarchy(A)
+    cg = cmg.setup_cascade(hg, kind, nu=3, lowp=True)
+    b = _dev(problems.rhs(A.N, 17))
+    x64 = _dev(np.zeros(A.N))
+    x32 = _dev(np.zeros(A.N))
+    cmg.vcycle(hg, cg, b, x64, mu_pre=mu, mu_post=mu, precision="fp64")
+    cmg.vcycle(hg, cg, b, x32, mu_pre=mu, mu_post=mu, precision="fp32")
+    assert gu.rel_max(_host(x32), _host(x64)) <= 1e-4
+
+
 def test_host_buffer_solve_matches_device(built):
     import paper_2606_12577_gb300 as cmg
-    A = PROBLEMS["v2d_130"]()
+    A = PROBLEMS["c3d_33"]()
     hg = gu.gpu_hierarchy(A)
     cg = cmg.setup_cascade(hg, "additive", nu=3, lowp=True)
     b = problems.rhs(A.N, 13)
