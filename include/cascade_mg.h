@@ -169,6 +169,42 @@ cs_status cs_coarse_solve(const cs_hierarchy *h, const double *b, double *x, cs_
 cs_status cs_residual(const cs_hierarchy *h, int level, const double *b, const double *x, double *r,
                       double *norm2, cs_stream stream);
 
+/* Allocation-free variant of cs_smooth (the paper has no counterpart: this is
+ * an interface convenience, not a step of the method).
+ *
+ * For callers that cannot allocate device memory: code that runs inside a
+ * host application or framework whose allocator already owns the whole GPU,
+ * callers that must not risk the implicit device synchronisation a
+ * cudaMalloc/cudaFree can cause, or callers that never create the handles of
+ * cs_setup_hierarchy / cs_setup_cascade (which allocate).  The caller passes
+ * the operator and Lambda directly; the ping-pong vector that cs_smooth takes
+ * from its hierarchy comes from a fixed 16 MiB device array inside the
+ * library (2,097,152 doubles), which every GPU that loads the library keeps
+ * until the process exits.  Nothing is allocated and no allocating library
+ * routine is called.
+ *
+ * Computes the same thing as cs_smooth: one application of the depth-nu
+ * cascade (forward, or reverse when reverse != 0), x updated in place.
+ *   dim, n:  grid (n[2] ignored in 2D); N = n[0]*n[1]*n[2] must be
+ *            <= 2,097,152, else CS_ERR_ARG.
+ *   box:     0: coeff holds a 5/7-point stencil in the order C,-x,+x,-y,+y[,-z,+z];
+ *            1: a 9/27-point stencil, entry s at offset ((s%3)-1, (s/3%3)-1, (s/9)-1)
+ *            (the layouts cs_query_level / cs_export_operator report);
+ *            coefficients to nodes outside the grid must be zero.
+ *   coeff:   device [nst][N];  lam: device [nu][N] (point-block Lambda_l, the
+ *            multiplicative Lambda_{l,k} on the nodes of colour k, as
+ *            cs_export_lambda returns);  b, x: device [N].
+ *   kind:    CS_ADDITIVE or CS_MULTIPLICATIVE (red-black).
+ * The first call on a device looks up the device address of the internal
+ * array (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the one array and leave
+ * their last intermediate vector in it; every step overwrites all N entries
+ * it later reads, so nothing needs clearing between calls.  Calls that
+ * overlap on the GPU (other streams, other host threads) race on the array:
+ * order them on one stream. */
+cs_status cs_smooth_noalloc(int dim, const int *n, int box, const double *coeff, const double *lam, int nu,
+                            int kind, int reverse, const double *b, double *x, cs_stream stream);
+
 /* ---------------------------------------------------------------- solve */
 enum { CS_STATIONARY = 0, CS_GMRES = 1, CS_REFINE = 2 };
 

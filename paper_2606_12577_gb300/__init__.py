@@ -20,7 +20,7 @@ from ._capi import CascadeError
 
 __all__ = ["setup_hierarchy", "setup_cascade", "vcycle", "solve", "smooth", "sweep", "residual_restrict",
            "prolong_correct", "coarse_solve", "residual", "query_level", "export_operator", "export_colours",
-           "export_lambda", "kernel_launches", "Hierarchy", "Cascade", "SolveInfo", "CascadeError"]
+           "export_lambda", "kernel_launches", "smooth_noalloc", "Hierarchy", "Cascade", "SolveInfo", "CascadeError"]
 
 
 def _torch():
@@ -193,6 +193,25 @@ def sweep(h, c, level, step, b, x, out, colour=-1, stream=None):
     _capi.check(_capi.lib().cs_sweep(h.ptr, c.ptr, level, step, colour, prec, C.c_void_p(b.data_ptr()),
                                      C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), _stream(stream)),
                 "cs_sweep")
+
+
+NOALLOC_MAX_N = 1 << 21
+
+
+def smooth_noalloc(dim, n, box, coeff, lam, nu, b, x, kind="additive", reverse=False, stream=None):
+    """cs_smooth_noalloc: one cascade application on a caller-given operator
+    (canonical stencil layout) and Lambda ([nu, N]) without any device
+    allocation; the ping-pong vector comes from a fixed internal 16 MiB
+    device array (N <= 2,097,152).  For callers that cannot allocate."""
+    nn = list(n) + [1] * (3 - len(n))
+    N = int(nn[0] * nn[1] * (nn[2] if dim == 3 else 1))
+    nst = (27 if dim == 3 else 9) if box else 2 * dim + 1
+    narr = (C.c_int * 3)(*[int(v) for v in nn])
+    k = _capi.CS_MULTIPLICATIVE if kind == "multiplicative" else _capi.CS_ADDITIVE
+    _capi.check(_capi.lib().cs_smooth_noalloc(dim, narr, int(bool(box)), _dev_ptr(coeff, nst * N, "coeff"),
+                                              _dev_ptr(lam, nu * N, "lam"), nu, k, int(bool(reverse)),
+                                              _dev_ptr(b, N, "b"), _dev_ptr(x, N, "x"), _stream(stream)),
+                "cs_smooth_noalloc")
 
 
 def kernel_launches() -> int:
