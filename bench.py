@@ -290,6 +290,15 @@ def main():
         torch.cuda.synchronize()
         result["setup_ms"] = ev[0].elapsed_time(ev[1])
         result["solve_ms"] = ev[1].elapsed_time(ev[2])
+        # the same setup computing every row (no repeated-row reuse): the cost
+        # on operators without a constant-coefficient interior
+        ev[0].record(s)
+        h0 = cmg.setup_hierarchy(A.dim, A.n, A.offsets, coeff, reuse=False)
+        c0 = cmg.setup_cascade(h0, a.kind, nu=a.nu, lowp=True, reuse=False)
+        ev[1].record(s)
+        torch.cuda.synchronize()
+        result["setup_every_row_ms"] = ev[0].elapsed_time(ev[1])
+        del c0, h0
         # ---- roofline of the sweep kernel (FP32 additive step, finest level)
         N = A.N
         lvl = cmg.query_level(h, 0)

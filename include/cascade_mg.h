@@ -75,6 +75,9 @@ typedef struct {
     int coarse_max; /* stop coarsening when every side is <= coarse_max (default 4) */
     int max_levels; /* 0 = no limit */
     int block;      /* block edge in nodes (1 = point blocks; >1 unsupported for now) */
+    int no_reuse;   /* 0 (default): coarse rows whose fine neighbourhood repeats the
+                       grid-centre row's are computed once and copied (exact: bitwise the
+                       same as computing each); 1: compute every row */
 } cs_hierarchy_opts;
 
 /* Geometric hierarchy (Sec. 2.4): coarse interior nodes are the fine nodes
@@ -101,6 +104,11 @@ typedef struct {
     int alpha;     /* residual truncation (Algorithm 2); 0 = none (only 0 supported) */
     int lowp;      /* 1: also keep FP32 copies of the level operators and Lambda for
                       CS_FP32 cycles (iterative refinement) */
+    int no_reuse;  /* 0 (default): on structured levels with a region of identical
+                      coefficient rows, rows whose whole setup dependency lies in that
+                      region are computed once per colour and copied -- the stencil
+                      repetition the paper's concluding remarks suggest caching; exact
+                      (bitwise the same as computing each row); 1: compute every row */
 } cs_cascade_opts;
 
 /* Build the cascade (Lambda_l, l = 1..nu; multiplicative: Lambda_{l,k},

@@ -117,7 +117,8 @@ class SolveInfo:
     history: np.ndarray
 
 
-def setup_hierarchy(dim, n, offsets, coeff, periodic=False, coarse_max=4, max_levels=0, block=1, stream=None):
+def setup_hierarchy(dim, n, offsets, coeff, periodic=False, coarse_max=4, max_levels=0, block=1, reuse=True,
+                    stream=None):
     """Build the hierarchy of the structured operator given by ``offsets``
     (list of (dx,dy,dz)) and ``coeff`` ([nst, N] float64: a CUDA tensor, or a
     host numpy array copied during the call)."""
@@ -139,7 +140,7 @@ def setup_hierarchy(dim, n, offsets, coeff, periodic=False, coarse_max=4, max_le
         st.coeff = _dev_ptr(coeff, name="coeff").value
         st.coeff_on_host = 0
     st.periodic = int(bool(periodic))
-    opts = _capi.cs_hierarchy_opts(coarse_max, max_levels, block)
+    opts = _capi.cs_hierarchy_opts(coarse_max, max_levels, block, int(not reuse))
     out = C.c_void_p()
     _capi.check(_capi.lib().cs_setup_hierarchy(C.byref(st), C.byref(opts), _stream(stream), C.byref(out)),
                 "cs_setup_hierarchy")
@@ -147,9 +148,9 @@ def setup_hierarchy(dim, n, offsets, coeff, periodic=False, coarse_max=4, max_le
     return Hierarchy(out.value, dim)
 
 
-def setup_cascade(h: Hierarchy, kind="additive", nu=3, prescale=True, alpha=0, lowp=False, stream=None):
+def setup_cascade(h: Hierarchy, kind="additive", nu=3, prescale=True, alpha=0, lowp=False, reuse=True, stream=None):
     k = _capi.CS_MULTIPLICATIVE if kind == "multiplicative" else _capi.CS_ADDITIVE
-    opts = _capi.cs_cascade_opts(k, nu, int(prescale), alpha, int(lowp))
+    opts = _capi.cs_cascade_opts(k, nu, int(prescale), alpha, int(lowp), int(not reuse))
     out = C.c_void_p()
     _capi.check(_capi.lib().cs_setup_cascade(h.ptr, C.byref(opts), _stream(stream), C.byref(out)),
                 "cs_setup_cascade")

@@ -29,11 +29,12 @@ class cs_stencil(C.Structure):
 
 
 class cs_hierarchy_opts(C.Structure):
-    _fields_ = [("coarse_max", C.c_int), ("max_levels", C.c_int), ("block", C.c_int)]
+    _fields_ = [("coarse_max", C.c_int), ("max_levels", C.c_int), ("block", C.c_int), ("no_reuse", C.c_int)]
 
 
 class cs_cascade_opts(C.Structure):
-    _fields_ = [("kind", C.c_int), ("nu", C.c_int), ("prescale", C.c_int), ("alpha", C.c_int), ("lowp", C.c_int)]
+    _fields_ = [("kind", C.c_int), ("nu", C.c_int), ("prescale", C.c_int), ("alpha", C.c_int), ("lowp", C.c_int),
+                ("no_reuse", C.c_int)]
 
 
 class cs_vcycle_opts(C.Structure):

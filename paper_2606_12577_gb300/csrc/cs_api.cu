@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "cs_internal.cuh"
@@ -31,9 +32,34 @@ cs_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
     return e == cudaErrorMemoryAllocation ? CS_ERR_NOMEM : CS_ERR_CUDA;
 }
 
-cs_status dalloc(void **p, size_t bytes, int64_t *acct) {
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {nullptr};
+
+static cs_status pool_for_current_device(cudaMemPool_t *out) {
+    int dev = 0;
+    CSX_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { set_error("device ordinal %d unsupported", dev); return CS_ERR_UNSUPPORTED; }
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        CSX_CUDA(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = ~(uint64_t)0;  // retain freed memory for the next setup
+        CSX_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return CS_OK;
+}
+
+cs_status dalloc(void **p, size_t bytes, int64_t *acct, cudaStream_t s) {
     *p = nullptr;
-    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    cudaMemPool_t pool = nullptr;
+    CSX_TRY(pool_for_current_device(&pool));
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
@@ -42,6 +68,10 @@ cs_status dalloc(void **p, size_t bytes, int64_t *acct) {
     }
     if (acct) *acct += (int64_t)bytes;
     return CS_OK;
+}
+
+void dfree(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
 }
 
 static bool is_star_offset(int dim, const int *o) {
@@ -263,7 +293,7 @@ cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts
     if (!A0 || !out) { set_error("null argument"); return CS_ERR_ARG; }
     *out = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
-    cs_hierarchy_opts opts{4, 0, 1};
+    cs_hierarchy_opts opts{4, 0, 1, 0};
     if (opts_in) opts = *opts_in;
     if (opts.coarse_max <= 0) opts.coarse_max = 4;
     if (opts.block == 0) opts.block = 1;
@@ -303,7 +333,7 @@ cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts
         L0.kind = star ? STAR : BOX;
         L0.nst = star ? 2 * dim + 1 : (dim == 3 ? 27 : 9);
         fill_offsets(L0);
-        if ((rc = dalloc_t(&L0.A, (size_t)L0.nst * L0.g.N, &h->bytes)) != CS_OK) goto fail_nolevel;
+        if ((rc = dalloc_t(&L0.A, (size_t)L0.nst * L0.g.N, &h->bytes, s)) != CS_OK) goto fail_nolevel;
         h->lev.push_back(L0);
         Level &L = h->lev[0];
         cudaError_t e = cudaMemsetAsync(L.A, 0, sizeof(double) * L.nst * L.g.N, s);
@@ -314,6 +344,7 @@ cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts
         }
         if (A0->coeff_on_host && e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { rc = cuda_fail(e, "copy operator", __FILE__, __LINE__); goto fail; }
+        if (!opts.no_reuse && (rc = level_margin(L, h->periodic, s)) != CS_OK) goto fail;
     }
     while (!h->periodic && (opts.max_levels <= 0 || (int)h->lev.size() < opts.max_levels)) {
         const Level &F = h->lev.back();
@@ -325,23 +356,24 @@ cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts
         C.kind = BOX;
         C.nst = dim == 3 ? 27 : 9;
         fill_offsets(C);
-        if ((rc = dalloc_t(&C.A, (size_t)C.nst * C.g.N, &h->bytes)) != CS_OK) goto fail;
+        if ((rc = dalloc_t(&C.A, (size_t)C.nst * C.g.N, &h->bytes, s)) != CS_OK) goto fail;
         h->lev.push_back(C);
-        if ((rc = galerkin_level(h->lev[h->lev.size() - 2], h->lev.back(), s)) != CS_OK) goto fail;
+        if ((rc = galerkin_level(h->lev[h->lev.size() - 2], h->lev.back(), !opts.no_reuse, s)) != CS_OK) goto fail;
+        if (!opts.no_reuse && (rc = level_margin(h->lev.back(), false, s)) != CS_OK) goto fail;
     }
     h->nlev = (int)h->lev.size();
     for (auto &L : h->lev) {
-        if ((rc = dalloc_t(&L.b, L.g.N, &h->bytes)) != CS_OK) goto fail;
-        if ((rc = dalloc_t(&L.x, L.g.N, &h->bytes)) != CS_OK) goto fail;
-        if ((rc = dalloc_t(&L.t, L.g.N, &h->bytes)) != CS_OK) goto fail;
+        if ((rc = dalloc_t(&L.b, L.g.N, &h->bytes, s)) != CS_OK) goto fail;
+        if ((rc = dalloc_t(&L.x, L.g.N, &h->bytes, s)) != CS_OK) goto fail;
+        if ((rc = dalloc_t(&L.t, L.g.N, &h->bytes, s)) != CS_OK) goto fail;
     }
     {
         int nred = std::max(residual_blocks(h->lev[0]), NRED);
-        if ((rc = dalloc_t(&h->red, (size_t)nred + 8, &h->bytes)) != CS_OK) goto fail;
+        if ((rc = dalloc_t(&h->red, (size_t)nred + 8, &h->bytes, s)) != CS_OK) goto fail;
         cudaError_t e = cudaMallocHost(&h->red_host, 64 * sizeof(double));
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMallocHost", __FILE__, __LINE__); goto fail; }
-        if ((rc = dalloc_t(&h->hb, h->lev[0].g.N, &h->bytes)) != CS_OK) goto fail;
-        if ((rc = dalloc_t(&h->hx, h->lev[0].g.N, &h->bytes)) != CS_OK) goto fail;
+        if ((rc = dalloc_t(&h->hb, h->lev[0].g.N, &h->bytes, s)) != CS_OK) goto fail;
+        if ((rc = dalloc_t(&h->hx, h->lev[0].g.N, &h->bytes, s)) != CS_OK) goto fail;
     }
     if (!h->periodic && h->lev.back().g.N <= 4096) {
         if ((rc = coarse_factor(h, s)) != CS_OK) goto fail;
@@ -360,8 +392,8 @@ fail_nolevel:
 
 void cs_destroy_hierarchy(cs_hierarchy *h) {
     if (!h) return;
-    for (auto &L : h->lev) { cudaFree(L.A); cudaFree(L.b); cudaFree(L.x); cudaFree(L.t); }
-    cudaFree(h->cinv); cudaFree(h->red); cudaFree(h->hb); cudaFree(h->hx); cudaFree(h->fine_r);
+    for (auto &L : h->lev) { dfree(L.A); dfree(L.b); dfree(L.x); dfree(L.t); }
+    dfree(h->cinv); dfree(h->red); dfree(h->hb); dfree(h->hx); dfree(h->fine_r);
     if (h->red_host) cudaFreeHost(h->red_host);
     delete h;
 }
@@ -388,8 +420,9 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
     c->lam.assign(c->nlev, nullptr);
     for (int l = 0; l < c->nlev; ++l) {
         const int64_t N = h->lev[l].g.N;
-        if ((rc = dalloc_t(&c->lam[l], (size_t)c->nu * N, &c->bytes)) != CS_OK) goto fail;
-        if ((rc = cascade_setup_level(h, l, c->kind, c->nu, o->prescale, c->lam[l], s, &peak)) != CS_OK) goto fail;
+        if ((rc = dalloc_t(&c->lam[l], (size_t)c->nu * N, &c->bytes, s)) != CS_OK) goto fail;
+        if ((rc = cascade_setup_level(h, l, c->kind, c->nu, o->prescale, !o->no_reuse, c->lam[l], s, &peak)) != CS_OK)
+            goto fail;
     }
     if (c->lowp) {
         c->lo.resize(h->nlev);
@@ -397,15 +430,15 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
             const Level &L = h->lev[l];
             LowLevel &lo = c->lo[l];
             const int64_t N = L.g.N;
-            if ((rc = dalloc_t(&lo.A, (size_t)L.nst * N, &c->bytes)) != CS_OK) goto fail;
+            if ((rc = dalloc_t(&lo.A, (size_t)L.nst * N, &c->bytes, s)) != CS_OK) goto fail;
             if ((rc = launch_copy_d2f((int64_t)L.nst * N, L.A, lo.A, s)) != CS_OK) goto fail;
             if (l < c->nlev) {
-                if ((rc = dalloc_t(&lo.lam, (size_t)c->nu * N, &c->bytes)) != CS_OK) goto fail;
+                if ((rc = dalloc_t(&lo.lam, (size_t)c->nu * N, &c->bytes, s)) != CS_OK) goto fail;
                 if ((rc = launch_copy_d2f((int64_t)c->nu * N, c->lam[l], lo.lam, s)) != CS_OK) goto fail;
             }
-            if ((rc = dalloc_t(&lo.b, N, &c->bytes)) != CS_OK) goto fail;
-            if ((rc = dalloc_t(&lo.x, N, &c->bytes)) != CS_OK) goto fail;
-            if ((rc = dalloc_t(&lo.t, N, &c->bytes)) != CS_OK) goto fail;
+            if ((rc = dalloc_t(&lo.b, N, &c->bytes, s)) != CS_OK) goto fail;
+            if ((rc = dalloc_t(&lo.x, N, &c->bytes, s)) != CS_OK) goto fail;
+            if ((rc = dalloc_t(&lo.t, N, &c->bytes, s)) != CS_OK) goto fail;
         }
     }
     {
@@ -423,9 +456,9 @@ fail:
 void cs_destroy_cascade(cs_cascade *c) {
     if (!c) return;
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
-    for (double *p : c->lam) cudaFree(p);
-    for (auto &lo : c->lo) { cudaFree(lo.A); cudaFree(lo.lam); cudaFree(lo.b); cudaFree(lo.x); cudaFree(lo.t); }
-    cudaFree(c->fine_b32); cudaFree(c->fine_x32); cudaFree(c->gm_V); cudaFree(c->gm_h);
+    for (double *p : c->lam) dfree(p);
+    for (auto &lo : c->lo) { dfree(lo.A); dfree(lo.lam); dfree(lo.b); dfree(lo.x); dfree(lo.t); }
+    dfree(c->fine_b32); dfree(c->fine_x32); dfree(c->gm_V); dfree(c->gm_h);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     delete c;
 }
@@ -625,10 +658,10 @@ static cs_status gmres(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts
     const int m = o->restart;
     const bool lowp = o->cycle.precision == CS_FP32;
     if (c->gm_restart < m) {
-        cudaFree(c->gm_V); cudaFree(c->gm_h);
+        dfree(c->gm_V, s); dfree(c->gm_h, s);
         c->gm_V = nullptr; c->gm_h = nullptr;
-        CSX_TRY(dalloc_t(&c->gm_V, (size_t)(m + 1) * N, &c->bytes));
-        CSX_TRY(dalloc_t(&c->gm_h, (size_t)(m + 2) * 2, &c->bytes));
+        CSX_TRY(dalloc_t(&c->gm_V, (size_t)(m + 1) * N, &c->bytes, s));
+        CSX_TRY(dalloc_t(&c->gm_h, (size_t)(m + 2) * 2, &c->bytes, s));
         c->gm_restart = m;
     }
     double *V = c->gm_V, *hd = c->gm_h;

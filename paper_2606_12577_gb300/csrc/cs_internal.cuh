@@ -36,6 +36,10 @@ struct Level {
     double *A = nullptr;  // [nst][N]
     // work vectors (FP64): b (rhs), x (iterate), t (ping-pong)
     double *b = nullptr, *x = nullptr, *t = nullptr;
+    // every row at boundary distance >= margin has a coefficient row equal
+    // (bitwise) to the grid-centre row; NO_MARGIN: no such region is used
+    int margin = NO_MARGIN;
+    static constexpr int NO_MARGIN = 1 << 30;
 };
 
 struct LowLevel {   // FP32 state of one level (owned by a cascade)
@@ -104,10 +108,14 @@ cs_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
 extern std::atomic<int64_t> g_launches;
 inline void count_launch(int64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-cs_status dalloc(void **p, size_t bytes, int64_t *acct);
+// Device memory comes from a library-owned stream-ordered pool per device
+// (cudaMallocFromPoolAsync / cudaFreeAsync) that keeps freed memory mapped,
+// so repeated setups of multi-GB residual buffers cost no driver calls.
+cs_status dalloc(void **p, size_t bytes, int64_t *acct, cudaStream_t s = 0);
+void dfree(void *p, cudaStream_t s = 0);
 template <typename T>
-cs_status dalloc_t(T **p, size_t count, int64_t *acct) {
-    return dalloc(reinterpret_cast<void **>(p), count * sizeof(T), acct);
+cs_status dalloc_t(T **p, size_t count, int64_t *acct, cudaStream_t s = 0) {
+    return dalloc(reinterpret_cast<void **>(p), count * sizeof(T), acct, s);
 }
 
 inline Grid make_grid(int dim, int nx, int ny, int nz) {
@@ -156,9 +164,10 @@ cs_status launch_axpy_multi(int64_t N, int m, const double *alpha, const double 
 constexpr int NRED = 1024;  // partial sums of a reduction
 
 // ---- setup kernels (cs_setup.cu)
-cs_status galerkin_level(const Level &f, Level &c, cudaStream_t s);
+cs_status galerkin_level(const Level &f, Level &c, bool reuse, cudaStream_t s);
+cs_status level_margin(Level &L, bool periodic, cudaStream_t s);
 cs_status coarse_factor(cs_hierarchy *h, cudaStream_t s);
-cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, double *lam,
+cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, double *lam,
                               cudaStream_t s, int64_t *peak_bytes);
 
 }  // namespace csx

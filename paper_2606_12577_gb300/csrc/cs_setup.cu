@@ -47,6 +47,131 @@ struct StenS {
     }
 };
 
+// ------------------------------------------------- repeated-row detection
+// Sec. 4 (concluding remarks) notes that on structured meshes with uniform
+// coefficients the smoother construction is the same almost everywhere and
+// can be cached.  We use that exactly: if every row at boundary distance
+// >= m has the same coefficient row as the grid-centre row, then any
+// quantity that depends only on rows within radius r of row i is identical
+// for all rows at distance >= m + r (for the multiplicative form: identical
+// among rows of one colour).  Such "deep" rows are computed once, in a
+// representative row, and copied; the result is bitwise the same as
+// computing every row.
+__device__ __forceinline__ int bdist(const Grid &g, int ix, int iy, int iz) {
+    int d = min(min(ix, g.nx - 1 - ix), min(iy, g.ny - 1 - iy));
+    if (g.dim == 3) d = min(d, min(iz, g.nz - 1 - iz));
+    return d;
+}
+__device__ __forceinline__ int rb_colour(const Grid &g, int ix, int iy, int iz) {
+    return ((ix + 1) + (iy + 1) + (g.dim == 3 ? iz + 1 : 0)) & 1;
+}
+static int bdist_host(const Grid &g, int ix, int iy, int iz) {
+    int d = std::min(std::min(ix, g.nx - 1 - ix), std::min(iy, g.ny - 1 - iy));
+    if (g.dim == 3) d = std::min(d, std::min(iz, g.nz - 1 - iz));
+    return d;
+}
+
+// The rows a reuse-enabled kernel computes: the grid minus an inner box of
+// deep rows (lo..hi inclusive per axis), enumerated densely so that warps
+// hold only rows with work, followed by nrep representative rows.
+struct RowSet {
+    int on;
+    int lo[3], hi[3];
+    int64_t nshell;
+    int nrep;
+    int rep[2][3];
+};
+
+static int64_t rowset_shell_count(const Grid &g, const int *lo, const int *hi) {
+    const int64_t nxi = hi[0] - lo[0] + 1, nyi = hi[1] - lo[1] + 1;
+    const int64_t nzi = g.dim == 3 ? hi[2] - lo[2] + 1 : 1;
+    return g.N - nxi * nyi * nzi;
+}
+
+// coordinates of the t-th row of the set; false past its end
+__device__ __forceinline__ bool rowset_coord(const RowSet &rs, const Grid &g, int64_t t, int &ix, int &iy, int &iz) {
+    if (t >= rs.nshell) {
+        const int r = (int)(t - rs.nshell);
+        if (r >= rs.nrep) return false;
+        ix = rs.rep[r][0]; iy = rs.rep[r][1]; iz = rs.rep[r][2];
+        return true;
+    }
+    const int nxi = rs.hi[0] - rs.lo[0] + 1, nyi = rs.hi[1] - rs.lo[1] + 1;
+    const int nxo = g.nx - nxi, nyo = g.ny - nyi;
+    int zlo = 0, nzi = 1;
+    if (g.dim == 3) {  // whole outer z-planes first
+        nzi = rs.hi[2] - rs.lo[2] + 1;
+        zlo = rs.lo[2];
+        const int64_t plane = (int64_t)g.nx * g.ny;
+        const int64_t pz = (int64_t)(g.nz - nzi) * plane;
+        if (t < pz) {
+            const int k = (int)(t / plane);
+            const int64_t rem = t - (int64_t)k * plane;
+            iz = k < rs.lo[2] ? k : k + nzi;
+            iy = (int)(rem / g.nx);
+            ix = (int)(rem - (int64_t)iy * g.nx);
+            return true;
+        }
+        t -= pz;
+    }
+    const int64_t pery = (int64_t)nyo * g.nx;  // outer y-rows of the inner z-range
+    const int64_t py = (int64_t)nzi * pery;
+    if (t < py) {
+        const int zz = (int)(t / pery);
+        const int64_t rem = t - (int64_t)zz * pery;
+        const int k = (int)(rem / g.nx);
+        iz = zlo + zz;
+        iy = k < rs.lo[1] ? k : k + nyi;
+        ix = (int)(rem - (int64_t)k * g.nx);
+        return true;
+    }
+    t -= py;  // outer x-columns of the inner y- and z-range
+    const int64_t perz = (int64_t)nyi * nxo;
+    const int zz = (int)(t / perz);
+    const int64_t rem = t - (int64_t)zz * perz;
+    const int yy = (int)(rem / nxo);
+    const int k = (int)(rem - (int64_t)yy * nxo);
+    iz = zlo + zz;
+    iy = rs.lo[1] + yy;
+    ix = k < rs.lo[0] ? k : k + nxi;
+    return true;
+}
+
+// maxd = max boundary distance of the rows whose coefficients differ from
+// row `ref` (bitwise); -1 if none
+__global__ void k_const_margin(Grid g, int nst, const double *__restrict__ A, int64_t ref, int *maxd) {
+    const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
+    if (ix >= g.nx || iy >= g.ny) return;
+    const int64_t i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
+    bool eq = true;
+    for (int s = 0; s < nst; ++s)
+        eq = eq && __double_as_longlong(A[(int64_t)s * g.N + i]) == __double_as_longlong(A[(int64_t)s * g.N + ref]);
+    if (!eq) atomicMax(maxd, bdist(g, ix, iy, iz));
+}
+
+cs_status level_margin(Level &L, bool periodic, cudaStream_t s) {
+    const Grid &g = L.g;
+    const int64_t ref = g.nx / 2 + (int64_t)g.nx * (g.ny / 2 + (int64_t)g.ny * (g.nz / 2));
+    int *d = nullptr;
+    CSX_TRY(dalloc_t(&d, 1, nullptr, s));
+    int init = -1, maxd = 0;
+    cudaError_t e = cudaMemcpyAsync(d, &init, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        k_const_margin<<<node_grid(g), node_block(), 0, s>>>(g, L.nst, L.A, ref, d);
+        count_launch();
+        e = cudaMemcpyAsync(&maxd, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dfree(d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "level margin", __FILE__, __LINE__);
+    if (periodic) L.margin = maxd < 0 ? 0 : Level::NO_MARGIN;
+    else {
+        L.margin = maxd + 1;
+        if (bdist_host(g, g.nx / 2, g.ny / 2, g.nz / 2) < L.margin) L.margin = Level::NO_MARGIN;
+    }
+    return CS_OK;
+}
+
 // ------------------------------------------------------------ Galerkin RAP
 // 1D interpolation weight between fine node 2J+1+u and coarse node J:
 // 1 at u = 0, 1/2 at u = +-1, else 0.
@@ -62,7 +187,7 @@ __host__ __device__ constexpr double pw(int u) { return u == 0 ? 1.0 : ((u == 1 
 // are skipped; entries whose coarse neighbour lies outside are set to zero.
 template <int DIM, int KIND>
 __global__ void __launch_bounds__(TBX *TBY) k_galerkin(Grid gf, Grid gc, const double *__restrict__ Af,
-                                                        double *__restrict__ Ac) {
+                                                        double *__restrict__ Ac, RowSet rs) {
     using S = StenS<DIM, KIND>;
     constexpr int NC = DIM == 3 ? 27 : 9;
     extern __shared__ double acc_sm[];  // [NC][TBX*TBY]
@@ -70,8 +195,14 @@ __global__ void __launch_bounds__(TBX *TBY) k_galerkin(Grid gf, Grid gc, const d
     double *acc = acc_sm + tid;
 #pragma unroll
     for (int t = 0; t < NC; ++t) acc[t * TBX * TBY] = 0.0;
-    const int cx = blockIdx.x * TBX + threadIdx.x, cy = blockIdx.y * TBY + threadIdx.y, cz = blockIdx.z;
-    if (cx >= gc.nx || cy >= gc.ny) return;
+    int cx, cy, cz;
+    if (rs.on) {  // only coarse rows outside the deep box (plus the representative)
+        if (!rowset_coord(rs, gc, (int64_t)blockIdx.x * (TBX * TBY) + tid, cx, cy, cz)) return;
+    } else {
+        cx = blockIdx.x * TBX + threadIdx.x; cy = blockIdx.y * TBY + threadIdx.y; cz = blockIdx.z;
+        if (cx >= gc.nx || cy >= gc.ny) return;
+    }
+    const int64_t ci = cx + (int64_t)gc.nx * (cy + (int64_t)gc.ny * cz);
     for (int e = 0; e < NC; ++e) {
         const int ex = e % 3 - 1, ey = (e / 3) % 3 - 1, ez = DIM == 3 ? e / 9 - 1 : 0;
         const int fx = 2 * cx + 1 + ex, fy = 2 * cy + 1 + ey, fz = DIM == 3 ? 2 * cz + 1 + ez : 0;
@@ -98,7 +229,6 @@ __global__ void __launch_bounds__(TBX *TBY) k_galerkin(Grid gf, Grid gc, const d
                     }
         }
     }
-    const int64_t ci = cx + (int64_t)gc.nx * (cy + (int64_t)gc.ny * cz);
     const double sc = DIM == 3 ? 0.125 : 0.25;
 #pragma unroll
     for (int t = 0; t < NC; ++t) {
@@ -108,12 +238,51 @@ __global__ void __launch_bounds__(TBX *TBY) k_galerkin(Grid gf, Grid gc, const d
     }
 }
 
-cs_status galerkin_level(const Level &f, Level &c, cudaStream_t s) {
+// rows inside the deep box take the representative row's values
+__global__ void k_copy_deep(Grid g, int nv, double *__restrict__ V, RowSet rs, int colour) {
+    const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
+    if (ix >= g.nx || iy >= g.ny) return;
+    if (ix < rs.lo[0] || ix > rs.hi[0] || iy < rs.lo[1] || iy > rs.hi[1]) return;
+    if (g.dim == 3 && (iz < rs.lo[2] || iz > rs.hi[2])) return;
+    const int c = rb_colour(g, ix, iy, iz);
+    if (colour >= 0 && c != colour) return;
+    const int r = rs.nrep == 2 ? c : 0;  // representative of this row's colour
+    const int64_t ri = rs.rep[r][0] + (int64_t)g.nx * (rs.rep[r][1] + (int64_t)g.ny * rs.rep[r][2]);
+    const int64_t i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
+    if (i == ri) return;
+    for (int t = 0; t < nv; ++t) V[(int64_t)t * g.N + i] = V[(int64_t)t * g.N + ri];
+}
+
+cs_status galerkin_level(const Level &f, Level &c, bool reuse, cudaStream_t s) {
     dim3 gr = node_grid(c.g), bl = node_block();
+    // fine rows at distance >= margin repeat the centre row; a coarse row I is
+    // deep when its fine neighbourhood (radius 1 around 2I+1) lies there and
+    // all its coarse neighbours exist: per axis lo <= I <= hi with
+    // 2I >= margin, 2I + 2 <= nf - 1 - margin, and 1 <= I <= nc - 2
+    RowSet rs{};
+    if (reuse && f.margin < Level::NO_MARGIN) {
+        const int nf[3] = {f.g.nx, f.g.ny, f.g.nz}, nc[3] = {c.g.nx, c.g.ny, c.g.nz};
+        bool ok = true;
+        for (int d = 0; d < 3; ++d) {
+            if (d == 2 && c.g.dim == 2) { rs.lo[2] = rs.hi[2] = 0; continue; }
+            rs.lo[d] = std::max(1, (f.margin + 1) / 2);
+            rs.hi[d] = std::min(nc[d] - 2, (nf[d] - 3 - f.margin) / 2);
+            const int cc = nc[d] / 2;
+            if (rs.lo[d] > cc || rs.hi[d] < cc) ok = false;  // the centre must be deep
+        }
+        if (ok) {
+            rs.on = 1;
+            rs.nrep = 1;
+            rs.rep[0][0] = c.g.nx / 2; rs.rep[0][1] = c.g.ny / 2; rs.rep[0][2] = c.g.dim == 3 ? c.g.nz / 2 : 0;
+            rs.nshell = rowset_shell_count(c.g, rs.lo, rs.hi);
+            gr = dim3((unsigned)((rs.nshell + rs.nrep + TBX * TBY - 1) / (TBX * TBY)), 1, 1);
+            bl = dim3(TBX * TBY, 1, 1);
+        }
+    }
     const size_t sm2 = sizeof(double) * 9 * TBX * TBY, sm3 = sizeof(double) * 27 * TBX * TBY;
     if (f.g.dim == 2) {
-        if (f.kind == STAR) k_galerkin<2, STAR><<<gr, bl, sm2, s>>>(f.g, c.g, f.A, c.A);
-        else k_galerkin<2, BOX><<<gr, bl, sm2, s>>>(f.g, c.g, f.A, c.A);
+        if (f.kind == STAR) k_galerkin<2, STAR><<<gr, bl, sm2, s>>>(f.g, c.g, f.A, c.A, rs);
+        else k_galerkin<2, BOX><<<gr, bl, sm2, s>>>(f.g, c.g, f.A, c.A, rs);
     } else {
         static bool attr = false;  // 27 x 256 doubles = 54 KB exceeds the default 48 KB
         if (!attr) {
@@ -121,11 +290,16 @@ cs_status galerkin_level(const Level &f, Level &c, cudaStream_t s) {
             CSX_CUDA(cudaFuncSetAttribute(k_galerkin<3, BOX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
             attr = true;
         }
-        if (f.kind == STAR) k_galerkin<3, STAR><<<gr, bl, sm3, s>>>(f.g, c.g, f.A, c.A);
-        else k_galerkin<3, BOX><<<gr, bl, sm3, s>>>(f.g, c.g, f.A, c.A);
+        if (f.kind == STAR) k_galerkin<3, STAR><<<gr, bl, sm3, s>>>(f.g, c.g, f.A, c.A, rs);
+        else k_galerkin<3, BOX><<<gr, bl, sm3, s>>>(f.g, c.g, f.A, c.A, rs);
     }
     CSX_CUDA(cudaGetLastError());
     count_launch();
+    if (rs.on) {
+        k_copy_deep<<<node_grid(c.g), node_block(), 0, s>>>(c.g, c.nst, c.A, rs, -1);
+        CSX_CUDA(cudaGetLastError());
+        count_launch();
+    }
     return CS_OK;
 }
 
@@ -253,17 +427,17 @@ cs_status coarse_factor(cs_hierarchy *h, cudaStream_t s) {
     h->cn = n;
     double *M = nullptr, *W = nullptr;
     int *piv = nullptr, *st = nullptr, *offs = nullptr;
-    CSX_TRY(dalloc_t(&h->cinv, (size_t)n * n, &h->bytes));
+    CSX_TRY(dalloc_t(&h->cinv, (size_t)n * n, &h->bytes, s));
     cs_status rc = CS_OK;
     int offh[81];
     for (int t = 0; t < L.nst; ++t)
         for (int d = 0; d < 3; ++d) offh[3 * t + d] = L.off[t][d];
     int sth = 0;
-    if ((rc = dalloc_t(&M, (size_t)n * n, nullptr)) != CS_OK) goto done;
-    if ((rc = dalloc_t(&W, (size_t)n * n, nullptr)) != CS_OK) goto done;
-    if ((rc = dalloc_t(&piv, (size_t)n + 1, nullptr)) != CS_OK) goto done;
-    if ((rc = dalloc_t(&st, 1, nullptr)) != CS_OK) goto done;
-    if ((rc = dalloc_t(&offs, 81, nullptr)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&M, (size_t)n * n, nullptr, s)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&W, (size_t)n * n, nullptr, s)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&piv, (size_t)n + 1, nullptr, s)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&st, 1, nullptr, s)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&offs, 81, nullptr, s)) != CS_OK) goto done;
     if (cudaMemcpyAsync(offs, offh, sizeof(int) * 3 * L.nst, cudaMemcpyHostToDevice, s) != cudaSuccess) {
         rc = cuda_fail(cudaGetLastError(), "copy offsets", __FILE__, __LINE__);
         goto done;
@@ -281,7 +455,7 @@ cs_status coarse_factor(cs_hierarchy *h, cudaStream_t s) {
         rc = CS_ERR_SINGULAR;
     }
 done:
-    cudaFree(M); cudaFree(W); cudaFree(piv); cudaFree(st); cudaFree(offs);
+    dfree(M, s); dfree(W, s); dfree(piv, s); dfree(st, s); dfree(offs, s);
     return rc;
 }
 
@@ -332,41 +506,70 @@ __global__ void k_fill(int64_t n, double *p, double v) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
 
+// Reuse of repeated rows in a setup step (see "repeated-row detection"):
+// rows at boundary distance >= d_now are deep after this step, rows at
+// distance >= d_prev were deep before it (their E_cur rows are stored only
+// in the representatives rep0 / rep1 of red / black).
+struct Reuse {
+    int on;
+    int d_now, d_prev;
+    int rep0, rep1;
+};
+
 // One setup step (l, k) over rows and a chunk of output offsets o'.
-// Per o' the host supplies (uniform across a warp): mask[o'] with bit s set
-// when o' - off(s) is in O_cur, its index cidx[o'*NST + s], and cur_of[o']
-// (index of o' in O_cur or -1).  Neighbours outside the grid carry a zero
-// prescaled coefficient, so they are read at the row itself (no branch).
-// nchunks == 1: the thread finishes the row (lambda, residual update);
-// otherwise partial <E_i,R_i>, <R_i,R_i> go to part[q*N + i] and
+// For every o' the host supplies the list of valid pairs (s, c) -- stencil
+// entry s and index c in O_cur of o' - off(s) -- packed as (s << 24) | c in
+// pairs[pstart[o'] .. pstart[o'+1]), plus cur_of[o'] (index of o' in O_cur or
+// -1).  Only valid pairs issue an FP64 FMA (on GB300 the FP64 pipe is the
+// bound of this kernel).  The row's prescaled coefficients and neighbour
+// indices sit in shared memory so that s can be a run-time index; a
+// neighbour outside the grid carries a zero coefficient and is read at the
+// row itself.  nchunks == 1: the thread finishes the row (lambda, residual
+// update); otherwise partial <E_i,R_i>, <R_i,R_i> go to part[q*N + i] and
 // k_setup_finish completes the row.  LAST: the final step of the cascade,
 // where E_nu is not needed -- R is neither stored nor used to update E.
 template <int DIM, int KIND, bool LAST>
 __global__ void __launch_bounds__(TBX *TBY) k_setup_rows(Grid g, int periodic, const double *__restrict__ At,
                                                           const double *__restrict__ w, const double *__restrict__ Ecur,
                                                           double *__restrict__ Enxt, int nnxt, int chunk, int nchunks,
-                                                          const unsigned *__restrict__ mask, const int *__restrict__ cidx,
+                                                          const int *__restrict__ pstart,
+                                                          const unsigned *__restrict__ pairs,
                                                           const int *__restrict__ cur_of, int colour,
-                                                          double *__restrict__ lam, double2 *__restrict__ part) {
+                                                          double *__restrict__ lam, double2 *__restrict__ part,
+                                                          Reuse ru, RowSet rs) {
     using S = StenS<DIM, KIND>;
     constexpr int NST = S::NST;
-    const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y;
-    const int iz = (int)(blockIdx.z % (unsigned)g.nz), q = (int)(blockIdx.z / (unsigned)g.nz);
-    if (ix >= g.nx || iy >= g.ny) return;
+    constexpr int NT = TBX * TBY;
+    extern __shared__ double sm_setup[];
+    double *sa = sm_setup;                                   // [NST][NT]
+    int *snb = reinterpret_cast<int *>(sm_setup + NST * NT);  // [NST][NT]
+    const int tid = threadIdx.x + TBX * threadIdx.y;
+    int ix, iy, iz, q;
+    if (rs.on) {  // shell rows and representatives only, packed densely
+        q = blockIdx.y;
+        if (!rowset_coord(rs, g, (int64_t)blockIdx.x * NT + tid, ix, iy, iz)) return;
+    } else {
+        ix = blockIdx.x * TBX + threadIdx.x; iy = blockIdx.y * TBY + threadIdx.y;
+        iz = (int)(blockIdx.z % (unsigned)g.nz); q = (int)(blockIdx.z / (unsigned)g.nz);
+        if (ix >= g.nx || iy >= g.ny) return;
+    }
     const int64_t N = g.N;
     const int i = ix + g.nx * (iy + g.ny * iz);
     const int o0 = q * chunk, o1 = min(nnxt, o0 + chunk);
-    const bool active = colour < 0 || ((((ix + 1) + (iy + 1) + (DIM == 3 ? iz + 1 : 0)) & 1) == colour);
+    const int cme = rb_colour(g, ix, iy, iz);
+    const bool active = colour < 0 || cme == colour;
+    const int dist = periodic ? (1 << 30) : bdist(g, ix, iy, iz);
+    const int repme = cme ? ru.rep1 : ru.rep0;
+    if (ru.on && dist >= ru.d_now && i != repme) return;  // deep row: copied from its representative
+    const int iread = (ru.on && dist >= ru.d_prev) ? repme : i;  // where this row's E_cur is stored
     if (!active) {
         if (!LAST)
             for (int o = o0; o < o1; ++o) {
                 int c = __ldg(cur_of + o);
-                Enxt[(int64_t)o * N + i] = c >= 0 ? Ecur[(int64_t)c * N + i] : 0.0;
+                Enxt[(int64_t)o * N + i] = c >= 0 ? Ecur[(int64_t)c * N + iread] : 0.0;
             }
         return;
     }
-    double a[NST];
-    int nb[NST];
 #pragma unroll
     for (int s = 0; s < NST; ++s) {
         int dx, dy, dz;
@@ -379,19 +582,24 @@ __global__ void __launch_bounds__(TBX *TBY) k_setup_rows(Grid g, int periodic, c
         } else {
             in = jx >= 0 && jx < g.nx && jy >= 0 && jy < g.ny && (DIM == 2 || (jz >= 0 && jz < g.nz));
         }
-        nb[s] = in ? jx + g.nx * (jy + g.ny * jz) : i;
-        a[s] = in ? At[(int64_t)s * N + i] : 0.0;
+        int j = in ? jx + g.nx * (jy + g.ny * jz) : iread;
+        if (in && ru.on && (periodic || bdist(g, jx, jy, jz) >= ru.d_prev))
+            j = rb_colour(g, jx, jy, jz) ? ru.rep1 : ru.rep0;
+        snb[s * NT + tid] = j;
+        sa[s * NT + tid] = in ? At[(int64_t)s * N + i] : 0.0;
     }
     double num = 0.0, den = 0.0;
+    int p = __ldg(pstart + o0);
     for (int o = o0; o < o1; ++o) {
-        const unsigned m = __ldg(mask + o);
-        const int *co = cidx + o * NST;
+        const int pe = __ldg(pstart + o + 1);
         double r = 0.0;
-#pragma unroll
-        for (int s = 0; s < NST; ++s)
-            if (m & (1u << s)) r = fma(a[s], Ecur[(int64_t)__ldg(co + s) * N + nb[s]], r);
+        for (; p < pe; ++p) {
+            const unsigned u = __ldg(pairs + p);
+            const int s = (int)(u >> 24), c = (int)(u & 0xffffffu);
+            r = fma(sa[s * NT + tid], Ecur[(int64_t)c * N + snb[s * NT + tid]], r);
+        }
         const int c0 = __ldg(cur_of + o);
-        if (c0 >= 0) num = fma(Ecur[(int64_t)c0 * N + i], r, num);
+        if (c0 >= 0) num = fma(Ecur[(int64_t)c0 * N + iread], r, num);
         den = fma(r, r, den);
         if (!LAST) Enxt[(int64_t)o * N + i] = r;
     }
@@ -405,7 +613,7 @@ __global__ void __launch_bounds__(TBX *TBY) k_setup_rows(Grid g, int periodic, c
     if (!LAST)
         for (int o = o0; o < o1; ++o) {
             const int c0 = __ldg(cur_of + o);
-            const double e = c0 >= 0 ? Ecur[(int64_t)c0 * N + i] : 0.0;
+            const double e = c0 >= 0 ? Ecur[(int64_t)c0 * N + iread] : 0.0;
             Enxt[(int64_t)o * N + i] = e - lt * Enxt[(int64_t)o * N + i];
         }
     const double wi = w[i];
@@ -420,14 +628,27 @@ __global__ void __launch_bounds__(TBX *TBY) k_setup_finish(Grid g, const double 
                                                             const double *__restrict__ Ecur, double *__restrict__ Enxt,
                                                             int nnxt, int chunk, int nchunks,
                                                             const int *__restrict__ cur_of, int colour,
-                                                            double *__restrict__ lam, const double2 *__restrict__ part) {
-    const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y;
-    const int iz = (int)(blockIdx.z % (unsigned)g.nz), q = (int)(blockIdx.z / (unsigned)g.nz);
-    if (ix >= g.nx || iy >= g.ny) return;
-    const bool active = colour < 0 || ((((ix + 1) + (iy + 1) + (DIM == 3 ? iz + 1 : 0)) & 1) == colour);
+                                                            double *__restrict__ lam, const double2 *__restrict__ part,
+                                                            int periodic, Reuse ru, RowSet rs) {
+    int ix, iy, iz, q;
+    if (rs.on) {
+        q = blockIdx.y;
+        if (!rowset_coord(rs, g, (int64_t)blockIdx.x * (TBX * TBY) + threadIdx.x + TBX * threadIdx.y, ix, iy, iz))
+            return;
+    } else {
+        ix = blockIdx.x * TBX + threadIdx.x; iy = blockIdx.y * TBY + threadIdx.y;
+        iz = (int)(blockIdx.z % (unsigned)g.nz); q = (int)(blockIdx.z / (unsigned)g.nz);
+        if (ix >= g.nx || iy >= g.ny) return;
+    }
+    const int cme = rb_colour(g, ix, iy, iz);
+    const bool active = colour < 0 || cme == colour;
     if (!active) return;
     const int64_t N = g.N;
     const int i = ix + g.nx * (iy + g.ny * iz);
+    const int dist = periodic ? (1 << 30) : bdist(g, ix, iy, iz);
+    const int repme = cme ? ru.rep1 : ru.rep0;
+    if (ru.on && dist >= ru.d_now && i != repme) return;
+    const int iread = (ru.on && dist >= ru.d_prev) ? repme : i;
     double num = 0.0, den = 0.0;
     for (int t = 0; t < nchunks; ++t) {
         double2 p = part[(int64_t)t * N + i];
@@ -440,24 +661,44 @@ __global__ void __launch_bounds__(TBX *TBY) k_setup_finish(Grid g, const double 
     const int o0 = q * chunk, o1 = min(nnxt, o0 + chunk);
     for (int o = o0; o < o1; ++o) {
         const int c0 = __ldg(cur_of + o);
-        const double e = c0 >= 0 ? Ecur[(int64_t)c0 * N + i] : 0.0;
+        const double e = c0 >= 0 ? Ecur[(int64_t)c0 * N + iread] : 0.0;
         Enxt[(int64_t)o * N + i] = e - lt * Enxt[(int64_t)o * N + i];
     }
 }
 
+
 template <int DIM, int KIND, bool LAST>
-static void launch_setup_rows(const Grid &g, int periodic, const double *At, const double *w, const double *Ecur,
-                              double *Enxt, int nn, int chunk, int nchunks, const unsigned *mask, const int *cidx,
-                              const int *cur_of, int colour, double *lam, double2 *part, cudaStream_t s) {
+static cs_status launch_setup_rows(const Grid &g, int periodic, const double *At, const double *w,
+                                   const double *Ecur, double *Enxt, int nn, int chunk, int nchunks,
+                                   const int *pstart, const unsigned *pairs, const int *cur_of, int colour,
+                                   double *lam, double2 *part, const Reuse &ru, const RowSet &rs, cudaStream_t s) {
     dim3 gr = node_grid(g), bl = node_block();
     gr.z *= nchunks;
-    k_setup_rows<DIM, KIND, LAST><<<gr, bl, 0, s>>>(g, periodic, At, w, Ecur, Enxt, nn, chunk, nchunks, mask, cidx,
-                                                    cur_of, colour, lam, part);
+    if (rs.on) {
+        gr = dim3((unsigned)((rs.nshell + rs.nrep + TBX * TBY - 1) / (TBX * TBY)), (unsigned)nchunks, 1);
+        bl = dim3(TBX * TBY, 1, 1);
+    }
+    const size_t smem = (size_t)StenS<DIM, KIND>::NST * TBX * TBY * (sizeof(double) + sizeof(int));
+    static bool attr = false;  // up to 27 x 256 x 12 B = 81 KB: above the default 48 KB
+    if (!attr) {
+        CSX_CUDA(cudaFuncSetAttribute(k_setup_rows<DIM, KIND, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        attr = true;
+    }
+    k_setup_rows<DIM, KIND, LAST><<<gr, bl, smem, s>>>(g, periodic, At, w, Ecur, Enxt, nn, chunk, nchunks, pstart,
+                                                       pairs, cur_of, colour, lam, part, ru, rs);
     count_launch();
     if (nchunks > 1) {
-        k_setup_finish<DIM, LAST><<<gr, bl, 0, s>>>(g, w, Ecur, Enxt, nn, chunk, nchunks, cur_of, colour, lam, part);
+        k_setup_finish<DIM, LAST><<<gr, bl, 0, s>>>(g, w, Ecur, Enxt, nn, chunk, nchunks, cur_of, colour, lam, part,
+                                                    periodic, ru, rs);
         count_launch();
     }
+    if (rs.on) {  // deep rows of the active colour take their representative's lambda
+        k_copy_deep<<<node_grid(g), node_block(), 0, s>>>(g, 1, lam, rs, colour);
+        count_launch();
+    }
+    CSX_CUDA(cudaGetLastError());
+    return CS_OK;
 }
 
 struct Off3 {
@@ -467,8 +708,8 @@ struct Off3 {
 };
 
 template <int DIM, int KIND>
-static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, int prescale, double *lam,
-                               cudaStream_t s, int64_t *peak) {
+static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse,
+                               double *lam, cudaStream_t s, int64_t *peak) {
     using S = StenS<DIM, KIND>;
     constexpr int NST = S::NST;
     const Level &L = h->lev[l];
@@ -477,18 +718,19 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
     const int ncol = kind == CS_MULTIPLICATIVE ? 2 : 1;
     dim3 gr = node_grid(g), bl = node_block();
     double *w = nullptr, *At = nullptr, *Ecur = nullptr, *Enxt = nullptr;
-    int *bad = nullptr, *cidx = nullptr, *cur_of = nullptr;
-    unsigned *mask = nullptr;
+    int *bad = nullptr, *pstart = nullptr, *cur_of = nullptr;
+    unsigned *pairs = nullptr;
     double2 *part = nullptr;
     cs_status rc = CS_OK;
     int badh = 0;
     std::vector<Off3> Ocur{{0, 0, 0}};
     int64_t live = 0, pk = 0;
     auto track = [&](int64_t d) { live += d; pk = std::max(pk, live); };
+    Reuse ru{0, 0, 0, 0, 0};
 
-    if ((rc = dalloc_t(&w, N, nullptr)) != CS_OK) goto done;
-    if ((rc = dalloc_t(&At, (size_t)NST * N, nullptr)) != CS_OK) goto done;
-    if ((rc = dalloc_t(&bad, 1, nullptr)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&w, N, nullptr, s)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&At, (size_t)NST * N, nullptr, s)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&bad, 1, nullptr, s)) != CS_OK) goto done;
     track((int64_t)(NST + 1) * N * 8);
     if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__); goto done; }
     k_prescale<DIM, KIND><<<gr, bl, 0, s>>>(g, h->periodic, prescale, L.A, w, At, bad);
@@ -505,13 +747,51 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
     }
     k_scale_op<DIM, KIND><<<gr, bl, 0, s>>>(g, h->periodic, L.A, w, At);
     count_launch();
-    if ((rc = dalloc_t(&Ecur, N, nullptr)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&Ecur, N, nullptr, s)) != CS_OK) goto done;
     track(N * 8);
     k_fill<<<1216, 256, 0, s>>>(N, Ecur, 1.0);
     count_launch();
 
+    // representatives: the grid centre and its +x neighbour (the other colour)
+    {
+        const int cx = g.nx / 2, cy = g.ny / 2, cz = DIM == 3 ? g.nz / 2 : 0;
+        const int ci = cx + g.nx * (cy + g.ny * cz);
+        const int cc = ((cx + 1) + (cy + 1) + (DIM == 3 ? cz + 1 : 0)) & 1;
+        const int steps = nu * ncol;
+        const bool deep_enough = h->periodic ? true : bdist_host(g, cx, cy, cz) - 1 >= L.margin + steps;
+        if (reuse && L.margin < Level::NO_MARGIN && deep_enough && cx + 1 < g.nx) {
+            ru.on = 1;
+            if (ncol == 1) {  // additive: all deep rows repeat one row, whatever their colour
+                ru.rep0 = ru.rep1 = ci;
+            } else {
+                ru.rep0 = cc == 0 ? ci : ci + 1;
+                ru.rep1 = cc == 0 ? ci + 1 : ci;
+            }
+        }
+    }
     for (int lev = 0; lev < nu; ++lev) {
         for (int k = 0; k < ncol; ++k) {
+            const int t = lev * ncol + k + 1;  // flattened step number
+            ru.d_now = L.margin + t;
+            ru.d_prev = L.margin + t - 1;
+            RowSet rs{};
+            if (ru.on) {
+                rs.on = 1;
+                const int nn3[3] = {g.nx, g.ny, g.nz};
+                for (int d = 0; d < 3; ++d) {
+                    if (d == 2 && DIM == 2) { rs.lo[2] = rs.hi[2] = 0; continue; }
+                    rs.lo[d] = h->periodic ? 0 : ru.d_now;
+                    rs.hi[d] = h->periodic ? nn3[d] - 1 : nn3[d] - 1 - ru.d_now;
+                }
+                rs.nshell = rowset_shell_count(g, rs.lo, rs.hi);
+                rs.nrep = ncol;
+                for (int c = 0; c < ncol; ++c) {
+                    const int ri = c == 0 ? ru.rep0 : ru.rep1;
+                    rs.rep[c][0] = ri % g.nx;
+                    rs.rep[c][1] = (ri / g.nx) % g.ny;
+                    rs.rep[c][2] = ri / (g.nx * g.ny);
+                }
+            }
             // O_next = O_cur + S
             std::vector<Off3> On;
             for (const Off3 &o : Ocur)
@@ -534,8 +814,8 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
             std::map<Off3, int> idx;
             for (size_t t = 0; t < Ocur.size(); ++t) idx[Ocur[t]] = (int)t;
             const int nn = (int)On.size();
-            std::vector<int> hci((size_t)nn * NST, 0), hc(nn);
-            std::vector<unsigned> hm(nn, 0u);
+            std::vector<int> hps(nn + 1, 0), hc(nn);
+            std::vector<unsigned> hpairs;
             for (int o = 0; o < nn; ++o) {
                 auto it = idx.find(On[o]);
                 hc[o] = it == idx.end() ? -1 : it->second;
@@ -543,11 +823,9 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
                     int dx, dy, dz;
                     S::off(t, dx, dy, dz);
                     auto jt = idx.find({On[o].x - dx, On[o].y - dy, On[o].z - dz});
-                    if (jt != idx.end()) {
-                        hm[o] |= 1u << t;
-                        hci[(size_t)o * NST + t] = jt->second;
-                    }
+                    if (jt != idx.end()) hpairs.push_back(((unsigned)t << 24) | (unsigned)jt->second);
                 }
+                hps[o + 1] = (int)hpairs.size();
             }
             const bool last = lev == nu - 1 && k == ncol - 1;
             // parallelism for small levels: split each row's offsets into chunks
@@ -555,36 +833,34 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
             nchunks = std::max(1, std::min(nchunks, 65535 / std::max(1, g.nz)));
             const int chunk = (nn + nchunks - 1) / nchunks;
             nchunks = (nn + chunk - 1) / chunk;
-            cudaFree(cidx); cudaFree(cur_of); cudaFree(mask); cudaFree(part);
-            cidx = nullptr; cur_of = nullptr; mask = nullptr; part = nullptr;
-            if ((rc = dalloc_t(&cidx, hci.size(), nullptr)) != CS_OK) goto done;
-            if ((rc = dalloc_t(&cur_of, hc.size(), nullptr)) != CS_OK) goto done;
-            if ((rc = dalloc_t(&mask, hm.size(), nullptr)) != CS_OK) goto done;
-            if (nchunks > 1 && (rc = dalloc_t(&part, (size_t)nchunks * N, nullptr)) != CS_OK) goto done;
-            if (cudaMemcpyAsync(cidx, hci.data(), hci.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            dfree(pstart, s); dfree(cur_of, s); dfree(pairs, s); dfree(part, s);
+            pstart = nullptr; cur_of = nullptr; pairs = nullptr; part = nullptr;
+            if ((rc = dalloc_t(&pstart, hps.size(), nullptr, s)) != CS_OK) goto done;
+            if ((rc = dalloc_t(&cur_of, hc.size(), nullptr, s)) != CS_OK) goto done;
+            if ((rc = dalloc_t(&pairs, hpairs.size(), nullptr, s)) != CS_OK) goto done;
+            if (nchunks > 1 && (rc = dalloc_t(&part, (size_t)nchunks * N, nullptr, s)) != CS_OK) goto done;
+            if (cudaMemcpyAsync(pstart, hps.data(), hps.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
                 cudaMemcpyAsync(cur_of, hc.data(), hc.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-                cudaMemcpyAsync(mask, hm.data(), hm.size() * sizeof(unsigned), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+                cudaMemcpyAsync(pairs, hpairs.data(), hpairs.size() * sizeof(unsigned), cudaMemcpyHostToDevice, s) !=
+                    cudaSuccess) {
                 rc = cuda_fail(cudaGetLastError(), "copy setup tables", __FILE__, __LINE__);
                 goto done;
             }
             if (!last) {
-                if ((rc = dalloc_t(&Enxt, (size_t)nn * N, nullptr)) != CS_OK) goto done;
+                if ((rc = dalloc_t(&Enxt, (size_t)nn * N, nullptr, s)) != CS_OK) goto done;
                 track((int64_t)nn * N * 8);
             }
             {
                 const int colour = ncol == 2 ? k : -1;
                 double *lam_l = lam + (int64_t)lev * N;
-                if (last)
-                    launch_setup_rows<DIM, KIND, true>(g, h->periodic, At, w, Ecur, Enxt, nn, chunk, nchunks, mask,
-                                                       cidx, cur_of, colour, lam_l, part, s);
-                else
-                    launch_setup_rows<DIM, KIND, false>(g, h->periodic, At, w, Ecur, Enxt, nn, chunk, nchunks, mask,
-                                                        cidx, cur_of, colour, lam_l, part, s);
+                rc = last ? launch_setup_rows<DIM, KIND, true>(g, h->periodic, At, w, Ecur, Enxt, nn, chunk, nchunks,
+                                                               pstart, pairs, cur_of, colour, lam_l, part, ru, rs, s)
+                          : launch_setup_rows<DIM, KIND, false>(g, h->periodic, At, w, Ecur, Enxt, nn, chunk, nchunks,
+                                                                pstart, pairs, cur_of, colour, lam_l, part, ru, rs, s);
+                if (rc != CS_OK) goto done;
             }
             if (cudaGetLastError() != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "k_setup_rows", __FILE__, __LINE__); goto done; }
-            // the host tables are rebuilt next step: wait for their copies
-            if (cudaStreamSynchronize(s) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "setup step", __FILE__, __LINE__); goto done; }
-            cudaFree(Ecur);
+            dfree(Ecur, s);
             track(-(int64_t)Ocur.size() * N * 8);
             Ecur = Enxt;
             Enxt = nullptr;
@@ -592,21 +868,21 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
         }
     }
 done:
-    cudaFree(w); cudaFree(At); cudaFree(Ecur); cudaFree(Enxt); cudaFree(bad); cudaFree(cidx); cudaFree(cur_of);
-    cudaFree(mask); cudaFree(part);
+    dfree(w, s); dfree(At, s); dfree(Ecur, s); dfree(Enxt, s); dfree(bad, s); dfree(pstart, s); dfree(cur_of, s);
+    dfree(pairs, s); dfree(part, s);
     if (peak) *peak = std::max(*peak, pk);
     return rc;
 }
 
-cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, double *lam,
+cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, double *lam,
                               cudaStream_t s, int64_t *peak) {
     const Level &L = h->lev[l];
     if (L.g.dim == 2) {
-        if (L.kind == STAR) return setup_level_t<2, STAR>(h, l, kind, nu, prescale, lam, s, peak);
-        return setup_level_t<2, BOX>(h, l, kind, nu, prescale, lam, s, peak);
+        if (L.kind == STAR) return setup_level_t<2, STAR>(h, l, kind, nu, prescale, reuse, lam, s, peak);
+        return setup_level_t<2, BOX>(h, l, kind, nu, prescale, reuse, lam, s, peak);
     }
-    if (L.kind == STAR) return setup_level_t<3, STAR>(h, l, kind, nu, prescale, lam, s, peak);
-    return setup_level_t<3, BOX>(h, l, kind, nu, prescale, lam, s, peak);
+    if (L.kind == STAR) return setup_level_t<3, STAR>(h, l, kind, nu, prescale, reuse, lam, s, peak);
+    return setup_level_t<3, BOX>(h, l, kind, nu, prescale, reuse, lam, s, peak);
 }
 
 }  // namespace csx

@@ -298,3 +298,26 @@ def test_zero_rhs(built):
     info = cmg.solve(hg, cg, _dev(np.zeros(A.N)), x)
     assert info.converged and info.iterations == 0
     assert not _host(x).any()
+
+
+@pytest.mark.parametrize("dim,n,kind,nu", [(3, 40, "additive", 3), (3, 41, "multiplicative", 2), (2, 97, "additive", 4),
+                                          (2, 96, "multiplicative", 3)])
+def test_repeated_row_reuse_is_exact(built, dim, n, kind, nu):
+    """Computing repeated rows once (constant-coefficient interior) gives
+    bitwise the same Galerkin operators and Lambda as computing every row,
+    and both match the oracle."""
+    import paper_2606_12577_gb300 as cmg
+    A = problems.poisson(dim, n)
+    h1 = gu.gpu_hierarchy(A)
+    h0 = gu.gpu_hierarchy(A, reuse=False)
+    assert h1.nlevels == h0.nlevels
+    for l in range(h1.nlevels):
+        assert np.array_equal(cmg.export_operator(h1, l)[1], cmg.export_operator(h0, l)[1]), f"operator {l}"
+    c1 = cmg.setup_cascade(h1, kind, nu=nu)
+    c0 = cmg.setup_cascade(h0, kind, nu=nu, reuse=False)
+    ho = oracle.Hierarchy(A)
+    co = oracle.Cascade(ho, kind, nu=nu)
+    for l in range(co.nlev):
+        l1, l0 = cmg.export_lambda(c1, l), cmg.export_lambda(c0, l)
+        assert np.array_equal(l1, l0), f"lambda level {l}"
+        assert gu.rel_max(l1, co.lam(l)) <= TOL
