@@ -51,7 +51,7 @@ def args_():
     p.add_argument("--order", default="RF")
     p.add_argument("--cpu-n", type=int, default=64, help="side of the oracle's bounded sample")
     p.add_argument("--no-extras", action="store_true", help="time the chosen form only")
-    p.add_argument("--profile", default="", choices=["", "setup", "step"],
+    p.add_argument("--profile", default="", choices=["", "setup", "step", "sweep"],
                    help="run one untimed setup (or setup + solve) and exit: the case ncu captures")
     return p.parse_args()
 
@@ -250,6 +250,12 @@ def main():
             x = torch.zeros(A.N, dtype=torch.float64, device=dev)
             cmg.solve(h, c, bd, x, method="refine", precision="fp32", tol=1e-10, mu_pre=mu, mu_post=mu,
                       order=a.order)
+        if a.profile == "sweep":  # the FP32 finest-level steps the roofline loop times
+            xb = [torch.rand(A.N, device=dev, dtype=torch.float32) for _ in range(2)]
+            b32 = torch.rand(A.N, device=dev, dtype=torch.float32)
+            for k in range(5):
+                cmg.sweep(h, c, 0, k % a.nu, b32, xb[k % 2], xb[(k + 1) % 2],
+                          colour=-1 if a.kind == "additive" else 0)
         torch.cuda.synchronize()
         print(json.dumps({"profile": a.profile, "n": a.n, "launches": cmg.kernel_launches()}), flush=True)
         return
