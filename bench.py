@@ -51,7 +51,7 @@ def args_():
     p.add_argument("--order", default="RF")
     p.add_argument("--cpu-n", type=int, default=64, help="side of the oracle's bounded sample")
     p.add_argument("--no-extras", action="store_true", help="time the chosen form only")
-    p.add_argument("--profile", default="", choices=["", "setup", "step", "sweep"],
+    p.add_argument("--profile", default="", choices=["", "setup", "step", "sweep", "multirhs"],
                    help="run one untimed setup (or setup + solve) and exit: the case ncu captures")
     return p.parse_args()
 
@@ -204,6 +204,18 @@ def main():
     import paper_2606_12577_gb300 as cmg
     import problems
 
+    if a.profile == "multirhs":  # the multi-RHS block steps the bench times (interface problem, n^2)
+        Ai = problems.interface2d(a.n)
+        hb = cmg.setup_hierarchy(Ai.dim, Ai.n, Ai.offsets, torch.tensor(Ai.coeff, device=dev), block=2)
+        cb = cmg.setup_cascade(hb, "additive", nu=3, lowp=True)
+        Xb = [torch.rand(Ai.N * 32, device=dev, dtype=torch.float32) for _ in range(2)]
+        Bb = torch.rand(Ai.N * 32, device=dev, dtype=torch.float32)
+        for k in range(5):
+            cmg.sweep_rhs(hb, cb, 0, k % 3, Bb, Xb[k % 2], Xb[(k + 1) % 2], 32)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": a.profile, "n": a.n}), flush=True)
+        return
+
     A, b = problems.poisson3d(a.n)
     coeff = torch.tensor(A.coeff, dtype=torch.float64, device=dev)
     bd = torch.tensor(b, dtype=torch.float64, device=dev)
@@ -340,6 +352,32 @@ def main():
                               "launch_ms": t_sweep * 1e3}
         result["smoother_gbs"] = achieved
         del h, c, x
+        torch.cuda.empty_cache()
+        # ---- multi-RHS block step (the block product X_b -= Lambda_b R_b):
+        # elliptic interface 1024^2, 200 inclusions, 2x2-node blocks, 32 RHS, FP32
+        Ai = problems.interface2d(1024)
+        ci = torch.tensor(Ai.coeff, dtype=torch.float64, device=dev)
+        hb = cmg.setup_hierarchy(Ai.dim, Ai.n, Ai.offsets, ci, block=2)
+        cb = cmg.setup_cascade(hb, "additive", nu=3, lowp=True)
+        m, Ni = 32, Ai.N
+        Xb = [torch.rand(Ni * m, device=dev, dtype=torch.float32) for _ in range(2)]
+        Bb = torch.rand(Ni * m, device=dev, dtype=torch.float32)
+        for k in range(3):
+            cmg.sweep_rhs(hb, cb, 0, k % 3, Bb, Xb[k % 2], Xb[(k + 1) % 2], m)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for k in range(reps):
+            cmg.sweep_rhs(hb, cb, 0, k % 3, Bb, Xb[k % 2], Xb[(k + 1) % 2], m)
+        e1.record(s)
+        torch.cuda.synchronize()
+        t_m = e0.elapsed_time(e1) / reps * 1e-3
+        bytes_m = (5 + 4 + 3 * m) * 4 * Ni  # A, Lambda (16 per 4-node block), B, X read, X written
+        result["multi_rhs_block_step"] = {
+            "workload": "elliptic interface 1024^2, 200 inclusions (contrast 1e-4..1e4), 2x2-node blocks "
+                        "(4x4 Lambda), 32 RHS, FP32, finest level",
+            "launch_ms": t_m * 1e3, "achieved_gbs": bytes_m / t_m / 1e9, "frac_of_peak": bytes_m / t_m / 1e9 / peak,
+            "algorithmic_bytes_per_launch": bytes_m, "bound": "hbm"}
+        del hb, cb, ci, Xb, Bb
         torch.cuda.empty_cache()
         # ---- plain FP64 path (stationary V-cycle iteration)
         pinfo = []

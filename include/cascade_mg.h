@@ -74,7 +74,8 @@ typedef struct {
 typedef struct {
     int coarse_max; /* stop coarsening when every side is <= coarse_max (default 4) */
     int max_levels; /* 0 = no limit */
-    int block;      /* block edge in nodes (1 = point blocks; >1 unsupported for now) */
+    int block;      /* block edge in nodes: 1 = point blocks; 2 or 3 (2D), 2 (3D) = blocks of
+                       block^dim nodes, partial at the upper edges (default 1) */
     int no_reuse;   /* 0 (default): coarse rows whose fine neighbourhood repeats the
                        grid-centre row's are computed once and copied (exact: bitwise the
                        same as computing each); 1: compute every row */
@@ -159,6 +160,16 @@ cs_status cs_smooth(const cs_hierarchy *h, cs_cascade *c, int level, int reverse
  * colouring); otherwise out must not alias x. */
 cs_status cs_sweep(const cs_hierarchy *h, cs_cascade *c, int level, int step, int colour, int precision,
                    const void *b, const void *x, void *out, cs_stream stream);
+
+/* One cascade step with nrhs right-hand sides (1..32), vectors stored
+ * RHS-contiguous (value r of node i at [i*nrhs + r]):
+ *     X_out = X - Lambda_{step+1[, colour]}^(T) (A X - B),  block by block,
+ * the multi-RHS block product X_b -= Lambda_b R_b of n_b x nrhs tiles;
+ * transpose != 0 applies Lambda^T (the reverse application).  precision
+ * CS_FP64: double vectors; CS_FP32: float vectors (needs lowp).  Aliasing
+ * rules as for cs_sweep. */
+cs_status cs_sweep_rhs(const cs_hierarchy *h, cs_cascade *c, int level, int step, int colour, int transpose,
+                       int precision, int nrhs, const void *b, const void *x, void *out, cs_stream stream);
 
 /* rc = R (A x - b) on `level` (Algorithm 1's restricted residual; R =
  * 2^-dim P^T).  rc has N_{level+1} doubles. */
@@ -252,6 +263,8 @@ typedef struct {
     int nst;          /* stencil entries stored for this level */
     int off[27][3];   /* their offsets */
     int nlevels;      /* levels in the hierarchy */
+    int block;        /* block edge in nodes */
+    int64_t lamsize;  /* doubles of Lambda per cascade step (sum of n_b^2 over blocks) */
 } cs_level_info;
 
 cs_status cs_query_level(const cs_hierarchy *h, int level, cs_level_info *info);
@@ -260,8 +273,11 @@ cs_status cs_query_level(const cs_hierarchy *h, int level, cs_level_info *info);
 cs_status cs_export_operator(const cs_hierarchy *h, int level, double *host_coeff);
 /* Red-black colour id of every node of `level` (0 = red) into HOST memory. */
 cs_status cs_export_colours(const cs_hierarchy *h, int level, int8_t *host_colour);
-/* Copy Lambda of `level` to HOST memory: [nu][N] doubles (point blocks; the
- * multiplicative Lambda_{l,k} occupy the nodes of colour k). */
+/* Copy Lambda of `level` to HOST memory: [nu][lamsize] doubles.  Point blocks:
+ * one value per node.  Blocks: for every block (x fastest over the block
+ * grid) its n_b x n_b matrix, row-major over its nodes in ascending index
+ * order.  The multiplicative Lambda_{l,k} occupy the blocks of colour k
+ * (red = even 1-based block index sum). */
 cs_status cs_export_lambda(const cs_cascade *c, int level, double *host_lambda);
 /* Number of device bytes the handle holds. */
 int64_t cs_hierarchy_bytes(const cs_hierarchy *h);

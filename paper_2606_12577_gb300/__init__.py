@@ -18,7 +18,7 @@ import numpy as np
 from . import _capi
 from ._capi import CascadeError
 
-__all__ = ["setup_hierarchy", "setup_cascade", "vcycle", "solve", "smooth", "sweep", "residual_restrict",
+__all__ = ["setup_hierarchy", "setup_cascade", "vcycle", "solve", "smooth", "sweep", "sweep_rhs", "residual_restrict",
            "prolong_correct", "coarse_solve", "residual", "query_level", "export_operator", "export_colours",
            "export_lambda", "kernel_launches", "smooth_noalloc", "Hierarchy", "Cascade", "SolveInfo", "CascadeError"]
 
@@ -70,7 +70,8 @@ class Hierarchy:
             _capi.check(_capi.lib().cs_query_level(self._p, level, C.byref(info)), "cs_query_level")
             self._infos[level] = {
                 "dim": info.dim, "n": tuple(info.n), "N": int(info.N), "nst": info.nst,
-                "offsets": [tuple(info.off[s]) for s in range(info.nst)], "nlevels": info.nlevels}
+                "offsets": [tuple(info.off[s]) for s in range(info.nst)], "nlevels": info.nlevels,
+                "block": info.block, "lamsize": int(info.lamsize)}
         return self._infos[level]
 
     def N(self, level=0):
@@ -215,6 +216,26 @@ def smooth_noalloc(dim, n, box, coeff, lam, nu, b, x, kind="additive", reverse=F
                 "cs_smooth_noalloc")
 
 
+def sweep_rhs(h, c, level, step, b, x, out, nrhs, colour=-1, transpose=False, stream=None):
+    """One cascade step with nrhs right-hand sides (RHS-contiguous [N, nrhs]
+    tensors, float64 or float32): out = x - Lambda^(T) (A x - b) block by block."""
+    torch = _torch()
+    N = h.N(level)
+    ts = (b, x, out)
+    if any((not isinstance(t, torch.Tensor)) or (not t.is_cuda) or (not t.is_contiguous()) or t.numel() != N * nrhs
+           for t in ts):
+        raise ValueError(f"b, x, out must be contiguous CUDA tensors of {N}x{nrhs} values")
+    if all(t.dtype == torch.float32 for t in ts):
+        prec = _capi.CS_FP32
+    elif all(t.dtype == torch.float64 for t in ts):
+        prec = _capi.CS_FP64
+    else:
+        raise TypeError("b, x, out must all be float64 or all float32")
+    _capi.check(_capi.lib().cs_sweep_rhs(h.ptr, c.ptr, level, step, colour, int(bool(transpose)), prec, nrhs,
+                                         C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()),
+                                         C.c_void_p(out.data_ptr()), _stream(stream)), "cs_sweep_rhs")
+
+
 def kernel_launches() -> int:
     """Kernel launches issued by the library in this process so far."""
     return int(_capi.lib().cs_kernel_launches())
@@ -302,6 +323,6 @@ def export_colours(h, level):
 
 
 def export_lambda(c, level):
-    out = np.zeros((c.nu, c.hier.N(level)))
+    out = np.zeros((c.nu, c.hier.level_info(level)["lamsize"]))
     _capi.check(_capi.lib().cs_export_lambda(c.ptr, level, out.ctypes.data_as(C.c_void_p)), "cs_export_lambda")
     return out

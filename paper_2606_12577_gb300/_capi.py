@@ -54,7 +54,7 @@ class cs_solve_info(C.Structure):
 
 class cs_level_info(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("N", C.c_int64), ("nst", C.c_int),
-                ("off", (C.c_int * 3) * 27), ("nlevels", C.c_int)]
+                ("off", (C.c_int * 3) * 27), ("nlevels", C.c_int), ("block", C.c_int), ("lamsize", C.c_int64)]
 
 
 _lock = threading.Lock()
@@ -70,6 +70,8 @@ _SIGS = {
     "cs_sweep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                            C.c_void_p, C.c_void_p]),
     "cs_kernel_launches": (C.c_int64, []),
+    "cs_sweep_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cs_smooth_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                     C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cs_residual_restrict": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -130,6 +130,18 @@ View<float> view<float>(const cs_hierarchy *, const cs_cascade *c, int l) {
     return {L.A, L.lam, L.b, L.x, L.t};
 }
 
+// doubles of Lambda per cascade step on a level
+static int64_t lam_step(const Level &L) { return L.bs > 1 ? L.nblocks * L.nmax * L.nmax : L.g.N; }
+
+static void set_blocks(Level &L, int bs) {
+    L.bs = bs;
+    L.nbx = (L.g.nx + bs - 1) / bs;
+    L.nby = (L.g.ny + bs - 1) / bs;
+    L.nbz = L.g.dim == 3 ? (L.g.nz + bs - 1) / bs : 1;
+    L.nblocks = (int64_t)L.nbx * L.nby * L.nbz;
+    L.nmax = L.g.dim == 3 ? bs * bs * bs : bs * bs;
+}
+
 static bool inplace_colours(const cs_cascade *c, const Level &L) {
     // red-black is a graph colouring of a STAR stencil: colour-k updates read
     // only the other colour, so they may overwrite x in place
@@ -142,20 +154,17 @@ template <typename T>
 static cs_status smooth_apply(const cs_hierarchy *h, const cs_cascade *c, int l, const View<T> &v, const T *b,
                               T *&cur, T *&other, bool reverse, bool &xzero, cudaStream_t s) {
     const Level &L = h->lev[l];
-    const int64_t N = L.g.N;
     const bool inpl = inplace_colours(c, L);
     for (int step = 0; step < c->nu; ++step) {
         int lv = reverse ? c->nu - 1 - step : step;
         for (int kk = 0; kk < c->ncol; ++kk) {
             int k = reverse ? c->ncol - 1 - kk : kk;
             int colour = c->ncol == 2 ? k : -1;
-            const T *lam = v.lam + (int64_t)lv * N;
-            if (inpl) {
-                CSX_TRY(launch_sweep<T>(L, v.A, lam, b, cur, cur, colour, xzero, s));
-            } else {  // snapshot semantics: read cur, write the other buffer
-                CSX_TRY(launch_sweep<T>(L, v.A, lam, b, cur, other, colour, xzero, s));
-                std::swap(cur, other);
-            }
+            const T *lam = v.lam + (int64_t)lv * lam_step(L);
+            T *dst = inpl ? cur : other;  // snapshot semantics unless colour steps may run in place
+            if (L.bs > 1) CSX_TRY(launch_block_sweep<T>(L, v.A, lam, b, cur, dst, colour, reverse, xzero, s));
+            else CSX_TRY(launch_sweep<T>(L, v.A, lam, b, cur, dst, colour, xzero, s));
+            if (!inpl) std::swap(cur, other);
             xzero = false;
         }
     }
@@ -303,7 +312,10 @@ cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts
     if (n[0] < 1 || n[1] < 1 || n[2] < 1 || (dim == 2 && A0->n[2] > 1)) { set_error("bad grid size"); return CS_ERR_ARG; }
     if ((int64_t)n[0] * n[1] * n[2] >= (int64_t)1 << 31) { set_error("grid too large (N must fit in 31 bits)"); return CS_ERR_ARG; }
     if (A0->nst < 1 || A0->nst > 27 || !A0->coeff) { set_error("bad stencil"); return CS_ERR_ARG; }
-    if (opts.block != 1) { set_error("only point blocks (block = 1) are implemented"); return CS_ERR_UNSUPPORTED; }
+    if (opts.block < 1 || opts.block > (dim == 3 ? 2 : 3)) {
+        set_error("block edge must be 1..%d in %dD", dim == 3 ? 2 : 3, dim);
+        return CS_ERR_UNSUPPORTED;
+    }
     bool star = true, centre = false;
     bool seen[27] = {false};
     for (int s2 = 0; s2 < A0->nst; ++s2) {
@@ -331,6 +343,7 @@ cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts
         Level L0;
         L0.g = make_grid(dim, n[0], n[1], n[2]);
         L0.kind = star ? STAR : BOX;
+        set_blocks(L0, opts.block);
         L0.nst = star ? 2 * dim + 1 : (dim == 3 ? 27 : 9);
         fill_offsets(L0);
         if ((rc = dalloc_t(&L0.A, (size_t)L0.nst * L0.g.N, &h->bytes, s)) != CS_OK) goto fail_nolevel;
@@ -354,6 +367,7 @@ cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts
         Level C;
         C.g = make_grid(dim, F.g.nx / 2, F.g.ny / 2, dim == 3 ? F.g.nz / 2 : 1);
         C.kind = BOX;
+        set_blocks(C, opts.block);
         C.nst = dim == 3 ? 27 : 9;
         fill_offsets(C);
         if ((rc = dalloc_t(&C.A, (size_t)C.nst * C.g.N, &h->bytes, s)) != CS_OK) goto fail;
@@ -420,9 +434,15 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
     c->lam.assign(c->nlev, nullptr);
     for (int l = 0; l < c->nlev; ++l) {
         const int64_t N = h->lev[l].g.N;
-        if ((rc = dalloc_t(&c->lam[l], (size_t)c->nu * N, &c->bytes, s)) != CS_OK) goto fail;
-        if ((rc = cascade_setup_level(h, l, c->kind, c->nu, o->prescale, !o->no_reuse, c->lam[l], s, &peak)) != CS_OK)
+        const Level &L = h->lev[l];
+        if ((rc = dalloc_t(&c->lam[l], (size_t)c->nu * lam_step(L), &c->bytes, s)) != CS_OK) goto fail;
+        if (L.bs > 1) {
+            if ((rc = cascade_setup_level_blocks(h, l, c->kind, c->nu, o->prescale, c->lam[l], s)) != CS_OK) goto fail;
+        } else if ((rc = cascade_setup_level(h, l, c->kind, c->nu, o->prescale, !o->no_reuse, c->lam[l], s, &peak)) !=
+                   CS_OK) {
             goto fail;
+        }
+        (void)N;
     }
     if (c->lowp) {
         c->lo.resize(h->nlev);
@@ -433,8 +453,8 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
             if ((rc = dalloc_t(&lo.A, (size_t)L.nst * N, &c->bytes, s)) != CS_OK) goto fail;
             if ((rc = launch_copy_d2f((int64_t)L.nst * N, L.A, lo.A, s)) != CS_OK) goto fail;
             if (l < c->nlev) {
-                if ((rc = dalloc_t(&lo.lam, (size_t)c->nu * N, &c->bytes, s)) != CS_OK) goto fail;
-                if ((rc = launch_copy_d2f((int64_t)c->nu * N, c->lam[l], lo.lam, s)) != CS_OK) goto fail;
+                if ((rc = dalloc_t(&lo.lam, (size_t)c->nu * lam_step(L), &c->bytes, s)) != CS_OK) goto fail;
+                if ((rc = launch_copy_d2f((int64_t)c->nu * lam_step(L), c->lam[l], lo.lam, s)) != CS_OK) goto fail;
             }
             if ((rc = dalloc_t(&lo.b, N, &c->bytes, s)) != CS_OK) goto fail;
             if ((rc = dalloc_t(&lo.x, N, &c->bytes, s)) != CS_OK) goto fail;
@@ -509,16 +529,50 @@ cs_status cs_sweep(const cs_hierarchy *h, cs_cascade *c, int level, int step, in
         return CS_ERR_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t N = L.g.N;
+    const int64_t st = (int64_t)step * lam_step(L);
     if (precision == CS_FP32) {
         if (!c->lowp) { set_error("FP32 steps need lowp"); return CS_ERR_ARG; }
         const LowLevel &lo = c->lo[level];
-        return launch_sweep<float>(L, lo.A, lo.lam + (int64_t)step * N, (const float *)b, (const float *)x,
-                                   (float *)out, colour, false, s);
+        if (L.bs > 1)
+            return launch_block_sweep<float>(L, lo.A, lo.lam + st, (const float *)b, (const float *)x, (float *)out,
+                                             colour, false, false, s);
+        return launch_sweep<float>(L, lo.A, lo.lam + st, (const float *)b, (const float *)x, (float *)out, colour,
+                                   false, s);
     }
     if (precision != CS_FP64) { set_error("bad precision"); return CS_ERR_ARG; }
-    return launch_sweep<double>(L, L.A, c->lam[level] + (int64_t)step * N, (const double *)b, (const double *)x,
-                                (double *)out, colour, false, s);
+    if (L.bs > 1)
+        return launch_block_sweep<double>(L, L.A, c->lam[level] + st, (const double *)b, (const double *)x,
+                                          (double *)out, colour, false, false, s);
+    return launch_sweep<double>(L, L.A, c->lam[level] + st, (const double *)b, (const double *)x, (double *)out,
+                                colour, false, s);
+}
+
+cs_status cs_sweep_rhs(const cs_hierarchy *h, cs_cascade *c, int level, int step, int colour, int transpose,
+                       int precision, int nrhs, const void *b, const void *x, void *out, cs_stream stream) {
+    if (!h || !c || !b || !x || !out) { set_error("null argument"); return CS_ERR_ARG; }
+    if (level < 0 || level >= c->nlev) { set_error("level %d has no smoother", level); return CS_ERR_ARG; }
+    if (step < 0 || step >= c->nu) { set_error("step out of range"); return CS_ERR_ARG; }
+    if (nrhs < 1 || nrhs > 32) { set_error("nrhs must be in 1..32"); return CS_ERR_ARG; }
+    if (colour < -1 || colour > 1 || (colour >= 0 && c->ncol != 2) || (colour < 0 && c->ncol != 1)) {
+        set_error("colour does not match the cascade kind");
+        return CS_ERR_ARG;
+    }
+    const Level &L = h->lev[level];
+    if (out == x && !(colour >= 0 && L.kind == STAR)) {
+        set_error("out may alias x only for a colour step on a 5/7-point level");
+        return CS_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t st = (int64_t)step * lam_step(L);
+    if (precision == CS_FP32) {
+        if (!c->lowp) { set_error("FP32 steps need lowp"); return CS_ERR_ARG; }
+        const LowLevel &lo = c->lo[level];
+        return launch_block_sweep_m<float>(L, lo.A, lo.lam + st, (const float *)b, (const float *)x, (float *)out,
+                                           nrhs, colour, transpose != 0, s);
+    }
+    if (precision != CS_FP64) { set_error("bad precision"); return CS_ERR_ARG; }
+    return launch_block_sweep_m<double>(L, L.A, c->lam[level] + st, (const double *)b, (const double *)x,
+                                        (double *)out, nrhs, colour, transpose != 0, s);
 }
 
 int64_t cs_kernel_launches(void) { return g_launches.load(); }
@@ -770,6 +824,17 @@ cs_status cs_query_level(const cs_hierarchy *h, int level, cs_level_info *info) 
     for (int s = 0; s < 27; ++s)
         for (int d = 0; d < 3; ++d) info->off[s][d] = s < L.nst ? L.off[s][d] : 0;
     info->nlevels = h->nlev;
+    info->block = L.bs;
+    int64_t ls = 0;
+    if (L.bs == 1) ls = L.g.N;
+    else
+        for (int64_t b = 0; b < L.nblocks; ++b) {
+            const int bx = (int)(b % L.nbx), by = (int)((b / L.nbx) % L.nby), bz = (int)(b / ((int64_t)L.nbx * L.nby));
+            const int64_t ex = std::min(L.bs, L.g.nx - L.bs * bx), ey = std::min(L.bs, L.g.ny - L.bs * by);
+            const int64_t ez = L.g.dim == 3 ? std::min(L.bs, L.g.nz - L.bs * bz) : 1;
+            ls += (ex * ey * ez) * (ex * ey * ez);
+        }
+    info->lamsize = ls;
     return CS_OK;
 }
 
@@ -798,7 +863,29 @@ cs_status cs_export_lambda(const cs_cascade *c, int level, double *host) {
     if (!c || !host) { set_error("null argument"); return CS_ERR_ARG; }
     if (level < 0 || level >= c->nlev) { set_error("bad level"); return CS_ERR_ARG; }
     CSX_CUDA(cudaDeviceSynchronize());
-    CSX_CUDA(cudaMemcpy(host, c->lam[level], sizeof(double) * c->nu * c->h->lev[level].g.N, cudaMemcpyDeviceToHost));
+    const Level &L = c->h->lev[level];
+    if (L.bs == 1) {
+        CSX_CUDA(cudaMemcpy(host, c->lam[level], sizeof(double) * c->nu * L.g.N, cudaMemcpyDeviceToHost));
+        return CS_OK;
+    }
+    // blocks: n_b x n_b per block over its nodes in ascending index order
+    const int64_t stride = lam_step(L);
+    std::vector<double> full((size_t)c->nu * stride);
+    CSX_CUDA(cudaMemcpy(full.data(), c->lam[level], sizeof(double) * full.size(), cudaMemcpyDeviceToHost));
+    int64_t k = 0;
+    for (int st = 0; st < c->nu; ++st)
+        for (int64_t b = 0; b < L.nblocks; ++b) {
+            const int bx = (int)(b % L.nbx), by = (int)((b / L.nbx) % L.nby), bz = (int)(b / ((int64_t)L.nbx * L.nby));
+            int lp[27], np = 0;
+            for (int q = 0; q < L.nmax; ++q) {
+                const int lx = q % L.bs, ly = (q / L.bs) % L.bs, lz = L.g.dim == 3 ? q / (L.bs * L.bs) : 0;
+                if (L.bs * bx + lx < L.g.nx && L.bs * by + ly < L.g.ny && (L.g.dim == 2 || L.bs * bz + lz < L.g.nz))
+                    lp[np++] = q;
+            }
+            const double *src = full.data() + st * stride + b * L.nmax * L.nmax;
+            for (int p = 0; p < np; ++p)
+                for (int q = 0; q < np; ++q) host[k++] = src[lp[p] * L.nmax + lp[q]];
+        }
     return CS_OK;
 }
 

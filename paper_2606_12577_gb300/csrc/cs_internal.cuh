@@ -40,6 +40,12 @@ struct Level {
     // (bitwise) to the grid-centre row; NO_MARGIN: no such region is used
     int margin = NO_MARGIN;
     static constexpr int NO_MARGIN = 1 << 30;
+    // block partition: blocks of bs^dim nodes (partial at the upper edges),
+    // block (bx,by,bz) = nodes bs*b .. bs*b+bs-1 per axis; nmax = bs^dim.
+    // Lambda of a block level is stored [nu][nblocks][nmax][nmax] over the
+    // local positions lp = lx + bs (ly + bs lz); absent positions are zero.
+    int bs = 1, nbx = 0, nby = 0, nbz = 0, nmax = 1;
+    int64_t nblocks = 0;
 };
 
 struct LowLevel {   // FP32 state of one level (owned by a cascade)
@@ -169,5 +175,16 @@ cs_status level_margin(Level &L, bool periodic, cudaStream_t s);
 cs_status coarse_factor(cs_hierarchy *h, cudaStream_t s);
 cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, double *lam,
                               cudaStream_t s, int64_t *peak_bytes);
+cs_status cascade_setup_level_blocks(const cs_hierarchy *h, int l, int kind, int nu, int prescale, double *lam,
+                                     cudaStream_t s);
+// block cascade step (bs > 1): out_b = x_b - Lambda_b^(T) (A x - b)_b over all
+// blocks or the blocks of one colour
+template <typename T>
+cs_status launch_block_sweep(const Level &L, const T *A, const T *lam, const T *b, const T *x, T *out, int colour,
+                             bool transpose, bool x_is_zero, cudaStream_t s);
+// the same with m right-hand sides, vectors RHS-contiguous (X[i*m + r], m <= 32)
+template <typename T>
+cs_status launch_block_sweep_m(const Level &L, const T *A, const T *lam, const T *b, const T *x, T *out, int m,
+                               int colour, bool transpose, cudaStream_t s);
 
 }  // namespace csx

@@ -885,4 +885,404 @@ cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, in
     return setup_level_t<3, BOX>(h, l, kind, nu, prescale, reuse, lam, s, peak);
 }
 
+
+// ------------------------------------------------------ block cascade setup
+// Blocks of bs^dim nodes (Algorithm 2 with n_b > 1).  E rows keep their
+// column offsets relative to their own node.  For block b with nodes p at
+// local displacement delta_p from the block anchor, the entry of row p at
+// column node_p + o sits at offset o, so with Delta_pq = delta_p - delta_q
+//   G_pq = sum_o R_p[o] R_q[o + Delta_pq],   C_pq = sum_o E_p[o] R_q[o + Delta_pq],
+//   Lam~_b = C G^{-1} (normal equations; minimum-norm C G^+ if a Cholesky
+//   pivot <= 1e-14 tr G),  E'_p[o] = E_p[o] - sum_q Lam~_pq R_q[o + Delta_pq].
+// R lives on O_R = O_cur + S; the update spreads each row over the block, so
+// O_next = O_R + D with D the displacements {-(bs-1)..bs-1}^dim.
+
+// R rows of the nodes of active blocks (one thread per node)
+template <int DIM, int KIND>
+__global__ void __launch_bounds__(TBX *TBY) k_block_R(Grid g, int periodic, const double *__restrict__ At,
+                                                       const double *__restrict__ Ecur, double *__restrict__ Rbuf,
+                                                       int nR, const int *__restrict__ pstart,
+                                                       const unsigned *__restrict__ pairs, int bs, int colour) {
+    using S = StenS<DIM, KIND>;
+    constexpr int NST = S::NST;
+    constexpr int NT = TBX * TBY;
+    extern __shared__ double sm_blk[];
+    double *sa = sm_blk;
+    int *snb = reinterpret_cast<int *>(sm_blk + NST * NT);
+    const int tid = threadIdx.x + TBX * threadIdx.y;
+    const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
+    if (ix >= g.nx || iy >= g.ny) return;
+    if (colour >= 0) {
+        const int bc = ((ix / bs + 1) + (iy / bs + 1) + (DIM == 3 ? iz / bs + 1 : 0)) & 1;
+        if (bc != colour) return;
+    }
+    const int64_t N = g.N;
+    const int i = ix + g.nx * (iy + g.ny * iz);
+#pragma unroll
+    for (int s = 0; s < NST; ++s) {
+        int dx, dy, dz;
+        S::off(s, dx, dy, dz);
+        int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+        bool in;
+        if (periodic) {
+            jx = (jx + g.nx) % g.nx; jy = (jy + g.ny) % g.ny; jz = DIM == 3 ? (jz + g.nz) % g.nz : 0;
+            in = true;
+        } else {
+            in = jx >= 0 && jx < g.nx && jy >= 0 && jy < g.ny && (DIM == 2 || (jz >= 0 && jz < g.nz));
+        }
+        snb[s * NT + tid] = in ? jx + g.nx * (jy + g.ny * jz) : i;
+        sa[s * NT + tid] = in ? At[(int64_t)s * N + i] : 0.0;
+    }
+    int p = __ldg(pstart);
+    for (int o = 0; o < nR; ++o) {
+        const int pe = __ldg(pstart + o + 1);
+        double r = 0.0;
+        for (; p < pe; ++p) {
+            const unsigned u = __ldg(pairs + p);
+            const int s = (int)(u >> 24), c = (int)(u & 0xffffffu);
+            r = fma(sa[s * NT + tid], Ecur[(int64_t)c * N + snb[s * NT + tid]], r);
+        }
+        Rbuf[(int64_t)o * N + i] = r;
+    }
+}
+
+// least squares Lam~ = C G^{-1} for an n x n block (n <= NMAX): Cholesky of
+// G with pivot threshold 1e-14 tr(G); otherwise the minimum-norm solution
+// C G^+ from a cyclic Jacobi eigendecomposition of G.
+template <int NMAX>
+__device__ void block_lstsq(const double *G, const double *C, int n, double *Lt) {
+    double tr = 0.0;
+    for (int k = 0; k < n; ++k) tr += G[k * NMAX + k];
+    const double tol = 1e-14 * tr;
+    double L[NMAX * NMAX];
+    bool ok = tr > 0.0;
+    for (int k = 0; k < n * NMAX; ++k) L[k] = G[k];
+    for (int j = 0; j < n && ok; ++j) {
+        double d = L[j * NMAX + j];
+        for (int k = 0; k < j; ++k) d -= L[j * NMAX + k] * L[j * NMAX + k];
+        if (!(d > tol)) { ok = false; break; }
+        d = sqrt(d);
+        L[j * NMAX + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double v = L[i * NMAX + j];
+            for (int k = 0; k < j; ++k) v -= L[i * NMAX + k] * L[j * NMAX + k];
+            L[i * NMAX + j] = v / d;
+        }
+    }
+    if (ok) {
+        for (int p = 0; p < n; ++p) {  // row p of C G^{-1}: solve G y = C_p^T
+            double y[NMAX];
+            for (int i = 0; i < n; ++i) {
+                double v = C[p * NMAX + i];
+                for (int k = 0; k < i; ++k) v -= L[i * NMAX + k] * y[k];
+                y[i] = v / L[i * NMAX + i];
+            }
+            for (int i = n - 1; i >= 0; --i) {
+                double v = y[i];
+                for (int k = i + 1; k < n; ++k) v -= L[k * NMAX + i] * y[k];
+                y[i] = v / L[i * NMAX + i];
+            }
+            for (int i = 0; i < n; ++i) Lt[p * NMAX + i] = y[i];
+        }
+        return;
+    }
+    // eigendecomposition G = Q diag(ev) Q^T by cyclic Jacobi rotations
+    double A[NMAX * NMAX], Q[NMAX * NMAX];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            A[i * NMAX + j] = G[i * NMAX + j];
+            Q[i * NMAX + j] = i == j ? 1.0 : 0.0;
+        }
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) off += A[i * NMAX + j] * A[i * NMAX + j];
+        if (off < 1e-300) break;
+        for (int a = 0; a < n; ++a)
+            for (int b = a + 1; b < n; ++b) {
+                const double apq = A[a * NMAX + b];
+                if (apq == 0.0) continue;
+                const double th = (A[b * NMAX + b] - A[a * NMAX + a]) / (2.0 * apq);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < n; ++k) {
+                    const double x0 = A[k * NMAX + a], x1 = A[k * NMAX + b];
+                    A[k * NMAX + a] = cs * x0 - sn * x1;
+                    A[k * NMAX + b] = sn * x0 + cs * x1;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double x0 = A[a * NMAX + k], x1 = A[b * NMAX + k];
+                    A[a * NMAX + k] = cs * x0 - sn * x1;
+                    A[b * NMAX + k] = sn * x0 + cs * x1;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double x0 = Q[k * NMAX + a], x1 = Q[k * NMAX + b];
+                    Q[k * NMAX + a] = cs * x0 - sn * x1;
+                    Q[k * NMAX + b] = sn * x0 + cs * x1;
+                }
+            }
+    }
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q) {
+            double v = 0.0;
+            for (int k = 0; k < n; ++k) {
+                const double ev = A[k * NMAX + k];
+                if (!(ev > tol)) continue;
+                double cq = 0.0;
+                for (int m = 0; m < n; ++m) cq += C[p * NMAX + m] * Q[m * NMAX + k];
+                v += cq * Q[q * NMAX + k] / ev;
+            }
+            Lt[p * NMAX + q] = v;
+        }
+}
+
+// One block per thread: Gram and cross products, the block least squares,
+// the unscaled Lambda_b, and (unless LAST) the new E rows.
+template <int DIM, int NMAX, bool LAST>
+__global__ void k_block_solve(Grid g, int bs, int nbx, int nby, int64_t nblocks, const double *__restrict__ w,
+                              const double *__restrict__ Ecur, const double *__restrict__ Rbuf,
+                              double *__restrict__ Enxt, int nR, int nN, const int *__restrict__ curR,
+                              const int *__restrict__ shiftR, const int *__restrict__ curN,
+                              const int *__restrict__ shiftN, int colour, double *__restrict__ lam) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((int64_t)nbx * nby));
+    const int64_t N = g.N;
+    const int side = 2 * bs - 1;
+    int node[NMAX], lpos[NMAX], dl[NMAX][3];
+    int np = 0;
+    for (int lp = 0; lp < NMAX; ++lp) {
+        const int lx = lp % bs, ly = (lp / bs) % bs, lz = DIM == 3 ? lp / (bs * bs) : 0;
+        const int ix = bs * bx + lx, iy = bs * by + ly, iz = DIM == 3 ? bs * bz + lz : 0;
+        if (ix >= g.nx || iy >= g.ny || (DIM == 3 && iz >= g.nz)) continue;
+        node[np] = ix + g.nx * (iy + g.ny * iz);
+        lpos[np] = lp;
+        dl[np][0] = lx; dl[np][1] = ly; dl[np][2] = lz;
+        ++np;
+    }
+    const int bc = ((bx + 1) + (by + 1) + (DIM == 3 ? bz + 1 : 0)) & 1;
+    if (colour >= 0 && bc != colour) {  // carried over unchanged
+        if (!LAST)
+            for (int k = 0; k < np; ++k)
+                for (int o = 0; o < nN; ++o) {
+                    const int c = __ldg(curN + o);
+                    Enxt[(int64_t)o * N + node[k]] = c >= 0 ? Ecur[(int64_t)c * N + node[k]] : 0.0;
+                }
+        return;
+    }
+    auto sidx = [&](int p, int q) {
+        const int ex = dl[p][0] - dl[q][0] + bs - 1, ey = dl[p][1] - dl[q][1] + bs - 1;
+        const int ez = DIM == 3 ? dl[p][2] - dl[q][2] + bs - 1 : 0;
+        return ex + side * (ey + side * ez);
+    };
+    double G[NMAX * NMAX], C[NMAX * NMAX], Lt[NMAX * NMAX];
+    for (int p = 0; p < np; ++p)
+        for (int q = 0; q < np; ++q) {
+            const int *sh = shiftR + (int64_t)sidx(p, q) * nR;
+            double gg = 0.0, cc = 0.0;
+            for (int o = 0; o < nR; ++o) {
+                const int t = __ldg(sh + o);
+                if (t < 0) continue;
+                const double rq = Rbuf[(int64_t)t * N + node[q]];
+                if (q >= p) gg = fma(Rbuf[(int64_t)o * N + node[p]], rq, gg);
+                const int c0 = __ldg(curR + o);
+                if (c0 >= 0) cc = fma(Ecur[(int64_t)c0 * N + node[p]], rq, cc);
+            }
+            if (q >= p) G[p * NMAX + q] = gg;
+            C[p * NMAX + q] = cc;
+        }
+    for (int p = 0; p < np; ++p)
+        for (int q = 0; q < p; ++q) G[p * NMAX + q] = G[q * NMAX + p];
+    block_lstsq<NMAX>(G, C, np, Lt);
+    double *lb = lam + b * (NMAX * NMAX);
+    for (int p = 0; p < np; ++p)
+        for (int q = 0; q < np; ++q) lb[lpos[p] * NMAX + lpos[q]] = w[node[p]] * Lt[p * NMAX + q] * w[node[q]];
+    if (!LAST)
+        for (int p = 0; p < np; ++p)
+            for (int o = 0; o < nN; ++o) {
+                const int c0 = __ldg(curN + o);
+                double v = c0 >= 0 ? Ecur[(int64_t)c0 * N + node[p]] : 0.0;
+                for (int q = 0; q < np; ++q) {
+                    const int t = __ldg(shiftN + (int64_t)sidx(p, q) * nN + o);
+                    if (t >= 0) v = fma(-Lt[p * NMAX + q], Rbuf[(int64_t)t * N + node[q]], v);
+                }
+                Enxt[(int64_t)o * N + node[p]] = v;
+            }
+}
+
+template <int DIM, int KIND>
+static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, int prescale, double *lam,
+                                cudaStream_t s) {
+    using S = StenS<DIM, KIND>;
+    constexpr int NST = S::NST;
+    const Level &L = h->lev[l];
+    const Grid g = L.g;
+    const int64_t N = g.N;
+    const int bs = L.bs, ncol = kind == CS_MULTIPLICATIVE ? 2 : 1;
+    const int nmax = L.nmax;
+    dim3 gr = node_grid(g), bl = node_block();
+    double *w = nullptr, *At = nullptr, *Ecur = nullptr, *Enxt = nullptr, *Rbuf = nullptr;
+    int *bad = nullptr, *pstart = nullptr, *curR = nullptr, *shiftR = nullptr, *curN = nullptr, *shiftN = nullptr;
+    unsigned *pairs = nullptr;
+    cs_status rc = CS_OK;
+    int badh = 0;
+    std::vector<Off3> Ocur{{0, 0, 0}};
+    std::vector<Off3> D;
+    const size_t smem = (size_t)NST * TBX * TBY * (sizeof(double) + sizeof(int));
+    for (int dz = (DIM == 3 ? -(bs - 1) : 0); dz <= (DIM == 3 ? bs - 1 : 0); ++dz)
+        for (int dy = -(bs - 1); dy <= bs - 1; ++dy)
+            for (int dx = -(bs - 1); dx <= bs - 1; ++dx) D.push_back({dx, dy, dz});  // lexicographic = sidx order
+
+    if ((rc = dalloc_t(&w, N, nullptr, s)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&At, (size_t)NST * N, nullptr, s)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&bad, 1, nullptr, s)) != CS_OK) goto done;
+    if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess ||
+        cudaMemsetAsync(lam, 0, sizeof(double) * (size_t)nu * L.nblocks * nmax * nmax, s) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__);
+        goto done;
+    }
+    k_prescale<DIM, KIND><<<gr, bl, 0, s>>>(g, h->periodic, prescale, L.A, w, At, bad);
+    count_launch();
+    if (cudaMemcpyAsync(&badh, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "prescale", __FILE__, __LINE__);
+        goto done;
+    }
+    if (badh) {
+        set_error("level %d: non-positive diagonal entry; elliptic prescaling needs A_ii > 0", l);
+        rc = CS_ERR_ARG;
+        goto done;
+    }
+    k_scale_op<DIM, KIND><<<gr, bl, 0, s>>>(g, h->periodic, L.A, w, At);
+    count_launch();
+    if ((rc = dalloc_t(&Ecur, N, nullptr, s)) != CS_OK) goto done;
+    k_fill<<<1216, 256, 0, s>>>(N, Ecur, 1.0);
+    count_launch();
+    {
+        static bool attr = false;
+        if (!attr) {
+            CSX_CUDA(cudaFuncSetAttribute(k_block_R<DIM, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr = true;
+        }
+    }
+    for (int lev = 0; lev < nu; ++lev) {
+        for (int k = 0; k < ncol; ++k) {
+            const bool last = lev == nu - 1 && k == ncol - 1;
+            std::vector<Off3> OR, ON;
+            for (const Off3 &o : Ocur)
+                for (int t = 0; t < NST; ++t) {
+                    int dx, dy, dz;
+                    S::off(t, dx, dy, dz);
+                    OR.push_back({o.x + dx, o.y + dy, o.z + dz});
+                }
+            std::sort(OR.begin(), OR.end());
+            OR.erase(std::unique(OR.begin(), OR.end()), OR.end());
+            for (const Off3 &o : OR)
+                for (const Off3 &d : D) ON.push_back({o.x + d.x, o.y + d.y, o.z + d.z});
+            std::sort(ON.begin(), ON.end());
+            ON.erase(std::unique(ON.begin(), ON.end()), ON.end());
+            if (h->periodic) {
+                int rx = 0, ry = 0, rz = 0;
+                for (const Off3 &o : ON) { rx = std::max(rx, std::abs(o.x)); ry = std::max(ry, std::abs(o.y)); rz = std::max(rz, std::abs(o.z)); }
+                if (2 * rx >= g.nx || 2 * ry >= g.ny || (DIM == 3 && 2 * rz >= g.nz)) {
+                    set_error("periodic grid too small for the fill-in of this cascade (side must exceed twice the fill radius)");
+                    rc = CS_ERR_UNSUPPORTED;
+                    goto done;
+                }
+            }
+            std::map<Off3, int> icur, iR;
+            for (size_t t = 0; t < Ocur.size(); ++t) icur[Ocur[t]] = (int)t;
+            for (size_t t = 0; t < OR.size(); ++t) iR[OR[t]] = (int)t;
+            const int nR = (int)OR.size(), nN = (int)ON.size();
+            std::vector<int> hps(nR + 1, 0), hcurR(nR), hshR((size_t)D.size() * nR), hcurN(nN), hshN((size_t)D.size() * nN);
+            std::vector<unsigned> hpairs;
+            for (int o = 0; o < nR; ++o) {
+                auto it = icur.find(OR[o]);
+                hcurR[o] = it == icur.end() ? -1 : it->second;
+                for (int t = 0; t < NST; ++t) {
+                    int dx, dy, dz;
+                    S::off(t, dx, dy, dz);
+                    auto jt = icur.find({OR[o].x - dx, OR[o].y - dy, OR[o].z - dz});
+                    if (jt != icur.end()) hpairs.push_back(((unsigned)t << 24) | (unsigned)jt->second);
+                }
+                hps[o + 1] = (int)hpairs.size();
+                for (size_t d = 0; d < D.size(); ++d) {
+                    auto jt = iR.find({OR[o].x + D[d].x, OR[o].y + D[d].y, OR[o].z + D[d].z});
+                    hshR[d * nR + o] = jt == iR.end() ? -1 : jt->second;
+                }
+            }
+            for (int o = 0; o < nN; ++o) {
+                auto it = icur.find(ON[o]);
+                hcurN[o] = it == icur.end() ? -1 : it->second;
+                for (size_t d = 0; d < D.size(); ++d) {
+                    auto jt = iR.find({ON[o].x + D[d].x, ON[o].y + D[d].y, ON[o].z + D[d].z});
+                    hshN[d * nN + o] = jt == iR.end() ? -1 : jt->second;
+                }
+            }
+            dfree(pstart, s); dfree(pairs, s); dfree(curR, s); dfree(shiftR, s); dfree(curN, s); dfree(shiftN, s);
+            pstart = nullptr; pairs = nullptr; curR = nullptr; shiftR = nullptr; curN = nullptr; shiftN = nullptr;
+            if ((rc = dalloc_t(&pstart, hps.size(), nullptr, s)) != CS_OK) goto done;
+            if ((rc = dalloc_t(&pairs, std::max<size_t>(1, hpairs.size()), nullptr, s)) != CS_OK) goto done;
+            if ((rc = dalloc_t(&curR, hcurR.size(), nullptr, s)) != CS_OK) goto done;
+            if ((rc = dalloc_t(&shiftR, hshR.size(), nullptr, s)) != CS_OK) goto done;
+            if ((rc = dalloc_t(&curN, hcurN.size(), nullptr, s)) != CS_OK) goto done;
+            if ((rc = dalloc_t(&shiftN, hshN.size(), nullptr, s)) != CS_OK) goto done;
+            if (cudaMemcpyAsync(pstart, hps.data(), hps.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(pairs, hpairs.data(), hpairs.size() * sizeof(unsigned), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(curR, hcurR.data(), hcurR.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(shiftR, hshR.data(), hshR.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(curN, hcurN.data(), hcurN.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(shiftN, hshN.data(), hshN.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+                rc = cuda_fail(cudaGetLastError(), "copy block setup tables", __FILE__, __LINE__);
+                goto done;
+            }
+            if ((rc = dalloc_t(&Rbuf, (size_t)nR * N, nullptr, s)) != CS_OK) goto done;
+            if (!last && (rc = dalloc_t(&Enxt, (size_t)nN * N, nullptr, s)) != CS_OK) goto done;
+            {
+                const int colour = ncol == 2 ? k : -1;
+                k_block_R<DIM, KIND><<<gr, bl, smem, s>>>(g, h->periodic, At, Ecur, Rbuf, nR, pstart, pairs, bs, colour);
+                count_launch();
+                const int threads = 128;
+                const unsigned nblk = (unsigned)((L.nblocks + threads - 1) / threads);
+                double *lam_l = lam + (int64_t)lev * L.nblocks * nmax * nmax;
+#define CSX_BLOCK_SOLVE(NM)                                                                                        \
+    if (last)                                                                                                      \
+        k_block_solve<DIM, NM, true><<<nblk, threads, 0, s>>>(g, bs, L.nbx, L.nby, L.nblocks, w, Ecur, Rbuf, Enxt, \
+                                                              nR, nN, curR, shiftR, curN, shiftN, colour, lam_l);  \
+    else                                                                                                           \
+        k_block_solve<DIM, NM, false><<<nblk, threads, 0, s>>>(g, bs, L.nbx, L.nby, L.nblocks, w, Ecur, Rbuf, Enxt, \
+                                                               nR, nN, curR, shiftR, curN, shiftN, colour, lam_l);
+                if (nmax <= 4) { CSX_BLOCK_SOLVE(4) }
+                else if (nmax <= 8) { CSX_BLOCK_SOLVE(8) }
+                else if (nmax <= 9) { CSX_BLOCK_SOLVE(9) }
+                else { set_error("blocks of more than 9 nodes are not supported"); rc = CS_ERR_UNSUPPORTED; goto done; }
+#undef CSX_BLOCK_SOLVE
+                count_launch();
+            }
+            if (cudaGetLastError() != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "block setup", __FILE__, __LINE__); goto done; }
+            dfree(Ecur, s);
+            dfree(Rbuf, s);
+            Rbuf = nullptr;
+            Ecur = Enxt;
+            Enxt = nullptr;
+            Ocur.swap(ON);
+        }
+    }
+done:
+    dfree(w, s); dfree(At, s); dfree(Ecur, s); dfree(Enxt, s); dfree(Rbuf, s); dfree(bad, s); dfree(pstart, s);
+    dfree(pairs, s); dfree(curR, s); dfree(shiftR, s); dfree(curN, s); dfree(shiftN, s);
+    return rc;
+}
+
+cs_status cascade_setup_level_blocks(const cs_hierarchy *h, int l, int kind, int nu, int prescale, double *lam,
+                                     cudaStream_t s) {
+    const Level &L = h->lev[l];
+    if (L.g.dim == 2) {
+        if (L.kind == STAR) return setup_blocks_t<2, STAR>(h, l, kind, nu, prescale, lam, s);
+        return setup_blocks_t<2, BOX>(h, l, kind, nu, prescale, lam, s);
+    }
+    if (L.kind == STAR) return setup_blocks_t<3, STAR>(h, l, kind, nu, prescale, lam, s);
+    return setup_blocks_t<3, BOX>(h, l, kind, nu, prescale, lam, s);
+}
+
 }  // namespace csx

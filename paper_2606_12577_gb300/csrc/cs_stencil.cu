@@ -119,6 +119,168 @@ template cs_status launch_sweep<double>(const Level &, const double *, const dou
 template cs_status launch_sweep<float>(const Level &, const float *, const float *, const float *, const float *,
                                        float *, int, bool, cudaStream_t);
 
+// ------------------------------------------------------------ block steps
+// Nodes of block (bx,by,bz): bs*b + l per axis, local position
+// lp = lx + bs (ly + bs lz); partial blocks at the upper edges skip absent
+// positions.  Lambda_b is nmax x nmax over local positions.
+template <int DIM, int NMAX>
+__device__ __forceinline__ int block_nodes(const Grid &g, int bs, int bx, int by, int bz, int *node, int *lpos,
+                                           int (*co)[3]) {
+    int np = 0;
+    for (int lp = 0; lp < NMAX; ++lp) {
+        const int lx = lp % bs, ly = (lp / bs) % bs, lz = DIM == 3 ? lp / (bs * bs) : 0;
+        if (DIM == 2 && lp >= bs * bs) break;
+        const int ix = bs * bx + lx, iy = bs * by + ly, iz = DIM == 3 ? bs * bz + lz : 0;
+        if (ix >= g.nx || iy >= g.ny || (DIM == 3 && iz >= g.nz)) continue;
+        node[np] = ix + g.nx * (iy + g.ny * iz);
+        lpos[np] = lp;
+        co[np][0] = ix; co[np][1] = iy; co[np][2] = iz;
+        ++np;
+    }
+    return np;
+}
+
+// out_b = x_b - Lambda_b^(T) ((A x)_b - b_b), one thread per block
+template <int DIM, int KIND, typename T, int NMAX, bool COLOURED>
+__global__ void k_block_sweep(Grid g, int bs, int nbx, int nby, int64_t nblocks, const T *__restrict__ A,
+                              const T *__restrict__ lam, const T *__restrict__ b, const T *x, T *out, int colour,
+                              int transpose, int xzero) {
+    const int64_t blk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (blk >= nblocks) return;
+    const int bx = (int)(blk % nbx), by = (int)((blk / nbx) % nby), bz = (int)(blk / ((int64_t)nbx * nby));
+    int node[NMAX], lpos[NMAX], co[NMAX][3];
+    const int np = block_nodes<DIM, NMAX>(g, bs, bx, by, bz, node, lpos, co);
+    if (COLOURED && ((((bx + 1) + (by + 1) + (DIM == 3 ? bz + 1 : 0)) & 1) != colour)) {
+        for (int p = 0; p < np; ++p) {
+            if (xzero) out[node[p]] = T(0);
+            else if (out != x) out[node[p]] = x[node[p]];
+        }
+        return;
+    }
+    T r[NMAX];
+    for (int p = 0; p < np; ++p)
+        r[p] = (xzero ? T(0) : apply_row<DIM, KIND, T>(g, A, x, co[p][0], co[p][1], co[p][2], node[p])) - b[node[p]];
+    const T *lb = lam + blk * (NMAX * NMAX);
+    T xo[NMAX];
+    for (int p = 0; p < np; ++p) {
+        T acc = xzero ? T(0) : x[node[p]];
+        for (int q = 0; q < np; ++q)
+            acc = fma(-(transpose ? lb[lpos[q] * NMAX + lpos[p]] : lb[lpos[p] * NMAX + lpos[q]]), r[q], acc);
+        xo[p] = acc;
+    }
+    for (int p = 0; p < np; ++p) out[node[p]] = xo[p];
+}
+
+template <typename T>
+cs_status launch_block_sweep(const Level &L, const T *A, const T *lam, const T *b, const T *x, T *out, int colour,
+                             bool transpose, bool xzero, cudaStream_t s) {
+    const int threads = 128;
+    const unsigned nblk = (unsigned)((L.nblocks + threads - 1) / threads);
+    const int tr = transpose ? 1 : 0, xz = xzero ? 1 : 0;
+#define CSX_BSW(DIM, KIND, NM)                                                                                   \
+    if (colour < 0)                                                                                              \
+        k_block_sweep<DIM, KIND, T, NM, false><<<nblk, threads, 0, s>>>(L.g, L.bs, L.nbx, L.nby, L.nblocks, A, lam, \
+                                                                         b, x, out, colour, tr, xz);              \
+    else                                                                                                         \
+        k_block_sweep<DIM, KIND, T, NM, true><<<nblk, threads, 0, s>>>(L.g, L.bs, L.nbx, L.nby, L.nblocks, A, lam, \
+                                                                        b, x, out, colour, tr, xz);
+    if (L.g.dim == 2) {
+        if (L.nmax <= 4) { if (L.kind == STAR) { CSX_BSW(2, STAR, 4) } else { CSX_BSW(2, BOX, 4) } }
+        else { if (L.kind == STAR) { CSX_BSW(2, STAR, 9) } else { CSX_BSW(2, BOX, 9) } }
+    } else {
+        if (L.kind == STAR) { CSX_BSW(3, STAR, 8) } else { CSX_BSW(3, BOX, 8) }
+    }
+#undef CSX_BSW
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+template cs_status launch_block_sweep<double>(const Level &, const double *, const double *, const double *,
+                                              const double *, double *, int, bool, bool, cudaStream_t);
+template cs_status launch_block_sweep<float>(const Level &, const float *, const float *, const float *, const float *,
+                                             float *, int, bool, bool, cudaStream_t);
+
+// The multi-RHS block step X_b <- X_b - Lambda_b^(T) (A X - B)_b.  One warp
+// per node of a block (lane r = right-hand side r, so every load of X and B
+// is a contiguous row of m values); the residual rows of a block meet in
+// shared memory and, after one barrier, each warp forms its node's row of the
+// n_b x m block product.  Per RHS and unknown this is nst + n_b FMAs against
+// (nst + n_b + 3 m) words moved: HBM-bound, so plain FMAs, no tensor cores.
+// BPC blocks adjacent in x share a CTA of 32 * NMAX * BPC threads; the grid
+// spans the block grid (x tiles of BPC, y, z), so no index division is needed.
+template <int DIM, int KIND, typename T, int BS, int BPC>
+__global__ void __launch_bounds__(32 * (DIM == 3 ? BS * BS * BS : BS * BS) * BPC)
+    k_block_sweep_m(Grid g, int nbx, const T *__restrict__ A, const T *__restrict__ lam, const T *__restrict__ B,
+                    const T *X, T *out, int m, int colour, int transpose) {
+    using S = Sten<DIM, KIND>;
+    constexpr int NMAX = DIM == 3 ? BS * BS * BS : BS * BS;
+    __shared__ T rsm[BPC][NMAX][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bl = warp / NMAX, lp = warp % NMAX;  // compile-time divisors
+    const int bx = blockIdx.x * BPC + bl, by = blockIdx.y, bz = blockIdx.z;
+    const int lx = lp % BS, ly = (lp / BS) % BS, lz = DIM == 3 ? lp / (BS * BS) : 0;
+    const int ix = BS * bx + lx, iy = BS * by + ly, iz = DIM == 3 ? BS * bz + lz : 0;
+    const bool present = bx < nbx && ix < g.nx && iy < g.ny && (DIM == 2 || iz < g.nz);
+    const bool active = colour < 0 || ((((bx + 1) + (by + 1) + (DIM == 3 ? bz + 1 : 0)) & 1) == colour);
+    const bool work = present && lane < m;
+    const int64_t i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
+    T r = T(0);
+    if (work && active) {
+        T ax = T(0);
+#pragma unroll
+        for (int s = 0; s < S::NST; ++s) {
+            int dx, dy, dz;
+            S::off(s, dx, dy, dz);
+            const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+            const bool in = (unsigned)jx < (unsigned)g.nx && (unsigned)jy < (unsigned)g.ny &&
+                            (DIM == 2 || (unsigned)jz < (unsigned)g.nz);
+            const int64_t j = i + dx + (int64_t)g.nx * (dy + (int64_t)g.ny * dz);
+            ax = fma(A[(int64_t)s * g.N + i], in ? X[j * m + lane] : T(0), ax);
+        }
+        r = ax - B[i * m + lane];
+    }
+    rsm[bl][lp][lane] = r;  // absent nodes contribute zero (their Lambda entries are zero too)
+    __syncthreads();
+    if (!work) return;
+    if (!active) {
+        if (out != X) out[i * m + lane] = X[i * m + lane];
+        return;
+    }
+    const int64_t blk = bx + (int64_t)nbx * (by + (int64_t)gridDim.y * bz);
+    const T *lb = lam + blk * (NMAX * NMAX);
+    T acc = X[i * m + lane];
+#pragma unroll
+    for (int q = 0; q < NMAX; ++q)
+        acc = fma(-(transpose ? lb[q * NMAX + lp] : lb[lp * NMAX + q]), rsm[bl][q][lane], acc);
+    out[i * m + lane] = acc;
+}
+
+template <typename T>
+cs_status launch_block_sweep_m(const Level &L, const T *A, const T *lam, const T *b, const T *x, T *out, int m,
+                               int colour, bool transpose, cudaStream_t s) {
+    const int tr = transpose ? 1 : 0;
+#define CSX_BSM(DIM, KIND, BS, BPC)                                                                              \
+    k_block_sweep_m<DIM, KIND, T, BS, BPC>                                                                       \
+        <<<dim3((unsigned)((L.nbx + BPC - 1) / BPC), (unsigned)L.nby, (unsigned)L.nbz),                          \
+           32 * (DIM == 3 ? BS * BS * BS : BS * BS) * BPC, 0, s>>>(L.g, L.nbx, A, lam, b, x, out, m, colour, tr);
+    if (L.g.dim == 2) {
+        if (L.bs == 1) { if (L.kind == STAR) { CSX_BSM(2, STAR, 1, 8) } else { CSX_BSM(2, BOX, 1, 8) } }
+        else if (L.bs == 2) { if (L.kind == STAR) { CSX_BSM(2, STAR, 2, 2) } else { CSX_BSM(2, BOX, 2, 2) } }
+        else { if (L.kind == STAR) { CSX_BSM(2, STAR, 3, 1) } else { CSX_BSM(2, BOX, 3, 1) } }
+    } else {
+        if (L.bs == 1) { if (L.kind == STAR) { CSX_BSM(3, STAR, 1, 8) } else { CSX_BSM(3, BOX, 1, 8) } }
+        else { if (L.kind == STAR) { CSX_BSM(3, STAR, 2, 1) } else { CSX_BSM(3, BOX, 2, 1) } }
+    }
+#undef CSX_BSM
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+template cs_status launch_block_sweep_m<double>(const Level &, const double *, const double *, const double *,
+                                                const double *, double *, int, int, bool, cudaStream_t);
+template cs_status launch_block_sweep_m<float>(const Level &, const float *, const float *, const float *,
+                                               const float *, float *, int, int, bool, cudaStream_t);
+
 // rc_I = 2^-dim sum_f P_{f,I} (A x - b)_f.  Coarse node I sits on fine node
 // 2I+1 (0-based); its fine neighbours 2I+1+d (d in {-1,0,1}) carry weight
 // 1/2 per nonzero component of d (bilinear / trilinear interpolation).

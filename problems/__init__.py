@@ -222,6 +222,33 @@ def log_uniform_field(dim: int, n: int, corr: float, seed: int, lo: float = -3.0
     return 10.0 ** (lo + (hi - lo) * ndtr(g))
 
 
+def inclusions_2d(n: int, count: int, seed: int, rmin: float = 8.0, rmax: float = 64.0,
+                  lo: float = -4.0, hi: float = 4.0) -> np.ndarray:
+    """Piecewise-constant cell coefficients on ``(n+1)^2`` cells: background 1
+    and ``count`` circular inclusions with centres ~ U(0,1)^2, radii ~
+    U[rmin, rmax] cells and mu = 10^U[lo, hi]; a cell belongs to an inclusion
+    when its centre does, later inclusions overwrite earlier ones (the
+    elliptic interface workload)."""
+    n1 = n + 1
+    h = 1.0 / n1
+    u = uniform01(seed, 4 * count).reshape(count, 4)
+    cx, cy = u[:, 0], u[:, 1]
+    rad = (rmin + (rmax - rmin) * u[:, 2]) * h
+    mu_inc = 10.0 ** (lo + (hi - lo) * u[:, 3])
+    xc = (np.arange(n1) + 0.5) * h
+    X, Y = np.meshgrid(xc, xc, indexing="xy")  # [cy, cx]
+    mu = np.ones((n1, n1))
+    for k in range(count):
+        mu[(X - cx[k]) ** 2 + (Y - cy[k]) ** 2 <= rad[k] ** 2] = mu_inc[k]
+    return mu
+
+
+def interface2d(n: int = 1024, count: int = 200):
+    """2D elliptic interface problem: FV 5-point operator on the inclusion
+    field above (seed of workload 3), Dirichlet."""
+    return variable_poisson(inclusions_2d(n, count, config_seed(3)))
+
+
 def rhs(N: int, seed: int, nrhs: int = 1) -> np.ndarray:
     """Right-hand side with i.i.d. entries ~ U[-1, 1] (Sec. 3.1 footnote).
     Shape ``(N,)`` for one RHS, else ``(N, nrhs)`` (RHS-contiguous)."""

@@ -1,0 +1,145 @@
+"""Block cascades (blocks of bs^dim nodes, Algorithm 2 with n_b > 1) and the
+multi-RHS block product X_b -= Lambda_b R_b, through the C ABI, against the
+FP64 oracle: Lambda to 1e-12 relative, smoothing (forward and reverse, i.e.
+transposed blocks), V-cycles and solves to 1e-12 / the oracle's iteration
+counts.  Sizes leave partial blocks at the upper edges."""
+import numpy as np
+import pytest
+
+import oracle
+import problems
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def _dev(a, dtype=None):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device="cuda")
+
+
+def _host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _var(dim, n, seed, lo=-1.0, hi=1.0):
+    return problems.variable_poisson(problems.random_coefficients(dim, n, seed, lo, hi))
+
+
+PROBS = {
+    "v2d_37": lambda: _var(2, 37, 3),
+    "c2d_66": lambda: problems.variable_poisson(problems.log_uniform_field(2, 66, 6.0, 266, -2.0, 2.0)),
+    "v3d_17": lambda: _var(3, 17, 5),
+    "p2d_33": lambda: problems.poisson(2, 33),
+}
+
+
+@pytest.fixture(scope="module")
+def built():
+    import __graft_entry__ as g
+    g.build()
+    return True
+
+
+@pytest.mark.parametrize("name,bs,kind,nu", [
+    ("v2d_37", 2, "additive", 3), ("v2d_37", 2, "multiplicative", 2), ("v2d_37", 3, "additive", 2),
+    ("v2d_37", 3, "multiplicative", 1), ("c2d_66", 2, "additive", 3), ("v3d_17", 2, "additive", 2),
+    ("v3d_17", 2, "multiplicative", 1), ("p2d_33", 3, "additive", 3)])
+def test_block_lambda_parity(built, name, bs, kind, nu):
+    import paper_2606_12577_gb300 as cmg
+    A = PROBS[name]()
+    ho = oracle.Hierarchy(A, bs=bs)
+    co = oracle.Cascade(ho, kind, nu=nu)
+    hg = gu.gpu_hierarchy(A, block=bs)
+    cg = cmg.setup_cascade(hg, kind, nu=nu)
+    assert hg.nlevels == ho.nlev
+    for l in range(co.nlev):
+        assert cmg.query_level(hg, l)["lamsize"] == co.lamsize(l)
+        assert gu.rel_max(cmg.export_lambda(cg, l), co.lam(l)) <= TOL, f"level {l}"
+
+
+@pytest.mark.parametrize("name,bs,kind", [("v2d_37", 2, "additive"), ("v2d_37", 3, "multiplicative"),
+                                          ("v3d_17", 2, "multiplicative"), ("c2d_66", 2, "additive")])
+def test_block_smooth_and_vcycle(built, name, bs, kind):
+    import paper_2606_12577_gb300 as cmg
+    A = PROBS[name]()
+    ho = oracle.Hierarchy(A, bs=bs)
+    co = oracle.Cascade(ho, kind, nu=2)
+    hg = gu.gpu_hierarchy(A, block=bs)
+    cg = cmg.setup_cascade(hg, kind, nu=2)
+    for l in range(min(2, co.nlev)):
+        N = ho.N(l)
+        b = problems.uniform(100 + l, N)
+        x0 = problems.uniform(200 + l, N)
+        for rev in (False, True):
+            xg = _dev(x0)
+            cmg.smooth(hg, cg, l, _dev(b), xg, reverse=rev)
+            assert gu.rel_max(_host(xg), oracle.smooth(ho, co, l, b, x0, reverse=rev)) <= TOL, f"{l} {rev}"
+    b = problems.rhs(A.N, 7)
+    for order in ("RF", "FF"):
+        xo = oracle.vcycle(ho, co, b, mu_pre=1, mu_post=1, rf=order == "RF")
+        xg = _dev(np.zeros(A.N))
+        cmg.vcycle(hg, cg, _dev(b), xg, mu_pre=1, mu_post=1, order=order)
+        assert gu.rel_max(_host(xg), xo) <= TOL
+
+
+@pytest.mark.parametrize("name,bs,kind,method", [("c2d_66", 2, "additive", "gmres"),
+                                                 ("v3d_17", 2, "multiplicative", "stationary")])
+def test_block_solve(built, name, bs, kind, method):
+    import paper_2606_12577_gb300 as cmg
+    A = PROBS[name]()
+    ho = oracle.Hierarchy(A, bs=bs)
+    co = oracle.Cascade(ho, kind, nu=3)
+    b = problems.rhs(A.N, 9)
+    xo, ito, _, _ = oracle.solve(ho, co, b, method=method, tol=1e-10)
+    assert ito > 0
+    hg = gu.gpu_hierarchy(A, block=bs)
+    cg = cmg.setup_cascade(hg, kind, nu=3, lowp=True)
+    xg = _dev(np.zeros(A.N))
+    info = cmg.solve(hg, cg, _dev(b), xg, method=method, tol=1e-10)
+    assert info.converged and info.iterations == ito
+    assert gu.rel_max(_host(xg), xo) <= 1e-11
+    x32 = _dev(np.zeros(A.N))
+    info32 = cmg.solve(hg, cg, _dev(b), x32, method="refine" if method == "stationary" else method,
+                       precision="fp32", tol=1e-10)
+    assert info32.converged
+    r = b - gu.stencil_matvec(A, _host(x32))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
+
+
+@pytest.mark.parametrize("name,bs,kind,m", [("c2d_66", 2, "additive", 32), ("v2d_37", 3, "additive", 5),
+                                            ("v3d_17", 2, "multiplicative", 32), ("v2d_37", 1, "additive", 7),
+                                            ("v3d_17", 1, "multiplicative", 3)])
+def test_multi_rhs_block_steps(built, name, bs, kind, m):
+    """A full forward and reverse cascade application built from cs_sweep_rhs
+    steps (n_b x m block products) equals the oracle's smoother applied to
+    every right-hand side; FP32 steps agree to FP32 accuracy."""
+    import torch
+
+    import paper_2606_12577_gb300 as cmg
+    A = PROBS[name]()
+    nu = 2
+    ho = oracle.Hierarchy(A, bs=bs)
+    co = oracle.Cascade(ho, kind, nu=nu)
+    hg = gu.gpu_hierarchy(A, block=bs)
+    cg = cmg.setup_cascade(hg, kind, nu=nu, lowp=True)
+    N = A.N
+    B = problems.uniform(31, N * m).reshape(N, m)
+    X0 = problems.uniform(32, N * m).reshape(N, m)
+    ncol = 2 if kind == "multiplicative" else 1
+    for rev in (False, True):
+        for dt, tol in ((torch.float64, TOL), (torch.float32, 2e-5)):
+            bg = _dev(B, dt)
+            cur, oth = _dev(X0, dt), _dev(np.zeros((N, m)), dt)
+            for st in range(nu):
+                lv = nu - 1 - st if rev else st
+                for kk in range(ncol):
+                    col = (ncol - 1 - kk if rev else kk) if ncol == 2 else -1
+                    cmg.sweep_rhs(hg, cg, 0, lv, bg, cur, oth, m, colour=col, transpose=rev)
+                    cur, oth = oth, cur
+            got = _host(cur).astype(np.float64)
+            ref = np.stack([oracle.smooth(ho, co, 0, B[:, r], X0[:, r], reverse=rev) for r in range(m)], axis=1)
+            assert gu.rel_max(got, ref) <= tol, f"reverse={rev} {dt}"
