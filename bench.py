@@ -51,6 +51,9 @@ def args_():
     p.add_argument("--order", default="RF")
     p.add_argument("--cpu-n", type=int, default=64, help="side of the oracle's bounded sample")
     p.add_argument("--no-extras", action="store_true", help="time the chosen form only")
+    p.add_argument("--learned-meshes", type=int, default=64, help="training meshes of the learned setup")
+    p.add_argument("--learned-n", type=int, default=127, help="interior nodes per side of a training mesh")
+    p.add_argument("--learned-steps", type=int, default=2000, help="Adam steps")
     p.add_argument("--profile", default="", choices=["", "setup", "step", "sweep", "multirhs"],
                    help="run one untimed setup (or setup + solve) and exit: the case ncu captures")
     return p.parse_args()
@@ -173,6 +176,53 @@ def config(a):
                         f"setup + solve to 1e-10",
             "global_batch": 1, "unknowns": a.n ** 3, "parallelism": f"replicas x{a.gpus}",
             "l2": "inputs larger than L2 (A alone is 0.94 GB)"}
+
+
+def learned_section(a, cmg, problems, dev):
+    """Learned setup (workload 5): Q1 elements on jittered meshes, log-normal
+    coefficients (sigma 2, correlation 16 elements), 3x3-node blocks,
+    additive nu = 3.  The network is trained on labels of the exact setup of
+    seeded training meshes, then the exact and learned setups of a 511^2
+    evaluation mesh are compared (setup time, GMRES iterations to 1e-10,
+    convergence factor)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2606_12577_gb300 import learned
+    t0 = time.perf_counter()
+    meshes = [problems.q1_jittered(a.learned_n, 50000 + k) for k in range(a.learned_meshes)]
+    t_gen = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X, T = learned.make_dataset(meshes)
+    torch.cuda.synchronize()
+    t_label = time.perf_counter() - t0
+    mdl = cmg.MLP(X.shape[1], 128, T.shape[1], max_batch=8192, seed=1)
+    t0 = time.perf_counter()
+    hist = learned.train(mdl, X, T, steps=a.learned_steps, batch=4096, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    A5 = problems.q1_jittered(511, 10000)
+    learned.setup_pair(A5, mdl)  # warm-up (graph capture, pool)
+    h5, res = learned.setup_pair(A5, mdl)
+    b5 = torch.tensor(problems.rhs(A5.N, 10000), dtype=torch.float64, device=dev)
+    out = {"workload": "Q1 FE, jittered 512^2-element mesh (511^2 unknowns), log-normal kappa (sigma 2, corr 16h), "
+                       "3x3-node blocks (9x9 Lambda), additive nu=3, GMRES V(1,1) RF to 1e-10",
+           "training": {"meshes": a.learned_meshes, "mesh_unknowns": a.learned_n ** 2, "samples": int(X.shape[0]),
+                        "steps": a.learned_steps, "batch": 4096, "loss_first": float(np.mean(hist[:10])),
+                        "loss_last": float(np.mean(hist[-50:])), "generate_s": t_gen, "label_s": t_label,
+                        "train_s": t_train}}
+    used, ratio = cmg.learned_status(res["learned"][0])
+    out["accepted"] = bool(used == 1)
+    out["level1_objective_ratio"] = ratio
+    for name in ("exact", "learned"):
+        c, setup_ms, wall_ms = res[name]
+        x = torch.zeros(A5.N, dtype=torch.float64, device=dev)
+        info = cmg.solve(h5, c, b5, x, method="gmres", tol=1e-10, maxit=300, raise_on_error=False)
+        out[name] = {"setup_ms": setup_ms, "gmres_iterations": info.iterations, "converged": info.converged,
+                     "rho": oracle.rho_from_history(info.history) if len(info.history) > 2 else None}
+    return out
 
 
 # ------------------------------------------------------------------- ours
@@ -378,6 +428,8 @@ def main():
             "launch_ms": t_m * 1e3, "achieved_gbs": bytes_m / t_m / 1e9, "frac_of_peak": bytes_m / t_m / 1e9 / peak,
             "algorithmic_bytes_per_launch": bytes_m, "bound": "hbm"}
         del hb, cb, ci, Xb, Bb
+        torch.cuda.empty_cache()
+        result["learned_setup"] = learned_section(a, cmg, problems, dev)
         torch.cuda.empty_cache()
         # ---- plain FP64 path (stationary V-cycle iteration)
         pinfo = []

@@ -51,6 +51,7 @@ enum {
 typedef void *cs_stream; /* cudaStream_t */
 typedef struct cs_hierarchy cs_hierarchy;
 typedef struct cs_cascade cs_cascade;
+typedef struct cs_mlp cs_mlp;
 
 /* ------------------------------------------------------------- operator */
 /* A structured-grid operator in stencil form (Sec. 2: the block-partitioned
@@ -110,6 +111,12 @@ typedef struct {
                       region are computed once per colour and copied -- the stencil
                       repetition the paper's concluding remarks suggest caching; exact
                       (bitwise the same as computing each row); 1: compute every row */
+    const cs_mlp *model; /* optional learned setup of the finest level (2D, blocks, additive):
+                      Lambda of every block predicted from its operator window (see the
+                      learned-setup section below); NULL: exact setup */
+    double model_tol;    /* accept the prediction when its level-1 Frobenius objective, summed
+                      over the level, is <= (1 + model_tol) x the exact one (default 0.05);
+                      otherwise the exact setup runs (fallback) */
 } cs_cascade_opts;
 
 /* Build the cascade (Lambda_l, l = 1..nu; multiplicative: Lambda_{l,k},
@@ -254,6 +261,42 @@ typedef struct {
  * CS_ERR_DIVERGED, CS_ERR_ARG, CS_ERR_CUDA. */
 cs_status cs_solve(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *opts, const double *b,
                    double *x, cs_solve_info *info, cs_stream stream);
+
+/* ------------------------------------------------------- learned setup */
+/* A small MLP (nin -> nhid -> nhid -> nout, ReLU) that maps a block's operator
+ * window to its prescaled Lambda~_1..nu blocks.  This learned form is not in
+ * the paper; the exact Frobenius setup (Algorithm 2) stays the reference and
+ * the fallback.  Weights are FP32 masters used in BF16 for every product,
+ * with FP32 accumulation; parameters are [W1 (nhid x nin), b1, W2, b2, W3
+ * (nout x nhid), b3], row-major.  max_batch: rows per forward/backward pass
+ * (longer forward calls are chunked).  Weights are He-uniform from seed. */
+cs_status cs_mlp_create(int nin, int nhid, int nout, int max_batch, uint64_t seed, cs_mlp **out);
+void cs_mlp_destroy(cs_mlp *m);
+int64_t cs_mlp_nparam(const cs_mlp *m);
+cs_status cs_mlp_get_params(const cs_mlp *m, float *host_params);
+cs_status cs_mlp_set_params(cs_mlp *m, const float *host_params);
+/* Y[batch x nout] = f(X[batch x nin]); X, Y device FP32, row-major. */
+cs_status cs_mlp_forward(cs_mlp *m, int batch, const float *X, float *Y, cs_stream stream);
+/* Mean-squared-error loss against T[batch x nout] (device) and its gradient
+ * w.r.t. every parameter (host copy if grad_host != NULL); batch <= max_batch.
+ * Synchronises. */
+cs_status cs_mlp_gradients(cs_mlp *m, int batch, const float *X, const float *T, float *grad_host, float *loss,
+                           cs_stream stream);
+/* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) on that loss; *loss
+ * (host, optional; then the call synchronises) receives the loss before the step. */
+cs_status cs_mlp_train_step(cs_mlp *m, int batch, const float *X, const float *T, float lr, float *loss,
+                            cs_stream stream);
+/* Features of every block of a 2D block level into F [nblocks x bs^2 (bs+2)^2]
+ * (device, FP32): for each block node its row of the prescaled operator
+ * W A W over the (bs+2)^2-node window around the block. */
+cs_status cs_block_features(const cs_hierarchy *h, int level, float *F, cs_stream stream);
+/* Training targets from an exact additive cascade: prescaled blocks
+ * W^-1 Lambda_l W^-1, l = 1..nu, into T [nblocks x nu bs^4] (device, FP32). */
+cs_status cs_block_targets(const cs_cascade *c, int level, float *T, cs_stream stream);
+/* After cs_setup_cascade with a model: *used = 1 if the prediction was
+ * accepted, 0 if the exact setup ran instead, -1 without a model; *ratio =
+ * level-1 Frobenius objective of the prediction / exact. */
+cs_status cs_learned_status(const cs_cascade *c, int *used, double *ratio);
 
 /* -------------------------------------------------------------- queries */
 typedef struct {

@@ -20,7 +20,7 @@ from ._capi import CascadeError
 
 __all__ = ["setup_hierarchy", "setup_cascade", "vcycle", "solve", "smooth", "sweep", "sweep_rhs", "residual_restrict",
            "prolong_correct", "coarse_solve", "residual", "query_level", "export_operator", "export_colours",
-           "export_lambda", "kernel_launches", "smooth_noalloc", "Hierarchy", "Cascade", "SolveInfo", "CascadeError"]
+           "export_lambda", "kernel_launches", "smooth_noalloc", "MLP", "block_features", "block_targets", "learned_status", "Hierarchy", "Cascade", "SolveInfo", "CascadeError"]
 
 
 def _torch():
@@ -149,13 +149,122 @@ def setup_hierarchy(dim, n, offsets, coeff, periodic=False, coarse_max=4, max_le
     return Hierarchy(out.value, dim)
 
 
-def setup_cascade(h: Hierarchy, kind="additive", nu=3, prescale=True, alpha=0, lowp=False, reuse=True, stream=None):
+def setup_cascade(h: Hierarchy, kind="additive", nu=3, prescale=True, alpha=0, lowp=False, reuse=True, model=None,
+                  model_tol=0.05, stream=None):
+    """Build the cascade; ``model`` (an ``MLP``) predicts the finest level's
+    Lambda blocks, accepted when its level-1 Frobenius objective is within
+    ``model_tol`` of the exact one (else the exact setup runs)."""
     k = _capi.CS_MULTIPLICATIVE if kind == "multiplicative" else _capi.CS_ADDITIVE
-    opts = _capi.cs_cascade_opts(k, nu, int(prescale), alpha, int(lowp), int(not reuse))
+    opts = _capi.cs_cascade_opts(k, nu, int(prescale), alpha, int(lowp), int(not reuse),
+                                 C.c_void_p(model.ptr if model is not None else None), float(model_tol))
     out = C.c_void_p()
     _capi.check(_capi.lib().cs_setup_cascade(h.ptr, C.byref(opts), _stream(stream), C.byref(out)),
                 "cs_setup_cascade")
-    return Cascade(out.value, h, kind, nu, lowp)
+    c = Cascade(out.value, h, kind, nu, lowp)
+    c.model = model
+    return c
+
+
+def learned_status(c):
+    """(used, ratio): 1 prediction accepted / 0 exact fallback / -1 no model;
+    level-1 Frobenius objective of the prediction over the exact one."""
+    used, ratio = C.c_int(0), C.c_double(0.0)
+    _capi.check(_capi.lib().cs_learned_status(c.ptr, C.byref(used), C.byref(ratio)), "cs_learned_status")
+    return int(used.value), float(ratio.value)
+
+
+class MLP:
+    """The learned-setup network (in -> hid -> hid -> out, ReLU; BF16 weights
+    with FP32 accumulation), trained by the library's own kernels."""
+
+    def __init__(self, nin, nhid, nout, max_batch=32768, seed=0):
+        out = C.c_void_p()
+        _capi.check(_capi.lib().cs_mlp_create(nin, nhid, nout, max_batch, seed, C.byref(out)), "cs_mlp_create")
+        self._p = out.value
+        self.nin, self.nhid, self.nout, self.max_batch = nin, nhid, nout, max_batch
+        self.nparam = int(_capi.lib().cs_mlp_nparam(self._p))
+
+    @property
+    def ptr(self):
+        return self._p
+
+    def __del__(self):
+        if getattr(self, "_p", None) and _capi._lib is not None:
+            _capi._lib.cs_mlp_destroy(self._p)
+            self._p = None
+
+    def get_params(self):
+        out = np.zeros(self.nparam, dtype=np.float32)
+        _capi.check(_capi.lib().cs_mlp_get_params(self._p, out.ctypes.data_as(C.c_void_p)), "cs_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.size != self.nparam:
+            raise ValueError(f"expected {self.nparam} parameters")
+        _capi.check(_capi.lib().cs_mlp_set_params(self._p, p.ctypes.data_as(C.c_void_p)), "cs_mlp_set_params")
+
+    def forward(self, X, Y=None, stream=None):
+        torch = _torch()
+        B = X.shape[0]
+        if Y is None:
+            Y = torch.empty((B, self.nout), dtype=torch.float32, device=X.device)
+        _f32(X, B * self.nin, "X"), _f32(Y, B * self.nout, "Y")
+        _capi.check(_capi.lib().cs_mlp_forward(self._p, B, C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr()),
+                                               _stream(stream)), "cs_mlp_forward")
+        return Y
+
+    def gradients(self, X, T, stream=None):
+        B = X.shape[0]
+        _f32(X, B * self.nin, "X"), _f32(T, B * self.nout, "T")
+        g = np.zeros(self.nparam, dtype=np.float32)
+        loss = C.c_float(0.0)
+        _capi.check(_capi.lib().cs_mlp_gradients(self._p, B, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
+                                                 g.ctypes.data_as(C.c_void_p), C.byref(loss), _stream(stream)),
+                    "cs_mlp_gradients")
+        return float(loss.value), g
+
+    def train_step(self, X, T, lr, stream=None):
+        B = X.shape[0]
+        _f32(X, B * self.nin, "X"), _f32(T, B * self.nout, "T")
+        loss = C.c_float(0.0)
+        _capi.check(_capi.lib().cs_mlp_train_step(self._p, B, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
+                                                  float(lr), C.byref(loss), _stream(stream)), "cs_mlp_train_step")
+        return float(loss.value)
+
+
+def _f32(t, n, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} values, expected {n}")
+
+
+def block_features(h, level=0, stream=None):
+    """Features of every block of a 2D block level: [nblocks, bs^2 (bs+2)^2] (CUDA float32)."""
+    torch = _torch()
+    info = h.level_info(level)
+    bs = info["block"]
+    n = info["n"]
+    nb = (-(-n[0] // bs)) * (-(-n[1] // bs))
+    F = torch.empty((nb, bs * bs * (bs + 2) ** 2), dtype=torch.float32, device="cuda")
+    _capi.check(_capi.lib().cs_block_features(h.ptr, level, C.c_void_p(F.data_ptr()), _stream(stream)),
+                "cs_block_features")
+    return F
+
+
+def block_targets(c, level=0, stream=None):
+    """Prescaled Lambda~ blocks of an exact additive cascade: [nblocks, nu bs^4] (CUDA float32)."""
+    torch = _torch()
+    info = c.hier.level_info(level)
+    bs = info["block"]
+    n = info["n"]
+    nb = (-(-n[0] // bs)) * (-(-n[1] // bs))
+    T = torch.empty((nb, c.nu * bs ** 4), dtype=torch.float32, device="cuda")
+    _capi.check(_capi.lib().cs_block_targets(c.ptr, level, C.c_void_p(T.data_ptr()), _stream(stream)),
+                "cs_block_targets")
+    return T
 
 
 def _cycle_opts(mu_pre, mu_post, order, precision):

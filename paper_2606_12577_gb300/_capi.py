@@ -34,7 +34,7 @@ class cs_hierarchy_opts(C.Structure):
 
 class cs_cascade_opts(C.Structure):
     _fields_ = [("kind", C.c_int), ("nu", C.c_int), ("prescale", C.c_int), ("alpha", C.c_int), ("lowp", C.c_int),
-                ("no_reuse", C.c_int)]
+                ("no_reuse", C.c_int), ("model", C.c_void_p), ("model_tol", C.c_double)]
 
 
 class cs_vcycle_opts(C.Structure):
@@ -87,6 +87,19 @@ _SIGS = {
     "cs_export_lambda": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "cs_hierarchy_bytes": (C.c_int64, [C.c_void_p]),
     "cs_cascade_bytes": (C.c_int64, [C.c_void_p]),
+    "cs_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_void_p)]),
+    "cs_mlp_destroy": (None, [C.c_void_p]),
+    "cs_mlp_nparam": (C.c_int64, [C.c_void_p]),
+    "cs_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "cs_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "cs_mlp_forward": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cs_mlp_gradients": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.POINTER(C.c_float), C.c_void_p]),
+    "cs_mlp_train_step": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_float, C.POINTER(C.c_float),
+                                    C.c_void_p]),
+    "cs_block_features": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "cs_block_targets": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "cs_learned_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "cs_last_error": (C.c_char_p, []),
     "cs_destroy_hierarchy": (None, [C.c_void_p]),
     "cs_destroy_cascade": (None, [C.c_void_p]),

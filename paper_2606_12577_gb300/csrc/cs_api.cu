@@ -436,6 +436,27 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
         const int64_t N = h->lev[l].g.N;
         const Level &L = h->lev[l];
         if ((rc = dalloc_t(&c->lam[l], (size_t)c->nu * lam_step(L), &c->bytes, s)) != CS_OK) goto fail;
+        if (l == 0 && o->model) {
+            if (L.bs < 2 || L.g.dim != 2 || c->kind != CS_ADDITIVE) {
+                set_error("the learned setup needs an additive cascade on a 2D block level");
+                rc = CS_ERR_UNSUPPORTED;
+                goto fail;
+            }
+            // exact level-1 blocks (one least-squares problem per block) judge the prediction
+            double *lam1 = nullptr;
+            if ((rc = dalloc_t(&lam1, (size_t)lam_step(L), nullptr, s)) != CS_OK) goto fail;
+            bool accepted = false;
+            double ratio = 0.0;
+            rc = cascade_setup_level_blocks(h, 0, CS_ADDITIVE, 1, o->prescale, lam1, s);
+            if (rc == CS_OK)
+                rc = learned_setup_level0(h, c, const_cast<cs_mlp *>(o->model), o->model_tol > 0 ? o->model_tol : 0.05,
+                                          c->lam[0], lam1, &accepted, &ratio, s);
+            dfree(lam1, s);
+            if (rc != CS_OK) goto fail;
+            c->learned_used = accepted ? 1 : 0;
+            c->learned_ratio = ratio;
+            if (accepted) continue;
+        }
         if (L.bs > 1) {
             if ((rc = cascade_setup_level_blocks(h, l, c->kind, c->nu, o->prescale, c->lam[l], s)) != CS_OK) goto fail;
         } else if ((rc = cascade_setup_level(h, l, c->kind, c->nu, o->prescale, !o->no_reuse, c->lam[l], s, &peak)) !=
@@ -576,6 +597,13 @@ cs_status cs_sweep_rhs(const cs_hierarchy *h, cs_cascade *c, int level, int step
 }
 
 int64_t cs_kernel_launches(void) { return g_launches.load(); }
+
+cs_status cs_learned_status(const cs_cascade *c, int *used, double *ratio) {
+    if (!c) { set_error("null argument"); return CS_ERR_ARG; }
+    if (used) *used = c->learned_used;
+    if (ratio) *ratio = c->learned_ratio;
+    return CS_OK;
+}
 
 cs_status cs_residual_restrict(const cs_hierarchy *h, int level, const double *b, const double *x, double *rc,
                                cs_stream stream) {

@@ -92,6 +92,10 @@ struct cs_cascade {
     int gm_restart = 0;
     double *gm_V = nullptr, *gm_h = nullptr;
     int64_t bytes = 0;
+    // learned setup of the finest level: 1 used, 0 fell back to the exact
+    // setup, -1 no model; ratio of level-1 Frobenius objectives (model / exact)
+    int learned_used = -1;
+    double learned_ratio = 0.0;
 };
 
 namespace csx {
@@ -105,9 +109,9 @@ cs_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
         cudaError_t _e = (call);                                        \
         if (_e != cudaSuccess) return csx::cuda_fail(_e, #call, __FILE__, __LINE__); \
     } while (0)
-#define CSX_TRY(call)                                                   \
+#define CSX_TRY(...)                                                    \
     do {                                                                \
-        cs_status _s = (call);                                          \
+        cs_status _s = (__VA_ARGS__);                                   \
         if (_s != CS_OK) return _s;                                     \
     } while (0)
 
@@ -177,6 +181,8 @@ cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, in
                               cudaStream_t s, int64_t *peak_bytes);
 cs_status cascade_setup_level_blocks(const cs_hierarchy *h, int l, int kind, int nu, int prescale, double *lam,
                                      cudaStream_t s);
+cs_status learned_setup_level0(const cs_hierarchy *h, cs_cascade *c, cs_mlp *M, double tol, double *lam,
+                               const double *lam_exact1, bool *accepted, double *ratio, cudaStream_t s);
 // block cascade step (bs > 1): out_b = x_b - Lambda_b^(T) (A x - b)_b over all
 // blocks or the blocks of one colour
 template <typename T>

@@ -1,0 +1,589 @@
+// Learned cascade setup: a 3-layer MLP that maps a block's local operator
+// neighbourhood to its prescaled Lambda~_1..nu blocks, with hand-written
+// forward, backward and Adam kernels, plus the feature / target extraction
+// from a hierarchy and an exact cascade.
+//
+// Network: in -> hid (ReLU) -> hid (ReLU) -> out, Y = H2 W3^T + b3.
+// Weights are kept as FP32 masters and rounded to BF16 for every product
+// (BF16 weights, FP32 accumulation); biases, activations and gradients FP32.
+// Layout: activations row-major [batch][width]; W_l row-major [out][in].
+//
+// Features of a block of bs x bs nodes (2D): for each block node p its row
+// of the prescaled operator W A W restricted to the (bs+2)^2-node window
+// around the block, at window position (lx + dx + 1) + (bs+2)(ly + dy + 1);
+// targets: the prescaled blocks Lambda~_l = W^-1 Lambda_l W^-1 of the exact
+// cascade, l = 1..nu, each bs^2 x bs^2 row-major (absent nodes zero).
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "cs_internal.cuh"
+
+struct cs_mlp {
+    int nin = 0, nhid = 0, nout = 0, max_batch = 0;
+    int64_t nparam = 0;
+    float *p = nullptr;          // FP32 master parameters: W1 b1 W2 b2 W3 b3
+    __nv_bfloat16 *w16 = nullptr;  // BF16 copies of W1, W2, W3
+    float *g = nullptr;          // gradients (same layout as p)
+    float *m = nullptr, *v = nullptr;  // Adam moments
+    float *z1 = nullptr, *z2 = nullptr, *h1 = nullptr, *h2 = nullptr, *y = nullptr;  // activations
+    float *d1 = nullptr, *d2 = nullptr, *dy = nullptr;  // backward buffers
+    float *loss = nullptr;       // device scalar
+    float *loss_host = nullptr;  // pinned
+    int64_t step = 0;
+    int64_t bytes = 0;
+    // offsets into p / g
+    int64_t oW1, ob1, oW2, ob2, oW3, ob3, o16W1, o16W2, o16W3;
+};
+
+namespace csx {
+
+// ------------------------------------------------------------------ GEMM
+// C[M x N] = A_op[M x K] B_op[K x N] (+ bias[n]) (ReLU), FP32 accumulation.
+// A_op(m,k) = TA ? A[k*lda + m] : A[m*lda + k]; B_op(k,n) = TB ? B[n*ldb + k]
+// : B[k*ldb + n].  64 x 64 tile per 256-thread CTA, 4 x 4 outputs a thread.
+template <bool TA, bool TB, typename TBt>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float *__restrict__ A, int lda,
+                                               const TBt *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
+                                               const float *__restrict__ bias, int relu, float *__restrict__ Z) {
+    __shared__ float As[16][64 + 4];
+    __shared__ float Bs[16][64 + 4];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int t = threadIdx.x; t < 16 * 64; t += 256) {
+            const int kk = t / 64, mm = t % 64;
+            const int gm = m0 + mm, gk = k0 + kk;
+            float va = 0.f;
+            if (gm < M && gk < K) va = TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
+            As[kk][mm] = va;
+            const int gn = n0 + mm;
+            float vb = 0.f;
+            if (gn < N && gk < K) vb = (float)(TB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn]);
+            Bs[kk][mm] = vb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + ty * 4 + i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gn = n0 + tx * 4 + j;
+            if (gn >= N) continue;
+            float v = acc[i][j];
+            if (bias) v += bias[gn];
+            if (Z) Z[(int64_t)gm * ldc + gn] = v;  // pre-activation, kept for the backward pass
+            if (relu) v = fmaxf(v, 0.f);
+            C[(int64_t)gm * ldc + gn] = v;
+        }
+    }
+}
+
+template <bool TA, bool TB, typename TBt>
+static cs_status gemm(int M, int N, int K, const float *A, int lda, const TBt *B, int ldb, float *C, int ldc,
+                      const float *bias, bool relu, cudaStream_t s, float *Z = nullptr) {
+    dim3 gr((N + 63) / 64, (M + 63) / 64);
+    k_gemm<TA, TB, TBt><<<gr, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu ? 1 : 0, Z);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+
+// h = relu(z) already fused; backward: d <- d * (z > 0)
+__global__ void k_relu_grad(int64_t n, const float *__restrict__ z, float *__restrict__ d) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!(z[i] > 0.f)) d[i] = 0.f;
+}
+
+// column sums of d [rows x cols] into db (deterministic: one CTA per column)
+__global__ void k_colsum(int rows, int cols, const float *__restrict__ d, float *__restrict__ db) {
+    __shared__ float sm[256];
+    const int c = blockIdx.x;
+    float v = 0.f;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) v += d[(int64_t)r * cols + c];
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[c] = sm[0];
+}
+
+// MSE loss over n values and dY = 2 (Y - T) / n; per-CTA partial sums of
+// squared errors then one CTA sums them in order.
+__global__ void k_mse(int64_t n, const float *__restrict__ y, const float *__restrict__ t, float *__restrict__ dy,
+                      float *__restrict__ part) {
+    __shared__ float sm[256];
+    float v = 0.f;
+    const float sc = 2.f / (float)n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float e = y[i] - t[i];
+        v = fmaf(e, e, v);
+        dy[i] = sc * e;
+    }
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+__global__ void k_mse_finish(int nparts, int64_t n, const float *__restrict__ part, float *__restrict__ loss) {
+    __shared__ float sm[256];
+    float v = 0.f;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += part[i];
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss[0] = sm[0] / (float)n;
+}
+
+// Adam (Kingma & Ba): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+// p -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)
+__global__ void k_adam(int64_t n, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+__global__ void k_to_bf16(int64_t n, const float *__restrict__ a, __nv_bfloat16 *__restrict__ o) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        o[i] = __float2bfloat16_rn(a[i]);
+}
+
+static cs_status refresh_bf16(cs_mlp *M, cudaStream_t s) {
+    const int64_t n1 = (int64_t)M->nhid * M->nin, n2 = (int64_t)M->nhid * M->nhid, n3 = (int64_t)M->nout * M->nhid;
+    k_to_bf16<<<256, 256, 0, s>>>(n1, M->p + M->oW1, M->w16 + M->o16W1);
+    k_to_bf16<<<256, 256, 0, s>>>(n2, M->p + M->oW2, M->w16 + M->o16W2);
+    k_to_bf16<<<256, 256, 0, s>>>(n3, M->p + M->oW3, M->w16 + M->o16W3);
+    count_launch(3);
+    CSX_CUDA(cudaGetLastError());
+    return CS_OK;
+}
+
+static cs_status forward(cs_mlp *M, int B, const float *X, cudaStream_t s) {
+    CSX_TRY(gemm<false, true, __nv_bfloat16>(B, M->nhid, M->nin, X, M->nin, M->w16 + M->o16W1, M->nin, M->h1,
+                                             M->nhid, M->p + M->ob1, true, s, M->z1));
+    CSX_TRY(gemm<false, true, __nv_bfloat16>(B, M->nhid, M->nhid, M->h1, M->nhid, M->w16 + M->o16W2, M->nhid, M->h2,
+                                             M->nhid, M->p + M->ob2, true, s, M->z2));
+    CSX_TRY(gemm<false, true, __nv_bfloat16>(B, M->nout, M->nhid, M->h2, M->nhid, M->w16 + M->o16W3, M->nhid, M->y,
+                                             M->nout, M->p + M->ob3, false, s));
+    return CS_OK;
+}
+
+// gradients of the mean squared error of the current forward pass w.r.t.
+// every parameter, into M->g; the loss into M->loss (device)
+static cs_status backward(cs_mlp *M, int B, const float *X, const float *T, cudaStream_t s) {
+    const int64_t ny = (int64_t)B * M->nout;
+    const int nparts = 256;
+    float *part = M->d2;  // scratch: nparts floats (d2 is rewritten below)
+    k_mse<<<nparts, 256, 0, s>>>(ny, M->y, T, M->dy, part);
+    k_mse_finish<<<1, 256, 0, s>>>(nparts, ny, part, M->loss);
+    count_launch(2);
+    // layer 3: dW3 = dY^T H2, db3 = colsum(dY), dH2 = dY W3
+    CSX_TRY(gemm<true, false, float>(M->nout, M->nhid, B, M->dy, M->nout, M->h2, M->nhid, M->g + M->oW3, M->nhid,
+                                     nullptr, false, s));
+    k_colsum<<<M->nout, 256, 0, s>>>(B, M->nout, M->dy, M->g + M->ob3);
+    count_launch();
+    CSX_TRY(gemm<false, false, __nv_bfloat16>(B, M->nhid, M->nout, M->dy, M->nout, M->w16 + M->o16W3, M->nhid, M->d2,
+                                              M->nhid, nullptr, false, s));
+    k_relu_grad<<<1024, 256, 0, s>>>((int64_t)B * M->nhid, M->z2, M->d2);
+    count_launch();
+    // layer 2
+    CSX_TRY(gemm<true, false, float>(M->nhid, M->nhid, B, M->d2, M->nhid, M->h1, M->nhid, M->g + M->oW2, M->nhid,
+                                     nullptr, false, s));
+    k_colsum<<<M->nhid, 256, 0, s>>>(B, M->nhid, M->d2, M->g + M->ob2);
+    count_launch();
+    CSX_TRY(gemm<false, false, __nv_bfloat16>(B, M->nhid, M->nhid, M->d2, M->nhid, M->w16 + M->o16W2, M->nhid, M->d1,
+                                              M->nhid, nullptr, false, s));
+    k_relu_grad<<<1024, 256, 0, s>>>((int64_t)B * M->nhid, M->z1, M->d1);
+    count_launch();
+    // layer 1
+    CSX_TRY(gemm<true, false, float>(M->nhid, M->nin, B, M->d1, M->nhid, X, M->nin, M->g + M->oW1, M->nin, nullptr,
+                                     false, s));
+    k_colsum<<<M->nhid, 256, 0, s>>>(B, M->nhid, M->d1, M->g + M->ob1);
+    count_launch();
+    CSX_CUDA(cudaGetLastError());
+    return CS_OK;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) for the weight initialisation
+static uint64_t splitmix(uint64_t &st) {
+    uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ------------------------------------------------ features and targets
+// one thread per block of the finest level
+__global__ void k_block_features(Grid g, int bs, int nbx, int64_t nblocks, int kind, const double *__restrict__ A,
+                                 float *__restrict__ F) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    const int bx = (int)(b % nbx), by = (int)(b / nbx);
+    const int win = bs + 2, nf = bs * bs * win * win;
+    float *f = F + b * nf;
+    for (int t = 0; t < nf; ++t) f[t] = 0.f;
+    const int C = kind == STAR ? 0 : 4;
+    const int nst = kind == STAR ? 5 : 9;
+    for (int p = 0; p < bs * bs; ++p) {
+        const int lx = p % bs, ly = p / bs;
+        const int ix = bs * bx + lx, iy = bs * by + ly;
+        if (ix >= g.nx || iy >= g.ny) continue;
+        const int64_t i = ix + (int64_t)g.nx * iy;
+        const double wi = 1.0 / sqrt(A[(int64_t)C * g.N + i]);
+        for (int s = 0; s < nst; ++s) {
+            int dx, dy;
+            if (kind == STAR) {
+                dx = s == 1 ? -1 : (s == 2 ? 1 : 0);
+                dy = s == 3 ? -1 : (s == 4 ? 1 : 0);
+            } else {
+                dx = s % 3 - 1;
+                dy = s / 3 - 1;
+            }
+            const int jx = ix + dx, jy = iy + dy;
+            if (jx < 0 || jx >= g.nx || jy < 0 || jy >= g.ny) continue;
+            const int64_t j = jx + (int64_t)g.nx * jy;
+            const double wj = 1.0 / sqrt(A[(int64_t)C * g.N + j]);
+            f[p * win * win + (lx + dx + 1) + win * (ly + dy + 1)] = (float)(wi * A[(int64_t)s * g.N + i] * wj);
+        }
+    }
+}
+
+// prescaled Lambda~ = Lambda / (w_p w_q) = Lambda sqrt(A_pp A_qq), per step
+__global__ void k_block_targets(Grid g, int bs, int nbx, int64_t nblocks, int nu, int kind,
+                                const double *__restrict__ A, const double *__restrict__ lam,
+                                float *__restrict__ T) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    const int bx = (int)(b % nbx), by = (int)(b / nbx);
+    const int nm = bs * bs, C = kind == STAR ? 0 : 4;
+    float *t = T + b * (int64_t)nu * nm * nm;
+    for (int l = 0; l < nu; ++l)
+        for (int p = 0; p < nm; ++p)
+            for (int q = 0; q < nm; ++q) {
+                const int px = bs * bx + p % bs, py = bs * by + p / bs, qx = bs * bx + q % bs, qy = bs * by + q / bs;
+                float v = 0.f;
+                if (px < g.nx && py < g.ny && qx < g.nx && qy < g.ny) {
+                    const double dp = A[(int64_t)C * g.N + px + (int64_t)g.nx * py];
+                    const double dq = A[(int64_t)C * g.N + qx + (int64_t)g.nx * qy];
+                    v = (float)(lam[((int64_t)l * nblocks + b) * nm * nm + p * nm + q] * sqrt(dp * dq));
+                }
+                t[((int64_t)l * nm + p) * nm + q] = v;
+            }
+}
+
+// predicted prescaled blocks -> unscaled Lambda (FP64), absent nodes zero
+__global__ void k_block_unscale(Grid g, int bs, int nbx, int64_t nblocks, int nu, int kind,
+                                const double *__restrict__ A, const float *__restrict__ Y, double *__restrict__ lam) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    const int bx = (int)(b % nbx), by = (int)(b / nbx);
+    const int nm = bs * bs, C = kind == STAR ? 0 : 4;
+    const float *y = Y + b * (int64_t)nu * nm * nm;
+    for (int l = 0; l < nu; ++l)
+        for (int p = 0; p < nm; ++p)
+            for (int q = 0; q < nm; ++q) {
+                const int px = bs * bx + p % bs, py = bs * by + p / bs, qx = bs * bx + q % bs, qy = bs * by + q / bs;
+                double v = 0.0;
+                if (px < g.nx && py < g.ny && qx < g.nx && qy < g.ny) {
+                    const double dp = A[(int64_t)C * g.N + px + (int64_t)g.nx * py];
+                    const double dq = A[(int64_t)C * g.N + qx + (int64_t)g.nx * qy];
+                    v = (double)y[((int64_t)l * nm + p) * nm + q] / sqrt(dp * dq);
+                }
+                lam[((int64_t)l * nblocks + b) * nm * nm + p * nm + q] = v;
+            }
+}
+
+// Frobenius objective of a level-1 block smoother on the prescaled operator:
+// obj_b = || E_0 rows - Lam~_b (A~ E_0) rows ||_F^2 = || I_b - Lam~_b A~_{b,:} ||_F^2
+// (E_0 = I); part[b] receives it for Lam~ from `lam` (unscaled, step 0).
+__global__ void k_level1_objective(Grid g, int bs, int nbx, int64_t nblocks, int kind, const double *__restrict__ A,
+                                   const double *__restrict__ lam, double *__restrict__ obj) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    const int bx = (int)(b % nbx), by = (int)(b / nbx);
+    const int nm = bs * bs, C = kind == STAR ? 0 : 4, nst = kind == STAR ? 5 : 9;
+    const int win = bs + 2;
+    double total = 0.0;
+    // columns of the block row: the (bs+2)^2 window; entry (p, col) of A~_{b,:}
+    for (int p = 0; p < nm; ++p) {
+        const int px = bs * bx + p % bs, py = bs * by + p / bs;
+        if (px >= g.nx || py >= g.ny) continue;
+        for (int cw = 0; cw < win * win; ++cw) {
+            const int cx = bs * bx - 1 + cw % win, cy = bs * by - 1 + cw / win;
+            if (cx < 0 || cx >= g.nx || cy < 0 || cy >= g.ny) continue;
+            const double dc = A[(int64_t)C * g.N + cx + (int64_t)g.nx * cy];
+            double v = (cx == px && cy == py) ? 1.0 : 0.0;
+            for (int q = 0; q < nm; ++q) {
+                const int qx = bs * bx + q % bs, qy = bs * by + q / bs;
+                if (qx >= g.nx || qy >= g.ny) continue;
+                const int dx = cx - qx, dy = cy - qy;
+                if (dx < -1 || dx > 1 || dy < -1 || dy > 1) continue;
+                int s = -1;
+                if (kind == STAR) {
+                    if (dx == 0 && dy == 0) s = 0;
+                    else if (dy == 0) s = dx < 0 ? 1 : 2;
+                    else if (dx == 0) s = dy < 0 ? 3 : 4;
+                } else {
+                    s = (dx + 1) + 3 * (dy + 1);
+                }
+                if (s < 0 || s >= nst) continue;
+                const double dq = A[(int64_t)C * g.N + qx + (int64_t)g.nx * qy];
+                const double dp = A[(int64_t)C * g.N + px + (int64_t)g.nx * py];
+                // prescaled Lam~_pq = Lam_pq sqrt(dp dq); A~_qc = A_qc / sqrt(dq dc)
+                const double lt = lam[b * nm * nm + p * nm + q] * sqrt(dp * dq);
+                v -= lt * A[(int64_t)s * g.N + qx + (int64_t)g.nx * qy] / sqrt(dq * dc);
+            }
+            total += v * v;
+        }
+    }
+    obj[b] = total;
+}
+
+}  // namespace csx
+
+using namespace csx;
+
+extern "C" {
+
+cs_status cs_mlp_create(int nin, int nhid, int nout, int max_batch, uint64_t seed, cs_mlp **out) {
+    if (!out || nin < 1 || nhid < 1 || nout < 1 || max_batch < 1) { set_error("bad MLP shape"); return CS_ERR_ARG; }
+    *out = nullptr;
+    cs_mlp *M = new cs_mlp();
+    M->nin = nin; M->nhid = nhid; M->nout = nout; M->max_batch = max_batch;
+    M->oW1 = 0; M->ob1 = M->oW1 + (int64_t)nhid * nin;
+    M->oW2 = M->ob1 + nhid; M->ob2 = M->oW2 + (int64_t)nhid * nhid;
+    M->oW3 = M->ob2 + nhid; M->ob3 = M->oW3 + (int64_t)nout * nhid;
+    M->nparam = M->ob3 + nout;
+    M->o16W1 = 0; M->o16W2 = (int64_t)nhid * nin; M->o16W3 = M->o16W2 + (int64_t)nhid * nhid;
+    const int64_t nw16 = M->o16W3 + (int64_t)nout * nhid;
+    cudaStream_t s = 0;
+    cs_status rc = CS_OK;
+    const int64_t B = max_batch;
+    // He-uniform weights U(-sqrt(6/fan_in), sqrt(6/fan_in)), zero biases
+    std::vector<float> h((size_t)M->nparam, 0.f);
+    uint64_t st = seed;
+    auto fill = [&](int64_t off, int64_t n, int fan_in) {
+        const double a = std::sqrt(6.0 / fan_in);
+        for (int64_t i = 0; i < n; ++i) h[off + i] = (float)(-a + 2.0 * a * ((splitmix(st) >> 11) * 0x1.0p-53));
+    };
+    fill(M->oW1, (int64_t)nhid * nin, nin);
+    fill(M->oW2, (int64_t)nhid * nhid, nhid);
+    fill(M->oW3, (int64_t)nout * nhid, nhid);
+    if ((rc = dalloc_t(&M->p, M->nparam, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&M->g, M->nparam, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&M->m, M->nparam, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&M->v, M->nparam, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&M->w16, nw16, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&M->z1, B * nhid, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&M->z2, B * nhid, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&M->h1, B * nhid, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&M->h2, B * nhid, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&M->d1, B * nhid, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&M->d2, std::max<int64_t>(B * nhid, 256), &M->bytes)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&M->y, B * nout, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&M->dy, B * nout, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&M->loss, 4, &M->bytes)) != CS_OK) goto fail;
+    if (cudaMallocHost(&M->loss_host, sizeof(float) * 4) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "cudaMallocHost", __FILE__, __LINE__); goto fail; }
+    if (cudaMemcpy(M->p, h.data(), sizeof(float) * M->nparam, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(M->m, 0, sizeof(float) * M->nparam) != cudaSuccess ||
+        cudaMemset(M->v, 0, sizeof(float) * M->nparam) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "MLP init", __FILE__, __LINE__);
+        goto fail;
+    }
+    if ((rc = refresh_bf16(M, s)) != CS_OK) goto fail;
+    if (cudaStreamSynchronize(s) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "MLP init", __FILE__, __LINE__); goto fail; }
+    *out = M;
+    return CS_OK;
+fail:
+    cs_mlp_destroy(M);
+    return rc;
+}
+
+void cs_mlp_destroy(cs_mlp *M) {
+    if (!M) return;
+    dfree(M->p); dfree(M->g); dfree(M->m); dfree(M->v); dfree(M->w16);
+    dfree(M->z1); dfree(M->z2); dfree(M->h1); dfree(M->h2); dfree(M->d1); dfree(M->d2); dfree(M->y); dfree(M->dy);
+    dfree(M->loss);
+    if (M->loss_host) cudaFreeHost(M->loss_host);
+    delete M;
+}
+
+int64_t cs_mlp_nparam(const cs_mlp *M) { return M ? M->nparam : 0; }
+
+cs_status cs_mlp_get_params(const cs_mlp *M, float *host) {
+    if (!M || !host) { set_error("null argument"); return CS_ERR_ARG; }
+    CSX_CUDA(cudaDeviceSynchronize());
+    CSX_CUDA(cudaMemcpy(host, M->p, sizeof(float) * M->nparam, cudaMemcpyDeviceToHost));
+    return CS_OK;
+}
+
+cs_status cs_mlp_set_params(cs_mlp *M, const float *host) {
+    if (!M || !host) { set_error("null argument"); return CS_ERR_ARG; }
+    CSX_CUDA(cudaMemcpy(M->p, host, sizeof(float) * M->nparam, cudaMemcpyHostToDevice));
+    CSX_TRY(refresh_bf16(M, 0));
+    CSX_CUDA(cudaDeviceSynchronize());
+    return CS_OK;
+}
+
+cs_status cs_mlp_forward(cs_mlp *M, int batch, const float *X, float *Y, cs_stream stream) {
+    if (!M || !X || !Y) { set_error("null argument"); return CS_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int b0 = 0; b0 < batch; b0 += M->max_batch) {
+        const int B = std::min(M->max_batch, batch - b0);
+        CSX_TRY(forward(M, B, X + (int64_t)b0 * M->nin, s));
+        CSX_CUDA(cudaMemcpyAsync(Y + (int64_t)b0 * M->nout, M->y, sizeof(float) * B * M->nout,
+                                 cudaMemcpyDeviceToDevice, s));
+    }
+    return CS_OK;
+}
+
+cs_status cs_mlp_gradients(cs_mlp *M, int batch, const float *X, const float *T, float *grad_host, float *loss,
+                           cs_stream stream) {
+    if (!M || !X || !T) { set_error("null argument"); return CS_ERR_ARG; }
+    if (batch < 1 || batch > M->max_batch) { set_error("batch must be in 1..max_batch"); return CS_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    CSX_TRY(forward(M, batch, X, s));
+    CSX_TRY(backward(M, batch, X, T, s));
+    CSX_CUDA(cudaMemcpyAsync(M->loss_host, M->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    CSX_CUDA(cudaStreamSynchronize(s));
+    if (loss) *loss = M->loss_host[0];
+    if (grad_host) CSX_CUDA(cudaMemcpy(grad_host, M->g, sizeof(float) * M->nparam, cudaMemcpyDeviceToHost));
+    return CS_OK;
+}
+
+cs_status cs_mlp_train_step(cs_mlp *M, int batch, const float *X, const float *T, float lr, float *loss,
+                            cs_stream stream) {
+    if (!M || !X || !T) { set_error("null argument"); return CS_ERR_ARG; }
+    if (batch < 1 || batch > M->max_batch) { set_error("batch must be in 1..max_batch"); return CS_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    CSX_TRY(forward(M, batch, X, s));
+    CSX_TRY(backward(M, batch, X, T, s));
+    M->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - std::pow(b1, (float)M->step), c2 = 1.f - std::pow(b2, (float)M->step);
+    k_adam<<<512, 256, 0, s>>>(M->nparam, M->p, M->g, M->m, M->v, lr, b1, b2, eps, c1, c2);
+    count_launch();
+    CSX_CUDA(cudaGetLastError());
+    CSX_TRY(refresh_bf16(M, s));
+    if (loss) {
+        CSX_CUDA(cudaMemcpyAsync(M->loss_host, M->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+        CSX_CUDA(cudaStreamSynchronize(s));
+        *loss = M->loss_host[0];
+    }
+    return CS_OK;
+}
+
+cs_status cs_block_features(const cs_hierarchy *h, int level, float *F, cs_stream stream) {
+    if (!h || !F) { set_error("null argument"); return CS_ERR_ARG; }
+    if (level < 0 || level >= h->nlev || h->lev[level].g.dim != 2 || h->lev[level].bs < 2) {
+        set_error("block features need a 2D level with blocks");
+        return CS_ERR_UNSUPPORTED;
+    }
+    const Level &L = h->lev[level];
+    k_block_features<<<(unsigned)((L.nblocks + 127) / 128), 128, 0, (cudaStream_t)stream>>>(L.g, L.bs, L.nbx, L.nblocks,
+                                                                                          L.kind, L.A, F);
+    count_launch();
+    CSX_CUDA(cudaGetLastError());
+    return CS_OK;
+}
+
+cs_status cs_block_targets(const cs_cascade *c, int level, float *T, cs_stream stream) {
+    if (!c || !T) { set_error("null argument"); return CS_ERR_ARG; }
+    const cs_hierarchy *h = c->h;
+    if (level < 0 || level >= c->nlev || h->lev[level].g.dim != 2 || h->lev[level].bs < 2 || c->kind != CS_ADDITIVE) {
+        set_error("block targets need an additive cascade on a 2D level with blocks");
+        return CS_ERR_UNSUPPORTED;
+    }
+    const Level &L = h->lev[level];
+    k_block_targets<<<(unsigned)((L.nblocks + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+        L.g, L.bs, L.nbx, L.nblocks, c->nu, L.kind, L.A, c->lam[level], T);
+    count_launch();
+    CSX_CUDA(cudaGetLastError());
+    return CS_OK;
+}
+
+}  // extern "C"
+
+namespace csx {
+
+// Learned setup of the finest level (see cs_cascade_opts.model): features,
+// MLP inference, unscaling; accepted when the level-1 Frobenius objective of
+// the prediction summed over the level is within `tol` of the exact one
+// (whose level-1 blocks cost one least-squares problem each); returns
+// *accepted = false otherwise, leaving lam untouched.
+cs_status learned_setup_level0(const cs_hierarchy *h, cs_cascade *c, cs_mlp *M, double tol, double *lam,
+                               const double *lam_exact1, bool *accepted, double *ratio, cudaStream_t s) {
+    const Level &L = h->lev[0];
+    const int nm = L.bs * L.bs, win = L.bs + 2;
+    if (M->nin != nm * win * win || M->nout != c->nu * nm * nm) {
+        set_error("model shape (%d -> %d) does not match %dx%d blocks with nu = %d", M->nin, M->nout, L.bs, L.bs, c->nu);
+        return CS_ERR_ARG;
+    }
+    float *F = nullptr, *Y = nullptr;
+    double *obj = nullptr;
+    cs_status rc = CS_OK;
+    std::vector<double> op, oe;
+    const unsigned nb = (unsigned)((L.nblocks + 127) / 128);
+    if ((rc = dalloc_t(&F, (size_t)L.nblocks * M->nin, nullptr, s)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&Y, (size_t)L.nblocks * M->nout, nullptr, s)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&obj, (size_t)2 * L.nblocks, nullptr, s)) != CS_OK) goto done;
+    k_block_features<<<nb, 128, 0, s>>>(L.g, L.bs, L.nbx, L.nblocks, L.kind, L.A, F);
+    count_launch();
+    if ((rc = cs_mlp_forward(M, (int)L.nblocks, F, Y, s)) != CS_OK) goto done;
+    k_block_unscale<<<nb, 128, 0, s>>>(L.g, L.bs, L.nbx, L.nblocks, c->nu, L.kind, L.A, Y, lam);
+    k_level1_objective<<<nb, 128, 0, s>>>(L.g, L.bs, L.nbx, L.nblocks, L.kind, L.A, lam, obj);
+    k_level1_objective<<<nb, 128, 0, s>>>(L.g, L.bs, L.nbx, L.nblocks, L.kind, L.A, lam_exact1, obj + L.nblocks);
+    count_launch(3);
+    op.resize(L.nblocks);
+    oe.resize(L.nblocks);
+    if (cudaMemcpyAsync(op.data(), obj, sizeof(double) * L.nblocks, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(oe.data(), obj + L.nblocks, sizeof(double) * L.nblocks, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "learned setup", __FILE__, __LINE__);
+        goto done;
+    }
+    {
+        double sp = 0.0, se = 0.0;
+        for (int64_t b = 0; b < L.nblocks; ++b) { sp += op[b]; se += oe[b]; }
+        *ratio = se > 0 ? sp / se : 1.0;
+        *accepted = std::isfinite(sp) && sp <= (1.0 + tol) * se;
+    }
+done:
+    dfree(F, s); dfree(Y, s); dfree(obj, s);
+    return rc;
+}
+
+}  // namespace csx

@@ -249,6 +249,64 @@ def interface2d(n: int = 1024, count: int = 200):
     return variable_poisson(inclusions_2d(n, count, config_seed(3)))
 
 
+def q1_jittered(n: int, seed: int, sigma: float = 2.0, corr: float = 16.0, jitter: float = 0.3,
+                kappa: np.ndarray | None = None) -> Stencil:
+    """Bilinear (Q1) finite elements for -div(kappa grad u) = f on the unit
+    square with (n+1)^2 quadrilateral elements, homogeneous Dirichlet.
+    Interior nodes are moved by U[-jitter h, jitter h] per coordinate
+    (isoparametric elements, 2x2 Gauss quadrature); kappa is constant per
+    element, log kappa = sigma g with g a unit-variance Gaussian field of
+    correlation length corr elements (workload 5).  Returns the 9-point
+    stencil of the interior nodes."""
+    n1 = n + 1
+    h = 1.0 / n1
+    I, J = np.meshgrid(np.arange(n + 2), np.arange(n + 2), indexing="xy")  # [J, I]
+    X = I * h
+    Y = J * h
+    if jitter > 0:
+        d = uniform(seed, 2 * n * n, -jitter * h, jitter * h).reshape(2, n, n)
+        X = X.copy(); Y = Y.copy()
+        X[1:-1, 1:-1] += d[0]
+        Y[1:-1, 1:-1] += d[1]
+    if kappa is None:
+        kappa = np.exp(sigma * gaussian_field((n1, n1), corr, seed + 7919))  # [ey, ex]
+    # element corners (ex,ey),(ex+1,ey),(ex+1,ey+1),(ex,ey+1)
+    cx = np.stack([X[:-1, :-1], X[:-1, 1:], X[1:, 1:], X[1:, :-1]], axis=-1)  # [ey, ex, 4]
+    cy = np.stack([Y[:-1, :-1], Y[:-1, 1:], Y[1:, 1:], Y[1:, :-1]], axis=-1)
+    xi_a = np.array([-1.0, 1.0, 1.0, -1.0])
+    eta_a = np.array([-1.0, -1.0, 1.0, 1.0])
+    g = 1.0 / np.sqrt(3.0)
+    K = np.zeros(cx.shape[:2] + (4, 4))
+    for xi in (-g, g):
+        for eta in (-g, g):
+            dNdxi = 0.25 * xi_a * (1 + eta_a * eta)
+            dNdeta = 0.25 * eta_a * (1 + xi_a * xi)
+            j11 = cx @ dNdxi; j12 = cy @ dNdxi   # d(x,y)/dxi
+            j21 = cx @ dNdeta; j22 = cy @ dNdeta  # d(x,y)/deta
+            det = j11 * j22 - j12 * j21
+            # grad_x N = J^{-T} grad_xi N, with J = [[j11, j12], [j21, j22]] (rows: xi, eta)
+            gx = (j22[..., None] * dNdxi - j12[..., None] * dNdeta) / det[..., None]
+            gy = (-j21[..., None] * dNdxi + j11[..., None] * dNdeta) / det[..., None]
+            K += (kappa * det)[..., None, None] * (gx[..., :, None] * gx[..., None, :] + gy[..., :, None] * gy[..., None, :])
+    offs = [(dx, dy, 0) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]  # BOX order
+    coeff = np.zeros((9, n, n))  # [s, iy, ix]
+    corner = [(0, 0), (1, 0), (1, 1), (0, 1)]  # (di, dj) of corner a
+    for a in range(4):
+        for b in range(4):
+            dx = corner[b][0] - corner[a][0]
+            dy = corner[b][1] - corner[a][1]
+            s = (dx + 1) + 3 * (dy + 1)
+            # node of corner a of element (ex, ey) is (ex + ia, ey + ja); interior when 1..n
+            ia, ja = corner[a]
+            ib, jb = corner[b]
+            ex0, ex1 = max(0, 1 - ia, 1 - ib), min(n1, n + 1 - ia, n + 1 - ib)  # keep a and b interior
+            ey0, ey1 = max(0, 1 - ja, 1 - jb), min(n1, n + 1 - ja, n + 1 - jb)
+            blk = K[ey0:ey1, ex0:ex1, a, b]
+            coeff[s, ey0 + ja - 1:ey1 + ja - 1, ex0 + ia - 1:ex1 + ia - 1] += blk
+    return Stencil(2, (n, n, 1), offs, coeff.reshape(9, n * n), False, name=f"q1_{n}",
+                   meta={"kappa": kappa})
+
+
 def rhs(N: int, seed: int, nrhs: int = 1) -> np.ndarray:
     """Right-hand side with i.i.d. entries ~ U[-1, 1] (Sec. 3.1 footnote).
     Shape ``(N,)`` for one RHS, else ``(N, nrhs)`` (RHS-contiguous)."""
