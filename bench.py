@@ -54,7 +54,7 @@ def args_():
     p.add_argument("--learned-meshes", type=int, default=64, help="training meshes of the learned setup")
     p.add_argument("--learned-n", type=int, default=127, help="interior nodes per side of a training mesh")
     p.add_argument("--learned-steps", type=int, default=2000, help="Adam steps")
-    p.add_argument("--profile", default="", choices=["", "setup", "step", "sweep", "multirhs"],
+    p.add_argument("--profile", default="", choices=["", "setup", "step", "sweep", "multirhs", "blocksetup"],
                    help="run one untimed setup (or setup + solve) and exit: the case ncu captures")
     return p.parse_args()
 
@@ -264,6 +264,14 @@ def main():
             cmg.sweep_rhs(hb, cb, 0, k % 3, Bb, Xb[k % 2], Xb[(k + 1) % 2], 32)
         torch.cuda.synchronize()
         print(json.dumps({"profile": a.profile, "n": a.n}), flush=True)
+        return
+
+    if a.profile == "blocksetup":  # the exact 3x3-block setup of the learned-setup workload (Q1, n^2)
+        Aq = problems.q1_jittered(a.n, 10000)
+        hq = cmg.setup_hierarchy(Aq.dim, Aq.n, Aq.offsets, torch.tensor(Aq.coeff, device=dev), block=3)
+        cmg.setup_cascade(hq, "additive", nu=3)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": a.profile, "n": a.n, "launches": cmg.kernel_launches()}), flush=True)
         return
 
     A, b = problems.poisson3d(a.n)

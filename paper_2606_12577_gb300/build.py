@@ -48,7 +48,7 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
         return LIB
     os.makedirs(OUT, exist_ok=True)
     cc = nvcc()
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-I", os.path.join(ROOT, "include"),
                     "--expt-relaxed-constexpr"] + (extra or [])
     objs = []
 
@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(_sources()), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, _sources()))
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [cc, "-shared", "-o", tmp] + ARCH + objs
+    cmd = [cc, "-shared", "-o", tmp] + ARCH + objs + ["-Xcompiler", "-pthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <string>
 
 #include "cs_internal.cuh"
@@ -430,40 +431,88 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
     c->nlev = h->nlev > 1 ? h->nlev - 1 : 1;
     c->lowp = o->lowp != 0;
     cs_status rc = CS_OK;
-    int64_t peak = 0;
     c->lam.assign(c->nlev, nullptr);
-    for (int l = 0; l < c->nlev; ++l) {
-        const int64_t N = h->lev[l].g.N;
-        const Level &L = h->lev[l];
-        if ((rc = dalloc_t(&c->lam[l], (size_t)c->nu * lam_step(L), &c->bytes, s)) != CS_OK) goto fail;
-        if (l == 0 && o->model) {
-            if (L.bs < 2 || L.g.dim != 2 || c->kind != CS_ADDITIVE) {
-                set_error("the learned setup needs an additive cascade on a 2D block level");
-                rc = CS_ERR_UNSUPPORTED;
-                goto fail;
+    for (int l = 0; l < c->nlev; ++l)
+        if ((rc = dalloc_t(&c->lam[l], (size_t)c->nu * lam_step(h->lev[l]), &c->bytes, s)) != CS_OK) goto fail;
+    {
+        // The levels' setups are independent of one another.  The coarse levels
+        // (small, latency-bound kernels) run concurrently, each from its own host
+        // thread on its own stream, while the finest level runs here on s.
+        auto level_setup = [&](int l, cudaStream_t st) -> cs_status {
+            const Level &L = h->lev[l];
+            if (L.bs > 1) return cascade_setup_level_blocks(h, l, c->kind, c->nu, o->prescale, c->lam[l], st);
+            int64_t peak = 0;
+            return cascade_setup_level(h, l, c->kind, c->nu, o->prescale, !o->no_reuse, c->lam[l], st, &peak);
+        };
+        auto finest = [&]() -> cs_status {
+            const Level &L = h->lev[0];
+            if (o->model) {
+                if (L.bs < 2 || L.g.dim != 2 || c->kind != CS_ADDITIVE) {
+                    set_error("the learned setup needs an additive cascade on a 2D block level");
+                    return CS_ERR_UNSUPPORTED;
+                }
+                // exact level-1 blocks (one least-squares problem per block) judge the prediction
+                double *lam1 = nullptr;
+                cs_status r = dalloc_t(&lam1, (size_t)lam_step(L), nullptr, s);
+                if (r != CS_OK) return r;
+                bool accepted = false;
+                double ratio = 0.0;
+                r = cascade_setup_level_blocks(h, 0, CS_ADDITIVE, 1, o->prescale, lam1, s);
+                if (r == CS_OK)
+                    r = learned_setup_level0(h, c, const_cast<cs_mlp *>(o->model), o->model_tol > 0 ? o->model_tol : 0.05,
+                                             c->lam[0], lam1, &accepted, &ratio, s);
+                dfree(lam1, s);
+                if (r != CS_OK) return r;
+                c->learned_used = accepted ? 1 : 0;
+                c->learned_ratio = ratio;
+                if (accepted) return CS_OK;
             }
-            // exact level-1 blocks (one least-squares problem per block) judge the prediction
-            double *lam1 = nullptr;
-            if ((rc = dalloc_t(&lam1, (size_t)lam_step(L), nullptr, s)) != CS_OK) goto fail;
-            bool accepted = false;
-            double ratio = 0.0;
-            rc = cascade_setup_level_blocks(h, 0, CS_ADDITIVE, 1, o->prescale, lam1, s);
-            if (rc == CS_OK)
-                rc = learned_setup_level0(h, c, const_cast<cs_mlp *>(o->model), o->model_tol > 0 ? o->model_tol : 0.05,
-                                          c->lam[0], lam1, &accepted, &ratio, s);
-            dfree(lam1, s);
-            if (rc != CS_OK) goto fail;
-            c->learned_used = accepted ? 1 : 0;
-            c->learned_ratio = ratio;
-            if (accepted) continue;
+            return level_setup(0, s);
+        };
+        const int nco = c->nlev - 1;
+        std::vector<cudaStream_t> ls(nco, nullptr);
+        std::vector<cudaEvent_t> ev(nco + 1, nullptr);
+        std::vector<cs_status> lrc(nco, CS_OK);
+        std::vector<std::string> lmsg(nco);
+        std::vector<std::thread> th;
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+        for (int k = 0; k < nco && e == cudaSuccess; ++k) {
+            e = cudaStreamCreateWithFlags(&ls[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[k + 1], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ls[k], ev[0], 0);
         }
-        if (L.bs > 1) {
-            if ((rc = cascade_setup_level_blocks(h, l, c->kind, c->nu, o->prescale, c->lam[l], s)) != CS_OK) goto fail;
-        } else if ((rc = cascade_setup_level(h, l, c->kind, c->nu, o->prescale, !o->no_reuse, c->lam[l], s, &peak)) !=
-                   CS_OK) {
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cascade setup streams", __FILE__, __LINE__);
+        } else {
+            for (int k = 0; k < nco; ++k)
+                th.emplace_back([&, k] {
+                    cudaError_t te = cudaSetDevice(dev);
+                    lrc[k] = te == cudaSuccess ? level_setup(k + 1, ls[k]) : cuda_fail(te, "set device", __FILE__, __LINE__);
+                    if (lrc[k] != CS_OK) lmsg[k] = cs_last_error();
+                    cudaEventRecord(ev[k + 1], ls[k]);
+                });
+            rc = finest();
+            for (auto &t : th) t.join();
+            for (int k = 0; k < nco; ++k) {
+                if (rc == CS_OK && lrc[k] != CS_OK) { rc = lrc[k]; set_error("%s", lmsg[k].c_str()); }
+                cudaStreamWaitEvent(s, ev[k + 1], 0);
+            }
+        }
+        for (int k = 0; k < nco; ++k) {
+            if (ls[k]) {
+                if (rc != CS_OK) cudaStreamSynchronize(ls[k]);
+                cudaStreamDestroy(ls[k]);
+            }
+        }
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+        if (rc != CS_OK) {
+            cudaStreamSynchronize(s);
             goto fail;
         }
-        (void)N;
     }
     if (c->lowp) {
         c->lo.resize(h->nlev);

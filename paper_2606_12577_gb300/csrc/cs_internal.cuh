@@ -109,6 +109,12 @@ cs_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
         cudaError_t _e = (call);                                        \
         if (_e != cudaSuccess) return csx::cuda_fail(_e, #call, __FILE__, __LINE__); \
     } while (0)
+// for functions that release their scratch at a `done:` label and return rc
+#define CSX_CUDA_GOTO(call)                                             \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) { rc = csx::cuda_fail(_e, #call, __FILE__, __LINE__); goto done; } \
+    } while (0)
 #define CSX_TRY(...)                                                    \
     do {                                                                \
         cs_status _s = (__VA_ARGS__);                                   \

@@ -284,12 +284,9 @@ cs_status galerkin_level(const Level &f, Level &c, bool reuse, cudaStream_t s) {
         if (f.kind == STAR) k_galerkin<2, STAR><<<gr, bl, sm2, s>>>(f.g, c.g, f.A, c.A, rs);
         else k_galerkin<2, BOX><<<gr, bl, sm2, s>>>(f.g, c.g, f.A, c.A, rs);
     } else {
-        static bool attr = false;  // 27 x 256 doubles = 54 KB exceeds the default 48 KB
-        if (!attr) {
-            CSX_CUDA(cudaFuncSetAttribute(k_galerkin<3, STAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-            CSX_CUDA(cudaFuncSetAttribute(k_galerkin<3, BOX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-            attr = true;
-        }
+        // 27 x 256 doubles = 54 KB exceeds the default 48 KB (set per call: the attribute is per device)
+        CSX_CUDA(cudaFuncSetAttribute(k_galerkin<3, STAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+        CSX_CUDA(cudaFuncSetAttribute(k_galerkin<3, BOX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
         if (f.kind == STAR) k_galerkin<3, STAR><<<gr, bl, sm3, s>>>(f.g, c.g, f.A, c.A, rs);
         else k_galerkin<3, BOX><<<gr, bl, sm3, s>>>(f.g, c.g, f.A, c.A, rs);
     }
@@ -679,12 +676,9 @@ static cs_status launch_setup_rows(const Grid &g, int periodic, const double *At
         bl = dim3(TBX * TBY, 1, 1);
     }
     const size_t smem = (size_t)StenS<DIM, KIND>::NST * TBX * TBY * (sizeof(double) + sizeof(int));
-    static bool attr = false;  // up to 27 x 256 x 12 B = 81 KB: above the default 48 KB
-    if (!attr) {
-        CSX_CUDA(cudaFuncSetAttribute(k_setup_rows<DIM, KIND, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-        attr = true;
-    }
+    // up to 27 x 256 x 12 B = 81 KB: above the default 48 KB (set per call: the attribute is per device)
+    CSX_CUDA(cudaFuncSetAttribute(k_setup_rows<DIM, KIND, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
     k_setup_rows<DIM, KIND, LAST><<<gr, bl, smem, s>>>(g, periodic, At, w, Ecur, Enxt, nn, chunk, nchunks, pstart,
                                                        pairs, cur_of, colour, lam, part, ru, rs);
     count_launch();
@@ -946,141 +940,63 @@ __global__ void __launch_bounds__(TBX *TBY) k_block_R(Grid g, int periodic, cons
     }
 }
 
-// least squares Lam~ = C G^{-1} for an n x n block (n <= NMAX): Cholesky of
-// G with pivot threshold 1e-14 tr(G); otherwise the minimum-norm solution
-// C G^+ from a cyclic Jacobi eigendecomposition of G.
-template <int NMAX>
-__device__ void block_lstsq(const double *G, const double *C, int n, double *Lt) {
-    double tr = 0.0;
-    for (int k = 0; k < n; ++k) tr += G[k * NMAX + k];
-    const double tol = 1e-14 * tr;
-    double L[NMAX * NMAX];
-    bool ok = tr > 0.0;
-    for (int k = 0; k < n * NMAX; ++k) L[k] = G[k];
-    for (int j = 0; j < n && ok; ++j) {
-        double d = L[j * NMAX + j];
-        for (int k = 0; k < j; ++k) d -= L[j * NMAX + k] * L[j * NMAX + k];
-        if (!(d > tol)) { ok = false; break; }
-        d = sqrt(d);
-        L[j * NMAX + j] = d;
-        for (int i = j + 1; i < n; ++i) {
-            double v = L[i * NMAX + j];
-            for (int k = 0; k < j; ++k) v -= L[i * NMAX + k] * L[j * NMAX + k];
-            L[i * NMAX + j] = v / d;
-        }
-    }
-    if (ok) {
-        for (int p = 0; p < n; ++p) {  // row p of C G^{-1}: solve G y = C_p^T
-            double y[NMAX];
-            for (int i = 0; i < n; ++i) {
-                double v = C[p * NMAX + i];
-                for (int k = 0; k < i; ++k) v -= L[i * NMAX + k] * y[k];
-                y[i] = v / L[i * NMAX + i];
-            }
-            for (int i = n - 1; i >= 0; --i) {
-                double v = y[i];
-                for (int k = i + 1; k < n; ++k) v -= L[k * NMAX + i] * y[k];
-                y[i] = v / L[i * NMAX + i];
-            }
-            for (int i = 0; i < n; ++i) Lt[p * NMAX + i] = y[i];
-        }
-        return;
-    }
-    // eigendecomposition G = Q diag(ev) Q^T by cyclic Jacobi rotations
-    double A[NMAX * NMAX], Q[NMAX * NMAX];
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) {
-            A[i * NMAX + j] = G[i * NMAX + j];
-            Q[i * NMAX + j] = i == j ? 1.0 : 0.0;
-        }
-    for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = 0.0;
-        for (int i = 0; i < n; ++i)
-            for (int j = i + 1; j < n; ++j) off += A[i * NMAX + j] * A[i * NMAX + j];
-        if (off < 1e-300) break;
-        for (int a = 0; a < n; ++a)
-            for (int b = a + 1; b < n; ++b) {
-                const double apq = A[a * NMAX + b];
-                if (apq == 0.0) continue;
-                const double th = (A[b * NMAX + b] - A[a * NMAX + a]) / (2.0 * apq);
-                const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
-                for (int k = 0; k < n; ++k) {
-                    const double x0 = A[k * NMAX + a], x1 = A[k * NMAX + b];
-                    A[k * NMAX + a] = cs * x0 - sn * x1;
-                    A[k * NMAX + b] = sn * x0 + cs * x1;
-                }
-                for (int k = 0; k < n; ++k) {
-                    const double x0 = A[a * NMAX + k], x1 = A[b * NMAX + k];
-                    A[a * NMAX + k] = cs * x0 - sn * x1;
-                    A[b * NMAX + k] = sn * x0 + cs * x1;
-                }
-                for (int k = 0; k < n; ++k) {
-                    const double x0 = Q[k * NMAX + a], x1 = Q[k * NMAX + b];
-                    Q[k * NMAX + a] = cs * x0 - sn * x1;
-                    Q[k * NMAX + b] = sn * x0 + cs * x1;
-                }
-            }
-    }
-    for (int p = 0; p < n; ++p)
-        for (int q = 0; q < n; ++q) {
-            double v = 0.0;
-            for (int k = 0; k < n; ++k) {
-                const double ev = A[k * NMAX + k];
-                if (!(ev > tol)) continue;
-                double cq = 0.0;
-                for (int m = 0; m < n; ++m) cq += C[p * NMAX + m] * Q[m * NMAX + k];
-                v += cq * Q[q * NMAX + k] / ev;
-            }
-            Lt[p * NMAX + q] = v;
-        }
-}
-
-// One block per thread: Gram and cross products, the block least squares,
-// the unscaled Lambda_b, and (unless LAST) the new E rows.
-template <int DIM, int NMAX, bool LAST>
-__global__ void k_block_solve(Grid g, int bs, int nbx, int nby, int64_t nblocks, const double *__restrict__ w,
-                              const double *__restrict__ Ecur, const double *__restrict__ Rbuf,
-                              double *__restrict__ Enxt, int nR, int nN, const int *__restrict__ curR,
-                              const int *__restrict__ shiftR, const int *__restrict__ curN,
-                              const int *__restrict__ shiftN, int colour, double *__restrict__ lam) {
-    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= nblocks) return;
+// Nodes of block b (x fastest inside the block; absent nodes past the upper
+// grid edges skipped): global index, position in the padded bs^d layout and
+// local coordinates.  Returns the count; *colour receives the block's
+// red-black colour (parity of the 1-based block coordinates).
+template <int DIM, int NMAX>
+__device__ __forceinline__ int block_nodes(const Grid &g, int bs, int nbx, int nby, int64_t b, int *node, int *lpos,
+                                           int (*dl)[3], int *colour) {
     const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((int64_t)nbx * nby));
-    const int64_t N = g.N;
-    const int side = 2 * bs - 1;
-    int node[NMAX], lpos[NMAX], dl[NMAX][3];
     int np = 0;
     for (int lp = 0; lp < NMAX; ++lp) {
         const int lx = lp % bs, ly = (lp / bs) % bs, lz = DIM == 3 ? lp / (bs * bs) : 0;
+        if (DIM == 2 && lp >= bs * bs) break;
         const int ix = bs * bx + lx, iy = bs * by + ly, iz = DIM == 3 ? bs * bz + lz : 0;
         if (ix >= g.nx || iy >= g.ny || (DIM == 3 && iz >= g.nz)) continue;
         node[np] = ix + g.nx * (iy + g.ny * iz);
         lpos[np] = lp;
-        dl[np][0] = lx; dl[np][1] = ly; dl[np][2] = lz;
+        if (dl) { dl[np][0] = lx; dl[np][1] = ly; dl[np][2] = lz; }
         ++np;
     }
-    const int bc = ((bx + 1) + (by + 1) + (DIM == 3 ? bz + 1 : 0)) & 1;
-    if (colour >= 0 && bc != colour) {  // carried over unchanged
-        if (!LAST)
-            for (int k = 0; k < np; ++k)
-                for (int o = 0; o < nN; ++o) {
-                    const int c = __ldg(curN + o);
-                    Enxt[(int64_t)o * N + node[k]] = c >= 0 ? Ecur[(int64_t)c * N + node[k]] : 0.0;
-                }
-        return;
-    }
-    auto sidx = [&](int p, int q) {
-        const int ex = dl[p][0] - dl[q][0] + bs - 1, ey = dl[p][1] - dl[q][1] + bs - 1;
-        const int ez = DIM == 3 ? dl[p][2] - dl[q][2] + bs - 1 : 0;
-        return ex + side * (ey + side * ez);
-    };
-    double G[NMAX * NMAX], C[NMAX * NMAX], Lt[NMAX * NMAX];
+    *colour = ((bx + 1) + (by + 1) + (DIM == 3 ? bz + 1 : 0)) & 1;
+    return np;
+}
+
+// Index of the displacement between block nodes p and q in the (2 bs - 1)^d
+// displacement list (lexicographic, x fastest).
+template <int DIM>
+__device__ __forceinline__ int block_sidx(const int (*dl)[3], int p, int q, int bs) {
+    const int side = 2 * bs - 1;
+    const int ex = dl[p][0] - dl[q][0] + bs - 1, ey = dl[p][1] - dl[q][1] + bs - 1;
+    const int ez = DIM == 3 ? dl[p][2] - dl[q][2] + bs - 1 : 0;
+    return ex + side * (ey + side * ez);
+}
+
+// Gram and cross products of one block per warp (Algorithm 2, the block
+// least-squares data): G = R_i R_i^T and C = E_i R_i^T over the prescaled
+// block rows R_i = (A~ E)_i.  Lanes split the offsets of each product,
+// warp-shuffle sums in a fixed order.  Output layout: entry e of block b at
+// GC[e * nblocks + b], e = p NMAX + q for G (q >= p only) and NMAX^2 + p NMAX
+// + q for C, so that the thread-per-block solve reads it coalesced.
+template <int DIM, int NMAX>
+__global__ void __launch_bounds__(128) k_block_gram(Grid g, int bs, int nbx, int nby, int64_t nblocks,
+                                                     const double *__restrict__ Ecur, const double *__restrict__ Rbuf,
+                                                     int nR, const int *__restrict__ curR,
+                                                     const int *__restrict__ shiftR, int colour,
+                                                     double *__restrict__ GC) {
+    const int lane = threadIdx.x & 31;
+    const int64_t b = blockIdx.x * (int64_t)4 + (threadIdx.x >> 5);
+    if (b >= nblocks) return;
+    int node[NMAX], lpos[NMAX], dl[NMAX][3], bc;
+    const int np = block_nodes<DIM, NMAX>(g, bs, nbx, nby, b, node, lpos, dl, &bc);
+    if (colour >= 0 && bc != colour) return;
+    const int64_t N = g.N;
     for (int p = 0; p < np; ++p)
         for (int q = 0; q < np; ++q) {
-            const int *sh = shiftR + (int64_t)sidx(p, q) * nR;
+            const int *sh = shiftR + (int64_t)block_sidx<DIM>(dl, p, q, bs) * nR;
             double gg = 0.0, cc = 0.0;
-            for (int o = 0; o < nR; ++o) {
+            for (int o = lane; o < nR; o += 32) {
                 const int t = __ldg(sh + o);
                 if (t < 0) continue;
                 const double rq = Rbuf[(int64_t)t * N + node[q]];
@@ -1088,26 +1004,348 @@ __global__ void k_block_solve(Grid g, int bs, int nbx, int nby, int64_t nblocks,
                 const int c0 = __ldg(curR + o);
                 if (c0 >= 0) cc = fma(Ecur[(int64_t)c0 * N + node[p]], rq, cc);
             }
-            if (q >= p) G[p * NMAX + q] = gg;
-            C[p * NMAX + q] = cc;
-        }
-    for (int p = 0; p < np; ++p)
-        for (int q = 0; q < p; ++q) G[p * NMAX + q] = G[q * NMAX + p];
-    block_lstsq<NMAX>(G, C, np, Lt);
-    double *lb = lam + b * (NMAX * NMAX);
-    for (int p = 0; p < np; ++p)
-        for (int q = 0; q < np; ++q) lb[lpos[p] * NMAX + lpos[q]] = w[node[p]] * Lt[p * NMAX + q] * w[node[q]];
-    if (!LAST)
-        for (int p = 0; p < np; ++p)
-            for (int o = 0; o < nN; ++o) {
-                const int c0 = __ldg(curN + o);
-                double v = c0 >= 0 ? Ecur[(int64_t)c0 * N + node[p]] : 0.0;
-                for (int q = 0; q < np; ++q) {
-                    const int t = __ldg(shiftN + (int64_t)sidx(p, q) * nN + o);
-                    if (t >= 0) v = fma(-Lt[p * NMAX + q], Rbuf[(int64_t)t * N + node[q]], v);
-                }
-                Enxt[(int64_t)o * N + node[p]] = v;
+            for (int off = 16; off > 0; off >>= 1) {
+                gg += __shfl_xor_sync(0xffffffffu, gg, off);
+                cc += __shfl_xor_sync(0xffffffffu, cc, off);
             }
+            if (lane == 0) {
+                if (q >= p) GC[(int64_t)(p * NMAX + q) * nblocks + b] = gg;
+                GC[(int64_t)(NMAX * NMAX + p * NMAX + q) * nblocks + b] = cc;
+            }
+        }
+}
+
+// Packed upper-triangle slot of the symmetric entry (i, j).
+template <int NMAX>
+__device__ __forceinline__ int pk(int i, int j) {
+    if (i > j) { const int t = i; i = j; j = t; }
+    return i * NMAX - (i * (i - 1)) / 2 + (j - i);
+}
+
+// Least squares Lam~ = C G^{-1} of one block per thread: Cholesky of G with
+// pivot threshold 1e-14 tr(G); otherwise the minimum-norm solution C G^+
+// from a cyclic Jacobi eigendecomposition of G (eigenvalues <= 1e-14 tr(G)
+// dropped).  A 3x3-node block whose centre node has its whole 9-point
+// stencil inside the block has an exactly singular G from the second cascade
+// level on (the level-1 step annihilates that row of A E), so the Jacobi
+// path is common, not exceptional.  One block per thread keeps every lane of
+// each FP64 instruction busy, which is what bounds this kernel: the
+// symmetric matrix (packed) and the eigenvectors sit in shared memory, entry
+// e of thread t at [e * 64 + t].  The sweeps stop once the off-diagonal mass
+// reaches rounding level (<= 1e-30 of the Frobenius mass, or no longer
+// decreasing).  Writes Lam~ (entry p NMAX + q of block b at Lt[e * nblocks +
+// b]) and the unscaled Lambda_ii = W_i Lam~ W_i into lam.
+template <int DIM, int NMAX>
+__global__ void __launch_bounds__(64) k_block_ls(Grid g, int bs, int nbx, int nby, int64_t nblocks,
+                                                  const double *__restrict__ w, int colour,
+                                                  const double *__restrict__ GC, double *__restrict__ Lt,
+                                                  double *__restrict__ lam) {
+    constexpr int NP = NMAX * (NMAX + 1) / 2;
+    extern __shared__ double sm_ls[];
+    const int tid = threadIdx.x;
+    double *A = sm_ls + tid;              // packed symmetric, stride 64
+    double *Q = sm_ls + NP * 64 + tid;    // NMAX x NMAX, stride 64
+    const int64_t b = blockIdx.x * (int64_t)64 + tid;
+    if (b >= nblocks) return;
+    int node[NMAX], lpos[NMAX], bc;
+    const int n = block_nodes<DIM, NMAX>(g, bs, nbx, nby, b, node, lpos, nullptr, &bc);
+    if (colour >= 0 && bc != colour) return;
+    auto Gat = [&](int i, int j) { return GC[(int64_t)(i * NMAX + j) * nblocks + b]; };  // i <= j
+    auto Cat = [&](int p, int m) { return GC[(int64_t)(NMAX * NMAX + p * NMAX + m) * nblocks + b]; };
+    auto out = [&](int p, int q, double v) {
+        Lt[(int64_t)(p * NMAX + q) * nblocks + b] = v;
+        lam[b * (NMAX * NMAX) + lpos[p] * NMAX + lpos[q]] = w[node[p]] * v * w[node[q]];
+    };
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += Gat(i, i);
+    const double tol = 1e-14 * tr;
+    bool ok = tr > 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) A[64 * pk<NMAX>(i, j)] = Gat(i, j);
+    // Cholesky in place: L(i, j), i >= j, in the slot of (j, i)
+    for (int j = 0; j < n && ok; ++j) {
+        double d = A[64 * pk<NMAX>(j, j)];
+        for (int k = 0; k < j; ++k) d -= A[64 * pk<NMAX>(j, k)] * A[64 * pk<NMAX>(j, k)];
+        if (!(d > tol)) { ok = false; break; }
+        d = sqrt(d);
+        A[64 * pk<NMAX>(j, j)] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double v = A[64 * pk<NMAX>(i, j)];
+            for (int k = 0; k < j; ++k) v -= A[64 * pk<NMAX>(i, k)] * A[64 * pk<NMAX>(j, k)];
+            A[64 * pk<NMAX>(i, j)] = v / d;
+        }
+    }
+    if (ok) {
+        for (int p = 0; p < n; ++p) {  // row p of C G^{-1}: G y = C_p^T by two triangular solves
+            double y[NMAX];
+#pragma unroll
+            for (int i = 0; i < NMAX; ++i) {
+                if (i >= n) break;
+                double v = Cat(p, i);
+#pragma unroll
+                for (int k = 0; k < i; ++k) v -= A[64 * pk<NMAX>(i, k)] * y[k];
+                y[i] = v / A[64 * pk<NMAX>(i, i)];
+            }
+#pragma unroll
+            for (int i = NMAX - 1; i >= 0; --i) {
+                if (i >= n) continue;
+                double v = y[i];
+#pragma unroll
+                for (int k = i + 1; k < NMAX; ++k)
+                    if (k < n) v -= A[64 * pk<NMAX>(k, i)] * y[k];
+                y[i] = v / A[64 * pk<NMAX>(i, i)];
+            }
+#pragma unroll
+            for (int q = 0; q < NMAX; ++q)
+                if (q < n) out(p, q, y[q]);
+        }
+        return;
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            if (j >= i) A[64 * pk<NMAX>(i, j)] = Gat(i, j);
+            Q[64 * (i * NMAX + j)] = i == j ? 1.0 : 0.0;
+        }
+    double frob = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) frob += A[64 * pk<NMAX>(i, j)] * A[64 * pk<NMAX>(i, j)];
+    double prev = frob;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) off += A[64 * pk<NMAX>(i, j)] * A[64 * pk<NMAX>(i, j)];
+        if (off < 1e-300 || off <= 1e-30 * frob || (sweep > 0 && off >= prev)) break;
+        prev = off;
+        for (int a = 0; a < n; ++a)
+            for (int c = a + 1; c < n; ++c) {
+                const double apq = A[64 * pk<NMAX>(a, c)];
+                if (apq == 0.0) continue;
+                const double th = (A[64 * pk<NMAX>(c, c)] - A[64 * pk<NMAX>(a, a)]) / (2.0 * apq);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < n; ++k) {
+                    if (k != a && k != c) {
+                        const double x0 = A[64 * pk<NMAX>(k, a)], x1 = A[64 * pk<NMAX>(k, c)];
+                        A[64 * pk<NMAX>(k, a)] = cs * x0 - sn * x1;
+                        A[64 * pk<NMAX>(k, c)] = sn * x0 + cs * x1;
+                    }
+                    const double q0 = Q[64 * (k * NMAX + a)], q1 = Q[64 * (k * NMAX + c)];
+                    Q[64 * (k * NMAX + a)] = cs * q0 - sn * q1;
+                    Q[64 * (k * NMAX + c)] = sn * q0 + cs * q1;
+                }
+                A[64 * pk<NMAX>(a, a)] -= t * apq;
+                A[64 * pk<NMAX>(c, c)] += t * apq;
+                A[64 * pk<NMAX>(a, c)] = 0.0;
+            }
+    }
+    double ev[NMAX];
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) ev[k] = k < n ? A[64 * pk<NMAX>(k, k)] : 0.0;
+    for (int p = 0; p < n; ++p) {  // row p of C G^+ = C Q diag(1/ev, ev > tol) Q^T
+        double cq[NMAX];
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k) cq[k] = 0.0;
+        for (int m = 0; m < n; ++m) {
+            const double cpm = Cat(p, m);
+#pragma unroll
+            for (int k = 0; k < NMAX; ++k)
+                if (k < n) cq[k] += cpm * Q[64 * (m * NMAX + k)];
+        }
+        for (int q = 0; q < n; ++q) {
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < NMAX; ++k)
+                if (k < n && ev[k] > tol) v += cq[k] * Q[64 * (q * NMAX + k)] / ev[k];
+            out(p, q, v);
+        }
+    }
+}
+
+// The same least squares with one warp per block, for levels with too few
+// blocks to fill the GPU one block per thread (there the serial FP64 chain of
+// a single thread, not the FP64 throughput, sets the time).  G, C (full, row
+// stride NMAX) are read only; Lt receives the n x n result; A, Q (NMAX^2) and
+// ev (NMAX) are per-warp shared workspace.  Lanes split the rows of each
+// elimination step, the right-hand sides of the triangular solves, the index
+// k of each plane rotation and the entries of C G^+; every lane evaluates the
+// scalar recurrences itself, so the rotations are those of the serial
+// algorithm (two-sided, as written for a full matrix).
+template <int NMAX>
+__device__ void block_lstsq_warp(const double *G, const double *C, int n, double *Lt, double *A, double *Q,
+                                 double *ev, int lane) {
+    double tr = 0.0;
+    for (int k = 0; k < n; ++k) tr += G[k * NMAX + k];
+    const double tol = 1e-14 * tr;
+    bool ok = tr > 0.0;
+    for (int k = lane; k < NMAX * NMAX; k += 32) A[k] = G[k];
+    __syncwarp();
+    for (int j = 0; j < n && ok; ++j) {
+        double d = A[j * NMAX + j];
+        for (int k = 0; k < j; ++k) d -= A[j * NMAX + k] * A[j * NMAX + k];
+        if (!(d > tol)) { ok = false; break; }
+        d = sqrt(d);
+        const int i = j + 1 + lane;
+        double v = 0.0;
+        if (i < n) {
+            v = A[i * NMAX + j];
+            for (int k = 0; k < j; ++k) v -= A[i * NMAX + k] * A[j * NMAX + k];
+        }
+        __syncwarp();
+        if (i < n) A[i * NMAX + j] = v / d;
+        if (lane == 0) A[j * NMAX + j] = d;
+        __syncwarp();
+    }
+    __syncwarp();
+    if (ok) {
+        if (lane < n) {  // row `lane` of C G^{-1}: G y = C_p^T by two triangular solves
+            double *y = Lt + lane * NMAX;
+            for (int i = 0; i < n; ++i) {
+                double v = C[lane * NMAX + i];
+                for (int k = 0; k < i; ++k) v -= A[i * NMAX + k] * y[k];
+                y[i] = v / A[i * NMAX + i];
+            }
+            for (int i = n - 1; i >= 0; --i) {
+                double v = y[i];
+                for (int k = i + 1; k < n; ++k) v -= A[k * NMAX + i] * y[k];
+                y[i] = v / A[i * NMAX + i];
+            }
+        }
+        __syncwarp();
+        return;
+    }
+    for (int k = lane; k < NMAX * NMAX; k += 32) {
+        const int r = k / NMAX, c = k % NMAX;
+        A[k] = r < n && c < n ? G[k] : 0.0;
+        Q[k] = r == c ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    double frob = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) frob += A[i * NMAX + j] * A[i * NMAX + j];
+    double prev = frob;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) off += A[i * NMAX + j] * A[i * NMAX + j];
+        if (off < 1e-300 || off <= 1e-30 * frob || (sweep > 0 && off >= prev)) break;
+        prev = off;
+        for (int a = 0; a < n; ++a)
+            for (int b = a + 1; b < n; ++b) {
+                const double apq = A[a * NMAX + b];
+                if (apq == 0.0) continue;
+                const double th = (A[b * NMAX + b] - A[a * NMAX + a]) / (2.0 * apq);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                __syncwarp();
+                if (lane < n) {
+                    const double x0 = A[lane * NMAX + a], x1 = A[lane * NMAX + b];
+                    A[lane * NMAX + a] = cs * x0 - sn * x1;
+                    A[lane * NMAX + b] = sn * x0 + cs * x1;
+                }
+                __syncwarp();
+                if (lane < n) {
+                    const double x0 = A[a * NMAX + lane], x1 = A[b * NMAX + lane];
+                    A[a * NMAX + lane] = cs * x0 - sn * x1;
+                    A[b * NMAX + lane] = sn * x0 + cs * x1;
+                    const double q0 = Q[lane * NMAX + a], q1 = Q[lane * NMAX + b];
+                    Q[lane * NMAX + a] = cs * q0 - sn * q1;
+                    Q[lane * NMAX + b] = sn * q0 + cs * q1;
+                }
+                __syncwarp();
+            }
+    }
+    if (lane < n) ev[lane] = A[lane * NMAX + lane];
+    __syncwarp();
+    for (int k = lane; k < n * n; k += 32) {  // (C Q)_{p,k} into A
+        const int p = k / n, kk = k % n;
+        double cq = 0.0;
+        for (int m = 0; m < n; ++m) cq += C[p * NMAX + m] * Q[m * NMAX + kk];
+        A[p * NMAX + kk] = cq;
+    }
+    __syncwarp();
+    for (int k = lane; k < n * n; k += 32) {  // G^+ = Q diag(1/ev, ev > tol) Q^T
+        const int p = k / n, q = k % n;
+        double v = 0.0;
+        for (int kk = 0; kk < n; ++kk)
+            if (ev[kk] > tol) v += A[p * NMAX + kk] * Q[q * NMAX + kk] / ev[kk];
+        Lt[p * NMAX + q] = v;
+    }
+    __syncwarp();
+}
+
+// Block counts below which the least squares run one warp per block.
+constexpr int64_t kLsThreadMin = 4096;
+
+template <int DIM, int NMAX>
+__global__ void __launch_bounds__(128) k_block_ls_warp(Grid g, int bs, int nbx, int nby, int64_t nblocks,
+                                                        const double *__restrict__ w, int colour,
+                                                        const double *__restrict__ GC, double *__restrict__ Lt,
+                                                        double *__restrict__ lam) {
+    __shared__ double sG[4][NMAX * NMAX], sC[4][NMAX * NMAX], sL[4][NMAX * NMAX], sA[4][NMAX * NMAX],
+        sQ[4][NMAX * NMAX], sEv[4][NMAX];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t b = blockIdx.x * (int64_t)4 + wib;
+    if (b >= nblocks) return;
+    int node[NMAX], lpos[NMAX], bc;
+    const int np = block_nodes<DIM, NMAX>(g, bs, nbx, nby, b, node, lpos, nullptr, &bc);
+    if (colour >= 0 && bc != colour) return;
+    for (int e = lane; e < NMAX * NMAX; e += 32) {
+        const int p = e / NMAX, q = e % NMAX;
+        const bool in = p < np && q < np;
+        sG[wib][e] = in ? GC[(int64_t)(p <= q ? e : q * NMAX + p) * nblocks + b] : 0.0;
+        sC[wib][e] = in ? GC[(int64_t)(NMAX * NMAX + e) * nblocks + b] : 0.0;
+    }
+    __syncwarp();
+    block_lstsq_warp<NMAX>(sG[wib], sC[wib], np, sL[wib], sA[wib], sQ[wib], sEv[wib], lane);
+    for (int e = lane; e < np * np; e += 32) {
+        const int p = e / np, q = e % np;
+        const double v = sL[wib][p * NMAX + q];
+        Lt[(int64_t)(p * NMAX + q) * nblocks + b] = v;
+        lam[b * (NMAX * NMAX) + lpos[p] * NMAX + lpos[q]] = w[node[p]] * v * w[node[q]];
+    }
+}
+
+// E update of one block per warp (Algorithm 2): new rows E_i - Lam~_ii R_i
+// over the next offset set; blocks of the other colour carry their rows
+// over unchanged.
+template <int DIM, int NMAX>
+__global__ void __launch_bounds__(128) k_block_update(Grid g, int bs, int nbx, int nby, int64_t nblocks,
+                                                       const double *__restrict__ Ecur,
+                                                       const double *__restrict__ Rbuf, double *__restrict__ Enxt,
+                                                       int nN, const int *__restrict__ curN,
+                                                       const int *__restrict__ shiftN, int colour,
+                                                       const double *__restrict__ Lt) {
+    __shared__ double sLt[4][NMAX * NMAX];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t b = blockIdx.x * (int64_t)4 + wib;
+    if (b >= nblocks) return;
+    int node[NMAX], lpos[NMAX], dl[NMAX][3], bc;
+    const int np = block_nodes<DIM, NMAX>(g, bs, nbx, nby, b, node, lpos, dl, &bc);
+    const int64_t N = g.N;
+    if (colour >= 0 && bc != colour) {
+        for (int k = 0; k < np; ++k)
+            for (int o = lane; o < nN; o += 32) {
+                const int c = __ldg(curN + o);
+                Enxt[(int64_t)o * N + node[k]] = c >= 0 ? Ecur[(int64_t)c * N + node[k]] : 0.0;
+            }
+        return;
+    }
+    double *L = sLt[wib];
+    for (int e = lane; e < NMAX * NMAX; e += 32) {
+        const int p = e / NMAX, q = e % NMAX;
+        L[e] = p < np && q < np ? Lt[(int64_t)e * nblocks + b] : 0.0;
+    }
+    __syncwarp();
+    for (int p = 0; p < np; ++p)
+        for (int o = lane; o < nN; o += 32) {
+            const int c0 = __ldg(curN + o);
+            double v = c0 >= 0 ? Ecur[(int64_t)c0 * N + node[p]] : 0.0;
+            for (int q = 0; q < np; ++q) {
+                const int t = __ldg(shiftN + (int64_t)block_sidx<DIM>(dl, p, q, bs) * nN + o);
+                if (t >= 0) v = fma(-L[p * NMAX + q], Rbuf[(int64_t)t * N + node[q]], v);
+            }
+            Enxt[(int64_t)o * N + node[p]] = v;
+        }
 }
 
 template <int DIM, int KIND>
@@ -1121,7 +1359,7 @@ static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, 
     const int bs = L.bs, ncol = kind == CS_MULTIPLICATIVE ? 2 : 1;
     const int nmax = L.nmax;
     dim3 gr = node_grid(g), bl = node_block();
-    double *w = nullptr, *At = nullptr, *Ecur = nullptr, *Enxt = nullptr, *Rbuf = nullptr;
+    double *w = nullptr, *At = nullptr, *Ecur = nullptr, *Enxt = nullptr, *Rbuf = nullptr, *GC = nullptr, *Ltb = nullptr;
     int *bad = nullptr, *pstart = nullptr, *curR = nullptr, *shiftR = nullptr, *curN = nullptr, *shiftN = nullptr;
     unsigned *pairs = nullptr;
     cs_status rc = CS_OK;
@@ -1156,15 +1394,12 @@ static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, 
     k_scale_op<DIM, KIND><<<gr, bl, 0, s>>>(g, h->periodic, L.A, w, At);
     count_launch();
     if ((rc = dalloc_t(&Ecur, N, nullptr, s)) != CS_OK) goto done;
+    // Gram/cross products and Lam~ of every block, entry-major (coalesced for the per-thread solve)
+    if ((rc = dalloc_t(&GC, (size_t)2 * nmax * nmax * L.nblocks, nullptr, s)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&Ltb, (size_t)nmax * nmax * L.nblocks, nullptr, s)) != CS_OK) goto done;
     k_fill<<<1216, 256, 0, s>>>(N, Ecur, 1.0);
     count_launch();
-    {
-        static bool attr = false;
-        if (!attr) {
-            CSX_CUDA(cudaFuncSetAttribute(k_block_R<DIM, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr = true;
-        }
-    }
+    CSX_CUDA_GOTO(cudaFuncSetAttribute(k_block_R<DIM, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int lev = 0; lev < nu; ++lev) {
         for (int k = 0; k < ncol; ++k) {
             const bool last = lev == nu - 1 && k == ncol - 1;
@@ -1242,22 +1477,33 @@ static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, 
                 const int colour = ncol == 2 ? k : -1;
                 k_block_R<DIM, KIND><<<gr, bl, smem, s>>>(g, h->periodic, At, Ecur, Rbuf, nR, pstart, pairs, bs, colour);
                 count_launch();
-                const int threads = 128;
-                const unsigned nblk = (unsigned)((L.nblocks + threads - 1) / threads);
+                const unsigned nwarp = (unsigned)((L.nblocks + 3) / 4), nthr = (unsigned)((L.nblocks + 63) / 64);
                 double *lam_l = lam + (int64_t)lev * L.nblocks * nmax * nmax;
-#define CSX_BLOCK_SOLVE(NM)                                                                                        \
-    if (last)                                                                                                      \
-        k_block_solve<DIM, NM, true><<<nblk, threads, 0, s>>>(g, bs, L.nbx, L.nby, L.nblocks, w, Ecur, Rbuf, Enxt, \
-                                                              nR, nN, curR, shiftR, curN, shiftN, colour, lam_l);  \
-    else                                                                                                           \
-        k_block_solve<DIM, NM, false><<<nblk, threads, 0, s>>>(g, bs, L.nbx, L.nby, L.nblocks, w, Ecur, Rbuf, Enxt, \
-                                                               nR, nN, curR, shiftR, curN, shiftN, colour, lam_l);
-                if (nmax <= 4) { CSX_BLOCK_SOLVE(4) }
-                else if (nmax <= 8) { CSX_BLOCK_SOLVE(8) }
-                else if (nmax <= 9) { CSX_BLOCK_SOLVE(9) }
-                else { set_error("blocks of more than 9 nodes are not supported"); rc = CS_ERR_UNSUPPORTED; goto done; }
-#undef CSX_BLOCK_SOLVE
-                count_launch();
+#define CSX_BLOCK_STEPS(NM)                                                                                         \
+    {                                                                                                               \
+        const size_t lsm = (size_t)64 * (NM * (NM + 1) / 2 + NM * NM) * sizeof(double);                          \
+        k_block_gram<DIM, NM><<<nwarp, 128, 0, s>>>(g, bs, L.nbx, L.nby, L.nblocks, Ecur, Rbuf, nR, curR, shiftR, \
+                                                     colour, GC);                                                   \
+        if (L.nblocks >= kLsThreadMin) {                                                                            \
+            CSX_CUDA_GOTO(cudaFuncSetAttribute(k_block_ls<DIM, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                               (int)lsm));                                                          \
+            k_block_ls<DIM, NM><<<nthr, 64, lsm, s>>>(g, bs, L.nbx, L.nby, L.nblocks, w, colour, GC, Ltb, lam_l); \
+        } else {                                                                                                    \
+            k_block_ls_warp<DIM, NM><<<nwarp, 128, 0, s>>>(g, bs, L.nbx, L.nby, L.nblocks, w, colour, GC, Ltb,    \
+                                                           lam_l);                                                  \
+        }                                                                                                           \
+        count_launch(2);                                                                                            \
+        if (!last) {                                                                                                \
+            k_block_update<DIM, NM><<<nwarp, 128, 0, s>>>(g, bs, L.nbx, L.nby, L.nblocks, Ecur, Rbuf, Enxt, nN,   \
+                                                          curN, shiftN, colour, Ltb);                               \
+            count_launch();                                                                                         \
+        }                                                                                                           \
+    }
+                if (nmax == 4) CSX_BLOCK_STEPS(4)
+                else if (nmax == 8) CSX_BLOCK_STEPS(8)
+                else if (nmax == 9) CSX_BLOCK_STEPS(9)
+                else { set_error("blocks of %d nodes are not supported (4, 8 or 9)", nmax); rc = CS_ERR_UNSUPPORTED; goto done; }
+#undef CSX_BLOCK_STEPS
             }
             if (cudaGetLastError() != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "block setup", __FILE__, __LINE__); goto done; }
             dfree(Ecur, s);
@@ -1270,6 +1516,7 @@ static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, 
     }
 done:
     dfree(w, s); dfree(At, s); dfree(Ecur, s); dfree(Enxt, s); dfree(Rbuf, s); dfree(bad, s); dfree(pstart, s);
+    dfree(GC, s); dfree(Ltb, s);
     dfree(pairs, s); dfree(curR, s); dfree(shiftR, s); dfree(curN, s); dfree(shiftN, s);
     return rc;
 }
