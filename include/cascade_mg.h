@@ -262,6 +262,78 @@ typedef struct {
 cs_status cs_solve(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *opts, const double *b,
                    double *x, cs_solve_info *info, cs_stream stream);
 
+/* ------------------------------------------------------ many problems */
+/* Set up nprob independent problems: cs_setup_hierarchy then
+ * cs_setup_cascade for each, run concurrently from nthreads host threads
+ * (<= 0: up to 16), each on its own stream.  The batched-solve form of the
+ * method (many uneven problems at once); the paper sets up one problem at a
+ * time.  A[p] may hold host or device coefficients (coeff_on_host).  The
+ * handles are returned in h[p], c[p]; on any failure every handle is released,
+ * all entries are NULL and the first failing problem's error is reported.
+ * `stream` waits for all the work. */
+cs_status cs_setup_many(int nprob, const cs_stencil *A, const cs_hierarchy_opts *hopts,
+                        const cs_cascade_opts *copts, int nthreads, cs_stream stream, cs_hierarchy **h,
+                        cs_cascade **c);
+
+/* Batched solve: nprob independent 2D Dirichlet problems of any sizes, each
+ * with its own red-black multiplicative cascade (point blocks, the same depth
+ * nu for all; eq. fwdm) and 1..8 right-hand sides, iterated together by
+ * FP64 refinement x += V0(b - A x) or by GMRES preconditioned with V0
+ * (Algorithm 1 V-cycles in opts.precision; FP64 residuals and Krylov
+ * vectors) until every problem meets its tolerance.  The whole solve
+ * is ONE persistent cooperative kernel launch (grid-wide barriers between its
+ * stages), replayed from a CUDA graph.  Vectors of problem p are
+ * [N_p][nrhs_p], right-hand sides contiguous per node: element (i, r) at
+ * i * nrhs_p + r.  The paper solves one problem at a time; this is the
+ * many-problem form of the same iteration. */
+typedef struct cs_batch cs_batch;
+typedef struct {
+    int precision;   /* CS_FP32 (FP32 cycles inside FP64 refinement) or CS_FP64 */
+    int order;       /* CS_RF or CS_FF, as for cs_vcycle */
+    int mu_pre, mu_post;
+    int autotune;    /* 1: time each (threads, tile_nodes) candidate on the batch and keep the fastest */
+    int threads;     /* CTA size if not autotuned (default 256; 32..512, multiple of 32) */
+    int tile_nodes;  /* grid nodes per work tile if not autotuned (default 1024) */
+    int method;      /* CS_REFINE: x += V0(b - A x); CS_GMRES: left-preconditioned restarted GMRES
+                        with M = V0 per right-hand side (modified Gram-Schmidt, Givens; inner
+                        steps stop on |g_{j+1}| <= tol ||M b||, restarts check the true residual) */
+    int restart;     /* GMRES restart length (default 30, at most 64) */
+} cs_batch_opts;
+typedef struct {
+    int threads;
+    int tile_nodes;
+    float ms;        /* measured time of two iterations on the batch */
+} cs_batch_tune;
+/* Plan a batched solve over existing handles (not owned; they must outlive
+ * the plan): validates them, allocates the multi-RHS level vectors and the
+ * tile tables, and autotunes if asked.  Errors: CS_ERR_ARG (null, nrhs not in
+ * 1..8, FP32 without lowp cascades, mixed nu), CS_ERR_UNSUPPORTED (3D,
+ * periodic, additive cascades, blocks > 1 node, no coarsest factorisation). */
+cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *c, const int *nrhs,
+                          const cs_batch_opts *opts, cs_stream stream, cs_batch **out);
+/* Solve all problems from the initial x[p] (device, [N_p][nrhs_p]) to
+ * ||b - A x||_2 / ||b||_2 <= tol for every right-hand side (tol <= 0: 1e-10;
+ * maxit <= 0: 100).  info[p] (host, optional): V-cycles applied, converged,
+ * worst relative residual over the problem's right-hand sides.  Synchronises
+ * the stream.  Errors: CS_ERR_NOTCONV / CS_ERR_DIVERGED if any problem did not
+ * converge (the others are still solved), CS_ERR_ARG, CS_ERR_CUDA. */
+cs_status cs_batch_solve(cs_batch *b, const double *const *bvec, double *const *x, double tol, int maxit,
+                         cs_solve_info *info, cs_stream stream);
+/* The configuration in use, the CTAs of the cooperative launch, and the
+ * autotuner's measurements (up to cap entries; *ntuned = their count). */
+cs_status cs_batch_config(const cs_batch *b, int *threads, int *tile_nodes, int *ctas, cs_batch_tune *tuned,
+                          int cap, int *ntuned);
+/* Force a configuration (e.g. to compare schedules); results do not depend on it. */
+cs_status cs_batch_set_config(cs_batch *b, int threads, int tile_nodes, cs_stream stream);
+int64_t cs_batch_bytes(const cs_batch *b);
+void cs_batch_destroy(cs_batch *b);
+/* One-shot form: plan (no autotuning), solve, release.  opts->cycle gives the
+ * precision, order and mu; opts->method (CS_GMRES, else refinement) and
+ * opts->restart the iteration; opts->tol and opts->maxit the stopping rule. */
+cs_status cs_solve_batched(int nprob, cs_hierarchy *const *h, cs_cascade *const *c, const cs_solve_opts *opts,
+                           const double *const *b, double *const *x, const int *nrhs, cs_solve_info *info,
+                           cs_stream stream);
+
 /* ------------------------------------------------------- learned setup */
 /* A small MLP (nin -> nhid -> nhid -> nout, ReLU) that maps a block's operator
  * window to its prescaled Lambda~_1..nu blocks.  This learned form is not in

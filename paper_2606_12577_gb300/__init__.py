@@ -20,7 +20,8 @@ from ._capi import CascadeError
 
 __all__ = ["setup_hierarchy", "setup_cascade", "vcycle", "solve", "smooth", "sweep", "sweep_rhs", "residual_restrict",
            "prolong_correct", "coarse_solve", "residual", "query_level", "export_operator", "export_colours",
-           "export_lambda", "kernel_launches", "smooth_noalloc", "MLP", "block_features", "block_targets", "learned_status", "Hierarchy", "Cascade", "SolveInfo", "CascadeError"]
+           "export_lambda", "kernel_launches", "smooth_noalloc", "MLP", "block_features", "block_targets", "learned_status", "setup_many", "Batch", "solve_batched", "Hierarchy", "Cascade", "SolveInfo",
+           "CascadeError"]
 
 
 def _torch():
@@ -398,6 +399,136 @@ def solve(h, c, b, x, method="stationary", tol=1e-10, maxit=100, restart=30, mu_
     if raise_on_error and st not in (_capi.CS_OK,):
         _capi.check(st, "cs_solve")
     return SolveInfo(st, info.iterations, bool(info.converged), info.final_rel_residual, hist[: info.nhist].copy())
+
+
+def _stencil_struct(dim, n, offsets, coeff, periodic=False):
+    """cs_stencil for (dim, n, offsets, coeff); returns (struct, keep-alive)."""
+    st = _capi.cs_stencil()
+    st.dim = dim
+    nn = list(n) + [1] * (3 - len(n))
+    for d in range(3):
+        st.n[d] = int(nn[d])
+    st.nst = len(offsets)
+    for s_, o in enumerate(offsets):
+        for d in range(3):
+            st.off[s_][d] = int(o[d])
+    keep = coeff
+    if isinstance(coeff, np.ndarray):
+        keep = np.ascontiguousarray(coeff, dtype=np.float64)
+        st.coeff = keep.ctypes.data_as(C.c_void_p)
+        st.coeff_on_host = 1
+    else:
+        st.coeff = _dev_ptr(coeff, name="coeff").value
+        st.coeff_on_host = 0
+    st.periodic = int(bool(periodic))
+    return st, keep
+
+
+def setup_many(problems, kind="multiplicative", nu=3, lowp=True, coarse_max=4, block=1, reuse=True, nthreads=0,
+               stream=None):
+    """Hierarchies and cascades of many independent problems, set up
+    concurrently (``cs_setup_many``).  ``problems``: objects with ``dim``,
+    ``n``, ``offsets``, ``coeff`` (host numpy or CUDA tensors) and optionally
+    ``periodic``.  Returns (hierarchies, cascades)."""
+    probs = list(problems)
+    n = len(probs)
+    arr = (_capi.cs_stencil * n)()
+    keep = []
+    for k, A in enumerate(probs):
+        st, kp = _stencil_struct(A.dim, A.n, A.offsets, A.coeff, getattr(A, "periodic", False))
+        arr[k] = st
+        keep.append(kp)
+    ho = _capi.cs_hierarchy_opts(coarse_max, 0, block, int(not reuse))
+    k = _capi.CS_MULTIPLICATIVE if kind == "multiplicative" else _capi.CS_ADDITIVE
+    co = _capi.cs_cascade_opts(k, nu, 1, 0, int(lowp), int(not reuse), C.c_void_p(None), 0.05)
+    hp = (C.c_void_p * n)()
+    cp = (C.c_void_p * n)()
+    _capi.check(_capi.lib().cs_setup_many(n, arr, C.byref(ho), C.byref(co), int(nthreads), _stream(stream), hp, cp),
+                "cs_setup_many")
+    del keep
+    hs = [Hierarchy(hp[i], probs[i].dim) for i in range(n)]
+    cs = [Cascade(cp[i], hs[i], kind, nu, lowp) for i in range(n)]
+    return hs, cs
+
+
+class Batch:
+    """A planned batched solve over existing (hierarchy, cascade) pairs
+    (``cs_batch_create``); ``solve`` runs one persistent cooperative launch.
+    Vectors of problem p are CUDA float64 tensors of N_p * nrhs[p] values,
+    right-hand sides contiguous per node."""
+
+    def __init__(self, hs, cs, nrhs, precision="fp32", order="RF", mu_pre=1, mu_post=1, autotune=False, threads=0,
+                 tile_nodes=0, method="refine", restart=30, stream=None):
+        self.hs, self.cs = list(hs), list(cs)
+        self.nprob = len(self.hs)
+        self.nrhs = [int(m) for m in nrhs]
+        self.N = [h.N(0) for h in self.hs]
+        o = _capi.cs_batch_opts(_capi.CS_FP32 if precision == "fp32" else _capi.CS_FP64,
+                                _capi.CS_RF if order == "RF" else _capi.CS_FF, mu_pre, mu_post, int(autotune),
+                                threads, tile_nodes, _capi.CS_GMRES if method == "gmres" else _capi.CS_REFINE,
+                                restart)
+        hp = (C.c_void_p * self.nprob)(*[h.ptr for h in self.hs])
+        cp = (C.c_void_p * self.nprob)(*[c.ptr for c in self.cs])
+        mp = (C.c_int * self.nprob)(*self.nrhs)
+        out = C.c_void_p()
+        _capi.check(_capi.lib().cs_batch_create(self.nprob, hp, cp, mp, C.byref(o), _stream(stream), C.byref(out)),
+                    "cs_batch_create")
+        self._p = out.value
+
+    def config(self):
+        t, tn, ct, nt = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        buf = (_capi.cs_batch_tune * 64)()
+        _capi.check(_capi.lib().cs_batch_config(self._p, C.byref(t), C.byref(tn), C.byref(ct), buf, 64,
+                                                C.byref(nt)), "cs_batch_config")
+        return {"threads": t.value, "tile_nodes": tn.value, "ctas": ct.value,
+                "tuned": [(buf[i].threads, buf[i].tile_nodes, buf[i].ms) for i in range(min(nt.value, 64))]}
+
+    def set_config(self, threads, tile_nodes, stream=None):
+        _capi.check(_capi.lib().cs_batch_set_config(self._p, threads, tile_nodes, _stream(stream)),
+                    "cs_batch_set_config")
+
+    def nbytes(self):
+        return int(_capi.lib().cs_batch_bytes(self._p))
+
+    def solve(self, bs, xs, tol=1e-10, maxit=100, raise_on_error=True, stream=None):
+        """Solve every problem in place from its x; returns a list of SolveInfo."""
+        if len(bs) != self.nprob or len(xs) != self.nprob:
+            raise ValueError("one b and one x per problem")
+        bp = (C.c_void_p * self.nprob)(*[_dev_ptr(b, self.N[i] * self.nrhs[i], f"b[{i}]").value
+                                         for i, b in enumerate(bs)])
+        xp = (C.c_void_p * self.nprob)(*[_dev_ptr(x, self.N[i] * self.nrhs[i], f"x[{i}]").value
+                                         for i, x in enumerate(xs)])
+        infos = (_capi.cs_solve_info * self.nprob)()
+        st = _capi.lib().cs_batch_solve(self._p, bp, xp, float(tol), int(maxit), infos, _stream(stream))
+        if raise_on_error and st != _capi.CS_OK:
+            _capi.check(st, "cs_batch_solve")
+        return [SolveInfo(st, infos[i].iterations, bool(infos[i].converged), infos[i].final_rel_residual,
+                          np.zeros(0)) for i in range(self.nprob)]
+
+    def __del__(self):
+        if getattr(self, "_p", None) and _capi._lib is not None:
+            _capi._lib.cs_batch_destroy(self._p)
+            self._p = None
+
+
+def solve_batched(hs, cs, bs, xs, nrhs, tol=1e-10, maxit=100, mu_pre=1, mu_post=1, order="RF", precision="fp32",
+                  method="refine", restart=30, raise_on_error=True, stream=None):
+    """One-shot batched solve (``cs_solve_batched``: plan without autotuning,
+    solve, release)."""
+    n = len(hs)
+    o = _capi.cs_solve_opts(_capi.CS_GMRES if method == "gmres" else _capi.CS_REFINE, restart, maxit, tol,
+                            _cycle_opts(mu_pre, mu_post, order, precision), 0, None, 0)
+    hp = (C.c_void_p * n)(*[h.ptr for h in hs])
+    cp = (C.c_void_p * n)(*[c.ptr for c in cs])
+    mp = (C.c_int * n)(*[int(m) for m in nrhs])
+    bp = (C.c_void_p * n)(*[_dev_ptr(b, hs[i].N(0) * int(nrhs[i]), f"b[{i}]").value for i, b in enumerate(bs)])
+    xp = (C.c_void_p * n)(*[_dev_ptr(x, hs[i].N(0) * int(nrhs[i]), f"x[{i}]").value for i, x in enumerate(xs)])
+    infos = (_capi.cs_solve_info * n)()
+    st = _capi.lib().cs_solve_batched(n, hp, cp, C.byref(o), bp, xp, mp, infos, _stream(stream))
+    if raise_on_error and st != _capi.CS_OK:
+        _capi.check(st, "cs_solve_batched")
+    return [SolveInfo(st, infos[i].iterations, bool(infos[i].converged), infos[i].final_rel_residual, np.zeros(0))
+            for i in range(n)]
 
 
 def _host_ptr(a, n, name):

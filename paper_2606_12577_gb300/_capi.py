@@ -57,6 +57,16 @@ class cs_level_info(C.Structure):
                 ("off", (C.c_int * 3) * 27), ("nlevels", C.c_int), ("block", C.c_int), ("lamsize", C.c_int64)]
 
 
+class cs_batch_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("order", C.c_int), ("mu_pre", C.c_int), ("mu_post", C.c_int),
+                ("autotune", C.c_int), ("threads", C.c_int), ("tile_nodes", C.c_int), ("method", C.c_int),
+                ("restart", C.c_int)]
+
+
+class cs_batch_tune(C.Structure):
+    _fields_ = [("threads", C.c_int), ("tile_nodes", C.c_int), ("ms", C.c_float)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -100,6 +110,21 @@ _SIGS = {
     "cs_block_features": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "cs_block_targets": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "cs_learned_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "cs_setup_many": (C.c_int, [C.c_int, C.POINTER(cs_stencil), C.POINTER(cs_hierarchy_opts),
+                                C.POINTER(cs_cascade_opts), C.c_int, C.c_void_p, C.POINTER(C.c_void_p),
+                                C.POINTER(C.c_void_p)]),
+    "cs_batch_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_int),
+                                  C.POINTER(cs_batch_opts), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "cs_batch_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_double, C.c_int,
+                                 C.POINTER(cs_solve_info), C.c_void_p]),
+    "cs_batch_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(cs_batch_tune), C.c_int, C.POINTER(C.c_int)]),
+    "cs_batch_set_config": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "cs_batch_bytes": (C.c_int64, [C.c_void_p]),
+    "cs_batch_destroy": (None, [C.c_void_p]),
+    "cs_solve_batched": (C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(cs_solve_opts),
+                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_int),
+                                   C.POINTER(cs_solve_info), C.c_void_p]),
     "cs_last_error": (C.c_char_p, []),
     "cs_destroy_hierarchy": (None, [C.c_void_p]),
     "cs_destroy_cascade": (None, [C.c_void_p]),

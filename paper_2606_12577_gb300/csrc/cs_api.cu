@@ -17,6 +17,7 @@
 namespace csx {
 
 static thread_local std::string g_err;
+static thread_local bool g_serial_levels = false;
 std::atomic<int64_t> g_launches{0};
 
 void set_error(const char *fmt, ...) {
@@ -469,7 +470,9 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
             }
             return level_setup(0, s);
         };
-        const int nco = c->nlev - 1;
+        // inside cs_setup_many's workers (already one thread per problem) the
+        // levels run one after another on s
+        const int nco = g_serial_levels ? 0 : c->nlev - 1;
         std::vector<cudaStream_t> ls(nco, nullptr);
         std::vector<cudaEvent_t> ev(nco + 1, nullptr);
         std::vector<cs_status> lrc(nco, CS_OK);
@@ -495,6 +498,7 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
                     cudaEventRecord(ev[k + 1], ls[k]);
                 });
             rc = finest();
+            for (int l = nco + 1; l < c->nlev && rc == CS_OK; ++l) rc = level_setup(l, s);
             for (auto &t : th) t.join();
             for (int k = 0; k < nco; ++k) {
                 if (rc == CS_OK && lrc[k] != CS_OK) { rc = lrc[k]; set_error("%s", lmsg[k].c_str()); }
@@ -540,6 +544,67 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
     return CS_OK;
 fail:
     cs_destroy_cascade(c);
+    return rc;
+}
+
+cs_status cs_setup_many(int nprob, const cs_stencil *A, const cs_hierarchy_opts *ho, const cs_cascade_opts *co,
+                        int nthreads, cs_stream stream, cs_hierarchy **h, cs_cascade **c) {
+    if (nprob < 0 || (nprob > 0 && (!A || !ho || !co || !h || !c))) { set_error("null argument"); return CS_ERR_ARG; }
+    for (int p = 0; p < nprob; ++p) { h[p] = nullptr; c[p] = nullptr; }
+    if (nprob == 0) return CS_OK;
+    if (nthreads <= 0) nthreads = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    nthreads = std::min(nthreads, nprob);
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    CSX_CUDA(cudaGetDevice(&dev));
+    cudaEvent_t ready = nullptr;
+    CSX_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ready, s);
+    if (e != cudaSuccess) { cudaEventDestroy(ready); return cuda_fail(e, "setup many", __FILE__, __LINE__); }
+    std::vector<cs_status> prc(nprob, CS_OK);
+    std::vector<std::string> pmsg(nprob);
+    std::vector<cudaStream_t> ws(nthreads, nullptr);
+    std::vector<cudaEvent_t> wd(nthreads, nullptr);
+    std::vector<std::thread> th;
+    for (int k = 0; k < nthreads; ++k)
+        th.emplace_back([&, k] {
+            g_serial_levels = true;
+            cudaError_t te = cudaSetDevice(dev);
+            if (te == cudaSuccess) te = cudaStreamCreateWithFlags(&ws[k], cudaStreamNonBlocking);
+            if (te == cudaSuccess) te = cudaEventCreateWithFlags(&wd[k], cudaEventDisableTiming);
+            if (te == cudaSuccess) te = cudaStreamWaitEvent(ws[k], ready, 0);
+            for (int p = k; p < nprob; p += nthreads) {
+                if (te != cudaSuccess) {
+                    prc[p] = cuda_fail(te, "setup worker", __FILE__, __LINE__);
+                } else {
+                    prc[p] = cs_setup_hierarchy(&A[p], ho, ws[k], &h[p]);
+                    if (prc[p] == CS_OK) prc[p] = cs_setup_cascade(h[p], co, ws[k], &c[p]);
+                }
+                if (prc[p] != CS_OK) pmsg[p] = cs_last_error();
+            }
+            if (wd[k]) cudaEventRecord(wd[k], ws[k]);
+        });
+    for (auto &t : th) t.join();
+    cs_status rc = CS_OK;
+    for (int p = 0; p < nprob && rc == CS_OK; ++p)
+        if (prc[p] != CS_OK) {
+            rc = prc[p];
+            set_error("problem %d: %s", p, pmsg[p].c_str());
+        }
+    for (int k = 0; k < nthreads; ++k) {
+        if (wd[k]) { cudaStreamWaitEvent(s, wd[k], 0); cudaEventDestroy(wd[k]); }
+        if (ws[k]) { if (rc != CS_OK) cudaStreamSynchronize(ws[k]); cudaStreamDestroy(ws[k]); }
+    }
+    cudaEventDestroy(ready);
+    if (rc != CS_OK) {
+        cudaStreamSynchronize(s);
+        for (int p = 0; p < nprob; ++p) {
+            cs_destroy_cascade(c[p]);
+            cs_destroy_hierarchy(h[p]);
+            c[p] = nullptr;
+            h[p] = nullptr;
+        }
+    }
     return rc;
 }
 

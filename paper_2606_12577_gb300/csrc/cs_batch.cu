@@ -1,0 +1,1223 @@
+// Batched solve of many independent problems of uneven size, each with its
+// own right-hand sides: the V-cycles (Algorithm 1) with multiplicative
+// red-black cascade smoothing (eq. fwdm and its reverse), the FP64 residual
+// and the update of every problem run in ONE persistent cooperative kernel
+// per solve, launched from a CUDA graph.  Stages are separated by grid-wide
+// barriers; the levels of all problems are aligned at the coarsest, so that
+// level slot t of the batch holds level t - (D - nlev_p) of problem p
+// (D = the largest level count) and every stage is one ragged sweep over the
+// slot's levels.  Work is dealt out in tiles (a problem, a level, a contiguous
+// range of its grid rows' nodes); the tile size and the CTA size are picked
+// by a measuring autotuner.
+//
+// Data layout: vectors of problem p hold its m_p right-hand sides
+// contiguously per node, v[i * m_p + r] (m_p <= 8); operators and Lambda are
+// the problem's own level arrays (structure of arrays, FP32 or FP64).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "cs_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace csx {
+
+constexpr int BMAXLEV = 16;
+constexpr int BMAXRHS = 8;
+
+template <typename T>
+struct BLevel {
+    int nx, ny, kind, inplace;
+    int64_t N;
+    const T *A;    // [nst][N]
+    const T *lam;  // [nu][N]
+    T *b, *x, *t;  // [N][m]
+};
+
+template <typename T>
+struct BProb {
+    int nlev, m, slot0, cn;
+    const double *A64;   // finest operator, FP64
+    const double *cinv;  // coarsest dense inverse, FP64 row-major
+    double *Z;           // GMRES work vector [N0][m]
+    double *V;           // GMRES basis: restart + 1 vectors of [N0][m]
+    BLevel<T> lev[BMAXLEV];
+};
+
+struct BTile {
+    int p, l, i0, ni;
+};
+
+enum { OP_SWEEP = 0, OP_RESTRICT = 1, OP_COARSE = 2, OP_PROLONG = 3 };
+struct BStep {
+    int op, slot, lv, colour, parity;
+};
+
+struct BCtl {
+    double tol;
+    int maxit;
+    int cnt[2];  // counts of the counting stages, alternating slots
+};
+
+enum { ST_ACTIVE = 0, ST_CONVERGED = 1, ST_DIVERGED = 2, ST_MAXIT = 3 };
+
+struct BArgs {
+    const void *probs;
+    int nprob;
+    const BTile *tiles;      // tiles of slot t: [slot_tile[t], slot_tile[t + 1])
+    const int *slot_tile;
+    int dmax;
+    const BTile *ftiles;     // finest-level tiles; problem p: [ftile_of[p], ftile_of[p + 1])
+    const int *ftile_of;
+    int nftiles;
+    const BStep *steps;
+    int nsteps;
+    const double *const *b64;  // per problem, [N0][m]
+    double *const *x64;
+    double *part;   // [nftiles][BMAXRHS]
+    double *nb;     // [nprob][BMAXRHS]
+    double *rel;    // [nprob][BMAXRHS]
+    double *rel0;   // [nprob]
+    int *state;     // [nprob]
+    int *iters;     // [nprob]
+    int *work;      // [nprob]: the problem takes part in the cycle stages
+    BCtl *ctl;
+    // GMRES (left preconditioned, restarted; per problem and right-hand side q = p * 8 + r)
+    int method, restart, hstride;
+    double *H;      // [q][(restart + 1) * restart]
+    double *cs, *sn, *y;  // [q][restart]
+    double *g;      // [q][restart + 1]
+    double *inv;    // [q]: 1 / ||Z|| of the last normalisation
+    double *nmb;    // [q]: ||M b||
+    int *jcols;     // [q]: Krylov columns built in this cycle
+    int *frozen;    // [q]: no longer extending in this cycle
+};
+
+__device__ __forceinline__ int bcolour(int ix, int iy) { return ((ix + 1) + (iy + 1)) & 1; }
+
+template <int KIND>
+__device__ __forceinline__ void boff(int s, int &dx, int &dy) {
+    if (KIND == STAR) {
+        dx = s == 1 ? -1 : s == 2 ? 1 : 0;
+        dy = s == 3 ? -1 : s == 4 ? 1 : 0;
+    } else {
+        dx = s % 3 - 1;
+        dy = s / 3 - 1;
+    }
+}
+
+// (A v)_{i,r} for r < m at node (ix, iy); neighbours outside contribute nothing
+template <int KIND, typename T, typename TA>
+__device__ __forceinline__ void row_apply(int nx, int ny, int64_t N, const TA *__restrict__ A, const T *v, int m,
+                                          int ix, int iy, int64_t i, T (&ax)[BMAXRHS]) {
+    constexpr int NST = KIND == STAR ? 5 : 9;
+#pragma unroll
+    for (int r = 0; r < BMAXRHS; ++r) ax[r] = T(0);
+#pragma unroll
+    for (int s = 0; s < NST; ++s) {
+        int dx, dy;
+        boff<KIND>(s, dx, dy);
+        const bool in = (unsigned)(ix + dx) < (unsigned)nx && (unsigned)(iy + dy) < (unsigned)ny;
+        const T a = (T)A[(int64_t)s * N + i];
+        const int64_t j = i + dx + (int64_t)nx * dy;
+#pragma unroll
+        for (int r = 0; r < BMAXRHS; ++r)
+            if (r < m) ax[r] = fma(a, in ? v[j * m + r] : T(0), ax[r]);
+    }
+}
+
+// deterministic CTA sum of m <= 8 values per thread into out[0..m)
+__device__ __forceinline__ void cta_sum8(double (&v)[BMAXRHS], int m, double (*red)[BMAXRHS], double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int r = 0; r < BMAXRHS; ++r)
+        for (int o = 16; o > 0; o >>= 1) v[r] += __shfl_down_sync(0xffffffffu, v[r], o);
+    if (lane == 0)
+#pragma unroll
+        for (int r = 0; r < BMAXRHS; ++r) red[warp][r] = v[r];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int r = 0; r < BMAXRHS; ++r) {
+            double t = lane < nw ? red[lane][r] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0 && r < m) out[r] = t;
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------- stages
+template <typename T, int KIND>
+__device__ __forceinline__ void sweep_node(const BLevel<T> &L, int m, int64_t i, int lv, int colour, const T *src,
+                                           T *dst) {
+    const int ix = (int)i % L.nx, iy = (int)i / L.nx;
+    if (bcolour(ix, iy) != colour) {
+        if (src != dst)
+            for (int r = 0; r < m; ++r) dst[i * m + r] = src[i * m + r];
+        return;
+    }
+    T ax[BMAXRHS];
+    row_apply<KIND, T, T>(L.nx, L.ny, L.N, L.A, src, m, ix, iy, i, ax);
+    const T lam = L.lam[(int64_t)lv * L.N + i];
+#pragma unroll
+    for (int r = 0; r < BMAXRHS; ++r)
+        if (r < m) {
+            const T res = ax[r] - L.b[i * m + r];
+            dst[i * m + r] = src[i * m + r] - lam * res;
+        }
+}
+
+// coarse node I of level l+1: b_c = 2^-2 sum_f P_{f,I} (A x - b)_f, x_c = 0
+template <typename T, int KIND>
+__device__ __forceinline__ void restrict_node(const BLevel<T> &F, const BLevel<T> &C, int m, int64_t I) {
+    const int cx = (int)I % C.nx, cy = (int)I / C.nx;
+    T acc[BMAXRHS];
+#pragma unroll
+    for (int r = 0; r < BMAXRHS; ++r) acc[r] = T(0);
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int fy = 2 * cy + 1 + dy;
+        if (fy >= F.ny) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int fx = 2 * cx + 1 + dx;
+            if (fx >= F.nx) continue;
+            const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0));
+            const int64_t f = fx + (int64_t)F.nx * fy;
+            T ax[BMAXRHS];
+            row_apply<KIND, T, T>(F.nx, F.ny, F.N, F.A, F.x, m, fx, fy, f, ax);
+#pragma unroll
+            for (int r = 0; r < BMAXRHS; ++r)
+                if (r < m) acc[r] = fma(w, ax[r] - F.b[f * m + r], acc[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < BMAXRHS; ++r)
+        if (r < m) {
+            C.b[I * m + r] = acc[r] * T(0.25);
+            C.x[I * m + r] = T(0);
+        }
+}
+
+// 1D interpolation weights of fine node f from the coarse nodes (see the
+// single-problem prolongation): odd f sits on coarse (f-1)/2, even f takes
+// half of coarse f/2-1 and f/2 where present.
+__device__ __forceinline__ int bp1d(int f, int nc, int *c, float *w) {
+    if (f & 1) {
+        c[0] = (f - 1) >> 1;
+        w[0] = 1.f;
+        return 1;
+    }
+    int k = 0;
+    const int lo = (f >> 1) - 1, hi = f >> 1;
+    if (lo >= 0) { c[k] = lo; w[k] = 0.5f; ++k; }
+    if (hi < nc) { c[k] = hi; w[k] = 0.5f; ++k; }
+    return k;
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong_node(const BLevel<T> &F, const BLevel<T> &C, int m, int64_t f) {
+    const int fx = (int)f % F.nx, fy = (int)f / F.nx;
+    int cxs[2], cys[2];
+    float wx[2], wy[2];
+    const int kx = bp1d(fx, C.nx, cxs, wx), ky = bp1d(fy, C.ny, cys, wy);
+    T acc[BMAXRHS];
+#pragma unroll
+    for (int r = 0; r < BMAXRHS; ++r) acc[r] = T(0);
+    for (int bb = 0; bb < ky; ++bb)
+        for (int a = 0; a < kx; ++a) {
+            const T w = T(wx[a] * wy[bb] * 1.f);
+            const int64_t c = cxs[a] + (int64_t)C.nx * cys[bb];
+#pragma unroll
+            for (int r = 0; r < BMAXRHS; ++r)
+                if (r < m) acc[r] = fma(w, C.x[c * m + r], acc[r]);
+        }
+#pragma unroll
+    for (int r = 0; r < BMAXRHS; ++r)
+        if (r < m) F.x[f * m + r] = F.x[f * m + r] - acc[r];
+}
+
+template <typename T>
+__device__ void stage_step(const BArgs &a, const BProb<T> *P, const BStep st) {
+    const int tslot = st.op == OP_RESTRICT ? st.slot + 1 : st.slot;
+    const int t0 = a.slot_tile[tslot], t1 = a.slot_tile[tslot + 1];
+    for (int k = t0 + blockIdx.x; k < t1; k += gridDim.x) {
+        const BTile tile = a.tiles[k];
+        if (__ldcg(a.work + tile.p) == 0) continue;
+        const BProb<T> &pr = P[tile.p];
+        const int m = pr.m;
+        if (st.op == OP_SWEEP) {
+            const BLevel<T> &L = pr.lev[tile.l];
+            const T *src = L.inplace || st.parity == 0 ? L.x : L.t;
+            T *dst = L.inplace || st.parity == 1 ? L.x : L.t;
+            for (int ii = threadIdx.x; ii < tile.ni; ii += blockDim.x) {
+                const int64_t i = tile.i0 + ii;
+                if (L.kind == STAR) sweep_node<T, STAR>(L, m, i, st.lv, st.colour, src, dst);
+                else sweep_node<T, BOX>(L, m, i, st.lv, st.colour, src, dst);
+            }
+        } else if (st.op == OP_RESTRICT) {
+            if (tile.l == 0) continue;  // this problem's finest level starts at the coarse slot
+            const BLevel<T> &F = pr.lev[tile.l - 1], &C = pr.lev[tile.l];
+            for (int ii = threadIdx.x; ii < tile.ni; ii += blockDim.x) {
+                const int64_t I = tile.i0 + ii;
+                if (F.kind == STAR) restrict_node<T, STAR>(F, C, m, I);
+                else restrict_node<T, BOX>(F, C, m, I);
+            }
+        } else if (st.op == OP_COARSE) {
+            const BLevel<T> &L = pr.lev[tile.l];
+            const int n = pr.cn;
+            for (int ii = threadIdx.x; ii < tile.ni; ii += blockDim.x) {
+                const int i = tile.i0 + ii;
+                for (int r = 0; r < m; ++r) {
+                    double s = 0.0;
+                    for (int j = 0; j < n; ++j) s = fma(pr.cinv[(int64_t)i * n + j], (double)L.b[(int64_t)j * m + r], s);
+                    L.x[(int64_t)i * m + r] = (T)s;
+                }
+            }
+        } else {  // OP_PROLONG
+            const BLevel<T> &F = pr.lev[tile.l], &C = pr.lev[tile.l + 1];
+            for (int ii = threadIdx.x; ii < tile.ni; ii += blockDim.x) prolong_node<T>(F, C, m, tile.i0 + ii);
+        }
+    }
+}
+
+// finest-level FP64 stages over the finest tiles.  Stages marked (A) run
+// for every problem still iterating (state active); (W) ones only for
+// problems with a right-hand side still extending its Krylov space in the
+// current GMRES cycle (for the refinement method W = A).
+enum {
+    F_BNORM = 0,   // (A) partial sums of b^2
+    F_ZEROX,       // (A) x = 0 for right-hand sides with b = 0
+    F_RESID,       // (A) r = b - A x in FP64 -> cycle input (T), cycle output = 0; partial sums of r^2
+    F_UPDATE,      // (A) x += cycle output (refinement)
+    F_MB,          // (A) cycle input = b, output = 0 (for ||M b||)
+    F_CONVZ,       // (W) Z = cycle output in FP64; partial sums of Z^2
+    F_MATVEC,      // (W) cycle input = A V_j, output = 0
+    F_DOT,         // (W) partial sums of <Z, V_i>
+    F_AXPY,        // (W) Z -= h_ij V_i
+    F_NRMZ,        // (W) partial sums of Z^2
+    F_SCALEV,      // (W) V_j = Z / ||Z||
+    F_XUPD         // (A) x += sum_k y_k V_k
+};
+
+__device__ __forceinline__ bool fine_gate_all(int what) {
+    return what == F_BNORM || what == F_ZEROX || what == F_RESID || what == F_UPDATE || what == F_MB ||
+           what == F_XUPD;
+}
+
+template <typename T, int KIND>
+__device__ __forceinline__ void resid_node(const BArgs &a, const BProb<T> &pr, int p, int64_t i, const double *xv,
+                                           bool with_b, double (&acc)[BMAXRHS]) {
+    const BLevel<T> &L = pr.lev[0];
+    const int m = pr.m;
+    const int ix = (int)i % L.nx, iy = (int)i / L.nx;
+    double ax[BMAXRHS];
+    row_apply<KIND, double, double>(L.nx, L.ny, L.N, pr.A64, xv, m, ix, iy, i, ax);
+    const double *b = a.b64[p];
+#pragma unroll
+    for (int r = 0; r < BMAXRHS; ++r)
+        if (r < m) {
+            const double v = with_b ? b[i * m + r] - ax[r] : ax[r];
+            acc[r] = fma(v, v, acc[r]);
+            L.b[i * m + r] = (T)v;
+            L.x[i * m + r] = T(0);
+        }
+}
+
+template <typename T>
+__device__ void stage_fine(const BArgs &a, const BProb<T> *P, int what, int iarg, int jarg,
+                           double (*red)[BMAXRHS]) {
+    const bool gate_all = fine_gate_all(what);
+    for (int k = blockIdx.x; k < a.nftiles; k += gridDim.x) {
+        const BTile tile = a.ftiles[k];
+        const int p = tile.p;
+        // uniform over the CTA: the flags change only in the per-problem stages
+        if (gate_all ? __ldcg(a.state + p) != ST_ACTIVE : __ldcg(a.work + p) == 0) continue;
+        const BProb<T> &pr = P[p];
+        const BLevel<T> &L = pr.lev[0];
+        const int m = pr.m;
+        const int64_t nm = L.N * m;
+        const int q0 = p * BMAXRHS;
+        double acc[BMAXRHS];
+#pragma unroll
+        for (int r = 0; r < BMAXRHS; ++r) acc[r] = 0.0;
+        for (int ii = threadIdx.x; ii < tile.ni; ii += blockDim.x) {
+            const int64_t i = tile.i0 + ii;
+            if (what == F_BNORM) {
+                const double *b = a.b64[p];
+#pragma unroll
+                for (int r = 0; r < BMAXRHS; ++r)
+                    if (r < m) acc[r] = fma(b[i * m + r], b[i * m + r], acc[r]);
+            } else if (what == F_ZEROX) {
+                for (int r = 0; r < m; ++r)
+                    if (a.nb[q0 + r] == 0.0) a.x64[p][i * m + r] = 0.0;
+            } else if (what == F_RESID || what == F_MATVEC) {
+                const double *xv = what == F_RESID ? a.x64[p] : pr.V + (int64_t)jarg * nm;
+                if (L.kind == STAR) resid_node<T, STAR>(a, pr, p, i, xv, what == F_RESID, acc);
+                else resid_node<T, BOX>(a, pr, p, i, xv, what == F_RESID, acc);
+            } else if (what == F_UPDATE) {
+                double *x = a.x64[p];
+                for (int r = 0; r < m; ++r) x[i * m + r] += (double)L.x[i * m + r];
+            } else if (what == F_MB) {
+                const double *b = a.b64[p];
+                for (int r = 0; r < m; ++r) {
+                    L.b[i * m + r] = (T)b[i * m + r];
+                    L.x[i * m + r] = T(0);
+                }
+            } else if (what == F_CONVZ) {
+#pragma unroll
+                for (int r = 0; r < BMAXRHS; ++r)
+                    if (r < m) {
+                        const double z = (double)L.x[i * m + r];
+                        pr.Z[i * m + r] = z;
+                        acc[r] = fma(z, z, acc[r]);
+                    }
+            } else if (what == F_DOT) {
+                const double *Vi = pr.V + (int64_t)iarg * nm;
+#pragma unroll
+                for (int r = 0; r < BMAXRHS; ++r)
+                    if (r < m) acc[r] = fma(pr.Z[i * m + r], Vi[i * m + r], acc[r]);
+            } else if (what == F_AXPY) {
+                const double *Vi = pr.V + (int64_t)iarg * nm;
+                for (int r = 0; r < m; ++r)
+                    if (!a.frozen[q0 + r]) {
+                        const double h = a.H[(int64_t)(q0 + r) * a.hstride + iarg * a.restart + jarg];
+                        pr.Z[i * m + r] = fma(-h, Vi[i * m + r], pr.Z[i * m + r]);
+                    }
+            } else if (what == F_NRMZ) {
+#pragma unroll
+                for (int r = 0; r < BMAXRHS; ++r)
+                    if (r < m) acc[r] = fma(pr.Z[i * m + r], pr.Z[i * m + r], acc[r]);
+            } else if (what == F_SCALEV) {
+                double *Vj = pr.V + (int64_t)jarg * nm;
+                for (int r = 0; r < m; ++r)
+                    if (!a.frozen[q0 + r] || jarg == 0) Vj[i * m + r] = pr.Z[i * m + r] * a.inv[q0 + r];
+            } else {  // F_XUPD
+                double *x = a.x64[p];
+                for (int r = 0; r < m; ++r) {
+                    const int nc = a.jcols[q0 + r];
+                    double sx = x[i * m + r];
+                    for (int kk = 0; kk < nc; ++kk)
+                        sx = fma(a.y[(int64_t)(q0 + r) * a.restart + kk], pr.V[(int64_t)kk * nm + i * m + r], sx);
+                    x[i * m + r] = sx;
+                }
+            }
+        }
+        if (what == F_BNORM || what == F_RESID || what == F_CONVZ || what == F_DOT || what == F_NRMZ)
+            cta_sum8(acc, m, red, a.part + (int64_t)k * BMAXRHS);
+    }
+}
+
+// Per-problem stages (one thread per problem, its right-hand sides in turn):
+// they sum the problem's tile partials in tile order and advance the small
+// per-right-hand-side state.  Stages that count write ctl->cnt[ph] and clear
+// ctl->cnt[ph ^ 1] (read before the barriers that precede this stage).
+enum {
+    P_NORMB = 0,  // ||b||
+    P_NORM,       // true relative residuals: convergence, divergence, limit; counts active problems
+    P_NMB,        // ||M b|| (GMRES stopping estimate scale)
+    P_BETA,       // beta = ||M r||, g = beta e_1, V_0 scale; counts extending right-hand sides
+    P_HSTORE,     // H(i, j) = <Z, V_i>
+    P_GIVENS,     // H(j+1, j) = ||Z||, rotations, g, freeze; counts extending right-hand sides
+    P_SOLVEY      // y = H^{-1} g (back substitution over the columns built)
+};
+
+template <typename T>
+__device__ void stage_prob(const BArgs &a, const BProb<T> *P, int what, int iarg, int jarg, int ph, bool first) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((what == P_NORM || what == P_BETA || what == P_GIVENS) && gid == 0) a.ctl->cnt[ph ^ 1] = 0;
+    const int R = a.restart;
+    for (int p = gid; p < a.nprob; p += gridDim.x * blockDim.x) {
+        if (a.state[p] != ST_ACTIVE) continue;
+        if ((what == P_HSTORE || what == P_GIVENS) && !a.work[p]) continue;
+        const int m = P[p].m;
+        const int q0 = p * BMAXRHS;
+        double ss[BMAXRHS];
+#pragma unroll
+        for (int r = 0; r < BMAXRHS; ++r) ss[r] = 0.0;
+        if (what != P_SOLVEY)
+            for (int k = a.ftile_of[p]; k < a.ftile_of[p + 1]; ++k)
+#pragma unroll
+                for (int r = 0; r < BMAXRHS; ++r)
+                    if (r < m) ss[r] += __ldcg(a.part + (int64_t)k * BMAXRHS + r);
+        if (what == P_NORMB) {
+#pragma unroll
+            for (int r = 0; r < BMAXRHS; ++r)
+                if (r < m) a.nb[q0 + r] = sqrt(ss[r]);
+        } else if (what == P_NMB) {
+#pragma unroll
+            for (int r = 0; r < BMAXRHS; ++r)
+                if (r < m) a.nmb[q0 + r] = sqrt(ss[r]);
+        } else if (what == P_NORM) {
+            double worst = 0.0;
+            bool conv = true, bad = false;
+#pragma unroll
+            for (int r = 0; r < BMAXRHS; ++r) {
+                if (r >= m) break;
+                const double nb = a.nb[q0 + r];
+                const double rel = nb > 0.0 ? sqrt(ss[r]) / nb : 0.0;
+                a.rel[q0 + r] = rel;
+                if (!(rel <= a.ctl->tol)) conv = false;
+                if (!isfinite(rel)) bad = true;
+                worst = fmax(worst, rel);
+            }
+            if (first) a.rel0[p] = worst;
+            if (!first && a.method == CS_REFINE) a.iters[p] += 1;
+            int st = ST_ACTIVE;
+            if (conv) st = ST_CONVERGED;
+            else if (bad || (a.method == CS_REFINE && worst > 1e3 * fmax(a.rel0[p], 1.0))) st = ST_DIVERGED;
+            else if (a.iters[p] >= a.ctl->maxit) st = ST_MAXIT;
+            a.state[p] = st;
+            a.work[p] = st == ST_ACTIVE;
+            if (st == ST_ACTIVE) atomicAdd(&a.ctl->cnt[ph], 1);
+        } else if (what == P_BETA) {
+            int ext = 0;
+#pragma unroll
+            for (int r = 0; r < BMAXRHS; ++r) {
+                if (r >= m) break;
+                const int q = q0 + r;
+                const double beta = sqrt(ss[r]);
+                a.g[(int64_t)q * (R + 1)] = beta;
+                a.inv[q] = beta > 0.0 ? 1.0 / sqrt(ss[r]) : 0.0;
+                a.jcols[q] = 0;
+                a.frozen[q] = !(beta > 0.0) || a.iters[p] >= a.ctl->maxit;
+                ext += !a.frozen[q];
+            }
+            a.work[p] = ext > 0;
+            if (ext) atomicAdd(&a.ctl->cnt[ph], ext);
+        } else if (what == P_HSTORE) {
+#pragma unroll
+            for (int r = 0; r < BMAXRHS; ++r)
+                if (r < m && !a.frozen[q0 + r]) a.H[(int64_t)(q0 + r) * a.hstride + iarg * R + jarg] = ss[r];
+        } else if (what == P_GIVENS) {
+            const int j = jarg;
+            a.iters[p] += 1;
+            const bool limit = a.iters[p] >= a.ctl->maxit;
+            int ext = 0;
+#pragma unroll
+            for (int r = 0; r < BMAXRHS; ++r) {
+                if (r >= m) break;
+                const int q = q0 + r;
+                if (a.frozen[q]) continue;
+                double *H = a.H + (int64_t)q * a.hstride;
+                double *cs = a.cs + (int64_t)q * R, *sn = a.sn + (int64_t)q * R, *g = a.g + (int64_t)q * (R + 1);
+                const double hn = sqrt(ss[r]);
+                a.inv[q] = hn > 0.0 ? 1.0 / sqrt(ss[r]) : 0.0;
+                H[(j + 1) * R + j] = hn;
+                for (int i = 0; i < j; ++i) {
+                    const double x0 = H[i * R + j], x1 = H[(i + 1) * R + j];
+                    H[i * R + j] = cs[i] * x0 + sn[i] * x1;
+                    H[(i + 1) * R + j] = -sn[i] * x0 + cs[i] * x1;
+                }
+                const double x0 = H[j * R + j], x1 = H[(j + 1) * R + j];
+                const double d = sqrt(x0 * x0 + x1 * x1);
+                cs[j] = d > 0 ? x0 / d : 1.0;
+                sn[j] = d > 0 ? x1 / d : 0.0;
+                H[j * R + j] = d;
+                H[(j + 1) * R + j] = 0.0;
+                g[j + 1] = -sn[j] * g[j];
+                g[j] = cs[j] * g[j];
+                a.jcols[q] = j + 1;
+                if (fabs(g[j + 1]) <= a.ctl->tol * a.nmb[q] || hn == 0.0 || limit || j + 1 >= R) a.frozen[q] = 1;
+                else ++ext;
+            }
+            a.work[p] = ext > 0;
+            if (ext) atomicAdd(&a.ctl->cnt[ph], ext);
+        } else {  // P_SOLVEY
+            for (int r = 0; r < m; ++r) {
+                const int q = q0 + r;
+                const double *H = a.H + (int64_t)q * a.hstride, *g = a.g + (int64_t)q * (R + 1);
+                double *y = a.y + (int64_t)q * R;
+                const int nc = a.jcols[q];
+                for (int i = nc - 1; i >= 0; --i) {
+                    double sum = g[i];
+                    for (int k = i + 1; k < nc; ++k) sum -= H[i * R + k] * y[k];
+                    y[i] = sum / H[i * R + i];
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void vcycle_stages(const BArgs &a, const BProb<T> *P, cg::grid_group &grid) {
+    for (int s = 0; s < a.nsteps; ++s) {
+        stage_step<T>(a, P, a.steps[s]);
+        grid.sync();
+    }
+}
+
+// The whole solve: every CTA runs every stage and passes every grid barrier
+// (no early exit anywhere).  Each loop ends for all CTAs at once: the count
+// it tests was written before the barrier that precedes the test (and is
+// cleared only by a later counting stage), and every loop is bounded by the
+// iteration limit in any case.
+template <typename T>
+__global__ void __launch_bounds__(512, 1) k_batch_solve(BArgs a) {
+    cg::grid_group grid = cg::this_grid();
+    __shared__ double red[16][BMAXRHS];
+    const BProb<T> *P = static_cast<const BProb<T> *>(a.probs);
+    const int maxit = a.ctl->maxit;
+    // counting stages write ctl->cnt[ph] after flipping ph and clear the other
+    // slot; the loop tests read the slot written last
+    int ph = 0;
+    stage_fine<T>(a, P, F_BNORM, 0, 0, red);
+    grid.sync();
+    stage_prob<T>(a, P, P_NORMB, 0, 0, ph, true);
+    grid.sync();
+    stage_fine<T>(a, P, F_ZEROX, 0, 0, red);
+    grid.sync();
+    if (a.method == CS_GMRES) {  // ||M b|| per right-hand side
+        stage_fine<T>(a, P, F_MB, 0, 0, red);
+        grid.sync();
+        vcycle_stages<T>(a, P, grid);
+        stage_fine<T>(a, P, F_CONVZ, 0, 0, red);
+        grid.sync();
+        stage_prob<T>(a, P, P_NMB, 0, 0, ph, true);
+        grid.sync();
+    }
+    stage_fine<T>(a, P, F_RESID, 0, 0, red);
+    grid.sync();
+    ph ^= 1;
+    stage_prob<T>(a, P, P_NORM, 0, 0, ph, true);
+    grid.sync();
+    if (a.method != CS_GMRES) {
+        for (int it = 0; it < maxit; ++it) {
+            if (__ldcg(&a.ctl->cnt[ph]) == 0) break;  // active problems
+            vcycle_stages<T>(a, P, grid);
+            stage_fine<T>(a, P, F_UPDATE, 0, 0, red);
+            grid.sync();
+            stage_fine<T>(a, P, F_RESID, 0, 0, red);
+            grid.sync();
+            ph ^= 1;
+            stage_prob<T>(a, P, P_NORM, 0, 0, ph, false);
+            grid.sync();
+        }
+        return;
+    }
+    const int R = a.restart;
+    for (int cyc = 0; cyc <= maxit; ++cyc) {
+        if (__ldcg(&a.ctl->cnt[ph]) == 0) break;  // active problems
+        vcycle_stages<T>(a, P, grid);  // M r (the cycle input is r from F_RESID)
+        stage_fine<T>(a, P, F_CONVZ, 0, 0, red);
+        grid.sync();
+        ph ^= 1;
+        stage_prob<T>(a, P, P_BETA, 0, 0, ph, false);
+        grid.sync();
+        stage_fine<T>(a, P, F_SCALEV, 0, 0, red);
+        grid.sync();
+        for (int j = 0; j < R; ++j) {
+            if (__ldcg(&a.ctl->cnt[ph]) == 0) break;  // right-hand sides still extending
+            stage_fine<T>(a, P, F_MATVEC, 0, j, red);
+            grid.sync();
+            vcycle_stages<T>(a, P, grid);
+            stage_fine<T>(a, P, F_CONVZ, 0, 0, red);
+            grid.sync();
+            for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt
+                stage_fine<T>(a, P, F_DOT, i, j, red);
+                grid.sync();
+                stage_prob<T>(a, P, P_HSTORE, i, j, ph, false);
+                grid.sync();
+                stage_fine<T>(a, P, F_AXPY, i, j, red);
+                grid.sync();
+            }
+            stage_fine<T>(a, P, F_NRMZ, 0, j, red);
+            grid.sync();
+            ph ^= 1;
+            stage_prob<T>(a, P, P_GIVENS, 0, j, ph, false);
+            grid.sync();
+            stage_fine<T>(a, P, F_SCALEV, 0, j + 1, red);
+            grid.sync();
+        }
+        // every problem still active solves its small systems and updates x
+        // (work flags may have cleared: these stages are gated on the state)
+        stage_prob<T>(a, P, P_SOLVEY, 0, 0, ph, false);
+        grid.sync();
+        stage_fine<T>(a, P, F_XUPD, 0, 0, red);
+        grid.sync();
+        stage_fine<T>(a, P, F_RESID, 0, 0, red);
+        grid.sync();
+        ph ^= 1;
+        stage_prob<T>(a, P, P_NORM, 0, 0, ph, false);
+        grid.sync();
+    }
+}
+
+}  // namespace csx
+
+using namespace csx;
+
+struct cs_batch {
+    int nprob = 0, dmax = 0, precision = CS_FP32, order = CS_RF, mu_pre = 1, mu_post = 1, nu = 1;
+    int dev = 0;
+    std::vector<int> m, nlev, slot0;
+    std::vector<int64_t> nfine;
+    std::vector<std::vector<int>> nx, ny;  // per problem per level
+    void *probs = nullptr;
+    size_t probs_bytes = 0;
+    std::vector<unsigned char> hprobs;
+    void *vec = nullptr;  // all multi-RHS level vectors
+    BTile *tiles = nullptr, *ftiles = nullptr;
+    int *slot_tile = nullptr, *ftile_of = nullptr;
+    int ntiles = 0, nftiles = 0;
+    BStep *steps = nullptr;
+    int nsteps = 0;
+    double *part = nullptr, *nb = nullptr, *rel = nullptr, *rel0 = nullptr;
+    int *state = nullptr, *iters = nullptr, *work = nullptr;
+    BCtl *ctl = nullptr;
+    int method = CS_REFINE, restart = 0;
+    void *gm = nullptr;   // GMRES basis and work vectors of all problems
+    void *gsm = nullptr;  // GMRES per-right-hand-side small state
+    double *H = nullptr, *gcs = nullptr, *gsn = nullptr, *gy = nullptr, *gg = nullptr, *ginv = nullptr,
+           *gnmb = nullptr;
+    int *jcols = nullptr, *frozen = nullptr;
+    const double **bptr = nullptr;
+    double **xptr = nullptr;
+    // pinned host staging
+    void *hstage = nullptr;
+    size_t hstage_bytes = 0;
+    int threads = 256, tile_nodes = 1024, ctas = 0;
+    std::vector<cs_batch_tune> tuned;
+    cudaGraphExec_t graph = nullptr;
+    int graph_cfg_threads = 0, graph_cfg_tile = 0;
+    bool graph_ok = true;
+    double *tune_b = nullptr, *tune_x = nullptr;
+    int64_t bytes = 0;
+};
+
+namespace {
+
+template <typename T>
+void *kernel_ptr() {
+    return reinterpret_cast<void *>(&k_batch_solve<T>);
+}
+
+void *kernel_of(const cs_batch *B) {
+    return B->precision == CS_FP32 ? kernel_ptr<float>() : kernel_ptr<double>();
+}
+
+// tiles of tile_nodes nodes over every (problem, level) of each slot, and
+// over every problem's finest level
+cs_status build_tiles(cs_batch *B, int tile_nodes, cudaStream_t s) {
+    std::vector<BTile> tl;
+    std::vector<int> st(B->dmax + 1, 0);
+    for (int t = 0; t < B->dmax; ++t) {
+        st[t] = (int)tl.size();
+        for (int p = 0; p < B->nprob; ++p) {
+            const int l = t - B->slot0[p];
+            if (l < 0) continue;
+            const int64_t n = (int64_t)B->nx[p][l] * B->ny[p][l];
+            for (int64_t i0 = 0; i0 < n; i0 += tile_nodes)
+                tl.push_back({p, l, (int)i0, (int)std::min<int64_t>(tile_nodes, n - i0)});
+        }
+    }
+    st[B->dmax] = (int)tl.size();
+    std::vector<BTile> ft;
+    std::vector<int> fo(B->nprob + 1, 0);
+    for (int p = 0; p < B->nprob; ++p) {
+        fo[p] = (int)ft.size();
+        const int64_t n = B->nfine[p];
+        for (int64_t i0 = 0; i0 < n; i0 += tile_nodes)
+            ft.push_back({p, 0, (int)i0, (int)std::min<int64_t>(tile_nodes, n - i0)});
+    }
+    fo[B->nprob] = (int)ft.size();
+    dfree(B->tiles, s); dfree(B->ftiles, s); dfree(B->slot_tile, s); dfree(B->ftile_of, s); dfree(B->part, s);
+    B->tiles = nullptr; B->ftiles = nullptr; B->slot_tile = nullptr; B->ftile_of = nullptr; B->part = nullptr;
+    CSX_TRY(dalloc_t(&B->tiles, tl.size(), nullptr, s));
+    CSX_TRY(dalloc_t(&B->ftiles, ft.size(), nullptr, s));
+    CSX_TRY(dalloc_t(&B->slot_tile, st.size(), nullptr, s));
+    CSX_TRY(dalloc_t(&B->ftile_of, fo.size(), nullptr, s));
+    CSX_TRY(dalloc_t(&B->part, ft.size() * BMAXRHS, nullptr, s));
+    CSX_CUDA(cudaMemcpyAsync(B->tiles, tl.data(), tl.size() * sizeof(BTile), cudaMemcpyHostToDevice, s));
+    CSX_CUDA(cudaMemcpyAsync(B->ftiles, ft.data(), ft.size() * sizeof(BTile), cudaMemcpyHostToDevice, s));
+    CSX_CUDA(cudaMemcpyAsync(B->slot_tile, st.data(), st.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CSX_CUDA(cudaMemcpyAsync(B->ftile_of, fo.data(), fo.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CSX_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+    B->ntiles = (int)tl.size();
+    B->nftiles = (int)ft.size();
+    B->tile_nodes = tile_nodes;
+    return CS_OK;
+}
+
+BArgs args_of(const cs_batch *B) {
+    BArgs a;
+    a.probs = B->probs;
+    a.nprob = B->nprob;
+    a.tiles = B->tiles;
+    a.slot_tile = B->slot_tile;
+    a.dmax = B->dmax;
+    a.ftiles = B->ftiles;
+    a.ftile_of = B->ftile_of;
+    a.nftiles = B->nftiles;
+    a.steps = B->steps;
+    a.nsteps = B->nsteps;
+    a.b64 = B->bptr;
+    a.x64 = B->xptr;
+    a.part = B->part;
+    a.nb = B->nb;
+    a.rel = B->rel;
+    a.rel0 = B->rel0;
+    a.state = B->state;
+    a.iters = B->iters;
+    a.work = B->work;
+    a.ctl = B->ctl;
+    a.method = B->method;
+    a.restart = B->restart;
+    a.hstride = (B->restart + 1) * B->restart;
+    a.H = B->H;
+    a.cs = B->gcs;
+    a.sn = B->gsn;
+    a.y = B->gy;
+    a.g = B->gg;
+    a.inv = B->ginv;
+    a.nmb = B->gnmb;
+    a.jcols = B->jcols;
+    a.frozen = B->frozen;
+    return a;
+}
+
+// CTAs that can be co-resident (a cooperative launch needs all of them)
+cs_status coresident(const cs_batch *B, int threads, int *ctas) {
+    int nsm = 0, per = 0;
+    CSX_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, B->dev));
+    CSX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel_of(B), threads, 0));
+    if (per < 1) {
+        set_error("batched solve kernel cannot run %d threads per CTA", threads);
+        return CS_ERR_UNSUPPORTED;
+    }
+    *ctas = per * nsm;
+    return CS_OK;
+}
+
+cs_status launch(cs_batch *B, cudaStream_t s) {
+    BArgs a = args_of(B);
+    void *params[] = {&a};
+    CSX_CUDA(cudaLaunchCooperativeKernel(kernel_of(B), dim3((unsigned)B->ctas), dim3((unsigned)B->threads), params, 0,
+                                         s));
+    count_launch();
+    return CS_OK;
+}
+
+// per-solve control: tolerance, iteration limit, zeroed counters and states
+cs_status reset_control(cs_batch *B, double tol, int maxit, cudaStream_t s) {
+    BCtl c;
+    c.tol = tol;
+    c.maxit = maxit;
+    c.cnt[0] = c.cnt[1] = 0;
+    std::memcpy(B->hstage, &c, sizeof(c));
+    CSX_CUDA(cudaMemcpyAsync(B->ctl, B->hstage, sizeof(c), cudaMemcpyHostToDevice, s));
+    CSX_CUDA(cudaMemsetAsync(B->state, 0, sizeof(int) * B->nprob, s));
+    CSX_CUDA(cudaMemsetAsync(B->iters, 0, sizeof(int) * B->nprob, s));
+    CSX_CUDA(cudaMemsetAsync(B->work, 1, sizeof(int) * B->nprob, s));  // nonzero: every problem takes part
+    return CS_OK;
+}
+
+cs_status set_pointers(cs_batch *B, const double *const *b, double *const *x, cudaStream_t s) {
+    char *h = static_cast<char *>(B->hstage) + 64;
+    std::memcpy(h, b, sizeof(double *) * B->nprob);
+    std::memcpy(h + sizeof(double *) * B->nprob, x, sizeof(double *) * B->nprob);
+    CSX_CUDA(cudaMemcpyAsync(B->bptr, h, sizeof(double *) * B->nprob, cudaMemcpyHostToDevice, s));
+    CSX_CUDA(cudaMemcpyAsync(B->xptr, h + sizeof(double *) * B->nprob, sizeof(double *) * B->nprob,
+                             cudaMemcpyHostToDevice, s));
+    return CS_OK;
+}
+
+// the kernel, captured once per configuration into a graph; if capturing a
+// cooperative launch is refused, it is launched directly
+cs_status run(cs_batch *B, cudaStream_t s) {
+    if (B->graph && (B->graph_cfg_threads != B->threads || B->graph_cfg_tile != B->tile_nodes)) {
+        cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+    }
+    if (!B->graph && B->graph_ok) {
+        cudaStream_t cs = nullptr;
+        CSX_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            BArgs a = args_of(B);
+            void *params[] = {&a};
+            cudaError_t le = cudaLaunchCooperativeKernel(kernel_of(B), dim3((unsigned)B->ctas),
+                                                         dim3((unsigned)B->threads), params, 0, cs);
+            e = cudaStreamEndCapture(cs, &g);
+            if (le != cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&B->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            B->graph = nullptr;
+            B->graph_ok = false;
+        } else {
+            B->graph_cfg_threads = B->threads;
+            B->graph_cfg_tile = B->tile_nodes;
+        }
+    }
+    if (B->graph) {
+        CSX_CUDA(cudaGraphLaunch(B->graph, s));
+        count_launch();
+        return CS_OK;
+    }
+    return launch(B, s);
+}
+
+void build_steps(const cs_batch *B, std::vector<BStep> &out) {
+    const bool rf = B->order == CS_RF;
+    for (int t = 0; t + 1 < B->dmax; ++t) {
+        for (int mu = 0; mu < B->mu_pre; ++mu)
+            for (int step = 0; step < B->nu; ++step)
+                for (int kk = 0; kk < 2; ++kk)
+                    out.push_back({OP_SWEEP, t, rf ? B->nu - 1 - step : step, rf ? 1 - kk : kk, kk});
+        out.push_back({OP_RESTRICT, t, 0, 0, 0});
+    }
+    out.push_back({OP_COARSE, B->dmax - 1, 0, 0, 0});
+    for (int t = B->dmax - 2; t >= 0; --t) {
+        out.push_back({OP_PROLONG, t, 0, 0, 0});
+        for (int mu = 0; mu < B->mu_post; ++mu)
+            for (int step = 0; step < B->nu; ++step)
+                for (int kk = 0; kk < 2; ++kk) out.push_back({OP_SWEEP, t, step, kk, kk});
+    }
+}
+
+template <typename T>
+cs_status fill_probs(cs_batch *B, cs_hierarchy *const *h, cs_cascade *const *c, T *vec, double *gm) {
+    B->probs_bytes = sizeof(BProb<T>) * B->nprob;
+    B->hprobs.assign(B->probs_bytes, 0);
+    BProb<T> *hp = reinterpret_cast<BProb<T> *>(B->hprobs.data());
+    T *v = vec;
+    for (int p = 0; p < B->nprob; ++p) {
+        BProb<T> &q = hp[p];
+        q.nlev = h[p]->nlev;
+        q.m = B->m[p];
+        q.slot0 = B->slot0[p];
+        q.cn = h[p]->cn;
+        q.A64 = h[p]->lev[0].A;
+        q.cinv = h[p]->cinv;
+        q.Z = nullptr;
+        q.V = nullptr;
+        if (gm) {
+            const int64_t n0 = h[p]->lev[0].g.N * B->m[p];
+            q.Z = gm;
+            q.V = gm + n0;
+            gm += (int64_t)(B->restart + 2) * n0;
+        }
+        for (int l = 0; l < q.nlev; ++l) {
+            const Level &L = h[p]->lev[l];
+            BLevel<T> &d = q.lev[l];
+            d.nx = L.g.nx;
+            d.ny = L.g.ny;
+            d.kind = L.kind;
+            d.inplace = L.kind == STAR ? 1 : 0;  // red-black is a graph colouring of the 5-point stencil only
+            d.N = L.g.N;
+            if (sizeof(T) == sizeof(float)) {
+                d.A = reinterpret_cast<const T *>(c[p]->lo[l].A);
+                d.lam = l < c[p]->nlev ? reinterpret_cast<const T *>(c[p]->lo[l].lam) : nullptr;
+            } else {
+                d.A = reinterpret_cast<const T *>(L.A);
+                d.lam = l < c[p]->nlev ? reinterpret_cast<const T *>(c[p]->lam[l]) : nullptr;
+            }
+            const int64_t n = L.g.N * q.m;
+            d.b = v; v += n;
+            d.x = v; v += n;
+            d.t = v; v += n;
+        }
+    }
+    return CS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *c, const int *nrhs,
+                          const cs_batch_opts *o, cs_stream stream, cs_batch **out) {
+    if (!out || !h || !c || !nrhs || !o || nprob < 1) { set_error("null argument or empty batch"); return CS_ERR_ARG; }
+    *out = nullptr;
+    if (o->precision != CS_FP32 && o->precision != CS_FP64) { set_error("bad precision"); return CS_ERR_ARG; }
+    if (o->order != CS_RF && o->order != CS_FF) { set_error("bad order"); return CS_ERR_ARG; }
+    if (o->method != CS_REFINE && o->method != CS_GMRES) { set_error("batched method must be CS_REFINE or CS_GMRES"); return CS_ERR_ARG; }
+    if (o->method == CS_GMRES && (o->restart < 0 || o->restart > 64)) { set_error("GMRES restart must be in 1..64"); return CS_ERR_ARG; }
+    if (o->mu_pre < 0 || o->mu_post < 0 || o->mu_pre + o->mu_post < 1 || o->mu_pre > 16 || o->mu_post > 16) {
+        set_error("bad smoothing counts");
+        return CS_ERR_ARG;
+    }
+    int nu = -1;
+    for (int p = 0; p < nprob; ++p) {
+        const cs_hierarchy *hp = h[p];
+        const cs_cascade *cp = c[p];
+        if (!hp || !cp || cp->h != hp) { set_error("problem %d: missing or mismatched handles", p); return CS_ERR_ARG; }
+        if (nrhs[p] < 1 || nrhs[p] > BMAXRHS) { set_error("problem %d: nrhs must be in 1..%d", p, BMAXRHS); return CS_ERR_ARG; }
+        if (hp->dim != 2 || hp->periodic) { set_error("problem %d: the batched solver takes 2D Dirichlet grids", p); return CS_ERR_UNSUPPORTED; }
+        if (cp->kind != CS_MULTIPLICATIVE) { set_error("problem %d: the batched solver takes red-black multiplicative cascades", p); return CS_ERR_UNSUPPORTED; }
+        if (hp->nlev < 2 || hp->nlev > BMAXLEV || !hp->cinv) { set_error("problem %d: need 2..%d levels and a coarsest factorisation", p, BMAXLEV); return CS_ERR_UNSUPPORTED; }
+        for (int l = 0; l < hp->nlev; ++l)
+            if (hp->lev[l].bs != 1) { set_error("problem %d: the batched solver takes point blocks", p); return CS_ERR_UNSUPPORTED; }
+        if (o->precision == CS_FP32 && !cp->lowp) { set_error("problem %d: FP32 cycles need a cascade built with lowp", p); return CS_ERR_ARG; }
+        if (nu < 0) nu = cp->nu;
+        if (cp->nu != nu) { set_error("all problems of a batch need the same cascade depth"); return CS_ERR_ARG; }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cs_batch *B = new cs_batch();
+    cs_status rc = CS_OK;
+    B->nprob = nprob;
+    B->precision = o->precision;
+    B->order = o->order;
+    B->mu_pre = o->mu_pre;
+    B->mu_post = o->mu_post;
+    B->nu = nu;
+    B->method = o->method == CS_GMRES ? CS_GMRES : CS_REFINE;
+    B->restart = o->restart > 0 ? o->restart : 30;
+    cudaGetDevice(&B->dev);
+    B->m.assign(nrhs, nrhs + nprob);
+    B->nlev.resize(nprob);
+    B->slot0.resize(nprob);
+    B->nfine.resize(nprob);
+    B->nx.resize(nprob);
+    B->ny.resize(nprob);
+    int64_t nvec = 0;
+    for (int p = 0; p < nprob; ++p) {
+        B->nlev[p] = h[p]->nlev;
+        B->dmax = std::max(B->dmax, h[p]->nlev);
+        B->nfine[p] = h[p]->lev[0].g.N;
+        for (int l = 0; l < h[p]->nlev; ++l) {
+            B->nx[p].push_back(h[p]->lev[l].g.nx);
+            B->ny[p].push_back(h[p]->lev[l].g.ny);
+            nvec += 3 * h[p]->lev[l].g.N * nrhs[p];
+        }
+    }
+    for (int p = 0; p < nprob; ++p) B->slot0[p] = B->dmax - B->nlev[p];
+    const size_t esz = o->precision == CS_FP32 ? sizeof(float) : sizeof(double);
+    std::vector<BStep> steps;
+    build_steps(B, steps);
+    B->nsteps = (int)steps.size();
+    int64_t nfine_rhs = 0;
+    for (int p = 0; p < nprob; ++p) nfine_rhs += B->nfine[p] * B->m[p];
+    if ((rc = dalloc(&B->vec, (size_t)nvec * esz, &B->bytes, s)) != CS_OK) goto fail;
+    if (B->method == CS_GMRES) {
+        // basis (restart + 1 vectors) and Z per problem, FP64, [N0][m] each
+        if ((rc = dalloc(&B->gm, (size_t)(B->restart + 2) * nfine_rhs * sizeof(double), &B->bytes, s)) != CS_OK)
+            goto fail;
+        const size_t nq = (size_t)nprob * BMAXRHS, R = (size_t)B->restart;
+        const size_t nd = nq * ((R + 1) * R + 3 * R + (R + 1) + 2);
+        if ((rc = dalloc(&B->gsm, nd * sizeof(double) + 2 * nq * sizeof(int), &B->bytes, s)) != CS_OK) goto fail;
+        double *d = static_cast<double *>(B->gsm);
+        B->H = d; d += nq * (R + 1) * R;
+        B->gcs = d; d += nq * R;
+        B->gsn = d; d += nq * R;
+        B->gy = d; d += nq * R;
+        B->gg = d; d += nq * (R + 1);
+        B->ginv = d; d += nq;
+        B->gnmb = d; d += nq;
+        B->jcols = reinterpret_cast<int *>(d);
+        B->frozen = B->jcols + nq;
+    }
+    if (o->precision == CS_FP32)
+        rc = fill_probs<float>(B, h, c, static_cast<float *>(B->vec), static_cast<double *>(B->gm));
+    else rc = fill_probs<double>(B, h, c, static_cast<double *>(B->vec), static_cast<double *>(B->gm));
+    if (rc != CS_OK) goto fail;
+    if ((rc = dalloc(&B->probs, B->probs_bytes, &B->bytes, s)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&B->steps, steps.size(), &B->bytes, s)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&B->nb, (size_t)nprob * BMAXRHS, &B->bytes, s)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&B->rel, (size_t)nprob * BMAXRHS, &B->bytes, s)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&B->rel0, (size_t)nprob, &B->bytes, s)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&B->state, (size_t)nprob, &B->bytes, s)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&B->iters, (size_t)nprob, &B->bytes, s)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&B->work, (size_t)nprob, &B->bytes, s)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&B->ctl, 1, &B->bytes, s)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&B->bptr, (size_t)nprob, &B->bytes, s)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&B->xptr, (size_t)nprob, &B->bytes, s)) != CS_OK) goto fail;
+    B->hstage_bytes = 64 + 2 * sizeof(double *) * nprob + sizeof(double) * nprob * (BMAXRHS + 1) + sizeof(int) * 2 * nprob;
+    {
+        cudaError_t e = cudaMallocHost(&B->hstage, B->hstage_bytes);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(B->probs, B->hprobs.data(), B->probs_bytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(B->steps, steps.data(), steps.size() * sizeof(BStep), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "batch create", __FILE__, __LINE__); goto fail; }
+    }
+    {
+        int threads = o->threads > 0 ? o->threads : 256;
+        int tile = o->tile_nodes > 0 ? o->tile_nodes : 1024;
+        if (o->autotune) {
+            // time each candidate on the batch itself: two cycles from x = 0
+            // with b = 1 (tol 0: exactly two iterations), best of three
+            if ((rc = dalloc_t(&B->tune_b, (size_t)nfine_rhs, nullptr, s)) != CS_OK) goto fail;
+            if ((rc = dalloc_t(&B->tune_x, (size_t)nfine_rhs, nullptr, s)) != CS_OK) goto fail;
+            std::vector<double> ones((size_t)std::min<int64_t>(nfine_rhs, 1 << 20), 1.0);
+            for (int64_t o0 = 0; o0 < nfine_rhs; o0 += (int64_t)ones.size()) {
+                const int64_t n = std::min<int64_t>((int64_t)ones.size(), nfine_rhs - o0);
+                if (cudaMemcpyAsync(B->tune_b + o0, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice, s) !=
+                    cudaSuccess) {
+                    rc = cuda_fail(cudaGetLastError(), "autotune input", __FILE__, __LINE__);
+                    goto fail;
+                }
+            }
+            std::vector<const double *> bp(nprob);
+            std::vector<double *> xp(nprob);
+            int64_t off = 0;
+            for (int p = 0; p < nprob; ++p) {
+                bp[p] = B->tune_b + off;
+                xp[p] = B->tune_x + off;
+                off += B->nfine[p] * B->m[p];
+            }
+            const int cand_threads[] = {128, 256, 512};
+            const int cand_tile[] = {256, 1024, 4096};
+            float best = 1e30f;
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (int ct : cand_threads)
+                for (int tt : cand_tile) {
+                    int ctas = 0;
+                    if (coresident(B, ct, &ctas) != CS_OK) continue;
+                    B->threads = ct;
+                    B->ctas = ctas;
+                    if ((rc = build_tiles(B, tt, s)) != CS_OK) break;
+                    float ms_best = 1e30f;
+                    for (int rep = 0; rep < 3 && rc == CS_OK; ++rep) {
+                        if (cudaMemsetAsync(B->tune_x, 0, sizeof(double) * nfine_rhs, s) != cudaSuccess) {
+                            rc = cuda_fail(cudaGetLastError(), "autotune", __FILE__, __LINE__);
+                            break;
+                        }
+                        if ((rc = set_pointers(B, bp.data(), xp.data(), s)) != CS_OK) break;
+                        if ((rc = reset_control(B, 0.0, 2, s)) != CS_OK) break;
+                        cudaEventRecord(e0, s);
+                        if ((rc = launch(B, s)) != CS_OK) break;
+                        cudaEventRecord(e1, s);
+                        if (cudaEventSynchronize(e1) != cudaSuccess) {
+                            rc = cuda_fail(cudaGetLastError(), "autotune", __FILE__, __LINE__);
+                            break;
+                        }
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        ms_best = std::min(ms_best, ms);
+                    }
+                    if (rc != CS_OK) break;
+                    B->tuned.push_back({ct, tt, ms_best});
+                    if (ms_best < best) {
+                        best = ms_best;
+                        threads = ct;
+                        tile = tt;
+                    }
+                }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            dfree(B->tune_b, s);
+            dfree(B->tune_x, s);
+            B->tune_b = B->tune_x = nullptr;
+            if (rc != CS_OK) goto fail;
+        }
+        if ((rc = coresident(B, threads, &B->ctas)) != CS_OK) goto fail;
+        B->threads = threads;
+        if ((rc = build_tiles(B, tile, s)) != CS_OK) goto fail;
+    }
+    *out = B;
+    return CS_OK;
+fail:
+    cs_batch_destroy(B);
+    return rc;
+}
+
+cs_status cs_batch_solve(cs_batch *B, const double *const *b, double *const *x, double tol, int maxit,
+                         cs_solve_info *info, cs_stream stream) {
+    if (!B || !b || !x) { set_error("null argument"); return CS_ERR_ARG; }
+    for (int p = 0; p < B->nprob; ++p)
+        if (!b[p] || !x[p]) { set_error("problem %d: null vector", p); return CS_ERR_ARG; }
+    if (tol <= 0) tol = 1e-10;
+    if (maxit <= 0) maxit = 100;
+    cudaStream_t s = (cudaStream_t)stream;
+    CSX_TRY(set_pointers(B, b, x, s));
+    CSX_TRY(reset_control(B, tol, maxit, s));
+    CSX_TRY(run(B, s));
+    const int np = B->nprob;
+    char *h = static_cast<char *>(B->hstage) + 64 + 2 * sizeof(double *) * np;
+    double *hrel = reinterpret_cast<double *>(h);
+    int *hst = reinterpret_cast<int *>(hrel + (size_t)np * BMAXRHS);
+    int *hit = hst + np;
+    CSX_CUDA(cudaMemcpyAsync(hrel, B->rel, sizeof(double) * np * BMAXRHS, cudaMemcpyDeviceToHost, s));
+    CSX_CUDA(cudaMemcpyAsync(hst, B->state, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
+    CSX_CUDA(cudaMemcpyAsync(hit, B->iters, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
+    CSX_CUDA(cudaStreamSynchronize(s));
+    cs_status rc = CS_OK;
+    int ndiv = 0, nnc = 0;
+    for (int p = 0; p < np; ++p) {
+        double worst = 0.0;
+        for (int r = 0; r < B->m[p]; ++r) worst = std::max(worst, hrel[(size_t)p * BMAXRHS + r]);
+        if (info) info[p] = {hit[p], hst[p] == ST_CONVERGED ? 1 : 0, worst, 0};
+        if (hst[p] == ST_DIVERGED) ++ndiv;
+        else if (hst[p] != ST_CONVERGED) ++nnc;
+    }
+    if (ndiv) {
+        set_error("%d of %d problems diverged", ndiv, np);
+        rc = CS_ERR_DIVERGED;
+    } else if (nnc) {
+        set_error("%d of %d problems not converged after %d iterations", nnc, np, maxit);
+        rc = CS_ERR_NOTCONV;
+    }
+    return rc;
+}
+
+cs_status cs_batch_config(const cs_batch *B, int *threads, int *tile_nodes, int *ctas, cs_batch_tune *tuned,
+                          int cap, int *ntuned) {
+    if (!B) { set_error("null argument"); return CS_ERR_ARG; }
+    if (threads) *threads = B->threads;
+    if (tile_nodes) *tile_nodes = B->tile_nodes;
+    if (ctas) *ctas = B->ctas;
+    if (ntuned) *ntuned = (int)B->tuned.size();
+    if (tuned)
+        for (int k = 0; k < cap && k < (int)B->tuned.size(); ++k) tuned[k] = B->tuned[k];
+    return CS_OK;
+}
+
+cs_status cs_batch_set_config(cs_batch *B, int threads, int tile_nodes, cs_stream stream) {
+    if (!B || threads < 32 || threads > 512 || (threads & 31) || tile_nodes < 1) {
+        set_error("bad batch configuration");
+        return CS_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int ctas = 0;
+    CSX_TRY(coresident(B, threads, &ctas));
+    B->threads = threads;
+    B->ctas = ctas;
+    CSX_TRY(build_tiles(B, tile_nodes, s));
+    return CS_OK;
+}
+
+int64_t cs_batch_bytes(const cs_batch *B) { return B ? B->bytes : 0; }
+
+void cs_batch_destroy(cs_batch *B) {
+    if (!B) return;
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    dfree(B->vec); dfree(B->probs); dfree(B->tiles); dfree(B->ftiles); dfree(B->slot_tile); dfree(B->ftile_of);
+    dfree(B->steps); dfree(B->part); dfree(B->nb); dfree(B->rel); dfree(B->rel0); dfree(B->state); dfree(B->iters);
+    dfree(B->ctl); dfree(B->bptr); dfree(B->xptr); dfree(B->tune_b); dfree(B->tune_x); dfree(B->work);
+    dfree(B->gm); dfree(B->gsm);
+    if (B->hstage) cudaFreeHost(B->hstage);
+    delete B;
+}
+
+cs_status cs_solve_batched(int nprob, cs_hierarchy *const *h, cs_cascade *const *c, const cs_solve_opts *o,
+                           const double *const *b, double *const *x, const int *nrhs, cs_solve_info *info,
+                           cs_stream stream) {
+    if (!o) { set_error("null argument"); return CS_ERR_ARG; }
+    cs_batch_opts bo{};
+    bo.precision = o->cycle.precision;
+    bo.order = o->cycle.order;
+    bo.mu_pre = o->cycle.mu_pre;
+    bo.mu_post = o->cycle.mu_post;
+    bo.autotune = 0;
+    bo.method = o->method == CS_GMRES ? CS_GMRES : CS_REFINE;
+    bo.restart = o->restart;
+    cs_batch *B = nullptr;
+    CSX_TRY(cs_batch_create(nprob, h, c, nrhs, &bo, stream, &B));
+    cs_status rc = cs_batch_solve(B, b, x, o->tol, o->maxit, info, stream);
+    cs_batch_destroy(B);
+    return rc;
+}
+
+}  // extern "C"

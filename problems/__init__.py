@@ -314,6 +314,24 @@ def rhs(N: int, seed: int, nrhs: int = 1) -> np.ndarray:
     return v if nrhs == 1 else v.reshape(N, nrhs)
 
 
+def batch_problem(k: int, nmin: int = 33, nmax: int = 513, mmax: int = 8, corr: float = 8.0,
+                  config: int = 4):
+    """Problem ``k`` of the batched workload: a 2D variable-coefficient
+    Poisson problem (5-point, Dirichlet) with side N ~ U{nmin..nmax} interior
+    nodes, nrhs ~ U{1..mmax}, correlated cell coefficients with a log-uniform
+    marginal on [1e-3, 1e3] (Gaussian field, correlation ``corr`` cells) and
+    right-hand sides ~ U[-1, 1], RHS-contiguous ``[N^2, nrhs]`` flattened.
+    Independent streams: sizes from seed s, field from s + 10^6, RHS from
+    s + 2*10^6, with s = config_seed(config, k).  Returns (Stencil, nrhs, b)."""
+    s = config_seed(config, k)
+    u = uniform01(s, 2)
+    n = nmin + int(u[0] * (nmax - nmin + 1))
+    m = 1 + int(u[1] * mmax)
+    A = variable_poisson(log_uniform_field(2, n, corr, s + 1_000_000))
+    b = uniform(s + 2_000_000, A.N * m, -1.0, 1.0)
+    return A, m, b
+
+
 def config_seed(config: int, problem: int = 0) -> int:
     """Seed of problem ``problem`` of workload ``config`` (run seed 0)."""
     return 1000 * config + problem
