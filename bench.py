@@ -54,7 +54,11 @@ def args_():
     p.add_argument("--learned-meshes", type=int, default=64, help="training meshes of the learned setup")
     p.add_argument("--learned-n", type=int, default=127, help="interior nodes per side of a training mesh")
     p.add_argument("--learned-steps", type=int, default=2000, help="Adam steps")
-    p.add_argument("--profile", default="", choices=["", "setup", "step", "sweep", "multirhs", "blocksetup"],
+    p.add_argument("--batch-count", type=int, default=32, help="problems of the batched workload timed")
+    p.add_argument("--batch-maxit", type=int, default=400, help="GMRES steps allowed per problem")
+    p.add_argument("--batch-single", type=int, default=4, help="problems also solved on the single-problem path")
+    p.add_argument("--batch-profile-count", type=int, default=16, help="problems in the batch profile case")
+    p.add_argument("--profile", default="", choices=["", "setup", "step", "sweep", "multirhs", "blocksetup", "batch"],
                    help="run one untimed setup (or setup + solve) and exit: the case ncu captures")
     return p.parse_args()
 
@@ -225,6 +229,77 @@ def learned_section(a, cmg, problems, dev):
     return out
 
 
+def batch_section(a, cmg, problems, dev):
+    """Batched solve (many uneven problems): the first ``--batch-count``
+    problems of the batched workload (2D variable-coefficient Poisson, sides
+    U{33..513}, 1..8 RHS each, correlated log-uniform coefficients on
+    [1e-3, 1e3]), red-black multiplicative nu = 3, V(1,1) RF, GMRES(30) to
+    1e-10 per RHS.  One persistent cooperative launch per solve (autotuned
+    schedule), against the single-problem path solving each RHS of the first
+    problems in turn."""
+    import numpy as np
+    import torch
+    K = a.batch_count
+    t0 = time.perf_counter()
+    P = [problems.batch_problem(k) for k in range(K)]
+    t_gen = time.perf_counter() - t0
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"first {K} problems of the 512-problem batch: 2D variable-coefficient Poisson, sides "
+                       "U{33..513}, 1..8 RHS, log-uniform coefficients [1e-3,1e3] (correlation 8h); multiplicative "
+                       "nu=3 red-black, V(1,1) RF, GMRES(30) to 1e-10 per RHS",
+           "problems": K, "unknowns": int(sum(A.N for A, _, _ in P)),
+           "rhs_unknowns": int(sum(A.N * m for A, m, _ in P)), "generate_s": t_gen}
+    cmg.setup_many([A for A, _, _ in P[:2]], kind="multiplicative", nu=3, lowp=True)  # warm-up
+    torch.cuda.synchronize()
+    e0.record(s)
+    hs, cs = cmg.setup_many([A for A, _, _ in P], kind="multiplicative", nu=3, lowp=True)
+    e1.record(s)
+    torch.cuda.synchronize()
+    out["setup_ms"] = e0.elapsed_time(e1)
+    t0 = time.perf_counter()
+    bs = [torch.tensor(b, device=dev) for _, _, b in P]
+    for prec in ("fp32", "fp64"):
+        bt = cmg.Batch(hs, cs, [m for _, m, _ in P], precision=prec, method="gmres", autotune=(prec == "fp32"))
+        if prec == "fp32":
+            out["autotune_s"] = time.perf_counter() - t0
+            out["schedule"] = bt.config()
+        xs = [torch.zeros_like(b) for b in bs]
+        torch.cuda.synchronize()
+        l0 = cmg.kernel_launches()
+        e0.record(s)
+        infos = bt.solve(bs, xs, tol=1e-10, maxit=a.batch_maxit, raise_on_error=False)
+        e1.record(s)
+        torch.cuda.synchronize()
+        its = [i.iterations for i in infos]
+        out[f"gmres_{prec}_cycles"] = {"solve_ms": e0.elapsed_time(e1), "converged": int(sum(i.converged for i in infos)),
+                                       "iterations_min_median_max": [int(np.min(its)), int(np.median(its)),
+                                                                     int(np.max(its))],
+                                       "worst_rel_residual": float(max(i.final_rel_residual for i in infos)),
+                                       "gpu_launches": int(cmg.kernel_launches() - l0)}
+        del bt
+    # the single-problem path on the first problems, one RHS at a time
+    nsub = min(K, a.batch_single)
+    torch.cuda.synchronize()
+    e0.record(s)
+    l0 = cmg.kernel_launches()
+    conv = 0
+    for p in range(nsub):
+        A, m, _ = P[p]
+        B = bs[p].view(A.N, m)
+        for r in range(m):
+            x1 = torch.zeros(A.N, dtype=torch.float64, device=dev)
+            conv += cmg.solve(hs[p], cs[p], B[:, r].contiguous(), x1, method="gmres", precision="fp32", tol=1e-10,
+                              maxit=a.batch_maxit, raise_on_error=False).converged
+    e1.record(s)
+    torch.cuda.synchronize()
+    out["single_problem_path"] = {"problems": nsub, "rhs_unknowns": int(sum(P[p][0].N * P[p][1] for p in range(nsub))),
+                                  "solve_ms": e0.elapsed_time(e1), "rhs_converged": int(conv),
+                                  "gpu_launches": int(cmg.kernel_launches() - l0)}
+    del hs, cs, bs
+    return out
+
+
 # ------------------------------------------------------------------- ours
 def main():
     a = args_()
@@ -264,6 +339,17 @@ def main():
             cmg.sweep_rhs(hb, cb, 0, k % 3, Bb, Xb[k % 2], Xb[(k + 1) % 2], 32)
         torch.cuda.synchronize()
         print(json.dumps({"profile": a.profile, "n": a.n}), flush=True)
+        return
+
+    if a.profile == "batch":  # one batched GMRES solve of the first problems of the batched workload, 3 steps
+        P = [problems.batch_problem(k) for k in range(a.batch_profile_count)]
+        hs, cs = cmg.setup_many([A for A, _, _ in P], kind="multiplicative", nu=3, lowp=True)
+        bt = cmg.Batch(hs, cs, [m for _, m, _ in P], precision="fp32", method="gmres", threads=512, tile_nodes=4096)
+        bs = [torch.tensor(b, device=dev) for _, _, b in P]
+        xs = [torch.zeros_like(b) for b in bs]
+        bt.solve(bs, xs, tol=1e-300, maxit=3, raise_on_error=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": a.profile, "problems": len(P), "launches": cmg.kernel_launches()}), flush=True)
         return
 
     if a.profile == "blocksetup":  # the exact 3x3-block setup of the learned-setup workload (Q1, n^2)
@@ -438,6 +524,8 @@ def main():
         del hb, cb, ci, Xb, Bb
         torch.cuda.empty_cache()
         result["learned_setup"] = learned_section(a, cmg, problems, dev)
+        torch.cuda.empty_cache()
+        result["batched_solve"] = batch_section(a, cmg, problems, dev)
         torch.cuda.empty_cache()
         # ---- plain FP64 path (stationary V-cycle iteration)
         pinfo = []

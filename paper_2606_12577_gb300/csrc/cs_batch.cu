@@ -110,99 +110,136 @@ __device__ __forceinline__ void boff(int s, int &dx, int &dy) {
     }
 }
 
-// (A v)_{i,r} for r < m at node (ix, iy); neighbours outside contribute nothing
+// (A v)_{i,r} at node i = (ix, iy); neighbours outside contribute nothing
 template <int KIND, typename T, typename TA>
-__device__ __forceinline__ void row_apply(int nx, int ny, int64_t N, const TA *__restrict__ A, const T *v, int m,
-                                          int ix, int iy, int64_t i, T (&ax)[BMAXRHS]) {
+__device__ __forceinline__ T row_apply(int nx, int ny, int64_t N, const TA *__restrict__ A, const T *v, int m, int r,
+                                       int ix, int iy, int i) {
     constexpr int NST = KIND == STAR ? 5 : 9;
-#pragma unroll
-    for (int r = 0; r < BMAXRHS; ++r) ax[r] = T(0);
+    T ax = T(0);
 #pragma unroll
     for (int s = 0; s < NST; ++s) {
         int dx, dy;
         boff<KIND>(s, dx, dy);
         const bool in = (unsigned)(ix + dx) < (unsigned)nx && (unsigned)(iy + dy) < (unsigned)ny;
         const T a = (T)A[(int64_t)s * N + i];
-        const int64_t j = i + dx + (int64_t)nx * dy;
-#pragma unroll
-        for (int r = 0; r < BMAXRHS; ++r)
-            if (r < m) ax[r] = fma(a, in ? v[j * m + r] : T(0), ax[r]);
+        const int j = i + dx + nx * dy;
+        ax = fma(a, in ? v[(int64_t)j * m + r] : T(0), ax);
     }
+    return ax;
 }
 
-// deterministic CTA sum of m <= 8 values per thread into out[0..m)
-__device__ __forceinline__ void cta_sum8(double (&v)[BMAXRHS], int m, double (*red)[BMAXRHS], double *out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int r = 0; r < BMAXRHS; ++r)
-        for (int o = 16; o > 0; o >>= 1) v[r] += __shfl_down_sync(0xffffffffu, v[r], o);
-    if (lane == 0)
-#pragma unroll
-        for (int r = 0; r < BMAXRHS; ++r) red[warp][r] = v[r];
+// Work items of a tile: item (node, right-hand side r).  Thread t < U, U the
+// largest multiple of m not above the CTA size, takes r = t % m for the
+// nodes i0 + t / m + k U / m, so no index is divided per item and the m
+// threads of a node are adjacent (its coefficient loads are one broadcast).
+struct TileMap {
+    int r, n0, step;
+    bool on;
+};
+__device__ __forceinline__ TileMap tile_map(int m) {
+    TileMap t;
+    const int U = ((int)blockDim.x / m) * m;
+    t.on = (int)threadIdx.x < U;
+    t.r = (int)threadIdx.x % m;
+    t.n0 = (int)threadIdx.x / m;
+    t.step = U / m;
+    return t;
+}
+
+// Deterministic CTA sums per right-hand side: red[t] holds thread t's sum;
+// threads t and t + k m (same r) are combined by a fixed pairwise tree over
+// the groups g = t / m; out[r] = the sum of right-hand side r.
+__device__ __forceinline__ void cta_sum_by_rhs(double v, int m, double *red, double *out) {
+    const int t = threadIdx.x;
+    const int G = (int)blockDim.x / m, U = G * m;
+    red[t] = t < U ? v : 0.0;
     __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int r = 0; r < BMAXRHS; ++r) {
-            double t = lane < nw ? red[lane][r] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-            if (lane == 0 && r < m) out[r] = t;
-        }
+    int P = 1;
+    while (2 * P <= G) P *= 2;
+    if (t < (G - P) * m) red[t] += red[t + P * m];  // fold the groups beyond the largest power of two
+    __syncthreads();
+    for (int h = P / 2; h > 0; h /= 2) {
+        if (t < h * m) red[t] += red[t + h * m];
+        __syncthreads();
     }
+    if (t < m) out[t] = red[t];
     __syncthreads();
 }
 
 // ------------------------------------------------------------- stages
+// (the level descriptors are read once per tile into registers: the item
+// loops touch only plain pointers and sizes)
+// Items are taken SW at a time, all loads before any store: in place (a
+// graph colouring) the loads of a colour step read only entries of the other
+// colour, which its stores never touch, so the order is free, and the SW
+// independent load groups keep SW times more requests in flight per thread.
+constexpr int SW = 4;
 template <typename T, int KIND>
-__device__ __forceinline__ void sweep_node(const BLevel<T> &L, int m, int64_t i, int lv, int colour, const T *src,
-                                           T *dst) {
-    const int ix = (int)i % L.nx, iy = (int)i / L.nx;
-    if (bcolour(ix, iy) != colour) {
-        if (src != dst)
-            for (int r = 0; r < m; ++r) dst[i * m + r] = src[i * m + r];
-        return;
-    }
-    T ax[BMAXRHS];
-    row_apply<KIND, T, T>(L.nx, L.ny, L.N, L.A, src, m, ix, iy, i, ax);
-    const T lam = L.lam[(int64_t)lv * L.N + i];
+__device__ __forceinline__ void sweep_tile(int nx, int ny, int64_t N, const T *__restrict__ A,
+                                           const T *__restrict__ lam, const T *__restrict__ b, int m, int r, int i0,
+                                           int ni, int n0, int step, int colour, const T *src, T *dst) {
+    const bool copy = src != dst;
+    for (int nn = n0; nn < ni; nn += SW * step) {
+        T val[SW];
+        int64_t ee[SW];
+        bool wr[SW];
 #pragma unroll
-    for (int r = 0; r < BMAXRHS; ++r)
-        if (r < m) {
-            const T res = ax[r] - L.b[i * m + r];
-            dst[i * m + r] = src[i * m + r] - lam * res;
+        for (int u = 0; u < SW; ++u) {
+            const int n = nn + u * step;
+            wr[u] = false;
+            ee[u] = 0;
+            val[u] = T(0);
+            if (n < ni) {
+                const int i = i0 + n;
+                const int iy = i / nx, ix = i - iy * nx;
+                const int64_t e = (int64_t)i * m + r;
+                ee[u] = e;
+                if (bcolour(ix, iy) != colour) {
+                    if (copy) { val[u] = src[e]; wr[u] = true; }
+                } else {
+                    const T ax = row_apply<KIND, T, T>(nx, ny, N, A, src, m, r, ix, iy, i);
+                    const T res = ax - b[e];
+                    val[u] = src[e] - lam[i] * res;
+                    wr[u] = true;
+                }
+            }
         }
+#pragma unroll
+        for (int u = 0; u < SW; ++u)
+            if (wr[u]) dst[ee[u]] = val[u];
+    }
 }
 
 // coarse node I of level l+1: b_c = 2^-2 sum_f P_{f,I} (A x - b)_f, x_c = 0
 template <typename T, int KIND>
-__device__ __forceinline__ void restrict_node(const BLevel<T> &F, const BLevel<T> &C, int m, int64_t I) {
-    const int cx = (int)I % C.nx, cy = (int)I / C.nx;
-    T acc[BMAXRHS];
-#pragma unroll
-    for (int r = 0; r < BMAXRHS; ++r) acc[r] = T(0);
-    for (int dy = -1; dy <= 1; ++dy) {
-        const int fy = 2 * cy + 1 + dy;
-        if (fy >= F.ny) continue;
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int fx = 2 * cx + 1 + dx;
-            if (fx >= F.nx) continue;
-            const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0));
-            const int64_t f = fx + (int64_t)F.nx * fy;
-            T ax[BMAXRHS];
-            row_apply<KIND, T, T>(F.nx, F.ny, F.N, F.A, F.x, m, fx, fy, f, ax);
-#pragma unroll
-            for (int r = 0; r < BMAXRHS; ++r)
-                if (r < m) acc[r] = fma(w, ax[r] - F.b[f * m + r], acc[r]);
+__device__ __forceinline__ void restrict_tile(int fnx, int fny, int64_t fN, const T *__restrict__ A,
+                                              const T *__restrict__ xf, const T *__restrict__ bf, int cnx,
+                                              T *__restrict__ bc, T *__restrict__ xc, int m, int r, int i0, int ni,
+                                              int n0, int step) {
+    for (int nn = n0; nn < ni; nn += step) {
+        const int I = i0 + nn;
+        const int cy = I / cnx, cx = I - cy * cnx;
+        T acc = T(0);
+#pragma unroll 1
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int fy = 2 * cy + 1 + dy;
+            if (fy >= fny) continue;
+#pragma unroll 1
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int fx = 2 * cx + 1 + dx;
+                if (fx >= fnx) continue;
+                const T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0));
+                const int f = fx + fnx * fy;
+                const T ax = row_apply<KIND, T, T>(fnx, fny, fN, A, xf, m, r, fx, fy, f);
+                acc = fma(w, ax - bf[(int64_t)f * m + r], acc);
+            }
         }
+        bc[(int64_t)I * m + r] = acc * T(0.25);
+        xc[(int64_t)I * m + r] = T(0);
     }
-#pragma unroll
-    for (int r = 0; r < BMAXRHS; ++r)
-        if (r < m) {
-            C.b[I * m + r] = acc[r] * T(0.25);
-            C.x[I * m + r] = T(0);
-        }
 }
 
-// 1D interpolation weights of fine node f from the coarse nodes (see the
+// 1D interpolation weights of fine node f from the coarse nodes (as in the
 // single-problem prolongation): odd f sits on coarse (f-1)/2, even f takes
 // half of coarse f/2-1 and f/2 where present.
 __device__ __forceinline__ int bp1d(int f, int nc, int *c, float *w) {
@@ -219,25 +256,25 @@ __device__ __forceinline__ int bp1d(int f, int nc, int *c, float *w) {
 }
 
 template <typename T>
-__device__ __forceinline__ void prolong_node(const BLevel<T> &F, const BLevel<T> &C, int m, int64_t f) {
-    const int fx = (int)f % F.nx, fy = (int)f / F.nx;
-    int cxs[2], cys[2];
-    float wx[2], wy[2];
-    const int kx = bp1d(fx, C.nx, cxs, wx), ky = bp1d(fy, C.ny, cys, wy);
-    T acc[BMAXRHS];
-#pragma unroll
-    for (int r = 0; r < BMAXRHS; ++r) acc[r] = T(0);
-    for (int bb = 0; bb < ky; ++bb)
-        for (int a = 0; a < kx; ++a) {
-            const T w = T(wx[a] * wy[bb] * 1.f);
-            const int64_t c = cxs[a] + (int64_t)C.nx * cys[bb];
-#pragma unroll
-            for (int r = 0; r < BMAXRHS; ++r)
-                if (r < m) acc[r] = fma(w, C.x[c * m + r], acc[r]);
-        }
-#pragma unroll
-    for (int r = 0; r < BMAXRHS; ++r)
-        if (r < m) F.x[f * m + r] = F.x[f * m + r] - acc[r];
+__device__ __forceinline__ void prolong_tile(int fnx, T *__restrict__ xf, int cnx, int cny,
+                                             const T *__restrict__ xc, int m, int r, int i0, int ni, int n0,
+                                             int step) {
+    for (int nn = n0; nn < ni; nn += step) {
+        const int f = i0 + nn;
+        const int fy = f / fnx, fx = f - fy * fnx;
+        int cxs[2], cys[2];
+        float wx[2], wy[2];
+        const int kx = bp1d(fx, cnx, cxs, wx), ky = bp1d(fy, cny, cys, wy);
+        T acc = T(0);
+        for (int bb = 0; bb < ky; ++bb)
+            for (int a = 0; a < kx; ++a) {
+                const T w = T(wx[a] * wy[bb] * 1.f);
+                const int c = cxs[a] + cnx * cys[bb];
+                acc = fma(w, xc[(int64_t)c * m + r], acc);
+            }
+        const int64_t e = (int64_t)f * m + r;
+        xf[e] = xf[e] - acc;
+    }
 }
 
 template <typename T>
@@ -247,39 +284,46 @@ __device__ void stage_step(const BArgs &a, const BProb<T> *P, const BStep st) {
     for (int k = t0 + blockIdx.x; k < t1; k += gridDim.x) {
         const BTile tile = a.tiles[k];
         if (__ldcg(a.work + tile.p) == 0) continue;
+        if (st.op == OP_RESTRICT && tile.l == 0) continue;  // this problem's finest level starts at the coarse slot
         const BProb<T> &pr = P[tile.p];
         const int m = pr.m;
+        const TileMap tm = tile_map(m);
+        if (!tm.on) continue;
+        const int r = tm.r;
         if (st.op == OP_SWEEP) {
-            const BLevel<T> &L = pr.lev[tile.l];
+            const BLevel<T> L = pr.lev[tile.l];
             const T *src = L.inplace || st.parity == 0 ? L.x : L.t;
             T *dst = L.inplace || st.parity == 1 ? L.x : L.t;
-            for (int ii = threadIdx.x; ii < tile.ni; ii += blockDim.x) {
-                const int64_t i = tile.i0 + ii;
-                if (L.kind == STAR) sweep_node<T, STAR>(L, m, i, st.lv, st.colour, src, dst);
-                else sweep_node<T, BOX>(L, m, i, st.lv, st.colour, src, dst);
-            }
+            const T *lam = L.lam + (int64_t)st.lv * L.N;
+            if (L.kind == STAR)
+                sweep_tile<T, STAR>(L.nx, L.ny, L.N, L.A, lam, L.b, m, r, tile.i0, tile.ni, tm.n0, tm.step, st.colour,
+                                    src, dst);
+            else
+                sweep_tile<T, BOX>(L.nx, L.ny, L.N, L.A, lam, L.b, m, r, tile.i0, tile.ni, tm.n0, tm.step, st.colour,
+                                   src, dst);
         } else if (st.op == OP_RESTRICT) {
-            if (tile.l == 0) continue;  // this problem's finest level starts at the coarse slot
-            const BLevel<T> &F = pr.lev[tile.l - 1], &C = pr.lev[tile.l];
-            for (int ii = threadIdx.x; ii < tile.ni; ii += blockDim.x) {
-                const int64_t I = tile.i0 + ii;
-                if (F.kind == STAR) restrict_node<T, STAR>(F, C, m, I);
-                else restrict_node<T, BOX>(F, C, m, I);
-            }
+            const BLevel<T> F = pr.lev[tile.l - 1], C = pr.lev[tile.l];
+            if (F.kind == STAR)
+                restrict_tile<T, STAR>(F.nx, F.ny, F.N, F.A, F.x, F.b, C.nx, C.b, C.x, m, r, tile.i0, tile.ni, tm.n0,
+                                       tm.step);
+            else
+                restrict_tile<T, BOX>(F.nx, F.ny, F.N, F.A, F.x, F.b, C.nx, C.b, C.x, m, r, tile.i0, tile.ni, tm.n0,
+                                      tm.step);
         } else if (st.op == OP_COARSE) {
-            const BLevel<T> &L = pr.lev[tile.l];
+            const BLevel<T> L = pr.lev[tile.l];
             const int n = pr.cn;
-            for (int ii = threadIdx.x; ii < tile.ni; ii += blockDim.x) {
-                const int i = tile.i0 + ii;
-                for (int r = 0; r < m; ++r) {
-                    double s = 0.0;
-                    for (int j = 0; j < n; ++j) s = fma(pr.cinv[(int64_t)i * n + j], (double)L.b[(int64_t)j * m + r], s);
-                    L.x[(int64_t)i * m + r] = (T)s;
-                }
+            const double *__restrict__ cinv = pr.cinv;
+            const T *__restrict__ lb = L.b;
+            T *__restrict__ lx = L.x;
+            for (int nn = tm.n0; nn < tile.ni; nn += tm.step) {
+                const int i = tile.i0 + nn;
+                double sacc = 0.0;
+                for (int j = 0; j < n; ++j) sacc = fma(cinv[(int64_t)i * n + j], (double)lb[(int64_t)j * m + r], sacc);
+                lx[(int64_t)i * m + r] = (T)sacc;
             }
         } else {  // OP_PROLONG
-            const BLevel<T> &F = pr.lev[tile.l], &C = pr.lev[tile.l + 1];
-            for (int ii = threadIdx.x; ii < tile.ni; ii += blockDim.x) prolong_node<T>(F, C, m, tile.i0 + ii);
+            const BLevel<T> F = pr.lev[tile.l], C = pr.lev[tile.l + 1];
+            prolong_tile<T>(F.nx, F.x, C.nx, C.ny, C.x, m, r, tile.i0, tile.ni, tm.n0, tm.step);
         }
     }
 }
@@ -307,107 +351,116 @@ __device__ __forceinline__ bool fine_gate_all(int what) {
     return what == F_BNORM || what == F_ZEROX || what == F_RESID || what == F_UPDATE || what == F_MB ||
            what == F_XUPD;
 }
-
-template <typename T, int KIND>
-__device__ __forceinline__ void resid_node(const BArgs &a, const BProb<T> &pr, int p, int64_t i, const double *xv,
-                                           bool with_b, double (&acc)[BMAXRHS]) {
-    const BLevel<T> &L = pr.lev[0];
-    const int m = pr.m;
-    const int ix = (int)i % L.nx, iy = (int)i / L.nx;
-    double ax[BMAXRHS];
-    row_apply<KIND, double, double>(L.nx, L.ny, L.N, pr.A64, xv, m, ix, iy, i, ax);
-    const double *b = a.b64[p];
-#pragma unroll
-    for (int r = 0; r < BMAXRHS; ++r)
-        if (r < m) {
-            const double v = with_b ? b[i * m + r] - ax[r] : ax[r];
-            acc[r] = fma(v, v, acc[r]);
-            L.b[i * m + r] = (T)v;
-            L.x[i * m + r] = T(0);
-        }
+__device__ __forceinline__ bool fine_reduces(int what) {
+    return what == F_BNORM || what == F_RESID || what == F_CONVZ || what == F_DOT || what == F_NRMZ;
 }
 
 template <typename T>
-__device__ void stage_fine(const BArgs &a, const BProb<T> *P, int what, int iarg, int jarg,
-                           double (*red)[BMAXRHS]) {
-    const bool gate_all = fine_gate_all(what);
+__device__ void stage_fine(const BArgs &a, const BProb<T> *P, int what, int iarg, int jarg, double *red) {
+    const bool gate_all = fine_gate_all(what), reduces = fine_reduces(what);
     for (int k = blockIdx.x; k < a.nftiles; k += gridDim.x) {
         const BTile tile = a.ftiles[k];
         const int p = tile.p;
         // uniform over the CTA: the flags change only in the per-problem stages
         if (gate_all ? __ldcg(a.state + p) != ST_ACTIVE : __ldcg(a.work + p) == 0) continue;
         const BProb<T> &pr = P[p];
-        const BLevel<T> &L = pr.lev[0];
-        const int m = pr.m;
-        const int64_t nm = L.N * m;
-        const int q0 = p * BMAXRHS;
-        double acc[BMAXRHS];
-#pragma unroll
-        for (int r = 0; r < BMAXRHS; ++r) acc[r] = 0.0;
-        for (int ii = threadIdx.x; ii < tile.ni; ii += blockDim.x) {
-            const int64_t i = tile.i0 + ii;
+        const BLevel<T> L = pr.lev[0];
+        const int m = pr.m, nx = L.nx, ny = L.ny;
+        const int64_t N = L.N, nm = N * m;
+        const TileMap tm = tile_map(m);
+        const int r = tm.r, q = p * BMAXRHS + r;
+        const int i0 = tile.i0, ni = tile.ni, n0 = tm.n0, step = tm.step;
+        const double *__restrict__ b = a.b64[p];
+        double *__restrict__ x = a.x64[p];
+        double *__restrict__ Z = pr.Z;
+        const double *__restrict__ V = pr.V;
+        T *__restrict__ lb = L.b;
+        T *__restrict__ lx = L.x;
+        double acc = 0.0;
+        if (tm.on) {
             if (what == F_BNORM) {
-                const double *b = a.b64[p];
-#pragma unroll
-                for (int r = 0; r < BMAXRHS; ++r)
-                    if (r < m) acc[r] = fma(b[i * m + r], b[i * m + r], acc[r]);
+                for (int nn = n0; nn < ni; nn += step) {
+                    const double v = b[(int64_t)(i0 + nn) * m + r];
+                    acc = fma(v, v, acc);
+                }
             } else if (what == F_ZEROX) {
-                for (int r = 0; r < m; ++r)
-                    if (a.nb[q0 + r] == 0.0) a.x64[p][i * m + r] = 0.0;
+                if (a.nb[q] == 0.0)
+                    for (int nn = n0; nn < ni; nn += step) x[(int64_t)(i0 + nn) * m + r] = 0.0;
             } else if (what == F_RESID || what == F_MATVEC) {
-                const double *xv = what == F_RESID ? a.x64[p] : pr.V + (int64_t)jarg * nm;
-                if (L.kind == STAR) resid_node<T, STAR>(a, pr, p, i, xv, what == F_RESID, acc);
-                else resid_node<T, BOX>(a, pr, p, i, xv, what == F_RESID, acc);
+                const bool res = what == F_RESID;
+                const double *__restrict__ xv = res ? x : V + (int64_t)jarg * nm;
+                const double *__restrict__ A64 = pr.A64;
+                const bool star = L.kind == STAR;
+                for (int nn = n0; nn < ni; nn += step) {
+                    const int i = i0 + nn;
+                    const int iy = i / nx, ix = i - iy * nx;
+                    const double ax = star ? row_apply<STAR, double, double>(nx, ny, N, A64, xv, m, r, ix, iy, i)
+                                           : row_apply<BOX, double, double>(nx, ny, N, A64, xv, m, r, ix, iy, i);
+                    const int64_t e = (int64_t)i * m + r;
+                    const double v = res ? b[e] - ax : ax;
+                    acc = fma(v, v, acc);
+                    lb[e] = (T)v;
+                    lx[e] = T(0);
+                }
             } else if (what == F_UPDATE) {
-                double *x = a.x64[p];
-                for (int r = 0; r < m; ++r) x[i * m + r] += (double)L.x[i * m + r];
+                for (int nn = n0; nn < ni; nn += step) {
+                    const int64_t e = (int64_t)(i0 + nn) * m + r;
+                    x[e] += (double)lx[e];
+                }
             } else if (what == F_MB) {
-                const double *b = a.b64[p];
-                for (int r = 0; r < m; ++r) {
-                    L.b[i * m + r] = (T)b[i * m + r];
-                    L.x[i * m + r] = T(0);
+                for (int nn = n0; nn < ni; nn += step) {
+                    const int64_t e = (int64_t)(i0 + nn) * m + r;
+                    lb[e] = (T)b[e];
+                    lx[e] = T(0);
                 }
             } else if (what == F_CONVZ) {
-#pragma unroll
-                for (int r = 0; r < BMAXRHS; ++r)
-                    if (r < m) {
-                        const double z = (double)L.x[i * m + r];
-                        pr.Z[i * m + r] = z;
-                        acc[r] = fma(z, z, acc[r]);
-                    }
+                for (int nn = n0; nn < ni; nn += step) {
+                    const int64_t e = (int64_t)(i0 + nn) * m + r;
+                    const double z = (double)lx[e];
+                    Z[e] = z;
+                    acc = fma(z, z, acc);
+                }
             } else if (what == F_DOT) {
-                const double *Vi = pr.V + (int64_t)iarg * nm;
-#pragma unroll
-                for (int r = 0; r < BMAXRHS; ++r)
-                    if (r < m) acc[r] = fma(pr.Z[i * m + r], Vi[i * m + r], acc[r]);
+                const double *__restrict__ Vi = V + (int64_t)iarg * nm;
+                for (int nn = n0; nn < ni; nn += step) {
+                    const int64_t e = (int64_t)(i0 + nn) * m + r;
+                    acc = fma(Z[e], Vi[e], acc);
+                }
             } else if (what == F_AXPY) {
-                const double *Vi = pr.V + (int64_t)iarg * nm;
-                for (int r = 0; r < m; ++r)
-                    if (!a.frozen[q0 + r]) {
-                        const double h = a.H[(int64_t)(q0 + r) * a.hstride + iarg * a.restart + jarg];
-                        pr.Z[i * m + r] = fma(-h, Vi[i * m + r], pr.Z[i * m + r]);
+                if (!a.frozen[q]) {
+                    const double *__restrict__ Vi = V + (int64_t)iarg * nm;
+                    const double h = a.H[(int64_t)q * a.hstride + iarg * a.restart + jarg];
+                    for (int nn = n0; nn < ni; nn += step) {
+                        const int64_t e = (int64_t)(i0 + nn) * m + r;
+                        Z[e] = fma(-h, Vi[e], Z[e]);
                     }
+                }
             } else if (what == F_NRMZ) {
-#pragma unroll
-                for (int r = 0; r < BMAXRHS; ++r)
-                    if (r < m) acc[r] = fma(pr.Z[i * m + r], pr.Z[i * m + r], acc[r]);
+                for (int nn = n0; nn < ni; nn += step) {
+                    const int64_t e = (int64_t)(i0 + nn) * m + r;
+                    acc = fma(Z[e], Z[e], acc);
+                }
             } else if (what == F_SCALEV) {
-                double *Vj = pr.V + (int64_t)jarg * nm;
-                for (int r = 0; r < m; ++r)
-                    if (!a.frozen[q0 + r] || jarg == 0) Vj[i * m + r] = pr.Z[i * m + r] * a.inv[q0 + r];
+                if (!a.frozen[q] || jarg == 0) {
+                    double *__restrict__ Vj = pr.V + (int64_t)jarg * nm;
+                    const double inv = a.inv[q];
+                    for (int nn = n0; nn < ni; nn += step) {
+                        const int64_t e = (int64_t)(i0 + nn) * m + r;
+                        Vj[e] = Z[e] * inv;
+                    }
+                }
             } else {  // F_XUPD
-                double *x = a.x64[p];
-                for (int r = 0; r < m; ++r) {
-                    const int nc = a.jcols[q0 + r];
-                    double sx = x[i * m + r];
-                    for (int kk = 0; kk < nc; ++kk)
-                        sx = fma(a.y[(int64_t)(q0 + r) * a.restart + kk], pr.V[(int64_t)kk * nm + i * m + r], sx);
-                    x[i * m + r] = sx;
+                const int nc = a.jcols[q];
+                const double *__restrict__ y = a.y + (int64_t)q * a.restart;
+                for (int nn = n0; nn < ni; nn += step) {
+                    const int64_t e = (int64_t)(i0 + nn) * m + r;
+                    double sx = x[e];
+                    for (int kk = 0; kk < nc; ++kk) sx = fma(y[kk], V[(int64_t)kk * nm + e], sx);
+                    x[e] = sx;
                 }
             }
         }
-        if (what == F_BNORM || what == F_RESID || what == F_CONVZ || what == F_DOT || what == F_NRMZ)
-            cta_sum8(acc, m, red, a.part + (int64_t)k * BMAXRHS);
+        if (reduces) cta_sum_by_rhs(acc, m, red, a.part + (int64_t)k * BMAXRHS);
     }
 }
 
@@ -426,39 +479,43 @@ enum {
 };
 
 template <typename T>
-__device__ void stage_prob(const BArgs &a, const BProb<T> *P, int what, int iarg, int jarg, int ph, bool first) {
+__device__ void stage_prob(const BArgs &a, const BProb<T> *P, int what, int iarg, int jarg, int ph, bool first,
+                           double *wsum) {
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     if ((what == P_NORM || what == P_BETA || what == P_GIVENS) && gid == 0) a.ctl->cnt[ph ^ 1] = 0;
     const int R = a.restart;
-    for (int p = gid; p < a.nprob; p += gridDim.x * blockDim.x) {
-        if (a.state[p] != ST_ACTIVE) continue;
+    const int lane = threadIdx.x & 31;
+    double *ws = wsum + (threadIdx.x >> 5) * BMAXRHS;
+    const bool sums = what != P_SOLVEY;
+    // one warp per problem: the lanes sum the problem's tile partials (lane
+    // l takes tiles k0 + l, k0 + l + 32, ...; fixed shuffle tree), lane 0 then
+    // advances the problem's state
+    for (int p = gid >> 5; p < a.nprob; p += (gridDim.x * blockDim.x) >> 5) {
+        if (a.state[p] != ST_ACTIVE) continue;  // warp-uniform
         if ((what == P_HSTORE || what == P_GIVENS) && !a.work[p]) continue;
         const int m = P[p].m;
         const int q0 = p * BMAXRHS;
-        double ss[BMAXRHS];
-#pragma unroll
-        for (int r = 0; r < BMAXRHS; ++r) ss[r] = 0.0;
-        if (what != P_SOLVEY)
-            for (int k = a.ftile_of[p]; k < a.ftile_of[p + 1]; ++k)
-#pragma unroll
-                for (int r = 0; r < BMAXRHS; ++r)
-                    if (r < m) ss[r] += __ldcg(a.part + (int64_t)k * BMAXRHS + r);
-        if (what == P_NORMB) {
-#pragma unroll
-            for (int r = 0; r < BMAXRHS; ++r)
-                if (r < m) a.nb[q0 + r] = sqrt(ss[r]);
-        } else if (what == P_NMB) {
-#pragma unroll
-            for (int r = 0; r < BMAXRHS; ++r)
-                if (r < m) a.nmb[q0 + r] = sqrt(ss[r]);
+        if (sums) {
+            const int k0 = a.ftile_of[p], k1 = a.ftile_of[p + 1];
+            for (int r = 0; r < m; ++r) {
+                double v = 0.0;
+                for (int k = k0 + lane; k < k1; k += 32) v += __ldcg(a.part + (int64_t)k * BMAXRHS + r);
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) ws[r] = v;
+            }
+        }
+        __syncwarp();
+        if (lane != 0) continue;
+        auto tsum = [&](int r) { return ws[r]; };
+        if (what == P_NORMB || what == P_NMB) {
+            double *dst = what == P_NORMB ? a.nb : a.nmb;
+            for (int r = 0; r < m; ++r) dst[q0 + r] = sqrt(tsum(r));
         } else if (what == P_NORM) {
             double worst = 0.0;
             bool conv = true, bad = false;
-#pragma unroll
-            for (int r = 0; r < BMAXRHS; ++r) {
-                if (r >= m) break;
+            for (int r = 0; r < m; ++r) {
                 const double nb = a.nb[q0 + r];
-                const double rel = nb > 0.0 ? sqrt(ss[r]) / nb : 0.0;
+                const double rel = nb > 0.0 ? sqrt(tsum(r)) / nb : 0.0;
                 a.rel[q0 + r] = rel;
                 if (!(rel <= a.ctl->tol)) conv = false;
                 if (!isfinite(rel)) bad = true;
@@ -475,13 +532,12 @@ __device__ void stage_prob(const BArgs &a, const BProb<T> *P, int what, int iarg
             if (st == ST_ACTIVE) atomicAdd(&a.ctl->cnt[ph], 1);
         } else if (what == P_BETA) {
             int ext = 0;
-#pragma unroll
-            for (int r = 0; r < BMAXRHS; ++r) {
-                if (r >= m) break;
+            for (int r = 0; r < m; ++r) {
                 const int q = q0 + r;
-                const double beta = sqrt(ss[r]);
+                const double ss = tsum(r);
+                const double beta = sqrt(ss);
                 a.g[(int64_t)q * (R + 1)] = beta;
-                a.inv[q] = beta > 0.0 ? 1.0 / sqrt(ss[r]) : 0.0;
+                a.inv[q] = beta > 0.0 ? 1.0 / sqrt(ss) : 0.0;
                 a.jcols[q] = 0;
                 a.frozen[q] = !(beta > 0.0) || a.iters[p] >= a.ctl->maxit;
                 ext += !a.frozen[q];
@@ -489,23 +545,21 @@ __device__ void stage_prob(const BArgs &a, const BProb<T> *P, int what, int iarg
             a.work[p] = ext > 0;
             if (ext) atomicAdd(&a.ctl->cnt[ph], ext);
         } else if (what == P_HSTORE) {
-#pragma unroll
-            for (int r = 0; r < BMAXRHS; ++r)
-                if (r < m && !a.frozen[q0 + r]) a.H[(int64_t)(q0 + r) * a.hstride + iarg * R + jarg] = ss[r];
+            for (int r = 0; r < m; ++r)
+                if (!a.frozen[q0 + r]) a.H[(int64_t)(q0 + r) * a.hstride + iarg * R + jarg] = tsum(r);
         } else if (what == P_GIVENS) {
             const int j = jarg;
             a.iters[p] += 1;
             const bool limit = a.iters[p] >= a.ctl->maxit;
             int ext = 0;
-#pragma unroll
-            for (int r = 0; r < BMAXRHS; ++r) {
-                if (r >= m) break;
+            for (int r = 0; r < m; ++r) {
                 const int q = q0 + r;
                 if (a.frozen[q]) continue;
                 double *H = a.H + (int64_t)q * a.hstride;
                 double *cs = a.cs + (int64_t)q * R, *sn = a.sn + (int64_t)q * R, *g = a.g + (int64_t)q * (R + 1);
-                const double hn = sqrt(ss[r]);
-                a.inv[q] = hn > 0.0 ? 1.0 / sqrt(ss[r]) : 0.0;
+                const double ss = tsum(r);
+                const double hn = sqrt(ss);
+                a.inv[q] = hn > 0.0 ? 1.0 / sqrt(ss) : 0.0;
                 H[(j + 1) * R + j] = hn;
                 for (int i = 0; i < j; ++i) {
                     const double x0 = H[i * R + j], x1 = H[(i + 1) * R + j];
@@ -556,9 +610,10 @@ __device__ __forceinline__ void vcycle_stages(const BArgs &a, const BProb<T> *P,
 // cleared only by a later counting stage), and every loop is bounded by the
 // iteration limit in any case.
 template <typename T>
-__global__ void __launch_bounds__(512, 1) k_batch_solve(BArgs a) {
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_batch_solve(BArgs a) {
     cg::grid_group grid = cg::this_grid();
-    __shared__ double red[16][BMAXRHS];
+    __shared__ double red[512];
+    __shared__ double wsum[16 * BMAXRHS];
     const BProb<T> *P = static_cast<const BProb<T> *>(a.probs);
     const int maxit = a.ctl->maxit;
     // counting stages write ctl->cnt[ph] after flipping ph and clear the other
@@ -566,7 +621,7 @@ __global__ void __launch_bounds__(512, 1) k_batch_solve(BArgs a) {
     int ph = 0;
     stage_fine<T>(a, P, F_BNORM, 0, 0, red);
     grid.sync();
-    stage_prob<T>(a, P, P_NORMB, 0, 0, ph, true);
+    stage_prob<T>(a, P, P_NORMB, 0, 0, ph, true, wsum);
     grid.sync();
     stage_fine<T>(a, P, F_ZEROX, 0, 0, red);
     grid.sync();
@@ -576,13 +631,13 @@ __global__ void __launch_bounds__(512, 1) k_batch_solve(BArgs a) {
         vcycle_stages<T>(a, P, grid);
         stage_fine<T>(a, P, F_CONVZ, 0, 0, red);
         grid.sync();
-        stage_prob<T>(a, P, P_NMB, 0, 0, ph, true);
+        stage_prob<T>(a, P, P_NMB, 0, 0, ph, true, wsum);
         grid.sync();
     }
     stage_fine<T>(a, P, F_RESID, 0, 0, red);
     grid.sync();
     ph ^= 1;
-    stage_prob<T>(a, P, P_NORM, 0, 0, ph, true);
+    stage_prob<T>(a, P, P_NORM, 0, 0, ph, true, wsum);
     grid.sync();
     if (a.method != CS_GMRES) {
         for (int it = 0; it < maxit; ++it) {
@@ -593,7 +648,7 @@ __global__ void __launch_bounds__(512, 1) k_batch_solve(BArgs a) {
             stage_fine<T>(a, P, F_RESID, 0, 0, red);
             grid.sync();
             ph ^= 1;
-            stage_prob<T>(a, P, P_NORM, 0, 0, ph, false);
+            stage_prob<T>(a, P, P_NORM, 0, 0, ph, false, wsum);
             grid.sync();
         }
         return;
@@ -605,7 +660,7 @@ __global__ void __launch_bounds__(512, 1) k_batch_solve(BArgs a) {
         stage_fine<T>(a, P, F_CONVZ, 0, 0, red);
         grid.sync();
         ph ^= 1;
-        stage_prob<T>(a, P, P_BETA, 0, 0, ph, false);
+        stage_prob<T>(a, P, P_BETA, 0, 0, ph, false, wsum);
         grid.sync();
         stage_fine<T>(a, P, F_SCALEV, 0, 0, red);
         grid.sync();
@@ -619,7 +674,7 @@ __global__ void __launch_bounds__(512, 1) k_batch_solve(BArgs a) {
             for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt
                 stage_fine<T>(a, P, F_DOT, i, j, red);
                 grid.sync();
-                stage_prob<T>(a, P, P_HSTORE, i, j, ph, false);
+                stage_prob<T>(a, P, P_HSTORE, i, j, ph, false, wsum);
                 grid.sync();
                 stage_fine<T>(a, P, F_AXPY, i, j, red);
                 grid.sync();
@@ -627,21 +682,21 @@ __global__ void __launch_bounds__(512, 1) k_batch_solve(BArgs a) {
             stage_fine<T>(a, P, F_NRMZ, 0, j, red);
             grid.sync();
             ph ^= 1;
-            stage_prob<T>(a, P, P_GIVENS, 0, j, ph, false);
+            stage_prob<T>(a, P, P_GIVENS, 0, j, ph, false, wsum);
             grid.sync();
             stage_fine<T>(a, P, F_SCALEV, 0, j + 1, red);
             grid.sync();
         }
         // every problem still active solves its small systems and updates x
         // (work flags may have cleared: these stages are gated on the state)
-        stage_prob<T>(a, P, P_SOLVEY, 0, 0, ph, false);
+        stage_prob<T>(a, P, P_SOLVEY, 0, 0, ph, false, wsum);
         grid.sync();
         stage_fine<T>(a, P, F_XUPD, 0, 0, red);
         grid.sync();
         stage_fine<T>(a, P, F_RESID, 0, 0, red);
         grid.sync();
         ph ^= 1;
-        stage_prob<T>(a, P, P_NORM, 0, 0, ph, false);
+        stage_prob<T>(a, P, P_NORM, 0, 0, ph, false, wsum);
         grid.sync();
     }
 }
