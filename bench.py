@@ -51,9 +51,9 @@ def args_():
     p.add_argument("--order", default="RF")
     p.add_argument("--cpu-n", type=int, default=64, help="side of the oracle's bounded sample")
     p.add_argument("--no-extras", action="store_true", help="time the chosen form only")
-    p.add_argument("--learned-meshes", type=int, default=64, help="training meshes of the learned setup")
+    p.add_argument("--learned-meshes", type=int, default=128, help="training meshes of the learned setup")
     p.add_argument("--learned-n", type=int, default=127, help="interior nodes per side of a training mesh")
-    p.add_argument("--learned-steps", type=int, default=2000, help="Adam steps")
+    p.add_argument("--learned-steps", type=int, default=6000, help="Adam steps")
     p.add_argument("--batch-count", type=int, default=32, help="problems of the batched workload timed")
     p.add_argument("--batch-maxit", type=int, default=400, help="GMRES steps allowed per problem")
     p.add_argument("--batch-single", type=int, default=4, help="problems also solved on the single-problem path")
@@ -218,14 +218,33 @@ def learned_section(a, cmg, problems, dev):
                         "loss_last": float(np.mean(hist[-50:])), "generate_s": t_gen, "label_s": t_label,
                         "train_s": t_train}}
     used, ratio = cmg.learned_status(res["learned"][0])
-    out["accepted"] = bool(used == 1)
-    out["level1_objective_ratio"] = ratio
-    for name in ("exact", "learned"):
+    out["predicted_blocks_in_use"] = bool(used == 1)
+    out["level1_objective_ratio_predicted"] = ratio
+    out["blocks"] = cmg.learned_stats(res["learned"][0])
+    # the method without the network at the learned path's setup cost: the
+    # exact level-1 blocks repeated nu = 3 times (a nu = 1 cascade applied
+    # mu = 3 times per smoothing: the same sweeps per cycle)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cmg.setup_cascade(h5, "additive", nu=1)
+    torch.cuda.synchronize()
+    e0.record(s)
+    c1 = cmg.setup_cascade(h5, "additive", nu=1)
+    e1.record(s)
+    torch.cuda.synchronize()
+    res["level1_repeated"] = (c1, e0.elapsed_time(e1), None)
+    for name in ("exact", "learned", "level1_repeated"):
         c, setup_ms, wall_ms = res[name]
+        mu = 3 if name == "level1_repeated" else 1
         x = torch.zeros(A5.N, dtype=torch.float64, device=dev)
-        info = cmg.solve(h5, c, b5, x, method="gmres", tol=1e-10, maxit=300, raise_on_error=False)
+        info = cmg.solve(h5, c, b5, x, method="gmres", tol=1e-10, maxit=300, mu_pre=mu, mu_post=mu,
+                         raise_on_error=False)
+        x = torch.zeros(A5.N, dtype=torch.float64, device=dev)
+        st = cmg.solve(h5, c, b5, x, method="stationary", tol=1e-10, maxit=40, mu_pre=mu, mu_post=mu,
+                       raise_on_error=False)
         out[name] = {"setup_ms": setup_ms, "gmres_iterations": info.iterations, "converged": info.converged,
-                     "rho": oracle.rho_from_history(info.history) if len(info.history) > 2 else None}
+                     "rho_gmres": oracle.rho_from_history(info.history) if len(info.history) > 2 else None,
+                     "rho_stationary": oracle.rho_from_history(st.history) if len(st.history) > 2 else None}
     return out
 
 

@@ -114,9 +114,11 @@ typedef struct {
     const cs_mlp *model; /* optional learned setup of the finest level (2D, blocks, additive):
                       Lambda of every block predicted from its operator window (see the
                       learned-setup section below); NULL: exact setup */
-    double model_tol;    /* accept the prediction when its level-1 Frobenius objective, summed
-                      over the level, is <= (1 + model_tol) x the exact one (default 0.05);
-                      otherwise the exact setup runs (fallback) */
+    double model_tol;    /* per block: keep the prediction of a full block when its level-1
+                      Frobenius objective is <= (1 + model_tol) x that of the exact level-1
+                      block (default 0.05); rejected and partial edge blocks take the exact
+                      level-1 block at every cascade step; if no block is kept the exact
+                      setup of the level runs (fallback) */
 } cs_cascade_opts;
 
 /* Build the cascade (Lambda_l, l = 1..nu; multiplicative: Lambda_{l,k},
@@ -365,10 +367,16 @@ cs_status cs_block_features(const cs_hierarchy *h, int level, float *F, cs_strea
 /* Training targets from an exact additive cascade: prescaled blocks
  * W^-1 Lambda_l W^-1, l = 1..nu, into T [nblocks x nu bs^4] (device, FP32). */
 cs_status cs_block_targets(const cs_cascade *c, int level, float *T, cs_stream stream);
-/* After cs_setup_cascade with a model: *used = 1 if the prediction was
- * accepted, 0 if the exact setup ran instead, -1 without a model; *ratio =
- * level-1 Frobenius objective of the prediction / exact. */
+/* After cs_setup_cascade with a model: *used = 1 if predicted blocks are in
+ * use, 0 if the exact setup ran instead, -1 without a model; *ratio = level-1
+ * Frobenius objective of the prediction (every block) / exact. */
 cs_status cs_learned_status(const cs_cascade *c, int *used, double *ratio);
+/* Per-block detail of the learned setup: blocks of the finest level, full
+ * blocks, blocks whose prediction is in use; level-1 Frobenius objective of
+ * the prediction and of the Lambda in use (predicted or exact level-1 block),
+ * each over the exact one. */
+cs_status cs_learned_stats(const cs_cascade *c, int64_t *blocks, int64_t *full_blocks, int64_t *predicted_blocks,
+                           double *ratio_predicted, double *ratio_used);
 
 /* -------------------------------------------------------------- queries */
 typedef struct {

@@ -20,7 +20,7 @@ from ._capi import CascadeError
 
 __all__ = ["setup_hierarchy", "setup_cascade", "vcycle", "solve", "smooth", "sweep", "sweep_rhs", "residual_restrict",
            "prolong_correct", "coarse_solve", "residual", "query_level", "export_operator", "export_colours",
-           "export_lambda", "kernel_launches", "smooth_noalloc", "MLP", "block_features", "block_targets", "learned_status", "setup_many", "Batch", "solve_batched", "Hierarchy", "Cascade", "SolveInfo",
+           "export_lambda", "kernel_launches", "smooth_noalloc", "MLP", "block_features", "block_targets", "learned_status", "learned_stats", "setup_many", "Batch", "solve_batched", "Hierarchy", "Cascade", "SolveInfo",
            "CascadeError"]
 
 
@@ -167,11 +167,21 @@ def setup_cascade(h: Hierarchy, kind="additive", nu=3, prescale=True, alpha=0, l
 
 
 def learned_status(c):
-    """(used, ratio): 1 prediction accepted / 0 exact fallback / -1 no model;
-    level-1 Frobenius objective of the prediction over the exact one."""
+    """(used, ratio): 1 predicted blocks in use / 0 exact fallback / -1 no
+    model; level-1 Frobenius objective of the prediction over the exact one."""
     used, ratio = C.c_int(0), C.c_double(0.0)
     _capi.check(_capi.lib().cs_learned_status(c.ptr, C.byref(used), C.byref(ratio)), "cs_learned_status")
     return int(used.value), float(ratio.value)
+
+
+def learned_stats(c):
+    """Per-block detail of the learned setup (``cs_learned_stats``)."""
+    nb, nf, npred = C.c_int64(), C.c_int64(), C.c_int64()
+    rp, ru = C.c_double(), C.c_double()
+    _capi.check(_capi.lib().cs_learned_stats(c.ptr, C.byref(nb), C.byref(nf), C.byref(npred), C.byref(rp),
+                                             C.byref(ru)), "cs_learned_stats")
+    return {"blocks": nb.value, "full_blocks": nf.value, "predicted_blocks": npred.value,
+            "ratio_predicted": rp.value, "ratio_used": ru.value}
 
 
 class MLP:

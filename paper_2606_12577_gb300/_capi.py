@@ -110,6 +110,8 @@ _SIGS = {
     "cs_block_features": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "cs_block_targets": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "cs_learned_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "cs_learned_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "cs_setup_many": (C.c_int, [C.c_int, C.POINTER(cs_stencil), C.POINTER(cs_hierarchy_opts),
                                 C.POINTER(cs_cascade_opts), C.c_int, C.c_void_p, C.POINTER(C.c_void_p),
                                 C.POINTER(C.c_void_p)]),

@@ -456,17 +456,15 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
                 double *lam1 = nullptr;
                 cs_status r = dalloc_t(&lam1, (size_t)lam_step(L), nullptr, s);
                 if (r != CS_OK) return r;
-                bool accepted = false;
-                double ratio = 0.0;
                 r = cascade_setup_level_blocks(h, 0, CS_ADDITIVE, 1, o->prescale, lam1, s);
                 if (r == CS_OK)
                     r = learned_setup_level0(h, c, const_cast<cs_mlp *>(o->model), o->model_tol > 0 ? o->model_tol : 0.05,
-                                             c->lam[0], lam1, &accepted, &ratio, s);
+                                             c->lam[0], lam1, s);
                 dfree(lam1, s);
                 if (r != CS_OK) return r;
-                c->learned_used = accepted ? 1 : 0;
-                c->learned_ratio = ratio;
-                if (accepted) return CS_OK;
+                // no block kept its prediction: the exact setup of the whole level
+                c->learned_used = c->learned_accepted > 0 ? 1 : 0;
+                if (c->learned_used) return CS_OK;
             }
             return level_setup(0, s);
         };
@@ -716,6 +714,17 @@ cs_status cs_learned_status(const cs_cascade *c, int *used, double *ratio) {
     if (!c) { set_error("null argument"); return CS_ERR_ARG; }
     if (used) *used = c->learned_used;
     if (ratio) *ratio = c->learned_ratio;
+    return CS_OK;
+}
+
+cs_status cs_learned_stats(const cs_cascade *c, int64_t *blocks, int64_t *full_blocks, int64_t *predicted_blocks,
+                           double *ratio_predicted, double *ratio_used) {
+    if (!c) { set_error("null argument"); return CS_ERR_ARG; }
+    if (blocks) *blocks = c->learned_blocks;
+    if (full_blocks) *full_blocks = c->learned_full;
+    if (predicted_blocks) *predicted_blocks = c->learned_used == 1 ? c->learned_accepted : 0;
+    if (ratio_predicted) *ratio_predicted = c->learned_ratio;
+    if (ratio_used) *ratio_used = c->learned_used == 1 ? c->learned_ratio_used : 1.0;
     return CS_OK;
 }
 

@@ -92,10 +92,12 @@ struct cs_cascade {
     int gm_restart = 0;
     double *gm_V = nullptr, *gm_h = nullptr;
     int64_t bytes = 0;
-    // learned setup of the finest level: 1 used, 0 fell back to the exact
-    // setup, -1 no model; ratio of level-1 Frobenius objectives (model / exact)
+    // learned setup of the finest level: 1 used (some blocks predicted), 0
+    // fell back to the exact setup, -1 no model; level-1 Frobenius objectives
+    // of the prediction and of the Lambda in use, over the exact one; block counts
     int learned_used = -1;
-    double learned_ratio = 0.0;
+    double learned_ratio = 0.0, learned_ratio_used = 0.0;
+    int64_t learned_blocks = 0, learned_full = 0, learned_accepted = 0;
 };
 
 namespace csx {
@@ -188,7 +190,7 @@ cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, in
 cs_status cascade_setup_level_blocks(const cs_hierarchy *h, int l, int kind, int nu, int prescale, double *lam,
                                      cudaStream_t s);
 cs_status learned_setup_level0(const cs_hierarchy *h, cs_cascade *c, cs_mlp *M, double tol, double *lam,
-                               const double *lam_exact1, bool *accepted, double *ratio, cudaStream_t s);
+                               const double *lam_exact1, cudaStream_t s);
 // block cascade step (bs > 1): out_b = x_b - Lambda_b^(T) (A x - b)_b over all
 // blocks or the blocks of one colour
 template <typename T>

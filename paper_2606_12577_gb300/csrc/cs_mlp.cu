@@ -538,13 +538,34 @@ cs_status cs_block_targets(const cs_cascade *c, int level, float *T, cs_stream s
 
 namespace csx {
 
+// Per block: the prediction stays when the block is full (all bs^2 nodes
+// inside the grid) and its level-1 objective is within (1 + tol) of the exact
+// one; otherwise every cascade step of the block takes the exact level-1
+// block.  flag[b] = 1 for a kept prediction.
+__global__ void k_block_accept(Grid g, int bs, int nbx, int64_t nblocks, int nu, double tol,
+                               const double *__restrict__ obj, const double *__restrict__ lam_exact1,
+                               double *__restrict__ lam, int *__restrict__ flag) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    const int bx = (int)(b % nbx), by = (int)(b / nbx);
+    const int nm2 = bs * bs * bs * bs;
+    const bool full = bs * bx + bs <= g.nx && bs * by + bs <= g.ny;
+    const double op = obj[b], oe = obj[nblocks + b];
+    const bool ok = full && isfinite(op) && op <= (1.0 + tol) * oe;
+    flag[b] = ok ? 1 : 0;
+    if (ok) return;
+    for (int l = 0; l < nu; ++l)
+        for (int e = 0; e < nm2; ++e) lam[((int64_t)l * nblocks + b) * nm2 + e] = lam_exact1[b * nm2 + e];
+}
+
 // Learned setup of the finest level (see cs_cascade_opts.model): features,
-// MLP inference, unscaling; accepted when the level-1 Frobenius objective of
-// the prediction summed over the level is within `tol` of the exact one
-// (whose level-1 blocks cost one least-squares problem each); returns
-// *accepted = false otherwise, leaving lam untouched.
+// MLP inference and unscaling for every block, then the per-block check of
+// the level-1 Frobenius objective against the exact level-1 blocks (which
+// cost one least-squares problem each); rejected and partial blocks take the
+// exact level-1 block at every step.  Records the counts and objective
+// ratios in c.
 cs_status learned_setup_level0(const cs_hierarchy *h, cs_cascade *c, cs_mlp *M, double tol, double *lam,
-                               const double *lam_exact1, bool *accepted, double *ratio, cudaStream_t s) {
+                               const double *lam_exact1, cudaStream_t s) {
     const Level &L = h->lev[0];
     const int nm = L.bs * L.bs, win = L.bs + 2;
     if (M->nin != nm * win * win || M->nout != c->nu * nm * nm) {
@@ -553,36 +574,53 @@ cs_status learned_setup_level0(const cs_hierarchy *h, cs_cascade *c, cs_mlp *M, 
     }
     float *F = nullptr, *Y = nullptr;
     double *obj = nullptr;
+    int *flag = nullptr;
     cs_status rc = CS_OK;
     std::vector<double> op, oe;
+    std::vector<int> fl;
     const unsigned nb = (unsigned)((L.nblocks + 127) / 128);
     if ((rc = dalloc_t(&F, (size_t)L.nblocks * M->nin, nullptr, s)) != CS_OK) goto done;
     if ((rc = dalloc_t(&Y, (size_t)L.nblocks * M->nout, nullptr, s)) != CS_OK) goto done;
     if ((rc = dalloc_t(&obj, (size_t)2 * L.nblocks, nullptr, s)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&flag, (size_t)L.nblocks, nullptr, s)) != CS_OK) goto done;
     k_block_features<<<nb, 128, 0, s>>>(L.g, L.bs, L.nbx, L.nblocks, L.kind, L.A, F);
     count_launch();
     if ((rc = cs_mlp_forward(M, (int)L.nblocks, F, Y, s)) != CS_OK) goto done;
     k_block_unscale<<<nb, 128, 0, s>>>(L.g, L.bs, L.nbx, L.nblocks, c->nu, L.kind, L.A, Y, lam);
     k_level1_objective<<<nb, 128, 0, s>>>(L.g, L.bs, L.nbx, L.nblocks, L.kind, L.A, lam, obj);
     k_level1_objective<<<nb, 128, 0, s>>>(L.g, L.bs, L.nbx, L.nblocks, L.kind, L.A, lam_exact1, obj + L.nblocks);
-    count_launch(3);
+    k_block_accept<<<nb, 128, 0, s>>>(L.g, L.bs, L.nbx, L.nblocks, c->nu, tol, obj, lam_exact1, lam, flag);
+    count_launch(4);
     op.resize(L.nblocks);
     oe.resize(L.nblocks);
+    fl.resize(L.nblocks);
     if (cudaMemcpyAsync(op.data(), obj, sizeof(double) * L.nblocks, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(oe.data(), obj + L.nblocks, sizeof(double) * L.nblocks, cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
+        cudaMemcpyAsync(fl.data(), flag, sizeof(int) * L.nblocks, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         rc = cuda_fail(cudaGetLastError(), "learned setup", __FILE__, __LINE__);
         goto done;
     }
     {
-        double sp = 0.0, se = 0.0;
-        for (int64_t b = 0; b < L.nblocks; ++b) { sp += op[b]; se += oe[b]; }
-        *ratio = se > 0 ? sp / se : 1.0;
-        *accepted = std::isfinite(sp) && sp <= (1.0 + tol) * se;
+        double sp = 0.0, se = 0.0, su = 0.0;
+        int64_t nacc = 0, nfull = 0;
+        for (int64_t b = 0; b < L.nblocks; ++b) {
+            const int bx = (int)(b % L.nbx), by = (int)(b / L.nbx);
+            nfull += L.bs * bx + L.bs <= L.g.nx && L.bs * by + L.bs <= L.g.ny;
+            sp += op[b];
+            se += oe[b];
+            su += fl[b] ? op[b] : oe[b];
+            nacc += fl[b];
+        }
+        c->learned_ratio = se > 0 ? sp / se : 1.0;
+        c->learned_ratio_used = se > 0 ? su / se : 1.0;
+        c->learned_blocks = L.nblocks;
+        c->learned_full = nfull;
+        c->learned_accepted = nacc;
     }
 done:
-    dfree(F, s); dfree(Y, s); dfree(obj, s);
+    dfree(F, s); dfree(Y, s); dfree(obj, s); dfree(flag, s);
     return rc;
 }
 

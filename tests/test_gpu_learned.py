@@ -80,6 +80,15 @@ def test_training_and_learned_setup(built):
     b = torch.tensor(problems.rhs(A.N, 5), dtype=torch.float64, device="cuda")
     used, ratio = cmg.learned_status(res["learned"][0])
     assert used in (0, 1) and ratio > 0
+    st = cmg.learned_stats(res["learned"][0])
+    assert st["blocks"] == 32 * 32 and st["full_blocks"] == 31 * 31  # 95 = 3 * 31 + 2
+    if used == 1:
+        # every kept block is within 5% of its exact level-1 objective and
+        # every other block carries the exact level-1 block
+        assert 0 < st["predicted_blocks"] <= st["full_blocks"]
+        assert st["ratio_used"] <= 1.05 + 1e-12
+    else:
+        assert st["predicted_blocks"] == 0
     rhos = {}
     for name in ("exact", "learned"):
         c = res[name][0]
