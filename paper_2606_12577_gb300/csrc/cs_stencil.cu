@@ -7,6 +7,8 @@
 // x hit L1/L2.  These kernels are HBM-bound in FP32 (bytes per node per
 // additive step: nst*sizeof(T) + 4*sizeof(T) for A, Lambda, b, x read, x
 // written).
+#include <algorithm>
+#include <cstdint>
 #include <cstdio>
 
 #include "cs_internal.cuh"
@@ -255,10 +257,133 @@ __global__ void __launch_bounds__(32 * (DIM == 3 ? BS * BS * BS : BS * BS) * BPC
     out[i * m + lane] = acc;
 }
 
+// The same block step in FP32 with four right-hand sides per lane (float4),
+// for m = 4 LPN right-hand sides and blocks of NMAX nodes with NMAX LPN
+// dividing 32: a warp holds 32 / (NMAX LPN) whole blocks, lane l takes node
+// (l / LPN) % NMAX of its block and right-hand sides 4 (l % LPN) .. +3.  Every
+// load of a step (coefficients, the x neighbourhood, b and the Lambda row) is
+// issued before the first use, the block's residuals meet through warp
+// shuffles (no CTA barrier), and warps stride over the blocks.  Per RHS and
+// node the arithmetic and its order are those of k_block_sweep_m.
+template <int DIM, int KIND, int BS, int LPN>
+__global__ void __launch_bounds__(256) k_block_sweep_m4(Grid g, int nbx, int nby, int64_t nblocks,
+                                                        const float *__restrict__ A, const float *__restrict__ lam,
+                                                        const float4 *__restrict__ B, const float4 *X, float4 *out,
+                                                        int colour, int transpose) {
+    using S = Sten<DIM, KIND>;
+    constexpr int NMAX = DIM == 3 ? BS * BS * BS : BS * BS;
+    constexpr int G = NMAX * LPN;  // lanes per block
+    constexpr int BPW = 32 / G;    // blocks per warp
+    const int lane = threadIdx.x & 31;
+    const int gsub = lane / G, lp = (lane % G) / LPN, rg = lane % LPN;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lx = lp % BS, ly = (lp / BS) % BS, lz = DIM == 3 ? lp / (BS * BS) : 0;
+    // block and node indices fit in 31 bits (the hierarchy checks N < 2^31): 32-bit index arithmetic
+    for (int64_t w = warp0; w * BPW < nblocks; w += nwarps) {
+        const int blk = (int)(w * BPW) + gsub;
+        const bool valid = blk < nblocks;
+        int bx = 0, by = 0, bz = 0;
+        if (valid) {
+            const int q = blk / nbx;
+            bx = blk - q * nbx;
+            if (DIM == 3) {
+                bz = q / nby;
+                by = q - bz * nby;
+            } else {
+                by = q;
+            }
+        }
+        const int ix = BS * bx + lx, iy = BS * by + ly, iz = DIM == 3 ? BS * bz + lz : 0;
+        const bool present = valid && ix < g.nx && iy < g.ny && (DIM == 2 || iz < g.nz);
+        const bool active = colour < 0 || ((((bx + 1) + (by + 1) + (DIM == 3 ? bz + 1 : 0)) & 1) == colour);
+        const int i = ix + g.nx * (iy + g.ny * iz);
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f), xo = r;
+        float lrow[NMAX];
+        if (present && active) {
+            const float *lb = lam + (int64_t)blk * (NMAX * NMAX);
+#pragma unroll
+            for (int q = 0; q < NMAX; ++q) lrow[q] = transpose ? lb[q * NMAX + lp] : lb[lp * NMAX + q];
+            float4 ax = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int s = 0; s < S::NST; ++s) {
+                int dx, dy, dz;
+                S::off(s, dx, dy, dz);
+                const bool in = (unsigned)(ix + dx) < (unsigned)g.nx && (unsigned)(iy + dy) < (unsigned)g.ny &&
+                                (DIM == 2 || (unsigned)(iz + dz) < (unsigned)g.nz);
+                const int j = i + dx + g.nx * (dy + g.ny * dz);
+                const float a = A[(int64_t)s * g.N + i];
+                const float4 xv = in ? X[(int64_t)j * LPN + rg] : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (dx == 0 && dy == 0 && dz == 0) xo = xv;
+                ax.x = fmaf(a, xv.x, ax.x);
+                ax.y = fmaf(a, xv.y, ax.y);
+                ax.z = fmaf(a, xv.z, ax.z);
+                ax.w = fmaf(a, xv.w, ax.w);
+            }
+            const float4 bv = B[(int64_t)i * LPN + rg];
+            r = make_float4(ax.x - bv.x, ax.y - bv.y, ax.z - bv.z, ax.w - bv.w);
+        } else if (present) {
+            xo = X[(int64_t)i * LPN + rg];
+        }
+        // residuals of the block's nodes (absent nodes: 0, their Lambda entries are 0 too)
+        float4 acc = xo;
+        const int base = gsub * G + rg;
+#pragma unroll
+        for (int q = 0; q < NMAX; ++q) {
+            const float rx = __shfl_sync(0xffffffffu, r.x, base + q * LPN);
+            const float ry = __shfl_sync(0xffffffffu, r.y, base + q * LPN);
+            const float rz = __shfl_sync(0xffffffffu, r.z, base + q * LPN);
+            const float rw = __shfl_sync(0xffffffffu, r.w, base + q * LPN);
+            if (present && active) {
+                acc.x = fmaf(-lrow[q], rx, acc.x);
+                acc.y = fmaf(-lrow[q], ry, acc.y);
+                acc.z = fmaf(-lrow[q], rz, acc.z);
+                acc.w = fmaf(-lrow[q], rw, acc.w);
+            }
+        }
+        if (present && (active || out != X)) out[(int64_t)i * LPN + rg] = acc;
+    }
+}
+
 template <typename T>
 cs_status launch_block_sweep_m(const Level &L, const T *A, const T *lam, const T *b, const T *x, T *out, int m,
                                int colour, bool transpose, cudaStream_t s) {
     const int tr = transpose ? 1 : 0;
+    if (sizeof(T) == sizeof(float) && m % 4 == 0 && L.bs == 2 && L.nmax * (m / 4) <= 32 &&
+        32 % (L.nmax * (m / 4)) == 0 && ((uintptr_t)b | (uintptr_t)x | (uintptr_t)out) % 16 == 0) {
+        const int lpn = m / 4, bpw = 32 / (L.nmax * lpn);
+        const int64_t warps = (L.nblocks + bpw - 1) / bpw;
+        int dev = 0, nsm = 0;
+        CSX_CUDA(cudaGetDevice(&dev));
+        CSX_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const unsigned grid = (unsigned)std::min<int64_t>((warps + 7) / 8, (int64_t)nsm * 8);
+        const float *Af = reinterpret_cast<const float *>(A), *lf = reinterpret_cast<const float *>(lam);
+        const float4 *b4 = reinterpret_cast<const float4 *>(b), *x4 = reinterpret_cast<const float4 *>(x);
+        float4 *o4 = reinterpret_cast<float4 *>(out);
+#define CSX_BSM4(DIM, LPN)                                                                                       \
+    do {                                                                                                         \
+        if (L.kind == STAR)                                                                                      \
+            k_block_sweep_m4<DIM, STAR, 2, LPN><<<grid, 256, 0, s>>>(L.g, L.nbx, L.nby, L.nblocks, Af, lf, b4, x4,  \
+                                                                     o4, colour, tr);                            \
+        else                                                                                                     \
+            k_block_sweep_m4<DIM, BOX, 2, LPN><<<grid, 256, 0, s>>>(L.g, L.nbx, L.nby, L.nblocks, Af, lf, b4, x4,   \
+                                                                    o4, colour, tr);                             \
+    } while (0)
+        if (L.g.dim == 2) {
+            if (lpn == 1) CSX_BSM4(2, 1);
+            else if (lpn == 2) CSX_BSM4(2, 2);
+            else if (lpn == 4) CSX_BSM4(2, 4);
+            else CSX_BSM4(2, 8);
+        } else {
+            if (lpn == 1) CSX_BSM4(3, 1);
+            else if (lpn == 2) CSX_BSM4(3, 2);
+            else CSX_BSM4(3, 4);
+        }
+#undef CSX_BSM4
+        CSX_CUDA(cudaGetLastError());
+        count_launch();
+        return CS_OK;
+    }
 #define CSX_BSM(DIM, KIND, BS, BPC)                                                                              \
     k_block_sweep_m<DIM, KIND, T, BS, BPC>                                                                       \
         <<<dim3((unsigned)((L.nbx + BPC - 1) / BPC), (unsigned)L.nby, (unsigned)L.nbz),                          \

@@ -112,7 +112,9 @@ def test_block_solve(built, name, bs, kind, method):
 
 @pytest.mark.parametrize("name,bs,kind,m", [("c2d_66", 2, "additive", 32), ("v2d_37", 3, "additive", 5),
                                             ("v3d_17", 2, "multiplicative", 32), ("v2d_37", 1, "additive", 7),
-                                            ("v3d_17", 1, "multiplicative", 3)])
+                                            ("v3d_17", 1, "multiplicative", 3), ("v2d_37", 2, "multiplicative", 16),
+                                            ("v2d_37", 2, "additive", 4), ("v3d_17", 2, "additive", 8),
+                                            ("v3d_17", 2, "multiplicative", 16)])
 def test_multi_rhs_block_steps(built, name, bs, kind, m):
     """A full forward and reverse cascade application built from cs_sweep_rhs
     steps (n_b x m block products) equals the oracle's smoother applied to
@@ -143,3 +145,27 @@ def test_multi_rhs_block_steps(built, name, bs, kind, m):
             got = _host(cur).astype(np.float64)
             ref = np.stack([oracle.smooth(ho, co, 0, B[:, r], X0[:, r], reverse=rev) for r in range(m)], axis=1)
             assert gu.rel_max(got, ref) <= tol, f"reverse={rev} {dt}"
+
+
+@pytest.mark.parametrize("m", [32, 16, 4])
+def test_multi_rhs_colour_steps_in_place(built, m):
+    """On a 5-point level red-black block steps may overwrite x in place
+    (block red-black is a graph colouring of the 5-point stencil): in-place
+    FP32 steps give bitwise the result of out-of-place ones."""
+    import torch
+
+    import paper_2606_12577_gb300 as cmg
+    A = PROBS["v2d_37"]()
+    hg = gu.gpu_hierarchy(A, block=2)
+    cg = cmg.setup_cascade(hg, "multiplicative", nu=2, lowp=True)
+    N = A.N
+    B = _dev(problems.uniform(41, N * m).reshape(N, m), torch.float32)
+    X0 = problems.uniform(42, N * m).reshape(N, m)
+    xin = _dev(X0, torch.float32)
+    cur, oth = _dev(X0, torch.float32), _dev(np.zeros((N, m)), torch.float32)
+    for st in range(2):
+        for col in (0, 1):
+            cmg.sweep_rhs(hg, cg, 0, st, B, xin, xin, m, colour=col)
+            cmg.sweep_rhs(hg, cg, 0, st, B, cur, oth, m, colour=col)
+            cur, oth = oth, cur
+    assert np.array_equal(_host(xin), _host(cur))
