@@ -103,7 +103,9 @@ typedef struct {
     int kind;      /* CS_ADDITIVE (Sec. 2.1) or CS_MULTIPLICATIVE (Sec. 2.2, red-black) */
     int nu;        /* depth, 1..8 */
     int prescale;  /* 1: elliptic prescaling W = diag(A_ii^-1/2) (Sec. 2.3.1); 0: none */
-    int alpha;     /* residual truncation (Algorithm 2); 0 = none (only 0 supported) */
+    int alpha;     /* residual truncation (Algorithm 2): after each row update keep the alpha columns
+                      of largest magnitude (ties: smaller column index); 0 = none; point blocks
+                      only (CS_ERR_UNSUPPORTED for block levels or with a model) */
     int lowp;      /* 1: also keep FP32 copies of the level operators and Lambda for
                       CS_FP32 cycles (iterative refinement) */
     int no_reuse;  /* 0 (default): on structured levels with a region of identical

@@ -422,7 +422,15 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
     *out = nullptr;
     if (o->kind != CS_ADDITIVE && o->kind != CS_MULTIPLICATIVE) { set_error("bad cascade kind"); return CS_ERR_ARG; }
     if (o->nu < 1 || o->nu > 8) { set_error("nu must be in 1..8"); return CS_ERR_ARG; }
-    if (o->alpha != 0) { set_error("residual truncation (alpha > 0) is not implemented"); return CS_ERR_UNSUPPORTED; }
+    if (o->alpha < 0) { set_error("alpha must be >= 0 (0: no truncation)"); return CS_ERR_ARG; }
+    if (o->alpha > 0) {
+        for (int l = 0; l + 1 < h->nlev; ++l)
+            if (h->lev[l].bs > 1) {
+                set_error("truncation (alpha > 0) is implemented for point blocks only");
+                return CS_ERR_UNSUPPORTED;
+            }
+        if (o->model) { set_error("truncation does not combine with the learned setup"); return CS_ERR_UNSUPPORTED; }
+    }
     cudaStream_t s = (cudaStream_t)stream;
     cs_cascade *c = new cs_cascade();
     c->h = h;
@@ -443,7 +451,7 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
             const Level &L = h->lev[l];
             if (L.bs > 1) return cascade_setup_level_blocks(h, l, c->kind, c->nu, o->prescale, c->lam[l], st);
             int64_t peak = 0;
-            return cascade_setup_level(h, l, c->kind, c->nu, o->prescale, !o->no_reuse, c->lam[l], st, &peak);
+            return cascade_setup_level(h, l, c->kind, c->nu, o->prescale, !o->no_reuse, o->alpha, c->lam[l], st, &peak);
         };
         auto finest = [&]() -> cs_status {
             const Level &L = h->lev[0];

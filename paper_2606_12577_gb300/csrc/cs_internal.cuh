@@ -185,8 +185,8 @@ constexpr int NRED = 1024;  // partial sums of a reduction
 cs_status galerkin_level(const Level &f, Level &c, bool reuse, cudaStream_t s);
 cs_status level_margin(Level &L, bool periodic, cudaStream_t s);
 cs_status coarse_factor(cs_hierarchy *h, cudaStream_t s);
-cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, double *lam,
-                              cudaStream_t s, int64_t *peak_bytes);
+cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, int alpha,
+                              double *lam, cudaStream_t s, int64_t *peak_bytes);
 cs_status cascade_setup_level_blocks(const cs_hierarchy *h, int l, int kind, int nu, int prescale, double *lam,
                                      cudaStream_t s);
 cs_status learned_setup_level0(const cs_hierarchy *h, cs_cascade *c, cs_mlp *M, double tol, double *lam,

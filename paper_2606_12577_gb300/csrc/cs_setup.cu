@@ -701,8 +701,60 @@ struct Off3 {
     bool operator==(const Off3 &o) const { return x == o.x && y == o.y && z == o.z; }
 };
 
+// Truncation of the updated rows (Algorithm 2, optional step): a row of the
+// step's colour keeps the alpha columns of largest |E_ij| -- ties go to the
+// smaller column index -- and the others are set to zero.  Candidates are the
+// row's offsets whose column lies in the grid (wrapped on periodic grids).
+// The alpha-th largest (value, column) pair is found by alpha passes of
+// "largest after the previous one", then one pass zeroes what ranks below it.
+template <int DIM>
+__global__ void __launch_bounds__(TBX *TBY) k_truncate_rows(Grid g, int periodic, int nn, const int *__restrict__ off,
+                                                             double *__restrict__ E, int alpha, int colour) {
+    const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
+    if (ix >= g.nx || iy >= g.ny) return;
+    if (colour >= 0 && (((ix + 1) + (iy + 1) + (DIM == 3 ? iz + 1 : 0)) & 1) != colour) return;
+    const int64_t N = g.N;
+    const int64_t i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
+    auto column = [&](int o, int64_t &j) {
+        int jx = ix + off[3 * o], jy = iy + off[3 * o + 1], jz = DIM == 3 ? iz + off[3 * o + 2] : 0;
+        if (periodic) {
+            jx = ((jx % g.nx) + g.nx) % g.nx;
+            jy = ((jy % g.ny) + g.ny) % g.ny;
+            jz = DIM == 3 ? ((jz % g.nz) + g.nz) % g.nz : 0;
+        } else if (jx < 0 || jx >= g.nx || jy < 0 || jy >= g.ny || (DIM == 3 && (jz < 0 || jz >= g.nz))) {
+            return false;
+        }
+        j = jx + (int64_t)g.nx * (jy + (int64_t)g.ny * jz);
+        return true;
+    };
+    double tn = INFINITY;  // threshold pair (tn, tc): the last one selected
+    int64_t tc = -1;
+    bool full = true;  // alpha pairs found
+    for (int a = 0; a < alpha; ++a) {
+        double bn = -1.0;
+        int64_t bc = 0;
+        for (int o = 0; o < nn; ++o) {
+            int64_t j;
+            if (!column(o, j)) continue;
+            const double v = E[(int64_t)o * N + i], n = v * v;
+            const bool after = n < tn || (n == tn && j > tc);
+            if (after && (n > bn || (n == bn && j < bc))) { bn = n; bc = j; }
+        }
+        if (bn < 0.0) { full = false; break; }
+        tn = bn;
+        tc = bc;
+    }
+    if (!full) return;  // no more candidates than alpha: all kept
+    for (int o = 0; o < nn; ++o) {
+        int64_t j;
+        if (!column(o, j)) continue;
+        const double v = E[(int64_t)o * N + i], n = v * v;
+        if (!(n > tn || (n == tn && j <= tc))) E[(int64_t)o * N + i] = 0.0;
+    }
+}
+
 template <int DIM, int KIND>
-static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse,
+static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, int alpha,
                                double *lam, cudaStream_t s, int64_t *peak) {
     using S = StenS<DIM, KIND>;
     constexpr int NST = S::NST;
@@ -712,7 +764,7 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
     const int ncol = kind == CS_MULTIPLICATIVE ? 2 : 1;
     dim3 gr = node_grid(g), bl = node_block();
     double *w = nullptr, *At = nullptr, *Ecur = nullptr, *Enxt = nullptr;
-    int *bad = nullptr, *pstart = nullptr, *cur_of = nullptr;
+    int *bad = nullptr, *pstart = nullptr, *cur_of = nullptr, *offs = nullptr;
     unsigned *pairs = nullptr;
     double2 *part = nullptr;
     cs_status rc = CS_OK;
@@ -854,6 +906,20 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
                 if (rc != CS_OK) goto done;
             }
             if (cudaGetLastError() != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "k_setup_rows", __FILE__, __LINE__); goto done; }
+            if (alpha > 0 && !last) {
+                std::vector<int> ho(3 * (size_t)nn);
+                for (int o = 0; o < nn; ++o) { ho[3 * o] = On[o].x; ho[3 * o + 1] = On[o].y; ho[3 * o + 2] = On[o].z; }
+                dfree(offs, s);
+                offs = nullptr;
+                if ((rc = dalloc_t(&offs, ho.size(), nullptr, s)) != CS_OK) goto done;
+                if (cudaMemcpyAsync(offs, ho.data(), ho.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+                    rc = cuda_fail(cudaGetLastError(), "copy offsets", __FILE__, __LINE__);
+                    goto done;
+                }
+                k_truncate_rows<DIM><<<gr, bl, 0, s>>>(g, h->periodic, nn, offs, Enxt, alpha, ncol == 2 ? k : -1);
+                count_launch();
+                if (cudaGetLastError() != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "k_truncate_rows", __FILE__, __LINE__); goto done; }
+            }
             dfree(Ecur, s);
             track(-(int64_t)Ocur.size() * N * 8);
             Ecur = Enxt;
@@ -863,20 +929,22 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
     }
 done:
     dfree(w, s); dfree(At, s); dfree(Ecur, s); dfree(Enxt, s); dfree(bad, s); dfree(pstart, s); dfree(cur_of, s);
-    dfree(pairs, s); dfree(part, s);
+    dfree(pairs, s); dfree(part, s); dfree(offs, s);
     if (peak) *peak = std::max(*peak, pk);
     return rc;
 }
 
-cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, double *lam,
-                              cudaStream_t s, int64_t *peak) {
+cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, int alpha,
+                              double *lam, cudaStream_t s, int64_t *peak) {
     const Level &L = h->lev[l];
+    // with truncation every row is computed (the repeated-row shortcut keeps deep rows unwritten)
+    if (alpha > 0) reuse = false;
     if (L.g.dim == 2) {
-        if (L.kind == STAR) return setup_level_t<2, STAR>(h, l, kind, nu, prescale, reuse, lam, s, peak);
-        return setup_level_t<2, BOX>(h, l, kind, nu, prescale, reuse, lam, s, peak);
+        if (L.kind == STAR) return setup_level_t<2, STAR>(h, l, kind, nu, prescale, reuse, alpha, lam, s, peak);
+        return setup_level_t<2, BOX>(h, l, kind, nu, prescale, reuse, alpha, lam, s, peak);
     }
-    if (L.kind == STAR) return setup_level_t<3, STAR>(h, l, kind, nu, prescale, reuse, lam, s, peak);
-    return setup_level_t<3, BOX>(h, l, kind, nu, prescale, reuse, lam, s, peak);
+    if (L.kind == STAR) return setup_level_t<3, STAR>(h, l, kind, nu, prescale, reuse, alpha, lam, s, peak);
+    return setup_level_t<3, BOX>(h, l, kind, nu, prescale, reuse, alpha, lam, s, peak);
 }
 
 

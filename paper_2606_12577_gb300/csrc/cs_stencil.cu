@@ -356,18 +356,23 @@ cs_status launch_block_sweep_m(const Level &L, const T *A, const T *lam, const T
         int dev = 0, nsm = 0;
         CSX_CUDA(cudaGetDevice(&dev));
         CSX_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        const unsigned grid = (unsigned)std::min<int64_t>((warps + 7) / 8, (int64_t)nsm * 8);
         const float *Af = reinterpret_cast<const float *>(A), *lf = reinterpret_cast<const float *>(lam);
         const float4 *b4 = reinterpret_cast<const float4 *>(b), *x4 = reinterpret_cast<const float4 *>(x);
         float4 *o4 = reinterpret_cast<float4 *>(out);
+        // one wave: as many CTAs as can be resident, so that no partial wave trails the strided loop
+#define CSX_BSM4_LAUNCH(DIM, KIND, LPN)                                                                          \
+    do {                                                                                                         \
+        int per = 0;                                                                                             \
+        CSX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_block_sweep_m4<DIM, KIND, 2, LPN>, 256, 0)); \
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8,                 \
+                                                                               (int64_t)nsm * std::max(per, 1))); \
+        k_block_sweep_m4<DIM, KIND, 2, LPN><<<grid, 256, 0, s>>>(L.g, L.nbx, L.nby, L.nblocks, Af, lf, b4, x4, o4,  \
+                                                                 colour, tr);                                    \
+    } while (0)
 #define CSX_BSM4(DIM, LPN)                                                                                       \
     do {                                                                                                         \
-        if (L.kind == STAR)                                                                                      \
-            k_block_sweep_m4<DIM, STAR, 2, LPN><<<grid, 256, 0, s>>>(L.g, L.nbx, L.nby, L.nblocks, Af, lf, b4, x4,  \
-                                                                     o4, colour, tr);                            \
-        else                                                                                                     \
-            k_block_sweep_m4<DIM, BOX, 2, LPN><<<grid, 256, 0, s>>>(L.g, L.nbx, L.nby, L.nblocks, Af, lf, b4, x4,   \
-                                                                    o4, colour, tr);                             \
+        if (L.kind == STAR) CSX_BSM4_LAUNCH(DIM, STAR, LPN);                                                     \
+        else CSX_BSM4_LAUNCH(DIM, BOX, LPN);                                                                     \
     } while (0)
         if (L.g.dim == 2) {
             if (lpn == 1) CSX_BSM4(2, 1);
@@ -380,6 +385,7 @@ cs_status launch_block_sweep_m(const Level &L, const T *A, const T *lam, const T
             else CSX_BSM4(3, 4);
         }
 #undef CSX_BSM4
+#undef CSX_BSM4_LAUNCH
         CSX_CUDA(cudaGetLastError());
         count_launch();
         return CS_OK;

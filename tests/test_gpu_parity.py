@@ -92,6 +92,46 @@ def test_lambda_parity(built, name, kind, nu):
         assert gu.rel_max(lg, lo) <= TOL, f"level {l}"
 
 
+@pytest.mark.parametrize("name,kind,alpha", [("v2d_37", "additive", 3), ("v2d_37", "multiplicative", 7),
+                                              ("v2d_37", "additive", 7), ("v3d_17", "additive", 7),
+                                              ("v3d_17", "multiplicative", 7)])
+def test_truncation_parity(built, name, kind, alpha):
+    """Truncation to the alpha largest columns per row after every update
+    (Algorithm 2's optional step, ties to the smaller column): Lambda on every
+    level equals the oracle's.  Variable coefficients keep the ranking free of
+    exact ties, which the two sides could otherwise break differently after
+    rounding."""
+    import paper_2606_12577_gb300 as cmg
+    A = PROBLEMS[name]()
+    ho = oracle.Hierarchy(A)
+    co = oracle.Cascade(ho, kind, nu=3, alpha=alpha)
+    cu = oracle.Cascade(ho, kind, nu=3)
+    hg = gu.gpu_hierarchy(A)
+    cg = cmg.setup_cascade(hg, kind, nu=3, alpha=alpha)
+    differs = False
+    for l in range(co.nlev):
+        lg = cmg.export_lambda(cg, l)
+        assert gu.rel_max(lg, co.lam(l)) <= TOL, f"level {l}"
+        differs |= gu.rel_max(co.lam(l), cu.lam(l)) > 1e-6
+    assert differs  # the truncation changed the cascade
+
+
+def test_truncation_limits(built):
+    """alpha at least the row length changes nothing; block levels and the
+    learned setup reject truncation."""
+    import paper_2606_12577_gb300 as cmg
+    A = PROBLEMS["v2d_37"]()
+    hg = gu.gpu_hierarchy(A)
+    full = cmg.setup_cascade(hg, "additive", nu=3)
+    wide = cmg.setup_cascade(hg, "additive", nu=3, alpha=10000)
+    for l in range(hg.nlevels - 1):
+        assert np.array_equal(cmg.export_lambda(full, l), cmg.export_lambda(wide, l))
+    hb = gu.gpu_hierarchy(A, block=2)
+    with pytest.raises(cmg.CascadeError) as e:
+        cmg.setup_cascade(hb, "additive", nu=2, alpha=3)
+    assert e.value.status == -7
+
+
 @pytest.mark.parametrize("dim,n", [(2, 32), (3, 20)])
 def test_periodic_table1_on_gpu(built, dim, n):
     """The GPU setup reproduces Table 1 on periodic grids and the oracle's
@@ -273,8 +313,8 @@ def test_errors_are_reported(built):
     hg = gu.gpu_hierarchy(A)
     with pytest.raises(cmg.CascadeError, match="CS_ERR_ARG"):
         cmg.setup_cascade(hg, "additive", nu=0)
-    with pytest.raises(cmg.CascadeError, match="CS_ERR_UNSUPPORTED"):
-        cmg.setup_cascade(hg, "additive", nu=2, alpha=5)
+    with pytest.raises(cmg.CascadeError, match="CS_ERR_ARG"):
+        cmg.setup_cascade(hg, "additive", nu=2, alpha=-1)
     cg = cmg.setup_cascade(hg, "additive", nu=2)
     with pytest.raises(cmg.CascadeError, match="CS_ERR_ARG"):
         cmg.vcycle(hg, cg, _dev(np.zeros(A.N)), _dev(np.zeros(A.N)), precision="fp32")
