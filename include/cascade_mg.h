@@ -281,7 +281,8 @@ cs_status cs_setup_many(int nprob, const cs_stencil *A, const cs_hierarchy_opts 
 
 /* Batched solve: nprob independent 2D Dirichlet problems of any sizes, each
  * with its own red-black multiplicative cascade (point blocks, the same depth
- * nu for all; eq. fwdm) and 1..8 right-hand sides, iterated together by
+ * nu for all: additive or red-black multiplicative, eq. fwda / fwdm; point
+ * or 2x2-node blocks) and 1..32 right-hand sides, iterated together by
  * FP64 refinement x += V0(b - A x) or by GMRES preconditioned with V0
  * (Algorithm 1 V-cycles in opts.precision; FP64 residuals and Krylov
  * vectors) until every problem meets its tolerance.  The whole solve
@@ -311,8 +312,9 @@ typedef struct {
 /* Plan a batched solve over existing handles (not owned; they must outlive
  * the plan): validates them, allocates the multi-RHS level vectors and the
  * tile tables, and autotunes if asked.  Errors: CS_ERR_ARG (null, nrhs not in
- * 1..8, FP32 without lowp cascades, mixed nu), CS_ERR_UNSUPPORTED (3D,
- * periodic, additive cascades, blocks > 1 node, no coarsest factorisation). */
+ * 1..32, FP32 without lowp cascades, mixed nu, cascade kinds or block sizes),
+ * CS_ERR_UNSUPPORTED (3D, periodic, blocks other than 1 or 2x2 nodes, no
+ * coarsest factorisation). */
 cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *c, const int *nrhs,
                           const cs_batch_opts *opts, cs_stream stream, cs_batch **out);
 /* Solve all problems from the initial x[p] (device, [N_p][nrhs_p]) to

@@ -27,14 +27,16 @@ namespace cg = cooperative_groups;
 namespace csx {
 
 constexpr int BMAXLEV = 16;
-constexpr int BMAXRHS = 8;
+constexpr int BMAXRHS = 32;
 
 template <typename T>
 struct BLevel {
     int nx, ny, kind, inplace;
     int64_t N;
+    int bs, nbx, nmax;  // blocks of bs x bs nodes (1: point blocks), nbx per row, nmax = bs^2
+    int64_t nblocks;
     const T *A;    // [nst][N]
-    const T *lam;  // [nu][N]
+    const T *lam;  // [nu][N] (points) or [nu][nblocks][nmax][nmax] (blocks)
     T *b, *x, *t;  // [N][m]
 };
 
@@ -53,8 +55,13 @@ struct BTile {
 };
 
 enum { OP_SWEEP = 0, OP_RESTRICT = 1, OP_COARSE = 2, OP_PROLONG = 3 };
+// colour >= 0: a multiplicative colour step (in place on 5-point levels, else
+// x -> t for parity 0 and t -> x for parity 1); colour < 0: an additive step
+// from buffer src to dst (0: x, 1: t).  Restriction reads the fine level's
+// buffer src; prolongation reads src and writes dst.  transpose: Lambda^T
+// (the reversed smoother on block levels).
 struct BStep {
-    int op, slot, lv, colour, parity;
+    int op, slot, lv, colour, parity, src, dst, transpose;
 };
 
 struct BCtl {
@@ -70,6 +77,8 @@ struct BArgs {
     int nprob;
     const BTile *tiles;      // tiles of slot t: [slot_tile[t], slot_tile[t + 1])
     const int *slot_tile;
+    const BTile *btiles;     // block tiles (i0, ni in blocks) of slot t, for block-level sweeps
+    const int *slot_btile;
     int dmax;
     const BTile *ftiles;     // finest-level tiles; problem p: [ftile_of[p], ftile_of[p + 1])
     const int *ftile_of;
@@ -194,7 +203,7 @@ __device__ __forceinline__ void sweep_tile(int nx, int ny, int64_t N, const T *_
                 const int iy = i / nx, ix = i - iy * nx;
                 const int64_t e = (int64_t)i * m + r;
                 ee[u] = e;
-                if (bcolour(ix, iy) != colour) {
+                if (colour >= 0 && bcolour(ix, iy) != colour) {
                     if (copy) { val[u] = src[e]; wr[u] = true; }
                 } else {
                     const T ax = row_apply<KIND, T, T>(nx, ny, N, A, src, m, r, ix, iy, i);
@@ -207,6 +216,60 @@ __device__ __forceinline__ void sweep_tile(int nx, int ny, int64_t N, const T *_
 #pragma unroll
         for (int u = 0; u < SW; ++u)
             if (wr[u]) dst[ee[u]] = val[u];
+    }
+}
+
+// Block step over a range of blocks (one thread per block and right-hand
+// side): the residual rows of the block's present nodes, then
+// x_b -= Lambda_b^(T) r_b (eq. fwda / fwdm with block Lambda).  Blocks of the
+// other colour are copied when the step is not in place.
+template <typename T, int KIND, int BS>
+__device__ __forceinline__ void block_sweep_tile(int nx, int ny, int64_t N, int nbx, const T *__restrict__ A,
+                                                 const T *__restrict__ lam, const T *__restrict__ b, int m, int r,
+                                                 int b0, int nb, int n0, int step, int colour, int transpose,
+                                                 const T *src, T *dst) {
+    constexpr int NM = BS * BS;
+    const bool copy = src != dst;
+    for (int nn = n0; nn < nb; nn += step) {
+        const int blk = b0 + nn;
+        const int by = blk / nbx, bx = blk - by * nbx;
+        int node[NM];
+        bool pres[NM];
+#pragma unroll
+        for (int lp = 0; lp < NM; ++lp) {
+            const int ix = BS * bx + lp % BS, iy = BS * by + lp / BS;
+            pres[lp] = ix < nx && iy < ny;
+            node[lp] = ix + nx * iy;
+        }
+        if (colour >= 0 && (((bx + 1) + (by + 1)) & 1) != colour) {
+            if (copy)
+#pragma unroll
+                for (int lp = 0; lp < NM; ++lp)
+                    if (pres[lp]) dst[(int64_t)node[lp] * m + r] = src[(int64_t)node[lp] * m + r];
+            continue;
+        }
+        T res[NM], xv[NM];
+#pragma unroll 1
+        for (int lp = 0; lp < NM; ++lp) {
+            res[lp] = T(0);
+            xv[lp] = T(0);
+            if (pres[lp]) {
+                const int i = node[lp], iy = i / nx, ix = i - iy * nx;
+                const int64_t e = (int64_t)i * m + r;
+                res[lp] = row_apply<KIND, T, T>(nx, ny, N, A, src, m, r, ix, iy, i) - b[e];
+                xv[lp] = src[e];
+            }
+        }
+        const T *lb = lam + (int64_t)blk * (NM * NM);
+#pragma unroll 1
+        for (int lp = 0; lp < NM; ++lp) {
+            if (!pres[lp]) continue;
+            T acc = xv[lp];
+#pragma unroll
+            for (int q = 0; q < NM; ++q)
+                acc = fma(-(transpose ? lb[q * NM + lp] : lb[lp * NM + q]), res[q], acc);
+            dst[(int64_t)node[lp] * m + r] = acc;
+        }
     }
 }
 
@@ -256,7 +319,7 @@ __device__ __forceinline__ int bp1d(int f, int nc, int *c, float *w) {
 }
 
 template <typename T>
-__device__ __forceinline__ void prolong_tile(int fnx, T *__restrict__ xf, int cnx, int cny,
+__device__ __forceinline__ void prolong_tile(int fnx, const T *xs, T *xf, int cnx, int cny,
                                              const T *__restrict__ xc, int m, int r, int i0, int ni, int n0,
                                              int step) {
     for (int nn = n0; nn < ni; nn += step) {
@@ -273,16 +336,19 @@ __device__ __forceinline__ void prolong_tile(int fnx, T *__restrict__ xf, int cn
                 acc = fma(w, xc[(int64_t)c * m + r], acc);
             }
         const int64_t e = (int64_t)f * m + r;
-        xf[e] = xf[e] - acc;
+        xf[e] = xs[e] - acc;
     }
 }
 
 template <typename T>
 __device__ void stage_step(const BArgs &a, const BProb<T> *P, const BStep st) {
     const int tslot = st.op == OP_RESTRICT ? st.slot + 1 : st.slot;
-    const int t0 = a.slot_tile[tslot], t1 = a.slot_tile[tslot + 1];
+    const bool blocks = st.op == OP_SWEEP && a.btiles != nullptr;
+    const BTile *tiles = blocks ? a.btiles : a.tiles;
+    const int *slot_tile = blocks ? a.slot_btile : a.slot_tile;
+    const int t0 = slot_tile[tslot], t1 = slot_tile[tslot + 1];
     for (int k = t0 + blockIdx.x; k < t1; k += gridDim.x) {
-        const BTile tile = a.tiles[k];
+        const BTile tile = tiles[k];
         if (__ldcg(a.work + tile.p) == 0) continue;
         if (st.op == OP_RESTRICT && tile.l == 0) continue;  // this problem's finest level starts at the coarse slot
         const BProb<T> &pr = P[tile.p];
@@ -292,8 +358,25 @@ __device__ void stage_step(const BArgs &a, const BProb<T> *P, const BStep st) {
         const int r = tm.r;
         if (st.op == OP_SWEEP) {
             const BLevel<T> L = pr.lev[tile.l];
-            const T *src = L.inplace || st.parity == 0 ? L.x : L.t;
-            T *dst = L.inplace || st.parity == 1 ? L.x : L.t;
+            const T *src;
+            T *dst;
+            if (st.colour >= 0) {
+                src = L.inplace || st.parity == 0 ? L.x : L.t;
+                dst = L.inplace || st.parity == 1 ? L.x : L.t;
+            } else {
+                src = st.src ? L.t : L.x;
+                dst = st.dst ? L.t : L.x;
+            }
+            if (blocks) {
+                const T *lamb = L.lam + (int64_t)st.lv * L.nblocks * L.nmax * L.nmax;
+                if (L.kind == STAR)  // 2x2-node blocks (the batch plan admits no others)
+                    block_sweep_tile<T, STAR, 2>(L.nx, L.ny, L.N, L.nbx, L.A, lamb, L.b, m, r, tile.i0, tile.ni,
+                                                 tm.n0, tm.step, st.colour, st.transpose, src, dst);
+                else
+                    block_sweep_tile<T, BOX, 2>(L.nx, L.ny, L.N, L.nbx, L.A, lamb, L.b, m, r, tile.i0, tile.ni, tm.n0,
+                                                tm.step, st.colour, st.transpose, src, dst);
+                continue;
+            }
             const T *lam = L.lam + (int64_t)st.lv * L.N;
             if (L.kind == STAR)
                 sweep_tile<T, STAR>(L.nx, L.ny, L.N, L.A, lam, L.b, m, r, tile.i0, tile.ni, tm.n0, tm.step, st.colour,
@@ -303,11 +386,12 @@ __device__ void stage_step(const BArgs &a, const BProb<T> *P, const BStep st) {
                                    src, dst);
         } else if (st.op == OP_RESTRICT) {
             const BLevel<T> F = pr.lev[tile.l - 1], C = pr.lev[tile.l];
+            const T *fx = st.src ? F.t : F.x;
             if (F.kind == STAR)
-                restrict_tile<T, STAR>(F.nx, F.ny, F.N, F.A, F.x, F.b, C.nx, C.b, C.x, m, r, tile.i0, tile.ni, tm.n0,
+                restrict_tile<T, STAR>(F.nx, F.ny, F.N, F.A, fx, F.b, C.nx, C.b, C.x, m, r, tile.i0, tile.ni, tm.n0,
                                        tm.step);
             else
-                restrict_tile<T, BOX>(F.nx, F.ny, F.N, F.A, F.x, F.b, C.nx, C.b, C.x, m, r, tile.i0, tile.ni, tm.n0,
+                restrict_tile<T, BOX>(F.nx, F.ny, F.N, F.A, fx, F.b, C.nx, C.b, C.x, m, r, tile.i0, tile.ni, tm.n0,
                                       tm.step);
         } else if (st.op == OP_COARSE) {
             const BLevel<T> L = pr.lev[tile.l];
@@ -323,7 +407,8 @@ __device__ void stage_step(const BArgs &a, const BProb<T> *P, const BStep st) {
             }
         } else {  // OP_PROLONG
             const BLevel<T> F = pr.lev[tile.l], C = pr.lev[tile.l + 1];
-            prolong_tile<T>(F.nx, F.x, C.nx, C.ny, C.x, m, r, tile.i0, tile.ni, tm.n0, tm.step);
+            prolong_tile<T>(F.nx, st.src ? F.t : F.x, st.dst ? F.t : F.x, C.nx, C.ny, C.x, m, r, tile.i0, tile.ni,
+                            tm.n0, tm.step);
         }
     }
 }
@@ -707,6 +792,7 @@ using namespace csx;
 
 struct cs_batch {
     int nprob = 0, dmax = 0, precision = CS_FP32, order = CS_RF, mu_pre = 1, mu_post = 1, nu = 1;
+    int kind = CS_MULTIPLICATIVE, bs = 1;
     int dev = 0;
     std::vector<int> m, nlev, slot0;
     std::vector<int64_t> nfine;
@@ -715,7 +801,8 @@ struct cs_batch {
     size_t probs_bytes = 0;
     std::vector<unsigned char> hprobs;
     void *vec = nullptr;  // all multi-RHS level vectors
-    BTile *tiles = nullptr, *ftiles = nullptr;
+    BTile *tiles = nullptr, *ftiles = nullptr, *btiles = nullptr;
+    int *slot_btile = nullptr;
     int *slot_tile = nullptr, *ftile_of = nullptr;
     int ntiles = 0, nftiles = 0;
     BStep *steps = nullptr;
@@ -779,8 +866,33 @@ cs_status build_tiles(cs_batch *B, int tile_nodes, cudaStream_t s) {
             ft.push_back({p, 0, (int)i0, (int)std::min<int64_t>(tile_nodes, n - i0)});
     }
     fo[B->nprob] = (int)ft.size();
+    // block tiles (block-level sweeps): about tile_nodes nodes of whole blocks each
+    std::vector<BTile> bt;
+    std::vector<int> sb(B->dmax + 1, 0);
+    if (B->bs > 1) {
+        const int tb = std::max(1, tile_nodes / (B->bs * B->bs));
+        for (int t = 0; t < B->dmax; ++t) {
+            sb[t] = (int)bt.size();
+            for (int p = 0; p < B->nprob; ++p) {
+                const int l = t - B->slot0[p];
+                if (l < 0) continue;
+                const int64_t nb = (int64_t)((B->nx[p][l] + B->bs - 1) / B->bs) * ((B->ny[p][l] + B->bs - 1) / B->bs);
+                for (int64_t b0 = 0; b0 < nb; b0 += tb)
+                    bt.push_back({p, l, (int)b0, (int)std::min<int64_t>(tb, nb - b0)});
+            }
+        }
+        sb[B->dmax] = (int)bt.size();
+    }
     dfree(B->tiles, s); dfree(B->ftiles, s); dfree(B->slot_tile, s); dfree(B->ftile_of, s); dfree(B->part, s);
+    dfree(B->btiles, s); dfree(B->slot_btile, s);
     B->tiles = nullptr; B->ftiles = nullptr; B->slot_tile = nullptr; B->ftile_of = nullptr; B->part = nullptr;
+    B->btiles = nullptr; B->slot_btile = nullptr;
+    if (B->bs > 1) {
+        CSX_TRY(dalloc_t(&B->btiles, bt.size(), nullptr, s));
+        CSX_TRY(dalloc_t(&B->slot_btile, sb.size(), nullptr, s));
+        CSX_CUDA(cudaMemcpyAsync(B->btiles, bt.data(), bt.size() * sizeof(BTile), cudaMemcpyHostToDevice, s));
+        CSX_CUDA(cudaMemcpyAsync(B->slot_btile, sb.data(), sb.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
     CSX_TRY(dalloc_t(&B->tiles, tl.size(), nullptr, s));
     CSX_TRY(dalloc_t(&B->ftiles, ft.size(), nullptr, s));
     CSX_TRY(dalloc_t(&B->slot_tile, st.size(), nullptr, s));
@@ -803,6 +915,8 @@ BArgs args_of(const cs_batch *B) {
     a.nprob = B->nprob;
     a.tiles = B->tiles;
     a.slot_tile = B->slot_tile;
+    a.btiles = B->btiles;
+    a.slot_btile = B->slot_btile;
     a.dmax = B->dmax;
     a.ftiles = B->ftiles;
     a.ftile_of = B->ftile_of;
@@ -921,20 +1035,41 @@ cs_status run(cs_batch *B, cudaStream_t s) {
 }
 
 void build_steps(const cs_batch *B, std::vector<BStep> &out) {
-    const bool rf = B->order == CS_RF;
+    // The buffer holding a level's iterate is the same for every problem at a
+    // slot: multiplicative steps come in colour pairs that end in x; additive
+    // steps flip between x and t, and the prolongation writes the buffer from
+    // which the post-smoothing steps end in x (the single-problem rule).
+    const bool rf = B->order == CS_RF, mult = B->kind == CS_MULTIPLICATIVE;
+    std::vector<int> pre_cur(B->dmax, 0);
     for (int t = 0; t + 1 < B->dmax; ++t) {
+        int cur = 0;
         for (int mu = 0; mu < B->mu_pre; ++mu)
-            for (int step = 0; step < B->nu; ++step)
-                for (int kk = 0; kk < 2; ++kk)
-                    out.push_back({OP_SWEEP, t, rf ? B->nu - 1 - step : step, rf ? 1 - kk : kk, kk});
-        out.push_back({OP_RESTRICT, t, 0, 0, 0});
+            for (int step = 0; step < B->nu; ++step) {
+                const int lv = rf ? B->nu - 1 - step : step;
+                if (mult) {
+                    for (int kk = 0; kk < 2; ++kk) out.push_back({OP_SWEEP, t, lv, rf ? 1 - kk : kk, kk, 0, 0, rf});
+                } else {
+                    out.push_back({OP_SWEEP, t, lv, -1, 0, cur, 1 - cur, rf});
+                    cur ^= 1;
+                }
+            }
+        out.push_back({OP_RESTRICT, t, 0, 0, 0, cur, 0, 0});
+        pre_cur[t] = cur;
     }
-    out.push_back({OP_COARSE, B->dmax - 1, 0, 0, 0});
+    out.push_back({OP_COARSE, B->dmax - 1, 0, 0, 0, 0, 0, 0});
+    const int post_flips = mult ? 0 : B->mu_post * B->nu;
     for (int t = B->dmax - 2; t >= 0; --t) {
-        out.push_back({OP_PROLONG, t, 0, 0, 0});
+        int cur = post_flips % 2 == 0 ? 0 : 1;
+        out.push_back({OP_PROLONG, t, 0, 0, 0, pre_cur[t], cur, 0});
         for (int mu = 0; mu < B->mu_post; ++mu)
-            for (int step = 0; step < B->nu; ++step)
-                for (int kk = 0; kk < 2; ++kk) out.push_back({OP_SWEEP, t, step, kk, kk});
+            for (int step = 0; step < B->nu; ++step) {
+                if (mult) {
+                    for (int kk = 0; kk < 2; ++kk) out.push_back({OP_SWEEP, t, step, kk, kk, 0, 0, 0});
+                } else {
+                    out.push_back({OP_SWEEP, t, step, -1, 0, cur, 1 - cur, 0});
+                    cur ^= 1;
+                }
+            }
     }
 }
 
@@ -966,8 +1101,13 @@ cs_status fill_probs(cs_batch *B, cs_hierarchy *const *h, cs_cascade *const *c, 
             d.nx = L.g.nx;
             d.ny = L.g.ny;
             d.kind = L.kind;
-            d.inplace = L.kind == STAR ? 1 : 0;  // red-black is a graph colouring of the 5-point stencil only
+            // red-black (of nodes or of blocks) is a graph colouring of the 5-point stencil only
+            d.inplace = B->kind == CS_MULTIPLICATIVE && L.kind == STAR ? 1 : 0;
             d.N = L.g.N;
+            d.bs = L.bs;
+            d.nbx = L.nbx;
+            d.nmax = L.nmax;
+            d.nblocks = L.nblocks;
             if (sizeof(T) == sizeof(float)) {
                 d.A = reinterpret_cast<const T *>(c[p]->lo[l].A);
                 d.lam = l < c[p]->nlev ? reinterpret_cast<const T *>(c[p]->lo[l].lam) : nullptr;
@@ -1007,10 +1147,11 @@ cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *
         if (!hp || !cp || cp->h != hp) { set_error("problem %d: missing or mismatched handles", p); return CS_ERR_ARG; }
         if (nrhs[p] < 1 || nrhs[p] > BMAXRHS) { set_error("problem %d: nrhs must be in 1..%d", p, BMAXRHS); return CS_ERR_ARG; }
         if (hp->dim != 2 || hp->periodic) { set_error("problem %d: the batched solver takes 2D Dirichlet grids", p); return CS_ERR_UNSUPPORTED; }
-        if (cp->kind != CS_MULTIPLICATIVE) { set_error("problem %d: the batched solver takes red-black multiplicative cascades", p); return CS_ERR_UNSUPPORTED; }
+        if (cp->kind != c[0]->kind) { set_error("all problems of a batch need the same cascade kind"); return CS_ERR_ARG; }
         if (hp->nlev < 2 || hp->nlev > BMAXLEV || !hp->cinv) { set_error("problem %d: need 2..%d levels and a coarsest factorisation", p, BMAXLEV); return CS_ERR_UNSUPPORTED; }
         for (int l = 0; l < hp->nlev; ++l)
-            if (hp->lev[l].bs != 1) { set_error("problem %d: the batched solver takes point blocks", p); return CS_ERR_UNSUPPORTED; }
+            if (hp->lev[l].bs != h[0]->lev[0].bs) { set_error("all problems of a batch need the same block size"); return CS_ERR_ARG; }
+        if (hp->lev[0].bs > 2) { set_error("problem %d: the batched solver takes point blocks or 2x2-node blocks", p); return CS_ERR_UNSUPPORTED; }
         if (o->precision == CS_FP32 && !cp->lowp) { set_error("problem %d: FP32 cycles need a cascade built with lowp", p); return CS_ERR_ARG; }
         if (nu < 0) nu = cp->nu;
         if (cp->nu != nu) { set_error("all problems of a batch need the same cascade depth"); return CS_ERR_ARG; }
@@ -1024,6 +1165,8 @@ cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *
     B->mu_pre = o->mu_pre;
     B->mu_post = o->mu_post;
     B->nu = nu;
+    B->kind = c[0]->kind;
+    B->bs = h[0]->lev[0].bs;
     B->method = o->method == CS_GMRES ? CS_GMRES : CS_REFINE;
     B->restart = o->restart > 0 ? o->restart : 30;
     cudaGetDevice(&B->dev);
@@ -1249,6 +1392,7 @@ void cs_batch_destroy(cs_batch *B) {
     if (!B) return;
     if (B->graph) cudaGraphExecDestroy(B->graph);
     dfree(B->vec); dfree(B->probs); dfree(B->tiles); dfree(B->ftiles); dfree(B->slot_tile); dfree(B->ftile_of);
+    dfree(B->btiles); dfree(B->slot_btile);
     dfree(B->steps); dfree(B->part); dfree(B->nb); dfree(B->rel); dfree(B->rel0); dfree(B->state); dfree(B->iters);
     dfree(B->ctl); dfree(B->bptr); dfree(B->xptr); dfree(B->tune_b); dfree(B->tune_x); dfree(B->work);
     dfree(B->gm); dfree(B->gsm);
