@@ -445,7 +445,7 @@ def main():
         c = cmg.setup_cascade(h, a.kind, nu=a.nu, lowp=lowp)
         x = torch.zeros(A.N, dtype=torch.float64, device=dev)
         info = cmg.solve(h, c, bd, x, method=method, precision=precision, tol=1e-10, mu_pre=mu, mu_post=mu,
-                         order=a.order)
+                         order=a.order, raise_on_error=precision != "bf16")
         if out is not None:
             out.append(info)
         return h, c, x
@@ -610,6 +610,12 @@ def main():
         result["plain_fp64"] = {"ms_per_step": ms64, "iterations": pinfo[-1].iterations,
                                 "final_rel_residual": pinfo[-1].final_rel_residual,
                                 "speedup_chosen_vs_plain": ms64 / ms}
+        # ---- BF16 storage (FP32 arithmetic) cycles inside FP64 refinement
+        binfo = []
+        ms16 = timed(lambda: step("bf16", "refine", 2, binfo), max(2, a.steps // 2), 1)
+        result["bf16_cycles"] = {"ms_per_step": ms16, "iterations": binfo[-1].iterations,
+                                 "final_rel_residual": binfo[-1].final_rel_residual,
+                                 "converged": bool(binfo[-1].converged)}
         # ---- end to end through the C ABI with host buffers (pinned)
         pin_coeff = torch.tensor(A.coeff, dtype=torch.float64).pin_memory()
         pin_b = torch.tensor(b, dtype=torch.float64).pin_memory()

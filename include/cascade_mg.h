@@ -97,7 +97,7 @@ cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts
 
 /* -------------------------------------------------------------- cascade */
 enum { CS_ADDITIVE = 0, CS_MULTIPLICATIVE = 1 };
-enum { CS_FP64 = 0, CS_FP32 = 1 };
+enum { CS_FP64 = 0, CS_FP32 = 1, CS_BF16 = 2 };
 
 typedef struct {
     int kind;      /* CS_ADDITIVE (Sec. 2.1) or CS_MULTIPLICATIVE (Sec. 2.2, red-black) */
@@ -107,7 +107,9 @@ typedef struct {
                       of largest magnitude (ties: smaller column index); 0 = none; point blocks
                       only (CS_ERR_UNSUPPORTED for block levels or with a model) */
     int lowp;      /* 1: also keep FP32 copies of the level operators and Lambda for
-                      CS_FP32 cycles (iterative refinement) */
+                      CS_FP32 cycles (iterative refinement); 2: FP32 and BF16 copies, the
+                      latter for CS_BF16 cycles (BF16 storage, FP32 arithmetic; point-block
+                      hierarchies only, else CS_ERR_UNSUPPORTED) */
     int no_reuse;  /* 0 (default): on structured levels with a region of identical
                       coefficient rows, rows whose whole setup dependency lies in that
                       region are computed once per colour and copied -- the stencil
@@ -144,7 +146,8 @@ typedef struct {
     int mu_post;   /* ... and after */
     int order;     /* CS_RF: reverse pre-smoother, forward post (symmetric V, SM Sec. 3);
                       CS_FF: forward both (Sec. 2.4) */
-    int precision; /* CS_FP64, or CS_FP32 (needs lowp; coarsest solve stays FP64) */
+    int precision; /* CS_FP64, CS_FP32 (needs lowp >= 1) or CS_BF16 (BF16 storage, FP32 arithmetic;
+                      needs lowp = 2); the coarsest solve stays FP64 */
 } cs_vcycle_opts;
 
 /* One V-cycle (Algorithm 1) on the finest level: x <- V(x, b), i.e.

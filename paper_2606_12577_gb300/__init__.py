@@ -152,9 +152,10 @@ def setup_hierarchy(dim, n, offsets, coeff, periodic=False, coarse_max=4, max_le
 
 def setup_cascade(h: Hierarchy, kind="additive", nu=3, prescale=True, alpha=0, lowp=False, reuse=True, model=None,
                   model_tol=0.05, stream=None):
-    """Build the cascade; ``model`` (an ``MLP``) predicts the finest level's
-    Lambda blocks, accepted when its level-1 Frobenius objective is within
-    ``model_tol`` of the exact one (else the exact setup runs)."""
+    """Build the cascade; ``lowp``: False, True (FP32 copies for FP32
+    cycles) or 2 (FP32 and BF16 copies); ``model`` (an ``MLP``) predicts the
+    finest level's Lambda blocks, kept per block when its level-1 Frobenius
+    objective is within ``model_tol`` of the exact one."""
     k = _capi.CS_MULTIPLICATIVE if kind == "multiplicative" else _capi.CS_ADDITIVE
     opts = _capi.cs_cascade_opts(k, nu, int(prescale), alpha, int(lowp), int(not reuse),
                                  C.c_void_p(model.ptr if model is not None else None), float(model_tol))
@@ -279,8 +280,8 @@ def block_targets(c, level=0, stream=None):
 
 
 def _cycle_opts(mu_pre, mu_post, order, precision):
-    return _capi.cs_vcycle_opts(mu_pre, mu_post, _capi.CS_RF if order.upper() == "RF" else _capi.CS_FF,
-                                _capi.CS_FP32 if precision == "fp32" else _capi.CS_FP64)
+    prec = {"fp64": _capi.CS_FP64, "fp32": _capi.CS_FP32, "bf16": _capi.CS_BF16}[precision]
+    return _capi.cs_vcycle_opts(mu_pre, mu_post, _capi.CS_RF if order.upper() == "RF" else _capi.CS_FF, prec)
 
 
 def vcycle(h, c, b, x, mu_pre=1, mu_post=1, order="RF", precision="fp64", stream=None):
@@ -299,7 +300,8 @@ def smooth(h, c, level, b, x, reverse=False, stream=None):
 
 def sweep(h, c, level, step, b, x, out, colour=-1, stream=None):
     """One cascade step (one kernel): out = x - Lambda_{step+1[,colour]} (A x - b).
-    float64 tensors run the FP64 kernel, float32 tensors the FP32 one (lowp)."""
+    float64 tensors run the FP64 kernel, float32 tensors the FP32 one (lowp),
+    bfloat16 tensors the BF16-storage one (lowp=2)."""
     torch = _torch()
     N = h.N(level)
     ts = (b, x, out)
@@ -310,8 +312,10 @@ def sweep(h, c, level, step, b, x, out, colour=-1, stream=None):
         prec = _capi.CS_FP32
     elif all(t.dtype == torch.float64 for t in ts):
         prec = _capi.CS_FP64
+    elif all(t.dtype == torch.bfloat16 for t in ts):
+        prec = _capi.CS_BF16
     else:
-        raise TypeError("b, x, out must all be float64 or all float32")
+        raise TypeError("b, x, out must all be float64, all float32 or all bfloat16")
     _capi.check(_capi.lib().cs_sweep(h.ptr, c.ptr, level, step, colour, prec, C.c_void_p(b.data_ptr()),
                                      C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), _stream(stream)),
                 "cs_sweep")

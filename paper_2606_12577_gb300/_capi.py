@@ -18,7 +18,7 @@ CS_ERR_DIVERGED, CS_ERR_TIMEOUT, CS_ERR_UNSUPPORTED, CS_ERR_NOTCONV = -5, -6, -7
 STATUS_NAMES = {0: "CS_OK", -1: "CS_ERR_ARG", -2: "CS_ERR_CUDA", -3: "CS_ERR_NOMEM", -4: "CS_ERR_SINGULAR",
                 -5: "CS_ERR_DIVERGED", -6: "CS_ERR_TIMEOUT", -7: "CS_ERR_UNSUPPORTED", -8: "CS_ERR_NOTCONV"}
 CS_ADDITIVE, CS_MULTIPLICATIVE = 0, 1
-CS_FP64, CS_FP32 = 0, 1
+CS_FP64, CS_FP32, CS_BF16 = 0, 1, 2
 CS_FF, CS_RF = 0, 1
 CS_STATIONARY, CS_GMRES, CS_REFINE = 0, 1, 2
 

@@ -131,6 +131,11 @@ View<float> view<float>(const cs_hierarchy *, const cs_cascade *c, int l) {
     const LowLevel &L = c->lo[l];
     return {L.A, L.lam, L.b, L.x, L.t};
 }
+template <>
+View<__nv_bfloat16> view<__nv_bfloat16>(const cs_hierarchy *, const cs_cascade *c, int l) {
+    const LowLevel16 &L = c->lo16[l];
+    return {L.A, L.lam, L.b, L.x, L.t};
+}
 
 // doubles of Lambda per cascade step on a level
 static int64_t lam_step(const Level &L) { return L.bs > 1 ? L.nblocks * L.nmax * L.nmax : L.g.N; }
@@ -188,6 +193,11 @@ template <>
 cs_status coarse_solve_t<float>(const cs_hierarchy *h, const float *b, float *x, cudaStream_t s) {
     return launch_coarse_solve32(h, b, x, s);
 }
+template <>
+cs_status coarse_solve_t<__nv_bfloat16>(const cs_hierarchy *h, const __nv_bfloat16 *b, __nv_bfloat16 *x,
+                                        cudaStream_t s) {
+    return launch_coarse_solve16(h, b, x, s);
+}
 
 // zero-initial-guess cycle on level l: reads v.b, leaves the result in v.x
 template <typename T>
@@ -236,8 +246,9 @@ static cs_status run_v0(const cs_hierarchy *h, cs_cascade *c, const cs_vcycle_op
     CSX_CUDA(cudaStreamSynchronize(s));
     CSX_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     const int64_t before = g_launches.load();
-    cs_status rc = o.precision == CS_FP32 ? v0_enqueue<float>(h, c, 0, o.order, o.mu_pre, o.mu_post, cs)
-                                          : v0_enqueue<double>(h, c, 0, o.order, o.mu_pre, o.mu_post, cs);
+    cs_status rc = o.precision == CS_FP32   ? v0_enqueue<float>(h, c, 0, o.order, o.mu_pre, o.mu_post, cs)
+                   : o.precision == CS_BF16 ? v0_enqueue<__nv_bfloat16>(h, c, 0, o.order, o.mu_pre, o.mu_post, cs)
+                                            : v0_enqueue<double>(h, c, 0, o.order, o.mu_pre, o.mu_post, cs);
     const int64_t kernels = g_launches.load() - before;  // recorded, not executed
     g_launches.fetch_sub(kernels);
     cudaGraph_t graph = nullptr;
@@ -259,12 +270,17 @@ static cs_status run_v0(const cs_hierarchy *h, cs_cascade *c, const cs_vcycle_op
 
 static cs_status check_cycle_opts(const cs_hierarchy *h, const cs_cascade *c, const cs_vcycle_opts *o) {
     if (!o || o->mu_pre < 0 || o->mu_post < 0 || o->mu_pre > 16 || o->mu_post > 16 ||
-        (o->order != CS_RF && o->order != CS_FF) || (o->precision != CS_FP64 && o->precision != CS_FP32)) {
+        (o->order != CS_RF && o->order != CS_FF) ||
+        (o->precision != CS_FP64 && o->precision != CS_FP32 && o->precision != CS_BF16)) {
         set_error("invalid V-cycle options");
         return CS_ERR_ARG;
     }
     if (o->precision == CS_FP32 && !c->lowp) {
         set_error("FP32 cycles need a cascade built with lowp = 1");
+        return CS_ERR_ARG;
+    }
+    if (o->precision == CS_BF16 && c->lo16.empty()) {
+        set_error("BF16 cycles need a cascade built with lowp = 2");
         return CS_ERR_ARG;
     }
     if (h->cn == 0) {
@@ -439,6 +455,14 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
     c->ncol = o->kind == CS_MULTIPLICATIVE ? 2 : 1;
     c->nlev = h->nlev > 1 ? h->nlev - 1 : 1;
     c->lowp = o->lowp != 0;
+    if (o->lowp < 0 || o->lowp > 2) { set_error("lowp must be 0, 1 or 2"); delete c; return CS_ERR_ARG; }
+    if (o->lowp == 2)
+        for (int l = 0; l < h->nlev; ++l)
+            if (h->lev[l].bs > 1) {
+                set_error("BF16 copies (lowp = 2) are implemented for point-block hierarchies only");
+                delete c;
+                return CS_ERR_UNSUPPORTED;
+            }
     cs_status rc = CS_OK;
     c->lam.assign(c->nlev, nullptr);
     for (int l = 0; l < c->nlev; ++l)
@@ -541,6 +565,23 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
             if ((rc = dalloc_t(&lo.t, N, &c->bytes, s)) != CS_OK) goto fail;
         }
     }
+    if (o->lowp == 2) {  // BF16 storage of operators, Lambda and vectors (FP32 arithmetic)
+        c->lo16.resize(h->nlev);
+        for (int l = 0; l < h->nlev; ++l) {
+            const Level &L = h->lev[l];
+            LowLevel16 &lo = c->lo16[l];
+            const int64_t N = L.g.N;
+            if ((rc = dalloc_t(&lo.A, (size_t)L.nst * N, &c->bytes, s)) != CS_OK) goto fail;
+            if ((rc = launch_copy_d2bf((int64_t)L.nst * N, L.A, lo.A, s)) != CS_OK) goto fail;
+            if (l < c->nlev) {
+                if ((rc = dalloc_t(&lo.lam, (size_t)c->nu * lam_step(L), &c->bytes, s)) != CS_OK) goto fail;
+                if ((rc = launch_copy_d2bf((int64_t)c->nu * lam_step(L), c->lam[l], lo.lam, s)) != CS_OK) goto fail;
+            }
+            if ((rc = dalloc_t(&lo.b, N, &c->bytes, s)) != CS_OK) goto fail;
+            if ((rc = dalloc_t(&lo.x, N, &c->bytes, s)) != CS_OK) goto fail;
+            if ((rc = dalloc_t(&lo.t, N, &c->bytes, s)) != CS_OK) goto fail;
+        }
+    }
     {
         cudaError_t e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -619,6 +660,7 @@ void cs_destroy_cascade(cs_cascade *c) {
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
     for (double *p : c->lam) dfree(p);
     for (auto &lo : c->lo) { dfree(lo.A); dfree(lo.lam); dfree(lo.b); dfree(lo.x); dfree(lo.t); }
+    for (auto &lo : c->lo16) { dfree(lo.A); dfree(lo.lam); dfree(lo.b); dfree(lo.x); dfree(lo.t); }
     dfree(c->fine_b32); dfree(c->fine_x32); dfree(c->gm_V); dfree(c->gm_h);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     delete c;
@@ -634,6 +676,10 @@ cs_status cs_vcycle(const cs_hierarchy *h, cs_cascade *c, const cs_vcycle_opts *
         CSX_TRY(launch_residual64(L, L.A, b, x, nullptr, c->lo[0].b, nullptr, 0, s));
         CSX_TRY(run_v0(h, c, *o, s));
         CSX_TRY(launch_axpy_f32(L.g.N, c->lo[0].x, x, s));
+    } else if (o->precision == CS_BF16) {
+        CSX_TRY(launch_residual64_bf16(L, L.A, b, x, c->lo16[0].b, s));
+        CSX_TRY(run_v0(h, c, *o, s));
+        CSX_TRY(launch_axpy_bf16(L.g.N, c->lo16[0].x, x, s));
     } else {
         CSX_TRY(launch_residual64(L, L.A, b, x, L.b, nullptr, nullptr, 0, s));
         CSX_TRY(run_v0(h, c, *o, s));
@@ -679,6 +725,12 @@ cs_status cs_sweep(const cs_hierarchy *h, cs_cascade *c, int level, int step, in
                                              colour, false, false, s);
         return launch_sweep<float>(L, lo.A, lo.lam + st, (const float *)b, (const float *)x, (float *)out, colour,
                                    false, s);
+    }
+    if (precision == CS_BF16) {
+        if (c->lo16.empty()) { set_error("BF16 steps need lowp = 2"); return CS_ERR_ARG; }
+        const LowLevel16 &lo = c->lo16[level];
+        return launch_sweep<__nv_bfloat16>(L, lo.A, lo.lam + st, (const __nv_bfloat16 *)b, (const __nv_bfloat16 *)x,
+                                           (__nv_bfloat16 *)out, colour, false, s);
     }
     if (precision != CS_FP64) { set_error("bad precision"); return CS_ERR_ARG; }
     if (L.bs > 1)
@@ -822,11 +874,16 @@ cs_status cs_solve(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *o_
     } else if (o.method == CS_GMRES) {
         rc = gmres(h, c, &o, b, x, nb, &inf, s);
     } else {
-        const bool lowp = o.cycle.precision == CS_FP32;
+        const bool lowp = o.cycle.precision == CS_FP32, bf16 = o.cycle.precision == CS_BF16;
         const int nred = residual_blocks(L);
         float *r32 = lowp ? c->lo[0].b : nullptr;
-        double *r64 = lowp ? nullptr : L.b;
-        CSX_TRY(launch_residual64(L, L.A, b, x, r64, r32, h->red, nred, s));
+        double *r64 = lowp ? nullptr : L.b;  // FP64 cycles read it; BF16 cycles take a BF16 copy
+        auto residual = [&]() -> cs_status {
+            CSX_TRY(launch_residual64(L, L.A, b, x, r64, r32, h->red, nred, s));
+            if (bf16) CSX_TRY(launch_copy_d2bf(N, L.b, c->lo16[0].b, s));
+            return CS_OK;
+        };
+        CSX_TRY(residual());
         double rel = std::sqrt(host_sum(h, nred, s, &rc)) / nb;
         if (rc != CS_OK) return rc;
         const double rel0 = rel;
@@ -834,9 +891,10 @@ cs_status cs_solve(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *o_
         while (rel > o.tol && inf.iterations < o.maxit) {
             CSX_TRY(run_v0(h, c, o.cycle, s));
             if (lowp) CSX_TRY(launch_axpy_f32(N, c->lo[0].x, x, s));
+            else if (bf16) CSX_TRY(launch_axpy_bf16(N, c->lo16[0].x, x, s));
             else CSX_TRY(launch_add64(N, L.x, x, s));
             ++inf.iterations;
-            CSX_TRY(launch_residual64(L, L.A, b, x, r64, r32, h->red, nred, s));
+            CSX_TRY(residual());
             rel = std::sqrt(host_sum(h, nred, s, &rc)) / nb;
             if (rc != CS_OK) return rc;
             if (o.hist && inf.nhist < o.hist_cap) o.hist[inf.nhist++] = rel;
@@ -869,7 +927,7 @@ static cs_status gmres(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts
     const Level &L = h->lev[0];
     const int64_t N = L.g.N;
     const int m = o->restart;
-    const bool lowp = o->cycle.precision == CS_FP32;
+    const bool lowp = o->cycle.precision == CS_FP32, bf16 = o->cycle.precision == CS_BF16;
     if (c->gm_restart < m) {
         dfree(c->gm_V, s); dfree(c->gm_h, s);
         c->gm_V = nullptr; c->gm_h = nullptr;
@@ -887,6 +945,11 @@ static cs_status gmres(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts
             CSX_TRY(run_v0(h, c, o->cycle, s));
             CSX_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * N, s));
             CSX_TRY(launch_axpy_f32(N, c->lo[0].x, z, s));
+        } else if (bf16) {
+            CSX_TRY(launch_copy_d2bf(N, rhs_dev, c->lo16[0].b, s));
+            CSX_TRY(run_v0(h, c, o->cycle, s));
+            CSX_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * N, s));
+            CSX_TRY(launch_axpy_bf16(N, c->lo16[0].x, z, s));
         } else {
             if (rhs_dev != L.b) CSX_CUDA(cudaMemcpyAsync(L.b, rhs_dev, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
             CSX_TRY(run_v0(h, c, o->cycle, s));

@@ -10,6 +10,7 @@
 //   * vectors are contiguous N-arrays in natural (x fastest) order.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <atomic>
 #include <cstdint>
@@ -54,6 +55,12 @@ struct LowLevel {   // FP32 state of one level (owned by a cascade)
     float *b = nullptr, *x = nullptr, *t = nullptr;
 };
 
+struct LowLevel16 {  // BF16 storage of one level (FP32 arithmetic; owned by a cascade)
+    __nv_bfloat16 *A = nullptr;    // [nst][N]
+    __nv_bfloat16 *lam = nullptr;  // [nu][N]
+    __nv_bfloat16 *b = nullptr, *x = nullptr, *t = nullptr;
+};
+
 }  // namespace csx
 
 struct cs_hierarchy {
@@ -79,6 +86,7 @@ struct cs_cascade {
     bool lowp = false;
     std::vector<double *> lam;  // per level [nu][N]
     std::vector<csx::LowLevel> lo;
+    std::vector<csx::LowLevel16> lo16;  // BF16 copies (lowp = 2, point-block hierarchies)
     float *fine_b32 = nullptr, *fine_x32 = nullptr;
     // captured zero-initial-guess V-cycles, keyed by (precision, order, mu)
     struct Graph {
@@ -170,6 +178,11 @@ cs_status launch_coarse_solve(const cs_hierarchy *h, const double *b, double *x,
 cs_status launch_coarse_solve32(const cs_hierarchy *h, const float *b, float *x, cudaStream_t s);
 cs_status launch_axpy_f32(int64_t N, const float *d, double *x, cudaStream_t s);  // x += d
 cs_status launch_copy_d2f(int64_t N, const double *a, float *o, cudaStream_t s);
+cs_status launch_copy_d2bf(int64_t N, const double *a, __nv_bfloat16 *o, cudaStream_t s);
+cs_status launch_axpy_bf16(int64_t N, const __nv_bfloat16 *d, double *x, cudaStream_t s);  // x += d
+cs_status launch_residual64_bf16(const Level &L, const double *A, const double *b, const double *x,
+                                 __nv_bfloat16 *r16, cudaStream_t s);
+cs_status launch_coarse_solve16(const cs_hierarchy *h, const __nv_bfloat16 *b, __nv_bfloat16 *x, cudaStream_t s);
 // sum of red[0..nred) into red[nred] (one block, fixed order)
 cs_status launch_finish_sum(double *red, int nred, cudaStream_t s);
 cs_status launch_dot(int64_t N, const double *a, const double *b, double *red, int nred, cudaStream_t s);
@@ -196,6 +209,10 @@ cs_status learned_setup_level0(const cs_hierarchy *h, cs_cascade *c, cs_mlp *M, 
 template <typename T>
 cs_status launch_block_sweep(const Level &L, const T *A, const T *lam, const T *b, const T *x, T *out, int colour,
                              bool transpose, bool x_is_zero, cudaStream_t s);
+template <>
+cs_status launch_block_sweep<__nv_bfloat16>(const Level &, const __nv_bfloat16 *, const __nv_bfloat16 *,
+                                            const __nv_bfloat16 *, const __nv_bfloat16 *, __nv_bfloat16 *, int, bool,
+                                            bool, cudaStream_t);
 // the same with m right-hand sides, vectors RHS-contiguous (X[i*m + r], m <= 32)
 template <typename T>
 cs_status launch_block_sweep_m(const Level &L, const T *A, const T *lam, const T *b, const T *x, T *out, int m,

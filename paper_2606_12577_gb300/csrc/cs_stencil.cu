@@ -11,6 +11,8 @@
 #include <cstdint>
 #include <cstdio>
 
+#include <cuda_bf16.h>
+
 #include "cs_internal.cuh"
 
 namespace csx {
@@ -36,7 +38,20 @@ struct Sten {
     }
 };
 
+// Arithmetic type of a storage type: FP64 and FP32 compute in their own
+// type, BF16 storage computes in FP32 (FP32 accumulation).
 template <typename T> struct AccT { using type = T; };
+template <> struct AccT<__nv_bfloat16> { using type = float; };
+template <typename T>
+__device__ __forceinline__ typename AccT<T>::type ld(T v) { return v; }
+template <>
+__device__ __forceinline__ float ld<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T>
+__device__ __forceinline__ T st(typename AccT<T>::type v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 st<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <typename T>
+__device__ __forceinline__ T zero() { return st<T>(typename AccT<T>::type(0)); }
 
 __device__ __forceinline__ int node_colour(int dim, int ix, int iy, int iz) {
     return ((ix + 1) + (iy + 1) + (dim == 3 ? iz + 1 : 0)) & 1;
@@ -44,18 +59,19 @@ __device__ __forceinline__ int node_colour(int dim, int ix, int iy, int iz) {
 
 // (A x)_i at node (ix,iy,iz); neighbours outside the grid contribute nothing
 template <int DIM, int KIND, typename T>
-__device__ __forceinline__ T apply_row(const Grid &g, const T *__restrict__ A, const T *x, int ix, int iy, int iz,
-                                       int64_t i) {
+__device__ __forceinline__ typename AccT<T>::type apply_row(const Grid &g, const T *__restrict__ A, const T *x, int ix,
+                                                            int iy, int iz, int64_t i) {
     using S = Sten<DIM, KIND>;
-    T ax = T(0);
+    using C = typename AccT<T>::type;
+    C ax = C(0);
 #pragma unroll
     for (int s = 0; s < S::NST; ++s) {
         int dx, dy, dz;
         S::off(s, dx, dy, dz);
         bool in = (unsigned)(ix + dx) < (unsigned)g.nx && (unsigned)(iy + dy) < (unsigned)g.ny &&
                   (DIM == 2 || (unsigned)(iz + dz) < (unsigned)g.nz);
-        T a = A[(int64_t)s * g.N + i];
-        T xv = in ? x[i + dx + (int64_t)g.nx * (dy + (int64_t)g.ny * dz)] : T(0);
+        C a = ld<T>(A[(int64_t)s * g.N + i]);
+        C xv = in ? ld<T>(x[i + dx + (int64_t)g.nx * (dy + (int64_t)g.ny * dz)]) : C(0);
         ax = fma(a, xv, ax);
     }
     return ax;
@@ -76,21 +92,22 @@ __global__ void __launch_bounds__(TBX *TBY) k_sweep(Grid g, const T *__restrict_
     int64_t i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
     if (COLOURED) {
         if (node_colour(DIM, ix, iy, iz) != colour) {
-            if (xzero) out[i] = T(0);
+            if (xzero) out[i] = zero<T>();
             else if (out != x) out[i] = x[i];
             return;
         }
     }
-    T r;
-    T xi;
+    using C = typename AccT<T>::type;
+    C r;
+    C xi;
     if (xzero) {
-        r = -b[i];
-        xi = T(0);
+        r = -ld<T>(b[i]);
+        xi = C(0);
     } else {
-        r = apply_row<DIM, KIND, T>(g, A, x, ix, iy, iz, i) - b[i];
-        xi = x[i];
+        r = apply_row<DIM, KIND, T>(g, A, x, ix, iy, iz, i) - ld<T>(b[i]);
+        xi = ld<T>(x[i]);
     }
-    out[i] = xi - lam[i] * r;
+    out[i] = st<T>(xi - ld<T>(lam[i]) * r);
 }
 
 template <typename T, bool COLOURED>
@@ -120,6 +137,9 @@ template cs_status launch_sweep<double>(const Level &, const double *, const dou
                                         const double *, double *, int, bool, cudaStream_t);
 template cs_status launch_sweep<float>(const Level &, const float *, const float *, const float *, const float *,
                                        float *, int, bool, cudaStream_t);
+template cs_status launch_sweep<__nv_bfloat16>(const Level &, const __nv_bfloat16 *, const __nv_bfloat16 *,
+                                               const __nv_bfloat16 *, const __nv_bfloat16 *, __nv_bfloat16 *, int, bool,
+                                               cudaStream_t);
 
 // ------------------------------------------------------------ block steps
 // Nodes of block (bx,by,bz): bs*b + l per axis, local position
@@ -201,6 +221,14 @@ template cs_status launch_block_sweep<double>(const Level &, const double *, con
                                               const double *, double *, int, bool, bool, cudaStream_t);
 template cs_status launch_block_sweep<float>(const Level &, const float *, const float *, const float *, const float *,
                                              float *, int, bool, bool, cudaStream_t);
+// BF16 storage is implemented for point-block levels only
+template <>
+cs_status launch_block_sweep<__nv_bfloat16>(const Level &, const __nv_bfloat16 *, const __nv_bfloat16 *,
+                                            const __nv_bfloat16 *, const __nv_bfloat16 *, __nv_bfloat16 *, int, bool,
+                                            bool, cudaStream_t) {
+    set_error("BF16 cycles are implemented for point-block levels only");
+    return CS_ERR_UNSUPPORTED;
+}
 
 // The multi-RHS block step X_b <- X_b - Lambda_b^(T) (A X - B)_b.  One warp
 // per node of a block (lane r = right-hand side r, so every load of X and B
@@ -423,7 +451,8 @@ __global__ void __launch_bounds__(TBX *TBY) k_res_restrict(Grid gf, Grid gc, con
     int cy = blockIdx.y * TBY + threadIdx.y;
     int cz = blockIdx.z;
     if (cx >= gc.nx || cy >= gc.ny) return;
-    T acc = T(0);
+    using C = typename AccT<T>::type;
+    C acc = C(0);
     const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
     for (int dz = zlo; dz <= zhi; ++dz) {
         int fz = DIM == 3 ? 2 * cz + 1 + dz : 0;
@@ -435,14 +464,14 @@ __global__ void __launch_bounds__(TBX *TBY) k_res_restrict(Grid gf, Grid gc, con
             for (int dx = -1; dx <= 1; ++dx) {
                 int fx = 2 * cx + 1 + dx;
                 if (fx >= gf.nx) continue;
-                T w = T((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+                C w = C((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
                 int64_t f = fx + (int64_t)gf.nx * (fy + (int64_t)gf.ny * fz);
-                T r = apply_row<DIM, KIND, T>(gf, A, x, fx, fy, fz, f) - b[f];
+                C r = apply_row<DIM, KIND, T>(gf, A, x, fx, fy, fz, f) - ld<T>(b[f]);
                 acc = fma(w, r, acc);
             }
         }
     }
-    rc[cx + (int64_t)gc.nx * (cy + (int64_t)gc.ny * cz)] = acc * T(DIM == 3 ? 0.125 : 0.25);
+    rc[cx + (int64_t)gc.nx * (cy + (int64_t)gc.ny * cz)] = st<T>(acc * C(DIM == 3 ? 0.125 : 0.25));
 }
 
 template <typename T>
@@ -464,6 +493,9 @@ template cs_status launch_residual_restrict<double>(const Level &, const Level &
                                                     const double *, double *, cudaStream_t);
 template cs_status launch_residual_restrict<float>(const Level &, const Level &, const float *, const float *,
                                                    const float *, float *, cudaStream_t);
+template cs_status launch_residual_restrict<__nv_bfloat16>(const Level &, const Level &, const __nv_bfloat16 *,
+                                                           const __nv_bfloat16 *, const __nv_bfloat16 *,
+                                                           __nv_bfloat16 *, cudaStream_t);
 
 // 1D interpolation weights of fine node f (0-based) from coarse nodes: an
 // odd f coincides with coarse (f-1)/2; an even f takes half of coarse f/2-1
@@ -494,14 +526,15 @@ __global__ void __launch_bounds__(TBX *TBY) k_prolong(Grid gf, Grid gc, const T 
     int kz = 1;
     czs[0] = 0; wz[0] = 1.f;
     if (DIM == 3) kz = p1d(fz, gc.nz, czs, wz);
-    T acc = T(0);
+    using C = typename AccT<T>::type;
+    C acc = C(0);
     for (int c = 0; c < kz; ++c)
         for (int bb = 0; bb < ky; ++bb)
             for (int a = 0; a < kx; ++a)
-                acc = fma(T(wx[a] * wy[bb] * wz[c]), xc[cxs[a] + (int64_t)gc.nx * (cys[bb] + (int64_t)gc.ny * czs[c])],
-                          acc);
+                acc = fma(C(wx[a] * wy[bb] * wz[c]),
+                          ld<T>(xc[cxs[a] + (int64_t)gc.nx * (cys[bb] + (int64_t)gc.ny * czs[c])]), acc);
     int64_t f = fx + (int64_t)gf.nx * (fy + (int64_t)gf.ny * fz);
-    xo[f] = x[f] - acc;
+    xo[f] = st<T>(ld<T>(x[f]) - acc);
 }
 
 template <typename T>
@@ -517,6 +550,8 @@ template cs_status launch_prolong_correct<double>(const Level &, const Level &, 
                                                   double *, cudaStream_t);
 template cs_status launch_prolong_correct<float>(const Level &, const Level &, const float *, const float *,
                                                  float *, cudaStream_t);
+template cs_status launch_prolong_correct<__nv_bfloat16>(const Level &, const Level &, const __nv_bfloat16 *,
+                                                         const __nv_bfloat16 *, __nv_bfloat16 *, cudaStream_t);
 
 // block-wide deterministic sum (fixed tree order)
 __device__ __forceinline__ double block_sum(double v, double *sm) {
@@ -535,10 +570,10 @@ __device__ __forceinline__ double block_sum(double v, double *sm) {
 }
 
 // r = b - A x in FP64; per-block partial sums of r^2 into red[block id]
-template <int DIM, int KIND>
+template <int DIM, int KIND, typename TL = float>
 __global__ void __launch_bounds__(TBX *TBY) k_residual64(Grid g, const double *__restrict__ A,
                                                           const double *__restrict__ b, const double *__restrict__ x,
-                                                          double *__restrict__ r, float *__restrict__ r32,
+                                                          double *__restrict__ r, TL *__restrict__ r32,
                                                           double *__restrict__ red) {
     __shared__ double sm[32];
     int ix = blockIdx.x * TBX + threadIdx.x;
@@ -549,7 +584,7 @@ __global__ void __launch_bounds__(TBX *TBY) k_residual64(Grid g, const double *_
         int64_t i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
         v = b[i] - apply_row<DIM, KIND, double>(g, A, x, ix, iy, iz, i);
         if (r) r[i] = v;
-        if (r32) r32[i] = (float)v;
+        if (r32) r32[i] = st<TL>((typename AccT<TL>::type)v);
     }
     if (red) {
         double t = block_sum(v * v, sm);
@@ -626,6 +661,42 @@ __global__ void k_scale_dev(int64_t N, const double *num, double *y, const doubl
 // y = x / sqrt(*num)
 cs_status launch_scale_dev(int64_t N, const double *num, double *y, const double *x, cudaStream_t s) {
     k_scale_dev<<<1216, 256, 0, s>>>(N, num, y, x);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+
+// r = b - A x in FP64, stored in BF16 for the cycle (no reduction)
+cs_status launch_residual64_bf16(const Level &L, const double *A, const double *b, const double *x,
+                                 __nv_bfloat16 *r16, cudaStream_t s) {
+    dim3 gr = node_grid(L.g), bl = node_block();
+    if (L.g.dim == 2) {
+        if (L.kind == STAR) k_residual64<2, STAR, __nv_bfloat16><<<gr, bl, 0, s>>>(L.g, A, b, x, nullptr, r16, nullptr);
+        else k_residual64<2, BOX, __nv_bfloat16><<<gr, bl, 0, s>>>(L.g, A, b, x, nullptr, r16, nullptr);
+    } else {
+        if (L.kind == STAR) k_residual64<3, STAR, __nv_bfloat16><<<gr, bl, 0, s>>>(L.g, A, b, x, nullptr, r16, nullptr);
+        else k_residual64<3, BOX, __nv_bfloat16><<<gr, bl, 0, s>>>(L.g, A, b, x, nullptr, r16, nullptr);
+    }
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+__global__ void k_axpy_bf16(int64_t N, const __nv_bfloat16 *__restrict__ d, double *__restrict__ x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += (double)__bfloat162float(d[i]);
+}
+cs_status launch_axpy_bf16(int64_t N, const __nv_bfloat16 *d, double *x, cudaStream_t s) {
+    k_axpy_bf16<<<1216, 256, 0, s>>>(N, d, x);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+__global__ void k_d2bf(int64_t N, const double *__restrict__ a, __nv_bfloat16 *__restrict__ o) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        o[i] = __double2bfloat16(a[i]);
+}
+cs_status launch_copy_d2bf(int64_t N, const double *a, __nv_bfloat16 *o, cudaStream_t s) {
+    k_d2bf<<<1216, 256, 0, s>>>(N, a, o);
     CSX_CUDA(cudaGetLastError());
     count_launch();
     return CS_OK;
@@ -711,9 +782,9 @@ __global__ void k_coarse_solve(int n, const double *__restrict__ Cinv, const T *
     int lane = threadIdx.x & 31;
     if (warp >= n) return;
     double s = 0.0;
-    for (int j = lane; j < n; j += 32) s = fma(Cinv[(int64_t)warp * n + j], (double)b[j], s);
+    for (int j = lane; j < n; j += 32) s = fma(Cinv[(int64_t)warp * n + j], (double)ld<T>(b[j]), s);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) x[warp] = (T)s;
+    if (lane == 0) x[warp] = st<T>((typename AccT<T>::type)s);
 }
 cs_status launch_coarse_solve(const cs_hierarchy *h, const double *b, double *x, cudaStream_t s) {
     int threads = 256, blocks = (h->cn * 32 + threads - 1) / threads;
@@ -725,6 +796,13 @@ cs_status launch_coarse_solve(const cs_hierarchy *h, const double *b, double *x,
 cs_status launch_coarse_solve32(const cs_hierarchy *h, const float *b, float *x, cudaStream_t s) {
     int threads = 256, blocks = (h->cn * 32 + threads - 1) / threads;
     k_coarse_solve<float><<<blocks, threads, 0, s>>>(h->cn, h->cinv, b, x);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+cs_status launch_coarse_solve16(const cs_hierarchy *h, const __nv_bfloat16 *b, __nv_bfloat16 *x, cudaStream_t s) {
+    int threads = 256, blocks = (h->cn * 32 + threads - 1) / threads;
+    k_coarse_solve<__nv_bfloat16><<<blocks, threads, 0, s>>>(h->cn, h->cinv, b, x);
     CSX_CUDA(cudaGetLastError());
     count_launch();
     return CS_OK;

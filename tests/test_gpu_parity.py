@@ -361,3 +361,52 @@ def test_repeated_row_reuse_is_exact(built, dim, n, kind, nu):
         l1, l0 = cmg.export_lambda(c1, l), cmg.export_lambda(c0, l)
         assert np.array_equal(l1, l0), f"lambda level {l}"
         assert gu.rel_max(l1, co.lam(l)) <= TOL
+
+
+@pytest.mark.parametrize("name,kind", [("v2d_37", "additive"), ("v3d_17", "multiplicative"), ("p2d_64", "additive")])
+def test_bf16_steps_match_oracle(built, name, kind):
+    """BF16 storage with FP32 arithmetic: one cascade step on the finest level
+    against the same step in FP64, out = x - Lambda_2 (A x - b) written out
+    here from the oracle's operator and Lambda and the same (BF16-rounded)
+    inputs, within 1e-2 of the result's scale (coefficients and Lambda carry
+    8-bit mantissas, the output is rounded once more)."""
+    import torch
+
+    import paper_2606_12577_gb300 as cmg
+    A = PROBLEMS[name]()
+    ho = oracle.Hierarchy(A)
+    co = oracle.Cascade(ho, kind, nu=2)
+    hg = gu.gpu_hierarchy(A)
+    cg = cmg.setup_cascade(hg, kind, nu=2, lowp=2)
+    rng = np.random.default_rng(7)
+    b = rng.uniform(-1, 1, A.N)
+    x = rng.uniform(-1, 1, A.N)
+    bb = torch.tensor(b, device="cuda").to(torch.bfloat16)
+    xb = torch.tensor(x, device="cuda").to(torch.bfloat16)
+    out = torch.zeros_like(xb)
+    col = 0 if kind == "multiplicative" else -1
+    cmg.sweep(hg, cg, 0, 1, bb, xb, out, colour=col)
+    got = out.double().cpu().numpy()
+    bd, xd = bb.double().cpu().numpy(), xb.double().cpu().numpy()
+    lam = co.lam(0).reshape(2, -1)[1]
+    ref = xd - lam * (gu.oracle_csr(ho, 0) @ xd - bd)
+    if col >= 0:
+        ref = np.where(ho.colours(0) == col, ref, xd)
+    assert gu.rel_max(got, ref) <= 1e-2
+
+
+@pytest.mark.parametrize("name,kind,method", [("p2d_64", "additive", "refine"), ("v3d_17", "multiplicative", "refine"),
+                                              ("c2d_130", "additive", "gmres")])
+def test_bf16_cycles_reach_1e10(built, name, kind, method):
+    """BF16 cycles inside FP64 refinement (or FP64 GMRES) reach 1e-10 in the
+    true residual, recomputed here from the stencil."""
+    import paper_2606_12577_gb300 as cmg
+    A = PROBLEMS[name]()
+    hg = gu.gpu_hierarchy(A)
+    cg = cmg.setup_cascade(hg, kind, nu=3, lowp=2)
+    b = problems.rhs(A.N, 11)
+    x = _dev(np.zeros(A.N))
+    info = cmg.solve(hg, cg, _dev(b), x, method=method, precision="bf16", tol=1e-10, maxit=200)
+    assert info.converged
+    r = b - gu.stencil_matvec(A, _host(x))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
