@@ -177,6 +177,18 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The largest of every rank's value (all ranks receive it): the job's
+    time is its slowest replica's.  One rank: the value itself."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def config(a):
     return {"workload": f"3D Poisson 7-point FD {a.n}^3 interior, Dirichlet, RHS U[-1,1] seed 2002; "
                         f"{a.kind} cascade nu={a.nu}, V({a.mu},{a.mu}) {a.order}, Galerkin to 4^3, "
@@ -467,12 +479,7 @@ def main():
         e1.record(s)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1) / steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
 
     if a.profile:
         h = cmg.setup_hierarchy(A.dim, A.n, A.offsets, coeff)
@@ -640,11 +647,7 @@ def main():
             e2e_step()
             torch.cuda.synchronize()
             times.append((time.perf_counter() - t0) * 1e3)
-        e2e_ms = float(np.median(times))
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(float(np.median(times)), world, dev)
         result["e2e"] = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(A.coeff.nbytes + 2 * 8 * A.N),
                          "d2h_bytes_per_step": int(8 * A.N), "steps_ms": [round(t, 2) for t in times]}
         if rank == 0 and world == 1:

@@ -236,13 +236,16 @@ class MLP:
                     "cs_mlp_gradients")
         return float(loss.value), g
 
-    def train_step(self, X, T, lr, stream=None):
+    def train_step(self, X, T, lr, with_loss=True, stream=None):
+        """One Adam step; returns the loss before it (the call then
+        synchronises), or None with ``with_loss=False`` (no synchronisation)."""
         B = X.shape[0]
         _f32(X, B * self.nin, "X"), _f32(T, B * self.nout, "T")
         loss = C.c_float(0.0)
         _capi.check(_capi.lib().cs_mlp_train_step(self._p, B, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
-                                                  float(lr), C.byref(loss), _stream(stream)), "cs_mlp_train_step")
-        return float(loss.value)
+                                                  float(lr), C.byref(loss) if with_loss else None, _stream(stream)),
+                    "cs_mlp_train_step")
+        return float(loss.value) if with_loss else None
 
 
 def _f32(t, n, name):

@@ -32,26 +32,34 @@ def make_dataset(meshes, bs: int = 3, nu: int = 3):
 
 
 def train(model: "cmg.MLP", X, T, steps: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
-          lr_final: float = 1e-5):
-    """Adam on minibatches drawn without replacement per epoch; learning rate
-    decays geometrically from lr to lr_final.  Returns the loss history."""
+          lr_final: float = 1e-5, log_every: int = 10):
+    """Adam on minibatches drawn without replacement per epoch (one permuted
+    copy of the data per epoch, batches are contiguous slices of it); the
+    learning rate decays geometrically from lr to lr_final.  The loss is read
+    back (one synchronisation) every ``log_every`` steps and at the last one;
+    returns those losses."""
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
     n = X.shape[0]
     batch = min(batch, n, model.max_batch)
-    perm = torch.randperm(n, device="cuda", generator=g)
+
+    def shuffled():
+        perm = torch.randperm(n, device="cuda", generator=g)
+        return X.index_select(0, perm).contiguous(), T.index_select(0, perm).contiguous()
+
+    Xs, Ts = shuffled()
     pos = 0
     hist = []
     decay = (lr_final / lr) ** (1.0 / max(1, steps - 1))
     for k in range(steps):
         if pos + batch > n:
-            perm = torch.randperm(n, device="cuda", generator=g)
+            Xs, Ts = shuffled()
             pos = 0
-        idx = perm[pos:pos + batch]
+        want = k % log_every == 0 or k == steps - 1
+        loss = model.train_step(Xs[pos:pos + batch], Ts[pos:pos + batch], lr * decay ** k, with_loss=want)
         pos += batch
-        xb = X.index_select(0, idx).contiguous()
-        tb = T.index_select(0, idx).contiguous()
-        hist.append(model.train_step(xb, tb, lr * decay ** k))
+        if want:
+            hist.append(loss)
     return hist
 
 
