@@ -56,8 +56,9 @@ typedef struct cs_mlp cs_mlp;
 /* ------------------------------------------------------------- operator */
 /* A structured-grid operator in stencil form (Sec. 2: the block-partitioned
  * A x = b; Sec. 3.3.1: FD Poisson).  coeff[s*N + i] couples unknown i to the
- * node at i + off[s]; it must be zero where that node lies outside the grid
- * (a Dirichlet node).  Offsets are in {-1,0,1}^dim and (0,0,0) must be
+ * node at i + off[s]; where that node lies outside the grid (a homogeneous
+ * Dirichlet node) the coefficient multiplies a zero value and is ignored:
+ * cs_setup_hierarchy stores it as zero.  Offsets are in {-1,0,1}^dim and (0,0,0) must be
  * present.  With periodic != 0 neighbours wrap around (accepted by
  * cs_setup_hierarchy only with max_levels == 1: used to check the setup
  * against the constant-coefficient coefficients of Table 1). */
@@ -223,7 +224,7 @@ cs_status cs_residual(const cs_hierarchy *h, int level, const double *b, const d
  *   box:     0: coeff holds a 5/7-point stencil in the order C,-x,+x,-y,+y[,-z,+z];
  *            1: a 9/27-point stencil, entry s at offset ((s%3)-1, (s/3%3)-1, (s/9)-1)
  *            (the layouts cs_query_level / cs_export_operator report);
- *            coefficients to nodes outside the grid must be zero.
+ *            coefficients to nodes outside the grid are ignored.
  *   coeff:   device [nst][N];  lam: device [nu][N] (point-block Lambda_l, the
  *            multiplicative Lambda_{l,k} on the nodes of colour k, as
  *            cs_export_lambda returns);  b, x: device [N].

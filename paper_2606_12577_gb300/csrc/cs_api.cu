@@ -375,6 +375,7 @@ cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts
         }
         if (A0->coeff_on_host && e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { rc = cuda_fail(e, "copy operator", __FILE__, __LINE__); goto fail; }
+        if (!h->periodic && (rc = drop_outside_couplings(L, s)) != CS_OK) goto fail;
         if (!opts.no_reuse && (rc = level_margin(L, h->periodic, s)) != CS_OK) goto fail;
     }
     while (!h->periodic && (opts.max_levels <= 0 || (int)h->lev.size() < opts.max_levels)) {

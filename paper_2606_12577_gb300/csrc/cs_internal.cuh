@@ -197,6 +197,8 @@ constexpr int NRED = 1024;  // partial sums of a reduction
 // ---- setup kernels (cs_setup.cu)
 cs_status galerkin_level(const Level &f, Level &c, bool reuse, cudaStream_t s);
 cs_status level_margin(Level &L, bool periodic, cudaStream_t s);
+// zeroes the coefficients of couplings to nodes outside a Dirichlet grid
+cs_status drop_outside_couplings(const Level &L, cudaStream_t s);
 cs_status coarse_factor(cs_hierarchy *h, cudaStream_t s);
 cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, int alpha,
                               double *lam, cudaStream_t s, int64_t *peak_bytes);

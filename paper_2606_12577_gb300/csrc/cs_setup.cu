@@ -149,6 +149,34 @@ __global__ void k_const_margin(Grid g, int nst, const double *__restrict__ A, in
     if (!eq) atomicMax(maxd, bdist(g, ix, iy, iz));
 }
 
+// Homogeneous Dirichlet elimination: a coupling to a node outside the grid
+// multiplies a zero boundary value, so its coefficient is dropped once, on
+// the copy of the fine operator; the Galerkin product and the margin scan
+// then see only couplings inside the grid.
+struct StencilOff {
+    signed char d[27][3];
+};
+__global__ void k_drop_outside(Grid g, int nst, StencilOff so, double *__restrict__ A) {
+    const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
+    if (ix >= g.nx || iy >= g.ny) return;
+    const int64_t i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
+    for (int s = 0; s < nst; ++s) {
+        const int jx = ix + so.d[s][0], jy = iy + so.d[s][1], jz = iz + so.d[s][2];
+        const bool in = jx >= 0 && jx < g.nx && jy >= 0 && jy < g.ny && jz >= 0 && jz < g.nz;
+        if (!in) A[(int64_t)s * g.N + i] = 0.0;
+    }
+}
+
+cs_status drop_outside_couplings(const Level &L, cudaStream_t s) {
+    StencilOff so{};
+    for (int t = 0; t < L.nst; ++t)
+        for (int d = 0; d < 3; ++d) so.d[t][d] = (signed char)L.off[t][d];
+    k_drop_outside<<<node_grid(L.g), node_block(), 0, s>>>(L.g, L.nst, so, L.A);
+    count_launch();
+    CSX_CUDA(cudaGetLastError());
+    return CS_OK;
+}
+
 cs_status level_margin(Level &L, bool periodic, cudaStream_t s) {
     const Grid &g = L.g;
     const int64_t ref = g.nx / 2 + (int64_t)g.nx * (g.ny / 2 + (int64_t)g.ny * (g.nz / 2));
@@ -183,8 +211,10 @@ __host__ __device__ constexpr double pw(int u) { return u == 0 ? 1.0 : ((u == 1 
 // u = d_k + s_k in [-2, 2] selects one coarse neighbour (u even) or two with
 // weight 1/2 (u odd).  The 3^dim accumulators of a thread live in shared
 // memory (registers would need dynamic indexing).  Couplings to nodes
-// outside the grid are zero coefficients; fine nodes beyond the upper edge
-// are skipped; entries whose coarse neighbour lies outside are set to zero.
+// outside the grid carry zero coefficients (dropped when the fine operator
+// is copied in, and zero by construction on Galerkin levels); fine nodes
+// beyond the upper edge are skipped; entries whose coarse neighbour lies
+// outside are set to zero.
 template <int DIM, int KIND>
 __global__ void __launch_bounds__(TBX *TBY) k_galerkin(Grid gf, Grid gc, const double *__restrict__ Af,
                                                         double *__restrict__ Ac, RowSet rs) {

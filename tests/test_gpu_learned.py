@@ -73,7 +73,7 @@ def test_training_and_learned_setup(built):
     meshes = [problems.q1_jittered(47, 100 + k) for k in range(8)]
     X, T = learned.make_dataset(meshes)
     m = cmg.MLP(X.shape[1], 128, T.shape[1], max_batch=4096, seed=7)
-    hist = learned.train(m, X, T, steps=600, batch=1024, lr=2e-3)
+    hist = learned.train(m, X, T, steps=600, batch=1024, lr=2e-3, log_every=1)
     assert np.mean(hist[-20:]) < 0.2 * np.mean(hist[:5])
     A = problems.q1_jittered(95, 9999)
     h, res = learned.setup_pair(A, m)

@@ -330,14 +330,16 @@ def test_errors_are_reported(built):
 
 
 def test_zero_rhs(built):
+    """b = 0: every method returns x = 0 after zero iterations, whatever x held."""
     import paper_2606_12577_gb300 as cmg
     A = problems.poisson(2, 16)
     hg = gu.gpu_hierarchy(A)
-    cg = cmg.setup_cascade(hg, "additive", nu=2)
-    x = _dev(np.ones(A.N))
-    info = cmg.solve(hg, cg, _dev(np.zeros(A.N)), x)
-    assert info.converged and info.iterations == 0
-    assert not _host(x).any()
+    cg = cmg.setup_cascade(hg, "additive", nu=2, lowp=True)
+    for method, prec in (("stationary", "fp64"), ("refine", "fp32"), ("gmres", "fp64")):
+        x = _dev(np.full(A.N, 5.0))
+        info = cmg.solve(hg, cg, _dev(np.zeros(A.N)), x, method=method, precision=prec)
+        assert info.converged and info.iterations == 0, method
+        assert not _host(x).any(), method
 
 
 @pytest.mark.parametrize("dim,n,kind,nu", [(3, 40, "additive", 3), (3, 41, "multiplicative", 2), (2, 97, "additive", 4),
@@ -410,3 +412,76 @@ def test_bf16_cycles_reach_1e10(built, name, kind, method):
     assert info.converged
     r = b - gu.stencil_matvec(A, _host(x))
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
+
+
+def _rect(nx, ny, nz=1, seed=0):
+    """Symmetric variable-coefficient 5/7-point operator on an nx x ny (x nz)
+    grid: every edge (including those to the Dirichlet boundary) carries a
+    random weight in [0.5, 2]; off-diagonal = -weight, diagonal = sum of the
+    node's edge weights (SPD).  The couplings to boundary nodes are left
+    nonzero in the arrays: the operator ignores them (they multiply a zero
+    boundary value), which the oracle's CSR assembly does by construction."""
+    dim = 2 if nz == 1 else 3
+    offs = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0)] + ([(0, 0, -1), (0, 0, 1)] if dim == 3 else [])
+    shape = (nz, ny, nx)
+    N = nx * ny * nz
+    coeff = np.zeros((len(offs), N))
+    for ax in range(dim):  # edges along axis ax (x = last array axis)
+        eshape = list(shape)
+        eshape[2 - ax] += 1
+        w = problems.uniform(900 + 10 * seed + ax, int(np.prod(eshape)), 0.5, 2.0).reshape(eshape)
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[2 - ax] = slice(0, shape[2 - ax])
+        hi[2 - ax] = slice(1, shape[2 - ax] + 1)
+        wlo, whi = w[tuple(lo)].ravel(), w[tuple(hi)].ravel()  # edge to the -e and +e neighbour
+        coeff[1 + 2 * ax] = -wlo
+        coeff[2 + 2 * ax] = -whi
+        coeff[0] += wlo + whi
+    return problems.Stencil(dim, (nx, ny, nz), offs, coeff, False)
+
+
+@pytest.mark.parametrize("n3", [(1, 1, 1), (2, 2, 1), (3, 3, 1), (5, 5, 1), (33, 5, 1), (2, 33, 1), (1, 40, 1),
+                                (17, 3, 2), (5, 2, 9), (4, 4, 4)])
+def test_degenerate_and_anisotropic_grids(built, n3):
+    """One-level hierarchies (the coarsest solve alone), one-node-wide and
+    anisotropic grids where coarsening stops at a side of 1: dimensions
+    bit-exact, Lambda and stationary solves equal to the oracle's, FP32
+    refinement to 1e-10."""
+    import paper_2606_12577_gb300 as cmg
+    A = _rect(*n3, seed=sum(n3))
+    ho = oracle.Hierarchy(A)
+    hg = gu.gpu_hierarchy(A)
+    assert hg.nlevels == ho.nlev
+    for l in range(ho.nlev):
+        info = cmg.query_level(hg, l)
+        assert info["n"] == ho.dims(l)
+        offs, coeff = cmg.export_operator(hg, l)
+        nx, ny, nz = info["n"]
+        ix, iy, iz = np.arange(nx)[None, None, :], np.arange(ny)[None, :, None], np.arange(nz)[:, None, None]
+        for s, (dx, dy, dz) in enumerate(offs):  # couplings to outside nodes are stored as zero
+            ok = ((ix + dx >= 0) & (ix + dx < nx) & (iy + dy >= 0) & (iy + dy < ny) & (iz + dz >= 0) &
+                  (iz + dz < nz)).ravel()
+            assert not coeff[s][~ok].any(), (l, s)
+        G = gu.stencil_to_csr(info["n"], offs, coeff)
+        O = gu.oracle_csr(ho, l)
+        assert abs(G - O).max() <= TOL * abs(O).max(), l
+    for kind in ("additive", "multiplicative"):
+        co = oracle.Cascade(ho, kind, nu=2)
+        cg = cmg.setup_cascade(hg, kind, nu=2, lowp=True)
+        for l in range(co.nlev):
+            lg, lo = cmg.export_lambda(cg, l), co.lam(l)
+            if ho.N(l) == 1:
+                # one unknown: the first step solves it, so every later
+                # least-squares problem has R = 0 in exact arithmetic and its
+                # lambda is a ratio of rounding errors; only step 1 is defined
+                lg, lo = lg[:1], lo[:1]
+            assert gu.rel_max(lg, lo) <= TOL
+        b = problems.rhs(A.N, 3)
+        xo, it, _, _ = oracle.solve(ho, co, b, method="stationary", tol=1e-10, maxit=100)
+        x = _dev(np.zeros(A.N))
+        info = cmg.solve(hg, cg, _dev(b), x, method="stationary", tol=1e-10, maxit=100)
+        assert info.converged and info.iterations == it
+        assert gu.rel_max(_host(x), xo) <= 1e-10
+        x32 = _dev(np.zeros(A.N))
+        assert cmg.solve(hg, cg, _dev(b), x32, method="refine", precision="fp32", tol=1e-10).converged
