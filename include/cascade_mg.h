@@ -300,17 +300,21 @@ typedef struct {
     int precision;   /* CS_FP32 (FP32 cycles inside FP64 refinement) or CS_FP64 */
     int order;       /* CS_RF or CS_FF, as for cs_vcycle */
     int mu_pre, mu_post;
-    int autotune;    /* 1: time each (threads, tile_nodes) candidate on the batch and keep the fastest */
+    int autotune;    /* 1: time each (threads, tiles_per_cta) candidate on the batch and keep the fastest */
     int threads;     /* CTA size if not autotuned (default 256; 32..512, multiple of 32) */
-    int tile_nodes;  /* grid nodes per work tile if not autotuned (default 1024) */
+    int tiles_per_cta; /* if not autotuned (default 2; 1..1024): each stage's work items (grid node x
+                        right-hand side) are cut into about tiles_per_cta x CTAs tiles of equal work,
+                        none smaller than the CTA size */
     int method;      /* CS_REFINE: x += V0(b - A x); CS_GMRES: left-preconditioned restarted GMRES
-                        with M = V0 per right-hand side (modified Gram-Schmidt, Givens; inner
-                        steps stop on |g_{j+1}| <= tol ||M b||, restarts check the true residual) */
+                        with M = V0 per right-hand side (classical Gram-Schmidt, projected a
+                        second time when the first removes more than half of ||Z||^2 (DGKS);
+                        Givens; inner steps stop on |g_{j+1}| <= tol ||M b||, restarts check
+                        the true residual) */
     int restart;     /* GMRES restart length (default 30, at most 64) */
 } cs_batch_opts;
 typedef struct {
     int threads;
-    int tile_nodes;
+    int tiles_per_cta;
     float ms;        /* measured time of two iterations on the batch */
 } cs_batch_tune;
 /* Plan a batched solve over existing handles (not owned; they must outlive
@@ -331,10 +335,10 @@ cs_status cs_batch_solve(cs_batch *b, const double *const *bvec, double *const *
                          cs_solve_info *info, cs_stream stream);
 /* The configuration in use, the CTAs of the cooperative launch, and the
  * autotuner's measurements (up to cap entries; *ntuned = their count). */
-cs_status cs_batch_config(const cs_batch *b, int *threads, int *tile_nodes, int *ctas, cs_batch_tune *tuned,
+cs_status cs_batch_config(const cs_batch *b, int *threads, int *tiles_per_cta, int *ctas, cs_batch_tune *tuned,
                           int cap, int *ntuned);
 /* Force a configuration (e.g. to compare schedules); results do not depend on it. */
-cs_status cs_batch_set_config(cs_batch *b, int threads, int tile_nodes, cs_stream stream);
+cs_status cs_batch_set_config(cs_batch *b, int threads, int tiles_per_cta, cs_stream stream);
 int64_t cs_batch_bytes(const cs_batch *b);
 void cs_batch_destroy(cs_batch *b);
 /* One-shot form: plan (no autotuning), solve, release.  opts->cycle gives the

@@ -475,14 +475,14 @@ class Batch:
     right-hand sides contiguous per node."""
 
     def __init__(self, hs, cs, nrhs, precision="fp32", order="RF", mu_pre=1, mu_post=1, autotune=False, threads=0,
-                 tile_nodes=0, method="refine", restart=30, stream=None):
+                 tiles_per_cta=0, method="refine", restart=30, stream=None):
         self.hs, self.cs = list(hs), list(cs)
         self.nprob = len(self.hs)
         self.nrhs = [int(m) for m in nrhs]
         self.N = [h.N(0) for h in self.hs]
         o = _capi.cs_batch_opts(_capi.CS_FP32 if precision == "fp32" else _capi.CS_FP64,
                                 _capi.CS_RF if order == "RF" else _capi.CS_FF, mu_pre, mu_post, int(autotune),
-                                threads, tile_nodes, _capi.CS_GMRES if method == "gmres" else _capi.CS_REFINE,
+                                threads, tiles_per_cta, _capi.CS_GMRES if method == "gmres" else _capi.CS_REFINE,
                                 restart)
         hp = (C.c_void_p * self.nprob)(*[h.ptr for h in self.hs])
         cp = (C.c_void_p * self.nprob)(*[c.ptr for c in self.cs])
@@ -497,11 +497,11 @@ class Batch:
         buf = (_capi.cs_batch_tune * 64)()
         _capi.check(_capi.lib().cs_batch_config(self._p, C.byref(t), C.byref(tn), C.byref(ct), buf, 64,
                                                 C.byref(nt)), "cs_batch_config")
-        return {"threads": t.value, "tile_nodes": tn.value, "ctas": ct.value,
-                "tuned": [(buf[i].threads, buf[i].tile_nodes, buf[i].ms) for i in range(min(nt.value, 64))]}
+        return {"threads": t.value, "tiles_per_cta": tn.value, "ctas": ct.value,
+                "tuned": [(buf[i].threads, buf[i].tiles_per_cta, buf[i].ms) for i in range(min(nt.value, 64))]}
 
-    def set_config(self, threads, tile_nodes, stream=None):
-        _capi.check(_capi.lib().cs_batch_set_config(self._p, threads, tile_nodes, _stream(stream)),
+    def set_config(self, threads, tiles_per_cta, stream=None):
+        _capi.check(_capi.lib().cs_batch_set_config(self._p, threads, tiles_per_cta, _stream(stream)),
                     "cs_batch_set_config")
 
     def nbytes(self):

@@ -59,12 +59,12 @@ class cs_level_info(C.Structure):
 
 class cs_batch_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("order", C.c_int), ("mu_pre", C.c_int), ("mu_post", C.c_int),
-                ("autotune", C.c_int), ("threads", C.c_int), ("tile_nodes", C.c_int), ("method", C.c_int),
+                ("autotune", C.c_int), ("threads", C.c_int), ("tiles_per_cta", C.c_int), ("method", C.c_int),
                 ("restart", C.c_int)]
 
 
 class cs_batch_tune(C.Structure):
-    _fields_ = [("threads", C.c_int), ("tile_nodes", C.c_int), ("ms", C.c_float)]
+    _fields_ = [("threads", C.c_int), ("tiles_per_cta", C.c_int), ("ms", C.c_float)]
 
 
 _lock = threading.Lock()

@@ -7,8 +7,8 @@
 // level slot t of the batch holds level t - (D - nlev_p) of problem p
 // (D = the largest level count) and every stage is one ragged sweep over the
 // slot's levels.  Work is dealt out in tiles (a problem, a level, a contiguous
-// range of its grid rows' nodes); the tile size and the CTA size are picked
-// by a measuring autotuner.
+// range of its grid rows' nodes) of about equal work; the number of tiles per
+// CTA and the CTA size are picked by a measuring autotuner.
 //
 // Data layout: vectors of problem p hold its m_p right-hand sides
 // contiguously per node, v[i * m_p + r] (m_p <= 8); operators and Lambda are
@@ -104,6 +104,15 @@ struct BArgs {
     double *nmb;    // [q]: ||M b||
     int *jcols;     // [q]: Krylov columns built in this cycle
     int *frozen;    // [q]: no longer extending in this cycle
+    // classical Gram-Schmidt: per-tile projection partials, problem p's
+    // block at p2off[p], [tile of p][slot i < restart + 2][r < m_p]
+    double *part2;
+    const int64_t *p2off;
+    int qtot;            // right-hand sides of all problems
+    const int *qlist;    // [qtot]: q = p * BMAXRHS + r
+    double *hsum;        // [q][restart + 2]: this pass's <Z, V_i> (slot j + 1: <Z, Z>)
+    double *znorm2;      // [q]: ||Z||^2 after the first projection
+    int *reorth;         // [q]: the step projects a second time
 };
 
 __device__ __forceinline__ int bcolour(int ix, int iy) { return ((ix + 1) + (iy + 1)) & 1; }
@@ -172,6 +181,32 @@ __device__ __forceinline__ void cta_sum_by_rhs(double v, int m, double *red, dou
         __syncthreads();
     }
     if (t < m) out[t] = red[t];
+    __syncthreads();
+}
+
+// The same tree for nv <= 4 sums at once (red holds 4 x blockDim.x values):
+// out[u * ostride + r] = the sum of value u over right-hand side r.
+__device__ __forceinline__ void cta_sum4_by_rhs(const double *v, int nv, int m, double *red, double *out,
+                                                int ostride) {
+    const int t = threadIdx.x, T = (int)blockDim.x;
+    const int G = T / m, U = G * m;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) red[u * T + t] = t < U && u < nv ? v[u] : 0.0;
+    __syncthreads();
+    int P = 1;
+    while (2 * P <= G) P *= 2;
+    if (t < (G - P) * m)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) red[u * T + t] += red[u * T + t + P * m];
+    __syncthreads();
+    for (int h = P / 2; h > 0; h /= 2) {
+        if (t < h * m)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) red[u * T + t] += red[u * T + t + h * m];
+        __syncthreads();
+    }
+    if (t < m)
+        for (int u = 0; u < nv; ++u) out[u * ostride + t] = red[u * T + t];
     __syncthreads();
 }
 
@@ -425,9 +460,8 @@ enum {
     F_MB,          // (A) cycle input = b, output = 0 (for ||M b||)
     F_CONVZ,       // (W) Z = cycle output in FP64; partial sums of Z^2
     F_MATVEC,      // (W) cycle input = A V_j, output = 0
-    F_DOT,         // (W) partial sums of <Z, V_i>
-    F_AXPY,        // (W) Z -= h_ij V_i
-    F_NRMZ,        // (W) partial sums of Z^2
+    F_PROJ,        // (W) partial sums of <Z, V_i>, i <= j (pass 0 also <Z, Z>) -> part2
+    F_PAXPY,       // (W) Z -= sum_i hsum_i V_i, i <= j; partial sums of Z^2
     F_SCALEV,      // (W) V_j = Z / ||Z||
     F_XUPD         // (A) x += sum_k y_k V_k
 };
@@ -437,7 +471,7 @@ __device__ __forceinline__ bool fine_gate_all(int what) {
            what == F_XUPD;
 }
 __device__ __forceinline__ bool fine_reduces(int what) {
-    return what == F_BNORM || what == F_RESID || what == F_CONVZ || what == F_DOT || what == F_NRMZ;
+    return what == F_BNORM || what == F_RESID || what == F_CONVZ || what == F_PAXPY;
 }
 
 template <typename T>
@@ -461,6 +495,33 @@ __device__ void stage_fine(const BArgs &a, const BProb<T> *P, int what, int iarg
         const double *__restrict__ V = pr.V;
         T *__restrict__ lb = L.b;
         T *__restrict__ lx = L.x;
+        if (what == F_PROJ) {
+            // projections of Z on V_0..V_j (pass 0 adds <Z, Z> as slot j + 1),
+            // four slots per sweep over the tile's items
+            const int nsl = iarg == 0 ? jarg + 2 : jarg + 1;
+            const bool on = tm.on && (iarg == 0 ? !a.frozen[q] : a.reorth[q] != 0);
+            double *dst = a.part2 + a.p2off[p] + (int64_t)(k - a.ftile_of[p]) * (a.restart + 2) * m;
+            for (int s0 = 0; s0 < nsl; s0 += 4) {
+                double pacc[4] = {0.0, 0.0, 0.0, 0.0};
+                const double *__restrict__ vs[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = s0 + u;
+                    vs[u] = i <= jarg ? V + (int64_t)i * nm : Z;
+                }
+                const int nv = min(4, nsl - s0);
+                if (on)
+                    for (int nn = n0; nn < ni; nn += step) {
+                        const int64_t e = (int64_t)(i0 + nn) * m + r;
+                        const double z = Z[e];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (u < nv) pacc[u] = fma(z, vs[u][e], pacc[u]);
+                    }
+                cta_sum4_by_rhs(pacc, nv, m, red, dst + (int64_t)s0 * m, m);
+            }
+            continue;
+        }
         double acc = 0.0;
         if (tm.on) {
             if (what == F_BNORM) {
@@ -505,25 +566,18 @@ __device__ void stage_fine(const BArgs &a, const BProb<T> *P, int what, int iarg
                     Z[e] = z;
                     acc = fma(z, z, acc);
                 }
-            } else if (what == F_DOT) {
-                const double *__restrict__ Vi = V + (int64_t)iarg * nm;
-                for (int nn = n0; nn < ni; nn += step) {
-                    const int64_t e = (int64_t)(i0 + nn) * m + r;
-                    acc = fma(Z[e], Vi[e], acc);
-                }
-            } else if (what == F_AXPY) {
-                if (!a.frozen[q]) {
-                    const double *__restrict__ Vi = V + (int64_t)iarg * nm;
-                    const double h = a.H[(int64_t)q * a.hstride + iarg * a.restart + jarg];
+            } else if (what == F_PAXPY) {
+                // pass iarg: 0 -> every extending right-hand side, 1 -> those reprojected
+                if (iarg == 0 ? !a.frozen[q] : a.reorth[q] != 0) {
+                    const double *__restrict__ hq = a.hsum + (int64_t)q * (a.restart + 2);
                     for (int nn = n0; nn < ni; nn += step) {
                         const int64_t e = (int64_t)(i0 + nn) * m + r;
-                        Z[e] = fma(-h, Vi[e], Z[e]);
+                        double z = Z[e];
+#pragma unroll 4
+                        for (int i = 0; i <= jarg; ++i) z = fma(-hq[i], V[(int64_t)i * nm + e], z);
+                        Z[e] = z;
+                        acc = fma(z, z, acc);
                     }
-                }
-            } else if (what == F_NRMZ) {
-                for (int nn = n0; nn < ni; nn += step) {
-                    const int64_t e = (int64_t)(i0 + nn) * m + r;
-                    acc = fma(Z[e], Z[e], acc);
                 }
             } else if (what == F_SCALEV) {
                 if (!a.frozen[q] || jarg == 0) {
@@ -558,7 +612,7 @@ enum {
     P_NORM,       // true relative residuals: convergence, divergence, limit; counts active problems
     P_NMB,        // ||M b|| (GMRES stopping estimate scale)
     P_BETA,       // beta = ||M r||, g = beta e_1, V_0 scale; counts extending right-hand sides
-    P_HSTORE,     // H(i, j) = <Z, V_i>
+    P_REORTH,     // ||Z||^2 after the first projection; reproject where it fell below half <Z, Z>; counts them
     P_GIVENS,     // H(j+1, j) = ||Z||, rotations, g, freeze; counts extending right-hand sides
     P_SOLVEY      // y = H^{-1} g (back substitution over the columns built)
 };
@@ -567,7 +621,8 @@ template <typename T>
 __device__ void stage_prob(const BArgs &a, const BProb<T> *P, int what, int iarg, int jarg, int ph, bool first,
                            double *wsum) {
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    if ((what == P_NORM || what == P_BETA || what == P_GIVENS) && gid == 0) a.ctl->cnt[ph ^ 1] = 0;
+    if ((what == P_NORM || what == P_BETA || what == P_GIVENS || what == P_REORTH) && gid == 0)
+        a.ctl->cnt[ph ^ 1] = 0;
     const int R = a.restart;
     const int lane = threadIdx.x & 31;
     double *ws = wsum + (threadIdx.x >> 5) * BMAXRHS;
@@ -577,7 +632,7 @@ __device__ void stage_prob(const BArgs &a, const BProb<T> *P, int what, int iarg
     // advances the problem's state
     for (int p = gid >> 5; p < a.nprob; p += (gridDim.x * blockDim.x) >> 5) {
         if (a.state[p] != ST_ACTIVE) continue;  // warp-uniform
-        if ((what == P_HSTORE || what == P_GIVENS) && !a.work[p]) continue;
+        if ((what == P_REORTH || what == P_GIVENS) && !a.work[p]) continue;
         const int m = P[p].m;
         const int q0 = p * BMAXRHS;
         if (sums) {
@@ -629,9 +684,22 @@ __device__ void stage_prob(const BArgs &a, const BProb<T> *P, int what, int iarg
             }
             a.work[p] = ext > 0;
             if (ext) atomicAdd(&a.ctl->cnt[ph], ext);
-        } else if (what == P_HSTORE) {
-            for (int r = 0; r < m; ++r)
-                if (!a.frozen[q0 + r]) a.H[(int64_t)(q0 + r) * a.hstride + iarg * R + jarg] = tsum(r);
+        } else if (what == P_REORTH) {
+            // DGKS criterion: a second projection when ||Z - V h|| < ||Z|| / sqrt(2)
+            int nre = 0;
+            for (int r = 0; r < m; ++r) {
+                const int q = q0 + r;
+                if (a.frozen[q]) {
+                    a.reorth[q] = 0;
+                    continue;
+                }
+                const double ss = tsum(r);
+                a.znorm2[q] = ss;
+                const int re = ss < 0.5 * a.hsum[(int64_t)q * (R + 2) + jarg + 1];
+                a.reorth[q] = re;
+                nre += re;
+            }
+            if (nre) atomicAdd(&a.ctl->cnt[ph], nre);
         } else if (what == P_GIVENS) {
             const int j = jarg;
             a.iters[p] += 1;
@@ -642,7 +710,7 @@ __device__ void stage_prob(const BArgs &a, const BProb<T> *P, int what, int iarg
                 if (a.frozen[q]) continue;
                 double *H = a.H + (int64_t)q * a.hstride;
                 double *cs = a.cs + (int64_t)q * R, *sn = a.sn + (int64_t)q * R, *g = a.g + (int64_t)q * (R + 1);
-                const double ss = tsum(r);
+                const double ss = a.reorth[q] ? tsum(r) : a.znorm2[q];  // ||Z||^2 after the last projection
                 const double hn = sqrt(ss);
                 a.inv[q] = hn > 0.0 ? 1.0 / sqrt(ss) : 0.0;
                 H[(j + 1) * R + j] = hn;
@@ -681,11 +749,73 @@ __device__ void stage_prob(const BArgs &a, const BProb<T> *P, int what, int iarg
     }
 }
 
+// Sums of the projection partials over each problem's tiles, one warp per
+// (slot i, right-hand side): hsum_i = <Z, V_i> (pass 0 also slot j + 1 =
+// <Z, Z>); H(i, j) takes the first pass's value and adds the second's.
+template <typename T>
+__device__ void stage_hsum(const BArgs &a, const BProb<T> *P, int j, int pass) {
+    const int R = a.restart, nsl = pass == 0 ? j + 2 : j + 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t nitems = (int64_t)nsl * a.qtot;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nitems; w += nwarps) {
+        const int qi = (int)(w % a.qtot), i = (int)(w / a.qtot);
+        const int q = a.qlist[qi], p = q / BMAXRHS, r = q - p * BMAXRHS;
+        // warp-uniform gates (flags written before the preceding barrier)
+        if (__ldcg(a.state + p) != ST_ACTIVE || __ldcg(a.work + p) == 0) continue;
+        if (pass == 0 ? __ldcg(a.frozen + q) != 0 : __ldcg(a.reorth + q) == 0) continue;
+        const int m = P[p].m;
+        const int k0 = a.ftile_of[p], k1 = a.ftile_of[p + 1];
+        const int64_t ts = (int64_t)(R + 2) * m;
+        const double *src = a.part2 + a.p2off[p] + (int64_t)i * m + r;
+        double v = 0.0;
+        for (int k = k0 + lane; k < k1; k += 32) v += __ldcg(src + (int64_t)(k - k0) * ts);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+            a.hsum[(int64_t)q * (R + 2) + i] = v;
+            if (i <= j) {
+                double *h = a.H + (int64_t)q * a.hstride + i * R + j;
+                *h = pass == 0 ? v : *h + v;
+            }
+        }
+    }
+}
+
+// Optional stage trace (compiled in with -DCS_BATCH_TRACE only): after each
+// grid barrier thread 0 of CTA 0 records (stage code, %globaltimer), so the
+// gap between consecutive records is the wall time of one stage including
+// its barrier.  Codes: 1000 + 100 op + slot (cycle stages), 2000 + F_* (fine
+// stages), 3000 + P_* (per-problem stages), 4000 + pass (projection sums),
+// 0 (kernel start).
+#ifdef CS_BATCH_TRACE
+constexpr int BTRACE_CAP = 1 << 20;
+__device__ unsigned long long g_btrace[2 * BTRACE_CAP];
+__device__ int g_btrace_n;
+__device__ __forceinline__ void btrace(int code) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        const int k = g_btrace_n++;
+        if (k < BTRACE_CAP) {
+            g_btrace[2 * k] = (unsigned long long)code;
+            g_btrace[2 * k + 1] = t;
+        }
+    }
+}
+#define BSYNC(code)     \
+    do {                \
+        grid.sync();    \
+        btrace(code);   \
+    } while (0)
+#else
+#define BSYNC(code) grid.sync()
+#endif
+
 template <typename T>
 __device__ __forceinline__ void vcycle_stages(const BArgs &a, const BProb<T> *P, cg::grid_group &grid) {
     for (int s = 0; s < a.nsteps; ++s) {
         stage_step<T>(a, P, a.steps[s]);
-        grid.sync();
+        BSYNC(1000 + 100 * a.steps[s].op + a.steps[s].slot);
     }
 }
 
@@ -697,44 +827,47 @@ __device__ __forceinline__ void vcycle_stages(const BArgs &a, const BProb<T> *P,
 template <typename T>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_batch_solve(BArgs a) {
     cg::grid_group grid = cg::this_grid();
-    __shared__ double red[512];
+    __shared__ double red[4 * 512];
     __shared__ double wsum[16 * BMAXRHS];
     const BProb<T> *P = static_cast<const BProb<T> *>(a.probs);
     const int maxit = a.ctl->maxit;
+#ifdef CS_BATCH_TRACE
+    btrace(0);
+#endif
     // counting stages write ctl->cnt[ph] after flipping ph and clear the other
     // slot; the loop tests read the slot written last
     int ph = 0;
     stage_fine<T>(a, P, F_BNORM, 0, 0, red);
-    grid.sync();
+    BSYNC(2000 + F_BNORM);
     stage_prob<T>(a, P, P_NORMB, 0, 0, ph, true, wsum);
-    grid.sync();
+    BSYNC(3000 + P_NORMB);
     stage_fine<T>(a, P, F_ZEROX, 0, 0, red);
-    grid.sync();
+    BSYNC(2000 + F_ZEROX);
     if (a.method == CS_GMRES) {  // ||M b|| per right-hand side
         stage_fine<T>(a, P, F_MB, 0, 0, red);
-        grid.sync();
+        BSYNC(2000 + F_MB);
         vcycle_stages<T>(a, P, grid);
         stage_fine<T>(a, P, F_CONVZ, 0, 0, red);
-        grid.sync();
+        BSYNC(2000 + F_CONVZ);
         stage_prob<T>(a, P, P_NMB, 0, 0, ph, true, wsum);
-        grid.sync();
+        BSYNC(3000 + P_NMB);
     }
     stage_fine<T>(a, P, F_RESID, 0, 0, red);
-    grid.sync();
+    BSYNC(2000 + F_RESID);
     ph ^= 1;
     stage_prob<T>(a, P, P_NORM, 0, 0, ph, true, wsum);
-    grid.sync();
+    BSYNC(3000 + P_NORM);
     if (a.method != CS_GMRES) {
         for (int it = 0; it < maxit; ++it) {
             if (__ldcg(&a.ctl->cnt[ph]) == 0) break;  // active problems
             vcycle_stages<T>(a, P, grid);
             stage_fine<T>(a, P, F_UPDATE, 0, 0, red);
-            grid.sync();
+            BSYNC(2000 + F_UPDATE);
             stage_fine<T>(a, P, F_RESID, 0, 0, red);
-            grid.sync();
+            BSYNC(2000 + F_RESID);
             ph ^= 1;
             stage_prob<T>(a, P, P_NORM, 0, 0, ph, false, wsum);
-            grid.sync();
+            BSYNC(3000 + P_NORM);
         }
         return;
     }
@@ -743,52 +876,75 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_batch_solve(BAr
         if (__ldcg(&a.ctl->cnt[ph]) == 0) break;  // active problems
         vcycle_stages<T>(a, P, grid);  // M r (the cycle input is r from F_RESID)
         stage_fine<T>(a, P, F_CONVZ, 0, 0, red);
-        grid.sync();
+        BSYNC(2000 + F_CONVZ);
         ph ^= 1;
         stage_prob<T>(a, P, P_BETA, 0, 0, ph, false, wsum);
-        grid.sync();
+        BSYNC(3000 + P_BETA);
         stage_fine<T>(a, P, F_SCALEV, 0, 0, red);
-        grid.sync();
+        BSYNC(2000 + F_SCALEV);
         for (int j = 0; j < R; ++j) {
             if (__ldcg(&a.ctl->cnt[ph]) == 0) break;  // right-hand sides still extending
             stage_fine<T>(a, P, F_MATVEC, 0, j, red);
-            grid.sync();
+            BSYNC(2000 + F_MATVEC);
             vcycle_stages<T>(a, P, grid);
             stage_fine<T>(a, P, F_CONVZ, 0, 0, red);
-            grid.sync();
-            for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt
-                stage_fine<T>(a, P, F_DOT, i, j, red);
-                grid.sync();
-                stage_prob<T>(a, P, P_HSTORE, i, j, ph, false, wsum);
-                grid.sync();
-                stage_fine<T>(a, P, F_AXPY, i, j, red);
-                grid.sync();
+            BSYNC(2000 + F_CONVZ);
+            // classical Gram-Schmidt with a second projection where the
+            // first cancelled more than half of ||Z|| (DGKS)
+            stage_fine<T>(a, P, F_PROJ, 0, j, red);
+            BSYNC(2000 + F_PROJ);
+            stage_hsum<T>(a, P, j, 0);
+            BSYNC(4000);
+            stage_fine<T>(a, P, F_PAXPY, 0, j, red);
+            BSYNC(2000 + F_PAXPY);
+            ph ^= 1;
+            stage_prob<T>(a, P, P_REORTH, 0, j, ph, false, wsum);
+            BSYNC(3000 + P_REORTH);
+            if (__ldcg(&a.ctl->cnt[ph]) != 0) {  // right-hand sides projected again
+                stage_fine<T>(a, P, F_PROJ, 1, j, red);
+                BSYNC(2000 + F_PROJ);
+                stage_hsum<T>(a, P, j, 1);
+                BSYNC(4001);
+                stage_fine<T>(a, P, F_PAXPY, 1, j, red);
+                BSYNC(2000 + F_PAXPY);
             }
-            stage_fine<T>(a, P, F_NRMZ, 0, j, red);
-            grid.sync();
             ph ^= 1;
             stage_prob<T>(a, P, P_GIVENS, 0, j, ph, false, wsum);
-            grid.sync();
+            BSYNC(3000 + P_GIVENS);
             stage_fine<T>(a, P, F_SCALEV, 0, j + 1, red);
-            grid.sync();
+            BSYNC(2000 + F_SCALEV);
         }
         // every problem still active solves its small systems and updates x
         // (work flags may have cleared: these stages are gated on the state)
         stage_prob<T>(a, P, P_SOLVEY, 0, 0, ph, false, wsum);
-        grid.sync();
+        BSYNC(3000 + P_SOLVEY);
         stage_fine<T>(a, P, F_XUPD, 0, 0, red);
-        grid.sync();
+        BSYNC(2000 + F_XUPD);
         stage_fine<T>(a, P, F_RESID, 0, 0, red);
-        grid.sync();
+        BSYNC(2000 + F_RESID);
         ph ^= 1;
         stage_prob<T>(a, P, P_NORM, 0, 0, ph, false, wsum);
-        grid.sync();
+        BSYNC(3000 + P_NORM);
     }
 }
 
 }  // namespace csx
 
 using namespace csx;
+
+#ifdef CS_BATCH_TRACE
+// copies up to cap (code, time) records of the trace to host memory and
+// clears it; returns the record count (not declared in the public header)
+extern "C" int cs_batch_trace_read(unsigned long long *host, int cap) {
+    int n = 0;
+    if (cudaMemcpyFromSymbol(&n, g_btrace_n, sizeof(int)) != cudaSuccess) return -1;
+    n = std::min(std::min(n, cap), BTRACE_CAP);
+    if (n > 0 && cudaMemcpyFromSymbol(host, g_btrace, sizeof(unsigned long long) * 2 * n) != cudaSuccess) return -1;
+    const int zero = 0;
+    if (cudaMemcpyToSymbol(g_btrace_n, &zero, sizeof(int)) != cudaSuccess) return -1;
+    return n;
+}
+#endif
 
 struct cs_batch {
     int nprob = 0, dmax = 0, precision = CS_FP32, order = CS_RF, mu_pre = 1, mu_post = 1, nu = 1;
@@ -816,15 +972,18 @@ struct cs_batch {
     double *H = nullptr, *gcs = nullptr, *gsn = nullptr, *gy = nullptr, *gg = nullptr, *ginv = nullptr,
            *gnmb = nullptr;
     int *jcols = nullptr, *frozen = nullptr;
+    double *part2 = nullptr, *hsum = nullptr, *znorm2 = nullptr;
+    int64_t *p2off = nullptr;
+    int *qlist = nullptr, *reorth = nullptr;
+    int qtot = 0;
     const double **bptr = nullptr;
     double **xptr = nullptr;
     // pinned host staging
     void *hstage = nullptr;
     size_t hstage_bytes = 0;
-    int threads = 256, tile_nodes = 1024, ctas = 0;
+    int threads = 256, tiles_per_cta = 2, ctas = 0;
     std::vector<cs_batch_tune> tuned;
     cudaGraphExec_t graph = nullptr;
-    int graph_cfg_threads = 0, graph_cfg_tile = 0;
     bool graph_ok = true;
     double *tune_b = nullptr, *tune_x = nullptr;
     int64_t bytes = 0;
@@ -841,52 +1000,90 @@ void *kernel_of(const cs_batch *B) {
     return B->precision == CS_FP32 ? kernel_ptr<float>() : kernel_ptr<double>();
 }
 
-// tiles of tile_nodes nodes over every (problem, level) of each slot, and
-// over every problem's finest level
-cs_status build_tiles(cs_batch *B, int tile_nodes, cudaStream_t s) {
+// Work tiles of about equal work (grid nodes x right-hand sides): every
+// slot's items, the finest levels' items and (block cascades) every slot's
+// block items are cut into about tiles_per_cta x CTAs tiles, but no tile
+// holds fewer items than a CTA has threads.  A problem's tiles are ranges of
+// its own nodes (or blocks), so a tile's node count is its item share over
+// the problem's right-hand side count.  Few large tiles per CTA keep each
+// stage's serial chain of tile start-up latencies short; equal work per tile
+// keeps the CTAs arriving at the stage barrier together.
+cs_status build_tiles(cs_batch *B, int tiles_per_cta, cudaStream_t s) {
+    const int64_t want = std::max<int64_t>(1, (int64_t)B->ctas * tiles_per_cta);
+    auto tile_items = [&](int64_t items) { return std::max<int64_t>(B->threads, (items + want - 1) / want); };
+    auto cut = [](std::vector<BTile> &out, int p, int l, int64_t n, int64_t per) {
+        for (int64_t i0 = 0; i0 < n; i0 += per) out.push_back({p, l, (int)i0, (int)std::min<int64_t>(per, n - i0)});
+    };
     std::vector<BTile> tl;
     std::vector<int> st(B->dmax + 1, 0);
     for (int t = 0; t < B->dmax; ++t) {
         st[t] = (int)tl.size();
+        int64_t items = 0;
+        for (int p = 0; p < B->nprob; ++p) {
+            const int l = t - B->slot0[p];
+            if (l >= 0) items += (int64_t)B->nx[p][l] * B->ny[p][l] * B->m[p];
+        }
+        const int64_t ti = tile_items(items);
         for (int p = 0; p < B->nprob; ++p) {
             const int l = t - B->slot0[p];
             if (l < 0) continue;
-            const int64_t n = (int64_t)B->nx[p][l] * B->ny[p][l];
-            for (int64_t i0 = 0; i0 < n; i0 += tile_nodes)
-                tl.push_back({p, l, (int)i0, (int)std::min<int64_t>(tile_nodes, n - i0)});
+            cut(tl, p, l, (int64_t)B->nx[p][l] * B->ny[p][l], (ti + B->m[p] - 1) / B->m[p]);
         }
     }
     st[B->dmax] = (int)tl.size();
     std::vector<BTile> ft;
     std::vector<int> fo(B->nprob + 1, 0);
-    for (int p = 0; p < B->nprob; ++p) {
-        fo[p] = (int)ft.size();
-        const int64_t n = B->nfine[p];
-        for (int64_t i0 = 0; i0 < n; i0 += tile_nodes)
-            ft.push_back({p, 0, (int)i0, (int)std::min<int64_t>(tile_nodes, n - i0)});
+    {
+        int64_t items = 0;
+        for (int p = 0; p < B->nprob; ++p) items += B->nfine[p] * B->m[p];
+        const int64_t ti = tile_items(items);
+        for (int p = 0; p < B->nprob; ++p) {
+            fo[p] = (int)ft.size();
+            cut(ft, p, 0, B->nfine[p], (ti + B->m[p] - 1) / B->m[p]);
+        }
     }
     fo[B->nprob] = (int)ft.size();
-    // block tiles (block-level sweeps): about tile_nodes nodes of whole blocks each
+    // block tiles (block-level sweeps: one item per block and right-hand side)
     std::vector<BTile> bt;
     std::vector<int> sb(B->dmax + 1, 0);
     if (B->bs > 1) {
-        const int tb = std::max(1, tile_nodes / (B->bs * B->bs));
+        auto nblk = [&](int p, int l) {
+            return (int64_t)((B->nx[p][l] + B->bs - 1) / B->bs) * ((B->ny[p][l] + B->bs - 1) / B->bs);
+        };
         for (int t = 0; t < B->dmax; ++t) {
             sb[t] = (int)bt.size();
+            int64_t items = 0;
+            for (int p = 0; p < B->nprob; ++p) {
+                const int l = t - B->slot0[p];
+                if (l >= 0) items += nblk(p, l) * B->m[p];
+            }
+            const int64_t ti = tile_items(items);
             for (int p = 0; p < B->nprob; ++p) {
                 const int l = t - B->slot0[p];
                 if (l < 0) continue;
-                const int64_t nb = (int64_t)((B->nx[p][l] + B->bs - 1) / B->bs) * ((B->ny[p][l] + B->bs - 1) / B->bs);
-                for (int64_t b0 = 0; b0 < nb; b0 += tb)
-                    bt.push_back({p, l, (int)b0, (int)std::min<int64_t>(tb, nb - b0)});
+                cut(bt, p, l, nblk(p, l), (ti + B->m[p] - 1) / B->m[p]);
             }
         }
         sb[B->dmax] = (int)bt.size();
     }
+    // a captured graph holds the old table pointers
+    if (B->graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+    }
     dfree(B->tiles, s); dfree(B->ftiles, s); dfree(B->slot_tile, s); dfree(B->ftile_of, s); dfree(B->part, s);
-    dfree(B->btiles, s); dfree(B->slot_btile, s);
+    dfree(B->btiles, s); dfree(B->slot_btile, s); dfree(B->part2, s); dfree(B->p2off, s);
     B->tiles = nullptr; B->ftiles = nullptr; B->slot_tile = nullptr; B->ftile_of = nullptr; B->part = nullptr;
-    B->btiles = nullptr; B->slot_btile = nullptr;
+    B->btiles = nullptr; B->slot_btile = nullptr; B->part2 = nullptr; B->p2off = nullptr;
+    if (B->method == CS_GMRES) {  // projection partials: (restart + 2) slots x m_p per finest tile
+        std::vector<int64_t> po(B->nprob + 1, 0);
+        for (int p = 0; p < B->nprob; ++p)
+            po[p + 1] = po[p] + (int64_t)(fo[p + 1] - fo[p]) * (B->restart + 2) * B->m[p];
+        CSX_TRY(dalloc_t(&B->p2off, po.size(), nullptr, s));
+        CSX_TRY(dalloc_t(&B->part2, (size_t)std::max<int64_t>(1, po[B->nprob]), nullptr, s));
+        CSX_CUDA(cudaMemcpyAsync(B->p2off, po.data(), po.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        CSX_CUDA(cudaStreamSynchronize(s));
+    }
     if (B->bs > 1) {
         CSX_TRY(dalloc_t(&B->btiles, bt.size(), nullptr, s));
         CSX_TRY(dalloc_t(&B->slot_btile, sb.size(), nullptr, s));
@@ -905,7 +1102,7 @@ cs_status build_tiles(cs_batch *B, int tile_nodes, cudaStream_t s) {
     CSX_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
     B->ntiles = (int)tl.size();
     B->nftiles = (int)ft.size();
-    B->tile_nodes = tile_nodes;
+    B->tiles_per_cta = tiles_per_cta;
     return CS_OK;
 }
 
@@ -945,6 +1142,13 @@ BArgs args_of(const cs_batch *B) {
     a.nmb = B->gnmb;
     a.jcols = B->jcols;
     a.frozen = B->frozen;
+    a.part2 = B->part2;
+    a.p2off = B->p2off;
+    a.qtot = B->qtot;
+    a.qlist = B->qlist;
+    a.hsum = B->hsum;
+    a.znorm2 = B->znorm2;
+    a.reorth = B->reorth;
     return a;
 }
 
@@ -997,10 +1201,6 @@ cs_status set_pointers(cs_batch *B, const double *const *b, double *const *x, cu
 // the kernel, captured once per configuration into a graph; if capturing a
 // cooperative launch is refused, it is launched directly
 cs_status run(cs_batch *B, cudaStream_t s) {
-    if (B->graph && (B->graph_cfg_threads != B->threads || B->graph_cfg_tile != B->tile_nodes)) {
-        cudaGraphExecDestroy(B->graph);
-        B->graph = nullptr;
-    }
     if (!B->graph && B->graph_ok) {
         cudaStream_t cs = nullptr;
         CSX_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -1021,9 +1221,6 @@ cs_status run(cs_batch *B, cudaStream_t s) {
             (void)cudaGetLastError();
             B->graph = nullptr;
             B->graph_ok = false;
-        } else {
-            B->graph_cfg_threads = B->threads;
-            B->graph_cfg_tile = B->tile_nodes;
         }
     }
     if (B->graph) {
@@ -1200,8 +1397,8 @@ cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *
         if ((rc = dalloc(&B->gm, (size_t)(B->restart + 2) * nfine_rhs * sizeof(double), &B->bytes, s)) != CS_OK)
             goto fail;
         const size_t nq = (size_t)nprob * BMAXRHS, R = (size_t)B->restart;
-        const size_t nd = nq * ((R + 1) * R + 3 * R + (R + 1) + 2);
-        if ((rc = dalloc(&B->gsm, nd * sizeof(double) + 2 * nq * sizeof(int), &B->bytes, s)) != CS_OK) goto fail;
+        const size_t nd = nq * ((R + 1) * R + 3 * R + (R + 1) + 2 + (R + 2) + 1);
+        if ((rc = dalloc(&B->gsm, nd * sizeof(double) + 3 * nq * sizeof(int), &B->bytes, s)) != CS_OK) goto fail;
         double *d = static_cast<double *>(B->gsm);
         B->H = d; d += nq * (R + 1) * R;
         B->gcs = d; d += nq * R;
@@ -1210,8 +1407,22 @@ cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *
         B->gg = d; d += nq * (R + 1);
         B->ginv = d; d += nq;
         B->gnmb = d; d += nq;
+        B->hsum = d; d += nq * (R + 2);
+        B->znorm2 = d; d += nq;
         B->jcols = reinterpret_cast<int *>(d);
         B->frozen = B->jcols + nq;
+        B->reorth = B->frozen + nq;
+        // every right-hand side of every problem, for the projection sums
+        std::vector<int> ql;
+        for (int p = 0; p < nprob; ++p)
+            for (int r = 0; r < B->m[p]; ++r) ql.push_back(p * BMAXRHS + r);
+        B->qtot = (int)ql.size();
+        if ((rc = dalloc_t(&B->qlist, ql.size(), &B->bytes, s)) != CS_OK) goto fail;
+        if (cudaMemcpyAsync(B->qlist, ql.data(), ql.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "batch create", __FILE__, __LINE__);
+            goto fail;
+        }
     }
     if (o->precision == CS_FP32)
         rc = fill_probs<float>(B, h, c, static_cast<float *>(B->vec), static_cast<double *>(B->gm));
@@ -1240,7 +1451,7 @@ cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *
     }
     {
         int threads = o->threads > 0 ? o->threads : 256;
-        int tile = o->tile_nodes > 0 ? o->tile_nodes : 1024;
+        int tile = o->tiles_per_cta > 0 ? o->tiles_per_cta : 2;
         if (o->autotune) {
             // time each candidate on the batch itself: two cycles from x = 0
             // with b = 1 (tol 0: exactly two iterations), best of three
@@ -1264,7 +1475,7 @@ cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *
                 off += B->nfine[p] * B->m[p];
             }
             const int cand_threads[] = {128, 256, 512};
-            const int cand_tile[] = {256, 1024, 4096};
+            const int cand_tile[] = {1, 2, 4};
             float best = 1e30f;
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
@@ -1360,11 +1571,11 @@ cs_status cs_batch_solve(cs_batch *B, const double *const *b, double *const *x, 
     return rc;
 }
 
-cs_status cs_batch_config(const cs_batch *B, int *threads, int *tile_nodes, int *ctas, cs_batch_tune *tuned,
+cs_status cs_batch_config(const cs_batch *B, int *threads, int *tiles_per_cta, int *ctas, cs_batch_tune *tuned,
                           int cap, int *ntuned) {
     if (!B) { set_error("null argument"); return CS_ERR_ARG; }
     if (threads) *threads = B->threads;
-    if (tile_nodes) *tile_nodes = B->tile_nodes;
+    if (tiles_per_cta) *tiles_per_cta = B->tiles_per_cta;
     if (ctas) *ctas = B->ctas;
     if (ntuned) *ntuned = (int)B->tuned.size();
     if (tuned)
@@ -1372,8 +1583,8 @@ cs_status cs_batch_config(const cs_batch *B, int *threads, int *tile_nodes, int 
     return CS_OK;
 }
 
-cs_status cs_batch_set_config(cs_batch *B, int threads, int tile_nodes, cs_stream stream) {
-    if (!B || threads < 32 || threads > 512 || (threads & 31) || tile_nodes < 1) {
+cs_status cs_batch_set_config(cs_batch *B, int threads, int tiles_per_cta, cs_stream stream) {
+    if (!B || threads < 32 || threads > 512 || (threads & 31) || tiles_per_cta < 1 || tiles_per_cta > 1024) {
         set_error("bad batch configuration");
         return CS_ERR_ARG;
     }
@@ -1382,7 +1593,7 @@ cs_status cs_batch_set_config(cs_batch *B, int threads, int tile_nodes, cs_strea
     CSX_TRY(coresident(B, threads, &ctas));
     B->threads = threads;
     B->ctas = ctas;
-    CSX_TRY(build_tiles(B, tile_nodes, s));
+    CSX_TRY(build_tiles(B, tiles_per_cta, s));
     return CS_OK;
 }
 
@@ -1395,7 +1606,7 @@ void cs_batch_destroy(cs_batch *B) {
     dfree(B->btiles); dfree(B->slot_btile);
     dfree(B->steps); dfree(B->part); dfree(B->nb); dfree(B->rel); dfree(B->rel0); dfree(B->state); dfree(B->iters);
     dfree(B->ctl); dfree(B->bptr); dfree(B->xptr); dfree(B->tune_b); dfree(B->tune_x); dfree(B->work);
-    dfree(B->gm); dfree(B->gsm);
+    dfree(B->gm); dfree(B->gsm); dfree(B->part2); dfree(B->p2off); dfree(B->qlist);
     if (B->hstage) cudaFreeHost(B->hstage);
     delete B;
 }

@@ -10,7 +10,8 @@ from tests.gpu_util import rel_max, stencil_matvec
 
 pytestmark = pytest.mark.gpu
 
-# ragged sides (several tiles and a partial one at tile_nodes 256) and every
+# ragged sides (several tiles per problem and partial ones: a tile holds about
+# one CTA of items at this batch size) and every
 # class of right-hand-side count
 SIDES = [17, 24, 33, 40, 47, 63]
 NRHS = [1, 2, 3, 5, 8, 4]
@@ -176,14 +177,14 @@ def test_gmres_converges_on_the_batched_workload():
 
 
 def test_results_do_not_depend_on_the_schedule():
-    """Tile size and CTA size change only how work is dealt out: x after a
-    fixed number of iterations is bitwise the same."""
+    """Tiles per CTA and CTA size change only how work is dealt out: x after
+    a fixed number of iterations is bitwise the same."""
     import paper_2606_12577_gb300 as cmg
     probs = _batch()
     hs, cs = _setup(probs)
     bt = cmg.Batch(hs, cs, NRHS, precision="fp32")
     outs = []
-    for threads, tile in ((128, 256), (512, 4096), (256, 1000)):
+    for threads, tile in ((128, 1), (512, 4), (256, 7), (64, 300)):
         bt.set_config(threads, tile)
         bs, xs = _vectors(probs)
         bt.solve(bs, xs, tol=1e-300, maxit=3, raise_on_error=False)
@@ -201,7 +202,7 @@ def test_autotuner_picks_the_fastest_measured_candidate():
     cfg = bt.config()
     assert len(cfg["tuned"]) >= 3
     best = min(cfg["tuned"], key=lambda t: t[2])
-    assert (cfg["threads"], cfg["tile_nodes"]) == (best[0], best[1])
+    assert (cfg["threads"], cfg["tiles_per_cta"]) == (best[0], best[1])
     assert cfg["ctas"] > 0
     bs, xs = _vectors(probs)
     assert all(i.converged for i in bt.solve(bs, xs, tol=1e-10))
