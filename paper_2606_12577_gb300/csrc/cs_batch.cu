@@ -218,12 +218,37 @@ __device__ __forceinline__ void cta_sum4_by_rhs(const double *v, int nv, int m, 
 // colour, which its stores never touch, so the order is free, and the SW
 // independent load groups keep SW times more requests in flight per thread.
 constexpr int SW = 4;
-template <typename T, int KIND>
-__device__ __forceinline__ void sweep_tile(int nx, int ny, int64_t N, const T *__restrict__ A,
-                                           const T *__restrict__ lam, const T *__restrict__ b, int m, int r, int i0,
-                                           int ni, int n0, int step, int colour, const T *src, T *dst) {
-    const bool copy = src != dst;
-    for (int nn = n0; nn < ni; nn += SW * step) {
+
+// Red-black colour c = (ix + iy) mod 2 of the nodes of an nx-wide grid,
+// enumerated in index order: colour_before counts the colour-c nodes with
+// index below i; colour_node gives the g-th one.  With nx odd the colour is
+// i mod 2; with nx even every row holds nx / 2 nodes of each colour, at the
+// x-parity (c + iy) mod 2.
+__device__ __forceinline__ int colour_before(int nx, int c, int i) {
+    if (nx & 1) return (i + 1 - c) >> 1;
+    const int iy = i / nx, ix = i - iy * nx;
+    return iy * (nx >> 1) + ((ix + 1 - ((c + iy) & 1)) >> 1);
+}
+__device__ __forceinline__ void colour_node(int nx, int c, int g, int &i, int &ix, int &iy) {
+    if (nx & 1) {
+        i = 2 * g + c;
+        iy = i / nx;
+        ix = i - iy * nx;
+    } else {
+        const int h = nx >> 1;
+        iy = g / h;
+        ix = 2 * (g - iy * h) + ((c + iy) & 1);
+        i = ix + iy * nx;
+    }
+}
+
+// x_i - lambda_i ((A x)_i - b_i) for cnt nodes: the nodes g0 .. g0 + cnt - 1
+// (COL false) or the colour-`colour` nodes of those ranks (COL true)
+template <typename T, int KIND, bool COL>
+__device__ __forceinline__ void relax_nodes(int nx, int ny, int64_t N, const T *__restrict__ A,
+                                            const T *__restrict__ lam, const T *__restrict__ b, int m, int r,
+                                            int g0, int cnt, int n0, int step, int colour, const T *src, T *dst) {
+    for (int nn = n0; nn < cnt; nn += SW * step) {
         T val[SW];
         int64_t ee[SW];
         bool wr[SW];
@@ -233,24 +258,52 @@ __device__ __forceinline__ void sweep_tile(int nx, int ny, int64_t N, const T *_
             wr[u] = false;
             ee[u] = 0;
             val[u] = T(0);
-            if (n < ni) {
-                const int i = i0 + n;
-                const int iy = i / nx, ix = i - iy * nx;
+            if (n < cnt) {
+                int i, ix, iy;
+                if (COL) {
+                    colour_node(nx, colour, g0 + n, i, ix, iy);
+                } else {
+                    i = g0 + n;
+                    iy = i / nx;
+                    ix = i - iy * nx;
+                }
                 const int64_t e = (int64_t)i * m + r;
                 ee[u] = e;
-                if (colour >= 0 && bcolour(ix, iy) != colour) {
-                    if (copy) { val[u] = src[e]; wr[u] = true; }
-                } else {
-                    const T ax = row_apply<KIND, T, T>(nx, ny, N, A, src, m, r, ix, iy, i);
-                    const T res = ax - b[e];
-                    val[u] = src[e] - lam[i] * res;
-                    wr[u] = true;
-                }
+                const T ax = row_apply<KIND, T, T>(nx, ny, N, A, src, m, r, ix, iy, i);
+                const T res = ax - b[e];
+                val[u] = src[e] - lam[i] * res;
+                wr[u] = true;
             }
         }
 #pragma unroll
         for (int u = 0; u < SW; ++u)
             if (wr[u]) dst[ee[u]] = val[u];
+    }
+}
+
+// One cascade step over the tile's nodes [i0, i0 + ni).  A colour step
+// (colour >= 0) deals out only the nodes of its colour, so no lane idles on
+// the other colour; out of place it then copies the other colour's nodes.
+template <typename T, int KIND>
+__device__ __forceinline__ void sweep_tile(int nx, int ny, int64_t N, const T *__restrict__ A,
+                                           const T *__restrict__ lam, const T *__restrict__ b, int m, int r, int i0,
+                                           int ni, int n0, int step, int colour, const T *src, T *dst) {
+    if (colour < 0) {
+        relax_nodes<T, KIND, false>(nx, ny, N, A, lam, b, m, r, i0, ni, n0, step, -1, src, dst);
+        return;
+    }
+    const int g0 = colour_before(nx, colour, i0);
+    relax_nodes<T, KIND, true>(nx, ny, N, A, lam, b, m, r, g0, colour_before(nx, colour, i0 + ni) - g0, n0, step,
+                               colour, src, dst);
+    if (src != dst) {
+        const int oc = colour ^ 1, h0 = colour_before(nx, oc, i0), hc = colour_before(nx, oc, i0 + ni) - h0;
+#pragma unroll 4
+        for (int nn = n0; nn < hc; nn += step) {
+            int i, ix, iy;
+            colour_node(nx, oc, h0 + nn, i, ix, iy);
+            const int64_t e = (int64_t)i * m + r;
+            dst[e] = src[e];
+        }
     }
 }
 
