@@ -309,7 +309,9 @@ typedef struct {
                         with M = V0 per right-hand side (classical Gram-Schmidt, projected a
                         second time when the first removes more than half of ||Z||^2 (DGKS);
                         Givens; inner steps stop on |g_{j+1}| <= tol ||M b||, restarts check
-                        the true residual) */
+                        the FP64 true residual).  The Krylov vectors have the cycle precision:
+                        with CS_FP32 a cycle also stops at |g_{j+1}| <= 1e-5 ||M r|| and the
+                        restart refines in FP64 (GMRES-based iterative refinement) */
     int restart;     /* GMRES restart length (default 30, at most 64) */
 } cs_batch_opts;
 typedef struct {

@@ -45,8 +45,8 @@ struct BProb {
     int nlev, m, slot0, cn;
     const double *A64;   // finest operator, FP64
     const double *cinv;  // coarsest dense inverse, FP64 row-major
-    double *Z;           // GMRES work vector [N0][m]
-    double *V;           // GMRES basis: restart + 1 vectors of [N0][m]
+    T *Z;                // GMRES work vector [N0][m] (the cycle precision)
+    T *V;                // GMRES basis: restart + 1 vectors of [N0][m]
     BLevel<T> lev[BMAXLEV];
 };
 
@@ -113,6 +113,8 @@ struct BArgs {
     double *hsum;        // [q][restart + 2]: this pass's <Z, V_i> (slot j + 1: <Z, Z>)
     double *znorm2;      // [q]: ||Z||^2 after the first projection
     int *reorth;         // [q]: the step projects a second time
+    double *beta;        // [q]: ||M r|| at the start of the GMRES cycle
+    double itol;         // inner stop |g_{j+1}| <= itol beta (FP32 Krylov vectors), 0: none
 };
 
 __device__ __forceinline__ int bcolour(int ix, int iy) { return ((ix + 1) + (iy + 1)) & 1; }
@@ -128,9 +130,10 @@ __device__ __forceinline__ void boff(int s, int &dx, int &dy) {
     }
 }
 
-// (A v)_{i,r} at node i = (ix, iy); neighbours outside contribute nothing
-template <int KIND, typename T, typename TA>
-__device__ __forceinline__ T row_apply(int nx, int ny, int64_t N, const TA *__restrict__ A, const T *v, int m, int r,
+// (A v)_{i,r} at node i = (ix, iy), computed in T; neighbours outside
+// contribute nothing
+template <int KIND, typename T, typename TA, typename TV = T>
+__device__ __forceinline__ T row_apply(int nx, int ny, int64_t N, const TA *__restrict__ A, const TV *v, int m, int r,
                                        int ix, int iy, int i) {
     constexpr int NST = KIND == STAR ? 5 : 9;
     T ax = T(0);
@@ -141,7 +144,7 @@ __device__ __forceinline__ T row_apply(int nx, int ny, int64_t N, const TA *__re
         const bool in = (unsigned)(ix + dx) < (unsigned)nx && (unsigned)(iy + dy) < (unsigned)ny;
         const T a = (T)A[(int64_t)s * N + i];
         const int j = i + dx + nx * dy;
-        ax = fma(a, in ? v[(int64_t)j * m + r] : T(0), ax);
+        ax = fma(a, in ? (T)v[(int64_t)j * m + r] : T(0), ax);
     }
     return ax;
 }
@@ -218,6 +221,10 @@ __device__ __forceinline__ void cta_sum4_by_rhs(const double *v, int nv, int m, 
 // colour, which its stores never touch, so the order is free, and the SW
 // independent load groups keep SW times more requests in flight per thread.
 constexpr int SW = 4;
+// Krylov dot products and norms: products are summed in the vector precision
+// over up to KCH items, and those partial sums in FP64 (on this part FP64
+// adds issue at 1/64 of the FP32 rate, so FP32 vectors keep them rare)
+constexpr int KCH = 8;
 
 // Red-black colour c = (ix + iy) mod 2 of the nodes of an nx-wide grid,
 // enumerated in index order: colour_before counts the colour-c nodes with
@@ -524,7 +531,7 @@ __device__ __forceinline__ bool fine_gate_all(int what) {
            what == F_XUPD;
 }
 __device__ __forceinline__ bool fine_reduces(int what) {
-    return what == F_BNORM || what == F_RESID || what == F_CONVZ || what == F_PAXPY;
+    return what == F_BNORM || what == F_RESID || what == F_CONVZ;
 }
 
 template <typename T>
@@ -544,19 +551,20 @@ __device__ void stage_fine(const BArgs &a, const BProb<T> *P, int what, int iarg
         const int i0 = tile.i0, ni = tile.ni, n0 = tm.n0, step = tm.step;
         const double *__restrict__ b = a.b64[p];
         double *__restrict__ x = a.x64[p];
-        double *__restrict__ Z = pr.Z;
-        const double *__restrict__ V = pr.V;
+        T *__restrict__ Z = pr.Z;
+        const T *__restrict__ V = pr.V;
         T *__restrict__ lb = L.b;
         T *__restrict__ lx = L.x;
         if (what == F_PROJ) {
             // projections of Z on V_0..V_j (pass 0 adds <Z, Z> as slot j + 1),
-            // four slots per sweep over the tile's items
+            // four slots per sweep over the tile's items; products summed in
+            // T over up to KCH items, those partial sums in FP64
             const int nsl = iarg == 0 ? jarg + 2 : jarg + 1;
             const bool on = tm.on && (iarg == 0 ? !a.frozen[q] : a.reorth[q] != 0);
             double *dst = a.part2 + a.p2off[p] + (int64_t)(k - a.ftile_of[p]) * (a.restart + 2) * m;
             for (int s0 = 0; s0 < nsl; s0 += 4) {
                 double pacc[4] = {0.0, 0.0, 0.0, 0.0};
-                const double *__restrict__ vs[4];
+                const T *__restrict__ vs[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int i = s0 + u;
@@ -564,15 +572,49 @@ __device__ void stage_fine(const BArgs &a, const BProb<T> *P, int what, int iarg
                 }
                 const int nv = min(4, nsl - s0);
                 if (on)
-                    for (int nn = n0; nn < ni; nn += step) {
-                        const int64_t e = (int64_t)(i0 + nn) * m + r;
-                        const double z = Z[e];
+                    for (int nn = n0; nn < ni;) {
+                        T c[4] = {T(0), T(0), T(0), T(0)};
+                        for (int t = 0; t < KCH && nn < ni; ++t, nn += step) {
+                            const int64_t e = (int64_t)(i0 + nn) * m + r;
+                            const T z = Z[e];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (u < nv) pacc[u] = fma(z, vs[u][e], pacc[u]);
+                            for (int u = 0; u < 4; ++u)
+                                if (u < nv) c[u] = fma(z, vs[u][e], c[u]);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) pacc[u] += (double)c[u];
                     }
                 cta_sum4_by_rhs(pacc, nv, m, red, dst + (int64_t)s0 * m, m);
             }
+            continue;
+        }
+        if (what == F_PAXPY) {
+            // Z -= sum_i h_i V_i in T (the coefficients staged in shared
+            // memory as T), ||Z||^2 as in F_PROJ; pass iarg: 0 -> every
+            // extending right-hand side, 1 -> those reprojected
+            T *hs = reinterpret_cast<T *>(red);  // [(j + 1) m] <= restart * BMAXRHS <= 2048 values
+            for (int t = threadIdx.x; t < (jarg + 1) * m; t += blockDim.x) {
+                const int i = t / m, rr = t - i * m;
+                hs[t] = (T)a.hsum[(int64_t)(p * BMAXRHS + rr) * (a.restart + 2) + i];
+            }
+            __syncthreads();
+            double acc = 0.0;
+            if (tm.on && (iarg == 0 ? !a.frozen[q] : a.reorth[q] != 0)) {
+                for (int nn = n0; nn < ni;) {
+                    T c = T(0);
+                    for (int t = 0; t < KCH && nn < ni; ++t, nn += step) {
+                        const int64_t e = (int64_t)(i0 + nn) * m + r;
+                        T z = Z[e];
+#pragma unroll 4
+                        for (int i = 0; i <= jarg; ++i) z = fma(-hs[i * m + r], V[(int64_t)i * nm + e], z);
+                        Z[e] = z;
+                        c = fma(z, z, c);
+                    }
+                    acc += (double)c;
+                }
+            }
+            __syncthreads();  // hs aliases the reduction buffer
+            cta_sum_by_rhs(acc, m, red, a.part + (int64_t)k * BMAXRHS);
             continue;
         }
         double acc = 0.0;
@@ -585,20 +627,34 @@ __device__ void stage_fine(const BArgs &a, const BProb<T> *P, int what, int iarg
             } else if (what == F_ZEROX) {
                 if (a.nb[q] == 0.0)
                     for (int nn = n0; nn < ni; nn += step) x[(int64_t)(i0 + nn) * m + r] = 0.0;
-            } else if (what == F_RESID || what == F_MATVEC) {
-                const bool res = what == F_RESID;
-                const double *__restrict__ xv = res ? x : V + (int64_t)jarg * nm;
+            } else if (what == F_RESID) {
+                // the true residual: FP64 operator and arithmetic
                 const double *__restrict__ A64 = pr.A64;
                 const bool star = L.kind == STAR;
                 for (int nn = n0; nn < ni; nn += step) {
                     const int i = i0 + nn;
                     const int iy = i / nx, ix = i - iy * nx;
-                    const double ax = star ? row_apply<STAR, double, double>(nx, ny, N, A64, xv, m, r, ix, iy, i)
-                                           : row_apply<BOX, double, double>(nx, ny, N, A64, xv, m, r, ix, iy, i);
+                    const double ax = star ? row_apply<STAR, double, double>(nx, ny, N, A64, x, m, r, ix, iy, i)
+                                           : row_apply<BOX, double, double>(nx, ny, N, A64, x, m, r, ix, iy, i);
                     const int64_t e = (int64_t)i * m + r;
-                    const double v = res ? b[e] - ax : ax;
+                    const double v = b[e] - ax;
                     acc = fma(v, v, acc);
                     lb[e] = (T)v;
+                    lx[e] = T(0);
+                }
+            } else if (what == F_MATVEC) {
+                // the Krylov product A V_j in the cycle precision (the
+                // operator the cycles use); the restarts' FP64 residual
+                // corrects its rounding
+                const T *__restrict__ vj = V + (int64_t)jarg * nm;
+                const bool star = L.kind == STAR;
+                for (int nn = n0; nn < ni; nn += step) {
+                    const int i = i0 + nn;
+                    const int iy = i / nx, ix = i - iy * nx;
+                    const T ax = star ? row_apply<STAR, T, T>(nx, ny, N, L.A, vj, m, r, ix, iy, i)
+                                      : row_apply<BOX, T, T>(nx, ny, N, L.A, vj, m, r, ix, iy, i);
+                    const int64_t e = (int64_t)i * m + r;
+                    lb[e] = ax;
                     lx[e] = T(0);
                 }
             } else if (what == F_UPDATE) {
@@ -613,42 +669,33 @@ __device__ void stage_fine(const BArgs &a, const BProb<T> *P, int what, int iarg
                     lx[e] = T(0);
                 }
             } else if (what == F_CONVZ) {
-                for (int nn = n0; nn < ni; nn += step) {
-                    const int64_t e = (int64_t)(i0 + nn) * m + r;
-                    const double z = (double)lx[e];
-                    Z[e] = z;
-                    acc = fma(z, z, acc);
-                }
-            } else if (what == F_PAXPY) {
-                // pass iarg: 0 -> every extending right-hand side, 1 -> those reprojected
-                if (iarg == 0 ? !a.frozen[q] : a.reorth[q] != 0) {
-                    const double *__restrict__ hq = a.hsum + (int64_t)q * (a.restart + 2);
-                    for (int nn = n0; nn < ni; nn += step) {
+                for (int nn = n0; nn < ni;) {
+                    T c = T(0);
+                    for (int t = 0; t < KCH && nn < ni; ++t, nn += step) {
                         const int64_t e = (int64_t)(i0 + nn) * m + r;
-                        double z = Z[e];
-#pragma unroll 4
-                        for (int i = 0; i <= jarg; ++i) z = fma(-hq[i], V[(int64_t)i * nm + e], z);
+                        const T z = lx[e];
                         Z[e] = z;
-                        acc = fma(z, z, acc);
+                        c = fma(z, z, c);
                     }
+                    acc += (double)c;
                 }
             } else if (what == F_SCALEV) {
                 if (!a.frozen[q] || jarg == 0) {
-                    double *__restrict__ Vj = pr.V + (int64_t)jarg * nm;
-                    const double inv = a.inv[q];
+                    T *__restrict__ Vj = pr.V + (int64_t)jarg * nm;
+                    const T inv = (T)a.inv[q];
                     for (int nn = n0; nn < ni; nn += step) {
                         const int64_t e = (int64_t)(i0 + nn) * m + r;
                         Vj[e] = Z[e] * inv;
                     }
                 }
-            } else {  // F_XUPD
+            } else {  // F_XUPD: x += V y, the combination formed in T
                 const int nc = a.jcols[q];
                 const double *__restrict__ y = a.y + (int64_t)q * a.restart;
                 for (int nn = n0; nn < ni; nn += step) {
                     const int64_t e = (int64_t)(i0 + nn) * m + r;
-                    double sx = x[e];
-                    for (int kk = 0; kk < nc; ++kk) sx = fma(y[kk], V[(int64_t)kk * nm + e], sx);
-                    x[e] = sx;
+                    T d = T(0);
+                    for (int kk = 0; kk < nc; ++kk) d = fma((T)y[kk], V[(int64_t)kk * nm + e], d);
+                    x[e] += (double)d;
                 }
             }
         }
@@ -730,6 +777,7 @@ __device__ void stage_prob(const BArgs &a, const BProb<T> *P, int what, int iarg
                 const double ss = tsum(r);
                 const double beta = sqrt(ss);
                 a.g[(int64_t)q * (R + 1)] = beta;
+                a.beta[q] = beta;
                 a.inv[q] = beta > 0.0 ? 1.0 / sqrt(ss) : 0.0;
                 a.jcols[q] = 0;
                 a.frozen[q] = !(beta > 0.0) || a.iters[p] >= a.ctl->maxit;
@@ -781,7 +829,9 @@ __device__ void stage_prob(const BArgs &a, const BProb<T> *P, int what, int iarg
                 g[j + 1] = -sn[j] * g[j];
                 g[j] = cs[j] * g[j];
                 a.jcols[q] = j + 1;
-                if (fabs(g[j + 1]) <= a.ctl->tol * a.nmb[q] || hn == 0.0 || limit || j + 1 >= R) a.frozen[q] = 1;
+                if (fabs(g[j + 1]) <= a.ctl->tol * a.nmb[q] || fabs(g[j + 1]) <= a.itol * a.beta[q] || hn == 0.0 ||
+                    limit || j + 1 >= R)
+                    a.frozen[q] = 1;
                 else ++ext;
             }
             a.work[p] = ext > 0;
@@ -1025,7 +1075,7 @@ struct cs_batch {
     double *H = nullptr, *gcs = nullptr, *gsn = nullptr, *gy = nullptr, *gg = nullptr, *ginv = nullptr,
            *gnmb = nullptr;
     int *jcols = nullptr, *frozen = nullptr;
-    double *part2 = nullptr, *hsum = nullptr, *znorm2 = nullptr;
+    double *part2 = nullptr, *hsum = nullptr, *znorm2 = nullptr, *gbeta = nullptr;
     int64_t *p2off = nullptr;
     int *qlist = nullptr, *reorth = nullptr;
     int qtot = 0;
@@ -1202,6 +1252,10 @@ BArgs args_of(const cs_batch *B) {
     a.hsum = B->hsum;
     a.znorm2 = B->znorm2;
     a.reorth = B->reorth;
+    a.beta = B->gbeta;
+    // FP32 Krylov vectors resolve about 1e-6 of ||M r||: a GMRES cycle stops
+    // at 1e-5 and the restart's FP64 residual refines (GMRES-IR)
+    a.itol = B->precision == CS_FP32 ? 1e-5 : 0.0;
     return a;
 }
 
@@ -1324,7 +1378,7 @@ void build_steps(const cs_batch *B, std::vector<BStep> &out) {
 }
 
 template <typename T>
-cs_status fill_probs(cs_batch *B, cs_hierarchy *const *h, cs_cascade *const *c, T *vec, double *gm) {
+cs_status fill_probs(cs_batch *B, cs_hierarchy *const *h, cs_cascade *const *c, T *vec, T *gm) {
     B->probs_bytes = sizeof(BProb<T>) * B->nprob;
     B->hprobs.assign(B->probs_bytes, 0);
     BProb<T> *hp = reinterpret_cast<BProb<T> *>(B->hprobs.data());
@@ -1446,11 +1500,11 @@ cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *
     for (int p = 0; p < nprob; ++p) nfine_rhs += B->nfine[p] * B->m[p];
     if ((rc = dalloc(&B->vec, (size_t)nvec * esz, &B->bytes, s)) != CS_OK) goto fail;
     if (B->method == CS_GMRES) {
-        // basis (restart + 1 vectors) and Z per problem, FP64, [N0][m] each
-        if ((rc = dalloc(&B->gm, (size_t)(B->restart + 2) * nfine_rhs * sizeof(double), &B->bytes, s)) != CS_OK)
+        // basis (restart + 1 vectors) and Z per problem, in the cycle precision, [N0][m] each
+        if ((rc = dalloc(&B->gm, (size_t)(B->restart + 2) * nfine_rhs * esz, &B->bytes, s)) != CS_OK)
             goto fail;
         const size_t nq = (size_t)nprob * BMAXRHS, R = (size_t)B->restart;
-        const size_t nd = nq * ((R + 1) * R + 3 * R + (R + 1) + 2 + (R + 2) + 1);
+        const size_t nd = nq * ((R + 1) * R + 3 * R + (R + 1) + 2 + (R + 2) + 2);
         if ((rc = dalloc(&B->gsm, nd * sizeof(double) + 3 * nq * sizeof(int), &B->bytes, s)) != CS_OK) goto fail;
         double *d = static_cast<double *>(B->gsm);
         B->H = d; d += nq * (R + 1) * R;
@@ -1462,6 +1516,7 @@ cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *
         B->gnmb = d; d += nq;
         B->hsum = d; d += nq * (R + 2);
         B->znorm2 = d; d += nq;
+        B->gbeta = d; d += nq;
         B->jcols = reinterpret_cast<int *>(d);
         B->frozen = B->jcols + nq;
         B->reorth = B->frozen + nq;
@@ -1478,7 +1533,7 @@ cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *
         }
     }
     if (o->precision == CS_FP32)
-        rc = fill_probs<float>(B, h, c, static_cast<float *>(B->vec), static_cast<double *>(B->gm));
+        rc = fill_probs<float>(B, h, c, static_cast<float *>(B->vec), static_cast<float *>(B->gm));
     else rc = fill_probs<double>(B, h, c, static_cast<double *>(B->vec), static_cast<double *>(B->gm));
     if (rc != CS_OK) goto fail;
     if ((rc = dalloc(&B->probs, B->probs_bytes, &B->bytes, s)) != CS_OK) goto fail;
