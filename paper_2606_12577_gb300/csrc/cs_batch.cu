@@ -643,18 +643,21 @@ __device__ void stage_fine(const BArgs &a, const BProb<T> *P, int what, int iarg
                     lx[e] = T(0);
                 }
             } else if (what == F_MATVEC) {
-                // the Krylov product A V_j in the cycle precision (the
-                // operator the cycles use); the restarts' FP64 residual
-                // corrects its rounding
+                // the Krylov product A V_j: the FP64 operator applied in FP64
+                // to the basis vector's (exact) values.  The cycles' rounded
+                // operator would perturb it by about u |A| |V_j|, which the
+                // preconditioner amplifies by the operator's (Skeel)
+                // condition number: too much for high-contrast coefficients.
                 const T *__restrict__ vj = V + (int64_t)jarg * nm;
+                const double *__restrict__ A64 = pr.A64;
                 const bool star = L.kind == STAR;
                 for (int nn = n0; nn < ni; nn += step) {
                     const int i = i0 + nn;
                     const int iy = i / nx, ix = i - iy * nx;
-                    const T ax = star ? row_apply<STAR, T, T>(nx, ny, N, L.A, vj, m, r, ix, iy, i)
-                                      : row_apply<BOX, T, T>(nx, ny, N, L.A, vj, m, r, ix, iy, i);
+                    const double ax = star ? row_apply<STAR, double, double, T>(nx, ny, N, A64, vj, m, r, ix, iy, i)
+                                           : row_apply<BOX, double, double, T>(nx, ny, N, A64, vj, m, r, ix, iy, i);
                     const int64_t e = (int64_t)i * m + r;
-                    lb[e] = ax;
+                    lb[e] = (T)ax;
                     lx[e] = T(0);
                 }
             } else if (what == F_UPDATE) {
@@ -688,14 +691,14 @@ __device__ void stage_fine(const BArgs &a, const BProb<T> *P, int what, int iarg
                         Vj[e] = Z[e] * inv;
                     }
                 }
-            } else {  // F_XUPD: x += V y, the combination formed in T
+            } else {  // F_XUPD: x += V y in FP64 (y can combine the basis with heavy cancellation)
                 const int nc = a.jcols[q];
                 const double *__restrict__ y = a.y + (int64_t)q * a.restart;
                 for (int nn = n0; nn < ni; nn += step) {
                     const int64_t e = (int64_t)(i0 + nn) * m + r;
-                    T d = T(0);
-                    for (int kk = 0; kk < nc; ++kk) d = fma((T)y[kk], V[(int64_t)kk * nm + e], d);
-                    x[e] += (double)d;
+                    double sx = x[e];
+                    for (int kk = 0; kk < nc; ++kk) sx = fma(y[kk], (double)V[(int64_t)kk * nm + e], sx);
+                    x[e] = sx;
                 }
             }
         }
