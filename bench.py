@@ -431,7 +431,7 @@ def main():
     if a.profile == "batch":  # one batched GMRES solve of the first problems of the batched workload, 3 steps
         P = [problems.batch_problem(k) for k in range(a.batch_profile_count)]
         hs, cs = cmg.setup_many([A for A, _, _ in P], kind="multiplicative", nu=3, lowp=True)
-        bt = cmg.Batch(hs, cs, [m for _, m, _ in P], precision="fp32", method="gmres", threads=512, tiles_per_cta=2)
+        bt = cmg.Batch(hs, cs, [m for _, m, _ in P], precision="fp32", method="gmres", threads=256, tiles_per_cta=4)
         bs = [torch.tensor(b, device=dev) for _, _, b in P]
         xs = [torch.zeros_like(b) for b in bs]
         bt.solve(bs, xs, tol=1e-300, maxit=3, raise_on_error=False)
