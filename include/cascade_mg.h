@@ -124,6 +124,12 @@ typedef struct {
                       block (default 0.05); rejected and partial edge blocks take the exact
                       level-1 block at every cascade step; if no block is kept the exact
                       setup of the level runs (fallback) */
+    int setup_precision; /* CS_FP64 (default): the Frobenius-norm setup of Algorithm 2 in FP64;
+                      CS_FP32: the residual rows R = A E and the propagator rows E in FP32,
+                      their inner products summed in FP64 over chunks of 8 terms and each
+                      row's lambda = <E_i, R_i> / <R_i, R_i> divided in FP64 (Lambda agrees
+                      with the FP64 setup to about 1e-5 relative; meant for FP32 cycles).
+                      Point blocks without alpha or model, else CS_ERR_UNSUPPORTED */
 } cs_cascade_opts;
 
 /* Build the cascade (Lambda_l, l = 1..nu; multiplicative: Lambda_{l,k},

@@ -151,14 +151,16 @@ def setup_hierarchy(dim, n, offsets, coeff, periodic=False, coarse_max=4, max_le
 
 
 def setup_cascade(h: Hierarchy, kind="additive", nu=3, prescale=True, alpha=0, lowp=False, reuse=True, model=None,
-                  model_tol=0.05, stream=None):
+                  model_tol=0.05, setup_precision="fp64", stream=None):
     """Build the cascade; ``lowp``: False, True (FP32 copies for FP32
     cycles) or 2 (FP32 and BF16 copies); ``model`` (an ``MLP``) predicts the
     finest level's Lambda blocks, kept per block when its level-1 Frobenius
-    objective is within ``model_tol`` of the exact one."""
+    objective is within ``model_tol`` of the exact one; ``setup_precision``
+    "fp32" forms the setup's residual and propagator rows in FP32."""
     k = _capi.CS_MULTIPLICATIVE if kind == "multiplicative" else _capi.CS_ADDITIVE
     opts = _capi.cs_cascade_opts(k, nu, int(prescale), alpha, int(lowp), int(not reuse),
-                                 C.c_void_p(model.ptr if model is not None else None), float(model_tol))
+                                 C.c_void_p(model.ptr if model is not None else None), float(model_tol),
+                                 _capi.CS_FP32 if setup_precision == "fp32" else _capi.CS_FP64)
     out = C.c_void_p()
     _capi.check(_capi.lib().cs_setup_cascade(h.ptr, C.byref(opts), _stream(stream), C.byref(out)),
                 "cs_setup_cascade")
@@ -457,7 +459,7 @@ def setup_many(problems, kind="multiplicative", nu=3, lowp=True, coarse_max=4, b
         keep.append(kp)
     ho = _capi.cs_hierarchy_opts(coarse_max, 0, block, int(not reuse))
     k = _capi.CS_MULTIPLICATIVE if kind == "multiplicative" else _capi.CS_ADDITIVE
-    co = _capi.cs_cascade_opts(k, nu, 1, 0, int(lowp), int(not reuse), C.c_void_p(None), 0.05)
+    co = _capi.cs_cascade_opts(k, nu, 1, 0, int(lowp), int(not reuse), C.c_void_p(None), 0.05, _capi.CS_FP64)
     hp = (C.c_void_p * n)()
     cp = (C.c_void_p * n)()
     _capi.check(_capi.lib().cs_setup_many(n, arr, C.byref(ho), C.byref(co), int(nthreads), _stream(stream), hp, cp),

@@ -457,6 +457,20 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
     c->nlev = h->nlev > 1 ? h->nlev - 1 : 1;
     c->lowp = o->lowp != 0;
     if (o->lowp < 0 || o->lowp > 2) { set_error("lowp must be 0, 1 or 2"); delete c; return CS_ERR_ARG; }
+    if (o->setup_precision != CS_FP64 && o->setup_precision != CS_FP32) {
+        set_error("setup_precision must be CS_FP64 or CS_FP32");
+        delete c;
+        return CS_ERR_ARG;
+    }
+    if (o->setup_precision == CS_FP32) {
+        bool blocks = false;
+        for (int l = 0; l < h->nlev; ++l) blocks = blocks || h->lev[l].bs > 1;
+        if (blocks || o->model || o->alpha > 0) {
+            set_error("the FP32 setup is implemented for point blocks without truncation or a model");
+            delete c;
+            return CS_ERR_UNSUPPORTED;
+        }
+    }
     if (o->lowp == 2)
         for (int l = 0; l < h->nlev; ++l)
             if (h->lev[l].bs > 1) {
@@ -476,7 +490,8 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
             const Level &L = h->lev[l];
             if (L.bs > 1) return cascade_setup_level_blocks(h, l, c->kind, c->nu, o->prescale, c->lam[l], st);
             int64_t peak = 0;
-            return cascade_setup_level(h, l, c->kind, c->nu, o->prescale, !o->no_reuse, o->alpha, c->lam[l], st, &peak);
+            return cascade_setup_level(h, l, c->kind, c->nu, o->prescale, !o->no_reuse, o->alpha,
+                                       o->setup_precision == CS_FP32, c->lam[l], st, &peak);
         };
         auto finest = [&]() -> cs_status {
             const Level &L = h->lev[0];

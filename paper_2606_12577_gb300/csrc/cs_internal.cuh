@@ -200,8 +200,10 @@ cs_status level_margin(Level &L, bool periodic, cudaStream_t s);
 // zeroes the coefficients of couplings to nodes outside a Dirichlet grid
 cs_status drop_outside_couplings(const Level &L, cudaStream_t s);
 cs_status coarse_factor(cs_hierarchy *h, cudaStream_t s);
+// fp32: form the residual rows R and the error propagator E in FP32 (the
+// row products summed in FP64 over chunks of 8); lambda is stored in FP64
 cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, int alpha,
-                              double *lam, cudaStream_t s, int64_t *peak_bytes);
+                              bool fp32, double *lam, cudaStream_t s, int64_t *peak_bytes);
 cs_status cascade_setup_level_blocks(const cs_hierarchy *h, int l, int kind, int nu, int prescale, double *lam,
                                      cudaStream_t s);
 cs_status learned_setup_level0(const cs_hierarchy *h, cs_cascade *c, cs_mlp *M, double tol, double *lam,

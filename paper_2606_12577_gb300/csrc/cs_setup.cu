@@ -153,25 +153,31 @@ __global__ void k_const_margin(Grid g, int nst, const double *__restrict__ A, in
 // multiplies a zero boundary value, so its coefficient is dropped once, on
 // the copy of the fine operator; the Galerkin product and the margin scan
 // then see only couplings inside the grid.
-struct StencilOff {
-    signed char d[27][3];
-};
-__global__ void k_drop_outside(Grid g, int nst, StencilOff so, double *__restrict__ A) {
+template <int DIM, int KIND>
+__global__ void k_drop_outside(Grid g, double *__restrict__ A) {
+    using S = StenS<DIM, KIND>;
     const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
     if (ix >= g.nx || iy >= g.ny) return;
     const int64_t i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
-    for (int s = 0; s < nst; ++s) {
-        const int jx = ix + so.d[s][0], jy = iy + so.d[s][1], jz = iz + so.d[s][2];
-        const bool in = jx >= 0 && jx < g.nx && jy >= 0 && jy < g.ny && jz >= 0 && jz < g.nz;
+#pragma unroll
+    for (int s = 0; s < S::NST; ++s) {
+        int dx, dy, dz;
+        S::off(s, dx, dy, dz);
+        const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+        const bool in = jx >= 0 && jx < g.nx && jy >= 0 && jy < g.ny && (DIM == 2 || (jz >= 0 && jz < g.nz));
         if (!in) A[(int64_t)s * g.N + i] = 0.0;
     }
 }
 
 cs_status drop_outside_couplings(const Level &L, cudaStream_t s) {
-    StencilOff so{};
-    for (int t = 0; t < L.nst; ++t)
-        for (int d = 0; d < 3; ++d) so.d[t][d] = (signed char)L.off[t][d];
-    k_drop_outside<<<node_grid(L.g), node_block(), 0, s>>>(L.g, L.nst, so, L.A);
+    const dim3 gr = node_grid(L.g), bl = node_block();
+    if (L.g.dim == 2) {
+        if (L.kind == STAR) k_drop_outside<2, STAR><<<gr, bl, 0, s>>>(L.g, L.A);
+        else k_drop_outside<2, BOX><<<gr, bl, 0, s>>>(L.g, L.A);
+    } else {
+        if (L.kind == STAR) k_drop_outside<3, STAR><<<gr, bl, 0, s>>>(L.g, L.A);
+        else k_drop_outside<3, BOX><<<gr, bl, 0, s>>>(L.g, L.A);
+    }
     count_launch();
     CSX_CUDA(cudaGetLastError());
     return CS_OK;
@@ -503,9 +509,9 @@ __global__ void k_prescale(Grid g, int periodic, int prescale, const double *__r
     (void)At;
 }
 
-template <int DIM, int KIND>
+template <int DIM, int KIND, typename W = double>
 __global__ void k_scale_op(Grid g, int periodic, const double *__restrict__ A, const double *__restrict__ w,
-                           double *__restrict__ At) {
+                           W *__restrict__ At) {
     using S = StenS<DIM, KIND>;
     int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
     if (ix >= g.nx || iy >= g.ny) return;
@@ -525,11 +531,12 @@ __global__ void k_scale_op(Grid g, int periodic, const double *__restrict__ A, c
         }
         double v = 0.0;
         if (in) v = wi * A[(int64_t)s * g.N + i] * w[jx + (int64_t)g.nx * (jy + (int64_t)g.ny * jz)];
-        At[(int64_t)s * g.N + i] = v;
+        At[(int64_t)s * g.N + i] = (W)v;
     }
 }
 
-__global__ void k_fill(int64_t n, double *p, double v) {
+template <typename W>
+__global__ void k_fill(int64_t n, W *p, W v) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
 
@@ -555,10 +562,10 @@ struct Reuse {
 // update); otherwise partial <E_i,R_i>, <R_i,R_i> go to part[q*N + i] and
 // k_setup_finish completes the row.  LAST: the final step of the cascade,
 // where E_nu is not needed -- R is neither stored nor used to update E.
-template <int DIM, int KIND, bool LAST>
-__global__ void __launch_bounds__(TBX *TBY) k_setup_rows(Grid g, int periodic, const double *__restrict__ At,
-                                                          const double *__restrict__ w, const double *__restrict__ Ecur,
-                                                          double *__restrict__ Enxt, int nnxt, int chunk, int nchunks,
+template <int DIM, int KIND, bool LAST, typename W = double>
+__global__ void __launch_bounds__(TBX *TBY) k_setup_rows(Grid g, int periodic, const W *__restrict__ At,
+                                                          const double *__restrict__ w, const W *__restrict__ Ecur,
+                                                          W *__restrict__ Enxt, int nnxt, int chunk, int nchunks,
                                                           const int *__restrict__ pstart,
                                                           const unsigned *__restrict__ pairs,
                                                           const int *__restrict__ cur_of, int colour,
@@ -568,8 +575,8 @@ __global__ void __launch_bounds__(TBX *TBY) k_setup_rows(Grid g, int periodic, c
     constexpr int NST = S::NST;
     constexpr int NT = TBX * TBY;
     extern __shared__ double sm_setup[];
-    double *sa = sm_setup;                                   // [NST][NT]
-    int *snb = reinterpret_cast<int *>(sm_setup + NST * NT);  // [NST][NT]
+    W *sa = reinterpret_cast<W *>(sm_setup);                 // [NST][NT]
+    int *snb = reinterpret_cast<int *>(sa + NST * NT);       // [NST][NT]
     const int tid = threadIdx.x + TBX * threadIdx.y;
     int ix, iy, iz, q;
     if (rs.on) {  // shell rows and representatives only, packed densely
@@ -593,7 +600,7 @@ __global__ void __launch_bounds__(TBX *TBY) k_setup_rows(Grid g, int periodic, c
         if (!LAST)
             for (int o = o0; o < o1; ++o) {
                 int c = __ldg(cur_of + o);
-                Enxt[(int64_t)o * N + i] = c >= 0 ? Ecur[(int64_t)c * N + iread] : 0.0;
+                Enxt[(int64_t)o * N + i] = c >= 0 ? Ecur[(int64_t)c * N + iread] : W(0);
             }
         return;
     }
@@ -613,22 +620,41 @@ __global__ void __launch_bounds__(TBX *TBY) k_setup_rows(Grid g, int periodic, c
         if (in && ru.on && (periodic || bdist(g, jx, jy, jz) >= ru.d_prev))
             j = rb_colour(g, jx, jy, jz) ? ru.rep1 : ru.rep0;
         snb[s * NT + tid] = j;
-        sa[s * NT + tid] = in ? At[(int64_t)s * N + i] : 0.0;
+        sa[s * NT + tid] = in ? At[(int64_t)s * N + i] : W(0);
     }
+    // <E_i, R_i> and <R_i, R_i>: in FP64, or (W = float) in FP32 over
+    // chunks of 8 offsets whose sums are added in FP64
+    constexpr bool CH = sizeof(W) < sizeof(double);
     double num = 0.0, den = 0.0;
+    W cnum = W(0), cden = W(0);
     int p = __ldg(pstart + o0);
     for (int o = o0; o < o1; ++o) {
         const int pe = __ldg(pstart + o + 1);
-        double r = 0.0;
+        W r = W(0);
         for (; p < pe; ++p) {
             const unsigned u = __ldg(pairs + p);
             const int s = (int)(u >> 24), c = (int)(u & 0xffffffu);
             r = fma(sa[s * NT + tid], Ecur[(int64_t)c * N + snb[s * NT + tid]], r);
         }
         const int c0 = __ldg(cur_of + o);
-        if (c0 >= 0) num = fma(Ecur[(int64_t)c0 * N + iread], r, num);
-        den = fma(r, r, den);
+        if (CH) {
+            if (c0 >= 0) cnum = fma(Ecur[(int64_t)c0 * N + iread], r, cnum);
+            cden = fma(r, r, cden);
+            if (((o - o0) & 7) == 7) {
+                num += (double)cnum;
+                den += (double)cden;
+                cnum = W(0);
+                cden = W(0);
+            }
+        } else {
+            if (c0 >= 0) num = fma((double)Ecur[(int64_t)c0 * N + iread], (double)r, num);
+            den = fma((double)r, (double)r, den);
+        }
         if (!LAST) Enxt[(int64_t)o * N + i] = r;
+    }
+    if (CH) {
+        num += (double)cnum;
+        den += (double)cden;
     }
     if (nchunks > 1) {
         part[(int64_t)q * N + i] = make_double2(num, den);
@@ -637,12 +663,14 @@ __global__ void __launch_bounds__(TBX *TBY) k_setup_rows(Grid g, int periodic, c
     // normal equations of the 1 x 1 least-squares problem; a zero row R_i
     // (pivot <= 1e-14 tr(G) = 0) gives the minimum-norm solution 0
     const double lt = den > 0.0 ? num / den : 0.0;
-    if (!LAST)
+    if (!LAST) {
+        const W ltw = (W)lt;
         for (int o = o0; o < o1; ++o) {
             const int c0 = __ldg(cur_of + o);
-            const double e = c0 >= 0 ? Ecur[(int64_t)c0 * N + iread] : 0.0;
-            Enxt[(int64_t)o * N + i] = e - lt * Enxt[(int64_t)o * N + i];
+            const W e = c0 >= 0 ? Ecur[(int64_t)c0 * N + iread] : W(0);
+            Enxt[(int64_t)o * N + i] = e - ltw * Enxt[(int64_t)o * N + i];
         }
+    }
     const double wi = w[i];
     lam[i] = wi * lt * wi;
 }
@@ -650,9 +678,9 @@ __global__ void __launch_bounds__(TBX *TBY) k_setup_rows(Grid g, int periodic, c
 // Completes rows processed in several chunks: sums the partial inner
 // products in chunk order, forms lambda and (unless LAST) updates this
 // chunk's entries of E.
-template <int DIM, bool LAST>
+template <int DIM, bool LAST, typename W = double>
 __global__ void __launch_bounds__(TBX *TBY) k_setup_finish(Grid g, const double *__restrict__ w,
-                                                            const double *__restrict__ Ecur, double *__restrict__ Enxt,
+                                                            const W *__restrict__ Ecur, W *__restrict__ Enxt,
                                                             int nnxt, int chunk, int nchunks,
                                                             const int *__restrict__ cur_of, int colour,
                                                             double *__restrict__ lam, const double2 *__restrict__ part,
@@ -685,18 +713,19 @@ __global__ void __launch_bounds__(TBX *TBY) k_setup_finish(Grid g, const double 
     const double lt = den > 0.0 ? num / den : 0.0;
     if (q == 0) lam[i] = w[i] * lt * w[i];
     if (LAST) return;
+    const W ltw = (W)lt;
     const int o0 = q * chunk, o1 = min(nnxt, o0 + chunk);
     for (int o = o0; o < o1; ++o) {
         const int c0 = __ldg(cur_of + o);
-        const double e = c0 >= 0 ? Ecur[(int64_t)c0 * N + iread] : 0.0;
-        Enxt[(int64_t)o * N + i] = e - lt * Enxt[(int64_t)o * N + i];
+        const W e = c0 >= 0 ? Ecur[(int64_t)c0 * N + iread] : W(0);
+        Enxt[(int64_t)o * N + i] = e - ltw * Enxt[(int64_t)o * N + i];
     }
 }
 
 
-template <int DIM, int KIND, bool LAST>
-static cs_status launch_setup_rows(const Grid &g, int periodic, const double *At, const double *w,
-                                   const double *Ecur, double *Enxt, int nn, int chunk, int nchunks,
+template <int DIM, int KIND, bool LAST, typename W>
+static cs_status launch_setup_rows(const Grid &g, int periodic, const W *At, const double *w,
+                                   const W *Ecur, W *Enxt, int nn, int chunk, int nchunks,
                                    const int *pstart, const unsigned *pairs, const int *cur_of, int colour,
                                    double *lam, double2 *part, const Reuse &ru, const RowSet &rs, cudaStream_t s) {
     dim3 gr = node_grid(g), bl = node_block();
@@ -705,16 +734,16 @@ static cs_status launch_setup_rows(const Grid &g, int periodic, const double *At
         gr = dim3((unsigned)((rs.nshell + rs.nrep + TBX * TBY - 1) / (TBX * TBY)), (unsigned)nchunks, 1);
         bl = dim3(TBX * TBY, 1, 1);
     }
-    const size_t smem = (size_t)StenS<DIM, KIND>::NST * TBX * TBY * (sizeof(double) + sizeof(int));
+    const size_t smem = (size_t)StenS<DIM, KIND>::NST * TBX * TBY * (sizeof(W) + sizeof(int));
     // up to 27 x 256 x 12 B = 81 KB: above the default 48 KB (set per call: the attribute is per device)
-    CSX_CUDA(cudaFuncSetAttribute(k_setup_rows<DIM, KIND, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CSX_CUDA(cudaFuncSetAttribute(k_setup_rows<DIM, KIND, LAST, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-    k_setup_rows<DIM, KIND, LAST><<<gr, bl, smem, s>>>(g, periodic, At, w, Ecur, Enxt, nn, chunk, nchunks, pstart,
-                                                       pairs, cur_of, colour, lam, part, ru, rs);
+    k_setup_rows<DIM, KIND, LAST, W><<<gr, bl, smem, s>>>(g, periodic, At, w, Ecur, Enxt, nn, chunk, nchunks,
+                                                          pstart, pairs, cur_of, colour, lam, part, ru, rs);
     count_launch();
     if (nchunks > 1) {
-        k_setup_finish<DIM, LAST><<<gr, bl, 0, s>>>(g, w, Ecur, Enxt, nn, chunk, nchunks, cur_of, colour, lam, part,
-                                                    periodic, ru, rs);
+        k_setup_finish<DIM, LAST, W><<<gr, bl, 0, s>>>(g, w, Ecur, Enxt, nn, chunk, nchunks, cur_of, colour, lam,
+                                                       part, periodic, ru, rs);
         count_launch();
     }
     if (rs.on) {  // deep rows of the active colour take their representative's lambda
@@ -737,9 +766,9 @@ struct Off3 {
 // row's offsets whose column lies in the grid (wrapped on periodic grids).
 // The alpha-th largest (value, column) pair is found by alpha passes of
 // "largest after the previous one", then one pass zeroes what ranks below it.
-template <int DIM>
+template <int DIM, typename W = double>
 __global__ void __launch_bounds__(TBX *TBY) k_truncate_rows(Grid g, int periodic, int nn, const int *__restrict__ off,
-                                                             double *__restrict__ E, int alpha, int colour) {
+                                                             W *__restrict__ E, int alpha, int colour) {
     const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
     if (ix >= g.nx || iy >= g.ny) return;
     if (colour >= 0 && (((ix + 1) + (iy + 1) + (DIM == 3 ? iz + 1 : 0)) & 1) != colour) return;
@@ -766,7 +795,7 @@ __global__ void __launch_bounds__(TBX *TBY) k_truncate_rows(Grid g, int periodic
         for (int o = 0; o < nn; ++o) {
             int64_t j;
             if (!column(o, j)) continue;
-            const double v = E[(int64_t)o * N + i], n = v * v;
+            const double v = (double)E[(int64_t)o * N + i], n = v * v;
             const bool after = n < tn || (n == tn && j > tc);
             if (after && (n > bn || (n == bn && j < bc))) { bn = n; bc = j; }
         }
@@ -778,12 +807,12 @@ __global__ void __launch_bounds__(TBX *TBY) k_truncate_rows(Grid g, int periodic
     for (int o = 0; o < nn; ++o) {
         int64_t j;
         if (!column(o, j)) continue;
-        const double v = E[(int64_t)o * N + i], n = v * v;
+        const double v = (double)E[(int64_t)o * N + i], n = v * v;
         if (!(n > tn || (n == tn && j <= tc))) E[(int64_t)o * N + i] = 0.0;
     }
 }
 
-template <int DIM, int KIND>
+template <int DIM, int KIND, typename W>
 static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, int alpha,
                                double *lam, cudaStream_t s, int64_t *peak) {
     using S = StenS<DIM, KIND>;
@@ -793,7 +822,8 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
     const int64_t N = g.N;
     const int ncol = kind == CS_MULTIPLICATIVE ? 2 : 1;
     dim3 gr = node_grid(g), bl = node_block();
-    double *w = nullptr, *At = nullptr, *Ecur = nullptr, *Enxt = nullptr;
+    double *w = nullptr;
+    W *At = nullptr, *Ecur = nullptr, *Enxt = nullptr;
     int *bad = nullptr, *pstart = nullptr, *cur_of = nullptr, *offs = nullptr;
     unsigned *pairs = nullptr;
     double2 *part = nullptr;
@@ -807,9 +837,9 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
     if ((rc = dalloc_t(&w, N, nullptr, s)) != CS_OK) goto done;
     if ((rc = dalloc_t(&At, (size_t)NST * N, nullptr, s)) != CS_OK) goto done;
     if ((rc = dalloc_t(&bad, 1, nullptr, s)) != CS_OK) goto done;
-    track((int64_t)(NST + 1) * N * 8);
+    track((int64_t)NST * N * sizeof(W) + N * 8);
     if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__); goto done; }
-    k_prescale<DIM, KIND><<<gr, bl, 0, s>>>(g, h->periodic, prescale, L.A, w, At, bad);
+    k_prescale<DIM, KIND><<<gr, bl, 0, s>>>(g, h->periodic, prescale, L.A, w, static_cast<double *>(nullptr), bad);
     count_launch();
     if (cudaMemcpyAsync(&badh, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -821,11 +851,11 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
         rc = CS_ERR_ARG;
         goto done;
     }
-    k_scale_op<DIM, KIND><<<gr, bl, 0, s>>>(g, h->periodic, L.A, w, At);
+    k_scale_op<DIM, KIND, W><<<gr, bl, 0, s>>>(g, h->periodic, L.A, w, At);
     count_launch();
     if ((rc = dalloc_t(&Ecur, N, nullptr, s)) != CS_OK) goto done;
-    track(N * 8);
-    k_fill<<<1216, 256, 0, s>>>(N, Ecur, 1.0);
+    track(N * (int64_t)sizeof(W));
+    k_fill<W><<<1216, 256, 0, s>>>(N, Ecur, W(1));
     count_launch();
 
     // representatives: the grid centre and its +x neighbour (the other colour)
@@ -924,14 +954,14 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
             }
             if (!last) {
                 if ((rc = dalloc_t(&Enxt, (size_t)nn * N, nullptr, s)) != CS_OK) goto done;
-                track((int64_t)nn * N * 8);
+                track((int64_t)nn * N * (int64_t)sizeof(W));
             }
             {
                 const int colour = ncol == 2 ? k : -1;
                 double *lam_l = lam + (int64_t)lev * N;
-                rc = last ? launch_setup_rows<DIM, KIND, true>(g, h->periodic, At, w, Ecur, Enxt, nn, chunk, nchunks,
+                rc = last ? launch_setup_rows<DIM, KIND, true, W>(g, h->periodic, At, w, Ecur, Enxt, nn, chunk, nchunks,
                                                                pstart, pairs, cur_of, colour, lam_l, part, ru, rs, s)
-                          : launch_setup_rows<DIM, KIND, false>(g, h->periodic, At, w, Ecur, Enxt, nn, chunk, nchunks,
+                          : launch_setup_rows<DIM, KIND, false, W>(g, h->periodic, At, w, Ecur, Enxt, nn, chunk, nchunks,
                                                                 pstart, pairs, cur_of, colour, lam_l, part, ru, rs, s);
                 if (rc != CS_OK) goto done;
             }
@@ -946,12 +976,12 @@ static cs_status setup_level_t(const cs_hierarchy *h, int l, int kind, int nu, i
                     rc = cuda_fail(cudaGetLastError(), "copy offsets", __FILE__, __LINE__);
                     goto done;
                 }
-                k_truncate_rows<DIM><<<gr, bl, 0, s>>>(g, h->periodic, nn, offs, Enxt, alpha, ncol == 2 ? k : -1);
+                k_truncate_rows<DIM, W><<<gr, bl, 0, s>>>(g, h->periodic, nn, offs, Enxt, alpha, ncol == 2 ? k : -1);
                 count_launch();
                 if (cudaGetLastError() != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "k_truncate_rows", __FILE__, __LINE__); goto done; }
             }
             dfree(Ecur, s);
-            track(-(int64_t)Ocur.size() * N * 8);
+            track(-(int64_t)Ocur.size() * N * (int64_t)sizeof(W));
             Ecur = Enxt;
             Enxt = nullptr;
             Ocur.swap(On);
@@ -964,17 +994,24 @@ done:
     return rc;
 }
 
-cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, int alpha,
-                              double *lam, cudaStream_t s, int64_t *peak) {
+template <typename W>
+static cs_status setup_level_w(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, int alpha,
+                               double *lam, cudaStream_t s, int64_t *peak) {
     const Level &L = h->lev[l];
+    if (L.g.dim == 2) {
+        if (L.kind == STAR) return setup_level_t<2, STAR, W>(h, l, kind, nu, prescale, reuse, alpha, lam, s, peak);
+        return setup_level_t<2, BOX, W>(h, l, kind, nu, prescale, reuse, alpha, lam, s, peak);
+    }
+    if (L.kind == STAR) return setup_level_t<3, STAR, W>(h, l, kind, nu, prescale, reuse, alpha, lam, s, peak);
+    return setup_level_t<3, BOX, W>(h, l, kind, nu, prescale, reuse, alpha, lam, s, peak);
+}
+
+cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, int alpha,
+                              bool fp32, double *lam, cudaStream_t s, int64_t *peak) {
     // with truncation every row is computed (the repeated-row shortcut keeps deep rows unwritten)
     if (alpha > 0) reuse = false;
-    if (L.g.dim == 2) {
-        if (L.kind == STAR) return setup_level_t<2, STAR>(h, l, kind, nu, prescale, reuse, alpha, lam, s, peak);
-        return setup_level_t<2, BOX>(h, l, kind, nu, prescale, reuse, alpha, lam, s, peak);
-    }
-    if (L.kind == STAR) return setup_level_t<3, STAR>(h, l, kind, nu, prescale, reuse, alpha, lam, s, peak);
-    return setup_level_t<3, BOX>(h, l, kind, nu, prescale, reuse, alpha, lam, s, peak);
+    return fp32 ? setup_level_w<float>(h, l, kind, nu, prescale, reuse, alpha, lam, s, peak)
+                : setup_level_w<double>(h, l, kind, nu, prescale, reuse, alpha, lam, s, peak);
 }
 
 

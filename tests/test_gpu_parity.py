@@ -116,6 +116,59 @@ def test_truncation_parity(built, name, kind, alpha):
     assert differs  # the truncation changed the cascade
 
 
+# The FP32 setup forms R = A E and E in FP32.  A residual row is a sum of at
+# most 27 x |O| products, so each R entry carries a relative error of a few
+# times 27 u (u = 2^-24 ~ 6e-8) of its absolute row sum, E inherits those over
+# nu steps, and <E_i, R_i> / <R_i, R_i> sums them in chunks of 8 (8 u each) in
+# FP64: lambda agrees with the FP64 setup to about 1e-5.  1e-4 leaves a
+# factor 10 for cancellation in the inner products.
+FP32_SETUP_TOL = 1e-4
+
+
+@pytest.mark.parametrize("name,kind,nu", [("p2d_64", "additive", 3), ("c2d_130", "multiplicative", 3),
+                                          ("v3d_17", "additive", 2), ("c3d_33", "multiplicative", 3),
+                                          ("v2d_37", "additive", 4)])
+def test_fp32_setup_matches_oracle(built, name, kind, nu):
+    """setup_precision fp32: Lambda of every level within FP32_SETUP_TOL of
+    the FP64 oracle, and GMRES with FP32 cycles reaches 1e-10 in about as
+    many iterations as with the FP64 setup (within 20% or 2: with FP32
+    cycles the preconditioner carries FP32 rounding, and on the contrast-1e4
+    case a 1e-5 change of Lambda moves the count by a few steps either way;
+    the stationary iteration converges too slowly on some of these cases)."""
+    import paper_2606_12577_gb300 as cmg
+    A = PROBLEMS[name]()
+    ho = oracle.Hierarchy(A)
+    co = oracle.Cascade(ho, kind, nu=nu)
+    hg = gu.gpu_hierarchy(A)
+    c32 = cmg.setup_cascade(hg, kind, nu=nu, lowp=True, setup_precision="fp32")
+    c64 = cmg.setup_cascade(hg, kind, nu=nu, lowp=True)
+    for l in range(co.nlev):
+        err = gu.rel_max(cmg.export_lambda(c32, l), co.lam(l))
+        assert err <= FP32_SETUP_TOL, (l, err)
+        assert err > 0.0 or ho.N(l) <= 16  # the FP32 path really ran (exact agreement only on tiny levels)
+    b = problems.rhs(A.N, 7)
+    its = []
+    for c in (c32, c64):
+        x = _dev(np.zeros(A.N))
+        info = cmg.solve(hg, c, _dev(b), x, method="gmres", precision="fp32", tol=1e-10, maxit=300)
+        assert info.converged
+        r = b - gu.stencil_matvec(A, _host(x))
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
+        its.append(info.iterations)
+    assert abs(its[0] - its[1]) <= max(2, its[1] // 5), its
+
+
+def test_fp32_setup_limits(built):
+    import paper_2606_12577_gb300 as cmg
+    A = PROBLEMS["v2d_37"]()
+    hg = gu.gpu_hierarchy(A)
+    with pytest.raises(cmg.CascadeError, match="FP32 setup"):
+        cmg.setup_cascade(hg, "additive", nu=2, alpha=3, setup_precision="fp32")
+    hb = gu.gpu_hierarchy(A, block=2)
+    with pytest.raises(cmg.CascadeError, match="FP32 setup"):
+        cmg.setup_cascade(hb, "additive", nu=2, setup_precision="fp32")
+
+
 def test_truncation_limits(built):
     """alpha at least the row length changes nothing; block levels and the
     learned setup reject truncation."""
