@@ -895,7 +895,8 @@ cs_status cs_solve(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *o_
         float *r32 = lowp ? c->lo[0].b : nullptr;
         double *r64 = lowp ? nullptr : L.b;  // FP64 cycles read it; BF16 cycles take a BF16 copy
         auto residual = [&]() -> cs_status {
-            CSX_TRY(launch_residual64(L, L.A, b, x, r64, r32, h->red, nred, s));
+            // with FP32 cycles the norm decides convergence only: block sums in FP32
+            CSX_TRY(launch_residual64(L, L.A, b, x, r64, r32, h->red, nred, s, lowp));
             if (bf16) CSX_TRY(launch_copy_d2bf(N, L.b, c->lo16[0].b, s));
             return CS_OK;
         };

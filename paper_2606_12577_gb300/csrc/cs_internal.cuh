@@ -171,9 +171,10 @@ template <typename T>
 cs_status launch_prolong_correct(const Level &f, const Level &c, const T *xc, const T *x, T *xo,
                                  cudaStream_t s);
 // r = b - A x (FP64) with FP64 or FP32-stored coefficients; optional FP32
-// copy of r and per-block partial sums of r^2 into red (nblocks entries).
+// copy of r and per-block partial sums of r^2 into red (nblocks entries;
+// norm32: the block sums in FP32, enough for a convergence test).
 cs_status launch_residual64(const Level &L, const double *A, const double *b, const double *x,
-                            double *r, float *r32, double *red, int nred, cudaStream_t s);
+                            double *r, float *r32, double *red, int nred, cudaStream_t s, bool norm32 = false);
 cs_status launch_coarse_solve(const cs_hierarchy *h, const double *b, double *x, cudaStream_t s);
 cs_status launch_coarse_solve32(const cs_hierarchy *h, const float *b, float *x, cudaStream_t s);
 cs_status launch_axpy_f32(int64_t N, const float *d, double *x, cudaStream_t s);  // x += d

@@ -569,13 +569,31 @@ __device__ __forceinline__ double block_sum(double v, double *sm) {
     return t;
 }
 
-// r = b - A x in FP64; per-block partial sums of r^2 into red[block id]
-template <int DIM, int KIND, typename TL = float>
+__device__ __forceinline__ float block_sum_f(float v, float *sm) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
+    int warp = (threadIdx.x + threadIdx.y * blockDim.x) >> 5;
+    int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    float t = 0.f;
+    if (warp == 0) {
+        t = lane < nw ? sm[lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    return t;
+}
+
+// r = b - A x in FP64; per-block partial sums of r^2 into red[block id],
+// summed in FP64 or (N32: for a convergence test only, where the FP64 adds
+// of the block tree would cost as much as the residual) in FP32
+template <int DIM, int KIND, typename TL = float, bool N32 = false>
 __global__ void __launch_bounds__(TBX *TBY) k_residual64(Grid g, const double *__restrict__ A,
                                                           const double *__restrict__ b, const double *__restrict__ x,
                                                           double *__restrict__ r, TL *__restrict__ r32,
                                                           double *__restrict__ red) {
     __shared__ double sm[32];
+    __shared__ float smf[32];
     int ix = blockIdx.x * TBX + threadIdx.x;
     int iy = blockIdx.y * TBY + threadIdx.y;
     int iz = blockIdx.z;
@@ -587,20 +605,34 @@ __global__ void __launch_bounds__(TBX *TBY) k_residual64(Grid g, const double *_
         if (r32) r32[i] = st<TL>((typename AccT<TL>::type)v);
     }
     if (red) {
-        double t = block_sum(v * v, sm);
+        double t;
+        if (N32) {
+            const float vf = (float)v;
+            t = (double)block_sum_f(vf * vf, smf);
+        } else {
+            t = block_sum(v * v, sm);
+        }
         if (threadIdx.x == 0 && threadIdx.y == 0)
             red[blockIdx.x + gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z)] = t;
     }
 }
 
 cs_status launch_residual64(const Level &L, const double *A, const double *b, const double *x, double *r,
-                            float *r32, double *red, int nred, cudaStream_t s) {
+                            float *r32, double *red, int nred, cudaStream_t s, bool norm32) {
     dim3 gr = node_grid(L.g), bl = node_block();
     if (red && (int64_t)gr.x * gr.y * gr.z != nred) {
         set_error("internal: reduction size mismatch");
         return CS_ERR_ARG;
     }
-    if (L.g.dim == 2) {
+    if (norm32) {
+        if (L.g.dim == 2) {
+            if (L.kind == STAR) k_residual64<2, STAR, float, true><<<gr, bl, 0, s>>>(L.g, A, b, x, r, r32, red);
+            else k_residual64<2, BOX, float, true><<<gr, bl, 0, s>>>(L.g, A, b, x, r, r32, red);
+        } else {
+            if (L.kind == STAR) k_residual64<3, STAR, float, true><<<gr, bl, 0, s>>>(L.g, A, b, x, r, r32, red);
+            else k_residual64<3, BOX, float, true><<<gr, bl, 0, s>>>(L.g, A, b, x, r, r32, red);
+        }
+    } else if (L.g.dim == 2) {
         if (L.kind == STAR) k_residual64<2, STAR><<<gr, bl, 0, s>>>(L.g, A, b, x, r, r32, red);
         else k_residual64<2, BOX><<<gr, bl, 0, s>>>(L.g, A, b, x, r, r32, red);
     } else {
