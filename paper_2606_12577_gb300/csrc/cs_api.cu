@@ -216,7 +216,7 @@ static cs_status v0_enqueue(const cs_hierarchy *h, const cs_cascade *c, int l, i
         CSX_CUDA(cudaMemsetAsync(cur, 0, sizeof(T) * L.g.N, s));
         xzero = false;
     }
-    CSX_TRY(launch_residual_restrict<T>(L, Lc, v.A, v.b, cur, vc.b, s));
+    CSX_TRY(launch_residual_restrict<T>(L, Lc, v.A, v.b, cur, vc.b, other, s));  // other: free until prolongation
     CSX_TRY(v0_enqueue<T>(h, c, l + 1, order, mu_pre, mu_post, s));
     int P = mu_post * out_of_place_steps<T>(c, L);
     T *out = (P % 2 == 0) ? v.x : v.t;
@@ -809,7 +809,7 @@ cs_status cs_residual_restrict(const cs_hierarchy *h, int level, const double *b
     if (!h || !b || !x || !rc) { set_error("null argument"); return CS_ERR_ARG; }
     if (level < 0 || level + 1 >= h->nlev) { set_error("level %d has no coarser level", level); return CS_ERR_ARG; }
     return launch_residual_restrict<double>(h->lev[level], h->lev[level + 1], h->lev[level].A, b, x, rc,
-                                            (cudaStream_t)stream);
+                                            h->lev[level].t, (cudaStream_t)stream);
 }
 
 cs_status cs_prolong_correct(const cs_hierarchy *h, int level, const double *xc, double *x, cs_stream stream) {

@@ -164,9 +164,11 @@ inline dim3 node_block() { return dim3(TBX, TBY, 1); }
 template <typename T>
 cs_status launch_sweep(const Level &L, const T *A, const T *lam, const T *b, const T *x, T *out,
                        int colour, bool x_is_zero, cudaStream_t s);
+// rc = R (A x - b) (full weighting, 2^-dim P^T); with a fine-level scratch
+// vector (FP32 / FP64) in two passes, else in one
 template <typename T>
 cs_status launch_residual_restrict(const Level &f, const Level &c, const T *A, const T *b, const T *x,
-                                   T *rc, cudaStream_t s);
+                                   T *rc, T *scratch, cudaStream_t s);
 template <typename T>
 cs_status launch_prolong_correct(const Level &f, const Level &c, const T *xc, const T *x, T *xo,
                                  cudaStream_t s);
