@@ -408,6 +408,9 @@ typedef struct {
     int nlevels;      /* levels in the hierarchy */
     int block;        /* block edge in nodes */
     int64_t lamsize;  /* doubles of Lambda per cascade step (sum of n_b^2 over blocks) */
+    int sym32;        /* 1: a 3D 27-point point-block level whose operator is symmetric (to 1e-12 of
+                         the diagonals); FP32 cycles store its centre and 13 forward couplings and
+                         take each backward coupling from the neighbour's row */
 } cs_level_info;
 
 cs_status cs_query_level(const cs_hierarchy *h, int level, cs_level_info *info);

@@ -72,7 +72,7 @@ class Hierarchy:
             self._infos[level] = {
                 "dim": info.dim, "n": tuple(info.n), "N": int(info.N), "nst": info.nst,
                 "offsets": [tuple(info.off[s]) for s in range(info.nst)], "nlevels": info.nlevels,
-                "block": info.block, "lamsize": int(info.lamsize)}
+                "block": info.block, "lamsize": int(info.lamsize), "sym32": bool(info.sym32)}
         return self._infos[level]
 
     def N(self, level=0):

@@ -54,7 +54,8 @@ class cs_solve_info(C.Structure):
 
 class cs_level_info(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("N", C.c_int64), ("nst", C.c_int),
-                ("off", (C.c_int * 3) * 27), ("nlevels", C.c_int), ("block", C.c_int), ("lamsize", C.c_int64)]
+                ("off", (C.c_int * 3) * 27), ("nlevels", C.c_int), ("block", C.c_int), ("lamsize", C.c_int64),
+                ("sym32", C.c_int)]
 
 
 class cs_batch_opts(C.Structure):

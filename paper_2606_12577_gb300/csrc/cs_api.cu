@@ -377,6 +377,7 @@ cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts
         if (e != cudaSuccess) { rc = cuda_fail(e, "copy operator", __FILE__, __LINE__); goto fail; }
         if (!h->periodic && (rc = drop_outside_couplings(L, s)) != CS_OK) goto fail;
         if (!opts.no_reuse && (rc = level_margin(L, h->periodic, s)) != CS_OK) goto fail;
+        if (!h->periodic && (rc = check_symmetric(L, s)) != CS_OK) goto fail;
     }
     while (!h->periodic && (opts.max_levels <= 0 || (int)h->lev.size() < opts.max_levels)) {
         const Level &F = h->lev.back();
@@ -392,6 +393,7 @@ cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts
         if ((rc = dalloc_t(&C.A, (size_t)C.nst * C.g.N, &h->bytes, s)) != CS_OK) goto fail;
         h->lev.push_back(C);
         if ((rc = galerkin_level(h->lev[h->lev.size() - 2], h->lev.back(), !opts.no_reuse, s)) != CS_OK) goto fail;
+        if ((rc = check_symmetric(h->lev.back(), s)) != CS_OK) goto fail;
         if (!opts.no_reuse && (rc = level_margin(h->lev.back(), false, s)) != CS_OK) goto fail;
     }
     h->nlev = (int)h->lev.size();
@@ -570,8 +572,12 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
             const Level &L = h->lev[l];
             LowLevel &lo = c->lo[l];
             const int64_t N = L.g.N;
-            if ((rc = dalloc_t(&lo.A, (size_t)L.nst * N, &c->bytes, s)) != CS_OK) goto fail;
-            if ((rc = launch_copy_d2f((int64_t)L.nst * N, L.A, lo.A, s)) != CS_OK) goto fail;
+            if ((rc = dalloc_t(&lo.A, (size_t)lo_nst(L) * N, &c->bytes, s)) != CS_OK) goto fail;
+            if (L.sym32) {
+                if ((rc = launch_copy_box_sym32(L, lo.A, s)) != CS_OK) goto fail;
+            } else if ((rc = launch_copy_d2f((int64_t)L.nst * N, L.A, lo.A, s)) != CS_OK) {
+                goto fail;
+            }
             if (l < c->nlev) {
                 if ((rc = dalloc_t(&lo.lam, (size_t)c->nu * lam_step(L), &c->bytes, s)) != CS_OK) goto fail;
                 if ((rc = launch_copy_d2f((int64_t)c->nu * lam_step(L), c->lam[l], lo.lam, s)) != CS_OK) goto fail;
@@ -776,6 +782,10 @@ cs_status cs_sweep_rhs(const cs_hierarchy *h, cs_cascade *c, int level, int step
     if (precision == CS_FP32) {
         if (!c->lowp) { set_error("FP32 steps need lowp"); return CS_ERR_ARG; }
         const LowLevel &lo = c->lo[level];
+        if (L.sym32) {
+            set_error("FP32 multi-RHS steps on a 3D 27-point level with symmetric FP32 storage are not implemented");
+            return CS_ERR_UNSUPPORTED;
+        }
         return launch_block_sweep_m<float>(L, lo.A, lo.lam + st, (const float *)b, (const float *)x, (float *)out,
                                            nrhs, colour, transpose != 0, s);
     }
@@ -1074,6 +1084,7 @@ cs_status cs_query_level(const cs_hierarchy *h, int level, cs_level_info *info) 
             ls += (ex * ey * ez) * (ex * ey * ez);
         }
     info->lamsize = ls;
+    info->sym32 = L.sym32;
     return CS_OK;
 }
 

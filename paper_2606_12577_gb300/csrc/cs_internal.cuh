@@ -47,7 +47,15 @@ struct Level {
     // local positions lp = lx + bs (ly + bs lz); absent positions are zero.
     int bs = 1, nbx = 0, nby = 0, nbz = 0, nmax = 1;
     int64_t nblocks = 0;
+    // a 3D 27-point point-block level whose operator is symmetric (to 1e-12
+    // of the diagonals): its FP32 copies keep the centre and the 13 forward
+    // couplings only, [14][N] (entry k = 27-point entry 13 + k); a backward
+    // coupling is the forward one stored at the neighbour
+    int sym32 = 0;
 };
+
+// entries per node of a level's FP32 operator copy
+inline int64_t lo_nst(const Level &L) { return L.sym32 ? 14 : L.nst; }
 
 struct LowLevel {   // FP32 state of one level (owned by a cascade)
     float *A = nullptr;    // [nst][N]
@@ -202,6 +210,10 @@ cs_status galerkin_level(const Level &f, Level &c, bool reuse, cudaStream_t s);
 cs_status level_margin(Level &L, bool periodic, cudaStream_t s);
 // zeroes the coefficients of couplings to nodes outside a Dirichlet grid
 cs_status drop_outside_couplings(const Level &L, cudaStream_t s);
+// sets L.sym32 (3D 27-point point-block levels; synchronises the stream)
+cs_status check_symmetric(Level &L, cudaStream_t s);
+// the FP32 copy of a sym32 level's operator ([14][N])
+cs_status launch_copy_box_sym32(const Level &L, float *o, cudaStream_t s);
 cs_status coarse_factor(cs_hierarchy *h, cudaStream_t s);
 // fp32: form the residual rows R and the error propagator E in FP32 (the
 // row products summed in FP64 over chunks of 8); lambda is stored in FP64

@@ -183,6 +183,42 @@ cs_status drop_outside_couplings(const Level &L, cudaStream_t s) {
     return CS_OK;
 }
 
+// Symmetry of a 3D 27-point operator: every forward coupling A_{i,i+o}
+// (entries 14..26) against the backward one stored at the neighbour,
+// A_{i+o,i} (entry 26 - s there), within 1e-12 of the two diagonals.
+__global__ void k_sym_check(Grid g, const double *__restrict__ A, int *asym) {
+    const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
+    if (ix >= g.nx || iy >= g.ny) return;
+    const int64_t N = g.N, i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
+    const double di = fabs(A[13 * N + i]);
+    for (int s = 14; s < 27; ++s) {
+        const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+        const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+        if (jx < 0 || jx >= g.nx || jy < 0 || jy >= g.ny || jz < 0 || jz >= g.nz) continue;
+        const int64_t j = jx + (int64_t)g.nx * (jy + (int64_t)g.ny * jz);
+        const double f = A[(int64_t)s * N + i], bk = A[(int64_t)(26 - s) * N + j];
+        if (!(fabs(f - bk) <= 1e-12 * (di + fabs(A[13 * N + j])))) atomicExch(asym, 1);
+    }
+}
+
+cs_status check_symmetric(Level &L, cudaStream_t s) {
+    L.sym32 = 0;
+    if (L.g.dim != 3 || L.kind != BOX || L.bs != 1) return CS_OK;
+    int *d = nullptr, asym = 1;
+    CSX_TRY(dalloc_t(&d, 1, nullptr, s));
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        k_sym_check<<<node_grid(L.g), node_block(), 0, s>>>(L.g, L.A, d);
+        count_launch();
+        e = cudaMemcpyAsync(&asym, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dfree(d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "symmetry check", __FILE__, __LINE__);
+    L.sym32 = asym ? 0 : 1;
+    return CS_OK;
+}
+
 cs_status level_margin(Level &L, bool periodic, cudaStream_t s) {
     const Grid &g = L.g;
     const int64_t ref = g.nx / 2 + (int64_t)g.nx * (g.ny / 2 + (int64_t)g.ny * (g.nz / 2));

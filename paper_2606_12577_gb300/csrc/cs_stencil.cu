@@ -111,11 +111,83 @@ __global__ void __launch_bounds__(TBX *TBY) k_sweep(Grid g, const T *__restrict_
     out[i] = st<T>(xi - ld<T>(lam[i]) * r);
 }
 
+// ---- 3D 27-point levels with symmetric FP32 storage (Level::sym32):
+// Af[k][i] holds entry 13 + k of row i (centre and forward couplings); the
+// backward entry s < 13 of row i is the forward entry 26 - s of the
+// neighbour j = i + off(s).  Same summation order as apply_row, so only the
+// (mirrored) coefficient values can differ from the full copy's.
+__device__ __forceinline__ float apply_row_box_sym(const Grid &g, const float *__restrict__ Af, const float *x,
+                                                   int ix, int iy, int iz, int64_t i) {
+    float ax = 0.f;
+#pragma unroll
+    for (int s = 0; s < 27; ++s) {
+        const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+        const bool in = (unsigned)(ix + dx) < (unsigned)g.nx && (unsigned)(iy + dy) < (unsigned)g.ny &&
+                        (unsigned)(iz + dz) < (unsigned)g.nz;
+        const int64_t j = i + dx + (int64_t)g.nx * (dy + (int64_t)g.ny * dz);
+        float a = 0.f, xv = 0.f;
+        if (s >= 13) a = Af[(int64_t)(s - 13) * g.N + i];
+        else if (in) a = Af[(int64_t)(13 - s) * g.N + j];
+        if (in) xv = x[j];
+        ax = fmaf(a, xv, ax);
+    }
+    return ax;
+}
+
+template <bool COLOURED>
+__global__ void __launch_bounds__(TBX *TBY) k_sweep_sym(Grid g, const float *__restrict__ Af,
+                                                         const float *__restrict__ lam, const float *__restrict__ b,
+                                                         const float *x, float *out, int colour, int xzero) {
+    const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
+    if (ix >= g.nx || iy >= g.ny) return;
+    const int64_t i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
+    if (COLOURED) {
+        if (node_colour(3, ix, iy, iz) != colour) {
+            if (xzero) out[i] = 0.f;
+            else if (out != x) out[i] = x[i];
+            return;
+        }
+    }
+    float r, xi;
+    if (xzero) {
+        r = -b[i];
+        xi = 0.f;
+    } else {
+        r = apply_row_box_sym(g, Af, x, ix, iy, iz, i) - b[i];
+        xi = x[i];
+    }
+    out[i] = xi - lam[i] * r;
+}
+
+__global__ void k_d2f_box_sym(int64_t N, const double *__restrict__ A, float *__restrict__ o) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 14 * N; t += (int64_t)gridDim.x * blockDim.x)
+        o[t] = (float)A[13 * N + t];
+}
+
+cs_status launch_copy_box_sym32(const Level &L, float *o, cudaStream_t s) {
+    if (!L.sym32) {
+        set_error("internal: symmetric FP32 copy of a level without symmetric storage");
+        return CS_ERR_ARG;
+    }
+    k_d2f_box_sym<<<1216, 256, 0, s>>>(L.g.N, L.A, o);
+    CSX_CUDA(cudaGetLastError());
+    count_launch();
+    return CS_OK;
+}
+
 template <typename T, bool COLOURED>
 static cs_status sweep_dispatch(const Level &L, const T *A, const T *lam, const T *b, const T *x, T *out,
                                 int colour, bool xzero, cudaStream_t s) {
     dim3 gr = node_grid(L.g), bl = node_block();
     int xz = xzero ? 1 : 0;
+    if constexpr (std::is_same<T, float>::value) {
+        if (L.sym32) {  // FP32 operators of these levels are stored symmetric
+            k_sweep_sym<COLOURED><<<gr, bl, 0, s>>>(L.g, A, lam, b, x, out, colour, xz);
+            CSX_CUDA(cudaGetLastError());
+            count_launch();
+            return CS_OK;
+        }
+    }
     if (L.g.dim == 2) {
         if (L.kind == STAR) k_sweep<2, STAR, T, COLOURED><<<gr, bl, 0, s>>>(L.g, A, lam, b, x, out, colour, xz);
         else k_sweep<2, BOX, T, COLOURED><<<gr, bl, 0, s>>>(L.g, A, lam, b, x, out, colour, xz);
@@ -490,6 +562,15 @@ __global__ void __launch_bounds__(TBX *TBY) k_fine_residual(Grid g, const T *__r
     r[i] = apply_row<DIM, KIND, T>(g, A, x, ix, iy, iz, i) - b[i];
 }
 
+__global__ void __launch_bounds__(TBX *TBY) k_fine_residual_sym(Grid g, const float *__restrict__ Af,
+                                                                 const float *__restrict__ b,
+                                                                 const float *__restrict__ x, float *__restrict__ r) {
+    const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
+    if (ix >= g.nx || iy >= g.ny) return;
+    const int64_t i = ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
+    r[i] = apply_row_box_sym(g, Af, x, ix, iy, iz, i) - b[i];
+}
+
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TBX *TBY) k_restrict_gather(Grid gf, Grid gc, const T *__restrict__ r,
                                                                T *__restrict__ rc) {
@@ -519,10 +600,18 @@ template <typename T>
 cs_status launch_residual_restrict(const Level &f, const Level &c, const T *A, const T *b, const T *x, T *rc,
                                    T *scratch, cudaStream_t s) {
     dim3 gr = node_grid(c.g), bl = node_block();
+    if (std::is_same<T, float>::value && f.sym32 && !scratch) {
+        set_error("internal: the restriction from a symmetric FP32 level needs a scratch vector");
+        return CS_ERR_ARG;
+    }
     if constexpr (std::is_same<T, float>::value || std::is_same<T, double>::value) {
         if (scratch) {
             const dim3 gf = node_grid(f.g);
-            if (f.g.dim == 2) {
+            if (std::is_same<T, float>::value && f.sym32) {
+                k_fine_residual_sym<<<gf, bl, 0, s>>>(f.g, (const float *)A, (const float *)b, (const float *)x,
+                                                      (float *)scratch);
+                k_restrict_gather<3, T><<<gr, bl, 0, s>>>(f.g, c.g, scratch, rc);
+            } else if (f.g.dim == 2) {
                 if (f.kind == STAR) k_fine_residual<2, STAR, T><<<gf, bl, 0, s>>>(f.g, A, b, x, scratch);
                 else k_fine_residual<2, BOX, T><<<gf, bl, 0, s>>>(f.g, A, b, x, scratch);
                 k_restrict_gather<2, T><<<gr, bl, 0, s>>>(f.g, c.g, scratch, rc);

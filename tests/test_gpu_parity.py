@@ -250,6 +250,54 @@ def test_level_steps(built, name, kind):
     assert gu.rel_max(_host(xg), ho.coarse_solve(bc)) <= TOL
 
 
+def _nonsym3d(n, seed):
+    """3D 7-point operator with unequal couplings in the two directions of
+    every edge (a convection-diffusion-like, nonsymmetric M-matrix): its
+    Galerkin levels are nonsymmetric 27-point operators."""
+    offs = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+    N = n ** 3
+    coeff = np.zeros((7, N))
+    for s in range(1, 7):
+        coeff[s] = -problems.uniform(700 + 10 * seed + s, N, 0.5, 2.0)
+    coeff[0] = -coeff[1:].sum(axis=0) + 0.1
+    return problems.Stencil(3, (n, n, n), offs, coeff, False)
+
+
+@pytest.mark.parametrize("kind", ["sym", "nonsym"])
+def test_fp32_box_levels_symmetric_storage(built, kind):
+    """Galerkin levels of a symmetric 3D operator are flagged symmetric and
+    their FP32 copies keep 14 of the 27 entries; a nonsymmetric operator keeps
+    full storage.  Either way an FP32 step on a 27-point level agrees with
+    the FP64 step to FP32 rounding, and FP32 cycles with FP64 refinement
+    reach 1e-10."""
+    import torch
+
+    import paper_2606_12577_gb300 as cmg
+    A = PROBLEMS["v3d_33x"]() if kind == "sym" else _nonsym3d(33, 1)
+    hg = gu.gpu_hierarchy(A)
+    assert hg.nlevels >= 3
+    flags = [cmg.query_level(hg, l)["sym32"] for l in range(hg.nlevels)]
+    assert not flags[0]  # the 7-point fine level keeps its layout
+    assert all(flags[1:]) if kind == "sym" else not any(flags)
+    cg = cmg.setup_cascade(hg, "additive", nu=2, lowp=True)
+    N1 = hg.N(1)
+    b = problems.uniform(21, N1)
+    x = problems.uniform(22, N1)
+    o64 = _dev(np.zeros(N1))
+    cmg.sweep(hg, cg, 1, 1, _dev(b), _dev(x), o64)
+    f32 = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    o32 = f32(np.zeros(N1))
+    cmg.sweep(hg, cg, 1, 1, f32(b), f32(x), o32)
+    ref = _host(o64)
+    assert np.abs(_host(o32).astype(np.float64) - ref).max() <= 1e-5 * np.abs(ref).max()
+    bb = problems.rhs(A.N, 23)
+    xg = _dev(np.zeros(A.N))
+    info = cmg.solve(hg, cg, _dev(bb), xg, method="gmres", precision="fp32", tol=1e-10, maxit=200)
+    assert info.converged
+    r = bb - gu.stencil_matvec(A, _host(xg))
+    assert np.linalg.norm(r) / np.linalg.norm(bb) <= 1e-10
+
+
 @pytest.mark.parametrize("name", ["p2d_64", "v2d_130", "v3d_33x"])
 @pytest.mark.parametrize("kind", ["additive", "multiplicative"])
 @pytest.mark.parametrize("order,mu", [("RF", 1), ("FF", 2)])
