@@ -579,7 +579,44 @@ def main():
                               "traffic": traffic, "algorithmic_bytes_per_launch": bytes_sweep,
                               "launch_ms": t_sweep * 1e3}
         result["smoother_gbs"] = achieved
-        del h, c, x
+        # ---- multiplicative red-black colour step (in place, FP32, finest level): the
+        # colours interleave, so A, Lambda, b and x are read for every node
+        # (sector granularity) and x is written for the colour's half
+        cm = cmg.setup_cascade(h, "multiplicative", nu=a.nu, lowp=True)
+        xr = xb[0]
+        for k in range(3):
+            cmg.sweep(h, cm, 0, k % a.nu, b32, xr, xr, colour=k % 2)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for k in range(reps):
+            cmg.sweep(h, cm, 0, k % a.nu, b32, xr, xr, colour=k % 2)
+        e1.record(s)
+        torch.cuda.synchronize()
+        t_col = e0.elapsed_time(e1) / reps * 1e-3
+        bytes_col = (nst + 3) * 4 * N + 4 * (N // 2)
+        result["colour_step_roofline"] = {
+            "bound": "hbm", "kernel": "k_sweep<3,STAR,float,COLOURED> (multiplicative colour step, in place, finest level)",
+            "achieved": bytes_col / t_col / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": bytes_col / t_col / 1e9 / peak, "algorithmic_bytes_per_launch": bytes_col, "launch_ms": t_col * 1e3}
+        # ---- BF16-storage additive step (FP32 arithmetic, finest level): (nst + 4) x 2 B per node
+        c16 = cmg.setup_cascade(h, a.kind, nu=a.nu, lowp=2)
+        x16 = [t.to(torch.bfloat16) for t in xb]
+        b16 = b32.to(torch.bfloat16)
+        for k in range(3):
+            cmg.sweep(h, c16, 0, k % a.nu, b16, x16[k % 2], x16[(k + 1) % 2], colour=-1 if a.kind == "additive" else 0)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for k in range(reps):
+            cmg.sweep(h, c16, 0, k % a.nu, b16, x16[k % 2], x16[(k + 1) % 2], colour=-1 if a.kind == "additive" else 0)
+        e1.record(s)
+        torch.cuda.synchronize()
+        t16 = e0.elapsed_time(e1) / reps * 1e-3
+        bytes16 = (nst + 4) * 2 * N
+        result["bf16_step_roofline"] = {
+            "bound": "hbm", "kernel": "k_sweep_bf16x2 (additive step, BF16 storage, FP32 arithmetic, finest level)",
+            "achieved": bytes16 / t16 / 1e9, "peak": peak, "unit": "GB/s", "frac": bytes16 / t16 / 1e9 / peak,
+            "algorithmic_bytes_per_launch": bytes16, "launch_ms": t16 * 1e3}
+        del h, c, x, cm, c16, x16, b16
         torch.cuda.empty_cache()
         # ---- multi-RHS block step (the block product X_b -= Lambda_b R_b):
         # elliptic interface 1024^2, 200 inclusions, 2x2-node blocks, 32 RHS, FP32
