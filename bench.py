@@ -573,7 +573,7 @@ def main():
                 traffic = tr["sweep_fp32_bytes_per_launch"]
         except Exception:
             traffic = None
-        result["roofline"] = {"bound": "hbm", "kernel": "k_sweep<3,STAR,float> (additive step, finest level)",
+        result["roofline"] = {"bound": "hbm", "kernel": "k_sweep_f32x2 (additive step, FP32, two nodes per thread, finest level)",
                               "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                               "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
                               "traffic": traffic, "algorithmic_bytes_per_launch": bytes_sweep,
