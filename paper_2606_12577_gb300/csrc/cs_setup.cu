@@ -310,6 +310,74 @@ __global__ void __launch_bounds__(TBX *TBY) k_galerkin(Grid gf, Grid gc, const d
     }
 }
 
+// The same product for levels of up to 16^3 coarse rows, one warp per
+// (coarse row, stencil entry t) with the 3^dim fine neighbours e of the
+// row's fine node on its lanes: each lane sums its neighbour's contributions
+// to t over the fine stencil entries, and a fixed shuffle tree adds the
+// lanes.  The row-per-thread kernel runs a row's 3^dim x nst contributions as
+// one chain of dependent loads; on these levels that chain, not the data,
+// set the launch time (about 0.4-0.5 ms per level from 16^3 down, against
+// 28-300 us here).  On 32^3 and 64^3 levels the warps cost more than the
+// chains (1.2 and 4.9 ms against 0.53 and 0.57 ms).  The summation order
+// differs from the row-per-thread kernel's, so a level always takes the
+// same kernel whether its deep rows are copied or not.
+constexpr int64_t GALERKIN_WARP_MAX_ROWS = 16 * 16 * 16;
+template <int DIM, int KIND>
+__global__ void __launch_bounds__(256) k_galerkin_w(Grid gf, Grid gc, const double *__restrict__ Af,
+                                                    double *__restrict__ Ac, RowSet rs, int64_t nrows) {
+    using S = StenS<DIM, KIND>;
+    constexpr int NC = DIM == 3 ? 27 : 9;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t row = w / NC;
+    const int t = (int)(w - row * NC);
+    if (row >= nrows) return;  // warp-uniform
+    int cx, cy, cz;
+    if (rs.on) {
+        if (!rowset_coord(rs, gc, row, cx, cy, cz)) return;
+    } else {
+        cx = (int)(row % gc.nx);
+        cy = (int)((row / gc.nx) % gc.ny);
+        cz = (int)(row / ((int64_t)gc.nx * gc.ny));
+    }
+    const int64_t ci = cx + (int64_t)gc.nx * (cy + (int64_t)gc.ny * cz);
+    const int tx = t % 3 - 1, ty = (t / 3) % 3 - 1, tz = DIM == 3 ? t / 9 - 1 : 0;
+    const int jx = cx + tx, jy = cy + ty, jz = cz + tz;
+    if (!(jx >= 0 && jx < gc.nx && jy >= 0 && jy < gc.ny && (DIM == 2 || (jz >= 0 && jz < gc.nz)))) {
+        if (lane == 0) Ac[(int64_t)t * gc.N + ci] = 0.0;
+        return;
+    }
+    double part = 0.0;
+    if (lane < NC) {
+        const int e = lane;
+        const int ex = e % 3 - 1, ey = (e / 3) % 3 - 1, ez = DIM == 3 ? e / 9 - 1 : 0;
+        const int fx = 2 * cx + 1 + ex, fy = 2 * cy + 1 + ey, fz = DIM == 3 ? 2 * cz + 1 + ez : 0;
+        if (fx < gf.nx && fy < gf.ny && (DIM == 2 || fz < gf.nz)) {
+            const int64_t fi = fx + (int64_t)gf.nx * (fy + (int64_t)gf.ny * fz);
+            const double wr = pw(ex) * pw(ey) * pw(ez);
+            // axis offset u = d + s reaches target offset tt: weight 1 (u even, tt = u / 2) or
+            // 1/2 (u odd, tt one of the two coarse nodes around it); else 0
+            auto wt = [](int u, int tt) {
+                if (u & 1) {
+                    const int j0 = (u - 1) >> 1;
+                    return (tt == j0 || tt == j0 + 1) ? 0.5 : 0.0;
+                }
+                return tt == (u >> 1) ? 1.0 : 0.0;
+            };
+#pragma unroll
+            for (int s2 = 0; s2 < S::NST; ++s2) {
+                int dx, dy, dz;
+                S::off(s2, dx, dy, dz);
+                const double wx = wt(ex + dx, tx), wy = wt(ey + dy, ty), wz = DIM == 3 ? wt(ez + dz, tz) : 1.0;
+                if (wx != 0.0 && wy != 0.0 && wz != 0.0) part += wr * Af[(int64_t)s2 * gf.N + fi] * wx * wy * wz;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if (lane == 0) Ac[(int64_t)t * gc.N + ci] = (DIM == 3 ? 0.125 : 0.25) * part;
+}
+
 // rows inside the deep box take the representative row's values
 __global__ void k_copy_deep(Grid g, int nv, double *__restrict__ V, RowSet rs, int colour) {
     const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
@@ -350,6 +418,26 @@ cs_status galerkin_level(const Level &f, Level &c, bool reuse, cudaStream_t s) {
             gr = dim3((unsigned)((rs.nshell + rs.nrep + TBX * TBY - 1) / (TBX * TBY)), 1, 1);
             bl = dim3(TBX * TBY, 1, 1);
         }
+    }
+    if (c.g.N <= GALERKIN_WARP_MAX_ROWS) {  // by level size, so that reuse does not change the kernel
+        const int64_t nrows = rs.on ? rs.nshell + rs.nrep : c.g.N;
+        const int nc = c.g.dim == 3 ? 27 : 9;
+        const unsigned nb = (unsigned)((nrows * nc * 32 + 255) / 256);
+        if (f.g.dim == 2) {
+            if (f.kind == STAR) k_galerkin_w<2, STAR><<<nb, 256, 0, s>>>(f.g, c.g, f.A, c.A, rs, nrows);
+            else k_galerkin_w<2, BOX><<<nb, 256, 0, s>>>(f.g, c.g, f.A, c.A, rs, nrows);
+        } else {
+            if (f.kind == STAR) k_galerkin_w<3, STAR><<<nb, 256, 0, s>>>(f.g, c.g, f.A, c.A, rs, nrows);
+            else k_galerkin_w<3, BOX><<<nb, 256, 0, s>>>(f.g, c.g, f.A, c.A, rs, nrows);
+        }
+        CSX_CUDA(cudaGetLastError());
+        count_launch();
+        if (rs.on) {
+            k_copy_deep<<<node_grid(c.g), node_block(), 0, s>>>(c.g, c.nst, c.A, rs, -1);
+            CSX_CUDA(cudaGetLastError());
+            count_launch();
+        }
+        return CS_OK;
     }
     const size_t sm2 = sizeof(double) * 9 * TBX * TBY, sm3 = sizeof(double) * 27 * TBX * TBY;
     if (f.g.dim == 2) {
