@@ -502,7 +502,7 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
                     set_error("the learned setup needs an additive cascade on a 2D block level");
                     return CS_ERR_UNSUPPORTED;
                 }
-                // exact level-1 blocks (one least-squares problem per block) judge the prediction
+                // exact level-1 blocks (one least-squares problem per block) are the yardstick of the prediction
                 double *lam1 = nullptr;
                 cs_status r = dalloc_t(&lam1, (size_t)lam_step(L), nullptr, s);
                 if (r != CS_OK) return r;
