@@ -267,8 +267,14 @@ static cs_status sweep_dispatch(const Level &L, const T *A, const T *lam, const 
                                 int colour, bool xzero, cudaStream_t s) {
     dim3 gr = node_grid(L.g), bl = node_block();
     int xz = xzero ? 1 : 0;
+    // the paired kernels load two values at once: every array must be aligned
+    // to two elements (caller-given vectors may be views at an odd offset)
+    auto pairs_aligned = [&](size_t bytes) {
+        const uintptr_t m = (uintptr_t)A | (uintptr_t)lam | (uintptr_t)b | (uintptr_t)x | (uintptr_t)out;
+        return (m % bytes) == 0;
+    };
     if constexpr (std::is_same<T, __nv_bfloat16>::value) {
-        if (!COLOURED && L.g.dim == 3 && L.kind == STAR && L.g.nx % 2 == 0 && out != x) {
+        if (!COLOURED && L.g.dim == 3 && L.kind == STAR && L.g.nx % 2 == 0 && out != x && pairs_aligned(4)) {
             const dim3 g2((unsigned)((L.g.nx / 2 + TBX - 1) / TBX), gr.y, gr.z);
             k_sweep_bf16x2<<<g2, bl, 0, s>>>(L.g, A, lam, b, x, out, xz);
             CSX_CUDA(cudaGetLastError());
@@ -277,7 +283,7 @@ static cs_status sweep_dispatch(const Level &L, const T *A, const T *lam, const 
         }
     }
     if constexpr (std::is_same<T, float>::value) {
-        if (!COLOURED && L.g.dim == 3 && L.kind == STAR && L.g.nx % 2 == 0 && out != x) {
+        if (!COLOURED && L.g.dim == 3 && L.kind == STAR && L.g.nx % 2 == 0 && out != x && pairs_aligned(8)) {
             const dim3 g2((unsigned)((L.g.nx / 2 + TBX - 1) / TBX), gr.y, gr.z);
             k_sweep_f32x2<<<g2, bl, 0, s>>>(L.g, A, lam, b, x, out, xz);
             CSX_CUDA(cudaGetLastError());

@@ -298,6 +298,30 @@ def test_fp32_box_levels_symmetric_storage(built, kind):
     assert np.linalg.norm(r) / np.linalg.norm(bb) <= 1e-10
 
 
+def test_paired_steps_take_misaligned_views(built):
+    """The FP32 and BF16 additive steps on an even-width 3D grid read two nodes
+    at a time; vectors that are views at an odd element offset go to the
+    one-node kernels instead, with bit-identical results."""
+    import torch
+
+    import paper_2606_12577_gb300 as cmg
+    A = _rect(18, 7, 5, seed=9)
+    hg = gu.gpu_hierarchy(A, max_levels=1)
+    cg = cmg.setup_cascade(hg, "additive", nu=2, lowp=2)
+    N = A.N
+    for dt in (torch.float32, torch.bfloat16):
+        b = torch.tensor(problems.uniform(31, N), device="cuda").to(dt)
+        x = torch.tensor(problems.uniform(32, N), device="cuda").to(dt)
+        out = torch.zeros(N, dtype=dt, device="cuda")
+        cmg.sweep(hg, cg, 0, 1, b, x, out)
+        pool = torch.zeros(3 * (N + 1), dtype=dt, device="cuda")
+        bv, xv, ov = pool[1:N + 1], pool[N + 2:2 * N + 2], pool[2 * N + 3:3 * N + 3]  # odd element offsets
+        bv.copy_(b)
+        xv.copy_(x)
+        cmg.sweep(hg, cg, 0, 1, bv, xv, ov)
+        assert torch.equal(ov, out), dt
+
+
 @pytest.mark.parametrize("name", ["p2d_64", "v2d_130", "v3d_33x"])
 @pytest.mark.parametrize("kind", ["additive", "multiplicative"])
 @pytest.mark.parametrize("order,mu", [("RF", 1), ("FF", 2)])
