@@ -327,6 +327,34 @@ def test_galerkin_matches_dense_rap(dim, n):
     np.testing.assert_allclose(h.prolong_correct(0, xc, x), x - P @ xc, rtol=1e-13, atol=1e-15)
 
 
+@pytest.mark.parametrize("sym", [True, False])
+def test_galerkin_levels_inherit_symmetry(sym):
+    """R A P with R = 2^-d P^T is symmetric when A is (the FP32 copies of the
+    GPU's 27-point levels store half of such an operator): every level of a
+    symmetric 3D variable-coefficient operator is symmetric to 1e-12 of its
+    diagonals, and a nonsymmetric fine operator gives nonsymmetric levels."""
+    n = 17
+    if sym:
+        A = problems.variable_poisson(problems.random_coefficients(3, n, 61, -2.0, 2.0))
+    else:
+        offs = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+        coeff = np.zeros((7, n ** 3))
+        for s2 in range(1, 7):
+            coeff[s2] = -problems.uniform(70 + s2, n ** 3, 0.5, 2.0)
+        coeff[0] = -coeff[1:].sum(axis=0) + 0.1
+        A = problems.Stencil(3, (n, n, n), offs, coeff, False)
+    h = oracle.Hierarchy(A)
+    assert h.nlev >= 3
+    for l in range(1, h.nlev):
+        D = h.dense(l)
+        d = np.abs(np.diag(D))
+        asym = np.abs(D - D.T) / (d[:, None] + d[None, :])
+        if sym:
+            assert asym.max() <= 1e-12, (l, asym.max())
+        else:
+            assert asym.max() > 1e-3, (l, asym.max())
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_galerkin_poisson_stencil_closed_form(dim):
     """Bilinear / trilinear Galerkin coarsening of the 5-/7-point Laplacian
