@@ -327,6 +327,25 @@ def test_galerkin_matches_dense_rap(dim, n):
     np.testing.assert_allclose(h.prolong_correct(0, xc, x), x - P @ xc, rtol=1e-13, atol=1e-15)
 
 
+def test_couplings_to_boundary_nodes_are_ignored():
+    """Homogeneous Dirichlet elimination (Sec. 2): a stencil coefficient that
+    couples a node to a point outside the grid multiplies a zero boundary
+    value.  Nonzero such coefficients in the input leave every level and the
+    cascade unchanged."""
+    n = 9
+    base = problems.poisson(3, n)
+    noisy = problems.Stencil(base.dim, base.n, base.offsets, base.coeff.copy(), False)
+    outside = base.coeff == 0.0  # the couplings to boundary nodes
+    outside[0] = False
+    noisy.coeff[outside] = -problems.uniform(5, int(outside.sum()), 1.0, 3.0)
+    h0, h1 = oracle.Hierarchy(base), oracle.Hierarchy(noisy)
+    assert h0.nlev == h1.nlev
+    for l in range(h0.nlev):
+        assert np.array_equal(h0.dense(l), h1.dense(l))
+    c0, c1 = oracle.Cascade(h0, "additive", nu=2), oracle.Cascade(h1, "additive", nu=2)
+    assert np.array_equal(c0.lam(0), c1.lam(0))
+
+
 @pytest.mark.parametrize("sym", [True, False])
 def test_galerkin_levels_inherit_symmetry(sym):
     """R A P with R = 2^-d P^T is symmetric when A is (the FP32 copies of the
