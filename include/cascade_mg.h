@@ -201,7 +201,26 @@ cs_status cs_residual_restrict(const cs_hierarchy *h, int level, const double *b
 cs_status cs_prolong_correct(const cs_hierarchy *h, int level, const double *xc, double *x,
                              cs_stream stream);
 
-/* x = A_c^-1 b on the coarsest level (bottom-level direct solve, FP64). */
+/* The transfers of a low-precision V-cycle (Algorithm 1's restricted
+ * residual and interpolate-and-correct, R = 2^-dim P^T), run by the same
+ * kernels the cycle launches: precision CS_FP32 takes float vectors and the
+ * cascade's FP32 operator copy (needs lowp >= 1); CS_BF16 takes bfloat16
+ * vectors and the BF16 operator copy (needs lowp = 2).  FP64 transfers are
+ * cs_residual_restrict / cs_prolong_correct.
+ *   b, x: device vectors of `level` (N_level values); rc: N_{level+1};
+ *   xc: N_{level+1}; x is updated in place by the prolongation.
+ * The FP32 restriction forms the fine residual in the cascade's own FP32
+ * scratch vector of that level, so calls on one cascade must not overlap
+ * on the GPU.  Errors: CS_ERR_ARG (null pointer, bad level, precision or
+ * missing lowp copies). */
+cs_status cs_residual_restrict_lowp(const cs_hierarchy *h, cs_cascade *c, int level, int precision,
+                                    const void *b, const void *x, void *rc, cs_stream stream);
+cs_status cs_prolong_correct_lowp(const cs_hierarchy *h, cs_cascade *c, int level, int precision,
+                                  const void *xc, void *x, cs_stream stream);
+
+/* x = A_c^-1 b on the coarsest level (bottom-level direct solve, FP64:
+ * Cholesky when A_c is symmetric to 1e-14 of its largest entry, else LU
+ * with partial pivoting; applied as the precomputed dense inverse). */
 cs_status cs_coarse_solve(const cs_hierarchy *h, const double *b, double *x, cs_stream stream);
 
 /* r = b - A x on `level`; if norm2 != NULL, *norm2 (HOST) receives ||r||_2

@@ -245,12 +245,18 @@ def vcycle(h: Hierarchy, c: Cascade, b, x=None, mu_pre: int = 1, mu_post: int = 
 
 def solve(h: Hierarchy, c: Cascade, b, x=None, method: str = "stationary", mu_pre: int = 1,
           mu_post: int = 1, rf: bool = True, tol: float = 1e-10, maxit: int = 100, restart: int = 30):
-    """Returns (x, iterations or -1, history, final relative true residual)."""
+    """Returns (x, iterations or -1, history, final relative true residual).
+
+    method: "stationary" (x <- V(x, b)), "gmres" (left-preconditioned
+    restarted GMRES, Sec. 3.1; history = preconditioned residual estimates
+    ||M r|| / ||M b||) or "gmres_right" (the cycle applied on the right,
+    minimising the true residual; history = ||b - A x|| / ||b|| estimates)."""
     x = np.zeros(h.N(0)) if x is None else _f64(x).copy()
     hist = np.zeros(2 * maxit + 4)
     nh = C.c_int(0)
     fin = C.c_double(0.0)
-    it = _lib.ora_solve(h._h, c._c, 0 if method == "stationary" else 1, mu_pre, mu_post, int(rf), tol,
+    code = {"stationary": 0, "gmres": 1, "gmres_right": 2}[method]
+    it = _lib.ora_solve(h._h, c._c, code, mu_pre, mu_post, int(rf), tol,
                         maxit, restart, _ptr(_f64(b)), _ptr(x), _ptr(hist), C.byref(nh), C.byref(fin))
     return x, int(it), hist[: nh.value].copy(), float(fin.value)
 

@@ -399,10 +399,27 @@ static void factor_coarsest(ora_hier *h) {
     h->cpiv = xmalloc(sizeof(int) * (size_t)n);
     for (int i = 0; i < n; ++i)
         for (int64_t p = A->rp[i]; p < A->rp[i + 1]; ++p) h->cfac[(size_t)i * n + A->ci[p]] += A->v[p];
+    /* Algorithm 1's bottom-level direct solve must solve A_c itself.  chol()
+     * reads only the lower triangle, so it is taken only when A_c is
+     * symmetric (to 1e-14 of its largest entry) and every pivot is positive;
+     * otherwise LU with partial pivoting. */
+    double amax = 0.0, asym = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double a = fabs(h->cfac[(size_t)i * n + j]);
+            double d = fabs(h->cfac[(size_t)i * n + j] - h->cfac[(size_t)j * n + i]);
+            if (a > amax) amax = a;
+            if (d > asym) asym = d;
+        }
     double *tmp = xmalloc(sizeof(double) * (size_t)n * n);
     memcpy(tmp, h->cfac, sizeof(double) * (size_t)n * n);
-    if (chol(tmp, n, 0.0) == 0) { h->cspd = 1; memcpy(h->cfac, tmp, sizeof(double) * (size_t)n * n); }
-    else { h->cspd = 0; lu(h->cfac, n, h->cpiv); }
+    if (asym <= 1e-14 * amax && chol(tmp, n, 0.0) == 0) {
+        h->cspd = 1;
+        memcpy(h->cfac, tmp, sizeof(double) * (size_t)n * n);
+    } else {
+        h->cspd = 0;
+        lu(h->cfac, n, h->cpiv);
+    }
     free(tmp);
 }
 
@@ -836,6 +853,73 @@ int ora_solve(const ora_hier *h, const ora_casc *c, int method, int mu_pre, int 
         }
         conv = rel <= tol;
         if (final_rel) *final_rel = rel;
+    } else if (method == 2) {
+        /* Right-preconditioned restarted GMRES (Sec. 3.1 with the cycle
+         * applied on the right): x_k minimises the TRUE residual
+         * ||b - A x|| over x_0 + span{Z_0..Z_{k-1}}, Z_j = M V_j, with V an
+         * orthonormal (modified Gram-Schmidt) basis of K_k(A M, r_0).  The
+         * Givens estimate |g_{j+1}| is ||b - A x_j|| itself, so the inner
+         * loop stops on the true residual. */
+        int m = restart;
+        double *V = xmalloc(sizeof(double) * (size_t)N * (m + 1));
+        double *Z = xmalloc(sizeof(double) * (size_t)N * m);
+        double *H = xcalloc((size_t)(m + 1) * m, sizeof(double));
+        double *cs = xmalloc(sizeof(double) * m), *sn = xmalloc(sizeof(double) * m);
+        double *g = xmalloc(sizeof(double) * (m + 1)), *y = xmalloc(sizeof(double) * m);
+        double rel = 1.0;
+        for (;;) {
+            ora_residual(h, 0, b, x, r); /* r = A x - b */
+            double beta = nrm2(r, N);
+            rel = beta / nb;
+            if (nh == 0) hist[nh++] = rel;
+            if (rel <= tol || it >= maxit) break;
+            for (int i = 0; i < N; ++i) V[i] = -r[i] / beta;
+            for (int i = 0; i <= m; ++i) g[i] = 0.0;
+            g[0] = beta;
+            int j;
+            for (j = 0; j < m && it < maxit; ++j) {
+                /* z_j = M v_j, w = A z_j */
+                double *z = Z + (size_t)j * N;
+                for (int i = 0; i < N; ++i) z[i] = 0.0;
+                ora_vcycle(h, c, mu_pre, mu_post, rf, V + (size_t)j * N, z);
+                ++it;
+                double *w = V + (size_t)(j + 1) * N;
+                csr_matvec(&h->A[0], z, w);
+                for (int i = 0; i <= j; ++i) {
+                    double d = 0.0;
+                    for (int q = 0; q < N; ++q) d += w[q] * V[(size_t)i * N + q];
+                    H[i * m + j] = d;
+                    for (int q = 0; q < N; ++q) w[q] -= d * V[(size_t)i * N + q];
+                }
+                double hn = nrm2(w, N);
+                H[(j + 1) * m + j] = hn;
+                if (hn > 0.0) for (int q = 0; q < N; ++q) w[q] /= hn;
+                for (int i = 0; i < j; ++i) {
+                    double a = H[i * m + j], bb = H[(i + 1) * m + j];
+                    H[i * m + j] = cs[i] * a + sn[i] * bb;
+                    H[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+                }
+                double a = H[j * m + j], bb = H[(j + 1) * m + j];
+                double d = sqrt(a * a + bb * bb);
+                cs[j] = d > 0 ? a / d : 1.0; sn[j] = d > 0 ? bb / d : 0.0;
+                H[j * m + j] = d; H[(j + 1) * m + j] = 0.0;
+                g[j + 1] = -sn[j] * g[j];
+                g[j] = cs[j] * g[j];
+                hist[nh++] = fabs(g[j + 1]) / nb;
+                if (fabs(g[j + 1]) <= tol * nb || hn == 0.0) { ++j; break; }
+            }
+            /* x += Z y, H y = g */
+            for (int i = j - 1; i >= 0; --i) {
+                double s = g[i];
+                for (int k = i + 1; k < j; ++k) s -= H[i * m + k] * y[k];
+                y[i] = s / H[i * m + i];
+            }
+            for (int i = 0; i < j; ++i)
+                for (int q = 0; q < N; ++q) x[q] += y[i] * Z[(size_t)i * N + q];
+        }
+        conv = rel <= tol;
+        if (final_rel) *final_rel = rel;
+        free(V); free(Z); free(H); free(cs); free(sn); free(g); free(y);
     } else {
         int m = restart;
         double *V = xmalloc(sizeof(double) * (size_t)N * (m + 1));

@@ -382,6 +382,37 @@ def prolong_correct(h, level, xc, x, stream=None):
                                                _stream(stream)), "cs_prolong_correct")
 
 
+def _lowp_vectors(ts, sizes, what):
+    torch = _torch()
+    for t, n in zip(ts, sizes):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"{what}: contiguous CUDA tensors of sizes {sizes} expected")
+    if all(t.dtype == torch.float32 for t in ts):
+        return _capi.CS_FP32
+    if all(t.dtype == torch.bfloat16 for t in ts):
+        return _capi.CS_BF16
+    raise TypeError(f"{what}: all float32 or all bfloat16 tensors expected")
+
+
+def residual_restrict_lowp(h, c, level, b, x, rc, stream=None):
+    """rc = R (A x - b) with the FP32 (float32 tensors) or BF16-storage
+    (bfloat16 tensors) kernels of a low-precision V-cycle."""
+    N, Nc = h.N(level), h.N(level + 1)
+    prec = _lowp_vectors((b, x, rc), (N, N, Nc), "residual_restrict_lowp")
+    _capi.check(_capi.lib().cs_residual_restrict_lowp(h.ptr, c.ptr, level, prec, C.c_void_p(b.data_ptr()),
+                                                      C.c_void_p(x.data_ptr()), C.c_void_p(rc.data_ptr()),
+                                                      _stream(stream)), "cs_residual_restrict_lowp")
+
+
+def prolong_correct_lowp(h, c, level, xc, x, stream=None):
+    """x <- x - P xc with the FP32 / BF16-storage kernels (dtype of the tensors)."""
+    N, Nc = h.N(level), h.N(level + 1)
+    prec = _lowp_vectors((xc, x), (Nc, N), "prolong_correct_lowp")
+    _capi.check(_capi.lib().cs_prolong_correct_lowp(h.ptr, c.ptr, level, prec, C.c_void_p(xc.data_ptr()),
+                                                    C.c_void_p(x.data_ptr()), _stream(stream)),
+                "cs_prolong_correct_lowp")
+
+
 def coarse_solve(h, b, x, stream=None):
     N = h.N(h.nlevels - 1)
     _capi.check(_capi.lib().cs_coarse_solve(h.ptr, _dev_ptr(b, N, "b"), _dev_ptr(x, N, "x"), _stream(stream)),

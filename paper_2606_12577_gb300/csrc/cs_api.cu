@@ -828,6 +828,46 @@ cs_status cs_prolong_correct(const cs_hierarchy *h, int level, const double *xc,
     return launch_prolong_correct<double>(h->lev[level], h->lev[level + 1], xc, x, x, (cudaStream_t)stream);
 }
 
+cs_status cs_residual_restrict_lowp(const cs_hierarchy *h, cs_cascade *c, int level, int precision, const void *b,
+                                    const void *x, void *rc, cs_stream stream) {
+    if (!h || !c || !b || !x || !rc) { set_error("null argument"); return CS_ERR_ARG; }
+    if (level < 0 || level + 1 >= h->nlev) { set_error("level %d has no coarser level", level); return CS_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Level &f = h->lev[level], &cl = h->lev[level + 1];
+    if (precision == CS_FP32) {
+        if (!c->lowp) { set_error("FP32 transfers need lowp"); return CS_ERR_ARG; }
+        const LowLevel &lo = c->lo[level];
+        return launch_residual_restrict<float>(f, cl, lo.A, (const float *)b, (const float *)x, (float *)rc, lo.t, s);
+    }
+    if (precision == CS_BF16) {
+        if (c->lo16.empty()) { set_error("BF16 transfers need lowp = 2"); return CS_ERR_ARG; }
+        const LowLevel16 &lo = c->lo16[level];
+        return launch_residual_restrict<__nv_bfloat16>(f, cl, lo.A, (const __nv_bfloat16 *)b,
+                                                       (const __nv_bfloat16 *)x, (__nv_bfloat16 *)rc, nullptr, s);
+    }
+    set_error("precision must be CS_FP32 or CS_BF16 (cs_residual_restrict takes FP64)");
+    return CS_ERR_ARG;
+}
+
+cs_status cs_prolong_correct_lowp(const cs_hierarchy *h, cs_cascade *c, int level, int precision, const void *xc,
+                                  void *x, cs_stream stream) {
+    if (!h || !c || !xc || !x) { set_error("null argument"); return CS_ERR_ARG; }
+    if (level < 0 || level + 1 >= h->nlev) { set_error("level %d has no coarser level", level); return CS_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Level &f = h->lev[level], &cl = h->lev[level + 1];
+    if (precision == CS_FP32) {
+        if (!c->lowp) { set_error("FP32 transfers need lowp"); return CS_ERR_ARG; }
+        return launch_prolong_correct<float>(f, cl, (const float *)xc, (const float *)x, (float *)x, s);
+    }
+    if (precision == CS_BF16) {
+        if (c->lo16.empty()) { set_error("BF16 transfers need lowp = 2"); return CS_ERR_ARG; }
+        return launch_prolong_correct<__nv_bfloat16>(f, cl, (const __nv_bfloat16 *)xc, (const __nv_bfloat16 *)x,
+                                                     (__nv_bfloat16 *)x, s);
+    }
+    set_error("precision must be CS_FP32 or CS_BF16 (cs_prolong_correct takes FP64)");
+    return CS_ERR_ARG;
+}
+
 cs_status cs_coarse_solve(const cs_hierarchy *h, const double *b, double *x, cs_stream stream) {
     if (!h || !b || !x) { set_error("null argument"); return CS_ERR_ARG; }
     if (h->cn == 0) { set_error("no coarsest-level factorisation"); return CS_ERR_UNSUPPORTED; }

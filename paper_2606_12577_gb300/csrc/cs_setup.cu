@@ -476,14 +476,35 @@ __global__ void k_assemble_dense(Grid g, int nst, const int *__restrict__ offs, 
     }
 }
 
-// Single-CTA dense factorisation and inverse: Cholesky (SPD), else LU with
-// partial pivoting.  status[0] = 0 ok, 1 singular.
+// Single-CTA dense factorisation and inverse (Algorithm 1's bottom-level
+// direct solve): Cholesky when M is symmetric to 1e-14 of its largest entry
+// and every pivot is positive, else LU with partial pivoting (the Cholesky
+// loop reads only the lower triangle, so it would solve another matrix when
+// M is not symmetric).  Launched with 256 threads.  status[0] = 0 ok,
+// 1 singular.
 __global__ void k_factor_inverse(int n, double *M, double *W, double *Inv, int *piv, int *status) {
     __shared__ int bad;
     __shared__ int spd;
+    __shared__ double red_max[256], red_asym[256];
     int tid = threadIdx.x, nt = blockDim.x;
-    for (int64_t t = tid; t < (int64_t)n * n; t += nt) W[t] = M[t];
-    if (tid == 0) { bad = 0; spd = 1; }
+    double amax = 0.0, asym = 0.0;
+    for (int64_t t = tid; t < (int64_t)n * n; t += nt) {
+        W[t] = M[t];
+        int i = (int)(t / n), j = (int)(t % n);
+        amax = fmax(amax, fabs(M[t]));
+        asym = fmax(asym, fabs(M[t] - M[(int64_t)j * n + i]));
+    }
+    red_max[tid] = amax;
+    red_asym[tid] = asym;
+    __syncthreads();
+    for (int w = nt / 2; w > 0; w >>= 1) {
+        if (tid < w) {
+            red_max[tid] = fmax(red_max[tid], red_max[tid + w]);
+            red_asym[tid] = fmax(red_asym[tid], red_asym[tid + w]);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) { bad = 0; spd = red_asym[0] <= 1e-14 * red_max[0]; }
     __syncthreads();
     for (int k = 0; k < n && spd; ++k) {  // right-looking Cholesky on W (lower)
         if (tid == 0) {

@@ -332,6 +332,22 @@ def batch_problem(k: int, nmin: int = 33, nmax: int = 513, mmax: int = 8, corr: 
     return A, m, b
 
 
+def nonsymmetric_3d(n: int, seed: int) -> Stencil:
+    """3D 7-point operator with unequal couplings in the two directions of
+    every edge, each ~ -U[0.5, 2] from stream ``700 + 10 seed + s`` for
+    stencil entry s, and a diagonal 0.1 above the row sum of their
+    magnitudes: a nonsymmetric, diagonally dominant M-matrix (a
+    convection-diffusion-like test operator whose Galerkin levels are
+    nonsymmetric 27-point operators)."""
+    offs = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+    N = n ** 3
+    coeff = np.zeros((7, N))
+    for s in range(1, 7):
+        coeff[s] = -uniform(700 + 10 * seed + s, N, 0.5, 2.0)
+    coeff[0] = -coeff[1:].sum(axis=0) + 0.1
+    return Stencil(3, (n, n, n), offs, coeff, False, name=f"nonsym3d_{n}")
+
+
 def config_seed(config: int, problem: int = 0) -> int:
     """Seed of problem ``problem`` of workload ``config`` (run seed 0)."""
     return 1000 * config + problem

@@ -427,6 +427,27 @@ def test_coarse_solve_is_direct():
     np.testing.assert_allclose(h.coarse_solve(b), np.linalg.solve(dense_ref.dense_from_stencil(A), b), rtol=1e-12)
 
 
+@pytest.mark.parametrize("n", [4, 8, 9])
+def test_coarse_solve_is_direct_nonsymmetric(n):
+    """Algorithm 1's bottom-level direct solve on a nonsymmetric operator: a
+    diagonally dominant M-matrix whose Cholesky pivots are all positive (so a
+    factorisation that reads one triangle would "succeed") must still be
+    solved exactly, here against numpy's LU solve of the dense coarsest
+    operator (n = 4: the operator itself; n = 8, 9: its Galerkin level)."""
+    A = problems.nonsymmetric_3d(n, 1)
+    h = oracle.Hierarchy(A)
+    M = h.dense(h.nlev - 1)
+    assert np.abs(M - M.T).max() > 0.01 * np.abs(M).max()  # genuinely nonsymmetric
+    np.linalg.cholesky(0.5 * (M + M.T))  # ...with an SPD symmetric part
+    b = problems.uniform(14, M.shape[0])
+    x = h.coarse_solve(b)
+    ref = np.linalg.solve(M, b)
+    assert np.abs(x - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert np.linalg.norm(M @ x - b) <= 1e-13 * np.linalg.norm(b) * np.linalg.cond(M)
+    if n == 4:
+        np.testing.assert_allclose(M, dense_ref.dense_from_stencil(A), rtol=0, atol=0)
+
+
 @pytest.mark.parametrize("kind", ["additive", "multiplicative"])
 def test_vcycle_symmetry_rf(kind):
     """RF gives V = V^T for symmetric A (SM Sec. 3); FF in general does not."""
@@ -504,3 +525,78 @@ def test_metrics():
     # C_d(nu, eta) = eta (1 + (2 nu + 1) / (1 - 2^-d)) (eq. cost)
     assert oracle.cost_cd(2, 1, 1.0) == pytest.approx(1 + 3 / 0.75)
     assert oracle.cost_cd(3, 2, 0.5) == pytest.approx(0.5 * (1 + 5 / 0.875))
+
+
+@pytest.mark.parametrize("kind", ["additive", "multiplicative"])
+def test_right_gmres_minimises_true_residual(kind):
+    """Right-preconditioned GMRES (the cycle M applied on the right): after k
+    Arnoldi steps x_k minimises ||b - A x|| over x_0 + M K_k(A M, r_0).  Here
+    that space is formed explicitly from the dense A and the dense M (the
+    cycle applied to unit vectors), orthonormalised by QR, and the least
+    squares problem solved by numpy; the oracle's residual history and its
+    iterate after k steps must agree."""
+    A = _small_problem(2, 9, seed=93)
+    h = oracle.Hierarchy(A)
+    assert h.nlev >= 2
+    c = oracle.Cascade(h, kind, nu=2)
+    N = A.N
+    Ad = dense_ref.dense_from_stencil(A)
+    M = np.zeros((N, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        M[:, j] = oracle.vcycle(h, c, e)
+    b = problems.uniform(17, N)
+    nb = np.linalg.norm(b)
+    K = 6
+    x, it, hist, fin = oracle.solve(h, c, b, method="gmres_right", tol=1e-300, maxit=K, restart=30)
+    assert it == -1 and len(hist) == K + 1
+    assert hist[0] == pytest.approx(1.0)
+    Z = []
+    v = b.copy()
+    for k in range(1, K + 1):
+        Z.append(M @ v)
+        v = Ad @ Z[-1]
+        Q, _ = np.linalg.qr(np.array(Z).T)
+        y, *_ = np.linalg.lstsq(Ad @ Q, b, rcond=None)
+        xk = Q @ y
+        rk = np.linalg.norm(b - Ad @ xk) / nb
+        assert hist[k] == pytest.approx(rk, rel=1e-8), k
+    assert np.abs(x - xk).max() <= 1e-9 * np.abs(xk).max()
+    assert fin == pytest.approx(np.linalg.norm(b - Ad @ x) / nb, rel=1e-10)
+
+
+def test_right_gmres_finite_termination_and_convergence():
+    """One level: M is the direct solve, so one step ends the solve.  On a
+    multilevel manufactured problem the true residual reaches 1e-10 and the
+    error is at the level cond(A) * 1e-10."""
+    A = _small_problem(2, 3, seed=91)
+    h = oracle.Hierarchy(A, max_levels=1)
+    c = oracle.Cascade(h, "additive", nu=1)
+    b = problems.uniform(16, A.N)
+    x, it, hist, fin = oracle.solve(h, c, b, method="gmres_right", tol=1e-12)
+    assert it == 1 and fin < 1e-12
+    A = problems.poisson(2, 31)
+    h = oracle.Hierarchy(A)
+    c = oracle.Cascade(h, "multiplicative", nu=3)
+    xs = problems.uniform(15, A.N)
+    b = dense_ref.dense_from_stencil(A) @ xs
+    x, it, hist, fin = oracle.solve(h, c, b, method="gmres_right", tol=1e-10)
+    assert it > 0 and fin <= 1e-10 and hist[-1] <= 1e-10
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-8
+
+
+def test_right_gmres_controls_the_true_residual_at_high_contrast():
+    """The reason the right-preconditioned form exists here: on the elliptic
+    interface family (contrast 1e8) the left-preconditioned GMRES stops each
+    cycle on the preconditioned residual ||M r||, which no longer bounds
+    ||r||, and stagnates; the right-preconditioned GMRES minimises ||r||
+    and reaches 1e-10."""
+    A = problems.interface2d(255, 200)
+    h = oracle.Hierarchy(A, bs=2)
+    c = oracle.Cascade(h, "additive", nu=3)
+    b = problems.rhs(A.N, 9)
+    _, itr, _, finr = oracle.solve(h, c, b, method="gmres_right", tol=1e-10, maxit=100)
+    _, itl, _, finl = oracle.solve(h, c, b, method="gmres", tol=1e-10, maxit=100)
+    assert itr > 0 and finr <= 1e-10
+    assert itl == -1 and finl > 1e3 * finr
