@@ -12,7 +12,8 @@ FP64) and runs the cycle in FP32 inside FP64 iterative refinement; the
 plain FP64 form (stationary FP64 V-cycle iteration) is timed
 beside it.  Also reported: the sweep kernel's achieved HBM bandwidth
 against the measured copy peak, the same step end to end through the C ABI
-with host buffers, and the FP64 CPU oracle on a bounded sample.
+with host buffers, and the FP64 CPU oracle on the whole workload (all host
+threads) and on a one-thread sample.
 
 ``--impl reference`` times the oracle alone (the baseline arm).
 Multi-GPU (torchrun): independent replicas, one problem per rank.
@@ -50,13 +51,17 @@ def args_():
     p.add_argument("--nu", type=int, default=3)
     p.add_argument("--mu", type=int, default=2)
     p.add_argument("--order", default="RF")
-    p.add_argument("--cpu-n", type=int, default=64, help="side of the oracle's bounded sample")
+    p.add_argument("--cpu-n", type=int, default=128, help="side of the oracle's one-thread sample")
     p.add_argument("--no-extras", action="store_true", help="time the chosen form only")
     p.add_argument("--learned-meshes", type=int, default=128, help="training meshes of the learned setup")
     p.add_argument("--learned-n", type=int, default=127, help="interior nodes per side of a training mesh")
     p.add_argument("--learned-steps", type=int, default=6000, help="Adam steps")
     p.add_argument("--interface-maxit", type=int, default=300, help="GMRES steps allowed on the interface workload")
-    p.add_argument("--batch-count", type=int, default=32, help="problems of the batched workload timed")
+    p.add_argument("--batch-count", type=int, default=512, help="problems of the batched workload timed")
+    p.add_argument("--batch-fp64-count", type=int, default=32,
+                   help="problems on which FP32 and FP64 cycles are compared")
+    p.add_argument("--krylov", default="gmres_right", choices=["gmres", "gmres_right"],
+                   help="GMRES form of the interface and batched workloads (cycle applied left or right)")
     p.add_argument("--batch-maxit", type=int, default=400, help="GMRES steps allowed per problem")
     p.add_argument("--batch-single", type=int, default=4, help="problems also solved on the single-problem path")
     p.add_argument("--batch-profile-count", type=int, default=16, help="problems in the batch profile case")
@@ -148,33 +153,71 @@ def oracle_step(n, kind, nu, mu, order):
     return dt, it, fin
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu; /proc/cpuinfo; the platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(a, n_full):
-    dt, it, fin = oracle_step(a.cpu_n, a.kind, a.nu, a.mu, a.order)
-    scale = (n_full / a.cpu_n) ** 3
-    return {"value": dt * 1e3 * scale, "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle, same problem family at {a.cpu_n}^3 (setup + stationary solve, "
-                      f"{it} cycles, {dt:.2f} s), scaled by N_full/N_sample = {scale:.0f} (O(N) method)"}
+    """The FP64 oracle on the host cores: the whole workload on every host
+    thread (OpenMP over rows and blocks; results are bitwise those of one
+    thread), and one thread on a --cpu-n^3 sample of the same family.
+    Measured, not scaled."""
+    import oracle
+    ncores = os.cpu_count() or 1
+    oracle.set_threads(ncores)
+    dt, it, fin = oracle_step(n_full, a.kind, a.nu, a.mu, a.order)
+    oracle.set_threads(1)
+    dt1, it1, _ = oracle_step(a.cpu_n, a.kind, a.nu, a.mu, a.order)
+    oracle.set_threads(ncores)
+    return {"value": dt * 1e3, "unit": "ms", "cores": ncores, "threads": ncores, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": f"the whole workload: FP64 oracle, {n_full}^3, setup + stationary solve to 1e-10 "
+                      f"({it} cycles, final {fin:.2e}) on {ncores} host threads; measured, not scaled",
+            "one_thread": {"value": dt1 * 1e3, "unit": "ms", "threads": 1,
+                           "workload": f"the same family at {a.cpu_n}^3 (setup + solve, {it1} cycles), "
+                                       f"one thread, measured, not scaled"}}
 
 
 def run_reference(a):
+    """The baseline arm: each step is the whole workload (setup + solve to
+    1e-10) in the FP64 oracle on every host thread."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import oracle
     cfg = config(a)
+    ncores = os.cpu_count() or 1
+    oracle.set_threads(ncores)
     for _ in range(a.warmup):
-        oracle_step(a.cpu_n, a.kind, a.nu, a.mu, a.order)
+        oracle_step(a.n, a.kind, a.nu, a.mu, a.order)
     ts = []
     for _ in range(a.steps):
-        dt, it, fin = oracle_step(a.cpu_n, a.kind, a.nu, a.mu, a.order)
+        dt, it, fin = oracle_step(a.n, a.kind, a.nu, a.mu, a.order)
         ts.append(dt)
-    scale = (a.n / a.cpu_n) ** 3
-    v = statistics.mean(ts) * 1e3 * scale
+    v = statistics.mean(ts) * 1e3
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: the FP64 oracle on the same problem at {a.cpu_n}^3 "
-                                       f"(setup + stationary solve to 1e-10), time scaled by {scale:.0f} = N ratio"},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": ncores, "threads": ncores, "kind": "oracle",
+                             "cpu_model": cpu_model(),
+                             "sample": f"each step: the whole workload in the FP64 oracle ({a.n}^3, setup + "
+                                       f"stationary solve to 1e-10, {it} cycles) on {ncores} host threads; "
+                                       f"measured, not scaled"},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -268,10 +311,11 @@ def learned_section(a, cmg, problems, dev):
 def interface_section(a, cmg, problems, dev):
     """Elliptic interface workload: 1024^2, ~200 inclusions (contrast
     1e-4..1e4), 2x2-node blocks, additive nu = 3, 32 seeded RHS, GMRES(30)
-    with V(1,1)-RF FP32 cycles to 1e-10 per RHS (at most --interface-maxit
-    steps).  The 32 RHS are solved together in one batched launch (RHS
-    contiguous per node, block steps over (block, RHS) items); the
-    single-RHS path solves the first RHS for comparison."""
+    (--krylov: the cycle applied on the right by default) with V(1,1)-RF FP32
+    cycles to 1e-10 per RHS (at most --interface-maxit steps).  The 32 RHS
+    are solved together in one batched launch (RHS contiguous per node,
+    block steps over (block, RHS) items); the single-RHS path solves the
+    first RHS for comparison."""
     import torch
     Ai = problems.interface2d(1024)
     m = 32
@@ -284,7 +328,7 @@ def interface_section(a, cmg, problems, dev):
     e[0].record(s)
     hs, cs = cmg.setup_many([Ai], kind="additive", nu=3, lowp=True, block=2)
     e[1].record(s)
-    bt = cmg.Batch(hs, cs, [m], precision="fp32", method="gmres", autotune=True)
+    bt = cmg.Batch(hs, cs, [m], precision="fp32", method=a.krylov, autotune=True)
     x = torch.zeros_like(bd)
     bt.solve([bd], [x], tol=1e-10, maxit=2, raise_on_error=False)  # warm-up (graph)
     x.zero_()
@@ -298,7 +342,8 @@ def interface_section(a, cmg, problems, dev):
     rel = []
     Xm = x.view(Ai.N, m)
     out = {"workload": "elliptic interface 1024^2, 200 inclusions (contrast 1e-4..1e4), 2x2-node blocks, additive "
-                       "nu=3, 32 RHS, GMRES(30) V(1,1) RF FP32 cycles to 1e-10, the 32 RHS in one batched launch",
+                       f"nu=3, 32 RHS, {a.krylov}(30) V(1,1) RF FP32 cycles to 1e-10, the 32 RHS in one batched launch",
+           "krylov": a.krylov,
            "setup_ms": e[0].elapsed_time(e[1]), "solve_ms": e[2].elapsed_time(e[3]),
            "gmres_steps": info.iterations, "all_converged": bool(info.converged),
            "worst_rel_residual": float(info.final_rel_residual), "gpu_launches": int(launches),
@@ -307,7 +352,7 @@ def interface_section(a, cmg, problems, dev):
     x1 = torch.zeros(Ai.N, dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
     e[2].record(s)
-    i1 = cmg.solve(hs[0], cs[0], bd.view(Ai.N, m)[:, 0].contiguous(), x1, method="gmres", precision="fp32",
+    i1 = cmg.solve(hs[0], cs[0], bd.view(Ai.N, m)[:, 0].contiguous(), x1, method=a.krylov, precision="fp32",
                    tol=1e-10, maxit=a.interface_maxit, raise_on_error=False)
     e[3].record(s)
     torch.cuda.synchronize()
@@ -318,26 +363,62 @@ def interface_section(a, cmg, problems, dev):
     return out
 
 
+def stencil_rel_residual(A, x, b, m, dev):
+    """max over right-hand sides of ||b - A x|| / ||b|| for a 2D stencil
+    operator (RHS-contiguous vectors), in FP64 torch arithmetic."""
+    import torch
+    nx, ny = A.n[0], A.n[1]
+    X = x.view(ny, nx, m)
+    Bm = b.view(ny, nx, m)
+    C = torch.tensor(A.coeff, dtype=torch.float64, device=dev).view(-1, ny, nx, 1)
+    Y = torch.zeros_like(X)
+    for s_, (dx, dy, _) in enumerate(A.offsets):
+        sh = torch.zeros_like(X)
+        sh[max(-dy, 0):ny + min(-dy, 0), max(-dx, 0):nx + min(-dx, 0)] = \
+            X[max(dy, 0):ny + min(dy, 0), max(dx, 0):nx + min(dx, 0)]
+        Y += C[s_] * sh
+    r = (Bm - Y).reshape(-1, m).norm(dim=0) / Bm.reshape(-1, m).norm(dim=0).clamp_min(1e-300)
+    return float(r.max())
+
+
+def _batch_problem(k):
+    import problems
+    return problems.batch_problem(k)
+
+
+def make_batch_problems(K):
+    """The first K problems of the batched workload, generated on the host
+    cores (a spawn pool: the parent already holds a CUDA context)."""
+    import multiprocessing as mpc
+    nproc = max(1, min(16, (os.cpu_count() or 1), K // 8))
+    if nproc == 1:
+        return [_batch_problem(k) for k in range(K)]
+    with mpc.get_context("spawn").Pool(nproc) as pool:
+        return pool.map(_batch_problem, range(K), chunksize=4)
+
+
 def batch_section(a, cmg, problems, dev):
     """Batched solve (many uneven problems): the first ``--batch-count``
-    problems of the batched workload (2D variable-coefficient Poisson, sides
-    U{33..513}, 1..8 RHS each, correlated log-uniform coefficients on
-    [1e-3, 1e3]), red-black multiplicative nu = 3, V(1,1) RF, GMRES(30) to
-    1e-10 per RHS.  One persistent cooperative launch per solve (autotuned
-    schedule), against the single-problem path solving each RHS of the first
-    problems in turn."""
+    problems (default all 512) of the batched workload (2D
+    variable-coefficient Poisson, sides U{33..513}, 1..8 RHS each,
+    correlated log-uniform coefficients on [1e-3, 1e3]), red-black
+    multiplicative nu = 3, V(1,1) RF, GMRES(30) (--krylov) to 1e-10 per RHS
+    with FP32 cycles: one persistent cooperative launch per solve (autotuned
+    schedule).  On the first ``--batch-fp64-count`` problems FP32 and FP64
+    cycles are compared, and the single-problem path solves each RHS of the
+    first problems in turn."""
     import numpy as np
     import torch
     K = a.batch_count
     t0 = time.perf_counter()
-    P = [problems.batch_problem(k) for k in range(K)]
+    P = make_batch_problems(K)
     t_gen = time.perf_counter() - t0
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {"workload": f"first {K} problems of the 512-problem batch: 2D variable-coefficient Poisson, sides "
                        "U{33..513}, 1..8 RHS, log-uniform coefficients [1e-3,1e3] (correlation 8h); multiplicative "
-                       "nu=3 red-black, V(1,1) RF, GMRES(30) to 1e-10 per RHS",
-           "problems": K, "unknowns": int(sum(A.N for A, _, _ in P)),
+                       f"nu=3 red-black, V(1,1) RF, {a.krylov}(30) to 1e-10 per RHS",
+           "krylov": a.krylov, "problems": K, "unknowns": int(sum(A.N for A, _, _ in P)),
            "rhs_unknowns": int(sum(A.N * m for A, m, _ in P)), "generate_s": t_gen}
     cmg.setup_many([A for A, _, _ in P[:2]], kind="multiplicative", nu=3, lowp=True)  # warm-up
     torch.cuda.synchronize()
@@ -346,27 +427,41 @@ def batch_section(a, cmg, problems, dev):
     e1.record(s)
     torch.cuda.synchronize()
     out["setup_ms"] = e0.elapsed_time(e1)
-    t0 = time.perf_counter()
     bs = [torch.tensor(b, device=dev) for _, _, b in P]
-    for prec in ("fp32", "fp64"):
-        bt = cmg.Batch(hs, cs, [m for _, m, _ in P], precision=prec, method="gmres", autotune=(prec == "fp32"))
-        if prec == "fp32":
-            out["autotune_s"] = time.perf_counter() - t0
-            out["schedule"] = bt.config()
-        xs = [torch.zeros_like(b) for b in bs]
+
+    def run(nprob, prec, tune):
+        t0 = time.perf_counter()
+        bt = cmg.Batch(hs[:nprob], cs[:nprob], [m for _, m, _ in P[:nprob]], precision=prec, method=a.krylov,
+                       autotune=tune)
+        plan_s = time.perf_counter() - t0
+        xs = [torch.zeros_like(b) for b in bs[:nprob]]
         torch.cuda.synchronize()
         l0 = cmg.kernel_launches()
         e0.record(s)
-        infos = bt.solve(bs, xs, tol=1e-10, maxit=a.batch_maxit, raise_on_error=False)
+        infos = bt.solve(bs[:nprob], xs, tol=1e-10, maxit=a.batch_maxit, raise_on_error=False)
         e1.record(s)
         torch.cuda.synchronize()
         its = [i.iterations for i in infos]
-        out[f"gmres_{prec}_cycles"] = {"solve_ms": e0.elapsed_time(e1), "converged": int(sum(i.converged for i in infos)),
-                                       "iterations_min_median_max": [int(np.min(its)), int(np.median(its)),
-                                                                     int(np.max(its))],
-                                       "worst_rel_residual": float(max(i.final_rel_residual for i in infos)),
-                                       "gpu_launches": int(cmg.kernel_launches() - l0)}
-        del bt
+        res = {"problems": nprob, "solve_ms": e0.elapsed_time(e1), "converged": int(sum(i.converged for i in infos)),
+               "all_converged": bool(all(i.converged for i in infos)),
+               "iterations_min_median_max": [int(np.min(its)), int(np.median(its)), int(np.max(its))],
+               "worst_rel_residual": float(max(i.final_rel_residual for i in infos)),
+               "gpu_launches": int(cmg.kernel_launches() - l0), "plan_s": plan_s,
+               "plan_bytes": int(bt.nbytes())}
+        if tune:
+            res["schedule"] = bt.config()
+        # the true residual of every problem and RHS, recomputed here from the
+        # stencil in FP64 with plain tensor arithmetic (a check beside the
+        # solver's own residual, outside the timed region)
+        res["checked_worst_rel_residual"] = max(
+            stencil_rel_residual(P[p][0], xs[p], bs[p], P[p][1], dev) for p in range(nprob))
+        del bt, xs
+        torch.cuda.empty_cache()
+        return res
+
+    out["gmres_fp32_cycles"] = run(K, "fp32", True)
+    nsub = min(K, a.batch_fp64_count)
+    out[f"first_{nsub}"] = {"gmres_fp32_cycles": run(nsub, "fp32", False), "gmres_fp64_cycles": run(nsub, "fp64", False)}
     # the single-problem path on the first problems, one RHS at a time
     nsub = min(K, a.batch_single)
     torch.cuda.synchronize()
@@ -378,7 +473,7 @@ def batch_section(a, cmg, problems, dev):
         B = bs[p].view(A.N, m)
         for r in range(m):
             x1 = torch.zeros(A.N, dtype=torch.float64, device=dev)
-            conv += cmg.solve(hs[p], cs[p], B[:, r].contiguous(), x1, method="gmres", precision="fp32", tol=1e-10,
+            conv += cmg.solve(hs[p], cs[p], B[:, r].contiguous(), x1, method=a.krylov, precision="fp32", tol=1e-10,
                               maxit=a.batch_maxit, raise_on_error=False).converged
     e1.record(s)
     torch.cuda.synchronize()

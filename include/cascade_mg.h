@@ -239,8 +239,8 @@ cs_status cs_residual(const cs_hierarchy *h, int level, const double *b, const d
  * the operator and Lambda directly; the ping-pong vector that cs_smooth takes
  * from its hierarchy comes from a fixed 16 MiB device array inside the
  * library (2,097,152 doubles), which every GPU that loads the library keeps
- * until the process exits.  Nothing is allocated and no allocating library
- * routine is called.
+ * until the process exits.  No call allocates device memory or calls an
+ * allocating library routine (but see the first call on a device below).
  *
  * Computes the same thing as cs_smooth: one application of the depth-nu
  * cascade (forward, or reverse when reverse != 0), x updated in place.
@@ -256,7 +256,14 @@ cs_status cs_residual(const cs_hierarchy *h, int level, const double *b, const d
  *   kind:    CS_ADDITIVE or CS_MULTIPLICATIVE (red-black).
  * The first call on a device looks up the device address of the internal
  * array (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the one array and leave
+ * call before any stream capture.  Under lazy module loading (the CUDA
+ * default) that first call, or the first kernel launch, also loads the
+ * library's device code on the device, which creates the array and the code
+ * there and may synchronise: make one warm-up call per device outside any
+ * capture and outside latency-critical regions.  coeff, lam, b and x must be
+ * device memory of the current device (else CS_ERR_ARG), and the grid must
+ * fit the node kernels' launch (ny <= 262,140, nz <= 65,535; else
+ * CS_ERR_ARG).  All calls share the one array and leave
  * their last intermediate vector in it; every step overwrites all N entries
  * it later reads, so nothing needs clearing between calls.  Calls that
  * overlap on the GPU (other streams, other host threads) race on the array:
@@ -265,19 +272,25 @@ cs_status cs_smooth_noalloc(int dim, const int *n, int box, const double *coeff,
                             int kind, int reverse, const double *b, double *x, cs_stream stream);
 
 /* ---------------------------------------------------------------- solve */
-enum { CS_STATIONARY = 0, CS_GMRES = 1, CS_REFINE = 2 };
+enum { CS_STATIONARY = 0, CS_GMRES = 1, CS_REFINE = 2, CS_GMRES_RIGHT = 3 };
 
 typedef struct {
     int method;      /* CS_STATIONARY: x <- V(x,b); CS_GMRES: left-preconditioned
                         restarted GMRES with V0 (Sec. 3.1); CS_REFINE: FP64 iterative
-                        refinement x += V0(b - A x) with the cycle in cycle.precision */
+                        refinement x += V0(b - A x) with the cycle in cycle.precision;
+                        CS_GMRES_RIGHT: restarted GMRES with V0 applied on the right,
+                        in flexible form (Z_j = V0 v_j kept, x += Z y): it minimises the
+                        true residual ||b - A x||, so it also stops on it where the
+                        left form's preconditioned residual ||V0 r|| no longer bounds
+                        ||r|| (high-contrast coefficients); one more N-vector per step */
     int restart;     /* GMRES restart length (default 30) */
     int maxit;       /* maximum V-cycle applications (default 100) */
     double tol;      /* stop when ||b - A x||_2 / ||b||_2 <= tol (default 1e-10) */
     cs_vcycle_opts cycle;
     int host_buffers; /* 1: b and x are HOST pointers; copies happen inside the call */
     double *hist;    /* optional host array: relative residual per iteration (true residual
-                        for stationary/refine, preconditioned estimate for GMRES) */
+                        for stationary/refine, preconditioned estimate ||V0 r||/||V0 b|| for
+                        CS_GMRES, true-residual estimate ||r||/||b|| for CS_GMRES_RIGHT) */
     int hist_cap;
 } cs_solve_opts;
 
@@ -336,7 +349,13 @@ typedef struct {
                         Givens; inner steps stop on |g_{j+1}| <= tol ||M b||, restarts check
                         the FP64 true residual).  The Krylov vectors have the cycle precision:
                         with CS_FP32 a cycle also stops at |g_{j+1}| <= 1e-5 ||M r|| and the
-                        restart refines in FP64 (GMRES-based iterative refinement) */
+                        restart refines in FP64 (GMRES-based iterative refinement);
+                        CS_GMRES_RIGHT: the same with M applied on the right in flexible form
+                        (Z_j = M V_j kept in the cycle precision, A Z_j formed with the FP64
+                        operator, x += Z y in FP64), so |g_{j+1}| estimates ||b - A x|| and the
+                        inner steps stop on |g_{j+1}| <= tol ||b|| (or 1e-5 ||r|| with CS_FP32):
+                        the form that converges where the coefficients' contrast makes ||M r||
+                        a poor measure of ||r||; restart more vectors of [N0][m] per problem */
     int restart;     /* GMRES restart length (default 30, at most 64) */
 } cs_batch_opts;
 typedef struct {

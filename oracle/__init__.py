@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
@@ -76,6 +76,8 @@ def _load():
             "ora_coarse_solve": (None, [P, P, P]),
             "ora_vcycle": (None, [P, P, I, I, I, P, P]),
             "ora_solve": (I, [P, P, I, I, I, I, D, I, I, P, P, P, P, P]),
+            "ora_set_threads": (None, [I]),
+            "ora_max_threads": (I, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -83,6 +85,15 @@ def _load():
             f.argtypes = args
         _lib = lib
         return lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (results do not depend on it)."""
+    _load().ora_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_load().ora_max_threads())
 
 
 def _ptr(a: np.ndarray):

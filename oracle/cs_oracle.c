@@ -18,12 +18,36 @@
  *   - left-preconditioned GMRES driver .. Sec. 3.1
  *
  * No blocking, fusion or reordering beyond what those definitions state.
+ *
+ * Threads (OpenMP, optional): loops over independent rows or blocks carry a
+ * parallel-for pragma and nothing else changes; every row or block is
+ * computed by the same statements in the same order whatever the thread
+ * count, and the reductions (norms, inner products) stay serial, so results
+ * are bitwise identical for any number of threads (ora_set_threads).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #include <stdio.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+void ora_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+int ora_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 #define ORA_MAXLEV 24
 
@@ -57,6 +81,7 @@ static int cmp_int(const void *a, const void *b) {
 
 /* y = A x */
 static void csr_matvec(const csr *A, const double *x, double *y) {
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < A->n; ++i) {
         double s = 0.0;
         for (int64_t p = A->rp[i]; p < A->rp[i + 1]; ++p) s += A->v[p] * x[A->ci[p]];
@@ -82,40 +107,59 @@ static void csr_transpose(const csr *A, csr *T) {
     free(fill);
 }
 
-/* C = s * A B (Gustavson; columns sorted in each row). */
+/* C = s * A B (Gustavson; columns sorted in each row).  Two passes over the
+ * rows (count, then fill) so that rows can be formed in parallel; each row's
+ * sums are accumulated in the same order either way. */
 static void csr_spgemm(const csr *A, const csr *B, double s, csr *C) {
     C->n = A->n; C->m = B->m;
-    int *mark = xmalloc(sizeof(int) * (size_t)B->m);
-    double *acc = xcalloc((size_t)B->m, sizeof(double));
-    int *list = xmalloc(sizeof(int) * (size_t)B->m);
-    for (int j = 0; j < B->m; ++j) mark[j] = -1;
-    int64_t cap = A->rp[A->n] * 4 + 16, nnz = 0;
     C->rp = xmalloc(sizeof(int64_t) * ((size_t)A->n + 1));
-    C->ci = xmalloc(sizeof(int) * (size_t)cap);
-    C->v = xmalloc(sizeof(double) * (size_t)cap);
-    C->rp[0] = 0;
-    for (int i = 0; i < A->n; ++i) {
-        int cnt = 0;
-        for (int64_t p = A->rp[i]; p < A->rp[i + 1]; ++p) {
-            int k = A->ci[p];
-            double a = A->v[p];
-            for (int64_t q = B->rp[k]; q < B->rp[k + 1]; ++q) {
-                int j = B->ci[q];
-                if (mark[j] != i) { mark[j] = i; list[cnt++] = j; acc[j] = 0.0; }
-                acc[j] += a * B->v[q];
+    int *cnt = xmalloc(sizeof(int) * ((size_t)A->n + 1));
+#pragma omp parallel
+    {
+        int *mark = xmalloc(sizeof(int) * (size_t)B->m);
+        for (int j = 0; j < B->m; ++j) mark[j] = -1;
+#pragma omp for schedule(static)
+        for (int i = 0; i < A->n; ++i) {
+            int c = 0;
+            for (int64_t p = A->rp[i]; p < A->rp[i + 1]; ++p) {
+                int k = A->ci[p];
+                for (int64_t q = B->rp[k]; q < B->rp[k + 1]; ++q)
+                    if (mark[B->ci[q]] != i) { mark[B->ci[q]] = i; ++c; }
             }
+            cnt[i] = c;
         }
-        qsort(list, (size_t)cnt, sizeof(int), cmp_int);
-        if (nnz + cnt > cap) {
-            while (nnz + cnt > cap) cap *= 2;
-            C->ci = realloc(C->ci, sizeof(int) * (size_t)cap);
-            C->v = realloc(C->v, sizeof(double) * (size_t)cap);
-            if (!C->ci || !C->v) { fprintf(stderr, "oracle: oom\n"); abort(); }
-        }
-        for (int t = 0; t < cnt; ++t) { C->ci[nnz] = list[t]; C->v[nnz] = s * acc[list[t]]; ++nnz; }
-        C->rp[i + 1] = nnz;
+        free(mark);
     }
-    free(mark); free(acc); free(list);
+    C->rp[0] = 0;
+    for (int i = 0; i < A->n; ++i) C->rp[i + 1] = C->rp[i] + cnt[i];
+    int64_t nnz = C->rp[A->n];
+    C->ci = xmalloc(sizeof(int) * (size_t)(nnz ? nnz : 1));
+    C->v = xmalloc(sizeof(double) * (size_t)(nnz ? nnz : 1));
+#pragma omp parallel
+    {
+        int *mark = xmalloc(sizeof(int) * (size_t)B->m);
+        double *acc = xcalloc((size_t)B->m, sizeof(double));
+        int *list = xmalloc(sizeof(int) * (size_t)B->m);
+        for (int j = 0; j < B->m; ++j) mark[j] = -1;
+#pragma omp for schedule(static)
+        for (int i = 0; i < A->n; ++i) {
+            int c = 0;
+            for (int64_t p = A->rp[i]; p < A->rp[i + 1]; ++p) {
+                int k = A->ci[p];
+                double a = A->v[p];
+                for (int64_t q = B->rp[k]; q < B->rp[k + 1]; ++q) {
+                    int j = B->ci[q];
+                    if (mark[j] != i) { mark[j] = i; list[c++] = j; acc[j] = 0.0; }
+                    acc[j] += a * B->v[q];
+                }
+            }
+            qsort(list, (size_t)c, sizeof(int), cmp_int);
+            int64_t o = C->rp[i];
+            for (int t = 0; t < c; ++t) { C->ci[o + t] = list[t]; C->v[o + t] = s * acc[list[t]]; }
+        }
+        free(mark); free(acc); free(list);
+    }
+    free(cnt);
 }
 
 /* Structured stencil -> CSR.  Row i = ix + nx*(iy + ny*iz); entry s couples
@@ -542,13 +586,6 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
         E[i].c[0] = i; E[i].v[0] = 1.0;
     }
     srow *Enew = xcalloc((size_t)N, sizeof(srow));
-    int *mark = xmalloc(sizeof(int) * (size_t)N);
-    int *pos = xmalloc(sizeof(int) * (size_t)N);
-    int *bmark = xmalloc(sizeof(int) * (size_t)nb);
-    for (int i = 0; i < N; ++i) mark[i] = -1;
-    for (int b = 0; b < nb; ++b) bmark[b] = -1;
-    int *ulist = xmalloc(sizeof(int) * (size_t)N);
-    int stamp = 0;
     memset(lam, 0, sizeof(double) * (size_t)nu * (size_t)lamsize);
 
     double fr = 0.0;
@@ -557,6 +594,17 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
 
     for (int lev = 0; lev < nu; ++lev) {
         for (int k = 0; k < ncol; ++k) {
+#pragma omp parallel
+          {
+            /* per-thread scratch: column marks and positions, block marks */
+            int *mark = xmalloc(sizeof(int) * (size_t)N);
+            int *pos = xmalloc(sizeof(int) * (size_t)N);
+            int *bmark = xmalloc(sizeof(int) * (size_t)nb);
+            int *ulist = xmalloc(sizeof(int) * (size_t)N);
+            for (int i = 0; i < N; ++i) mark[i] = -1;
+            for (int b = 0; b < nb; ++b) bmark[b] = -1;
+            int stamp = 0;
+#pragma omp for schedule(dynamic, 64)
             for (int b = 0; b < nb; ++b) {
                 if (block_colour(h, l, kind, b) != k) continue;
                 int nbk = bptr[b + 1] - bptr[b];
@@ -652,6 +700,8 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
                 }
                 free(keep); free(Rb); free(Eb); free(G); free(C);
             }
+            free(mark); free(pos); free(bmark); free(ulist);
+          }
             /* commit colour k (all blocks for the additive form) */
             for (int b = 0; b < nb; ++b) {
                 if (block_colour(h, l, kind, b) != k) continue;
@@ -679,7 +729,7 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
                 for (int q = 0; q < nbk; ++q) Lb[p * nbk + q] *= w[rows[p]] * w[rows[q]];
         }
     for (int i = 0; i < N; ++i) { free(E[i].c); free(E[i].v); }
-    free(E); free(Enew); free(mark); free(pos); free(bmark); free(ulist); free(blk_of); free(w);
+    free(E); free(Enew); free(blk_of); free(w);
     csr_free(&A);
     return 0;
 }
@@ -741,6 +791,7 @@ void ora_casc_efrob(const ora_casc *c, int l, double *out) {
 void ora_residual(const ora_hier *h, int l, const double *b, const double *x, double *r) {
     const csr *A = &h->A[l];
     csr_matvec(A, x, r);
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < A->n; ++i) r[i] -= b[i];
 }
 
@@ -759,6 +810,7 @@ void ora_smooth(const ora_hier *h, const ora_casc *c, int l, int reverse, const 
         for (int kk = 0; kk < c->ncol; ++kk) {
             int K = reverse ? c->ncol - 1 - kk : kk;
             ora_residual(h, l, b, x, r);
+#pragma omp parallel for schedule(static)
             for (int bk = 0; bk < nb; ++bk) {
                 if (block_colour(h, l, c->kind, bk) != K) continue;
                 int nbk = bptr[bk + 1] - bptr[bk];
@@ -781,6 +833,7 @@ void ora_restrict(const ora_hier *h, int l, const double *r, double *rc) { csr_m
 /* x -= P xc */
 void ora_prolong_correct(const ora_hier *h, int l, const double *xc, double *x) {
     const csr *P = &h->P[l];
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < P->n; ++i) {
         double s = 0.0;
         for (int64_t p = P->rp[i]; p < P->rp[i + 1]; ++p) s += P->v[p] * xc[P->ci[p]];

@@ -339,6 +339,12 @@ def smooth_noalloc(dim, n, box, coeff, lam, nu, b, x, kind="additive", reverse=F
     nst = (27 if dim == 3 else 9) if box else 2 * dim + 1
     narr = (C.c_int * 3)(*[int(v) for v in nn])
     k = _capi.CS_MULTIPLICATIVE if kind == "multiplicative" else _capi.CS_ADDITIVE
+    torch = _torch()
+    for name, t in (("coeff", coeff), ("lam", lam), ("b", b), ("x", x)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on {t.device}, not on the current device cuda:{torch.cuda.current_device()}")
     _capi.check(_capi.lib().cs_smooth_noalloc(dim, narr, int(bool(box)), _dev_ptr(coeff, nst * N, "coeff"),
                                               _dev_ptr(lam, nu * N, "lam"), nu, k, int(bool(reverse)),
                                               _dev_ptr(b, N, "b"), _dev_ptr(x, N, "x"), _stream(stream)),
@@ -428,7 +434,8 @@ def residual(h, level, b, x, r, norm=False, stream=None):
     return float(nrm.value) if norm else None
 
 
-_METHODS = {"stationary": _capi.CS_STATIONARY, "gmres": _capi.CS_GMRES, "refine": _capi.CS_REFINE}
+_METHODS = {"stationary": _capi.CS_STATIONARY, "gmres": _capi.CS_GMRES, "refine": _capi.CS_REFINE,
+            "gmres_right": _capi.CS_GMRES_RIGHT}
 
 
 def solve(h, c, b, x, method="stationary", tol=1e-10, maxit=100, restart=30, mu_pre=1, mu_post=1, order="RF",
@@ -501,6 +508,9 @@ def setup_many(problems, kind="multiplicative", nu=3, lowp=True, coarse_max=4, b
     return hs, cs
 
 
+_BATCH_METHODS = {"refine": _capi.CS_REFINE, "gmres": _capi.CS_GMRES, "gmres_right": _capi.CS_GMRES_RIGHT}
+
+
 class Batch:
     """A planned batched solve over existing (hierarchy, cascade) pairs
     (``cs_batch_create``); ``solve`` runs one persistent cooperative launch.
@@ -515,8 +525,7 @@ class Batch:
         self.N = [h.N(0) for h in self.hs]
         o = _capi.cs_batch_opts(_capi.CS_FP32 if precision == "fp32" else _capi.CS_FP64,
                                 _capi.CS_RF if order == "RF" else _capi.CS_FF, mu_pre, mu_post, int(autotune),
-                                threads, tiles_per_cta, _capi.CS_GMRES if method == "gmres" else _capi.CS_REFINE,
-                                restart)
+                                threads, tiles_per_cta, _BATCH_METHODS[method], restart)
         hp = (C.c_void_p * self.nprob)(*[h.ptr for h in self.hs])
         cp = (C.c_void_p * self.nprob)(*[c.ptr for c in self.cs])
         mp = (C.c_int * self.nprob)(*self.nrhs)
@@ -566,7 +575,7 @@ def solve_batched(hs, cs, bs, xs, nrhs, tol=1e-10, maxit=100, mu_pre=1, mu_post=
     """One-shot batched solve (``cs_solve_batched``: plan without autotuning,
     solve, release)."""
     n = len(hs)
-    o = _capi.cs_solve_opts(_capi.CS_GMRES if method == "gmres" else _capi.CS_REFINE, restart, maxit, tol,
+    o = _capi.cs_solve_opts(_BATCH_METHODS[method], restart, maxit, tol,
                             _cycle_opts(mu_pre, mu_post, order, precision), 0, None, 0)
     hp = (C.c_void_p * n)(*[h.ptr for h in hs])
     cp = (C.c_void_p * n)(*[c.ptr for c in cs])

@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "CS_OK", -1: "CS_ERR_ARG", -2: "CS_ERR_CUDA", -3: "CS_ERR_NOM
 CS_ADDITIVE, CS_MULTIPLICATIVE = 0, 1
 CS_FP64, CS_FP32, CS_BF16 = 0, 1, 2
 CS_FF, CS_RF = 0, 1
-CS_STATIONARY, CS_GMRES, CS_REFINE = 0, 1, 2
+CS_STATIONARY, CS_GMRES, CS_REFINE, CS_GMRES_RIGHT = 0, 1, 2, 3
 
 
 class cs_stencil(C.Structure):

@@ -683,7 +683,7 @@ void cs_destroy_cascade(cs_cascade *c) {
     for (double *p : c->lam) dfree(p);
     for (auto &lo : c->lo) { dfree(lo.A); dfree(lo.lam); dfree(lo.b); dfree(lo.x); dfree(lo.t); }
     for (auto &lo : c->lo16) { dfree(lo.A); dfree(lo.lam); dfree(lo.b); dfree(lo.x); dfree(lo.t); }
-    dfree(c->fine_b32); dfree(c->fine_x32); dfree(c->gm_V); dfree(c->gm_h);
+    dfree(c->fine_b32); dfree(c->fine_x32); dfree(c->gm_V); dfree(c->gm_h); dfree(c->gm_Z);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     delete c;
 }
@@ -903,6 +903,8 @@ cs_status cs_residual(const cs_hierarchy *h, int level, const double *b, const d
 
 static cs_status gmres(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *o, const double *b, double *x,
                        double nb, cs_solve_info *info, cudaStream_t s);
+static cs_status gmres_right(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *o, const double *b,
+                             double *x, double nb, cs_solve_info *info, cudaStream_t s);
 
 cs_status cs_solve(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *o_in, const double *b_in, double *x_in,
                    cs_solve_info *info, cs_stream stream) {
@@ -912,7 +914,7 @@ cs_status cs_solve(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *o_
     if (o.tol <= 0) o.tol = 1e-10;
     if (o.restart <= 0) o.restart = 30;
     CSX_TRY(check_cycle_opts(h, c, &o.cycle));
-    if (o.method != CS_STATIONARY && o.method != CS_GMRES && o.method != CS_REFINE) {
+    if (o.method != CS_STATIONARY && o.method != CS_GMRES && o.method != CS_REFINE && o.method != CS_GMRES_RIGHT) {
         set_error("bad solve method");
         return CS_ERR_ARG;
     }
@@ -939,6 +941,8 @@ cs_status cs_solve(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *o_
         inf.converged = 1;
     } else if (o.method == CS_GMRES) {
         rc = gmres(h, c, &o, b, x, nb, &inf, s);
+    } else if (o.method == CS_GMRES_RIGHT) {
+        rc = gmres_right(h, c, &o, b, x, nb, &inf, s);
     } else {
         const bool lowp = o.cycle.precision == CS_FP32, bf16 = o.cycle.precision == CS_BF16;
         const int nred = residual_blocks(L);
@@ -1091,6 +1095,122 @@ static cs_status gmres(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts
         }
         CSX_CUDA(cudaMemcpyAsync(hd, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
         CSX_TRY(launch_axpy_multi(N, j, hd, V, x, s));
+        CSX_CUDA(cudaStreamSynchronize(s));  // y is a host buffer reused next restart
+    }
+    inf->final_rel_residual = rel;
+    inf->converged = rel <= o->tol;
+    if (!inf->converged) {
+        set_error("GMRES not converged after %d iterations (relative residual %g)", inf->iterations, rel);
+        return CS_ERR_NOTCONV;
+    }
+    return CS_OK;
+}
+
+// Right-preconditioned restarted GMRES in its flexible form: Z_j = M V_j is
+// kept and x += Z y, with V an orthonormal (modified Gram-Schmidt) basis
+// built from w = A Z_j.  With an FP64 cycle M is one fixed linear map and
+// this is right-preconditioned GMRES (x_k minimises ||b - A x|| over
+// x_0 + M K_k(A M, r_0)).  With FP32 / BF16 cycles M is that map only up to
+// the cycle's rounding; keeping Z makes b - A x_k = V_{k+1}(beta e_1 - H y)
+// hold up to FP64 rounding all the same, so the Givens estimate |g_{k+1}| is
+// the true residual and the solve stops on it.  Costs one vector of Z per
+// step beside V.
+static cs_status gmres_right(const cs_hierarchy *h, cs_cascade *c, const cs_solve_opts *o, const double *b,
+                             double *x, double nb, cs_solve_info *inf, cudaStream_t s) {
+    const Level &L = h->lev[0];
+    const int64_t N = L.g.N;
+    const int m = o->restart;
+    const bool lowp = o->cycle.precision == CS_FP32, bf16 = o->cycle.precision == CS_BF16;
+    if (c->gm_restart < m || !c->gm_Z) {
+        dfree(c->gm_V, s); dfree(c->gm_h, s); dfree(c->gm_Z, s);
+        c->gm_V = nullptr; c->gm_h = nullptr; c->gm_Z = nullptr;
+        CSX_TRY(dalloc_t(&c->gm_V, (size_t)(m + 1) * N, &c->bytes, s));
+        CSX_TRY(dalloc_t(&c->gm_Z, (size_t)m * N, &c->bytes, s));
+        CSX_TRY(dalloc_t(&c->gm_h, (size_t)(m + 2) * 2, &c->bytes, s));
+        c->gm_restart = m;
+    }
+    double *V = c->gm_V, *Z = c->gm_Z, *hd = c->gm_h;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), hh(m + 2);
+    // Z_j = M v: the cycle output of the right-hand side v, in FP64
+    auto precond_to = [&](const double *v, double *zout) -> cs_status {
+        if (lowp) {
+            CSX_TRY(launch_copy_d2f(N, v, c->lo[0].b, s));
+            CSX_TRY(run_v0(h, c, o->cycle, s));
+            CSX_CUDA(cudaMemsetAsync(zout, 0, sizeof(double) * N, s));
+            CSX_TRY(launch_axpy_f32(N, c->lo[0].x, zout, s));
+        } else if (bf16) {
+            CSX_TRY(launch_copy_d2bf(N, v, c->lo16[0].b, s));
+            CSX_TRY(run_v0(h, c, o->cycle, s));
+            CSX_CUDA(cudaMemsetAsync(zout, 0, sizeof(double) * N, s));
+            CSX_TRY(launch_axpy_bf16(N, c->lo16[0].x, zout, s));
+        } else {
+            CSX_CUDA(cudaMemcpyAsync(L.b, v, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+            CSX_TRY(run_v0(h, c, o->cycle, s));
+            CSX_CUDA(cudaMemcpyAsync(zout, L.x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        }
+        return CS_OK;
+    };
+    auto dot_to = [&](const double *a, const double *bb, double *dst) -> cs_status {
+        CSX_TRY(launch_dot(N, a, bb, h->red, NRED, s));
+        CSX_CUDA(cudaMemcpyAsync(dst, h->red + NRED, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        return CS_OK;
+    };
+    const int nred = residual_blocks(L);
+    double rel = 1.0;
+    cs_status rc = CS_OK;
+    for (;;) {
+        CSX_TRY(launch_residual64(L, L.A, b, x, L.t, nullptr, h->red, nred, s));  // L.t = b - A x
+        rel = std::sqrt(host_sum(h, nred, s, &rc)) / nb;
+        if (rc != CS_OK) return rc;
+        if (!std::isfinite(rel)) { set_error("GMRES diverged"); return CS_ERR_DIVERGED; }
+        if (inf->nhist == 0 && o->hist && inf->nhist < o->hist_cap) o->hist[inf->nhist++] = rel;
+        if (rel <= o->tol || inf->iterations >= o->maxit) break;
+        CSX_TRY(dot_to(L.t, L.t, hd));
+        CSX_TRY(launch_scale_dev(N, hd, V, L.t, s));
+        CSX_CUDA(cudaMemcpyAsync(hh.data(), hd, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CSX_CUDA(cudaStreamSynchronize(s));
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = std::sqrt(hh[0]);
+        int j;
+        for (j = 0; j < m && inf->iterations < o->maxit; ++j) {
+            double *zj = Z + (int64_t)j * N, *w = V + (int64_t)(j + 1) * N;
+            CSX_TRY(precond_to(V + (int64_t)j * N, zj));
+            ++inf->iterations;
+            CSX_TRY(launch_matvec64(L, L.A, zj, w, s));
+            for (int i = 0; i <= j; ++i) {
+                CSX_TRY(dot_to(w, V + (int64_t)i * N, hd + i));
+                CSX_TRY(launch_axpy_dev(N, hd + i, -1.0, V + (int64_t)i * N, w, s));
+            }
+            CSX_TRY(dot_to(w, w, hd + j + 1));
+            CSX_CUDA(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+            CSX_CUDA(cudaStreamSynchronize(s));
+            double hn = std::sqrt(hh[j + 1]);
+            if (hn > 0.0) CSX_TRY(launch_scale_dev(N, hd + j + 1, w, w, s));
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i];
+            H[(size_t)(j + 1) * m + j] = hn;
+            for (int i = 0; i < j; ++i) {
+                double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+            }
+            double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+            double d = std::sqrt(a * a + bb * bb);
+            cs[j] = d > 0 ? a / d : 1.0;
+            sn[j] = d > 0 ? bb / d : 0.0;
+            H[(size_t)j * m + j] = d;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            if (o->hist && inf->nhist < o->hist_cap) o->hist[inf->nhist++] = std::fabs(g[j + 1]) / nb;
+            if (std::fabs(g[j + 1]) <= o->tol * nb || hn == 0.0) { ++j; break; }
+        }
+        for (int i = j - 1; i >= 0; --i) {
+            double sum = g[i];
+            for (int k = i + 1; k < j; ++k) sum -= H[(size_t)i * m + k] * y[k];
+            y[i] = sum / H[(size_t)i * m + i];
+        }
+        CSX_CUDA(cudaMemcpyAsync(hd, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
+        CSX_TRY(launch_axpy_multi(N, j, hd, Z, x, s));
         CSX_CUDA(cudaStreamSynchronize(s));  // y is a host buffer reused next restart
     }
     inf->final_rel_residual = rel;

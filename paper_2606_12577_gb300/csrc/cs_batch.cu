@@ -47,6 +47,7 @@ struct BProb {
     const double *cinv;  // coarsest dense inverse, FP64 row-major
     T *Z;                // GMRES work vector [N0][m] (the cycle precision)
     T *V;                // GMRES basis: restart + 1 vectors of [N0][m]
+    T *ZB;               // right-preconditioned GMRES: restart vectors Z_j = M V_j of [N0][m]
     BLevel<T> lev[BMAXLEV];
 };
 
@@ -95,13 +96,13 @@ struct BArgs {
     int *iters;     // [nprob]
     int *work;      // [nprob]: the problem takes part in the cycle stages
     BCtl *ctl;
-    // GMRES (left preconditioned, restarted; per problem and right-hand side q = p * 8 + r)
+    // GMRES (restarted, left or right preconditioned; per problem and right-hand side q = p * BMAXRHS + r)
     int method, restart, hstride;
     double *H;      // [q][(restart + 1) * restart]
     double *cs, *sn, *y;  // [q][restart]
     double *g;      // [q][restart + 1]
     double *inv;    // [q]: 1 / ||Z|| of the last normalisation
-    double *nmb;    // [q]: ||M b||
+    double *nmb;    // [q]: ||M b|| (left) or ||b|| (right): the scale of the GMRES stopping test
     int *jcols;     // [q]: Krylov columns built in this cycle
     int *frozen;    // [q]: no longer extending in this cycle
     // classical Gram-Schmidt: per-tile projection partials, problem p's
@@ -523,7 +524,9 @@ enum {
     F_PROJ,        // (W) partial sums of <Z, V_i>, i <= j (pass 0 also <Z, Z>) -> part2
     F_PAXPY,       // (W) Z -= sum_i hsum_i V_i, i <= j; partial sums of Z^2
     F_SCALEV,      // (W) V_j = Z / ||Z||
-    F_XUPD         // (A) x += sum_k y_k V_k
+    F_XUPD,        // (A) x += sum_k y_k V_k (left) or sum_k y_k Z_k (right)
+    F_VTOB,        // (W) right: cycle input = V_j, output = 0
+    F_AZ           // (W) right: Z_j = cycle output (kept), Z = A Z_j in FP64
 };
 
 __device__ __forceinline__ bool fine_gate_all(int what) {
@@ -641,6 +644,30 @@ __device__ void stage_fine(const BArgs &a, const BProb<T> *P, int what, int iarg
                     acc = fma(v, v, acc);
                     lb[e] = (T)v;
                     lx[e] = T(0);
+                    if (a.method == CS_GMRES_RIGHT) Z[e] = (T)v;  // V_0 = r / ||r|| next
+                }
+            } else if (what == F_AZ) {
+                // right preconditioning: keep Z_j = M V_j (the cycle output,
+                // exact in T) and form the Krylov product A Z_j with the FP64
+                // operator, as F_MATVEC does for the left form
+                T *__restrict__ zj = pr.ZB + (int64_t)jarg * nm;
+                const double *__restrict__ A64 = pr.A64;
+                const bool star = L.kind == STAR;
+                for (int nn = n0; nn < ni; nn += step) {
+                    const int i = i0 + nn;
+                    const int iy = i / nx, ix = i - iy * nx;
+                    const double ax = star ? row_apply<STAR, double, double, T>(nx, ny, N, A64, lx, m, r, ix, iy, i)
+                                           : row_apply<BOX, double, double, T>(nx, ny, N, A64, lx, m, r, ix, iy, i);
+                    const int64_t e = (int64_t)i * m + r;
+                    zj[e] = lx[e];
+                    Z[e] = (T)ax;
+                }
+            } else if (what == F_VTOB) {
+                const T *__restrict__ vj = V + (int64_t)jarg * nm;
+                for (int nn = n0; nn < ni; nn += step) {
+                    const int64_t e = (int64_t)(i0 + nn) * m + r;
+                    lb[e] = vj[e];
+                    lx[e] = T(0);
                 }
             } else if (what == F_MATVEC) {
                 // the Krylov product A V_j: the FP64 operator applied in FP64
@@ -691,13 +718,14 @@ __device__ void stage_fine(const BArgs &a, const BProb<T> *P, int what, int iarg
                         Vj[e] = Z[e] * inv;
                     }
                 }
-            } else {  // F_XUPD: x += V y in FP64 (y can combine the basis with heavy cancellation)
+            } else {  // F_XUPD: x += V y (left) or Z y (right) in FP64 (y can combine with heavy cancellation)
                 const int nc = a.jcols[q];
                 const double *__restrict__ y = a.y + (int64_t)q * a.restart;
+                const T *__restrict__ basis = a.method == CS_GMRES_RIGHT ? pr.ZB : V;
                 for (int nn = n0; nn < ni; nn += step) {
                     const int64_t e = (int64_t)(i0 + nn) * m + r;
                     double sx = x[e];
-                    for (int kk = 0; kk < nc; ++kk) sx = fma(y[kk], (double)V[(int64_t)kk * nm + e], sx);
+                    for (int kk = 0; kk < nc; ++kk) sx = fma(y[kk], (double)basis[(int64_t)kk * nm + e], sx);
                     x[e] = sx;
                 }
             }
@@ -714,7 +742,7 @@ enum {
     P_NORMB = 0,  // ||b||
     P_NORM,       // true relative residuals: convergence, divergence, limit; counts active problems
     P_NMB,        // ||M b|| (GMRES stopping estimate scale)
-    P_BETA,       // beta = ||M r||, g = beta e_1, V_0 scale; counts extending right-hand sides
+    P_BETA,       // beta = ||M r|| (left) or ||r|| (right), g = beta e_1, V_0 scale; counts extending ones
     P_REORTH,     // ||Z||^2 after the first projection; reproject where it fell below half <Z, Z>; counts them
     P_GIVENS,     // H(j+1, j) = ||Z||, rotations, g, freeze; counts extending right-hand sides
     P_SOLVEY      // y = H^{-1} g (back substitution over the columns built)
@@ -753,6 +781,8 @@ __device__ void stage_prob(const BArgs &a, const BProb<T> *P, int what, int iarg
         if (what == P_NORMB || what == P_NMB) {
             double *dst = what == P_NORMB ? a.nb : a.nmb;
             for (int r = 0; r < m; ++r) dst[q0 + r] = sqrt(tsum(r));
+            if (what == P_NORMB && a.method == CS_GMRES_RIGHT)  // right: the test is on ||r|| / ||b||
+                for (int r = 0; r < m; ++r) a.nmb[q0 + r] = a.nb[q0 + r];
         } else if (what == P_NORM) {
             double worst = 0.0;
             bool conv = true, bad = false;
@@ -949,6 +979,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_batch_solve(BAr
     BSYNC(3000 + P_NORMB);
     stage_fine<T>(a, P, F_ZEROX, 0, 0, red);
     BSYNC(2000 + F_ZEROX);
+    const bool gmres = a.method == CS_GMRES || a.method == CS_GMRES_RIGHT;
+    const bool right = a.method == CS_GMRES_RIGHT;
     if (a.method == CS_GMRES) {  // ||M b|| per right-hand side
         stage_fine<T>(a, P, F_MB, 0, 0, red);
         BSYNC(2000 + F_MB);
@@ -963,7 +995,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_batch_solve(BAr
     ph ^= 1;
     stage_prob<T>(a, P, P_NORM, 0, 0, ph, true, wsum);
     BSYNC(3000 + P_NORM);
-    if (a.method != CS_GMRES) {
+    if (!gmres) {
         for (int it = 0; it < maxit; ++it) {
             if (__ldcg(&a.ctl->cnt[ph]) == 0) break;  // active problems
             vcycle_stages<T>(a, P, grid);
@@ -980,9 +1012,11 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_batch_solve(BAr
     const int R = a.restart;
     for (int cyc = 0; cyc <= maxit; ++cyc) {
         if (__ldcg(&a.ctl->cnt[ph]) == 0) break;  // active problems
-        vcycle_stages<T>(a, P, grid);  // M r (the cycle input is r from F_RESID)
-        stage_fine<T>(a, P, F_CONVZ, 0, 0, red);
-        BSYNC(2000 + F_CONVZ);
+        if (!right) {
+            vcycle_stages<T>(a, P, grid);  // M r (the cycle input is r from F_RESID)
+            stage_fine<T>(a, P, F_CONVZ, 0, 0, red);
+            BSYNC(2000 + F_CONVZ);
+        }  // right: Z = r and the partial sums of r^2 come from F_RESID
         ph ^= 1;
         stage_prob<T>(a, P, P_BETA, 0, 0, ph, false, wsum);
         BSYNC(3000 + P_BETA);
@@ -990,11 +1024,19 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_batch_solve(BAr
         BSYNC(2000 + F_SCALEV);
         for (int j = 0; j < R; ++j) {
             if (__ldcg(&a.ctl->cnt[ph]) == 0) break;  // right-hand sides still extending
-            stage_fine<T>(a, P, F_MATVEC, 0, j, red);
-            BSYNC(2000 + F_MATVEC);
-            vcycle_stages<T>(a, P, grid);
-            stage_fine<T>(a, P, F_CONVZ, 0, 0, red);
-            BSYNC(2000 + F_CONVZ);
+            if (right) {  // Z = A M V_j, M V_j kept
+                stage_fine<T>(a, P, F_VTOB, 0, j, red);
+                BSYNC(2000 + F_VTOB);
+                vcycle_stages<T>(a, P, grid);
+                stage_fine<T>(a, P, F_AZ, 0, j, red);
+                BSYNC(2000 + F_AZ);
+            } else {  // Z = M A V_j
+                stage_fine<T>(a, P, F_MATVEC, 0, j, red);
+                BSYNC(2000 + F_MATVEC);
+                vcycle_stages<T>(a, P, grid);
+                stage_fine<T>(a, P, F_CONVZ, 0, 0, red);
+                BSYNC(2000 + F_CONVZ);
+            }
             // classical Gram-Schmidt with a second projection where the
             // first cancelled more than half of ||Z|| (DGKS)
             stage_fine<T>(a, P, F_PROJ, 0, j, red);
@@ -1181,7 +1223,7 @@ cs_status build_tiles(cs_batch *B, int tiles_per_cta, cudaStream_t s) {
     dfree(B->btiles, s); dfree(B->slot_btile, s); dfree(B->part2, s); dfree(B->p2off, s);
     B->tiles = nullptr; B->ftiles = nullptr; B->slot_tile = nullptr; B->ftile_of = nullptr; B->part = nullptr;
     B->btiles = nullptr; B->slot_btile = nullptr; B->part2 = nullptr; B->p2off = nullptr;
-    if (B->method == CS_GMRES) {  // projection partials: (restart + 2) slots x m_p per finest tile
+    if (B->method != CS_REFINE) {  // projection partials: (restart + 2) slots x m_p per finest tile
         std::vector<int64_t> po(B->nprob + 1, 0);
         for (int p = 0; p < B->nprob; ++p)
             po[p + 1] = po[p] + (int64_t)(fo[p + 1] - fo[p]) * (B->restart + 2) * B->m[p];
@@ -1396,11 +1438,16 @@ cs_status fill_probs(cs_batch *B, cs_hierarchy *const *h, cs_cascade *const *c, 
         q.cinv = h[p]->cinv;
         q.Z = nullptr;
         q.V = nullptr;
+        q.ZB = nullptr;
         if (gm) {
             const int64_t n0 = h[p]->lev[0].g.N * B->m[p];
             q.Z = gm;
             q.V = gm + n0;
             gm += (int64_t)(B->restart + 2) * n0;
+            if (B->method == CS_GMRES_RIGHT) {
+                q.ZB = gm;
+                gm += (int64_t)B->restart * n0;
+            }
         }
         for (int l = 0; l < q.nlev; ++l) {
             const Level &L = h[p]->lev[l];
@@ -1441,8 +1488,11 @@ cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *
     *out = nullptr;
     if (o->precision != CS_FP32 && o->precision != CS_FP64) { set_error("bad precision"); return CS_ERR_ARG; }
     if (o->order != CS_RF && o->order != CS_FF) { set_error("bad order"); return CS_ERR_ARG; }
-    if (o->method != CS_REFINE && o->method != CS_GMRES) { set_error("batched method must be CS_REFINE or CS_GMRES"); return CS_ERR_ARG; }
-    if (o->method == CS_GMRES && (o->restart < 0 || o->restart > 64)) { set_error("GMRES restart must be in 1..64"); return CS_ERR_ARG; }
+    if (o->method != CS_REFINE && o->method != CS_GMRES && o->method != CS_GMRES_RIGHT) {
+        set_error("batched method must be CS_REFINE, CS_GMRES or CS_GMRES_RIGHT");
+        return CS_ERR_ARG;
+    }
+    if (o->method != CS_REFINE && (o->restart < 0 || o->restart > 64)) { set_error("GMRES restart must be in 1..64"); return CS_ERR_ARG; }
     if (o->mu_pre < 0 || o->mu_post < 0 || o->mu_pre + o->mu_post < 1 || o->mu_pre > 16 || o->mu_post > 16) {
         set_error("bad smoothing counts");
         return CS_ERR_ARG;
@@ -1474,7 +1524,7 @@ cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *
     B->nu = nu;
     B->kind = c[0]->kind;
     B->bs = h[0]->lev[0].bs;
-    B->method = o->method == CS_GMRES ? CS_GMRES : CS_REFINE;
+    B->method = o->method;
     B->restart = o->restart > 0 ? o->restart : 30;
     cudaGetDevice(&B->dev);
     B->m.assign(nrhs, nrhs + nprob);
@@ -1502,9 +1552,11 @@ cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *
     int64_t nfine_rhs = 0;
     for (int p = 0; p < nprob; ++p) nfine_rhs += B->nfine[p] * B->m[p];
     if ((rc = dalloc(&B->vec, (size_t)nvec * esz, &B->bytes, s)) != CS_OK) goto fail;
-    if (B->method == CS_GMRES) {
-        // basis (restart + 1 vectors) and Z per problem, in the cycle precision, [N0][m] each
-        if ((rc = dalloc(&B->gm, (size_t)(B->restart + 2) * nfine_rhs * esz, &B->bytes, s)) != CS_OK)
+    if (B->method != CS_REFINE) {
+        // basis (restart + 1 vectors) and Z per problem, in the cycle precision, [N0][m] each;
+        // right preconditioning keeps restart more (Z_j = M V_j)
+        const size_t nv = (size_t)(B->restart + 2) + (B->method == CS_GMRES_RIGHT ? (size_t)B->restart : 0);
+        if ((rc = dalloc(&B->gm, nv * nfine_rhs * esz, &B->bytes, s)) != CS_OK)
             goto fail;
         const size_t nq = (size_t)nprob * BMAXRHS, R = (size_t)B->restart;
         const size_t nd = nq * ((R + 1) * R + 3 * R + (R + 1) + 2 + (R + 2) + 2);
@@ -1732,7 +1784,7 @@ cs_status cs_solve_batched(int nprob, cs_hierarchy *const *h, cs_cascade *const 
     bo.mu_pre = o->cycle.mu_pre;
     bo.mu_post = o->cycle.mu_post;
     bo.autotune = 0;
-    bo.method = o->method == CS_GMRES ? CS_GMRES : CS_REFINE;
+    bo.method = (o->method == CS_GMRES || o->method == CS_GMRES_RIGHT) ? o->method : CS_REFINE;
     bo.restart = o->restart;
     cs_batch *B = nullptr;
     CSX_TRY(cs_batch_create(nprob, h, c, nrhs, &bo, stream, &B));

@@ -107,6 +107,7 @@ struct cs_cascade {
     // GMRES workspace (lazily allocated at first GMRES solve)
     int gm_restart = 0;
     double *gm_V = nullptr, *gm_h = nullptr;
+    double *gm_Z = nullptr;  // right-preconditioned GMRES: Z_j = M V_j
     int64_t bytes = 0;
     // learned setup of the finest level: 1 used (some blocks predicted), 0
     // fell back to the exact setup, -1 no model; level-1 Frobenius objectives

@@ -39,6 +39,27 @@ static cs_status noalloc_scratch(double **out) {
     return CS_OK;
 }
 
+// Every vector must be device (or managed) memory of the current device: the
+// kernels and the scratch array run there, and a pointer into another GPU's
+// memory (or into host memory) would be dereferenced without peer access.
+static cs_status check_on_device(const void *ptr, const char *name) {
+    int dev = 0;
+    CSX_CUDA(cudaGetDevice(&dev));
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+        set_error("%s is not a CUDA device pointer", name);
+        return CS_ERR_ARG;
+    }
+    if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev) {
+        set_error("%s must be device memory of the current device %d (memory type %d, device %d)", name, dev,
+                  (int)at.type, at.device);
+        return CS_ERR_ARG;
+    }
+    return CS_OK;
+}
+
 }  // namespace csx
 
 using namespace csx;
@@ -58,8 +79,18 @@ extern "C" cs_status cs_smooth_noalloc(int dim, const int *n, int box, const dou
                   (long long)L.g.N);
         return CS_ERR_ARG;
     }
+    // the node kernels launch ceil(nx/TBX) x ceil(ny/TBY) x nz CTAs
+    if ((int64_t)L.g.ny > (int64_t)TBY * 65535 || L.g.nz > 65535) {
+        set_error("cs_smooth_noalloc: grid %d x %d x %d exceeds the launch limits (ny <= %d, nz <= 65535)", L.g.nx,
+                  L.g.ny, L.g.nz, TBY * 65535);
+        return CS_ERR_ARG;
+    }
     L.kind = box ? BOX : STAR;
     L.nst = box ? (dim == 3 ? 27 : 9) : 2 * dim + 1;
+    CSX_TRY(check_on_device(coeff, "coeff"));
+    CSX_TRY(check_on_device(lam, "lam"));
+    CSX_TRY(check_on_device(b, "b"));
+    CSX_TRY(check_on_device(x, "x"));
     double *scratch = nullptr;
     CSX_TRY(noalloc_scratch(&scratch));
     cudaStream_t s = (cudaStream_t)stream;

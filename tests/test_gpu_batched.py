@@ -309,3 +309,85 @@ def test_block_gmres_with_32_rhs_converges():
     for r in range(m):
         res = Bm[:, r] - stencil_matvec(A, X[:, r])
         assert np.linalg.norm(res) / np.linalg.norm(Bm[:, r]) <= 1.0001e-10
+
+
+def test_right_gmres_fixed_steps_match_single_problem_gmres():
+    """FP64 cycles, right-preconditioned GMRES(30) stopped after 5 Arnoldi
+    steps: every problem and right-hand side equals the single-problem
+    right-preconditioned GMRES after 5 steps (classical Gram-Schmidt with
+    reprojection against modified Gram-Schmidt: the same basis in exact
+    arithmetic)."""
+    import torch
+
+    import paper_2606_12577_gb300 as cmg
+    probs = _batch()
+    hs, cs = _setup(probs)
+    bt = cmg.Batch(hs, cs, NRHS, precision="fp64", method="gmres_right", restart=30)
+    bs, xs = _vectors(probs)
+    infos = bt.solve(bs, xs, tol=1e-300, maxit=5, raise_on_error=False)
+    assert all(i.iterations == 5 and not i.converged for i in infos)
+    for p, (A, m, b) in enumerate(probs):
+        X = xs[p].cpu().numpy().reshape(A.N, m)
+        B = b.reshape(A.N, m)
+        for r in range(m):
+            x1 = torch.zeros(A.N, dtype=torch.float64, device="cuda")
+            cmg.solve(hs[p], cs[p], torch.tensor(B[:, r].copy(), device="cuda"), x1, method="gmres_right",
+                      precision="fp64", tol=1e-300, maxit=5, restart=30, raise_on_error=False)
+            assert rel_max(X[:, r], x1.cpu().numpy()) <= 1e-10, (p, r)
+
+
+def test_right_gmres_batch_matches_oracle_iterations():
+    """FP64 cycles: the batched right-preconditioned GMRES converges on every
+    right-hand side of the batched workload's first problems (sides <= 129)
+    in about the oracle's right-preconditioned GMRES step count (the batch
+    restarts per problem, so a problem can take more steps than its slowest
+    right-hand side alone, never more than twice as many)."""
+    import torch
+
+    import paper_2606_12577_gb300 as cmg
+    probs = [problems.batch_problem(k, nmin=40, nmax=129) for k in range(6)]
+    hs, cs = _setup(probs)
+    bt = cmg.Batch(hs, cs, [m for _, m, _ in probs], precision="fp64", method="gmres_right")
+    bs = [torch.tensor(b, dtype=torch.float64, device="cuda") for _, _, b in probs]
+    xs = [torch.zeros_like(b) for b in bs]
+    infos = bt.solve(bs, xs, tol=1e-10, maxit=300)
+    for p, (A, m, b) in enumerate(probs):
+        assert infos[p].converged
+        X = xs[p].cpu().numpy().reshape(A.N, m)
+        B = b.reshape(A.N, m)
+        ho = oracle.Hierarchy(A)
+        co = oracle.Cascade(ho, "multiplicative", nu=3)
+        worst = 0
+        for r in range(m):
+            res = B[:, r] - stencil_matvec(A, X[:, r])
+            assert np.linalg.norm(res) / np.linalg.norm(B[:, r]) <= 1.0001e-10
+            _, ito, _, _ = oracle.solve(ho, co, B[:, r].copy(), method="gmres_right", tol=1e-10, maxit=300)
+            assert ito > 0
+            worst = max(worst, ito)
+        assert worst - 1 <= infos[p].iterations <= 2 * worst + 1, (p, infos[p].iterations, worst)
+
+
+@pytest.mark.parametrize("n,count", [(127, 60), (255, 200)])
+def test_right_gmres_interface_32_rhs_fp32(n, count):
+    """The elliptic interface family with 32 right-hand sides solved together
+    (2x2-node blocks, additive nu = 3, FP32 cycles and Krylov vectors,
+    right-preconditioned GMRES-IR): every right-hand side reaches 1e-10 in the
+    FP64 true residual, at 255^2 where the left-preconditioned form
+    stagnates (in the oracle as well)."""
+    import torch
+
+    import paper_2606_12577_gb300 as cmg
+    A = problems.interface2d(n, count)
+    m = 32
+    B = problems.uniform(79, A.N * m, -1.0, 1.0)
+    hs, cs = cmg.setup_many([A], kind="additive", nu=3, lowp=True, block=2)
+    bt = cmg.Batch(hs, cs, [m], precision="fp32", method="gmres_right")
+    b = torch.tensor(B, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    info = bt.solve([b], [x], tol=1e-10, maxit=300)[0]
+    assert info.converged
+    X = x.cpu().numpy().reshape(A.N, m)
+    Bm = B.reshape(A.N, m)
+    for r in range(m):
+        res = Bm[:, r] - stencil_matvec(A, X[:, r])
+        assert np.linalg.norm(res) / np.linalg.norm(Bm[:, r]) <= 1.0001e-10

@@ -169,3 +169,36 @@ def test_multi_rhs_colour_steps_in_place(built, m):
             cmg.sweep_rhs(hg, cg, 0, st, B, cur, oth, m, colour=col)
             cur, oth = oth, cur
     assert np.array_equal(_host(xin), _host(cur))
+
+
+@pytest.mark.parametrize("n,count,method,maxit", [(63, 8, "gmres", 100), (127, 60, "gmres_right", 100),
+                                                  (255, 200, "gmres_right", 60)])
+def test_interface_workload_parity(built, n, count, method, maxit):
+    """The elliptic interface family (problems.interface2d: ~count circular
+    inclusions of contrast up to 1e8, 2x2-node blocks, additive nu = 3) at
+    sizes the oracle solves in seconds: Lambda blocks, the FP64 solve's
+    iteration count and residual history equal the oracle's; FP32 cycles
+    reach the same 1e-10 true residual.  At 255^2 the left-preconditioned
+    GMRES stagnates in the oracle too (its test in the oracle pins); the
+    right-preconditioned one converges on both sides."""
+    import paper_2606_12577_gb300 as cmg
+    A = problems.interface2d(n, count)
+    ho = oracle.Hierarchy(A, bs=2)
+    co = oracle.Cascade(ho, "additive", nu=3)
+    hg = gu.gpu_hierarchy(A, block=2)
+    cg = cmg.setup_cascade(hg, "additive", nu=3, lowp=True)
+    for l in range(co.nlev):
+        assert gu.rel_max(cmg.export_lambda(cg, l), co.lam(l)) <= TOL, l
+    b = problems.rhs(A.N, 9)
+    xo, ito, hist_o, fin_o = oracle.solve(ho, co, b, method=method, tol=1e-10, maxit=maxit)
+    assert ito > 0
+    xg = _dev(np.zeros(A.N))
+    info = cmg.solve(hg, cg, _dev(b), xg, method=method, tol=1e-10, maxit=maxit)
+    assert info.converged and info.iterations == ito
+    np.testing.assert_allclose(info.history, hist_o, rtol=1e-8, atol=1e-13)
+    assert gu.rel_max(_host(xg), xo) <= 1e-9
+    x32 = _dev(np.zeros(A.N))
+    info32 = cmg.solve(hg, cg, _dev(b), x32, method=method, precision="fp32", tol=1e-10, maxit=2 * maxit)
+    assert info32.converged
+    r = b - gu.stencil_matvec(A, _host(x32))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10

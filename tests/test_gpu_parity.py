@@ -385,7 +385,9 @@ def test_vcycle_parity(built, name, kind, order, mu):
     ("p2d_64", "additive", "stationary"), ("p2d_64", "multiplicative", "gmres"),
     ("c2d_130", "multiplicative", "gmres"), ("c2d_130", "additive", "gmres"),
     ("v3d_33x", "additive", "stationary"), ("c3d_33", "multiplicative", "stationary"),
-    ("p3d_16", "multiplicative", "gmres")])
+    ("p3d_16", "multiplicative", "gmres"), ("p2d_64", "additive", "gmres_right"),
+    ("c2d_130", "multiplicative", "gmres_right"), ("v3d_33x", "additive", "gmres_right"),
+    ("c3d_33", "multiplicative", "gmres_right")])
 def test_solve_parity(built, name, kind, method):
     import paper_2606_12577_gb300 as cmg
     A = PROBLEMS[name]()
@@ -412,7 +414,8 @@ def test_solve_parity(built, name, kind, method):
 
 @pytest.mark.parametrize("name,kind,method", [
     ("p2d_64", "additive", "refine"), ("c3d_33", "multiplicative", "refine"), ("v3d_33x", "additive", "refine"),
-    ("v3d_33x", "additive", "gmres"), ("c2d_130", "additive", "gmres")])
+    ("v3d_33x", "additive", "gmres"), ("c2d_130", "additive", "gmres"), ("c2d_130", "multiplicative", "gmres_right"),
+    ("v3d_33x", "additive", "gmres_right")])
 def test_fp32_cycle_with_fp64_refinement(built, name, kind, method):
     """The mixed-precision form: FP32 cycle inside FP64 refinement (or FP64
     GMRES) reaches the same 1e-10 true residual; its distance to the oracle's

@@ -51,11 +51,12 @@ def test_slowest_replica_sets_the_time():
 def test_reference_arm_runs_on_rank_zero_only():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2")
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
-                        "--cpu-n", "8"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+                        "--n", "8"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == ""
     env["RANK"] = "0"
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
-                        "--cpu-n", "8"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+                        "--n", "8"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["cores"] >= 1 and line["cpu_baseline"]["cpu_model"]

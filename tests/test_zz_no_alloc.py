@@ -86,3 +86,52 @@ def test_noalloc_rejects_oversize():
     with pytest.raises(cmg.CascadeError, match="CS_ERR_ARG"):
         cmg.smooth_noalloc(3, n, 0, big, lam, 1, v, v.clone())
     del z
+
+
+def test_noalloc_rejects_grids_beyond_the_launch_limits():
+    """N within the array's limit but a grid whose node-kernel launch would
+    exceed the CTA grid limits (nz > 65535, or ny > 4 x 65535 in 2D) is
+    rejected with CS_ERR_ARG before any launch."""
+    import __graft_entry__ as g
+    g.build()
+    import torch
+
+    import paper_2606_12577_gb300 as cmg
+    for dim, n in ((3, (1, 1, 1 << 17)), (2, (1, 1 << 19))):
+        N = 1 << 17 if dim == 3 else 1 << 19
+        nst = 2 * dim + 1
+        coeff = torch.zeros(nst * N, dtype=torch.float64, device="cuda")
+        lam = torch.zeros(N, dtype=torch.float64, device="cuda")
+        v = torch.zeros(N, dtype=torch.float64, device="cuda")
+        with pytest.raises(cmg.CascadeError, match="launch limits"):
+            cmg.smooth_noalloc(dim, n, 0, coeff, lam, 1, v, v.clone())
+
+
+def test_noalloc_rejects_memory_of_another_device():
+    """A vector that is not device memory of the current device (here host
+    memory, passed through the C ABI directly) is rejected with CS_ERR_ARG
+    before any launch; the binding rejects CPU tensors itself."""
+    import ctypes
+
+    import __graft_entry__ as g
+    g.build()
+    import torch
+
+    import paper_2606_12577_gb300 as cmg
+    from paper_2606_12577_gb300 import _capi
+    n = (8, 8, 1)
+    N = 64
+    coeff = torch.zeros(5 * N, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(N, dtype=torch.float64, device="cuda")
+    v = torch.zeros(N, dtype=torch.float64, device="cuda")
+    host = np.zeros(N)
+    narr = (ctypes.c_int * 3)(*n)
+    st = _capi.lib().cs_smooth_noalloc(2, narr, 0, ctypes.c_void_p(coeff.data_ptr()),
+                                       ctypes.c_void_p(lam.data_ptr()), 1, _capi.CS_ADDITIVE, 0,
+                                       ctypes.c_void_p(host.ctypes.data), ctypes.c_void_p(v.data_ptr()),
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == _capi.CS_ERR_ARG
+    assert b"current device" in _capi.lib().cs_last_error() or b"not a CUDA device pointer" in \
+        _capi.lib().cs_last_error()
+    with pytest.raises(TypeError):
+        cmg.smooth_noalloc(2, n, 0, coeff, lam, 1, torch.zeros(N, dtype=torch.float64), v)
