@@ -957,8 +957,9 @@ __device__ __forceinline__ void vcycle_stages(const BArgs &a, const BProb<T> *P,
 
 // The whole solve: every CTA runs every stage and passes every grid barrier
 // (no early exit anywhere).  Each loop ends for all CTAs at once: the count
-// it tests was written before the barrier that precedes the test (and is
-// cleared only by a later counting stage), and every loop is bounded by the
+// it tests was written before the barrier that precedes the test, and the
+// counting stage that clears it again runs only after at least one more
+// barrier (or only when the count is zero); every loop is bounded by the
 // iteration limit in any case.
 template <typename T>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_batch_solve(BArgs a) {
@@ -1016,7 +1017,12 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_batch_solve(BAr
             vcycle_stages<T>(a, P, grid);  // M r (the cycle input is r from F_RESID)
             stage_fine<T>(a, P, F_CONVZ, 0, 0, red);
             BSYNC(2000 + F_CONVZ);
-        }  // right: Z = r and the partial sums of r^2 come from F_RESID
+        } else {
+            // right: Z = r and the partial sums of r^2 come from F_RESID.  P_BETA
+            // clears the count slot every CTA has just tested; the barrier keeps
+            // a fast CTA from clearing it before a slow one has read it
+            BSYNC(5000);
+        }
         ph ^= 1;
         stage_prob<T>(a, P, P_BETA, 0, 0, ph, false, wsum);
         BSYNC(3000 + P_BETA);
