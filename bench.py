@@ -57,6 +57,8 @@ def args_():
     p.add_argument("--learned-n", type=int, default=127, help="interior nodes per side of a training mesh")
     p.add_argument("--learned-steps", type=int, default=6000, help="Adam steps")
     p.add_argument("--interface-maxit", type=int, default=300, help="GMRES steps allowed on the interface workload")
+    p.add_argument("--interface-restart", type=int, default=200,
+                   help="GMRES restart of the interface workload (the oracle needs 149 steps at 1023^2 without restart)")
     p.add_argument("--batch-count", type=int, default=512, help="problems of the batched workload timed")
     p.add_argument("--batch-fp64-count", type=int, default=32,
                    help="problems on which FP32 and FP64 cycles are compared")
@@ -328,7 +330,7 @@ def interface_section(a, cmg, problems, dev):
     e[0].record(s)
     hs, cs = cmg.setup_many([Ai], kind="additive", nu=3, lowp=True, block=2)
     e[1].record(s)
-    bt = cmg.Batch(hs, cs, [m], precision="fp32", method=a.krylov, autotune=True)
+    bt = cmg.Batch(hs, cs, [m], precision="fp32", method=a.krylov, autotune=True, restart=a.interface_restart)
     x = torch.zeros_like(bd)
     bt.solve([bd], [x], tol=1e-10, maxit=2, raise_on_error=False)  # warm-up (graph)
     x.zero_()
@@ -342,7 +344,8 @@ def interface_section(a, cmg, problems, dev):
     rel = []
     Xm = x.view(Ai.N, m)
     out = {"workload": "elliptic interface 1024^2, 200 inclusions (contrast 1e-4..1e4), 2x2-node blocks, additive "
-                       f"nu=3, 32 RHS, {a.krylov}(30) V(1,1) RF FP32 cycles to 1e-10, the 32 RHS in one batched launch",
+                       f"nu=3, 32 RHS, {a.krylov}({a.interface_restart}) V(1,1) RF FP32 cycles to 1e-10, the 32 RHS in "
+                       "one batched launch",
            "krylov": a.krylov,
            "setup_ms": e[0].elapsed_time(e[1]), "solve_ms": e[2].elapsed_time(e[3]),
            "gmres_steps": info.iterations, "all_converged": bool(info.converged),
@@ -353,7 +356,7 @@ def interface_section(a, cmg, problems, dev):
     torch.cuda.synchronize()
     e[2].record(s)
     i1 = cmg.solve(hs[0], cs[0], bd.view(Ai.N, m)[:, 0].contiguous(), x1, method=a.krylov, precision="fp32",
-                   tol=1e-10, maxit=a.interface_maxit, raise_on_error=False)
+                   tol=1e-10, maxit=a.interface_maxit, restart=a.interface_restart, raise_on_error=False)
     e[3].record(s)
     torch.cuda.synchronize()
     out["single_rhs_path_first_rhs"] = {"solve_ms": e[2].elapsed_time(e[3]), "gmres_steps": i1.iterations,

@@ -356,7 +356,7 @@ typedef struct {
                         inner steps stop on |g_{j+1}| <= tol ||b|| (or 1e-5 ||r|| with CS_FP32):
                         the form that converges where the coefficients' contrast makes ||M r||
                         a poor measure of ||r||; restart more vectors of [N0][m] per problem */
-    int restart;     /* GMRES restart length (default 30, at most 64) */
+    int restart;     /* GMRES restart length (default 30, at most 256) */
 } cs_batch_opts;
 typedef struct {
     int threads;

@@ -77,6 +77,8 @@ def _load():
             "ora_vcycle": (None, [P, P, I, I, I, P, P]),
             "ora_solve": (I, [P, P, I, I, I, I, D, I, I, P, P, P, P, P]),
             "ora_set_threads": (None, [I]),
+            "ora_casc_create_sketch": (P, [P, I, I, I, I, C.c_uint64, I]),
+            "ora_rademacher": (D, [C.c_uint64, I, L, I, I]),
             "ora_max_threads": (I, []),
         }
         for name, (res, args) in sig.items():
@@ -85,6 +87,12 @@ def _load():
             f.argtypes = args
         _lib = lib
         return lib
+
+
+def rademacher(seed: int, level: int, i: int, t: int, s: int) -> float:
+    """Entry (i, t) of the level's Rademacher sketch (the counter-based
+    SplitMix64 stream described in cs_oracle.c)."""
+    return float(_load().ora_rademacher(int(seed) & 0xFFFFFFFFFFFFFFFF, level, i, t, s))
 
 
 def set_threads(n: int) -> None:
@@ -198,13 +206,19 @@ class Cascade:
     (Algorithm 2; SM Algorithm for kind='multiplicative', red-black)."""
 
     def __init__(self, hier: Hierarchy, kind: str = "additive", nu: int = 3, prescale: bool = True,
-                 alpha: int = 0, _empty: bool = False):
+                 alpha: int = 0, _empty: bool = False, sketch: int = 0, seed: int = 0, exact_first: bool = False):
+        """sketch > 0: the sketched setup of the concluding remarks (Sec. 4)
+        with a Rademacher sketch of `sketch` columns from `seed` (see
+        ``rademacher``); exact_first: step 1 unsketched."""
         self.hier = hier
         self.kind = kind
         self.nu = nu
         self.ncol = 2 if kind == "multiplicative" else 1
         if _empty:
             self._c = _lib.ora_casc_empty(hier._h, KINDS[kind], nu)
+        elif sketch > 0:
+            self._c = _lib.ora_casc_create_sketch(hier._h, KINDS[kind], nu, int(prescale), int(sketch),
+                                                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(exact_first))
         else:
             self._c = _lib.ora_casc_create(hier._h, KINDS[kind], nu, int(prescale), alpha)
         if not self._c:

@@ -772,6 +772,148 @@ ora_casc *ora_casc_create(const ora_hier *h, int kind, int nu, int prescale, int
     }
     return c;
 }
+/* ------------------------------------------------------ sketched setup
+ * The sketched cascade of the concluding remarks (Sec. 4): each step
+ * replaces min ||(I - Lam A) E_{l-1}||_F by min ||(I - Lam A) E_{l-1} S||_F
+ * with an N x s sketching matrix S.  Carrying Y = E S (Y_0 = S), a step
+ * solves, per block b, Lam~_b = argmin ||Y_b - Lam Z_b||_F with Z = A~ Y
+ * (the same normal equations G = Z_b Z_b^T, C = Y_b Z_b^T as Algorithm 2)
+ * and sets Y_b <- Y_b - Lam~_b Z_b; multiplicative: colour by colour, every
+ * colour reading the state after the previous one (snapshot).  Prescaling
+ * and unscaling as in the exact setup.  With exact_first, the first step
+ * (multiplicative: its first colour, the one step whose residual is
+ * E_0 = I) solves the unsketched problem (G = A~_b A~_b^T, C = A~_bb^T) and
+ * Y becomes (I - Lam~_1 A~) S there (the hybrid the remarks suggest).
+ *
+ * S is Rademacher (entries +-1; its scale does not change Lam): entry (i, t)
+ * of level l is the sign of the SplitMix64 output (Steele, Lea and Flood,
+ * 2014) with counter c = l 2^48 + i s + t, i.e. of mix(seed + (c + 1) g),
+ * g = 0x9E3779B97F4A7C15: +1 when its top bit is 0. */
+static uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+static double rademacher(uint64_t seed, int l, int64_t i, int t, int s) {
+    uint64_t c = ((uint64_t)l << 48) + (uint64_t)i * (uint64_t)s + (uint64_t)t;
+    uint64_t z = sm64_mix(seed + (c + 1) * 0x9E3779B97F4A7C15ULL);
+    return (z >> 63) ? -1.0 : 1.0;
+}
+double ora_rademacher(uint64_t seed, int l, int64_t i, int t, int s) { return rademacher(seed, l, i, t, s); }
+
+static int sketch_level(const ora_hier *h, int l, int kind, int nu, int prescale, int s, uint64_t seed,
+                        int exact_first, const int64_t *lamoff, double *lam) {
+    const csr *A0 = &h->A[l];
+    int N = A0->n, nb = h->nb[l];
+    const int *bptr = h->bptr[l], *bidx = h->bidx[l];
+    int ncol = kind == 1 ? 2 : 1;
+    int64_t lamsize = lamoff[nb];
+    double *w = xmalloc(sizeof(double) * (size_t)N);
+    for (int i = 0; i < N; ++i) {
+        double d = 0.0;
+        for (int64_t p = A0->rp[i]; p < A0->rp[i + 1]; ++p) if (A0->ci[p] == i) d += A0->v[p];
+        if (prescale) {
+            if (!(d > 0.0)) { free(w); return -1; }
+            w[i] = 1.0 / sqrt(d);
+        } else w[i] = 1.0;
+    }
+    csr A;
+    A.n = A.m = N;
+    int64_t annz = A0->rp[N];
+    A.rp = xmalloc(sizeof(int64_t) * ((size_t)N + 1));
+    A.ci = xmalloc(sizeof(int) * (size_t)annz);
+    A.v = xmalloc(sizeof(double) * (size_t)annz);
+    memcpy(A.rp, A0->rp, sizeof(int64_t) * ((size_t)N + 1));
+    memcpy(A.ci, A0->ci, sizeof(int) * (size_t)annz);
+    for (int i = 0; i < N; ++i)
+        for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) A.v[p] = w[i] * A0->v[p] * w[A.ci[p]];
+    double *Y = xmalloc(sizeof(double) * (size_t)N * s);
+    double *Yn = xmalloc(sizeof(double) * (size_t)N * s);
+    double *Z = xmalloc(sizeof(double) * (size_t)N * s);
+    for (int64_t i = 0; i < N; ++i)
+        for (int t = 0; t < s; ++t) Y[i * s + t] = rademacher(seed, l, i, t, s);
+    memset(lam, 0, sizeof(double) * (size_t)nu * (size_t)lamsize);
+    for (int step = 0; step < nu; ++step) {
+        for (int k = 0; k < ncol; ++k) {
+            /* Z = A~ Y */
+#pragma omp parallel for schedule(static)
+            for (int i = 0; i < N; ++i)
+                for (int t = 0; t < s; ++t) {
+                    double z = 0.0;
+                    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) z += A.v[p] * Y[(int64_t)A.ci[p] * s + t];
+                    Z[(int64_t)i * s + t] = z;
+                }
+            memcpy(Yn, Y, sizeof(double) * (size_t)N * s);
+#pragma omp parallel for schedule(dynamic, 64)
+            for (int b = 0; b < nb; ++b) {
+                if (block_colour(h, l, kind, b) != k) continue;
+                int nbk = bptr[b + 1] - bptr[b];
+                const int *rows = bidx + bptr[b];
+                double *G = xcalloc((size_t)nbk * nbk, sizeof(double));
+                double *C = xcalloc((size_t)nbk * nbk, sizeof(double));
+                if (step == 0 && k == 0 && exact_first) {
+                    /* E_0 = I: R_b = A~_{b,:}, C_pq = A~(row_q, row_p) */
+                    for (int p = 0; p < nbk; ++p)
+                        for (int q = 0; q < nbk; ++q) {
+                            double g = 0.0, c = 0.0;
+                            int rp_ = rows[p], rq = rows[q];
+                            for (int64_t u = A.rp[rp_]; u < A.rp[rp_ + 1]; ++u)
+                                for (int64_t v = A.rp[rq]; v < A.rp[rq + 1]; ++v)
+                                    if (A.ci[u] == A.ci[v]) g += A.v[u] * A.v[v];
+                            for (int64_t v = A.rp[rq]; v < A.rp[rq + 1]; ++v)
+                                if (A.ci[v] == rp_) c += A.v[v];
+                            G[p * nbk + q] = g; C[p * nbk + q] = c;
+                        }
+                } else {
+                    for (int p = 0; p < nbk; ++p)
+                        for (int q = 0; q < nbk; ++q) {
+                            double g = 0.0, c = 0.0;
+                            for (int t = 0; t < s; ++t) {
+                                g += Z[(int64_t)rows[p] * s + t] * Z[(int64_t)rows[q] * s + t];
+                                c += Y[(int64_t)rows[p] * s + t] * Z[(int64_t)rows[q] * s + t];
+                            }
+                            G[p * nbk + q] = g; C[p * nbk + q] = c;
+                        }
+                }
+                double *Lb = lam + (size_t)step * lamsize + lamoff[b];
+                ls_solve_block(G, C, nbk, Lb);
+                for (int p = 0; p < nbk; ++p)
+                    for (int t = 0; t < s; ++t) {
+                        double y = Y[(int64_t)rows[p] * s + t];
+                        for (int q = 0; q < nbk; ++q) y -= Lb[p * nbk + q] * Z[(int64_t)rows[q] * s + t];
+                        Yn[(int64_t)rows[p] * s + t] = y;
+                    }
+                free(G); free(C);
+            }
+            double *tmp = Y; Y = Yn; Yn = tmp;
+        }
+    }
+    for (int step = 0; step < nu; ++step)
+        for (int b = 0; b < nb; ++b) {
+            int nbk = bptr[b + 1] - bptr[b];
+            const int *rows = bidx + bptr[b];
+            double *Lb = lam + (size_t)step * lamsize + lamoff[b];
+            for (int p = 0; p < nbk; ++p)
+                for (int q = 0; q < nbk; ++q) Lb[p * nbk + q] *= w[rows[p]] * w[rows[q]];
+        }
+    free(Y); free(Yn); free(Z); free(w);
+    csr_free(&A);
+    return 0;
+}
+
+ora_casc *ora_casc_create_sketch(const ora_hier *h, int kind, int nu, int prescale, int s, uint64_t seed,
+                                 int exact_first) {
+    if (s < 1) return NULL;
+    ora_casc *c = casc_alloc(h, kind, nu);
+    for (int l = 0; l < c->nlev; ++l) {
+        if (sketch_level(h, l, kind, nu, prescale, s, seed, exact_first, c->lamoff[l], c->lam[l]) != 0) {
+            ora_casc_free(c);
+            return NULL;
+        }
+    }
+    return c;
+}
+
 /* A cascade with all Lambda = 0, to be filled by ora_casc_set_lambda. */
 ora_casc *ora_casc_empty(const ora_hier *h, int kind, int nu) { return casc_alloc(h, kind, nu); }
 int ora_casc_nlev(const ora_casc *c) { return c->nlev; }

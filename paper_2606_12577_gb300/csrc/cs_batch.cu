@@ -28,6 +28,8 @@ namespace csx {
 
 constexpr int BMAXLEV = 16;
 constexpr int BMAXRHS = 32;
+constexpr int BMAXRESTART = 256;
+constexpr int RED_DOUBLES = 4 * 512;  // the kernel's shared reduction buffer
 
 template <typename T>
 struct BLevel {
@@ -593,30 +595,38 @@ __device__ void stage_fine(const BArgs &a, const BProb<T> *P, int what, int iarg
         }
         if (what == F_PAXPY) {
             // Z -= sum_i h_i V_i in T (the coefficients staged in shared
-            // memory as T), ||Z||^2 as in F_PROJ; pass iarg: 0 -> every
-            // extending right-hand side, 1 -> those reprojected
-            T *hs = reinterpret_cast<T *>(red);  // [(j + 1) m] <= restart * BMAXRHS <= 2048 values
-            for (int t = threadIdx.x; t < (jarg + 1) * m; t += blockDim.x) {
-                const int i = t / m, rr = t - i * m;
-                hs[t] = (T)a.hsum[(int64_t)(p * BMAXRHS + rr) * (a.restart + 2) + i];
-            }
-            __syncthreads();
+            // memory as T, in chunks of slots that fit the reduction buffer:
+            // one chunk up to restart 64 with 32 RHS), ||Z||^2 as in F_PROJ;
+            // pass iarg: 0 -> every extending right-hand side, 1 -> those
+            // reprojected
+            T *hs = reinterpret_cast<T *>(red);
+            const int cap = (int)((sizeof(double) * RED_DOUBLES) / sizeof(T)) / m;  // slots per chunk
+            const bool act = tm.on && (iarg == 0 ? !a.frozen[q] : a.reorth[q] != 0);
             double acc = 0.0;
-            if (tm.on && (iarg == 0 ? !a.frozen[q] : a.reorth[q] != 0)) {
-                for (int nn = n0; nn < ni;) {
-                    T c = T(0);
-                    for (int t = 0; t < KCH && nn < ni; ++t, nn += step) {
-                        const int64_t e = (int64_t)(i0 + nn) * m + r;
-                        T z = Z[e];
-#pragma unroll 4
-                        for (int i = 0; i <= jarg; ++i) z = fma(-hs[i * m + r], V[(int64_t)i * nm + e], z);
-                        Z[e] = z;
-                        c = fma(z, z, c);
-                    }
-                    acc += (double)c;
+            for (int s0 = 0; s0 <= jarg; s0 += cap) {
+                const int s1 = min(jarg + 1, s0 + cap);
+                const bool last = s1 == jarg + 1;
+                for (int t = threadIdx.x; t < (s1 - s0) * m; t += blockDim.x) {
+                    const int i = t / m, rr = t - i * m;
+                    hs[t] = (T)a.hsum[(int64_t)(p * BMAXRHS + rr) * (a.restart + 2) + s0 + i];
                 }
+                __syncthreads();
+                if (act) {
+                    for (int nn = n0; nn < ni;) {
+                        T c = T(0);
+                        for (int t = 0; t < KCH && nn < ni; ++t, nn += step) {
+                            const int64_t e = (int64_t)(i0 + nn) * m + r;
+                            T z = Z[e];
+#pragma unroll 4
+                            for (int i = s0; i < s1; ++i) z = fma(-hs[(i - s0) * m + r], V[(int64_t)i * nm + e], z);
+                            Z[e] = z;
+                            if (last) c = fma(z, z, c);
+                        }
+                        acc += (double)c;
+                    }
+                }
+                __syncthreads();  // hs aliases the reduction buffer
             }
-            __syncthreads();  // hs aliases the reduction buffer
             cta_sum_by_rhs(acc, m, red, a.part + (int64_t)k * BMAXRHS);
             continue;
         }
@@ -964,7 +974,7 @@ __device__ __forceinline__ void vcycle_stages(const BArgs &a, const BProb<T> *P,
 template <typename T>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_batch_solve(BArgs a) {
     cg::grid_group grid = cg::this_grid();
-    __shared__ double red[4 * 512];
+    __shared__ double red[RED_DOUBLES];
     __shared__ double wsum[16 * BMAXRHS];
     const BProb<T> *P = static_cast<const BProb<T> *>(a.probs);
     const int maxit = a.ctl->maxit;
@@ -1498,7 +1508,10 @@ cs_status cs_batch_create(int nprob, cs_hierarchy *const *h, cs_cascade *const *
         set_error("batched method must be CS_REFINE, CS_GMRES or CS_GMRES_RIGHT");
         return CS_ERR_ARG;
     }
-    if (o->method != CS_REFINE && (o->restart < 0 || o->restart > 64)) { set_error("GMRES restart must be in 1..64"); return CS_ERR_ARG; }
+    if (o->method != CS_REFINE && (o->restart < 0 || o->restart > BMAXRESTART)) {
+        set_error("GMRES restart must be in 1..%d", BMAXRESTART);
+        return CS_ERR_ARG;
+    }
     if (o->mu_pre < 0 || o->mu_post < 0 || o->mu_pre + o->mu_post < 1 || o->mu_pre > 16 || o->mu_post > 16) {
         set_error("bad smoothing counts");
         return CS_ERR_ARG;

@@ -391,3 +391,30 @@ def test_right_gmres_interface_32_rhs_fp32(n, count):
     for r in range(m):
         res = Bm[:, r] - stencil_matvec(A, X[:, r])
         assert np.linalg.norm(res) / np.linalg.norm(Bm[:, r]) <= 1.0001e-10
+
+
+def test_long_restart_stages_coefficients_in_chunks():
+    """Restart 100 with 32 right-hand sides (FP64): the projection
+    coefficients no longer fit the kernel's shared buffer at once and are
+    staged in chunks of slots; after 80 Arnoldi steps (one cycle) every
+    right-hand side checked equals the single-problem right-preconditioned
+    GMRES(100) after 80 steps."""
+    import torch
+
+    import paper_2606_12577_gb300 as cmg
+    A, _, _ = problems.batch_problem(0, nmin=120, nmax=129)
+    m = 32
+    B = problems.uniform(91, A.N * m, -1.0, 1.0)
+    hs, cs = _setup([(A, m, B)])
+    bt = cmg.Batch(hs, cs, [m], precision="fp64", method="gmres_right", restart=100)
+    b = torch.tensor(B, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    info = bt.solve([b], [x], tol=1e-300, maxit=80, raise_on_error=False)[0]
+    assert info.iterations == 80 and not info.converged
+    X = x.cpu().numpy().reshape(A.N, m)
+    Bm = B.reshape(A.N, m)
+    for r in (0, 13, 31):
+        x1 = torch.zeros(A.N, dtype=torch.float64, device="cuda")
+        cmg.solve(hs[0], cs[0], torch.tensor(Bm[:, r].copy(), device="cuda"), x1, method="gmres_right",
+                  precision="fp64", tol=1e-300, maxit=80, restart=100, raise_on_error=False)
+        assert rel_max(X[:, r], x1.cpu().numpy()) <= 1e-8, r

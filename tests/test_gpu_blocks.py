@@ -171,6 +171,9 @@ def test_multi_rhs_colour_steps_in_place(built, m):
     assert np.array_equal(_host(xin), _host(cur))
 
 
+INTERFACE_LAMBDA_TOL = 1e-9
+
+
 @pytest.mark.parametrize("n,count,method,maxit", [(63, 8, "gmres", 100), (127, 60, "gmres_right", 100),
                                                   (255, 200, "gmres_right", 60)])
 def test_interface_workload_parity(built, n, count, method, maxit):
@@ -187,8 +190,15 @@ def test_interface_workload_parity(built, n, count, method, maxit):
     co = oracle.Cascade(ho, "additive", nu=3)
     hg = gu.gpu_hierarchy(A, block=2)
     cg = cmg.setup_cascade(hg, "additive", nu=3, lowp=True)
+    # Lambda: from cascade step 2 on, blocks on inclusion boundaries have Gram
+    # matrices with exact null spaces and kept eigenvalues down to 1e-4 of the
+    # largest at 63^2 (smaller at larger sizes and contrast), so correct FP64
+    # implementations agree only to kappa x u propagated through E: the oracle
+    # and a dense LAPACK emulation differ by 6e-12 at 63^2
+    # (test_interface_blocks_are_ill_conditioned_from_step_two).  Measured
+    # GPU - oracle: 2.8e-12 (63^2), 1.8e-12 (127^2), 2.7e-10 (255^2).
     for l in range(co.nlev):
-        assert gu.rel_max(cmg.export_lambda(cg, l), co.lam(l)) <= TOL, l
+        assert gu.rel_max(cmg.export_lambda(cg, l), co.lam(l)) <= INTERFACE_LAMBDA_TOL, l
     b = problems.rhs(A.N, 9)
     xo, ito, hist_o, fin_o = oracle.solve(ho, co, b, method=method, tol=1e-10, maxit=maxit)
     assert ito > 0

@@ -571,6 +571,11 @@ def test_bf16_steps_match_oracle(built, name, kind):
         ref = np.where(keep, xd, ref)
         bound = np.where(keep, 0.0, bound)  # the other colour is copied exactly
     assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / np.maximum(bound, 1e-300)))
+    # the global max-norm check is the per-node bound's worst case: with
+    # |Lambda| |A| |x| <= 2 d lambda_max diag max|x| ~ 1.7 max|x| (Poisson,
+    # lambda <= 0.93 / diag), the bound reaches 2^-9 (1 + 3 (1 + 1.7 + ...))
+    # max|x| ~ 2e-2 max|ref|; 1e-2 (the earlier value) sat below that worst
+    # case and is not implied by the rounding analysis
     assert gu.rel_max(got, ref) <= 2e-2
 
 
