@@ -487,6 +487,47 @@ def batch_section(a, cmg, problems, dev):
     return out
 
 
+def cascade_forms_section(a, cmg, A, coeff, bd, dev):
+    """The headline workload (3D Poisson 256^3, V(2,2) RF, FP32 cycles in FP64
+    refinement to 1e-10) with other cascades: multiplicative red-black
+    nu = 2 and 3 (exact setup), and the sketched setup (32 Rademacher
+    columns, FP32 sketch vectors) for multiplicative nu = 3 and 4 and additive
+    nu = 3.  The exact multiplicative nu = 4 setup would keep radius-8 residual
+    rows (about 94 GB in FP64 at 256^3); the sketched one keeps two N x 32
+    arrays.  Each form: one untimed run, then one run timed with events
+    around the setup and the solve."""
+    import torch
+    forms = [("multiplicative", 2, {}), ("multiplicative", 3, {}),
+             ("multiplicative", 3, {"sketch": 32, "setup_precision": "fp32"}),
+             ("multiplicative", 4, {"sketch": 32, "setup_precision": "fp32"}),
+             ("additive", 3, {"sketch": 32, "setup_precision": "fp32"})]
+    s = torch.cuda.current_stream()
+    out = {}
+    for kind, nu, kw in forms:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        res = None
+        for rep in range(2):
+            torch.cuda.synchronize()
+            ev[0].record(s)
+            h = cmg.setup_hierarchy(A.dim, A.n, A.offsets, coeff)
+            c = cmg.setup_cascade(h, kind, nu=nu, lowp=True, sketch_seed=2024, **kw)
+            ev[1].record(s)
+            x = torch.zeros(A.N, dtype=torch.float64, device=dev)
+            info = cmg.solve(h, c, bd, x, method="refine", precision="fp32", tol=1e-10, mu_pre=a.mu,
+                             mu_post=a.mu, order=a.order, maxit=100, raise_on_error=False)
+            ev[2].record(s)
+            torch.cuda.synchronize()
+            res = {"setup_ms": ev[0].elapsed_time(ev[1]), "solve_ms": ev[1].elapsed_time(ev[2]),
+                   "total_ms": ev[0].elapsed_time(ev[2]), "iterations": info.iterations,
+                   "converged": bool(info.converged), "final_rel_residual": float(info.final_rel_residual),
+                   "cascade_bytes": int(c.nbytes()) if hasattr(c, "nbytes") else None}
+            del h, c, x
+            torch.cuda.empty_cache()
+        name = f"{kind}_nu{nu}" + ("_sketch32" if kw.get("sketch") else "_exact")
+        out[name] = res
+    return out
+
+
 # ------------------------------------------------------------------- ours
 def main():
     a = args_()
@@ -747,6 +788,8 @@ def main():
         result["interface_solve"] = interface_section(a, cmg, problems, dev)
         torch.cuda.empty_cache()
         result["batched_solve"] = batch_section(a, cmg, problems, dev)
+        torch.cuda.empty_cache()
+        result["cascade_forms"] = cascade_forms_section(a, cmg, A, coeff, bd, dev)
         torch.cuda.empty_cache()
         # ---- plain FP64 path (stationary V-cycle iteration)
         pinfo = []

@@ -129,7 +129,21 @@ typedef struct {
                       their inner products summed in FP64 over chunks of 8 terms and each
                       row's lambda = <E_i, R_i> / <R_i, R_i> divided in FP64 (Lambda agrees
                       with the FP64 setup to about 1e-5 relative; meant for FP32 cycles).
-                      Point blocks without alpha or model, else CS_ERR_UNSUPPORTED */
+                      Point blocks without alpha or model, else CS_ERR_UNSUPPORTED.  With
+                      sketch > 0: the sketch vectors Y and Z = A~ Y in FP32, the inner
+                      products and lambda in FP64 */
+    int sketch;          /* 0 (default): the exact setup.  s in 1..128: the sketched setup of the
+                      concluding remarks (Sec. 4): step l minimises ||(I - Lambda A) E_{l-1} S||_F
+                      for an N x s Rademacher sketch S of every level, carrying Y = E S
+                      (Y_0 = S; per node lam~ = <Y_i, Z_i> / <Z_i, Z_i>, Z = A~ Y, then
+                      Y_i -= lam~ Z_i; multiplicative colour by colour).  No residual
+                      fill-in: two N x s arrays per level whatever the depth.  Point-block
+                      hierarchies without alpha or model, else CS_ERR_UNSUPPORTED */
+    int sketch_exact_first; /* 1: the first step (multiplicative: its first colour, whose
+                      residual is E_0 = I) solves the unsketched problem, then sketches */
+    uint64_t sketch_seed;   /* S(i, t) of level l = sign of SplitMix64 (Steele, Lea and Flood
+                      2014) output mix(seed + (c + 1) 0x9E3779B97F4A7C15), c = l 2^48 + i s + t:
+                      +1 when its top bit is 0, else -1 */
 } cs_cascade_opts;
 
 /* Build the cascade (Lambda_l, l = 1..nu; multiplicative: Lambda_{l,k},

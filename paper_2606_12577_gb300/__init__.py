@@ -151,16 +151,20 @@ def setup_hierarchy(dim, n, offsets, coeff, periodic=False, coarse_max=4, max_le
 
 
 def setup_cascade(h: Hierarchy, kind="additive", nu=3, prescale=True, alpha=0, lowp=False, reuse=True, model=None,
-                  model_tol=0.05, setup_precision="fp64", stream=None):
+                  model_tol=0.05, setup_precision="fp64", sketch=0, sketch_seed=0, sketch_exact_first=False,
+                  stream=None):
     """Build the cascade; ``lowp``: False, True (FP32 copies for FP32
     cycles) or 2 (FP32 and BF16 copies); ``model`` (an ``MLP``) predicts the
     finest level's Lambda blocks, kept per block when its level-1 Frobenius
     objective is within ``model_tol`` of the exact one; ``setup_precision``
-    "fp32" forms the setup's residual and propagator rows in FP32."""
+    "fp32" forms the setup's residual and propagator rows (or the sketch
+    vectors) in FP32; ``sketch`` > 0 builds the sketched cascade with that
+    many Rademacher columns from ``sketch_seed``."""
     k = _capi.CS_MULTIPLICATIVE if kind == "multiplicative" else _capi.CS_ADDITIVE
     opts = _capi.cs_cascade_opts(k, nu, int(prescale), alpha, int(lowp), int(not reuse),
                                  C.c_void_p(model.ptr if model is not None else None), float(model_tol),
-                                 _capi.CS_FP32 if setup_precision == "fp32" else _capi.CS_FP64)
+                                 _capi.CS_FP32 if setup_precision == "fp32" else _capi.CS_FP64, int(sketch),
+                                 int(bool(sketch_exact_first)), int(sketch_seed) & 0xFFFFFFFFFFFFFFFF)
     out = C.c_void_p()
     _capi.check(_capi.lib().cs_setup_cascade(h.ptr, C.byref(opts), _stream(stream), C.byref(out)),
                 "cs_setup_cascade")

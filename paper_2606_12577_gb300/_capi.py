@@ -34,7 +34,8 @@ class cs_hierarchy_opts(C.Structure):
 
 class cs_cascade_opts(C.Structure):
     _fields_ = [("kind", C.c_int), ("nu", C.c_int), ("prescale", C.c_int), ("alpha", C.c_int), ("lowp", C.c_int),
-                ("no_reuse", C.c_int), ("model", C.c_void_p), ("model_tol", C.c_double), ("setup_precision", C.c_int)]
+                ("no_reuse", C.c_int), ("model", C.c_void_p), ("model_tol", C.c_double), ("setup_precision", C.c_int),
+                ("sketch", C.c_int), ("sketch_exact_first", C.c_int), ("sketch_seed", C.c_uint64)]
 
 
 class cs_vcycle_opts(C.Structure):

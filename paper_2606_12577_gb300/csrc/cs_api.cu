@@ -473,6 +473,21 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
             return CS_ERR_UNSUPPORTED;
         }
     }
+    if (o->sketch < 0 || o->sketch > 128) {
+        set_error("sketch must be in 0..128 (0: the exact setup)");
+        delete c;
+        return CS_ERR_ARG;
+    }
+    if (o->sketch > 0) {
+        bool blocks = false;
+        for (int l = 0; l < h->nlev; ++l) blocks = blocks || h->lev[l].bs > 1;
+        if (blocks || o->model || o->alpha > 0 || h->periodic) {
+            set_error("the sketched setup is implemented for Dirichlet point-block hierarchies without truncation "
+                      "or a model");
+            delete c;
+            return CS_ERR_UNSUPPORTED;
+        }
+    }
     if (o->lowp == 2)
         for (int l = 0; l < h->nlev; ++l)
             if (h->lev[l].bs > 1) {
@@ -490,6 +505,9 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
         // thread on its own stream, while the finest level runs here on s.
         auto level_setup = [&](int l, cudaStream_t st) -> cs_status {
             const Level &L = h->lev[l];
+            if (o->sketch > 0)
+                return cascade_setup_level_sketch(h, l, c->kind, c->nu, o->prescale, o->sketch, o->sketch_seed,
+                                                  o->sketch_exact_first, o->setup_precision == CS_FP32, c->lam[l], st);
             if (L.bs > 1) return cascade_setup_level_blocks(h, l, c->kind, c->nu, o->prescale, c->lam[l], st);
             int64_t peak = 0;
             return cascade_setup_level(h, l, c->kind, c->nu, o->prescale, !o->no_reuse, o->alpha,

@@ -927,35 +927,10 @@ __device__ void stage_hsum(const BArgs &a, const BProb<T> *P, int j, int pass) {
     }
 }
 
-// Optional stage trace (compiled in with -DCS_BATCH_TRACE only): after each
-// grid barrier thread 0 of CTA 0 records (stage code, %globaltimer), so the
-// gap between consecutive records is the wall time of one stage including
-// its barrier.  Codes: 1000 + 100 op + slot (cycle stages), 2000 + F_* (fine
-// stages), 3000 + P_* (per-problem stages), 4000 + pass (projection sums),
-// 0 (kernel start).
-#ifdef CS_BATCH_TRACE
-constexpr int BTRACE_CAP = 1 << 20;
-__device__ unsigned long long g_btrace[2 * BTRACE_CAP];
-__device__ int g_btrace_n;
-__device__ __forceinline__ void btrace(int code) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        unsigned long long t;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        const int k = g_btrace_n++;
-        if (k < BTRACE_CAP) {
-            g_btrace[2 * k] = (unsigned long long)code;
-            g_btrace[2 * k + 1] = t;
-        }
-    }
-}
-#define BSYNC(code)     \
-    do {                \
-        grid.sync();    \
-        btrace(code);   \
-    } while (0)
-#else
+// A grid-wide barrier between stages; the code names the stage it closes
+// (1000 + 100 op + slot: cycle stages, 2000 + F_*: fine stages, 3000 + P_*:
+// per-problem stages, 4000 + pass: projection sums, 5000: loop tests).
 #define BSYNC(code) grid.sync()
-#endif
 
 template <typename T>
 __device__ __forceinline__ void vcycle_stages(const BArgs &a, const BProb<T> *P, cg::grid_group &grid) {
@@ -978,9 +953,6 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_batch_solve(BAr
     __shared__ double wsum[16 * BMAXRHS];
     const BProb<T> *P = static_cast<const BProb<T> *>(a.probs);
     const int maxit = a.ctl->maxit;
-#ifdef CS_BATCH_TRACE
-    btrace(0);
-#endif
     // counting stages write ctl->cnt[ph] after flipping ph and clear the other
     // slot; the loop tests read the slot written last
     int ph = 0;
@@ -1096,19 +1068,6 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_batch_solve(BAr
 
 using namespace csx;
 
-#ifdef CS_BATCH_TRACE
-// copies up to cap (code, time) records of the trace to host memory and
-// clears it; returns the record count (not declared in the public header)
-extern "C" int cs_batch_trace_read(unsigned long long *host, int cap) {
-    int n = 0;
-    if (cudaMemcpyFromSymbol(&n, g_btrace_n, sizeof(int)) != cudaSuccess) return -1;
-    n = std::min(std::min(n, cap), BTRACE_CAP);
-    if (n > 0 && cudaMemcpyFromSymbol(host, g_btrace, sizeof(unsigned long long) * 2 * n) != cudaSuccess) return -1;
-    const int zero = 0;
-    if (cudaMemcpyToSymbol(g_btrace_n, &zero, sizeof(int)) != cudaSuccess) return -1;
-    return n;
-}
-#endif
 
 struct cs_batch {
     int nprob = 0, dmax = 0, precision = CS_FP32, order = CS_RF, mu_pre = 1, mu_post = 1, nu = 1;

@@ -220,6 +220,8 @@ cs_status coarse_factor(cs_hierarchy *h, cudaStream_t s);
 // row products summed in FP64 over chunks of 8); lambda is stored in FP64
 cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, int prescale, bool reuse, int alpha,
                               bool fp32, double *lam, cudaStream_t s, int64_t *peak_bytes);
+cs_status cascade_setup_level_sketch(const cs_hierarchy *h, int l, int kind, int nu, int prescale, int s,
+                                     uint64_t seed, int exact_first, bool fp32, double *lam, cudaStream_t st);
 cs_status cascade_setup_level_blocks(const cs_hierarchy *h, int l, int kind, int nu, int prescale, double *lam,
                                      cudaStream_t s);
 cs_status learned_setup_level0(const cs_hierarchy *h, cs_cascade *c, cs_mlp *M, double tol, double *lam,
