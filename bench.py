@@ -57,7 +57,10 @@ def args_():
     p.add_argument("--learned-n", type=int, default=127, help="interior nodes per side of a training mesh")
     p.add_argument("--learned-steps", type=int, default=6000, help="Adam steps")
     p.add_argument("--interface-maxit", type=int, default=300, help="GMRES steps allowed on the interface workload")
-    p.add_argument("--interface-restart", type=int, default=200,
+    p.add_argument("--interface-precision", default="fp64", choices=["fp32", "fp64"],
+                   help="cycle and Krylov precision of the batched interface solve (FP32 Krylov vectors resolve "
+                        "~1e-6 of ||r|| per GMRES cycle and restart, which the 1e8-contrast modes punish)")
+    p.add_argument("--interface-restart", type=int, default=160,
                    help="GMRES restart of the interface workload (the oracle needs 149 steps at 1023^2 without restart)")
     p.add_argument("--batch-count", type=int, default=512, help="problems of the batched workload timed")
     p.add_argument("--batch-fp64-count", type=int, default=32,
@@ -330,7 +333,8 @@ def interface_section(a, cmg, problems, dev):
     e[0].record(s)
     hs, cs = cmg.setup_many([Ai], kind="additive", nu=3, lowp=True, block=2)
     e[1].record(s)
-    bt = cmg.Batch(hs, cs, [m], precision="fp32", method=a.krylov, autotune=True, restart=a.interface_restart)
+    bt = cmg.Batch(hs, cs, [m], precision=a.interface_precision, method=a.krylov, autotune=True,
+                   restart=a.interface_restart)
     x = torch.zeros_like(bd)
     bt.solve([bd], [x], tol=1e-10, maxit=2, raise_on_error=False)  # warm-up (graph)
     x.zero_()
@@ -344,8 +348,9 @@ def interface_section(a, cmg, problems, dev):
     rel = []
     Xm = x.view(Ai.N, m)
     out = {"workload": "elliptic interface 1024^2, 200 inclusions (contrast 1e-4..1e4), 2x2-node blocks, additive "
-                       f"nu=3, 32 RHS, {a.krylov}({a.interface_restart}) V(1,1) RF FP32 cycles to 1e-10, the 32 RHS in "
-                       "one batched launch",
+                       f"nu=3, 32 RHS, {a.krylov}({a.interface_restart}) V(1,1) RF {a.interface_precision} cycles and "
+                       "Krylov vectors to 1e-10, the 32 RHS in one batched launch",
+           "precision": a.interface_precision,
            "krylov": a.krylov,
            "setup_ms": e[0].elapsed_time(e[1]), "solve_ms": e[2].elapsed_time(e[3]),
            "gmres_steps": info.iterations, "all_converged": bool(info.converged),

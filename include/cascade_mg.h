@@ -138,7 +138,8 @@ typedef struct {
                       (Y_0 = S; per node lam~ = <Y_i, Z_i> / <Z_i, Z_i>, Z = A~ Y, then
                       Y_i -= lam~ Z_i; multiplicative colour by colour).  No residual
                       fill-in: two N x s arrays per level whatever the depth.  Point-block
-                      hierarchies without alpha or model, else CS_ERR_UNSUPPORTED */
+                      hierarchies without alpha or model, else CS_ERR_UNSUPPORTED.  s = 1
+                      is degenerate beyond step 1 (it leaves Y = 0 in exact arithmetic) */
     int sketch_exact_first; /* 1: the first step (multiplicative: its first colour, whose
                       residual is E_0 = I) solves the unsketched problem, then sketches */
     uint64_t sketch_seed;   /* S(i, t) of level l = sign of SplitMix64 (Steele, Lea and Flood

@@ -37,11 +37,13 @@ PROBS = {
 @pytest.mark.parametrize("name,kind,s,exact_first", [
     ("p2d_64", "additive", 8, False), ("p2d_64", "multiplicative", 32, False), ("v2d_37", "additive", 64, True),
     ("v2d_37", "multiplicative", 100, True), ("v3d_17", "additive", 32, False), ("v3d_17", "multiplicative", 16, True),
-    ("c3d_33", "multiplicative", 32, False), ("c3d_33", "additive", 1, False)])
+    ("c3d_33", "multiplicative", 32, False), ("c3d_33", "additive", 2, False)])
 def test_sketched_lambda_matches_oracle(built, name, kind, s, exact_first):
     """FP64 sketched setup on every smoothing level (7/5-point fine levels,
     27/9-point Galerkin levels; 1..4 sketch entries per lane) equals the
-    oracle's to 1e-12."""
+    oracle's to 1e-12.  (A sketch needs more columns than a block has nodes:
+    with s = 1 a point's first step leaves Y = 0 in exact arithmetic and
+    every later lambda is a ratio of rounding errors.)"""
     import paper_2606_12577_gb300 as cmg
     A = PROBS[name]()
     ho = oracle.Hierarchy(A)
