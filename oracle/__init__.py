@@ -77,6 +77,12 @@ def _load():
             "ora_vcycle": (None, [P, P, I, I, I, P, P]),
             "ora_solve": (I, [P, P, I, I, I, I, D, I, I, P, P, P, P, P]),
             "ora_set_threads": (None, [I]),
+            "ora_ghier_new": (P, [I, P, P, P, D]),
+            "ora_ghier_add_level": (I, [P, I, P, P, P]),
+            "ora_ghier_set_blocks": (I, [P, I, P, P]),
+            "ora_ghier_finish": (None, [P, C.c_uint64]),
+            "ora_hier_ncol": (I, [P, I]),
+            "ora_block_prio": (C.c_uint64, [C.c_uint64, I, I]),
             "ora_casc_create_sketch": (P, [P, I, I, I, I, C.c_uint64, I]),
             "ora_rademacher": (D, [C.c_uint64, I, L, I, I]),
             "ora_max_threads": (I, []),
@@ -93,6 +99,12 @@ def rademacher(seed: int, level: int, i: int, t: int, s: int) -> float:
     """Entry (i, t) of the level's Rademacher sketch (the counter-based
     SplitMix64 stream described in cs_oracle.c)."""
     return float(_load().ora_rademacher(int(seed) & 0xFFFFFFFFFFFFFFFF, level, i, t, s))
+
+
+def block_priority(seed: int, level: int, b: int) -> int:
+    """Priority of block b of a level in the greedy colouring (SplitMix64
+    output at counter level 2^40 + b of the stream seeded with `seed`)."""
+    return int(_load().ora_block_prio(int(seed) & 0xFFFFFFFFFFFFFFFF, level, b))
 
 
 def set_threads(n: int) -> None:
@@ -134,6 +146,41 @@ class Hierarchy:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.ora_hier_free(self._h)
             self._h = None
+
+    @classmethod
+    def from_csr(cls, A, Ps, rscale: float = 1.0, blocks=None, seed: int = 0):
+        """Hierarchy of a general sparse operator (the CSR path): A (scipy
+        CSR, N0 x N0), one interpolation P_l per coarser level (scipy CSR,
+        N_l x N_{l+1}), Galerkin A_{l+1} = rscale P_l^T A_l P_l; blocks =
+        (bptr, bidx) of level 0 (point blocks if None, and on coarse levels);
+        greedy colouring with the block priorities of `seed`."""
+        lib = _load()
+        self = cls.__new__(cls)
+        self.dim, self.bs = 0, 0
+        A = A.tocsr()
+        A.sort_indices()
+        rp = np.ascontiguousarray(A.indptr, dtype=np.int64)
+        ci = np.ascontiguousarray(A.indices, dtype=np.int32)
+        v = _f64(A.data)
+        self._h = lib.ora_ghier_new(A.shape[0], _ptr(rp), _ptr(ci), _ptr(v), float(rscale))
+        for P in Ps:
+            P = P.tocsr()
+            P.sort_indices()
+            prp = np.ascontiguousarray(P.indptr, dtype=np.int64)
+            pci = np.ascontiguousarray(P.indices, dtype=np.int32)
+            if lib.ora_ghier_add_level(self._h, P.shape[1], _ptr(prp), _ptr(pci), _ptr(_f64(P.data))) != 0:
+                raise RuntimeError("too many levels")
+        if blocks is not None:
+            bptr = np.ascontiguousarray(blocks[0], dtype=np.int32)
+            bidx = np.ascontiguousarray(blocks[1], dtype=np.int32)
+            if lib.ora_ghier_set_blocks(self._h, len(bptr) - 1, _ptr(bptr), _ptr(bidx)) != 0:
+                raise ValueError("blocks are not a partition of the unknowns")
+        lib.ora_ghier_finish(self._h, int(seed) & 0xFFFFFFFFFFFFFFFF)
+        self.nlev = lib.ora_hier_nlev(self._h)
+        return self
+
+    def ncolours(self, l: int) -> int:
+        return int(_lib.ora_hier_ncol(self._h, l))
 
     def dims(self, l: int):
         out = np.zeros(3, dtype=np.int32)

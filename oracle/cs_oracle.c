@@ -395,6 +395,7 @@ typedef struct {
     /* block partition per level */
     int nb[ORA_MAXLEV];
     int *bptr[ORA_MAXLEV], *bidx[ORA_MAXLEV], *bpar[ORA_MAXLEV];
+    int ncol[ORA_MAXLEV];  /* colours of the multiplicative cascade per level (red-black: 2) */
     /* coarsest-level dense factor */
     int cn, cspd;
     double *cfac;
@@ -499,7 +500,7 @@ ora_hier *ora_hier_create(int dim, const int *n3, int nst, const int *off, const
         h->n3[l][0] = nc[0]; h->n3[l][1] = nc[1]; h->n3[l][2] = nc[2];
     }
     h->nlev = l + 1;
-    for (int k = 0; k < h->nlev; ++k) make_blocks(h, k);
+    for (int k = 0; k < h->nlev; ++k) { make_blocks(h, k); h->ncol[k] = 2; }
     factor_coarsest(h);
     return h;
 }
@@ -528,13 +529,162 @@ void ora_hier_blocks(const ora_hier *h, int l, int *bptr, int *bidx, int *bpar) 
     memcpy(bpar, h->bpar[l], sizeof(int) * (size_t)h->nb[l]);
 }
 
+/* ----------------------------------------- hierarchy from a CSR operator
+ * The block partition of A x = b is the user's (Sec. 2), and so are the
+ * hierarchy's transfers (Sec. 2.4): the user gives the finest operator and
+ * one interpolation P_l (N_l x N_{l+1}) per coarser level; the coarse
+ * operators are Galerkin, A_{l+1} = R_l A_l P_l with R_l = rscale P_l^T.
+ * Blocks: the user's partition of level 0, point blocks on coarser levels.
+ * The multiplicative cascade uses a greedy colouring of each level's block
+ * graph (blocks adjacent when A couples them in either direction): blocks
+ * in decreasing order of a pseudo-random priority (ties: smaller index
+ * first) take the smallest colour that no adjacent, already coloured block
+ * holds -- the colouring a parallel Jones-Plassmann pass with the same
+ * priorities produces.  Block b of level l has priority mix(seed + (c + 1) g)
+ * (SplitMix64, counter c = l 2^40 + b). */
+static uint64_t sm64_mix(uint64_t z);
+static uint64_t block_prio(uint64_t seed, int l, int b) {
+    uint64_t c = ((uint64_t)l << 40) + (uint64_t)b;
+    return sm64_mix(seed + (c + 1) * 0x9E3779B97F4A7C15ULL);
+}
+uint64_t ora_block_prio(uint64_t seed, int l, int b) { return block_prio(seed, l, b); }
+
+static void csr_copy_in(csr *A, int n, int m, const int64_t *rp, const int *ci, const double *v) {
+    A->n = n; A->m = m;
+    int64_t nnz = rp[n];
+    A->rp = xmalloc(sizeof(int64_t) * ((size_t)n + 1));
+    A->ci = xmalloc(sizeof(int) * (size_t)(nnz ? nnz : 1));
+    A->v = xmalloc(sizeof(double) * (size_t)(nnz ? nnz : 1));
+    memcpy(A->rp, rp, sizeof(int64_t) * ((size_t)n + 1));
+    memcpy(A->ci, ci, sizeof(int) * (size_t)nnz);
+    memcpy(A->v, v, sizeof(double) * (size_t)nnz);
+}
+
+ora_hier *ora_ghier_new(int N, const int64_t *rp, const int *ci, const double *v, double rscale) {
+    ora_hier *h = xcalloc(1, sizeof(ora_hier));
+    h->dim = 0; h->bs = 0; h->rscale = rscale; h->nlev = 1;
+    h->n3[0][0] = N; h->n3[0][1] = 1; h->n3[0][2] = 1;
+    csr_copy_in(&h->A[0], N, N, rp, ci, v);
+    return h;
+}
+
+/* Appends level l+1 below the current coarsest level l: P is N_l x Nc. */
+int ora_ghier_add_level(ora_hier *h, int Nc, const int64_t *prp, const int *pci, const double *pv) {
+    int l = h->nlev - 1;
+    if (h->nlev >= ORA_MAXLEV) return -1;
+    csr_copy_in(&h->P[l], h->A[l].n, Nc, prp, pci, pv);
+    csr Pt, AP;
+    csr_transpose(&h->P[l], &Pt);
+    csr_spgemm(&h->A[l], &h->P[l], 1.0, &AP);
+    csr_spgemm(&Pt, &AP, h->rscale, &h->A[l + 1]);
+    csr_transpose(&h->P[l], &h->R[l]);
+    for (int64_t p = 0; p < h->R[l].rp[h->R[l].n]; ++p) h->R[l].v[p] *= h->rscale;
+    csr_free(&Pt); csr_free(&AP);
+    h->nlev = l + 2;
+    h->n3[l + 1][0] = Nc; h->n3[l + 1][1] = 1; h->n3[l + 1][2] = 1;
+    return 0;
+}
+
+/* The user's block partition of level 0 (every node in exactly one block;
+ * the nodes of a block are used in the order given).  Returns -1 if it is
+ * not a partition. */
+int ora_ghier_set_blocks(ora_hier *h, int nb, const int *bptr, const int *bidx) {
+    int N = h->A[0].n;
+    if (nb < 1 || bptr[0] != 0 || bptr[nb] != N) return -1;
+    int *seen = xcalloc((size_t)N, sizeof(int));
+    for (int p = 0; p < N; ++p) {
+        if (bidx[p] < 0 || bidx[p] >= N || seen[bidx[p]]++) { free(seen); return -1; }
+    }
+    free(seen);
+    for (int b = 0; b < nb; ++b) if (bptr[b + 1] <= bptr[b]) return -1;
+    free(h->bptr[0]); free(h->bidx[0]);
+    h->nb[0] = nb;
+    h->bptr[0] = xmalloc(sizeof(int) * ((size_t)nb + 1));
+    h->bidx[0] = xmalloc(sizeof(int) * (size_t)N);
+    memcpy(h->bptr[0], bptr, sizeof(int) * ((size_t)nb + 1));
+    memcpy(h->bidx[0], bidx, sizeof(int) * (size_t)N);
+    return 0;
+}
+
+typedef struct { uint64_t p; int b; } prio_t;
+static int cmp_prio(const void *a, const void *b) {
+    const prio_t *x = a, *y = b;
+    if (x->p != y->p) return x->p > y->p ? -1 : 1; /* larger priority first */
+    return (x->b > y->b) - (x->b < y->b);          /* then smaller index */
+}
+
+static void greedy_colour(ora_hier *h, int l, uint64_t seed) {
+    const csr *A = &h->A[l];
+    int N = A->n, nb = h->nb[l];
+    int *blk = xmalloc(sizeof(int) * (size_t)N);
+    for (int b = 0; b < nb; ++b) for (int p = h->bptr[l][b]; p < h->bptr[l][b + 1]; ++p) blk[h->bidx[l][p]] = b;
+    /* symmetrised block adjacency as lists (duplicates allowed) */
+    int64_t nnz = A->rp[N];
+    int *deg = xcalloc((size_t)nb + 1, sizeof(int));
+    for (int i = 0; i < N; ++i)
+        for (int64_t q = A->rp[i]; q < A->rp[i + 1]; ++q) {
+            int bi = blk[i], bj = blk[A->ci[q]];
+            if (bi != bj) { deg[bi + 1]++; deg[bj + 1]++; }
+        }
+    for (int b = 0; b < nb; ++b) deg[b + 1] += deg[b];
+    int *adj = xmalloc(sizeof(int) * (size_t)(deg[nb] ? deg[nb] : 1));
+    int *fill = xmalloc(sizeof(int) * (size_t)nb);
+    for (int b = 0; b < nb; ++b) fill[b] = deg[b];
+    for (int i = 0; i < N; ++i)
+        for (int64_t q = A->rp[i]; q < A->rp[i + 1]; ++q) {
+            int bi = blk[i], bj = blk[A->ci[q]];
+            if (bi != bj) { adj[fill[bi]++] = bj; adj[fill[bj]++] = bi; }
+        }
+    (void)nnz;
+    prio_t *ord = xmalloc(sizeof(prio_t) * (size_t)nb);
+    for (int b = 0; b < nb; ++b) { ord[b].p = block_prio(seed, l, b); ord[b].b = b; }
+    qsort(ord, (size_t)nb, sizeof(prio_t), cmp_prio);
+    int *col = h->bpar[l];
+    for (int b = 0; b < nb; ++b) col[b] = -1;
+    int maxc = 0;
+    char used[256];
+    for (int k = 0; k < nb; ++k) {
+        int b = ord[k].b;
+        memset(used, 0, sizeof(used));
+        for (int q = deg[b]; q < deg[b + 1]; ++q)
+            if (col[adj[q]] >= 0 && col[adj[q]] < 256) used[col[adj[q]]] = 1;
+        int c = 0;
+        while (c < 255 && used[c]) ++c;
+        col[b] = c;
+        if (c + 1 > maxc) maxc = c + 1;
+    }
+    h->ncol[l] = maxc;
+    free(blk); free(deg); free(adj); free(fill); free(ord);
+}
+
+/* Point blocks on every level without a partition, the colourings, and the
+ * coarsest factorisation. */
+void ora_ghier_finish(ora_hier *h, uint64_t seed) {
+    for (int l = 0; l < h->nlev; ++l) {
+        int N = h->A[l].n;
+        if (!h->bptr[l]) {
+            h->nb[l] = N;
+            h->bptr[l] = xmalloc(sizeof(int) * ((size_t)N + 1));
+            h->bidx[l] = xmalloc(sizeof(int) * (size_t)N);
+            for (int i = 0; i <= N; ++i) h->bptr[l][i] = i;
+            for (int i = 0; i < N; ++i) h->bidx[l][i] = i;
+        }
+        free(h->bpar[l]);
+        h->bpar[l] = xmalloc(sizeof(int) * (size_t)h->nb[l]);
+        greedy_colour(h, l, seed);
+    }
+    factor_coarsest(h);
+}
+int ora_hier_ncol(const ora_hier *h, int l) { return h->ncol[l]; }
+
 /* ------------------------------------------------------- cascade setup */
 typedef struct { int nnz; int *c; double *v; } srow;
 
 typedef struct {
     int nlev;      /* levels with a smoother */
     int kind;      /* 0 additive, 1 multiplicative red-black */
-    int ncol, nu;
+    int ncol, nu;      /* ncol: the largest colour count over the levels */
+    int ncl[ORA_MAXLEV]; /* colours per level (1 for the additive form) */
     int64_t lamsize[ORA_MAXLEV];
     int64_t *lamoff[ORA_MAXLEV];
     double *lam[ORA_MAXLEV];   /* [nu][lamsize]; block b row-major n_b x n_b */
@@ -552,7 +702,7 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
     const csr *A0 = &h->A[l];
     int N = A0->n, nb = h->nb[l];
     const int *bptr = h->bptr[l], *bidx = h->bidx[l];
-    int ncol = kind == 1 ? 2 : 1;
+    int ncol = kind == 1 ? h->ncol[l] : 1;
     int64_t lamsize = lamoff[nb];
     /* prescaling W = diag(A_ii^{-1/2}) (Sec. 2.3.1) */
     double *w = xmalloc(sizeof(double) * (size_t)N);
@@ -736,8 +886,13 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
 
 static ora_casc *casc_alloc(const ora_hier *h, int kind, int nu) {
     ora_casc *c = xcalloc(1, sizeof(ora_casc));
-    c->kind = kind; c->nu = nu; c->ncol = kind == 1 ? 2 : 1;
+    c->kind = kind; c->nu = nu;
     c->nlev = h->nlev > 1 ? h->nlev - 1 : 1;
+    c->ncol = 1;
+    for (int l = 0; l < c->nlev; ++l) {
+        c->ncl[l] = kind == 1 ? h->ncol[l] : 1;
+        if (c->ncl[l] > c->ncol) c->ncol = c->ncl[l];
+    }
     for (int l = 0; l < c->nlev; ++l) {
         int nb = h->nb[l];
         c->lamoff[l] = xmalloc(sizeof(int64_t) * ((size_t)nb + 1));
@@ -748,7 +903,7 @@ static ora_casc *casc_alloc(const ora_hier *h, int kind, int nu) {
         }
         c->lamsize[l] = c->lamoff[l][nb];
         c->lam[l] = xcalloc((size_t)nu * (size_t)c->lamsize[l], sizeof(double));
-        c->efrob[l] = xcalloc((size_t)nu * c->ncol + 1, sizeof(double));
+        c->efrob[l] = xcalloc((size_t)nu * c->ncl[l] + 1, sizeof(double));
     }
     return c;
 }
@@ -806,7 +961,7 @@ static int sketch_level(const ora_hier *h, int l, int kind, int nu, int prescale
     const csr *A0 = &h->A[l];
     int N = A0->n, nb = h->nb[l];
     const int *bptr = h->bptr[l], *bidx = h->bidx[l];
-    int ncol = kind == 1 ? 2 : 1;
+    int ncol = kind == 1 ? h->ncol[l] : 1;
     int64_t lamsize = lamoff[nb];
     double *w = xmalloc(sizeof(double) * (size_t)N);
     for (int i = 0; i < N; ++i) {
@@ -925,7 +1080,7 @@ void ora_casc_set_lambda(ora_casc *c, int l, const double *in) {
     memcpy(c->lam[l], in, sizeof(double) * (size_t)c->nu * (size_t)c->lamsize[l]);
 }
 void ora_casc_efrob(const ora_casc *c, int l, double *out) {
-    memcpy(out, c->efrob[l], sizeof(double) * ((size_t)c->nu * c->ncol + 1));
+    memcpy(out, c->efrob[l], sizeof(double) * ((size_t)c->nu * c->ncl[l] + 1));
 }
 
 /* ------------------------------------------------------------ smoother */
@@ -949,8 +1104,8 @@ void ora_smooth(const ora_hier *h, const ora_casc *c, int l, int reverse, const 
     double *r = xmalloc(sizeof(double) * (size_t)N);
     for (int step = 0; step < c->nu; ++step) {
         int L = reverse ? c->nu - 1 - step : step;
-        for (int kk = 0; kk < c->ncol; ++kk) {
-            int K = reverse ? c->ncol - 1 - kk : kk;
+        for (int kk = 0; kk < c->ncl[l]; ++kk) {
+            int K = reverse ? c->ncl[l] - 1 - kk : kk;
             ora_residual(h, l, b, x, r);
 #pragma omp parallel for schedule(static)
             for (int bk = 0; bk < nb; ++bk) {

@@ -348,6 +348,90 @@ def nonsymmetric_3d(n: int, seed: int) -> Stencil:
     return Stencil(3, (n, n, n), offs, coeff, False, name=f"nonsym3d_{n}")
 
 
+def stencil_csr(A: Stencil):
+    """The operator of a Stencil as a scipy CSR matrix (couplings to nodes
+    outside the grid dropped; periodic stencils wrap)."""
+    import scipy.sparse as sp
+    nx, ny, nz = A.n
+    N = A.N
+    i = np.arange(N)
+    ix, iy, iz = i % nx, (i // nx) % ny, i // (nx * ny)
+    rows, cols, vals = [], [], []
+    for s_, (dx, dy, dz) in enumerate(A.offsets):
+        jx, jy, jz = ix + dx, iy + dy, iz + dz
+        if A.periodic:
+            jx, jy, jz = jx % nx, jy % ny, jz % nz
+            ok = np.ones(N, bool)
+        else:
+            ok = (jx >= 0) & (jx < nx) & (jy >= 0) & (jy < ny) & (jz >= 0) & (jz < nz)
+        rows.append(i[ok])
+        cols.append((jx + nx * (jy + ny * jz))[ok])
+        vals.append(A.coeff[s_][ok])
+    M = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N))
+    M.sum_duplicates()
+    M.sort_indices()
+    return M
+
+
+def interpolation_1d(n: int):
+    """Linear interpolation from the coarse nodes (the fine nodes with even
+    1-based index, n // 2 of them) to the n fine nodes of one axis, as a
+    dense (n, n // 2) array."""
+    nc = n // 2
+    P = np.zeros((n, nc))
+    for c in range(nc):
+        f = 2 * c + 1
+        P[f, c] = 1.0
+        P[f - 1, c] = 0.5
+        if f + 1 < n:
+            P[f + 1, c] = 0.5
+    return P
+
+
+def permutation(n: int, seed: int) -> np.ndarray:
+    """A seeded random permutation of range(n): perm[new] = old."""
+    return np.argsort(uniform01(seed, n), kind="stable")
+
+
+def unstructured_q1(n: int, seed: int, coarse_side: int = 3, block: int = 3):
+    """The jittered Q1 operator of ``q1_jittered(n, seed)`` handed over as a
+    general sparse problem: its CSR matrix with the interior nodes renumbered
+    by a seeded random permutation, the bilinear interpolations P_l of the
+    even-index coarsening (down to sides <= coarse_side) renumbered the same
+    way on both of their levels, and a partition of level 0 into
+    block x block node blocks (partial at the upper edges) in the new
+    numbering.  Nothing of the grid survives in the numbering, so a solver
+    that reads it sees an unstructured mesh.  Returns a dict with A (scipy
+    CSR), Ps (list of scipy CSR), blocks (bptr, bidx) and perms (perm[new] =
+    old per level)."""
+    import scipy.sparse as sp
+    St = q1_jittered(n, seed)
+    sides = [n]
+    while sides[-1] > coarse_side and sides[-1] // 2 >= 1:
+        sides.append(sides[-1] // 2)
+    perms = [permutation(m * m, seed + 7919 * (k + 1)) for k, m in enumerate(sides)]
+    inv = [np.argsort(pm) for pm in perms]  # inv[old] = new
+    A = stencil_csr(St)
+    A = A[perms[0]][:, perms[0]].tocsr()
+    A.sort_indices()
+    Ps = []
+    for k in range(len(sides) - 1):
+        P1 = sp.csr_matrix(interpolation_1d(sides[k]))
+        P = sp.kron(P1, P1, format="csr")  # index ix + n iy: kron(P_y, P_x)
+        P = P[perms[k]][:, perms[k + 1]].tocsr()
+        P.sort_indices()
+        Ps.append(P)
+    nb1 = (n + block - 1) // block
+    members = [[] for _ in range(nb1 * nb1)]
+    for old in range(n * n):
+        ix, iy = old % n, old // n
+        members[ix // block + nb1 * (iy // block)].append(int(inv[0][old]))
+    bptr = np.zeros(len(members) + 1, dtype=np.int32)
+    bptr[1:] = np.cumsum([len(m) for m in members])
+    bidx = np.concatenate([np.sort(np.array(m, dtype=np.int32)) for m in members]).astype(np.int32)
+    return {"A": A, "Ps": Ps, "blocks": (bptr, bidx), "perms": perms, "sides": sides}
+
+
 def config_seed(config: int, problem: int = 0) -> int:
     """Seed of problem ``problem`` of workload ``config`` (run seed 0)."""
     return 1000 * config + problem

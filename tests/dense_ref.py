@@ -62,7 +62,7 @@ def dense_cascade(Ad, blocks, parity, kind, nu, alpha=0, bs_blocks=None):
     w = 1.0 / np.sqrt(np.diag(Ad))
     At = w[:, None] * Ad * w[None, :]
     E = np.eye(N)
-    ncol = 2 if kind == "multiplicative" else 1
+    ncol = (int(np.max(parity)) + 1 if len(parity) else 1) if kind == "multiplicative" else 1
     blk_of = np.zeros(N, dtype=int)
     for b, m in enumerate(blocks):
         blk_of[m] = b
@@ -74,12 +74,17 @@ def dense_cascade(Ad, blocks, parity, kind, nu, alpha=0, bs_blocks=None):
             Enew = E.copy()
             AE = At @ E
             for b, rows in enumerate(blocks):
-                if ncol == 2 and parity[b] != k:
+                if kind == "multiplicative" and parity[b] != k:
                     continue
                 Rb = AE[rows, :]
                 Eb = E[rows, :]
-                # Lam Rb ~= Eb in the least-squares sense  <=>  Rb^T Lam^T ~= Eb^T
-                lt = np.linalg.lstsq(Rb.T, Eb.T, rcond=None)[0].T
+                # Lam Rb ~= Eb in the least-squares sense  <=>  Rb^T Lam^T ~= Eb^T,
+                # minimum norm where Rb is rank deficient: singular values with
+                # sigma^2 <= 1e-14 sum(sigma^2) count as zero (the method's rule,
+                # eigenvalues of G = Rb Rb^T at or below 1e-14 tr G), as lstsq's rcond
+                sv = np.linalg.svd(Rb, compute_uv=False)
+                rc = np.sqrt(1e-14 * np.sum(sv ** 2)) / sv[0] if sv.size and sv[0] > 0 else 1.0
+                lt = np.linalg.lstsq(Rb.T, Eb.T, rcond=rc)[0].T
                 L[np.ix_(rows, rows)] = lt
                 new = Eb - lt @ Rb
                 if alpha > 0:

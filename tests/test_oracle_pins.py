@@ -757,3 +757,92 @@ def test_sketched_setup_gives_a_converging_multigrid(kind):
         fro = np.linalg.norm(Y)
         assert prev is None or fro <= prev * (1 + 1e-12)
         prev = fro
+
+
+# ------------------------------------------- general sparse (CSR) hierarchy
+def test_csr_hierarchy_galerkin_and_greedy_colouring():
+    """The CSR path on a renumbered (unstructured) jittered Q1 mesh: every
+    coarse operator is rscale P^T A P (scipy's sparse product), and every
+    level's colouring is a proper colouring of the block graph that is
+    greedy in priority order (each smaller colour sits on a neighbour of
+    higher priority)."""
+    from tests import gpu_util as gu
+    u = problems.unstructured_q1(31, 3)
+    seed = 11
+    h = oracle.Hierarchy.from_csr(u["A"], u["Ps"], rscale=0.25, seed=seed)
+    assert h.nlev == len(u["Ps"]) + 1
+    A = u["A"]
+    for l, P in enumerate(u["Ps"]):
+        ref = (0.25 * (P.T @ A @ P)).tocsr()
+        got = gu.oracle_csr(h, l + 1)
+        assert abs(got - ref).max() <= 1e-14 * abs(ref).max(), l
+        A = ref
+    for l in range(h.nlev):
+        bptr, bidx, col = h.blocks(l)
+        M = gu.oracle_csr(h, l).tocoo()
+        blk = np.empty(M.shape[0], dtype=int)
+        for b in range(len(bptr) - 1):
+            blk[bidx[bptr[b]:bptr[b + 1]]] = b
+        bi, bj = blk[M.row], blk[M.col]
+        off = bi != bj
+        assert not np.any(col[bi[off]] == col[bj[off]]), l
+        assert h.ncolours(l) == col.max() + 1
+        nbrs = [set() for _ in range(len(bptr) - 1)]
+        for x, y in zip(bi[off], bj[off]):
+            nbrs[x].add(y)
+            nbrs[y].add(x)
+        pr = [oracle.block_priority(seed, l, b) for b in range(len(bptr) - 1)]
+        for b in range(len(bptr) - 1):
+            higher = [c for c in nbrs[b] if (pr[c], -c) > (pr[b], -b)]
+            assert set(range(col[b])) <= {col[c] for c in higher}, (l, b)
+
+
+def test_csr_hierarchy_reduces_to_the_structured_one():
+    """A structured operator handed over as CSR with the bilinear
+    interpolations and rscale = 2^-2 gives the structured hierarchy's
+    operators, its additive cascade and its solve."""
+    import scipy.sparse as sp
+    from tests import gpu_util as gu
+    A = _small_problem(2, 15, seed=99)
+    hs = oracle.Hierarchy(A)
+    Ps, n = [], 15
+    while n > 4:
+        P1 = sp.csr_matrix(problems.interpolation_1d(n))
+        Ps.append(sp.kron(P1, P1, format="csr"))
+        n //= 2
+    hc = oracle.Hierarchy.from_csr(problems.stencil_csr(A), Ps, rscale=0.25, seed=1)
+    assert hc.nlev == hs.nlev
+    for l in range(hs.nlev):
+        S, G = gu.oracle_csr(hs, l), gu.oracle_csr(hc, l)
+        assert abs(S - G).max() <= 1e-14 * abs(S).max(), l
+    cs = oracle.Cascade(hs, "additive", nu=3)
+    cc = oracle.Cascade(hc, "additive", nu=3)
+    for l in range(cs.nlev):
+        assert np.abs(cs.lam(l) - cc.lam(l)).max() <= 1e-13 * np.abs(cs.lam(l)).max()
+    b = problems.rhs(A.N, 4)
+    assert oracle.solve(hs, cs, b, method="gmres_right")[1] == oracle.solve(hc, cc, b, method="gmres_right")[1]
+
+
+@pytest.mark.parametrize("kind,use_blocks", [("multiplicative", False), ("multiplicative", True), ("additive", True)])
+def test_csr_cascade_matches_dense_lstsq(kind, use_blocks):
+    """Algorithm 2 / the SM algorithm on the unstructured mesh with the
+    greedy colouring (more than two colours: the snapshot per colour of
+    E_{l,k} = (I - Lambda_{l,k} A) E_{l,k-1}) and with user blocks of 3x3
+    nodes, against explicit dense matrices and numpy lstsq."""
+    u = problems.unstructured_q1(9, 5)
+    h = oracle.Hierarchy.from_csr(u["A"], u["Ps"], rscale=0.25, seed=2, blocks=u["blocks"] if use_blocks else None)
+    if kind == "multiplicative":
+        assert h.ncolours(0) > 2
+    c = oracle.Cascade(h, kind, nu=2)
+    bptr, bidx, col = h.blocks(0)
+    blist = [bidx[bptr[b]:bptr[b + 1]] for b in range(len(bptr) - 1)]
+    _, lam_u, _ = dense_ref.dense_cascade(u["A"].toarray(), blist, col, kind, 2)
+    lam = c.lam(0)
+    for step in range(2):
+        off = 0
+        for b, rows in enumerate(blist):
+            nb = len(rows)
+            got = lam[step, off:off + nb * nb].reshape(nb, nb)
+            ref = lam_u[step][col[b] if kind == "multiplicative" else 0][np.ix_(rows, rows)]
+            assert np.abs(got - ref).max() <= 1e-10 * max(np.abs(ref).max(), 1e-300), (step, b)
+            off += nb * nb
