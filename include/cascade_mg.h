@@ -451,6 +451,82 @@ cs_status cs_learned_status(const cs_cascade *c, int *used, double *ratio);
 cs_status cs_learned_stats(const cs_cascade *c, int64_t *blocks, int64_t *full_blocks, int64_t *predicted_blocks,
                            double *ratio_predicted, double *ratio_used);
 
+/* ------------------------------------------ general sparse operators */
+/* The method for an arbitrary block-partitioned A x = b (Sec. 2: the user
+ * chooses the blocks; Sec. 2.4: the user chooses the transfers), with
+ * index-driven kernels instead of stencils.  The user gives the finest
+ * operator in CSR form, one interpolation P_l (N_l x N_{l+1}) per coarser
+ * level, the restriction scale (R_l = rscale P_l^T; the V-cycle does not
+ * depend on it) and optionally a block partition of the finest level
+ * (point blocks elsewhere).  The coarse operators are Galerkin,
+ * A_{l+1} = R_l A_l P_l, formed on the device.  The multiplicative cascade
+ * colours every level's block graph (blocks adjacent when A couples them in
+ * either direction) greedily in decreasing order of a pseudo-random
+ * priority (ties: smaller block index), computed in parallel by
+ * Jones-Plassmann rounds: block b of level l has priority
+ * mix(seed + (c + 1) 0x9E3779B97F4A7C15) (SplitMix64, c = l 2^40 + b); the
+ * colouring is a graph colouring, so colour steps run in place.  Setup
+ * (Algorithm 2 / SM Algorithm), cycles and solves are FP64. */
+typedef struct {
+    int n, m;                /* rows, columns */
+    const int64_t *rowptr;   /* [n + 1] */
+    const int32_t *col;      /* [nnz], ascending within every row */
+    const double *val;       /* [nnz] */
+    int on_host;             /* 1: host arrays; 0: device arrays (both are copied) */
+} cs_csr;
+
+typedef struct cs_ghier cs_ghier;
+typedef struct cs_gcascade cs_gcascade;
+
+/* nP interpolations P[0..nP-1] (P[l]: N_l x N_{l+1}); blocks: nblocks > 0 with
+ * HOST arrays bptr [nblocks + 1] and bidx [N_0] (a partition of the finest
+ * unknowns, at most 16 per block; the nodes of a block in the order given),
+ * or nblocks = 0 for point blocks.  The coarsest level (at most 4096
+ * unknowns) is factorised densely.  Errors: CS_ERR_ARG (shapes, not a
+ * partition, block too large, more than 64 colours), CS_ERR_SINGULAR,
+ * CS_ERR_NOMEM, CS_ERR_CUDA. */
+cs_status cs_gsetup_hierarchy(const cs_csr *A0, int nP, const cs_csr *P, double rscale, int nblocks,
+                              const int *bptr, const int *bidx, uint64_t colour_seed, cs_stream stream,
+                              cs_ghier **out);
+/* The cascade of every smoothing level: kind CS_ADDITIVE or
+ * CS_MULTIPLICATIVE (greedy colours), depth nu (1..8), prescale as in
+ * cs_cascade_opts.  The residual rows E are kept per block over the union
+ * of the block rows' columns; their patterns are built on the host, their
+ * values on the device.  Errors: CS_ERR_ARG (non-positive diagonal under
+ * prescaling), CS_ERR_NOMEM, CS_ERR_CUDA. */
+cs_status cs_gsetup_cascade(cs_ghier *h, int kind, int nu, int prescale, cs_stream stream, cs_gcascade **out);
+/* One cascade step (a single kernel launch on point-block levels):
+ * out = x - Lambda_{step+1[, colour]} (A x - b) over every block (colour
+ * = -1, additive) or over the blocks of one colour (multiplicative; out may
+ * equal x, and with out != x the other blocks are copied). */
+cs_status cs_gsweep(const cs_ghier *h, cs_gcascade *c, int level, int step, int colour, const double *b,
+                    const double *x, double *out, cs_stream stream);
+/* One application of the depth-nu cascade (forward, or reverse with the
+ * transposed blocks in reverse step and colour order), x in place. */
+cs_status cs_gsmooth(const cs_ghier *h, cs_gcascade *c, int level, int reverse, const double *b, double *x,
+                     cs_stream stream);
+/* x <- V(x, b) (Algorithm 1) with the cycle options of cs_vcycle (FP64). */
+cs_status cs_gvcycle(const cs_ghier *h, cs_gcascade *c, const cs_vcycle_opts *opts, const double *b, double *x,
+                     cs_stream stream);
+/* Solve as cs_solve; methods CS_STATIONARY and CS_GMRES_RIGHT; FP64
+ * cycles; b, x device vectors.  Errors as cs_solve. */
+cs_status cs_gsolve(const cs_ghier *h, cs_gcascade *c, const cs_solve_opts *opts, const double *b, double *x,
+                    cs_solve_info *info, cs_stream stream);
+/* Level sizes: rows, stored entries, blocks, colours (HOST outputs, any may be NULL). */
+cs_status cs_gquery_level(const cs_ghier *h, int level, int *n, int64_t *nnz, int *nblocks, int *ncolours);
+int cs_gnlevels(const cs_ghier *h);
+/* HOST copies: the level's CSR operator; the colour of every block; the
+ * block partition (bptr [nblocks + 1], bidx [n]); Lambda as [nu][lamsize]
+ * (block b's n_b x n_b matrix row-major at its offset, blocks in order;
+ * Lambda_{l,k} on the blocks of colour k). */
+cs_status cs_gexport_operator(const cs_ghier *h, int level, int64_t *rowptr, int32_t *col, double *val);
+cs_status cs_gexport_colours(const cs_ghier *h, int level, int32_t *colour);
+cs_status cs_gexport_blocks(const cs_ghier *h, int level, int32_t *bptr, int32_t *bidx);
+int64_t cs_glamsize(const cs_gcascade *c, int level);
+cs_status cs_gexport_lambda(const cs_gcascade *c, int level, double *host_lambda);
+void cs_gdestroy_hierarchy(cs_ghier *h);
+void cs_gdestroy_cascade(cs_gcascade *c);
+
 /* -------------------------------------------------------------- queries */
 typedef struct {
     int dim;

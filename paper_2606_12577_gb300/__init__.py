@@ -21,7 +21,8 @@ from ._capi import CascadeError
 __all__ = ["setup_hierarchy", "setup_cascade", "vcycle", "solve", "smooth", "sweep", "sweep_rhs", "residual_restrict",
            "prolong_correct", "coarse_solve", "residual", "query_level", "export_operator", "export_colours",
            "export_lambda", "kernel_launches", "smooth_noalloc", "MLP", "block_features", "block_targets", "learned_status", "learned_stats", "setup_many", "Batch", "solve_batched", "Hierarchy", "Cascade", "SolveInfo",
-           "CascadeError"]
+           "CascadeError", "GHierarchy", "GCascade", "gsetup_hierarchy", "gsetup_cascade", "gexport_lambda", "gsweep",
+           "gsmooth", "gvcycle", "gsolve", "residual_restrict_lowp", "prolong_correct_lowp"]
 
 
 def _torch():
@@ -629,3 +630,149 @@ def export_lambda(c, level):
     out = np.zeros((c.nu, c.hier.level_info(level)["lamsize"]))
     _capi.check(_capi.lib().cs_export_lambda(c.ptr, level, out.ctypes.data_as(C.c_void_p)), "cs_export_lambda")
     return out
+
+
+# ------------------------------------------------ general sparse operators
+def _csr_struct(M, keep):
+    """cs_csr of a scipy CSR matrix (host arrays, kept alive in `keep`)."""
+    M = M.tocsr()
+    M.sort_indices()
+    rp = np.ascontiguousarray(M.indptr, dtype=np.int64)
+    ci = np.ascontiguousarray(M.indices, dtype=np.int32)
+    v = np.ascontiguousarray(M.data, dtype=np.float64)
+    keep += [rp, ci, v]
+    return _capi.cs_csr(M.shape[0], M.shape[1], rp.ctypes.data, ci.ctypes.data, v.ctypes.data, 1)
+
+
+class GHierarchy:
+    """Handle of a general sparse hierarchy (``cs_gsetup_hierarchy``)."""
+
+    def __init__(self, ptr):
+        self._p = ptr
+        self.nlevels = _capi.lib().cs_gnlevels(ptr)
+
+    @property
+    def ptr(self):
+        return C.c_void_p(self._p)
+
+    def level(self, l):
+        n, nb, nc = C.c_int(), C.c_int(), C.c_int()
+        nnz = C.c_int64()
+        _capi.check(_capi.lib().cs_gquery_level(self._p, l, C.byref(n), C.byref(nnz), C.byref(nb), C.byref(nc)),
+                    "cs_gquery_level")
+        return {"N": n.value, "nnz": nnz.value, "nblocks": nb.value, "ncolours": nc.value}
+
+    def N(self, l):
+        return self.level(l)["N"]
+
+    def operator(self, l):
+        """(rowptr, col, val) of the level's operator (host arrays)."""
+        q = self.level(l)
+        rp = np.zeros(q["N"] + 1, dtype=np.int64)
+        ci = np.zeros(max(q["nnz"], 1), dtype=np.int32)
+        v = np.zeros(max(q["nnz"], 1))
+        _capi.check(_capi.lib().cs_gexport_operator(self._p, l, rp.ctypes.data, ci.ctypes.data, v.ctypes.data),
+                    "cs_gexport_operator")
+        return rp, ci[: q["nnz"]], v[: q["nnz"]]
+
+    def colours(self, l):
+        out = np.zeros(self.level(l)["nblocks"], dtype=np.int32)
+        _capi.check(_capi.lib().cs_gexport_colours(self._p, l, out.ctypes.data), "cs_gexport_colours")
+        return out
+
+    def blocks(self, l):
+        q = self.level(l)
+        bptr = np.zeros(q["nblocks"] + 1, dtype=np.int32)
+        bidx = np.zeros(q["N"], dtype=np.int32)
+        _capi.check(_capi.lib().cs_gexport_blocks(self._p, l, bptr.ctypes.data, bidx.ctypes.data), "cs_gexport_blocks")
+        return bptr, bidx
+
+    def __del__(self):
+        if getattr(self, "_p", None) and _capi._lib is not None:
+            _capi._lib.cs_gdestroy_hierarchy(self._p)
+            self._p = None
+
+
+class GCascade:
+    def __init__(self, ptr, h, kind, nu):
+        self._p, self.h, self.kind, self.nu = ptr, h, kind, nu
+
+    @property
+    def ptr(self):
+        return C.c_void_p(self._p)
+
+    def __del__(self):
+        if getattr(self, "_p", None) and _capi._lib is not None:
+            _capi._lib.cs_gdestroy_cascade(self._p)
+            self._p = None
+
+
+def gsetup_hierarchy(A, Ps, rscale=1.0, blocks=None, seed=0, stream=None):
+    """General sparse hierarchy: A (scipy sparse, N0 x N0), interpolations
+    Ps (scipy sparse, N_l x N_{l+1}), Galerkin coarse operators
+    rscale P^T A P, an optional level-0 block partition (bptr, bidx), and the
+    greedy colouring's priority seed."""
+    keep = []
+    a = _csr_struct(A, keep)
+    ps = (_capi.cs_csr * max(len(Ps), 1))(*[_csr_struct(P, keep) for P in Ps])
+    nb, bp, bi = 0, None, None
+    if blocks is not None:
+        bp = np.ascontiguousarray(blocks[0], dtype=np.int32)
+        bi = np.ascontiguousarray(blocks[1], dtype=np.int32)
+        keep += [bp, bi]
+        nb = len(bp) - 1
+    out = C.c_void_p()
+    _capi.check(_capi.lib().cs_gsetup_hierarchy(C.byref(a), len(Ps), ps, float(rscale), nb,
+                                                bp.ctypes.data if bp is not None else None,
+                                                bi.ctypes.data if bi is not None else None,
+                                                int(seed) & 0xFFFFFFFFFFFFFFFF, _stream(stream), C.byref(out)),
+                "cs_gsetup_hierarchy")
+    return GHierarchy(out.value)
+
+
+def gsetup_cascade(h, kind="additive", nu=3, prescale=True, stream=None):
+    k = _capi.CS_MULTIPLICATIVE if kind == "multiplicative" else _capi.CS_ADDITIVE
+    out = C.c_void_p()
+    _capi.check(_capi.lib().cs_gsetup_cascade(h.ptr, k, nu, int(prescale), _stream(stream), C.byref(out)),
+                "cs_gsetup_cascade")
+    return GCascade(out.value, h, kind, nu)
+
+
+def gexport_lambda(c, level):
+    ls = int(_capi.lib().cs_glamsize(c.ptr, level))
+    out = np.zeros((c.nu, ls))
+    _capi.check(_capi.lib().cs_gexport_lambda(c.ptr, level, out.ctypes.data), "cs_gexport_lambda")
+    return out
+
+
+def gsweep(h, c, level, step, b, x, out, colour=-1, stream=None):
+    N = h.N(level)
+    _capi.check(_capi.lib().cs_gsweep(h.ptr, c.ptr, level, step, colour, _dev_ptr(b, N, "b"), _dev_ptr(x, N, "x"),
+                                      _dev_ptr(out, N, "out"), _stream(stream)), "cs_gsweep")
+
+
+def gsmooth(h, c, level, b, x, reverse=False, stream=None):
+    N = h.N(level)
+    _capi.check(_capi.lib().cs_gsmooth(h.ptr, c.ptr, level, int(reverse), _dev_ptr(b, N, "b"), _dev_ptr(x, N, "x"),
+                                       _stream(stream)), "cs_gsmooth")
+
+
+def gvcycle(h, c, b, x, mu_pre=1, mu_post=1, order="RF", stream=None):
+    N = h.N(0)
+    o = _cycle_opts(mu_pre, mu_post, order, "fp64")
+    _capi.check(_capi.lib().cs_gvcycle(h.ptr, c.ptr, C.byref(o), _dev_ptr(b, N, "b"), _dev_ptr(x, N, "x"),
+                                       _stream(stream)), "cs_gvcycle")
+
+
+def gsolve(h, c, b, x, method="gmres_right", tol=1e-10, maxit=100, restart=30, mu_pre=1, mu_post=1, order="RF",
+           raise_on_error=True, stream=None) -> SolveInfo:
+    N = h.N(0)
+    hist = np.zeros(4 * maxit + 8)
+    o = _capi.cs_solve_opts(_METHODS[method], restart, maxit, tol, _cycle_opts(mu_pre, mu_post, order, "fp64"), 0,
+                            hist.ctypes.data_as(C.POINTER(C.c_double)), len(hist))
+    info = _capi.cs_solve_info()
+    st = _capi.lib().cs_gsolve(h.ptr, c.ptr, C.byref(o), _dev_ptr(b, N, "b"), _dev_ptr(x, N, "x"), C.byref(info),
+                               _stream(stream))
+    if raise_on_error and st != _capi.CS_OK:
+        _capi.check(st, "cs_gsolve")
+    return SolveInfo(st, info.iterations, bool(info.converged), info.final_rel_residual, hist[: info.nhist].copy())

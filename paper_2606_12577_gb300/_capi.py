@@ -59,6 +59,11 @@ class cs_level_info(C.Structure):
                 ("sym32", C.c_int)]
 
 
+class cs_csr(C.Structure):
+    _fields_ = [("n", C.c_int), ("m", C.c_int), ("rowptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p),
+                ("on_host", C.c_int)]
+
+
 class cs_batch_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("order", C.c_int), ("mu_pre", C.c_int), ("mu_post", C.c_int),
                 ("autotune", C.c_int), ("threads", C.c_int), ("tiles_per_cta", C.c_int), ("method", C.c_int),
@@ -93,6 +98,25 @@ _SIGS = {
     "cs_prolong_correct_lowp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                           C.c_void_p]),
     "cs_coarse_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cs_gsetup_hierarchy": (C.c_int, [C.POINTER(cs_csr), C.c_int, C.POINTER(cs_csr), C.c_double, C.c_int,
+                                      C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "cs_gsetup_cascade": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "cs_gsweep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                            C.c_void_p]),
+    "cs_gsmooth": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cs_gvcycle": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(cs_vcycle_opts), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cs_gsolve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(cs_solve_opts), C.c_void_p, C.c_void_p,
+                            C.POINTER(cs_solve_info), C.c_void_p]),
+    "cs_gquery_level": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int)]),
+    "cs_gnlevels": (C.c_int, [C.c_void_p]),
+    "cs_gexport_operator": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cs_gexport_colours": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "cs_gexport_blocks": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "cs_glamsize": (C.c_int64, [C.c_void_p, C.c_int]),
+    "cs_gexport_lambda": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "cs_gdestroy_hierarchy": (None, [C.c_void_p]),
+    "cs_gdestroy_cascade": (None, [C.c_void_p]),
     "cs_residual": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                               C.c_void_p]),
     "cs_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(cs_solve_opts), C.c_void_p, C.c_void_p,

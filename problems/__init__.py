@@ -393,7 +393,7 @@ def permutation(n: int, seed: int) -> np.ndarray:
     return np.argsort(uniform01(seed, n), kind="stable")
 
 
-def unstructured_q1(n: int, seed: int, coarse_side: int = 3, block: int = 3):
+def unstructured_q1(n: int, seed: int, coarse_side: int = 3, block: int = 3, renumber: bool = True):
     """The jittered Q1 operator of ``q1_jittered(n, seed)`` handed over as a
     general sparse problem: its CSR matrix with the interior nodes renumbered
     by a seeded random permutation, the bilinear interpolations P_l of the
@@ -401,15 +401,16 @@ def unstructured_q1(n: int, seed: int, coarse_side: int = 3, block: int = 3):
     way on both of their levels, and a partition of level 0 into
     block x block node blocks (partial at the upper edges) in the new
     numbering.  Nothing of the grid survives in the numbering, so a solver
-    that reads it sees an unstructured mesh.  Returns a dict with A (scipy
-    CSR), Ps (list of scipy CSR), blocks (bptr, bidx) and perms (perm[new] =
-    old per level)."""
+    that reads it sees an unstructured mesh (renumber=False keeps the grid
+    order).  Returns a dict with A (scipy CSR), Ps (list of scipy CSR),
+    blocks (bptr, bidx) and perms (perm[new] = old per level)."""
     import scipy.sparse as sp
     St = q1_jittered(n, seed)
     sides = [n]
     while sides[-1] > coarse_side and sides[-1] // 2 >= 1:
         sides.append(sides[-1] // 2)
-    perms = [permutation(m * m, seed + 7919 * (k + 1)) for k, m in enumerate(sides)]
+    perms = [permutation(m * m, seed + 7919 * (k + 1)) if renumber else np.arange(m * m)
+             for k, m in enumerate(sides)]
     inv = [np.argsort(pm) for pm in perms]  # inv[old] = new
     A = stencil_csr(St)
     A = A[perms[0]][:, perms[0]].tocsr()
@@ -422,13 +423,13 @@ def unstructured_q1(n: int, seed: int, coarse_side: int = 3, block: int = 3):
         P.sort_indices()
         Ps.append(P)
     nb1 = (n + block - 1) // block
-    members = [[] for _ in range(nb1 * nb1)]
-    for old in range(n * n):
-        ix, iy = old % n, old // n
-        members[ix // block + nb1 * (iy // block)].append(int(inv[0][old]))
-    bptr = np.zeros(len(members) + 1, dtype=np.int32)
-    bptr[1:] = np.cumsum([len(m) for m in members])
-    bidx = np.concatenate([np.sort(np.array(m, dtype=np.int32)) for m in members]).astype(np.int32)
+    old = np.arange(n * n)
+    bid = (old % n) // block + nb1 * ((old // n) // block)
+    new = inv[0][old]
+    order = np.lexsort((new, bid))  # by block, then by new index
+    bptr = np.zeros(nb1 * nb1 + 1, dtype=np.int32)
+    bptr[1:] = np.cumsum(np.bincount(bid, minlength=nb1 * nb1))
+    bidx = new[order].astype(np.int32)
     return {"A": A, "Ps": Ps, "blocks": (bptr, bidx), "perms": perms, "sides": sides}
 
 

@@ -1,0 +1,165 @@
+"""The general sparse path (CSR operator, user transfers and blocks, greedy
+colouring) against the oracle's CSR hierarchy on a jittered Q1 mesh whose
+unknowns are renumbered at random (nothing structured survives): Galerkin
+operators to 1e-14, colour ids bit-exact, Lambda, cascade steps, V-cycles
+and solves to 1e-12 / the oracle's iteration counts."""
+import numpy as np
+import pytest
+
+import oracle
+import problems
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def built():
+    import __graft_entry__ as g
+    g.build()
+    return True
+
+
+def _dev(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+MESHES = {"q1_31": (31, 3), "q1_63": (63, 4), "q1_40": (40, 6)}
+
+
+def _pair(name, blocks=False, seed=11):
+    import paper_2606_12577_gb300 as cmg
+    n, s = MESHES[name]
+    u = problems.unstructured_q1(n, s)
+    bl = u["blocks"] if blocks else None
+    ho = oracle.Hierarchy.from_csr(u["A"], u["Ps"], rscale=0.25, blocks=bl, seed=seed)
+    hg = cmg.gsetup_hierarchy(u["A"], u["Ps"], rscale=0.25, blocks=bl, seed=seed)
+    return u, ho, hg
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_general_hierarchy_matches_oracle(built, name):
+    u, ho, hg = _pair(name)
+    assert hg.nlevels == ho.nlev
+    for l in range(ho.nlev):
+        rp, ci, v = hg.operator(l)
+        orp, oci, ov = ho.csr(l)
+        assert np.array_equal(rp, orp) and np.array_equal(ci, oci), l
+        assert np.abs(v - ov).max() <= 1e-14 * np.abs(ov).max(), l
+        assert np.array_equal(hg.colours(l), ho.blocks(l)[2]), l  # bit-exact colour ids
+        assert hg.level(l)["ncolours"] == ho.ncolours(l)
+    assert ho.ncolours(0) > 2
+
+
+@pytest.mark.parametrize("name,kind,nu,blocks", [("q1_31", "additive", 3, False), ("q1_31", "multiplicative", 2, False),
+                                                 ("q1_63", "multiplicative", 3, False), ("q1_40", "additive", 3, True),
+                                                 ("q1_31", "multiplicative", 2, True)])
+def test_general_lambda_matches_oracle(built, name, kind, nu, blocks):
+    import paper_2606_12577_gb300 as cmg
+    u, ho, hg = _pair(name, blocks)
+    co = oracle.Cascade(ho, kind, nu=nu)
+    cg = cmg.gsetup_cascade(hg, kind, nu=nu)
+    for l in range(co.nlev):
+        assert gu.rel_max(cmg.gexport_lambda(cg, l), co.lam(l)) <= TOL, l
+
+
+@pytest.mark.parametrize("name,kind,blocks", [("q1_31", "additive", False), ("q1_63", "multiplicative", False),
+                                              ("q1_40", "additive", True), ("q1_31", "multiplicative", True)])
+def test_general_steps_and_cycles_match_oracle(built, name, kind, blocks):
+    """One cascade application forward and reverse on the first two levels
+    (one-thread-per-row kernel on point levels, warp-per-block kernel on the
+    3x3-node blocks, colour steps in place), and two V-cycles in RF and FF
+    order."""
+    import paper_2606_12577_gb300 as cmg
+    u, ho, hg = _pair(name, blocks)
+    co = oracle.Cascade(ho, kind, nu=2)
+    cg = cmg.gsetup_cascade(hg, kind, nu=2)
+    for l in range(min(2, co.nlev)):
+        N = ho.N(l)
+        b = problems.uniform(100 + l, N)
+        x0 = problems.uniform(200 + l, N)
+        for rev in (False, True):
+            xg = _dev(x0)
+            cmg.gsmooth(hg, cg, l, _dev(b), xg, reverse=rev)
+            assert gu.rel_max(_host(xg), oracle.smooth(ho, co, l, b, x0, reverse=rev)) <= TOL, (l, rev)
+    b = problems.rhs(ho.N(0), 7)
+    for order in ("RF", "FF"):
+        xo = oracle.vcycle(ho, co, b, rf=order == "RF")
+        xo = oracle.vcycle(ho, co, b, xo, rf=order == "RF")
+        xg = _dev(np.zeros(ho.N(0)))
+        for _ in range(2):
+            cmg.gvcycle(hg, cg, _dev(b), xg, order=order)
+        assert gu.rel_max(_host(xg), xo) <= TOL, order
+
+
+@pytest.mark.parametrize("name,kind,method,blocks", [("q1_63", "additive", "gmres_right", False),
+                                                     ("q1_63", "multiplicative", "stationary", False),
+                                                     ("q1_40", "additive", "gmres_right", True),
+                                                     ("q1_31", "multiplicative", "gmres_right", True)])
+def test_general_solve_matches_oracle(built, name, kind, method, blocks):
+    import paper_2606_12577_gb300 as cmg
+    u, ho, hg = _pair(name, blocks)
+    co = oracle.Cascade(ho, kind, nu=3)
+    cg = cmg.gsetup_cascade(hg, kind, nu=3)
+    b = problems.rhs(ho.N(0), 9)
+    xo, ito, hist_o, _ = oracle.solve(ho, co, b, method=method, tol=1e-10)
+    assert ito > 0
+    x = _dev(np.zeros(ho.N(0)))
+    info = cmg.gsolve(hg, cg, _dev(b), x, method=method, tol=1e-10)
+    assert info.converged and info.iterations == ito
+    np.testing.assert_allclose(info.history, hist_o, rtol=1e-9, atol=1e-13)
+    r = b - u["A"] @ _host(x)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
+    assert gu.rel_max(_host(x), xo) <= 1e-11
+
+
+def test_general_path_reduces_to_the_structured_path(built):
+    """A structured operator given as CSR with the bilinear transfers: the
+    general path's additive Lambda equals the structured path's, and the
+    solves take the same iterations."""
+    import scipy.sparse as sp
+    import torch
+
+    import paper_2606_12577_gb300 as cmg
+    A = problems.variable_poisson(problems.random_coefficients(2, 47, 3))
+    Ps, n = [], 47
+    while n > 4:
+        P1 = sp.csr_matrix(problems.interpolation_1d(n))
+        Ps.append(sp.kron(P1, P1, format="csr"))
+        n //= 2
+    hg = cmg.gsetup_hierarchy(problems.stencil_csr(A), Ps, rscale=0.25)
+    cg = cmg.gsetup_cascade(hg, "additive", nu=3)
+    hs = gu.gpu_hierarchy(A)
+    cs = cmg.setup_cascade(hs, "additive", nu=3)
+    assert hg.nlevels == hs.nlevels
+    for l in range(hs.nlevels - 1):
+        assert gu.rel_max(cmg.gexport_lambda(cg, l), cmg.export_lambda(cs, l)) <= TOL, l
+    b = problems.rhs(A.N, 5)
+    x1 = torch.zeros(A.N, dtype=torch.float64, device="cuda")
+    x2 = torch.zeros(A.N, dtype=torch.float64, device="cuda")
+    i1 = cmg.gsolve(hg, cg, _dev(b), x1, method="gmres_right")
+    i2 = cmg.solve(hs, cs, _dev(b), x2, method="gmres_right")
+    assert i1.iterations == i2.iterations
+    assert gu.rel_max(_host(x1), _host(x2)) <= 1e-10
+
+
+def test_general_path_rejects_bad_input(built):
+    import scipy.sparse as sp
+
+    import paper_2606_12577_gb300 as cmg
+    u = problems.unstructured_q1(15, 2)
+    bptr, bidx = u["blocks"]
+    bad = bidx.copy()
+    bad[0] = bad[1]  # a node twice: not a partition
+    with pytest.raises(cmg.CascadeError, match="CS_ERR_ARG"):
+        cmg.gsetup_hierarchy(u["A"], u["Ps"], rscale=0.25, blocks=(bptr, bad))
+    with pytest.raises(cmg.CascadeError, match="CS_ERR_ARG"):
+        cmg.gsetup_hierarchy(u["A"], [sp.csr_matrix(np.ones((3, 2)))], rscale=0.25)  # wrong shape
