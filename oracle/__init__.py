@@ -31,6 +31,7 @@ _lock = threading.Lock()
 _lib = None
 
 KINDS = {"additive": 0, "multiplicative": 1}
+PRESCALE = {"none": 0, "elliptic": 1, "stokes1": 2, "stokes2": 3, "stokesinf": 4, False: 0, True: 1}
 
 
 def build(force: bool = False) -> str:
@@ -79,8 +80,10 @@ def _load():
             "ora_set_threads": (None, [I]),
             "ora_ghier_new": (P, [I, P, P, P, D]),
             "ora_ghier_add_level": (I, [P, I, P, P, P]),
-            "ora_ghier_set_blocks": (I, [P, I, P, P]),
-            "ora_ghier_finish": (None, [P, C.c_uint64]),
+            "ora_ghier_set_blocks": (I, [P, I, I, P, P]),
+            "ora_ghier_set_fields": (None, [P, P]),
+            "ora_ghier_finish": (I, [P, C.c_uint64]),
+            "ora_prescale_weights": (I, [P, I, I, P]),
             "ora_hier_ncol": (I, [P, I]),
             "ora_block_prio": (C.c_uint64, [C.c_uint64, I, I]),
             "ora_casc_create_sketch": (P, [P, I, I, I, I, C.c_uint64, I]),
@@ -148,12 +151,13 @@ class Hierarchy:
             self._h = None
 
     @classmethod
-    def from_csr(cls, A, Ps, rscale: float = 1.0, blocks=None, seed: int = 0):
+    def from_csr(cls, A, Ps, rscale: float = 1.0, blocks=None, seed: int = 0, fields=None):
         """Hierarchy of a general sparse operator (the CSR path): A (scipy
         CSR, N0 x N0), one interpolation P_l per coarser level (scipy CSR,
         N_l x N_{l+1}), Galerkin A_{l+1} = rscale P_l^T A_l P_l; blocks =
-        (bptr, bidx) of level 0 (point blocks if None, and on coarse levels);
-        greedy colouring with the block priorities of `seed`."""
+        (bptr, bidx) of level 0, or a list of such pairs per level (None:
+        point blocks); greedy colouring with the block priorities of `seed`;
+        fields: 0 (velocity / scalar) or 1 (pressure) per finest unknown."""
         lib = _load()
         self = cls.__new__(cls)
         self.dim, self.bs = 0, 0
@@ -171,13 +175,29 @@ class Hierarchy:
             if lib.ora_ghier_add_level(self._h, P.shape[1], _ptr(prp), _ptr(pci), _ptr(_f64(P.data))) != 0:
                 raise RuntimeError("too many levels")
         if blocks is not None:
-            bptr = np.ascontiguousarray(blocks[0], dtype=np.int32)
-            bidx = np.ascontiguousarray(blocks[1], dtype=np.int32)
-            if lib.ora_ghier_set_blocks(self._h, len(bptr) - 1, _ptr(bptr), _ptr(bidx)) != 0:
-                raise ValueError("blocks are not a partition of the unknowns")
-        lib.ora_ghier_finish(self._h, int(seed) & 0xFFFFFFFFFFFFFFFF)
+            per_level = blocks if isinstance(blocks, list) else [blocks]
+            for l, bl in enumerate(per_level):
+                if bl is None:
+                    continue
+                bptr = np.ascontiguousarray(bl[0], dtype=np.int32)
+                bidx = np.ascontiguousarray(bl[1], dtype=np.int32)
+                if lib.ora_ghier_set_blocks(self._h, l, len(bptr) - 1, _ptr(bptr), _ptr(bidx)) != 0:
+                    raise ValueError(f"level {l}: blocks are not a partition of the unknowns")
+        if fields is not None:
+            f = np.ascontiguousarray(fields, dtype=np.int32)
+            lib.ora_ghier_set_fields(self._h, _ptr(f))
+        if lib.ora_ghier_finish(self._h, int(seed) & 0xFFFFFFFFFFFFFFFF) != 0:
+            raise ValueError("an interpolation maps one coarse unknown to fine unknowns of two fields")
         self.nlev = lib.ora_hier_nlev(self._h)
         return self
+
+    def prescale_weights(self, l: int, mode) -> np.ndarray:
+        """The diagonal of W on level l: mode 'none', 'elliptic' or
+        'stokes1' / 'stokes2' / 'stokesinf' (q = 1, 2, infinity)."""
+        out = np.zeros(self.N(l))
+        if _lib.ora_prescale_weights(self._h, l, PRESCALE[mode], _ptr(out)) != 0:
+            raise ValueError("prescaling weight undefined (non-positive diagonal or norm)")
+        return out
 
     def ncolours(self, l: int) -> int:
         return int(_lib.ora_hier_ncol(self._h, l))
@@ -264,10 +284,10 @@ class Cascade:
         if _empty:
             self._c = _lib.ora_casc_empty(hier._h, KINDS[kind], nu)
         elif sketch > 0:
-            self._c = _lib.ora_casc_create_sketch(hier._h, KINDS[kind], nu, int(prescale), int(sketch),
+            self._c = _lib.ora_casc_create_sketch(hier._h, KINDS[kind], nu, PRESCALE[prescale], int(sketch),
                                                   int(seed) & 0xFFFFFFFFFFFFFFFF, int(exact_first))
         else:
-            self._c = _lib.ora_casc_create(hier._h, KINDS[kind], nu, int(prescale), alpha)
+            self._c = _lib.ora_casc_create(hier._h, KINDS[kind], nu, PRESCALE[prescale], alpha)
         if not self._c:
             raise RuntimeError("oracle cascade setup failed (non-positive diagonal under prescaling?)")
         self.nlev = _lib.ora_casc_nlev(self._c)

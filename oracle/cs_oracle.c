@@ -396,6 +396,7 @@ typedef struct {
     int nb[ORA_MAXLEV];
     int *bptr[ORA_MAXLEV], *bidx[ORA_MAXLEV], *bpar[ORA_MAXLEV];
     int ncol[ORA_MAXLEV];  /* colours of the multiplicative cascade per level (red-black: 2) */
+    int *field[ORA_MAXLEV];  /* per unknown: 0 velocity / scalar, 1 pressure (constraint); NULL: all 0 */
     /* coarsest-level dense factor */
     int cn, cspd;
     double *cfac;
@@ -509,7 +510,7 @@ void ora_hier_free(ora_hier *h) {
     if (!h) return;
     for (int l = 0; l < h->nlev; ++l) {
         csr_free(&h->A[l]); csr_free(&h->P[l]); csr_free(&h->R[l]);
-        free(h->bptr[l]); free(h->bidx[l]); free(h->bpar[l]);
+        free(h->bptr[l]); free(h->bidx[l]); free(h->bpar[l]); free(h->field[l]);
     }
     free(h->cfac); free(h->cpiv); free(h);
 }
@@ -588,8 +589,9 @@ int ora_ghier_add_level(ora_hier *h, int Nc, const int64_t *prp, const int *pci,
 /* The user's block partition of level 0 (every node in exactly one block;
  * the nodes of a block are used in the order given).  Returns -1 if it is
  * not a partition. */
-int ora_ghier_set_blocks(ora_hier *h, int nb, const int *bptr, const int *bidx) {
-    int N = h->A[0].n;
+int ora_ghier_set_blocks(ora_hier *h, int l, int nb, const int *bptr, const int *bidx) {
+    if (l < 0 || l >= h->nlev) return -1;
+    int N = h->A[l].n;
     if (nb < 1 || bptr[0] != 0 || bptr[nb] != N) return -1;
     int *seen = xcalloc((size_t)N, sizeof(int));
     for (int p = 0; p < N; ++p) {
@@ -597,13 +599,22 @@ int ora_ghier_set_blocks(ora_hier *h, int nb, const int *bptr, const int *bidx) 
     }
     free(seen);
     for (int b = 0; b < nb; ++b) if (bptr[b + 1] <= bptr[b]) return -1;
-    free(h->bptr[0]); free(h->bidx[0]);
-    h->nb[0] = nb;
-    h->bptr[0] = xmalloc(sizeof(int) * ((size_t)nb + 1));
-    h->bidx[0] = xmalloc(sizeof(int) * (size_t)N);
-    memcpy(h->bptr[0], bptr, sizeof(int) * ((size_t)nb + 1));
-    memcpy(h->bidx[0], bidx, sizeof(int) * (size_t)N);
+    free(h->bptr[l]); free(h->bidx[l]);
+    h->nb[l] = nb;
+    h->bptr[l] = xmalloc(sizeof(int) * ((size_t)nb + 1));
+    h->bidx[l] = xmalloc(sizeof(int) * (size_t)N);
+    memcpy(h->bptr[l], bptr, sizeof(int) * ((size_t)nb + 1));
+    memcpy(h->bidx[l], bidx, sizeof(int) * (size_t)N);
     return 0;
+}
+
+/* Field of every finest unknown (0 velocity or scalar, 1 pressure); the
+ * coarse unknowns take the field of the fine unknowns P maps them to. */
+void ora_ghier_set_fields(ora_hier *h, const int *field) {
+    int N = h->A[0].n;
+    free(h->field[0]);
+    h->field[0] = xmalloc(sizeof(int) * (size_t)N);
+    memcpy(h->field[0], field, sizeof(int) * (size_t)N);
 }
 
 typedef struct { uint64_t p; int b; } prio_t;
@@ -659,7 +670,20 @@ static void greedy_colour(ora_hier *h, int l, uint64_t seed) {
 
 /* Point blocks on every level without a partition, the colourings, and the
  * coarsest factorisation. */
-void ora_ghier_finish(ora_hier *h, uint64_t seed) {
+int ora_ghier_finish(ora_hier *h, uint64_t seed) {
+    for (int l = 0; l + 1 < h->nlev && h->field[0]; ++l) {
+        const csr *P = &h->P[l];
+        int Nc = P->m;
+        h->field[l + 1] = xmalloc(sizeof(int) * (size_t)Nc);
+        for (int j = 0; j < Nc; ++j) h->field[l + 1][j] = -1;
+        for (int i = 0; i < P->n; ++i)
+            for (int64_t p = P->rp[i]; p < P->rp[i + 1]; ++p) {
+                int *f = &h->field[l + 1][P->ci[p]];
+                if (*f >= 0 && *f != h->field[l][i]) return -1; /* a coarse unknown of two fields */
+                *f = h->field[l][i];
+            }
+        for (int j = 0; j < Nc; ++j) if (h->field[l + 1][j] < 0) h->field[l + 1][j] = 0;
+    }
     for (int l = 0; l < h->nlev; ++l) {
         int N = h->A[l].n;
         if (!h->bptr[l]) {
@@ -674,6 +698,7 @@ void ora_ghier_finish(ora_hier *h, uint64_t seed) {
         greedy_colour(h, l, seed);
     }
     factor_coarsest(h);
+    return 0;
 }
 int ora_hier_ncol(const ora_hier *h, int l) { return h->ncol[l]; }
 
@@ -695,6 +720,53 @@ static int block_colour(const ora_hier *h, int l, int kind, int b) {
     return kind == 1 ? h->bpar[l][b] : 0;
 }
 
+/* The diagonal prescaling W of level l (Sec. 2.3; SM "Prescaling Stokes
+ * problems"): mode 0 none (W = I); 1 elliptic, w_i = A_ii^{-1/2}; 2, 3, 4
+ * Stokes with q = 1, 2, infinity: every velocity unknown (field 0) takes
+ * w_i = sqrt(||A_{i,:}||_1) / A_ii, the 1-norm over the velocity columns of
+ * its row (so that the diagonal of W A W there is ||A_{i,:}||_1 / A_ii), and
+ * every pressure unknown (field 1) takes the w_k that gives its row of
+ * diag(w_p) D diag(w_u) (the velocity columns) unit q-norm.  Returns -1 when
+ * a weight is undefined (a non-positive diagonal or norm). */
+static int prescale_weights(const ora_hier *h, int l, int mode, double *w) {
+    const csr *A = &h->A[l];
+    int N = A->n;
+    const int *fld = h->field[l];
+    for (int i = 0; i < N; ++i) {
+        double d = 0.0;
+        for (int64_t p = A->rp[i]; p < A->rp[i + 1]; ++p) if (A->ci[p] == i) d += A->v[p];
+        if (mode == 0) w[i] = 1.0;
+        else if (mode == 1) {
+            if (!(d > 0.0)) return -1;
+            w[i] = 1.0 / sqrt(d);
+        } else if (!fld || fld[i] == 0) {
+            double l1 = 0.0;
+            for (int64_t p = A->rp[i]; p < A->rp[i + 1]; ++p)
+                if (!fld || fld[A->ci[p]] == 0) l1 += fabs(A->v[p]);
+            if (!(d > 0.0) || !(l1 > 0.0)) return -1;
+            w[i] = sqrt(l1) / d;
+        }
+    }
+    if (mode >= 2 && fld)
+        for (int k = 0; k < N; ++k) {
+            if (fld[k] != 1) continue;
+            double nrm = 0.0;
+            for (int64_t p = A->rp[k]; p < A->rp[k + 1]; ++p) {
+                int j = A->ci[p];
+                if (fld[j] != 0) continue;
+                double a = fabs(A->v[p]) * w[j];
+                if (mode == 2) nrm += a;
+                else if (mode == 3) nrm += a * a;
+                else if (a > nrm) nrm = a;
+            }
+            if (mode == 3) nrm = sqrt(nrm);
+            if (!(nrm > 0.0)) return -1;
+            w[k] = 1.0 / nrm;
+        }
+    return 0;
+}
+int ora_prescale_weights(const ora_hier *h, int l, int mode, double *w) { return prescale_weights(h, l, mode, w); }
+
 /* One level's cascade (Algorithm 2 / SM Algorithm).  A is the level
  * operator; lam receives nu * lamsize doubles, efrob nu*ncol+1 doubles. */
 static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescale, int alpha,
@@ -704,16 +776,9 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
     const int *bptr = h->bptr[l], *bidx = h->bidx[l];
     int ncol = kind == 1 ? h->ncol[l] : 1;
     int64_t lamsize = lamoff[nb];
-    /* prescaling W = diag(A_ii^{-1/2}) (Sec. 2.3.1) */
+    /* the prescaling W (Sec. 2.3) */
     double *w = xmalloc(sizeof(double) * (size_t)N);
-    for (int i = 0; i < N; ++i) {
-        double d = 0.0;
-        for (int64_t p = A0->rp[i]; p < A0->rp[i + 1]; ++p) if (A0->ci[p] == i) d += A0->v[p];
-        if (prescale) {
-            if (!(d > 0.0)) { free(w); return -1; }
-            w[i] = 1.0 / sqrt(d);
-        } else w[i] = 1.0;
-    }
+    if (prescale_weights(h, l, prescale, w) != 0) { free(w); return -1; }
     csr A;
     A.n = A.m = N;
     int64_t annz = A0->rp[N];
@@ -964,14 +1029,7 @@ static int sketch_level(const ora_hier *h, int l, int kind, int nu, int prescale
     int ncol = kind == 1 ? h->ncol[l] : 1;
     int64_t lamsize = lamoff[nb];
     double *w = xmalloc(sizeof(double) * (size_t)N);
-    for (int i = 0; i < N; ++i) {
-        double d = 0.0;
-        for (int64_t p = A0->rp[i]; p < A0->rp[i + 1]; ++p) if (A0->ci[p] == i) d += A0->v[p];
-        if (prescale) {
-            if (!(d > 0.0)) { free(w); return -1; }
-            w[i] = 1.0 / sqrt(d);
-        } else w[i] = 1.0;
-    }
+    if (prescale_weights(h, l, prescale, w) != 0) { free(w); return -1; }
     csr A;
     A.n = A.m = N;
     int64_t annz = A0->rp[N];

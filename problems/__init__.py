@@ -433,6 +433,138 @@ def unstructured_q1(n: int, seed: int, coarse_side: int = 3, block: int = 3, ren
     return {"A": A, "Ps": Ps, "blocks": (bptr, bidx), "perms": perms, "sides": sides}
 
 
+def _mac_index(n: int):
+    """Unknown numbering of a MAC grid of n x n cells on the unit square:
+    u at the interior vertical faces (i = 1..n-1, j = 0..n-1), then v at the
+    interior horizontal faces (i = 0..n-1, j = 1..n-1), then p at the cells."""
+    nu = (n - 1) * n
+    U = lambda i, j: (i - 1) + (n - 1) * j  # noqa: E731
+    V = lambda i, j: nu + i + n * (j - 1)  # noqa: E731
+    Pc = lambda i, j: 2 * nu + i + n * j  # noqa: E731
+    return nu, U, V, Pc
+
+
+def mac_stokes_2d(n: int, mu: float = 1.0, delta: float = 1e-3, coarse_cells: int = 4):
+    """Steady Stokes, -mu Lap u + grad p = f, -div u = g, on the unit square
+    with no-slip walls, discretised by the MAC staggered-grid finite
+    difference method on n x n cells (n a power of two times coarse_cells),
+    in finite-volume scaling (every equation times h^2): the viscous block
+    mu (4 u_c - sum of neighbours, a wall-side tangential neighbour replaced
+    by the reflected ghost -u_c), G = h (p_right - p_left), D = G^T, and a
+    small pressure stabilisation -delta h^2 I that removes the constant
+    pressure mode.  Unknowns as in _mac_index; fields 0 (velocity) / 1
+    (pressure).  Transfers per coarsening (n -> n/2): pressure piecewise
+    constant over the 2 x 2 subcells; a u face linear along x between the
+    coarse faces it lies between (wall faces contribute zero) and constant
+    along y over the coarse cell row; v likewise with x and y exchanged.
+    Blocks: per cell its pressure and its right and top faces (d + 1 = 3
+    unknowns; fewer at the upper walls), on every level.  Returns a dict
+    with A (scipy CSR), fields, Ps, blocks (list per level) and sides."""
+    import scipy.sparse as sp
+
+    def operator(m):
+        h = 1.0 / m
+        nu, U, V, Pc = _mac_index(m)
+        N = 2 * nu + m * m
+        rows, cols, vals = [], [], []
+
+        def add(r, c, v):
+            rows.append(r)
+            cols.append(c)
+            vals.append(v)
+        for j in range(m):  # u momentum
+            for i in range(1, m):
+                r, d = U(i, j), 4.0
+                for ii in (i - 1, i + 1):
+                    if 1 <= ii <= m - 1:
+                        add(r, U(ii, j), -mu)
+                for jj in (j - 1, j + 1):
+                    if 0 <= jj <= m - 1:
+                        add(r, U(i, jj), -mu)
+                    else:
+                        d += 1.0  # ghost -u across the wall
+                add(r, r, mu * d)
+                add(r, Pc(i, j), h)
+                add(r, Pc(i - 1, j), -h)
+        for j in range(1, m):  # v momentum
+            for i in range(m):
+                r, d = V(i, j), 4.0
+                for jj in (j - 1, j + 1):
+                    if 1 <= jj <= m - 1:
+                        add(r, V(i, jj), -mu)
+                for ii in (i - 1, i + 1):
+                    if 0 <= ii <= m - 1:
+                        add(r, V(ii, j), -mu)
+                    else:
+                        d += 1.0
+                add(r, r, mu * d)
+                add(r, Pc(i, j), h)
+                add(r, Pc(i, j - 1), -h)
+        for j in range(m):  # continuity: -div u (= G^T) and the stabilisation
+            for i in range(m):
+                r = Pc(i, j)
+                if i + 1 <= m - 1:
+                    add(r, U(i + 1, j), -h)
+                if i >= 1:
+                    add(r, U(i, j), h)
+                if j + 1 <= m - 1:
+                    add(r, V(i, j + 1), -h)
+                if j >= 1:
+                    add(r, V(i, j), h)
+                add(r, r, -delta * h * h)
+        A = sp.csr_matrix((vals, (rows, cols)), shape=(N, N))
+        A.sum_duplicates()
+        A.sort_indices()
+        return A
+
+    def transfer(m):
+        mc = m // 2
+        nuf, Uf, Vf, Pf = _mac_index(m)
+        nuc, Uc, Vc, Pcc = _mac_index(mc)
+        rows, cols, vals = [], [], []
+        for j in range(m):
+            for i in range(1, m):
+                J = j // 2
+                for I, wgt in (((i // 2, 1.0),) if i % 2 == 0 else (((i - 1) // 2, 0.5), ((i + 1) // 2, 0.5))):
+                    if 1 <= I <= mc - 1:
+                        rows.append(Uf(i, j)); cols.append(Uc(I, J)); vals.append(wgt)
+        for j in range(1, m):
+            for i in range(m):
+                I = i // 2
+                for J, wgt in (((j // 2, 1.0),) if j % 2 == 0 else (((j - 1) // 2, 0.5), ((j + 1) // 2, 0.5))):
+                    if 1 <= J <= mc - 1:
+                        rows.append(Vf(i, j)); cols.append(Vc(I, J)); vals.append(wgt)
+        for j in range(m):
+            for i in range(m):
+                rows.append(Pf(i, j)); cols.append(Pcc(i // 2, j // 2)); vals.append(1.0)
+        P = sp.csr_matrix((vals, (rows, cols)), shape=(2 * nuf + m * m, 2 * nuc + mc * mc))
+        P.sum_duplicates()
+        P.sort_indices()
+        return P
+
+    def blocks(m):
+        nu, U, V, Pc = _mac_index(m)
+        bptr, bidx = [0], []
+        for j in range(m):
+            for i in range(m):
+                mem = [Pc(i, j)]
+                if i + 1 <= m - 1:
+                    mem.append(U(i + 1, j))
+                if j + 1 <= m - 1:
+                    mem.append(V(i, j + 1))
+                bidx += sorted(mem)
+                bptr.append(len(bidx))
+        return np.array(bptr, dtype=np.int32), np.array(bidx, dtype=np.int32)
+
+    sides = [n]
+    while sides[-1] > coarse_cells and sides[-1] % 2 == 0:
+        sides.append(sides[-1] // 2)
+    nu0 = (n - 1) * n
+    fields = np.concatenate([np.zeros(2 * nu0, dtype=np.int32), np.ones(n * n, dtype=np.int32)])
+    return {"A": operator(n), "fields": fields, "Ps": [transfer(m) for m in sides[:-1]],
+            "blocks": [blocks(m) for m in sides], "sides": sides}
+
+
 def config_seed(config: int, problem: int = 0) -> int:
     """Seed of problem ``problem`` of workload ``config`` (run seed 0)."""
     return 1000 * config + problem

@@ -52,14 +52,15 @@ def block_partition(n3, dim, bs):
     return [np.array(sorted(m)) for m in members], np.array(par)
 
 
-def dense_cascade(Ad, blocks, parity, kind, nu, alpha=0, bs_blocks=None):
+def dense_cascade(Ad, blocks, parity, kind, nu, alpha=0, bs_blocks=None, w=None):
     """Cascade setup by explicit dense matrices and numpy lstsq.
 
     Returns (lam_tilde, lam, Es): prescaled and unscaled Lambda per step as
     dense block-diagonal matrices (list over l of list over colours), and the
     dense residual E~ after every (l, k) step (prescaled space)."""
     N = Ad.shape[0]
-    w = 1.0 / np.sqrt(np.diag(Ad))
+    if w is None:  # elliptic prescaling
+        w = 1.0 / np.sqrt(np.diag(Ad))
     At = w[:, None] * Ad * w[None, :]
     E = np.eye(N)
     ncol = (int(np.max(parity)) + 1 if len(parity) else 1) if kind == "multiplicative" else 1
