@@ -63,6 +63,7 @@ def args_():
     p.add_argument("--interface-restart", type=int, default=160,
                    help="GMRES restart of the interface workload (the oracle needs 149 steps at 1023^2 without restart)")
     p.add_argument("--general-n", type=int, default=1535, help="interior nodes per side of the general-path mesh")
+    p.add_argument("--stokes-n", type=int, default=256, help="cells per side of the MAC Stokes problem")
     p.add_argument("--batch-count", type=int, default=512, help="problems of the batched workload timed")
     p.add_argument("--batch-fp64-count", type=int, default=32,
                    help="problems on which FP32 and FP64 cycles are compared")
@@ -598,6 +599,40 @@ def general_section(a, cmg, problems, dev):
             "final_rel_residual": float(info.final_rel_residual)}
 
 
+def stokes_section(a, cmg, problems, dev):
+    """Stokes prescaling on a synthetic saddle-point problem: the MAC
+    staggered-grid steady Stokes operator on --stokes-n^2 cells with no-slip
+    walls, (d+1)-DOF cell blocks on every level, staggered transfers,
+    Galerkin levels, additive nu = 3, right GMRES V(1,1) to 1e-10, with the
+    Stokes prescaling (q = 1 and q = infinity) and without prescaling."""
+    import torch
+    t0 = time.perf_counter()
+    u = problems.mac_stokes_2d(a.stokes_n)
+    t_gen = time.perf_counter() - t0
+    hg = cmg.gsetup_hierarchy(u["A"], u["Ps"], rscale=0.25, blocks=u["blocks"], fields=u["fields"], seed=3)
+    N = u["A"].shape[0]
+    bd = torch.tensor(problems.rhs(N, 5), dtype=torch.float64, device=dev)
+    s = torch.cuda.current_stream()
+    out = {"workload": f"MAC staggered-grid steady Stokes, {a.stokes_n}^2 cells, no-slip walls ({N} unknowns), "
+                       "cell blocks of pressure + right and top faces, Galerkin levels, additive nu=3, right GMRES "
+                       "V(1,1) RF to 1e-10", "generate_s": t_gen, "levels": hg.nlevels}
+    for mode in ("stokes1", "stokesinf", "none"):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        ev[0].record(s)
+        cg = cmg.gsetup_cascade(hg, "additive", nu=3, prescale=mode)
+        ev[1].record(s)
+        x = torch.zeros(N, dtype=torch.float64, device=dev)
+        info = cmg.gsolve(hg, cg, bd, x, method="gmres_right", tol=1e-10, maxit=300, raise_on_error=False)
+        ev[2].record(s)
+        torch.cuda.synchronize()
+        out[mode] = {"cascade_ms": ev[0].elapsed_time(ev[1]), "solve_ms": ev[1].elapsed_time(ev[2]),
+                     "iterations": info.iterations, "converged": bool(info.converged),
+                     "final_rel_residual": float(info.final_rel_residual)}
+        del cg
+    return out
+
+
 # ------------------------------------------------------------------- ours
 def main():
     a = args_()
@@ -862,6 +897,8 @@ def main():
         result["cascade_forms"] = cascade_forms_section(a, cmg, A, coeff, bd, dev)
         torch.cuda.empty_cache()
         result["general_path"] = general_section(a, cmg, problems, dev)
+        torch.cuda.empty_cache()
+        result["stokes_prescaling"] = stokes_section(a, cmg, problems, dev)
         torch.cuda.empty_cache()
         # ---- plain FP64 path (stationary V-cycle iteration)
         pinfo = []

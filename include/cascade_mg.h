@@ -478,19 +478,31 @@ typedef struct {
 typedef struct cs_ghier cs_ghier;
 typedef struct cs_gcascade cs_gcascade;
 
-/* nP interpolations P[0..nP-1] (P[l]: N_l x N_{l+1}); blocks: nblocks > 0 with
- * HOST arrays bptr [nblocks + 1] and bidx [N_0] (a partition of the finest
- * unknowns, at most 16 per block; the nodes of a block in the order given),
- * or nblocks = 0 for point blocks.  The coarsest level (at most 4096
- * unknowns) is factorised densely.  Errors: CS_ERR_ARG (shapes, not a
- * partition, block too large, more than 64 colours), CS_ERR_SINGULAR,
- * CS_ERR_NOMEM, CS_ERR_CUDA. */
-cs_status cs_gsetup_hierarchy(const cs_csr *A0, int nP, const cs_csr *P, double rscale, int nblocks,
-                              const int *bptr, const int *bidx, uint64_t colour_seed, cs_stream stream,
-                              cs_ghier **out);
+/* nP interpolations P[0..nP-1] (P[l]: N_l x N_{l+1}).  Blocks per level:
+ * nblocks[l] > 0 with HOST arrays bptr[l] [nblocks[l] + 1] and bidx[l] [N_l]
+ * (a partition of the level's unknowns, at most 16 per block, the nodes of
+ * a block in the order given), nblocks[l] = 0 (or nblocks NULL) for point
+ * blocks.  field (HOST, [N_0], or NULL): 0 for a velocity or scalar unknown,
+ * 1 for a pressure (constraint) unknown; a coarse unknown takes the field
+ * of the fine unknowns its interpolation column reaches (two fields:
+ * CS_ERR_ARG).  The coarsest level (at most 1024 unknowns) is factorised
+ * densely.  Errors: CS_ERR_ARG (shapes, not a partition, block too large,
+ * more than 64 colours, fields), CS_ERR_SINGULAR, CS_ERR_NOMEM, CS_ERR_CUDA. */
+cs_status cs_gsetup_hierarchy(const cs_csr *A0, int nP, const cs_csr *P, double rscale, const int *nblocks,
+                              const int *const *bptr, const int *const *bidx, const int *field,
+                              uint64_t colour_seed, cs_stream stream, cs_ghier **out);
+/* Prescaling W of the general path (Sec. 2.3): none; elliptic,
+ * W = diag(A_ii^-1/2); Stokes (SM "Prescaling Stokes problems"): a velocity
+ * unknown takes w_i = sqrt(||A_{i,:}||_1) / A_ii, the 1-norm over the
+ * velocity columns (so the velocity diagonal of W A W is ||A_{i,:}||_1 /
+ * A_ii), and the pressure weights make every row of diag(w_p) D diag(w_u)
+ * of unit q-norm, q = 1 (the paper's choice for finite differences), 2 or
+ * infinity (its choice for element methods). */
+enum { CS_PRESCALE_NONE = 0, CS_PRESCALE_ELLIPTIC = 1, CS_PRESCALE_STOKES_L1 = 2, CS_PRESCALE_STOKES_L2 = 3,
+       CS_PRESCALE_STOKES_LINF = 4 };
 /* The cascade of every smoothing level: kind CS_ADDITIVE or
- * CS_MULTIPLICATIVE (greedy colours), depth nu (1..8), prescale as in
- * cs_cascade_opts.  The residual rows E are kept per block over the union
+ * CS_MULTIPLICATIVE (greedy colours), depth nu (1..8), prescale a
+ * CS_PRESCALE_* mode (Stokes modes need the fields).  The residual rows E are kept per block over the union
  * of the block rows' columns; their patterns are built on the host, their
  * values on the device.  Errors: CS_ERR_ARG (non-positive diagonal under
  * prescaling), CS_ERR_NOMEM, CS_ERR_CUDA. */

@@ -84,6 +84,9 @@ def _load():
             "ora_ghier_set_fields": (None, [P, P]),
             "ora_ghier_finish": (I, [P, C.c_uint64]),
             "ora_prescale_weights": (I, [P, I, I, P]),
+            "ora_hier_nbidx": (I, [P, I]),
+            "ora_hier_overlap": (I, [P, I]),
+            "ora_casc_create_ex": (P, [P, I, I, I, I, I]),
             "ora_hier_ncol": (I, [P, I]),
             "ora_block_prio": (C.c_uint64, [C.c_uint64, I, I]),
             "ora_casc_create_sketch": (P, [P, I, I, I, I, C.c_uint64, I]),
@@ -199,6 +202,9 @@ class Hierarchy:
             raise ValueError("prescaling weight undefined (non-positive diagonal or norm)")
         return out
 
+    def overlapping(self, l: int) -> bool:
+        return bool(_lib.ora_hier_overlap(self._h, l))
+
     def ncolours(self, l: int) -> int:
         return int(_lib.ora_hier_ncol(self._h, l))
 
@@ -233,7 +239,7 @@ class Hierarchy:
         """(bptr, members, parity) of the level-l block partition."""
         nb = _lib.ora_hier_nblocks(self._h, l)
         bptr = np.zeros(nb + 1, dtype=np.int32)
-        bidx = np.zeros(self.N(l), dtype=np.int32)
+        bidx = np.zeros(_lib.ora_hier_nbidx(self._h, l), dtype=np.int32)
         bpar = np.zeros(nb, dtype=np.int32)
         _lib.ora_hier_blocks(self._h, l, _ptr(bptr), _ptr(bidx), _ptr(bpar))
         return bptr, bidx, bpar
@@ -273,7 +279,8 @@ class Cascade:
     (Algorithm 2; SM Algorithm for kind='multiplicative', red-black)."""
 
     def __init__(self, hier: Hierarchy, kind: str = "additive", nu: int = 3, prescale: bool = True,
-                 alpha: int = 0, _empty: bool = False, sketch: int = 0, seed: int = 0, exact_first: bool = False):
+                 alpha: int = 0, _empty: bool = False, sketch: int = 0, seed: int = 0, exact_first: bool = False,
+                 spd: bool = False):
         """sketch > 0: the sketched setup of the concluding remarks (Sec. 4)
         with a Rademacher sketch of `sketch` columns from `seed` (see
         ``rademacher``); exact_first: step 1 unsketched."""
@@ -287,7 +294,7 @@ class Cascade:
             self._c = _lib.ora_casc_create_sketch(hier._h, KINDS[kind], nu, PRESCALE[prescale], int(sketch),
                                                   int(seed) & 0xFFFFFFFFFFFFFFFF, int(exact_first))
         else:
-            self._c = _lib.ora_casc_create(hier._h, KINDS[kind], nu, PRESCALE[prescale], alpha)
+            self._c = _lib.ora_casc_create_ex(hier._h, KINDS[kind], nu, PRESCALE[prescale], alpha, int(spd))
         if not self._c:
             raise RuntimeError("oracle cascade setup failed (non-positive diagonal under prescaling?)")
         self.nlev = _lib.ora_casc_nlev(self._c)
@@ -347,7 +354,7 @@ def solve(h: Hierarchy, c: Cascade, b, x=None, method: str = "stationary", mu_pr
     hist = np.zeros(2 * maxit + 4)
     nh = C.c_int(0)
     fin = C.c_double(0.0)
-    code = {"stationary": 0, "gmres": 1, "gmres_right": 2}[method]
+    code = {"stationary": 0, "gmres": 1, "gmres_right": 2, "pcg": 3}[method]
     it = _lib.ora_solve(h._h, c._c, code, mu_pre, mu_post, int(rf), tol,
                         maxit, restart, _ptr(_f64(b)), _ptr(x), _ptr(hist), C.byref(nh), C.byref(fin))
     return x, int(it), hist[: nh.value].copy(), float(fin.value)

@@ -384,6 +384,77 @@ static void ls_solve_block(const double *G, const double *C, int n, double *Lam)
     free(L); free(y);
 }
 
+/* The SPD projection of a block of Lambda~ for PCG (SM "On preconditioned
+ * conjugate gradient": Lambda symmetric, I - Lambda A a contraction, the
+ * projection guided by block Jacobi), read as: the nearest matrix, in the
+ * Frobenius norm weighted by D = A~_bb (the block's diagonal block of the
+ * prescaled operator), to the symmetric part of L among the matrices
+ * 0 <= X <= D^{-1}, i.e. between zero and the block-Jacobi block.  With
+ * D = U diag(d) U^T, M = D^{1/2} sym(L) D^{1/2} = Q diag(m) Q^T, the result
+ * is D^{-1/2} Q diag(clip(m, 0, 1)) Q^T D^{-1/2}.  When D is not positive
+ * definite the Frobenius-nearest positive semidefinite matrix is taken
+ * (the symmetric part with its negative eigenvalues set to zero; Higham
+ * 1988). */
+static void project_spd_block(double *L, const double *D, int n) {
+    double *S = xmalloc(sizeof(double) * (size_t)n * n), *Q = xmalloc(sizeof(double) * (size_t)n * n);
+    double *U = xmalloc(sizeof(double) * (size_t)n * n), *T = xmalloc(sizeof(double) * (size_t)n * n);
+    double *ev = xmalloc(sizeof(double) * (size_t)n), *dv = xmalloc(sizeof(double) * (size_t)n);
+    double *Dh = xmalloc(sizeof(double) * (size_t)n * n), *Di = xmalloc(sizeof(double) * (size_t)n * n);
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q) S[p * n + q] = 0.5 * (L[p * n + q] + L[q * n + p]);
+    memcpy(T, D, sizeof(double) * (size_t)n * n);
+    sym_eig(T, n, dv, U);
+    int pd = 1;
+    for (int k = 0; k < n; ++k) if (!(dv[k] > 0.0)) pd = 0;
+    if (pd) {
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) {
+                double a = 0.0, b = 0.0;
+                for (int k = 0; k < n; ++k) {
+                    a += U[p * n + k] * sqrt(dv[k]) * U[q * n + k];
+                    b += U[p * n + k] / sqrt(dv[k]) * U[q * n + k];
+                }
+                Dh[p * n + q] = a;
+                Di[p * n + q] = b;
+            }
+        /* T = Dh S Dh */
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) {
+                double a = 0.0;
+                for (int r = 0; r < n; ++r)
+                    for (int t = 0; t < n; ++t) a += Dh[p * n + r] * S[r * n + t] * Dh[t * n + q];
+                T[p * n + q] = a;
+            }
+        sym_eig(T, n, ev, Q);
+        for (int k = 0; k < n; ++k) ev[k] = ev[k] < 0.0 ? 0.0 : (ev[k] > 1.0 ? 1.0 : ev[k]);
+        /* S = Q diag(ev) Q^T, then L = Di S Di */
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) {
+                double a = 0.0;
+                for (int k = 0; k < n; ++k) a += Q[p * n + k] * ev[k] * Q[q * n + k];
+                S[p * n + q] = a;
+            }
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) {
+                double a = 0.0;
+                for (int r = 0; r < n; ++r)
+                    for (int t = 0; t < n; ++t) a += Di[p * n + r] * S[r * n + t] * Di[t * n + q];
+                L[p * n + q] = a;
+            }
+    } else {
+        memcpy(T, S, sizeof(double) * (size_t)n * n);
+        sym_eig(T, n, ev, Q);
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) {
+                double a = 0.0;
+                for (int k = 0; k < n; ++k)
+                    if (ev[k] > 0.0) a += Q[p * n + k] * ev[k] * Q[q * n + k];
+                L[p * n + q] = a;
+            }
+    }
+    free(S); free(Q); free(U); free(T); free(ev); free(dv); free(Dh); free(Di);
+}
+
 /* ----------------------------------------------------- hierarchy */
 typedef struct {
     int dim, nlev, periodic, bs;
@@ -397,6 +468,7 @@ typedef struct {
     int *bptr[ORA_MAXLEV], *bidx[ORA_MAXLEV], *bpar[ORA_MAXLEV];
     int ncol[ORA_MAXLEV];  /* colours of the multiplicative cascade per level (red-black: 2) */
     int *field[ORA_MAXLEV];  /* per unknown: 0 velocity / scalar, 1 pressure (constraint); NULL: all 0 */
+    int overlap[ORA_MAXLEV]; /* the blocks overlap (a node in several blocks) */
     /* coarsest-level dense factor */
     int cn, cspd;
     double *cfac;
@@ -524,9 +596,10 @@ void ora_hier_csr(const ora_hier *h, int l, int64_t *rp, int *ci, double *v) {
     memcpy(v, A->v, sizeof(double) * (size_t)A->rp[A->n]);
 }
 int ora_hier_nblocks(const ora_hier *h, int l) { return h->nb[l]; }
+int ora_hier_nbidx(const ora_hier *h, int l) { return h->bptr[l][h->nb[l]]; }
 void ora_hier_blocks(const ora_hier *h, int l, int *bptr, int *bidx, int *bpar) {
     memcpy(bptr, h->bptr[l], sizeof(int) * ((size_t)h->nb[l] + 1));
-    memcpy(bidx, h->bidx[l], sizeof(int) * (size_t)h->A[l].n);
+    memcpy(bidx, h->bidx[l], sizeof(int) * (size_t)h->bptr[l][h->nb[l]]);
     memcpy(bpar, h->bpar[l], sizeof(int) * (size_t)h->nb[l]);
 }
 
@@ -592,20 +665,53 @@ int ora_ghier_add_level(ora_hier *h, int Nc, const int64_t *prp, const int *pci,
 int ora_ghier_set_blocks(ora_hier *h, int l, int nb, const int *bptr, const int *bidx) {
     if (l < 0 || l >= h->nlev) return -1;
     int N = h->A[l].n;
-    if (nb < 1 || bptr[0] != 0 || bptr[nb] != N) return -1;
-    int *seen = xcalloc((size_t)N, sizeof(int));
-    for (int p = 0; p < N; ++p) {
-        if (bidx[p] < 0 || bidx[p] >= N || seen[bidx[p]]++) { free(seen); return -1; }
-    }
-    free(seen);
+    if (nb < 1 || bptr[0] != 0) return -1;
     for (int b = 0; b < nb; ++b) if (bptr[b + 1] <= bptr[b]) return -1;
+    int M = bptr[nb];
+    /* every node in at least one block, no node twice in one block; a node
+     * in several blocks makes the blocks overlapping (Sec. 3.6.2) */
+    int *cnt = xcalloc((size_t)N, sizeof(int)), *last = xmalloc(sizeof(int) * (size_t)N);
+    for (int i = 0; i < N; ++i) last[i] = -1;
+    int over = 0, bad = 0;
+    for (int b = 0; b < nb && !bad; ++b)
+        for (int p = bptr[b]; p < bptr[b + 1]; ++p) {
+            int i = bidx[p];
+            if (i < 0 || i >= N || last[i] == b) { bad = 1; break; }
+            last[i] = b;
+            if (cnt[i]++) over = 1;
+        }
+    for (int i = 0; i < N && !bad; ++i) if (!cnt[i]) bad = 1;
+    free(cnt); free(last);
+    if (bad) return -1;
     free(h->bptr[l]); free(h->bidx[l]);
     h->nb[l] = nb;
+    h->overlap[l] = over;
     h->bptr[l] = xmalloc(sizeof(int) * ((size_t)nb + 1));
-    h->bidx[l] = xmalloc(sizeof(int) * (size_t)N);
+    h->bidx[l] = xmalloc(sizeof(int) * (size_t)M);
     memcpy(h->bptr[l], bptr, sizeof(int) * ((size_t)nb + 1));
-    memcpy(h->bidx[l], bidx, sizeof(int) * (size_t)N);
+    memcpy(h->bidx[l], bidx, sizeof(int) * (size_t)M);
     return 0;
+}
+int ora_hier_overlap(const ora_hier *h, int l) { return h->overlap[l]; }
+
+/* node -> blocks containing it, in ascending block order (CSR: nptr [N+1],
+ * nblk / nloc [M]: the block and the node's position in it) */
+static void node_blocks(const ora_hier *h, int l, int **nptr, int **nblk, int **nloc) {
+    int N = h->A[l].n, nb = h->nb[l], M = h->bptr[l][nb];
+    *nptr = xcalloc((size_t)N + 1, sizeof(int));
+    *nblk = xmalloc(sizeof(int) * (size_t)M);
+    *nloc = xmalloc(sizeof(int) * (size_t)M);
+    for (int p = 0; p < M; ++p) (*nptr)[h->bidx[l][p] + 1]++;
+    for (int i = 0; i < N; ++i) (*nptr)[i + 1] += (*nptr)[i];
+    int *fill = xmalloc(sizeof(int) * (size_t)N);
+    for (int i = 0; i < N; ++i) fill[i] = (*nptr)[i];
+    for (int b = 0; b < nb; ++b)
+        for (int p = h->bptr[l][b]; p < h->bptr[l][b + 1]; ++p) {
+            int q = fill[h->bidx[l][p]]++;
+            (*nblk)[q] = b;
+            (*nloc)[q] = p - h->bptr[l][b];
+        }
+    free(fill);
 }
 
 /* Field of every finest unknown (0 velocity or scalar, 1 pressure); the
@@ -626,27 +732,39 @@ static int cmp_prio(const void *a, const void *b) {
 
 static void greedy_colour(ora_hier *h, int l, uint64_t seed) {
     const csr *A = &h->A[l];
-    int N = A->n, nb = h->nb[l];
-    int *blk = xmalloc(sizeof(int) * (size_t)N);
-    for (int b = 0; b < nb; ++b) for (int p = h->bptr[l][b]; p < h->bptr[l][b + 1]; ++p) blk[h->bidx[l][p]] = b;
-    /* symmetrised block adjacency as lists (duplicates allowed) */
-    int64_t nnz = A->rp[N];
+    int nb = h->nb[l];
+    int *nptr, *nblk, *nloc;
+    node_blocks(h, l, &nptr, &nblk, &nloc);
+    /* symmetrised block adjacency as lists (duplicates allowed): blocks b and
+     * c touch when a row of b couples to a node of c, or they share a node */
     int *deg = xcalloc((size_t)nb + 1, sizeof(int));
-    for (int i = 0; i < N; ++i)
-        for (int64_t q = A->rp[i]; q < A->rp[i + 1]; ++q) {
-            int bi = blk[i], bj = blk[A->ci[q]];
-            if (bi != bj) { deg[bi + 1]++; deg[bj + 1]++; }
+    for (int b = 0; b < nb; ++b)
+        for (int p = h->bptr[l][b]; p < h->bptr[l][b + 1]; ++p) {
+            int i = h->bidx[l][p];
+            for (int64_t q = A->rp[i] - 1; q < A->rp[i + 1]; ++q) {  /* q = rp[i] - 1: the node itself */
+                int j = q < A->rp[i] ? i : A->ci[q];
+                for (int u = nptr[j]; u < nptr[j + 1]; ++u)
+                    if (nblk[u] != b) { deg[b + 1]++; deg[nblk[u] + 1]++; }
+            }
         }
     for (int b = 0; b < nb; ++b) deg[b + 1] += deg[b];
     int *adj = xmalloc(sizeof(int) * (size_t)(deg[nb] ? deg[nb] : 1));
     int *fill = xmalloc(sizeof(int) * (size_t)nb);
     for (int b = 0; b < nb; ++b) fill[b] = deg[b];
-    for (int i = 0; i < N; ++i)
-        for (int64_t q = A->rp[i]; q < A->rp[i + 1]; ++q) {
-            int bi = blk[i], bj = blk[A->ci[q]];
-            if (bi != bj) { adj[fill[bi]++] = bj; adj[fill[bj]++] = bi; }
+    for (int b = 0; b < nb; ++b)
+        for (int p = h->bptr[l][b]; p < h->bptr[l][b + 1]; ++p) {
+            int i = h->bidx[l][p];
+            for (int64_t q = A->rp[i] - 1; q < A->rp[i + 1]; ++q) {
+                int j = q < A->rp[i] ? i : A->ci[q];
+                for (int u = nptr[j]; u < nptr[j + 1]; ++u) {
+                    int c = nblk[u];
+                    if (c == b) continue;
+                    adj[fill[b]++] = c; adj[fill[c]++] = b;
+                }
+            }
         }
-    (void)nnz;
+    free(nptr); free(nblk); free(nloc);
+    int *blk = NULL;
     prio_t *ord = xmalloc(sizeof(prio_t) * (size_t)nb);
     for (int b = 0; b < nb; ++b) { ord[b].p = block_prio(seed, l, b); ord[b].b = b; }
     qsort(ord, (size_t)nb, sizeof(prio_t), cmp_prio);
@@ -769,7 +887,7 @@ int ora_prescale_weights(const ora_hier *h, int l, int mode, double *w) { return
 
 /* One level's cascade (Algorithm 2 / SM Algorithm).  A is the level
  * operator; lam receives nu * lamsize doubles, efrob nu*ncol+1 doubles. */
-static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescale, int alpha,
+static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescale, int alpha, int spd,
                          const int64_t *lamoff, double *lam, double *efrob) {
     const csr *A0 = &h->A[l];
     int N = A0->n, nb = h->nb[l];
@@ -779,6 +897,8 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
     /* the prescaling W (Sec. 2.3) */
     double *w = xmalloc(sizeof(double) * (size_t)N);
     if (prescale_weights(h, l, prescale, w) != 0) { free(w); return -1; }
+    const int over = h->overlap[l];
+    if (over && alpha > 0) { free(w); return -1; }
     csr A;
     A.n = A.m = N;
     int64_t annz = A0->rp[N];
@@ -789,6 +909,15 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
     memcpy(A.ci, A0->ci, sizeof(int) * (size_t)annz);
     for (int i = 0; i < N; ++i)
         for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) A.v[p] = w[i] * A0->v[p] * w[A.ci[p]];
+    /* overlapping additive blocks (Sec. 3.6.2): every block's new rows are
+     * kept and the node rows fused by weighted averaging,
+     * E_l = diag(theta)^{-1} Theta^T (Theta - Lambda Theta A) E_{l-1} */
+    int *nptr = NULL, *nblk = NULL, *nloc = NULL;
+    srow *bnew = NULL;
+    if (over) {
+        node_blocks(h, l, &nptr, &nblk, &nloc);
+        bnew = xcalloc((size_t)bptr[nb], sizeof(srow));  /* per (block, row) */
+    }
 
     /* block id of each unknown, for the truncation ranking */
     int *blk_of = xmalloc(sizeof(int) * (size_t)N);
@@ -865,6 +994,15 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
                     }
                 double *Lb = lam + (size_t)lev * lamsize + lamoff[b];
                 ls_solve_block(G, C, nbk, Lb);
+                if (spd) {
+                    double *Dbb = xcalloc((size_t)nbk * nbk, sizeof(double));
+                    for (int p = 0; p < nbk; ++p)
+                        for (int64_t q = A.rp[rows[p]]; q < A.rp[rows[p] + 1]; ++q)
+                            for (int t = 0; t < nbk; ++t)
+                                if (A.ci[q] == rows[t]) Dbb[p * nbk + t] += A.v[q];
+                    project_spd_block(Lb, Dbb, nbk);
+                    free(Dbb);
+                }
                 /* new block rows E_b - Lam R_b */
                 for (int p = 0; p < nbk; ++p)
                     for (int t = 0; t < nu_cols; ++t) {
@@ -905,7 +1043,7 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
                 for (int p = 0; p < nbk; ++p) {
                     int cnt = 0;
                     for (int t = 0; t < nu_cols; ++t) cnt += keep[t];
-                    srow *o = &Enew[rows[p]];
+                    srow *o = (over && kind == 0) ? &bnew[bptr[b] + p] : &Enew[rows[p]];
                     o->nnz = cnt;
                     o->c = xmalloc(sizeof(int) * (size_t)(cnt ? cnt : 1));
                     o->v = xmalloc(sizeof(double) * (size_t)(cnt ? cnt : 1));
@@ -917,6 +1055,41 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
             }
             free(mark); free(pos); free(bmark); free(ulist);
           }
+            if (over && kind == 0) {
+                /* fuse: node i's row is the average of its blocks' rows, summed in
+                 * ascending block order over the union of their columns */
+#pragma omp parallel
+              {
+                int *mk = xmalloc(sizeof(int) * (size_t)N), *ps = xmalloc(sizeof(int) * (size_t)N);
+                int *ul = xmalloc(sizeof(int) * (size_t)N);
+                for (int i = 0; i < N; ++i) mk[i] = -1;
+#pragma omp for schedule(dynamic, 64)
+                for (int i = 0; i < N; ++i) {
+                    int nc = 0;
+                    for (int u = nptr[i]; u < nptr[i + 1]; ++u) {
+                        const srow *br = &bnew[bptr[nblk[u]] + nloc[u]];
+                        for (int t = 0; t < br->nnz; ++t)
+                            if (mk[br->c[t]] != i) { mk[br->c[t]] = i; ul[nc++] = br->c[t]; }
+                    }
+                    qsort(ul, (size_t)nc, sizeof(int), cmp_int);
+                    for (int t = 0; t < nc; ++t) ps[ul[t]] = t;
+                    srow *o = &Enew[i];
+                    o->nnz = nc;
+                    o->c = xmalloc(sizeof(int) * (size_t)(nc ? nc : 1));
+                    o->v = xcalloc((size_t)(nc ? nc : 1), sizeof(double));
+                    for (int t = 0; t < nc; ++t) o->c[t] = ul[t];
+                    for (int u = nptr[i]; u < nptr[i + 1]; ++u) {
+                        const srow *br = &bnew[bptr[nblk[u]] + nloc[u]];
+                        for (int t = 0; t < br->nnz; ++t) o->v[ps[br->c[t]]] += br->v[t];
+                    }
+                    const double th = (double)(nptr[i + 1] - nptr[i]);
+                    for (int t = 0; t < nc; ++t) o->v[t] /= th;
+                }
+                free(mk); free(ps); free(ul);
+              }
+                for (int q = 0; q < bptr[nb]; ++q) { free(bnew[q].c); free(bnew[q].v); bnew[q].c = NULL; bnew[q].v = NULL; bnew[q].nnz = 0; }
+                for (int i = 0; i < N; ++i) { free(E[i].c); free(E[i].v); E[i] = Enew[i]; Enew[i].c = NULL; Enew[i].v = NULL; Enew[i].nnz = 0; }
+            } else
             /* commit colour k (all blocks for the additive form) */
             for (int b = 0; b < nb; ++b) {
                 if (block_colour(h, l, kind, b) != k) continue;
@@ -945,6 +1118,7 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
         }
     for (int i = 0; i < N; ++i) { free(E[i].c); free(E[i].v); }
     free(E); free(Enew); free(blk_of); free(w);
+    free(nptr); free(nblk); free(nloc); free(bnew);
     csr_free(&A);
     return 0;
 }
@@ -982,10 +1156,12 @@ void ora_casc_free(ora_casc *c) {
 /* kind: 0 additive, 1 multiplicative (red-black).  Builds a cascade on every
  * level that has a smoother (all but the coarsest; a single-level hierarchy
  * gets one on its only level). */
-ora_casc *ora_casc_create(const ora_hier *h, int kind, int nu, int prescale, int alpha) {
+/* spd != 0: every block of Lambda~ projected to the nearest symmetric
+ * positive semidefinite matrix before the next step (for PCG). */
+ora_casc *ora_casc_create_ex(const ora_hier *h, int kind, int nu, int prescale, int alpha, int spd) {
     ora_casc *c = casc_alloc(h, kind, nu);
     for (int l = 0; l < c->nlev; ++l) {
-        if (cascade_level(h, l, kind, nu, prescale, alpha, c->lamoff[l], c->lam[l], c->efrob[l]) != 0) {
+        if (cascade_level(h, l, kind, nu, prescale, alpha, spd, c->lamoff[l], c->lam[l], c->efrob[l]) != 0) {
             ora_casc_free(c);
             return NULL;
         }
@@ -1127,6 +1303,10 @@ ora_casc *ora_casc_create_sketch(const ora_hier *h, int kind, int nu, int presca
     return c;
 }
 
+ora_casc *ora_casc_create(const ora_hier *h, int kind, int nu, int prescale, int alpha) {
+    return ora_casc_create_ex(h, kind, nu, prescale, alpha, 0);
+}
+
 /* A cascade with all Lambda = 0, to be filled by ora_casc_set_lambda. */
 ora_casc *ora_casc_empty(const ora_hier *h, int kind, int nu) { return casc_alloc(h, kind, nu); }
 int ora_casc_nlev(const ora_casc *c) { return c->nlev; }
@@ -1165,6 +1345,33 @@ void ora_smooth(const ora_hier *h, const ora_casc *c, int l, int reverse, const 
         for (int kk = 0; kk < c->ncl[l]; ++kk) {
             int K = reverse ? c->ncl[l] - 1 - kk : kk;
             ora_residual(h, l, b, x, r);
+            if (h->overlap[l] && c->kind == 0) {
+                /* x -= diag(theta)^{-1} Theta^T Lambda Theta r (Sec. 3.6.2): the
+                 * block corrections, then each node's average over its blocks */
+                double *d = xmalloc(sizeof(double) * (size_t)bptr[nb]);
+#pragma omp parallel for schedule(static)
+                for (int bk = 0; bk < nb; ++bk) {
+                    int nbk = bptr[bk + 1] - bptr[bk];
+                    const int *rows = bidx + bptr[bk];
+                    const double *Lb = c->lam[l] + (size_t)L * c->lamsize[l] + c->lamoff[l][bk];
+                    for (int p = 0; p < nbk; ++p) {
+                        double s = 0.0;
+                        for (int q = 0; q < nbk; ++q)
+                            s += (reverse ? Lb[q * nbk + p] : Lb[p * nbk + q]) * r[rows[q]];
+                        d[bptr[bk] + p] = s;
+                    }
+                }
+                int *nptr, *nblk, *nloc;
+                node_blocks(h, l, &nptr, &nblk, &nloc);
+#pragma omp parallel for schedule(static)
+                for (int i = 0; i < N; ++i) {
+                    double s = 0.0;
+                    for (int u = nptr[i]; u < nptr[i + 1]; ++u) s += d[bptr[nblk[u]] + nloc[u]];
+                    x[i] -= s / (double)(nptr[i + 1] - nptr[i]);
+                }
+                free(d); free(nptr); free(nblk); free(nloc);
+                continue;
+            }
 #pragma omp parallel for schedule(static)
             for (int bk = 0; bk < nb; ++bk) {
                 if (block_colour(h, l, c->kind, bk) != K) continue;
@@ -1261,6 +1468,44 @@ int ora_solve(const ora_hier *h, const ora_casc *c, int method, int mu_pre, int 
         }
         conv = rel <= tol;
         if (final_rel) *final_rel = rel;
+    } else if (method == 3) {
+        /* preconditioned conjugate gradient with M = V(0, .) (SM "On
+         * preconditioned conjugate gradient"; M must be SPD for it to
+         * converge); history: ||b - A x_k|| / ||b|| of the recurrence */
+        double *z = xmalloc(sizeof(double) * (size_t)N), *pv = xmalloc(sizeof(double) * (size_t)N);
+        double *q = xmalloc(sizeof(double) * (size_t)N);
+        ora_residual(h, 0, b, x, r);
+        for (int i = 0; i < N; ++i) r[i] = -r[i];
+        double rel = nrm2(r, N) / nb;
+        hist[nh++] = rel;
+        for (int i = 0; i < N; ++i) z[i] = 0.0;
+        ora_vcycle(h, c, mu_pre, mu_post, rf, r, z);
+        double rz = 0.0;
+        for (int i = 0; i < N; ++i) { pv[i] = z[i]; rz += r[i] * z[i]; }
+        while (rel > tol && it < maxit) {
+            csr_matvec(&h->A[0], pv, q);
+            double pq = 0.0;
+            for (int i = 0; i < N; ++i) pq += pv[i] * q[i];
+            double alpha = rz / pq;
+            for (int i = 0; i < N; ++i) { x[i] += alpha * pv[i]; r[i] -= alpha * q[i]; }
+            ++it;
+            rel = nrm2(r, N) / nb;
+            hist[nh++] = rel;
+            if (!(rel > tol)) break;
+            for (int i = 0; i < N; ++i) z[i] = 0.0;
+            ora_vcycle(h, c, mu_pre, mu_post, rf, r, z);
+            double rz1 = 0.0;
+            for (int i = 0; i < N; ++i) rz1 += r[i] * z[i];
+            double beta = rz1 / rz;
+            rz = rz1;
+            for (int i = 0; i < N; ++i) pv[i] = z[i] + beta * pv[i];
+        }
+        /* the true residual decides */
+        ora_residual(h, 0, b, x, r);
+        rel = nrm2(r, N) / nb;
+        conv = rel <= tol;
+        if (final_rel) *final_rel = rel;
+        free(z); free(pv); free(q);
     } else if (method == 2) {
         /* Right-preconditioned restarted GMRES (Sec. 3.1 with the cycle
          * applied on the right): x_k minimises the TRUE residual

@@ -707,33 +707,50 @@ class GCascade:
             self._p = None
 
 
-def gsetup_hierarchy(A, Ps, rscale=1.0, blocks=None, seed=0, stream=None):
+def gsetup_hierarchy(A, Ps, rscale=1.0, blocks=None, seed=0, fields=None, stream=None):
     """General sparse hierarchy: A (scipy sparse, N0 x N0), interpolations
     Ps (scipy sparse, N_l x N_{l+1}), Galerkin coarse operators
-    rscale P^T A P, an optional level-0 block partition (bptr, bidx), and the
-    greedy colouring's priority seed."""
+    rscale P^T A P; blocks: (bptr, bidx) of level 0 or a list of such pairs
+    (or None) per level, point blocks elsewhere; the greedy colouring's
+    priority seed; fields (0 velocity / scalar, 1 pressure) of the finest
+    unknowns for Stokes prescaling."""
     keep = []
     a = _csr_struct(A, keep)
     ps = (_capi.cs_csr * max(len(Ps), 1))(*[_csr_struct(P, keep) for P in Ps])
-    nb, bp, bi = 0, None, None
+    nlev = len(Ps) + 1
+    per = [None] * nlev
     if blocks is not None:
-        bp = np.ascontiguousarray(blocks[0], dtype=np.int32)
-        bi = np.ascontiguousarray(blocks[1], dtype=np.int32)
+        lst = blocks if isinstance(blocks, list) else [blocks]
+        per[:len(lst)] = lst
+    nbl = (C.c_int * nlev)()
+    bpp = (C.c_void_p * nlev)()
+    bip = (C.c_void_p * nlev)()
+    for l, bl in enumerate(per):
+        if bl is None:
+            continue
+        bp = np.ascontiguousarray(bl[0], dtype=np.int32)
+        bi = np.ascontiguousarray(bl[1], dtype=np.int32)
         keep += [bp, bi]
-        nb = len(bp) - 1
+        nbl[l], bpp[l], bip[l] = len(bp) - 1, bp.ctypes.data, bi.ctypes.data
+    fp = None
+    if fields is not None:
+        f = np.ascontiguousarray(fields, dtype=np.int32)
+        keep.append(f)
+        fp = f.ctypes.data
     out = C.c_void_p()
-    _capi.check(_capi.lib().cs_gsetup_hierarchy(C.byref(a), len(Ps), ps, float(rscale), nb,
-                                                bp.ctypes.data if bp is not None else None,
-                                                bi.ctypes.data if bi is not None else None,
+    _capi.check(_capi.lib().cs_gsetup_hierarchy(C.byref(a), len(Ps), ps, float(rscale), C.cast(nbl, C.c_void_p),
+                                                C.cast(bpp, C.c_void_p), C.cast(bip, C.c_void_p), fp,
                                                 int(seed) & 0xFFFFFFFFFFFFFFFF, _stream(stream), C.byref(out)),
                 "cs_gsetup_hierarchy")
     return GHierarchy(out.value)
 
 
 def gsetup_cascade(h, kind="additive", nu=3, prescale=True, stream=None):
+    """prescale: True / "elliptic", False / "none", or "stokes1", "stokes2",
+    "stokesinf" (Stokes prescaling with q = 1, 2, infinity)."""
     k = _capi.CS_MULTIPLICATIVE if kind == "multiplicative" else _capi.CS_ADDITIVE
     out = C.c_void_p()
-    _capi.check(_capi.lib().cs_gsetup_cascade(h.ptr, k, nu, int(prescale), _stream(stream), C.byref(out)),
+    _capi.check(_capi.lib().cs_gsetup_cascade(h.ptr, k, nu, _capi.PRESCALE[prescale], _stream(stream), C.byref(out)),
                 "cs_gsetup_cascade")
     return GCascade(out.value, h, kind, nu)
 

@@ -21,6 +21,7 @@ CS_ADDITIVE, CS_MULTIPLICATIVE = 0, 1
 CS_FP64, CS_FP32, CS_BF16 = 0, 1, 2
 CS_FF, CS_RF = 0, 1
 CS_STATIONARY, CS_GMRES, CS_REFINE, CS_GMRES_RIGHT = 0, 1, 2, 3
+PRESCALE = {"none": 0, "elliptic": 1, "stokes1": 2, "stokes2": 3, "stokesinf": 4, False: 0, True: 1}
 
 
 class cs_stencil(C.Structure):
@@ -98,8 +99,9 @@ _SIGS = {
     "cs_prolong_correct_lowp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                           C.c_void_p]),
     "cs_coarse_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "cs_gsetup_hierarchy": (C.c_int, [C.POINTER(cs_csr), C.c_int, C.POINTER(cs_csr), C.c_double, C.c_int,
-                                      C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "cs_gsetup_hierarchy": (C.c_int, [C.POINTER(cs_csr), C.c_int, C.POINTER(cs_csr), C.c_double, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p,
+                                      C.POINTER(C.c_void_p)]),
     "cs_gsetup_cascade": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
     "cs_gsweep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                             C.c_void_p]),

@@ -48,6 +48,8 @@ struct GLevel {
     GCsr A, P, R;  // P, R: transfers to the next coarser level
     int nb = 0, nbmax = 1;
     int ident = 0;  // the blocks are the points in order (block b = node b)
+    std::vector<int> hfield;      // per unknown: 0 velocity / scalar, 1 pressure
+    int *field = nullptr;
     std::vector<int> hbptr, hbidx, hcol;  // block partition and colour per block
     int *bptr = nullptr, *bidx = nullptr;
     int ncol = 1;
@@ -418,7 +420,7 @@ void cs_gdestroy_hierarchy(cs_ghier *h) {
     cudaDeviceSynchronize();
     for (GLevel &L : h->lev) {
         gcsr_free(L.A); gcsr_free(L.P); gcsr_free(L.R);
-        dfree(L.bptr); dfree(L.bidx); dfree(L.cblocks);
+        dfree(L.bptr); dfree(L.bidx); dfree(L.cblocks); dfree(L.field);
         dfree(L.b); dfree(L.x); dfree(L.t); dfree(L.r);
     }
     dfree(h->cinv); dfree(h->red);
@@ -426,9 +428,9 @@ void cs_gdestroy_hierarchy(cs_ghier *h) {
     delete h;
 }
 
-cs_status cs_gsetup_hierarchy(const cs_csr *A0, int nP, const cs_csr *P, double rscale, int nblocks,
-                              const int *bptr, const int *bidx, uint64_t colour_seed, cs_stream stream,
-                              cs_ghier **out) {
+cs_status cs_gsetup_hierarchy(const cs_csr *A0, int nP, const cs_csr *P, double rscale, const int *nblocks,
+                              const int *const *bptr, const int *const *bidx, const int *field,
+                              uint64_t colour_seed, cs_stream stream, cs_ghier **out) {
     if (!A0 || !out || nP < 0 || (nP > 0 && !P)) { set_error("null argument"); return CS_ERR_ARG; }
     *out = nullptr;
     if (A0->n != A0->m) { set_error("A0 must be square"); return CS_ERR_ARG; }
@@ -454,21 +456,53 @@ cs_status cs_gsetup_hierarchy(const cs_csr *A0, int nP, const cs_csr *P, double 
         gcsr_free(AP); gcsr_free(Pt);
         if (rc != CS_OK) goto fail;
     }
+    if (field) {  // fields: the user's on level 0, the coarse ones through the interpolations
+        h->lev[0].hfield.assign(field, field + h->lev[0].A.n);
+        for (int f : h->lev[0].hfield)
+            if (f != 0 && f != 1) { set_error("field values must be 0 or 1"); rc = CS_ERR_ARG; goto fail; }
+        for (int l = 0; l + 1 < h->nlev; ++l) {
+            const GCsr &Pl = h->lev[l].P;
+            std::vector<int> &fc = h->lev[l + 1].hfield;
+            fc.assign((size_t)Pl.m, -1);
+            for (int i = 0; i < Pl.n; ++i)
+                for (int64_t p = Pl.hrp[i]; p < Pl.hrp[i + 1]; ++p) {
+                    int &f = fc[Pl.hci[p]];
+                    if (f >= 0 && f != h->lev[l].hfield[i]) {
+                        set_error("P[%d] maps coarse unknown %d to fine unknowns of two fields", l, Pl.hci[p]);
+                        rc = CS_ERR_ARG;
+                        goto fail;
+                    }
+                    f = h->lev[l].hfield[i];
+                }
+            for (int &f : fc) f = f < 0 ? 0 : f;
+        }
+        for (int l = 0; l < h->nlev; ++l) {
+            GLevel &L = h->lev[l];
+            if ((rc = dalloc_t(&L.field, L.hfield.size(), &h->bytes, s)) != CS_OK) goto fail;
+            if (cudaMemcpyAsync(L.field, L.hfield.data(), sizeof(int) * L.hfield.size(), cudaMemcpyHostToDevice, s) !=
+                cudaSuccess) {
+                rc = cuda_fail(cudaGetLastError(), "copy fields", __FILE__, __LINE__);
+                goto fail;
+            }
+        }
+    }
     for (int l = 0; l < h->nlev; ++l) {
         GLevel &L = h->lev[l];
         const int N = L.A.n;
-        if (l == 0 && nblocks > 0) {
-            if (!bptr || !bidx || bptr[0] != 0 || bptr[nblocks] != N) { set_error("blocks: bad bptr"); rc = CS_ERR_ARG; goto fail; }
+        const int nbl = nblocks ? nblocks[l] : 0;
+        if (nbl > 0) {
+            const int *bp = bptr ? bptr[l] : nullptr, *bi = bidx ? bidx[l] : nullptr;
+            if (!bp || !bi || bp[0] != 0 || bp[nbl] != N) { set_error("level %d blocks: bad bptr", l); rc = CS_ERR_ARG; goto fail; }
             std::vector<char> seen((size_t)N, 0);
-            for (int b = 0; b < nblocks; ++b) {
-                const int nbk = bptr[b + 1] - bptr[b];
-                if (nbk < 1 || nbk > GMAXBLK) { set_error("block %d has %d nodes (1..%d)", b, nbk, GMAXBLK); rc = CS_ERR_ARG; goto fail; }
+            for (int b = 0; b < nbl; ++b) {
+                const int nbk = bp[b + 1] - bp[b];
+                if (nbk < 1 || nbk > GMAXBLK) { set_error("level %d block %d has %d nodes (1..%d)", l, b, nbk, GMAXBLK); rc = CS_ERR_ARG; goto fail; }
             }
             for (int p = 0; p < N; ++p)
-                if (bidx[p] < 0 || bidx[p] >= N || seen[bidx[p]]++) { set_error("blocks are not a partition"); rc = CS_ERR_ARG; goto fail; }
-            L.nb = nblocks;
-            L.hbptr.assign(bptr, bptr + nblocks + 1);
-            L.hbidx.assign(bidx, bidx + N);
+                if (bi[p] < 0 || bi[p] >= N || seen[bi[p]]++) { set_error("level %d blocks are not a partition", l); rc = CS_ERR_ARG; goto fail; }
+            L.nb = nbl;
+            L.hbptr.assign(bp, bp + nbl + 1);
+            L.hbidx.assign(bi, bi + N);
         } else {
             L.nb = N;
             L.hbptr.resize((size_t)N + 1);
@@ -628,15 +662,45 @@ __device__ void gls_small(int n, double *G, const double *C, double *L, double *
         }
 }
 
-// w_i = A_ii^{-1/2} (1 without prescaling); A~_ij = (w_i A_ij) w_j
+// The prescaling W (Sec. 2.3; SM "Prescaling Stokes problems"):
+// mode CS_PRESCALE_NONE: 1; CS_PRESCALE_ELLIPTIC: A_ii^{-1/2};
+// Stokes (q = 1, 2, infinity): a velocity / scalar unknown (field 0) takes
+// sqrt(||A_{i,:}||_1) / A_ii over the field-0 columns (pass 0), a pressure
+// unknown (field 1) the inverse q-norm of its field-0 columns scaled by
+// their weights (pass 1, after pass 0).  bad = 1 when a weight is undefined.
 __global__ void k_gprescale(int n, const int64_t *__restrict__ rp, const int *__restrict__ ci,
-                            const double *__restrict__ v, int prescale, double *__restrict__ w, int *bad) {
+                            const double *__restrict__ v, const int *__restrict__ field, int mode, int pass,
+                            double *__restrict__ w, int *bad) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double d = 0.0;
-        for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
-            if (ci[p] == i) d += v[p];
-        if (prescale && !(d > 0.0)) atomicExch(bad, 1);
-        w[i] = prescale ? 1.0 / sqrt(d) : 1.0;
+        const int fi = field ? field[i] : 0;
+        if (pass == 0) {
+            double d = 0.0, l1 = 0.0;
+            for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+                if (ci[p] == i) d += v[p];
+                if (!field || field[ci[p]] == 0) l1 += fabs(v[p]);
+            }
+            if (mode == CS_PRESCALE_NONE) {
+                w[i] = 1.0;
+            } else if (mode == CS_PRESCALE_ELLIPTIC) {
+                if (!(d > 0.0)) atomicExch(bad, 1);
+                w[i] = 1.0 / sqrt(d);
+            } else if (fi == 0) {
+                if (!(d > 0.0) || !(l1 > 0.0)) atomicExch(bad, 1);
+                w[i] = sqrt(l1) / d;
+            }
+        } else if (mode >= CS_PRESCALE_STOKES_L1 && fi == 1) {
+            double nrm = 0.0;
+            for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+                if (field[ci[p]] != 0) continue;
+                const double a = fabs(v[p]) * w[ci[p]];
+                if (mode == CS_PRESCALE_STOKES_L1) nrm += a;
+                else if (mode == CS_PRESCALE_STOKES_L2) nrm += a * a;
+                else nrm = fmax(nrm, a);
+            }
+            if (mode == CS_PRESCALE_STOKES_L2) nrm = sqrt(nrm);
+            if (!(nrm > 0.0)) atomicExch(bad, 1);
+            w[i] = 1.0 / nrm;
+        }
     }
 }
 __global__ void k_gscale_op(int n, const int64_t *__restrict__ rp, const int *__restrict__ ci,
@@ -824,14 +888,16 @@ static cs_status gsetup_level(const cs_ghier *h, int l, int kind, int nu, int pr
     CSX_CUDA_GOTO(cudaMemcpyAsync(dblk, blk.data(), sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, s));
     CSX_CUDA_GOTO(cudaMemcpyAsync(dloc, loc.data(), sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, s));
     CSX_CUDA_GOTO(cudaMemsetAsync(lam, 0, sizeof(double) * (size_t)nu * lamsize, s));
-    k_gprescale<<<std::max(1, std::min(1216, (N + 255) / 256)), 256, 0, s>>>(N, L.A.rp, L.A.ci, L.A.v, prescale, w, bad);
+    for (int pass = 0; pass < 2; ++pass)
+        k_gprescale<<<std::max(1, std::min(1216, (N + 255) / 256)), 256, 0, s>>>(N, L.A.rp, L.A.ci, L.A.v, L.field,
+                                                                                   prescale, pass, w, bad);
     k_gscale_op<<<std::max(1, std::min(1216, (N + 255) / 256)), 256, 0, s>>>(N, L.A.rp, L.A.ci, L.A.v, w, at);
     count_launch(2);
     CSX_CUDA_GOTO(cudaGetLastError());
     CSX_CUDA_GOTO(cudaMemcpyAsync(&badh, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     CSX_CUDA_GOTO(cudaStreamSynchronize(s));
     if (badh) {
-        set_error("level %d: a non-positive diagonal entry under elliptic prescaling", l);
+        set_error("level %d: a prescaling weight is undefined (non-positive diagonal or norm)", l);
         rc = CS_ERR_ARG;
         goto done;
     }
@@ -931,6 +997,11 @@ cs_status cs_gsetup_cascade(cs_ghier *h, int kind, int nu, int prescale, cs_stre
     *out = nullptr;
     if (kind != CS_ADDITIVE && kind != CS_MULTIPLICATIVE) { set_error("bad cascade kind"); return CS_ERR_ARG; }
     if (nu < 1 || nu > 8) { set_error("nu must be in 1..8"); return CS_ERR_ARG; }
+    if (prescale < CS_PRESCALE_NONE || prescale > CS_PRESCALE_STOKES_LINF) { set_error("bad prescaling mode"); return CS_ERR_ARG; }
+    if (prescale >= CS_PRESCALE_STOKES_L1 && h->lev[0].hfield.empty()) {
+        set_error("Stokes prescaling needs the fields of the unknowns");
+        return CS_ERR_ARG;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     cs_gcascade *c = new cs_gcascade();
     c->h = h;

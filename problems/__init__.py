@@ -403,7 +403,8 @@ def unstructured_q1(n: int, seed: int, coarse_side: int = 3, block: int = 3, ren
     numbering.  Nothing of the grid survives in the numbering, so a solver
     that reads it sees an unstructured mesh (renumber=False keeps the grid
     order).  Returns a dict with A (scipy CSR), Ps (list of scipy CSR),
-    blocks (bptr, bidx) and perms (perm[new] = old per level)."""
+    blocks (bptr, bidx), cells (overlapping blocks: the interior nodes of
+    every element) and perms (perm[new] = old per level)."""
     import scipy.sparse as sp
     St = q1_jittered(n, seed)
     sides = [n]
@@ -430,7 +431,16 @@ def unstructured_q1(n: int, seed: int, coarse_side: int = 3, block: int = 3, ren
     bptr = np.zeros(nb1 * nb1 + 1, dtype=np.int32)
     bptr[1:] = np.cumsum(np.bincount(bid, minlength=nb1 * nb1))
     bidx = new[order].astype(np.int32)
-    return {"A": A, "Ps": Ps, "blocks": (bptr, bidx), "perms": perms, "sides": sides}
+    # overlapping cell blocks: the interior nodes of each of the (n+1)^2
+    # elements (an interior node lies in 4 of them)
+    ex, ey = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="xy")
+    cptr, cidx = [0], []
+    for cx, cy in zip(ex.ravel(), ey.ravel()):
+        mem = [inv[0][x + n * y] for y in (cy - 1, cy) for x in (cx - 1, cx) if 0 <= x < n and 0 <= y < n]
+        cidx += sorted(int(v) for v in mem)
+        cptr.append(len(cidx))
+    cells = (np.array(cptr, dtype=np.int32), np.array(cidx, dtype=np.int32))
+    return {"A": A, "Ps": Ps, "blocks": (bptr, bidx), "cells": cells, "perms": perms, "sides": sides}
 
 
 def _mac_index(n: int):

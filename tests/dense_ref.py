@@ -125,3 +125,43 @@ def prolongation(n3, dim) -> np.ndarray:
     if dim == 2:
         return np.kron(Py, Px)
     return np.kron(prolongation_1d(n3[2]), np.kron(Py, Px))
+
+
+def dense_overlap_cascade(Ad, blocks, nu, w=None):
+    """Overlapping-block additive cascade (Sec. 3.6.2) by explicit dense
+    matrices: Theta (M x N) replicates the nodes of the blocks, theta its
+    column sums; per step Lambda_l = argmin over block-diagonal Lambda of
+    ||(Theta - Lambda Theta A~) E_{l-1}||_F (per block lstsq with the
+    method's rank rule) and E_l = diag(theta)^-1 Theta^T (Theta - Lambda_l
+    Theta A~) E_{l-1}.  Returns the unscaled per-block Lambda per step (list
+    over steps of lists over blocks) and the dense Theta."""
+    N = Ad.shape[0]
+    if w is None:
+        w = 1.0 / np.sqrt(np.diag(Ad))
+    At = w[:, None] * Ad * w[None, :]
+    M = sum(len(b) for b in blocks)
+    Th = np.zeros((M, N))
+    r = 0
+    for b in blocks:
+        for i in b:
+            Th[r, i] = 1.0
+            r += 1
+    theta = Th.sum(axis=0)
+    E = np.eye(N)
+    out = []
+    for _ in range(nu):
+        AE = At @ E
+        new = np.zeros((M, N))
+        lams = []
+        r = 0
+        for b in blocks:
+            Rb, Eb = AE[b, :], E[b, :]
+            sv = np.linalg.svd(Rb, compute_uv=False)
+            rc = np.sqrt(1e-14 * np.sum(sv ** 2)) / sv[0] if sv.size and sv[0] > 0 else 1.0
+            lt = np.linalg.lstsq(Rb.T, Eb.T, rcond=rc)[0].T
+            new[r:r + len(b)] = Eb - lt @ Rb
+            lams.append(w[b][:, None] * lt * w[b][None, :])
+            r += len(b)
+        E = (Th.T @ new) / theta[:, None]
+        out.append(lams)
+    return out, Th

@@ -163,3 +163,49 @@ def test_general_path_rejects_bad_input(built):
         cmg.gsetup_hierarchy(u["A"], u["Ps"], rscale=0.25, blocks=(bptr, bad))
     with pytest.raises(cmg.CascadeError, match="CS_ERR_ARG"):
         cmg.gsetup_hierarchy(u["A"], [sp.csr_matrix(np.ones((3, 2)))], rscale=0.25)  # wrong shape
+
+
+def _stokes_pair(n, seed=3):
+    import paper_2606_12577_gb300 as cmg
+    u = problems.mac_stokes_2d(n)
+    ho = oracle.Hierarchy.from_csr(u["A"], u["Ps"], rscale=0.25, blocks=u["blocks"], fields=u["fields"], seed=seed)
+    hg = cmg.gsetup_hierarchy(u["A"], u["Ps"], rscale=0.25, blocks=u["blocks"], fields=u["fields"], seed=seed)
+    return u, ho, hg
+
+
+@pytest.mark.parametrize("n,kind,mode", [(16, "additive", "stokes1"), (32, "multiplicative", "stokes1"),
+                                         (32, "additive", "stokesinf"), (16, "multiplicative", "stokes2")])
+def test_stokes_prescaled_cascade_matches_oracle(built, n, kind, mode):
+    """The MAC Stokes operator with (d+1)-DOF cell blocks on every level and
+    Stokes prescaling (SM "Prescaling Stokes problems"): Galerkin levels,
+    colours, Lambda and the right-GMRES solve equal the oracle's."""
+    import paper_2606_12577_gb300 as cmg
+    u, ho, hg = _stokes_pair(n)
+    for l in range(ho.nlev):
+        rp, ci, v = hg.operator(l)
+        orp, oci, ov = ho.csr(l)
+        assert np.array_equal(ci, oci) and np.abs(v - ov).max() <= 1e-14 * np.abs(ov).max(), l
+        assert np.array_equal(hg.colours(l), ho.blocks(l)[2]), l
+    co = oracle.Cascade(ho, kind, nu=3, prescale=mode)
+    cg = cmg.gsetup_cascade(hg, kind, nu=3, prescale=mode)
+    for l in range(co.nlev):
+        assert gu.rel_max(cmg.gexport_lambda(cg, l), co.lam(l)) <= TOL, l
+    b = problems.rhs(u["A"].shape[0], 11)
+    xo, ito, hist_o, _ = oracle.solve(ho, co, b, method="gmres_right", tol=1e-10, maxit=200)
+    assert ito > 0
+    x = _dev(np.zeros(len(b)))
+    info = cmg.gsolve(hg, cg, _dev(b), x, method="gmres_right", tol=1e-10, maxit=200)
+    assert info.converged and info.iterations == ito
+    np.testing.assert_allclose(info.history, hist_o, rtol=1e-8, atol=1e-13)
+    r = b - u["A"] @ _host(x)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
+
+
+def test_stokes_prescaling_needs_fields_and_rejects_elliptic(built):
+    import paper_2606_12577_gb300 as cmg
+    u, ho, hg = _stokes_pair(16)
+    with pytest.raises(cmg.CascadeError, match="CS_ERR_ARG"):
+        cmg.gsetup_cascade(hg, "additive", nu=2, prescale="elliptic")  # the pressure diagonal is negative
+    hn = cmg.gsetup_hierarchy(u["A"], u["Ps"], rscale=0.25, blocks=u["blocks"])
+    with pytest.raises(cmg.CascadeError, match="fields"):
+        cmg.gsetup_cascade(hn, "additive", nu=2, prescale="stokes1")

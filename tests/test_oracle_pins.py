@@ -914,3 +914,155 @@ def test_stokes_prescaling_makes_the_cascade_a_working_smoother():
         its[mode] = oracle.solve(h, c, b, method="gmres_right", tol=1e-10, maxit=200)[1]
     assert 0 < its["stokes1"] <= 40 and its["stokes1"] <= its["stokesinf"]
     assert its["none"] == -1
+
+
+# --------------------------------------------- overlapping blocks and PCG
+def _cells_problem(n=9, seed=5):
+    u = problems.unstructured_q1(n, seed)
+    return u, oracle.Hierarchy.from_csr(u["A"], u["Ps"], rscale=0.25, blocks=u["cells"], seed=3)
+
+
+def test_overlapping_additive_cascade_matches_dense_definition():
+    """Sec. 3.6.2: the overlapping-block additive cascade (the interior nodes
+    of every element as a block, an interior node in 4 blocks) against the
+    dense definition with Theta, and one application of the smoother
+    against x - diag(theta)^-1 Theta^T Lambda Theta (A x - b) step by step."""
+    u, h = _cells_problem()
+    assert h.overlapping(0)
+    c = oracle.Cascade(h, "additive", nu=2)
+    bptr, bidx, _ = h.blocks(0)
+    blist = [bidx[bptr[b]:bptr[b + 1]] for b in range(len(bptr) - 1)]
+    lams, Th = dense_ref.dense_overlap_cascade(u["A"].toarray(), blist, 2)
+    lam = c.lam(0)
+    offs = np.cumsum([0] + [len(b) ** 2 for b in blist])
+    for step in range(2):
+        for k, b in enumerate(blist):
+            got = lam[step, offs[k]:offs[k + 1]].reshape(len(b), len(b))
+            assert np.abs(got - lams[step][k]).max() <= 1e-10 * np.abs(lams[step][k]).max(), (step, k)
+    A = u["A"].toarray()
+    theta = Th.sum(axis=0)
+    b = problems.uniform(3, A.shape[0])
+    x0 = problems.uniform(4, A.shape[0])
+    x = x0.copy()
+    for step in range(2):
+        Lbar = np.zeros((Th.shape[0], Th.shape[0]))
+        r0 = 0
+        for k, bl in enumerate(blist):
+            Lbar[r0:r0 + len(bl), r0:r0 + len(bl)] = lam[step, offs[k]:offs[k + 1]].reshape(len(bl), len(bl))
+            r0 += len(bl)
+        x = x - (Th.T @ (Lbar @ (Th @ (A @ x - b)))) / theta
+    got = oracle.smooth(h, c, 0, b, x0)
+    assert np.abs(got - x).max() <= 1e-12 * np.abs(x).max()
+
+
+def test_overlapping_multiplicative_colours_are_disjoint():
+    """The multiplicative form overwrites (no averaging), so blocks of one
+    colour must share no node and not be coupled by A; the smoother equals
+    the colour steps applied one after another."""
+    u, h = _cells_problem()
+    c = oracle.Cascade(h, "multiplicative", nu=1)
+    bptr, bidx, col = h.blocks(0)
+    A = u["A"].toarray()
+    blist = [bidx[bptr[b]:bptr[b + 1]] for b in range(len(bptr) - 1)]
+    for k in range(h.ncolours(0)):
+        mine = [bl for bl, cc in zip(blist, col) if cc == k]
+        seen = np.zeros(A.shape[0], int)
+        for bl in mine:
+            assert not seen[bl].any()
+            seen[bl] = 1
+        for i, bl in enumerate(mine):
+            for bj in mine[i + 1:]:
+                assert not A[np.ix_(bl, bj)].any() and not A[np.ix_(bj, bl)].any()
+    lam = c.lam(0)
+    offs = np.cumsum([0] + [len(b) ** 2 for b in blist])
+    b = problems.uniform(5, A.shape[0])
+    x = problems.uniform(6, A.shape[0])
+    ref = x.copy()
+    for k in range(h.ncolours(0)):
+        r = A @ ref - b
+        for kk, bl in enumerate(blist):
+            if col[kk] == k:
+                ref[bl] -= lam[0, offs[kk]:offs[kk + 1]].reshape(len(bl), len(bl)) @ r[bl]
+    assert np.abs(oracle.smooth(h, c, 0, b, x) - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_spd_projection_is_bounded_by_block_jacobi():
+    """The SPD-projected cascade (the supplement's suggestion for PCG: Lambda
+    symmetric, I - Lambda A a contraction, guided by block Jacobi), read as
+    the nearest block, in the Frobenius norm weighted by D = A~_bb, to the
+    symmetric part of the least-squares block among 0 <= X <= D^-1: step-1
+    blocks equal that projection of the unprojected step-1 blocks (written
+    out here with numpy's eigh), every block of every step is symmetric with
+    0 <= D^1/2 Lambda~ D^1/2 <= I, and the RF V-cycle is symmetric positive
+    definite."""
+    from tests import gpu_util as gu
+    u = problems.unstructured_q1(9, 5)
+    h = oracle.Hierarchy.from_csr(u["A"], u["Ps"], rscale=0.25, blocks=u["blocks"], seed=3)
+    plain = oracle.Cascade(h, "additive", nu=3)
+    proj = oracle.Cascade(h, "additive", nu=3, spd=True)
+    bptr, bidx, _ = h.blocks(0)
+    A = gu.oracle_csr(h, 0).toarray()
+    w = 1.0 / np.sqrt(np.diag(A))
+    At = w[:, None] * A * w[None, :]
+    off = 0
+    for b in range(len(bptr) - 1):
+        rows = bidx[bptr[b]:bptr[b + 1]]
+        nb = len(rows)
+        W = np.outer(w[rows], w[rows])
+        dv, U = np.linalg.eigh(At[np.ix_(rows, rows)])
+        Dh, Di = (U * np.sqrt(dv)) @ U.T, (U / np.sqrt(dv)) @ U.T
+        lt = plain.lam(0)[0, off:off + nb * nb].reshape(nb, nb) / W
+        m, Q = np.linalg.eigh(Dh @ (0.5 * (lt + lt.T)) @ Dh)
+        ref = Di @ ((Q * np.clip(m, 0.0, 1.0)) @ Q.T) @ Di
+        got = proj.lam(0)[0, off:off + nb * nb].reshape(nb, nb) / W
+        assert np.abs(got - ref).max() <= 1e-11 * max(np.abs(ref).max(), 1e-300), b
+        for step in range(3):
+            L = proj.lam(0)[step, off:off + nb * nb].reshape(nb, nb) / W
+            assert np.abs(L - L.T).max() <= 1e-13 * np.abs(L).max()
+            e = np.linalg.eigvalsh(Dh @ (0.5 * (L + L.T)) @ Dh)
+            assert e.min() >= -1e-12 and e.max() <= 1.0 + 1e-12
+        off += nb * nb
+    N = h.N(0)
+    V = np.zeros((N, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        V[:, j] = oracle.vcycle(h, proj, e, rf=True)
+    assert np.abs(V - V.T).max() <= 1e-12 * np.abs(V).max()
+    assert np.linalg.eigvalsh(0.5 * (V + V.T)).min() > 0
+
+
+@pytest.mark.parametrize("blocks", ["points", "cells"])
+def test_pcg_matches_a_plain_pcg_around_the_oracle_cycle(blocks):
+    """The oracle's PCG (method 'pcg') against conjugate gradients written out
+    here in numpy with the oracle's RF V-cycle as the preconditioner: the
+    same iteration count to 1e-10 and the same iterate."""
+    u = problems.unstructured_q1(31, 3)
+    h = oracle.Hierarchy.from_csr(u["A"], u["Ps"], rscale=0.25, blocks=u["cells"] if blocks == "cells" else None,
+                                  seed=3)
+    c = oracle.Cascade(h, "additive", nu=3, spd=True)
+    A = u["A"]
+    b = problems.rhs(A.shape[0], 8)
+    x, it, hist, fin = oracle.solve(h, c, b, method="pcg", tol=1e-10, maxit=100)
+    assert it > 0 and fin <= 1e-10
+    M = lambda r: oracle.vcycle(h, c, r, rf=True)  # noqa: E731
+    y = np.zeros_like(b)
+    r = b.copy()
+    z = M(r)
+    p = z.copy()
+    rz = r @ z
+    k = 0
+    while np.linalg.norm(r) / np.linalg.norm(b) > 1e-10 and k < 100:
+        q = A @ p
+        al = rz / (p @ q)
+        y += al * p
+        r -= al * q
+        k += 1
+        if np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10:
+            break
+        z = M(r)
+        rz1 = r @ z
+        p = z + (rz1 / rz) * p
+        rz = rz1
+    assert k == it
+    assert np.abs(x - y).max() <= 1e-10 * np.abs(y).max()
