@@ -287,7 +287,7 @@ cs_status cs_smooth_noalloc(int dim, const int *n, int box, const double *coeff,
                             int kind, int reverse, const double *b, double *x, cs_stream stream);
 
 /* ---------------------------------------------------------------- solve */
-enum { CS_STATIONARY = 0, CS_GMRES = 1, CS_REFINE = 2, CS_GMRES_RIGHT = 3 };
+enum { CS_STATIONARY = 0, CS_GMRES = 1, CS_REFINE = 2, CS_GMRES_RIGHT = 3, CS_PCG = 4 };
 
 typedef struct {
     int method;      /* CS_STATIONARY: x <- V(x,b); CS_GMRES: left-preconditioned
@@ -297,7 +297,8 @@ typedef struct {
                         in flexible form (Z_j = V0 v_j kept, x += Z y): it minimises the
                         true residual ||b - A x||, so it also stops on it where the
                         left form's preconditioned residual ||V0 r|| no longer bounds
-                        ||r|| (high-contrast coefficients); one more N-vector per step */
+                        ||r|| (high-contrast coefficients); one more N-vector per step;
+                        CS_PCG: preconditioned conjugate gradients (general path only) */
     int restart;     /* GMRES restart length (default 30) */
     int maxit;       /* maximum V-cycle applications (default 100) */
     double tol;      /* stop when ||b - A x||_2 / ||b||_2 <= tol (default 1e-10) */
@@ -479,14 +480,18 @@ typedef struct cs_ghier cs_ghier;
 typedef struct cs_gcascade cs_gcascade;
 
 /* nP interpolations P[0..nP-1] (P[l]: N_l x N_{l+1}).  Blocks per level:
- * nblocks[l] > 0 with HOST arrays bptr[l] [nblocks[l] + 1] and bidx[l] [N_l]
- * (a partition of the level's unknowns, at most 16 per block, the nodes of
- * a block in the order given), nblocks[l] = 0 (or nblocks NULL) for point
- * blocks.  field (HOST, [N_0], or NULL): 0 for a velocity or scalar unknown,
+ * nblocks[l] > 0 with HOST arrays bptr[l] [nblocks[l] + 1] and bidx[l]
+ * [bptr[l][nblocks[l]]]: 1..16 distinct nodes per block in the order given,
+ * every node in at least one block.  A node in several blocks makes the
+ * level's blocks overlapping (Sec. 3.6.2): the additive cascade averages
+ * the blocks' rows and corrections at each node over its theta_i blocks,
+ * and the colouring separates blocks that share a node, so a
+ * multiplicative colour step writes each node once.  nblocks[l] = 0 (or
+ * nblocks NULL) for point blocks.  field (HOST, [N_0], or NULL): 0 for a velocity or scalar unknown,
  * 1 for a pressure (constraint) unknown; a coarse unknown takes the field
  * of the fine unknowns its interpolation column reaches (two fields:
  * CS_ERR_ARG).  The coarsest level (at most 1024 unknowns) is factorised
- * densely.  Errors: CS_ERR_ARG (shapes, not a partition, block too large,
+ * densely.  Errors: CS_ERR_ARG (shapes, a node in no block or twice in one, block too large,
  * more than 64 colours, fields), CS_ERR_SINGULAR, CS_ERR_NOMEM, CS_ERR_CUDA. */
 cs_status cs_gsetup_hierarchy(const cs_csr *A0, int nP, const cs_csr *P, double rscale, const int *nblocks,
                               const int *const *bptr, const int *const *bidx, const int *field,
@@ -502,11 +507,19 @@ enum { CS_PRESCALE_NONE = 0, CS_PRESCALE_ELLIPTIC = 1, CS_PRESCALE_STOKES_L1 = 2
        CS_PRESCALE_STOKES_LINF = 4 };
 /* The cascade of every smoothing level: kind CS_ADDITIVE or
  * CS_MULTIPLICATIVE (greedy colours), depth nu (1..8), prescale a
- * CS_PRESCALE_* mode (Stokes modes need the fields).  The residual rows E are kept per block over the union
- * of the block rows' columns; their patterns are built on the host, their
- * values on the device.  Errors: CS_ERR_ARG (non-positive diagonal under
- * prescaling), CS_ERR_NOMEM, CS_ERR_CUDA. */
-cs_status cs_gsetup_cascade(cs_ghier *h, int kind, int nu, int prescale, cs_stream stream, cs_gcascade **out);
+ * CS_PRESCALE_* mode (Stokes modes need the fields).  spd = 1 projects
+ * every block of Lambda~, as soon as it is solved and before the next
+ * step uses it, onto the symmetric matrices between 0 and the block-Jacobi
+ * block (A~_bb)^{-1}, nearest in the Frobenius norm weighted by A~_bb (the
+ * plain positive semidefinite projection where A~_bb is not positive
+ * definite), so that the cycle can precondition CS_PCG (SM "On
+ * preconditioned conjugate gradient").  The residual rows E are kept per
+ * block over the union of the block rows' columns (per node when blocks
+ * overlap); their patterns are built on the host, their values on the
+ * device.  Errors: CS_ERR_ARG (non-positive diagonal under prescaling, bad
+ * kind / nu / mode / spd), CS_ERR_NOMEM, CS_ERR_CUDA. */
+cs_status cs_gsetup_cascade(cs_ghier *h, int kind, int nu, int prescale, int spd, cs_stream stream,
+                            cs_gcascade **out);
 /* One cascade step (a single kernel launch on point-block levels):
  * out = x - Lambda_{step+1[, colour]} (A x - b) over every block (colour
  * = -1, additive) or over the blocks of one colour (multiplicative; out may
@@ -520,15 +533,19 @@ cs_status cs_gsmooth(const cs_ghier *h, cs_gcascade *c, int level, int reverse, 
 /* x <- V(x, b) (Algorithm 1) with the cycle options of cs_vcycle (FP64). */
 cs_status cs_gvcycle(const cs_ghier *h, cs_gcascade *c, const cs_vcycle_opts *opts, const double *b, double *x,
                      cs_stream stream);
-/* Solve as cs_solve; methods CS_STATIONARY and CS_GMRES_RIGHT; FP64
- * cycles; b, x device vectors.  Errors as cs_solve. */
+/* Solve as cs_solve; methods CS_STATIONARY, CS_GMRES_RIGHT and CS_PCG
+ * (conjugate gradients preconditioned by V(0, .); the iteration stops when
+ * the recurrence residual reaches tol, the history holds those residuals
+ * and final_rel_residual the true one; it needs a symmetric cycle, e.g. an
+ * spd cascade with mu_pre = mu_post and the RF order); FP64 cycles; b, x
+ * device vectors.  Errors as cs_solve. */
 cs_status cs_gsolve(const cs_ghier *h, cs_gcascade *c, const cs_solve_opts *opts, const double *b, double *x,
                     cs_solve_info *info, cs_stream stream);
 /* Level sizes: rows, stored entries, blocks, colours (HOST outputs, any may be NULL). */
 cs_status cs_gquery_level(const cs_ghier *h, int level, int *n, int64_t *nnz, int *nblocks, int *ncolours);
 int cs_gnlevels(const cs_ghier *h);
 /* HOST copies: the level's CSR operator; the colour of every block; the
- * block partition (bptr [nblocks + 1], bidx [n]); Lambda as [nu][lamsize]
+ * blocks (bptr [nblocks + 1], bidx [bptr[nblocks]]; bidx NULL: bptr only); Lambda as [nu][lamsize]
  * (block b's n_b x n_b matrix row-major at its offset, blocks in order;
  * Lambda_{l,k} on the blocks of colour k). */
 cs_status cs_gexport_operator(const cs_ghier *h, int level, int64_t *rowptr, int32_t *col, double *val);

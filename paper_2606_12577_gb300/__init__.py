@@ -440,7 +440,7 @@ def residual(h, level, b, x, r, norm=False, stream=None):
 
 
 _METHODS = {"stationary": _capi.CS_STATIONARY, "gmres": _capi.CS_GMRES, "refine": _capi.CS_REFINE,
-            "gmres_right": _capi.CS_GMRES_RIGHT}
+            "gmres_right": _capi.CS_GMRES_RIGHT, "pcg": _capi.CS_PCG}
 
 
 def solve(h, c, b, x, method="stationary", tol=1e-10, maxit=100, restart=30, mu_pre=1, mu_post=1, order="RF",
@@ -683,9 +683,10 @@ class GHierarchy:
     def blocks(self, l):
         q = self.level(l)
         bptr = np.zeros(q["nblocks"] + 1, dtype=np.int32)
-        bidx = np.zeros(q["N"], dtype=np.int32)
+        _capi.check(_capi.lib().cs_gexport_blocks(self._p, l, bptr.ctypes.data, None), "cs_gexport_blocks")
+        bidx = np.zeros(max(int(bptr[-1]), 1), dtype=np.int32)
         _capi.check(_capi.lib().cs_gexport_blocks(self._p, l, bptr.ctypes.data, bidx.ctypes.data), "cs_gexport_blocks")
-        return bptr, bidx
+        return bptr, bidx[: bptr[-1]]
 
     def __del__(self):
         if getattr(self, "_p", None) and _capi._lib is not None:
@@ -745,13 +746,14 @@ def gsetup_hierarchy(A, Ps, rscale=1.0, blocks=None, seed=0, fields=None, stream
     return GHierarchy(out.value)
 
 
-def gsetup_cascade(h, kind="additive", nu=3, prescale=True, stream=None):
+def gsetup_cascade(h, kind="additive", nu=3, prescale=True, spd=False, stream=None):
     """prescale: True / "elliptic", False / "none", or "stokes1", "stokes2",
-    "stokesinf" (Stokes prescaling with q = 1, 2, infinity)."""
+    "stokesinf" (Stokes prescaling with q = 1, 2, infinity); spd: project
+    every Lambda~ block between 0 and the block-Jacobi block, for PCG."""
     k = _capi.CS_MULTIPLICATIVE if kind == "multiplicative" else _capi.CS_ADDITIVE
     out = C.c_void_p()
-    _capi.check(_capi.lib().cs_gsetup_cascade(h.ptr, k, nu, _capi.PRESCALE[prescale], _stream(stream), C.byref(out)),
-                "cs_gsetup_cascade")
+    _capi.check(_capi.lib().cs_gsetup_cascade(h.ptr, k, nu, _capi.PRESCALE[prescale], int(bool(spd)),
+                                              _stream(stream), C.byref(out)), "cs_gsetup_cascade")
     return GCascade(out.value, h, kind, nu)
 
 

@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "CS_OK", -1: "CS_ERR_ARG", -2: "CS_ERR_CUDA", -3: "CS_ERR_NOM
 CS_ADDITIVE, CS_MULTIPLICATIVE = 0, 1
 CS_FP64, CS_FP32, CS_BF16 = 0, 1, 2
 CS_FF, CS_RF = 0, 1
-CS_STATIONARY, CS_GMRES, CS_REFINE, CS_GMRES_RIGHT = 0, 1, 2, 3
+CS_STATIONARY, CS_GMRES, CS_REFINE, CS_GMRES_RIGHT, CS_PCG = 0, 1, 2, 3, 4
 PRESCALE = {"none": 0, "elliptic": 1, "stokes1": 2, "stokes2": 3, "stokesinf": 4, False: 0, True: 1}
 
 
@@ -102,7 +102,8 @@ _SIGS = {
     "cs_gsetup_hierarchy": (C.c_int, [C.POINTER(cs_csr), C.c_int, C.POINTER(cs_csr), C.c_double, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p,
                                       C.POINTER(C.c_void_p)]),
-    "cs_gsetup_cascade": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "cs_gsetup_cascade": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                    C.POINTER(C.c_void_p)]),
     "cs_gsweep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                             C.c_void_p]),
     "cs_gsmooth": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),

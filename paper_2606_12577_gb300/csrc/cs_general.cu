@@ -50,6 +50,12 @@ struct GLevel {
     int ident = 0;  // the blocks are the points in order (block b = node b)
     std::vector<int> hfield;      // per unknown: 0 velocity / scalar, 1 pressure
     int *field = nullptr;
+    // overlapping blocks (a node in several blocks): node -> blocks holding it,
+    // ascending (nptr [N + 1], nblk / nloc [M]: block and position in it)
+    int overlap = 0;
+    std::vector<int> hnptr, hnblk, hnloc;
+    int *nptr = nullptr, *nblk = nullptr, *nloc = nullptr;
+    double *dpool = nullptr;  // per (block, row) corrections of the overlapping additive step
     std::vector<int> hbptr, hbidx, hcol;  // block partition and colour per block
     int *bptr = nullptr, *bidx = nullptr;
     int ncol = 1;
@@ -79,6 +85,7 @@ struct cs_gcascade {
     std::vector<int64_t> lamsize;
     int gm_restart = 0;
     double *gm_V = nullptr, *gm_Z = nullptr, *gm_h = nullptr;
+    double *cg = nullptr;  // PCG vectors r, z, p, q
     int64_t bytes = 0;
 };
 
@@ -288,17 +295,37 @@ __global__ void k_gjpl(int nb, const int *__restrict__ gp, const int *__restrict
     }
 }
 
-static cs_status gcolour(GLevel &L, int l, uint64_t seed, cudaStream_t s) {
-    const int N = L.A.n, nb = L.nb;
-    std::vector<int> blk((size_t)N);
+static void gnode_blocks(GLevel &L) {
+    const int N = L.A.n, nb = L.nb, M = L.hbptr[nb];
+    L.hnptr.assign((size_t)N + 1, 0);
+    L.hnblk.assign((size_t)M, 0);
+    L.hnloc.assign((size_t)M, 0);
+    for (int p = 0; p < M; ++p) L.hnptr[L.hbidx[p] + 1]++;
+    for (int i = 0; i < N; ++i) L.hnptr[i + 1] += L.hnptr[i];
+    std::vector<int> fill(L.hnptr.begin(), L.hnptr.end() - 1);
     for (int b = 0; b < nb; ++b)
-        for (int p = L.hbptr[b]; p < L.hbptr[b + 1]; ++p) blk[L.hbidx[p]] = b;
-    // symmetrised block graph without duplicates
+        for (int p = L.hbptr[b]; p < L.hbptr[b + 1]; ++p) {
+            const int q = fill[L.hbidx[p]]++;
+            L.hnblk[q] = b;
+            L.hnloc[q] = p - L.hbptr[b];
+        }
+}
+
+static cs_status gcolour(GLevel &L, int l, uint64_t seed, cudaStream_t s) {
+    const int nb = L.nb;
+    // symmetrised block graph without duplicates: blocks b and c touch when a
+    // row of b couples to a node of c or they share a node
     std::vector<std::vector<int>> nbr((size_t)nb);
-    for (int i = 0; i < N; ++i)
-        for (int64_t p = L.A.hrp[i]; p < L.A.hrp[i + 1]; ++p) {
-            const int bi = blk[i], bj = blk[L.A.hci[p]];
-            if (bi != bj) { nbr[bi].push_back(bj); nbr[bj].push_back(bi); }
+    for (int b = 0; b < nb; ++b)
+        for (int p = L.hbptr[b]; p < L.hbptr[b + 1]; ++p) {
+            const int i = L.hbidx[p];
+            for (int64_t q = L.A.hrp[i] - 1; q < L.A.hrp[i + 1]; ++q) {
+                const int j = q < L.A.hrp[i] ? i : L.A.hci[q];
+                for (int u = L.hnptr[j]; u < L.hnptr[j + 1]; ++u) {
+                    const int c = L.hnblk[u];
+                    if (c != b) { nbr[b].push_back(c); nbr[c].push_back(b); }
+                }
+            }
         }
     std::vector<int> gp((size_t)nb + 1, 0), gi;
     for (int b = 0; b < nb; ++b) {
@@ -357,11 +384,18 @@ static cs_status gblock_tables(GLevel &L, int64_t *acct, cudaStream_t s) {
     for (int b = 0; b < L.nb; ++b) cbl[fill[L.hcol[b]]++] = b;
     L.nbmax = 1;
     for (int b = 0; b < L.nb; ++b) L.nbmax = std::max(L.nbmax, L.hbptr[b + 1] - L.hbptr[b]);
-    L.ident = L.nb == L.A.n;
+    L.ident = L.nb == L.A.n && (int)L.hbidx.size() == L.A.n;
     for (int i = 0; i < L.A.n && L.ident; ++i) L.ident = L.hbidx[i] == i;
     CSX_TRY(dalloc_t(&L.cblocks, (size_t)L.nb, acct, s));
     CSX_TRY(dalloc_t(&L.bptr, (size_t)L.nb + 1, acct, s));
-    CSX_TRY(dalloc_t(&L.bidx, (size_t)L.A.n, acct, s));
+    CSX_TRY(dalloc_t(&L.bidx, L.hbidx.size(), acct, s));
+    CSX_TRY(dalloc_t(&L.nptr, L.hnptr.size(), acct, s));
+    CSX_TRY(dalloc_t(&L.nblk, L.hnblk.size(), acct, s));
+    CSX_TRY(dalloc_t(&L.nloc, L.hnloc.size(), acct, s));
+    if (L.overlap) CSX_TRY(dalloc_t(&L.dpool, L.hbidx.size(), acct, s));
+    CSX_CUDA(cudaMemcpyAsync(L.nptr, L.hnptr.data(), sizeof(int) * L.hnptr.size(), cudaMemcpyHostToDevice, s));
+    CSX_CUDA(cudaMemcpyAsync(L.nblk, L.hnblk.data(), sizeof(int) * L.hnblk.size(), cudaMemcpyHostToDevice, s));
+    CSX_CUDA(cudaMemcpyAsync(L.nloc, L.hnloc.data(), sizeof(int) * L.hnloc.size(), cudaMemcpyHostToDevice, s));
     CSX_CUDA(cudaMemcpyAsync(L.cblocks, cbl.data(), sizeof(int) * cbl.size(), cudaMemcpyHostToDevice, s));
     CSX_CUDA(cudaMemcpyAsync(L.bptr, L.hbptr.data(), sizeof(int) * L.hbptr.size(), cudaMemcpyHostToDevice, s));
     CSX_CUDA(cudaMemcpyAsync(L.bidx, L.hbidx.data(), sizeof(int) * L.hbidx.size(), cudaMemcpyHostToDevice, s));
@@ -421,6 +455,7 @@ void cs_gdestroy_hierarchy(cs_ghier *h) {
     for (GLevel &L : h->lev) {
         gcsr_free(L.A); gcsr_free(L.P); gcsr_free(L.R);
         dfree(L.bptr); dfree(L.bidx); dfree(L.cblocks); dfree(L.field);
+        dfree(L.nptr); dfree(L.nblk); dfree(L.nloc); dfree(L.dpool);
         dfree(L.b); dfree(L.x); dfree(L.t); dfree(L.r);
     }
     dfree(h->cinv); dfree(h->red);
@@ -492,17 +527,27 @@ cs_status cs_gsetup_hierarchy(const cs_csr *A0, int nP, const cs_csr *P, double 
         const int nbl = nblocks ? nblocks[l] : 0;
         if (nbl > 0) {
             const int *bp = bptr ? bptr[l] : nullptr, *bi = bidx ? bidx[l] : nullptr;
-            if (!bp || !bi || bp[0] != 0 || bp[nbl] != N) { set_error("level %d blocks: bad bptr", l); rc = CS_ERR_ARG; goto fail; }
-            std::vector<char> seen((size_t)N, 0);
+            if (!bp || !bi || bp[0] != 0) { set_error("level %d blocks: bad bptr", l); rc = CS_ERR_ARG; goto fail; }
+            // every node in at least one block and in no block twice; a node
+            // in several blocks makes the level's blocks overlapping
+            std::vector<int> cnt((size_t)N, 0), last((size_t)N, -1);
             for (int b = 0; b < nbl; ++b) {
                 const int nbk = bp[b + 1] - bp[b];
                 if (nbk < 1 || nbk > GMAXBLK) { set_error("level %d block %d has %d nodes (1..%d)", l, b, nbk, GMAXBLK); rc = CS_ERR_ARG; goto fail; }
             }
-            for (int p = 0; p < N; ++p)
-                if (bi[p] < 0 || bi[p] >= N || seen[bi[p]]++) { set_error("level %d blocks are not a partition", l); rc = CS_ERR_ARG; goto fail; }
+            if (bp[nbl] > (int64_t)N * GMAXBLK) { set_error("level %d blocks: bad bptr", l); rc = CS_ERR_ARG; goto fail; }
+            for (int b = 0; b < nbl; ++b)
+                for (int p = bp[b]; p < bp[b + 1]; ++p) {
+                    const int i = bi[p];
+                    if (i < 0 || i >= N || last[i] == b) { set_error("level %d block %d: node out of range or repeated", l, b); rc = CS_ERR_ARG; goto fail; }
+                    last[i] = b;
+                    L.overlap |= cnt[i]++ > 0;
+                }
+            for (int i = 0; i < N; ++i)
+                if (!cnt[i]) { set_error("level %d: node %d is in no block", l, i); rc = CS_ERR_ARG; goto fail; }
             L.nb = nbl;
             L.hbptr.assign(bp, bp + nbl + 1);
-            L.hbidx.assign(bi, bi + N);
+            L.hbidx.assign(bi, bi + bp[nbl]);
         } else {
             L.nb = N;
             L.hbptr.resize((size_t)N + 1);
@@ -510,6 +555,7 @@ cs_status cs_gsetup_hierarchy(const cs_csr *A0, int nP, const cs_csr *P, double 
             for (int i = 0; i <= N; ++i) L.hbptr[i] = i;
             for (int i = 0; i < N; ++i) L.hbidx[i] = i;
         }
+        gnode_blocks(L);
         if ((rc = gcolour(L, l, colour_seed, s)) != CS_OK) goto fail;
         if ((rc = gblock_tables(L, &h->bytes, s)) != CS_OK) goto fail;
         if ((rc = dalloc_t(&L.b, (size_t)N, &h->bytes, s)) != CS_OK) goto fail;
@@ -564,11 +610,11 @@ cs_status cs_gexport_colours(const cs_ghier *h, int level, int32_t *colour) {
 }
 
 cs_status cs_gexport_blocks(const cs_ghier *h, int level, int32_t *bptr, int32_t *bidx) {
-    if (!h || !bptr || !bidx) { set_error("null argument"); return CS_ERR_ARG; }
+    if (!h || !bptr) { set_error("null argument"); return CS_ERR_ARG; }
     if (level < 0 || level >= h->nlev) { set_error("bad level"); return CS_ERR_ARG; }
     const GLevel &L = h->lev[level];
     std::memcpy(bptr, L.hbptr.data(), sizeof(int) * L.hbptr.size());
-    std::memcpy(bidx, L.hbidx.data(), sizeof(int) * L.hbidx.size());
+    if (bidx) std::memcpy(bidx, L.hbidx.data(), sizeof(int) * L.hbidx.size());
     return CS_OK;
 }
 
@@ -577,6 +623,44 @@ cs_status cs_gexport_blocks(const cs_ghier *h, int level, int32_t *bptr, int32_t
 namespace csx {
 
 // ------------------------------------------------------------ cascade setup
+// Cyclic Jacobi eigendecomposition of a symmetric n x n matrix a, one
+// thread: a is left diagonal (the eigenvalues), q holds the eigenvectors in
+// its columns; sweeps until the squared off-diagonal mass is below 1e-300,
+// 100 at most.
+__device__ void gjacobi(int n, double *a, double *q) {
+    for (int i = 0; i < n * n; ++i) q[i] = 0.0;
+    for (int i = 0; i < n; ++i) q[i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) off += a[i * n + j] * a[i * n + j];
+        if (off < 1e-300) break;
+        for (int p = 0; p < n; ++p)
+            for (int r = p + 1; r < n; ++r) {
+                const double apr = a[p * n + r];
+                if (apr == 0.0) continue;
+                const double th = (a[r * n + r] - a[p * n + p]) / (2.0 * apr);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    const double akp = a[k * n + p], akr = a[k * n + r];
+                    a[k * n + p] = c * akp - s * akr;
+                    a[k * n + r] = s * akp + c * akr;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double apk = a[p * n + k], ark = a[r * n + k];
+                    a[p * n + k] = c * apk - s * ark;
+                    a[r * n + k] = s * apk + c * ark;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double qkp = q[k * n + p], qkr = q[k * n + r];
+                    q[k * n + p] = c * qkp - s * qkr;
+                    q[k * n + r] = s * qkp + c * qkr;
+                }
+            }
+    }
+}
+
 // Lambda~ (n x n) = C G^{-1} for a symmetric positive semidefinite G, one
 // thread: Cholesky when every pivot exceeds 1e-14 tr(G); otherwise the
 // minimum-norm solution C G^+, eigenvalues at or below 1e-14 tr(G) taken as
@@ -617,37 +701,7 @@ __device__ void gls_small(int n, double *G, const double *C, double *L, double *
         }
         return;
     }
-    for (int i = 0; i < n * n; ++i) Q[i] = 0.0;
-    for (int i = 0; i < n; ++i) Q[i * n + i] = 1.0;
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0;
-        for (int i = 0; i < n; ++i)
-            for (int j = i + 1; j < n; ++j) off += G[i * n + j] * G[i * n + j];
-        if (off < 1e-300) break;
-        for (int p = 0; p < n; ++p)
-            for (int r = p + 1; r < n; ++r) {
-                const double apr = G[p * n + r];
-                if (apr == 0.0) continue;
-                const double th = (G[r * n + r] - G[p * n + p]) / (2.0 * apr);
-                const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < n; ++k) {
-                    const double akp = G[k * n + p], akr = G[k * n + r];
-                    G[k * n + p] = c * akp - s * akr;
-                    G[k * n + r] = s * akp + c * akr;
-                }
-                for (int k = 0; k < n; ++k) {
-                    const double apk = G[p * n + k], ark = G[r * n + k];
-                    G[p * n + k] = c * apk - s * ark;
-                    G[r * n + k] = s * apk + c * ark;
-                }
-                for (int k = 0; k < n; ++k) {
-                    const double qkp = Q[k * n + p], qkr = Q[k * n + r];
-                    Q[k * n + p] = c * qkp - s * qkr;
-                    Q[k * n + r] = s * qkp + c * qkr;
-                }
-            }
-    }
+    gjacobi(n, G, Q);
     for (int p = 0; p < n; ++p)
         for (int q = 0; q < n; ++q) {
             double acc = 0.0;
@@ -660,6 +714,78 @@ __device__ void gls_small(int n, double *G, const double *C, double *L, double *
             }
             L[p * n + q] = acc;
         }
+}
+
+// Scratch doubles one thread needs for gproject_spd (and the block of A~).
+constexpr int GSPD_SCR = 7 * GMAXBLK * GMAXBLK + 2 * GMAXBLK;
+
+// The SPD projection of one block of Lambda~ (SM "On preconditioned
+// conjugate gradient"), one thread, L (n x n) in place.  D = A~_bb, the
+// block's diagonal block of the prescaled operator.  When D is positive
+// definite: with D = U diag(d) U^T, Dh = D^{1/2}, Di = D^{-1/2}, the
+// symmetric part S of L is mapped to M = Dh S Dh = Q diag(m) Q^T and back
+// as Di Q diag(min(max(m, 0), 1)) Q^T Di: the D-weighted Frobenius-nearest
+// matrix between 0 and the block-Jacobi block D^{-1}.  Otherwise the
+// nearest positive semidefinite matrix (S with its negative eigenvalues
+// set to zero).
+__device__ void gproject_spd(int n, double *L, const double *D, double *scr) {
+    const int nn = n * n;
+    double *S = scr, *Q = S + nn, *U = Q + nn, *T = U + nn, *Dh = T + nn, *Di = Dh + nn, *dv = Di + nn;
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q) S[p * n + q] = 0.5 * (L[p * n + q] + L[q * n + p]);
+    for (int e = 0; e < nn; ++e) T[e] = D[e];
+    gjacobi(n, T, U);
+    bool pd = true;
+    for (int k = 0; k < n; ++k) {
+        dv[k] = T[k * n + k];
+        pd = pd && dv[k] > 0.0;
+    }
+    if (pd) {
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) {
+                double a = 0.0, b = 0.0;
+                for (int k = 0; k < n; ++k) {
+                    const double sq = sqrt(dv[k]);
+                    a += U[p * n + k] * sq * U[q * n + k];
+                    b += U[p * n + k] / sq * U[q * n + k];
+                }
+                Dh[p * n + q] = a;
+                Di[p * n + q] = b;
+            }
+        for (int p = 0; p < n; ++p)  // T = Dh S Dh
+            for (int q = 0; q < n; ++q) {
+                double a = 0.0;
+                for (int r = 0; r < n; ++r)
+                    for (int t = 0; t < n; ++t) a += Dh[p * n + r] * S[r * n + t] * Dh[t * n + q];
+                T[p * n + q] = a;
+            }
+        gjacobi(n, T, Q);
+        for (int p = 0; p < n; ++p)  // S = Q diag(clip(m)) Q^T
+            for (int q = 0; q < n; ++q) {
+                double a = 0.0;
+                for (int k = 0; k < n; ++k) a += Q[p * n + k] * fmin(fmax(T[k * n + k], 0.0), 1.0) * Q[q * n + k];
+                S[p * n + q] = a;
+            }
+        for (int p = 0; p < n; ++p)  // L = Di S Di
+            for (int q = 0; q < n; ++q) {
+                double a = 0.0;
+                for (int r = 0; r < n; ++r)
+                    for (int t = 0; t < n; ++t) a += Di[p * n + r] * S[r * n + t] * Di[t * n + q];
+                L[p * n + q] = a;
+            }
+    } else {
+        for (int e = 0; e < nn; ++e) T[e] = S[e];
+        gjacobi(n, T, Q);
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) {
+                double a = 0.0;
+                for (int k = 0; k < n; ++k) {
+                    const double ev = T[k * n + k];
+                    if (ev > 0.0) a += Q[p * n + k] * ev * Q[q * n + k];
+                }
+                L[p * n + q] = a;
+            }
+    }
 }
 
 // The prescaling W (Sec. 2.3; SM "Prescaling Stokes problems"):
@@ -709,9 +835,12 @@ __global__ void k_gscale_op(int n, const int64_t *__restrict__ rp, const int *__
         for (int64_t p = rp[i]; p < rp[i + 1]; ++p) at[p] = __dmul_rn(__dmul_rn(w[i], v[p]), w[ci[p]]);
 }
 
-// The residual rows of one cascade step, block-row storage: block c holds
+// The residual rows of one cascade step in group-row storage: group c holds
 // cols[coff[c] .. + u[c]) (ascending) and values [n_c][u[c]] at voff[c];
-// ident[c]: E_c is still the identity rows (E_0).
+// ident[c]: the group's rows are still the identity rows (E_0).  The groups
+// are the blocks of a partition (n_c = the block's nodes), or the nodes
+// (n_c = 1) when blocks overlap; grp[j] / gloc[j] give node j's group and
+// row in it.
 struct GEView {
     const int64_t *coff, *voff;
     const int *u, *cols;
@@ -722,15 +851,17 @@ struct GEView {
 constexpr int GSETUP_WARPS = 4;
 
 // One step for the listed blocks: R_b = (A~ E)_{b,:} over the new pattern,
-// E_b mapped into it, G = R_b R_b^T, C = E_b R_b^T, Lambda~_b, the new rows
-// E_b - Lambda~_b R_b, and the unscaled Lambda_b = W_b Lambda~_b W_b.
+// E_b mapped into it, G = R_b R_b^T, C = E_b R_b^T, Lambda~_b (projected
+// when spd_scr is given: GSPD_SCR doubles per warp of the grid), the new
+// rows E_b - Lambda~_b R_b (block-row storage at nvoff[b]), and the
+// unscaled Lambda_b = W_b Lambda~_b W_b.
 __global__ void __launch_bounds__(32 * GSETUP_WARPS) k_gsetup_step(
     int nupd, const int *__restrict__ upd, const int *__restrict__ bptr, const int *__restrict__ bidx,
-    const int *__restrict__ blk, const int *__restrict__ loc, const int64_t *__restrict__ arp,
+    const int *__restrict__ grp, const int *__restrict__ gloc, const int64_t *__restrict__ arp,
     const int *__restrict__ aci, const double *__restrict__ at, GEView E, const int64_t *__restrict__ ncoff,
     const int64_t *__restrict__ nvoff, const int *__restrict__ nu, const int *__restrict__ ncols,
     double *__restrict__ nvals, double *__restrict__ Rpool, const int64_t *__restrict__ lamoff,
-    const double *__restrict__ w, double *__restrict__ lam) {
+    const double *__restrict__ w, double *__restrict__ lam, double *__restrict__ spd_scr) {
     __shared__ double sh[GSETUP_WARPS][4][GMAXBLK * GMAXBLK];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     double *G = sh[wl][0], *Cm = sh[wl][1], *Lt = sh[wl][2], *Q = sh[wl][3];
@@ -750,7 +881,7 @@ __global__ void __launch_bounds__(32 * GSETUP_WARPS) k_gsetup_step(
             for (int64_t q = arp[row]; q < arp[row + 1]; ++q) {
                 const int j = aci[q];
                 const double a = at[q];
-                const int c = blk[j];
+                const int c = grp[j];
                 if (E.ident[c]) {
                     if (lane == 0) {
                         const int64_t pos = gfind(U, 0, u, j);
@@ -759,7 +890,7 @@ __global__ void __launch_bounds__(32 * GSETUP_WARPS) k_gsetup_step(
                 } else {
                     const int uc = E.u[c];
                     const int *Uc = E.cols + E.coff[c];
-                    const double *Ec = E.vals + E.voff[c] + (int64_t)loc[j] * uc;
+                    const double *Ec = E.vals + E.voff[c] + (int64_t)gloc[j] * uc;
                     for (int t = lane; t < uc; t += 32) {
                         const int64_t pos = gfind(U, 0, u, Uc[t]);
                         Rb[p * u + pos] = __dadd_rn(Rb[p * u + pos], __dmul_rn(a, Ec[t]));
@@ -768,15 +899,15 @@ __global__ void __launch_bounds__(32 * GSETUP_WARPS) k_gsetup_step(
                 __syncwarp();
             }
         }
-        if (E.ident[b]) {
-            if (lane < n) Eb[lane * u + gfind(U, 0, u, rows[lane])] = 1.0;
-        } else {
-            const int ub = E.u[b];
-            const int *Ub = E.cols + E.coff[b];
-            const double *Eo = E.vals + E.voff[b];
-            for (int t = lane; t < ub; t += 32) {
-                const int64_t pos = gfind(U, 0, u, Ub[t]);
-                for (int p = 0; p < n; ++p) Eb[p * u + pos] = Eo[p * ub + t];
+        for (int p = 0; p < n; ++p) {  // the block's own rows of E
+            const int r = rows[p], g = grp[r];
+            if (E.ident[g]) {
+                if (lane == 0) Eb[p * u + gfind(U, 0, u, r)] = 1.0;
+            } else {
+                const int ug = E.u[g];
+                const int *Ug = E.cols + E.coff[g];
+                const double *Eo = E.vals + E.voff[g] + (int64_t)gloc[r] * ug;
+                for (int t = lane; t < ug; t += 32) Eb[p * u + gfind(U, 0, u, Ug[t])] = Eo[t];
             }
         }
         __syncwarp();
@@ -794,7 +925,18 @@ __global__ void __launch_bounds__(32 * GSETUP_WARPS) k_gsetup_step(
             if (lane == 0) { G[pq] = g; Cm[pq] = cc; }
         }
         __syncwarp();
-        if (lane == 0) gls_small(n, G, Cm, Lt, Q);
+        if (lane == 0) {
+            gls_small(n, G, Cm, Lt, Q);
+            if (spd_scr) {  // D = A~_bb in G, then the projection of Lt
+                double *scr = spd_scr + (int64_t)w0 * GSPD_SCR;
+                for (int e = 0; e < n * n; ++e) G[e] = 0.0;
+                for (int p = 0; p < n; ++p)
+                    for (int64_t q = arp[rows[p]]; q < arp[rows[p] + 1]; ++q)
+                        for (int t = 0; t < n; ++t)
+                            if (aci[q] == rows[t]) G[p * n + t] += at[q];
+                gproject_spd(n, Lt, G, scr);
+            }
+        }
         __syncwarp();
         for (int t = lane; t < u; t += 32)
             for (int p = 0; p < n; ++p) {
@@ -821,6 +963,48 @@ __global__ void k_gsetup_copy(int ncp, const int *__restrict__ cp, const int *__
         if (E.ident[b]) continue;
         const int64_t cnt = (int64_t)(bptr[b + 1] - bptr[b]) * E.u[b];
         for (int64_t e = lane; e < cnt; e += 32) nvals[nvoff[b] + e] = E.vals[E.voff[b] + e];
+    }
+}
+
+// Overlapping blocks, node rows after a step (Sec. 3.6.2): node i's new row
+// sums, in ascending block order over the union of their columns, the rows
+// fptr[i] .. fptr[i+1] of the updated blocks holding it (block fblk, row
+// floc, block-row storage B), divided by their count when average is set
+// (the additive form: diag(theta)^{-1} Theta^T); a node no updated block
+// holds keeps its row of E.  One warp per node.
+__global__ void k_gfuse(int N, const int *__restrict__ fptr, const int *__restrict__ fblk,
+                        const int *__restrict__ floc, GEView B, GEView E, const int64_t *__restrict__ ncoff,
+                        const int64_t *__restrict__ nvoff, const int *__restrict__ nu,
+                        const int *__restrict__ ncols, double *__restrict__ nvals, int average) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < N; i += nw) {
+        const int c0 = fptr[i], c1 = fptr[i + 1], uo = nu[i];
+        double *out = nvals + nvoff[i];
+        if (c0 == c1) {
+            if (!E.ident[i])
+                for (int t = lane; t < uo; t += 32) out[t] = E.vals[E.voff[i] + t];
+            continue;
+        }
+        const int *Uo = ncols + ncoff[i];
+        for (int t = lane; t < uo; t += 32) out[t] = 0.0;
+        __syncwarp();
+        for (int c = c0; c < c1; ++c) {
+            const int b = fblk[c], ub = B.u[b];
+            const int *Ub = B.cols + B.coff[b];
+            const double *src = B.vals + B.voff[b] + (int64_t)floc[c] * ub;
+            for (int t = lane; t < ub; t += 32) {
+                const int64_t pos = gfind(Uo, 0, uo, Ub[t]);
+                out[pos] = __dadd_rn(out[pos], src[t]);
+            }
+            __syncwarp();
+        }
+        if (average) {
+            const double th = (double)(c1 - c0);
+            for (int t = lane; t < uo; t += 32) out[t] = out[t] / th;
+        }
+        __syncwarp();
     }
 }
 
@@ -863,36 +1047,69 @@ static cs_status gehost_upload(GEHost &E, cudaStream_t s) {
     return CS_OK;
 }
 
-static cs_status gsetup_level(const cs_ghier *h, int l, int kind, int nu, int prescale, double *lam,
+// Column pattern of block b's new rows: the union of the columns of its rows
+// of A~ E and of its own rows of E, ascending.
+static void gblock_pattern(const GLevel &L, int b, const GEHost &E, const std::vector<int> &grp,
+                           std::vector<int> &mark, int stamp, std::vector<int> &row) {
+    row.clear();
+    auto add = [&](int c) { if (mark[c] != stamp) { mark[c] = stamp; row.push_back(c); } };
+    auto add_row = [&](int j) {
+        const int g = grp[j];
+        if (E.ident[g]) add(j);
+        else for (int t = 0; t < E.u[g]; ++t) add(E.cols[E.coff[g] + t]);
+    };
+    for (int p = L.hbptr[b]; p < L.hbptr[b + 1]; ++p) {
+        const int r = L.hbidx[p];
+        for (int64_t q = L.A.hrp[r]; q < L.A.hrp[r + 1]; ++q) add_row(L.A.hci[q]);
+        add_row(r);
+    }
+    std::sort(row.begin(), row.end());
+}
+
+static cs_status gsetup_level(const cs_ghier *h, int l, int kind, int nu, int prescale, int spd, double *lam,
                               const int64_t *dlamoff, int64_t lamsize, cudaStream_t s) {
     const GLevel &L = h->lev[l];
     const int N = L.A.n, nb = L.nb;
-    std::vector<int> blk((size_t)N), loc((size_t)N);
-    for (int b = 0; b < nb; ++b)
-        for (int p = L.hbptr[b]; p < L.hbptr[b + 1]; ++p) { blk[L.hbidx[p]] = b; loc[L.hbidx[p]] = p - L.hbptr[b]; }
-    double *w = nullptr, *at = nullptr, *R = nullptr;
-    int *dblk = nullptr, *dloc = nullptr, *bad = nullptr, *dlist = nullptr;
+    const bool over = L.overlap != 0;
+    const int ng = over ? N : nb;  // row groups of E: the blocks, or the nodes when blocks overlap
+    std::vector<int> grp((size_t)N), gloc((size_t)N, 0);
+    if (over) {
+        for (int i = 0; i < N; ++i) grp[i] = i;
+    } else {
+        for (int b = 0; b < nb; ++b)
+            for (int p = L.hbptr[b]; p < L.hbptr[b + 1]; ++p) { grp[L.hbidx[p]] = b; gloc[L.hbidx[p]] = p - L.hbptr[b]; }
+    }
+    double *w = nullptr, *at = nullptr, *R = nullptr, *scr = nullptr;
+    int *dgrp = nullptr, *dgloc = nullptr, *bad = nullptr, *dlist = nullptr;
+    int *dfp = nullptr, *dfb = nullptr, *dfl = nullptr;
     int badh = 0;
-    GEHost E, En;
+    GEHost E, En, B;
     cs_status rc = CS_OK;
     std::vector<int> mark((size_t)N, -1), row;
     int stamp = 0;
     const int ncol = kind == CS_MULTIPLICATIVE ? L.ncol : 1;
+    const unsigned spd_grid = 152 * 4;
     if ((rc = dalloc_t(&w, (size_t)N, nullptr, s)) != CS_OK) goto done;
     if ((rc = dalloc_t(&at, (size_t)std::max<int64_t>(L.A.nnz, 1), nullptr, s)) != CS_OK) goto done;
-    if ((rc = dalloc_t(&dblk, (size_t)N, nullptr, s)) != CS_OK) goto done;
-    if ((rc = dalloc_t(&dloc, (size_t)N, nullptr, s)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&dgrp, (size_t)N, nullptr, s)) != CS_OK) goto done;
+    if ((rc = dalloc_t(&dgloc, (size_t)N, nullptr, s)) != CS_OK) goto done;
     if ((rc = dalloc_t(&bad, 1, nullptr, s)) != CS_OK) goto done;
     if ((rc = dalloc_t(&dlist, (size_t)nb, nullptr, s)) != CS_OK) goto done;
+    if (spd && (rc = dalloc_t(&scr, (size_t)spd_grid * GSETUP_WARPS * GSPD_SCR, nullptr, s)) != CS_OK) goto done;
+    if (over) {
+        if ((rc = dalloc_t(&dfp, (size_t)N + 1, nullptr, s)) != CS_OK) goto done;
+        if ((rc = dalloc_t(&dfb, L.hnblk.size(), nullptr, s)) != CS_OK) goto done;
+        if ((rc = dalloc_t(&dfl, L.hnloc.size(), nullptr, s)) != CS_OK) goto done;
+    }
     CSX_CUDA_GOTO(cudaMemsetAsync(bad, 0, sizeof(int), s));
-    CSX_CUDA_GOTO(cudaMemcpyAsync(dblk, blk.data(), sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, s));
-    CSX_CUDA_GOTO(cudaMemcpyAsync(dloc, loc.data(), sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, s));
+    CSX_CUDA_GOTO(cudaMemcpyAsync(dgrp, grp.data(), sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, s));
+    CSX_CUDA_GOTO(cudaMemcpyAsync(dgloc, gloc.data(), sizeof(int) * (size_t)N, cudaMemcpyHostToDevice, s));
     CSX_CUDA_GOTO(cudaMemsetAsync(lam, 0, sizeof(double) * (size_t)nu * lamsize, s));
     for (int pass = 0; pass < 2; ++pass)
         k_gprescale<<<std::max(1, std::min(1216, (N + 255) / 256)), 256, 0, s>>>(N, L.A.rp, L.A.ci, L.A.v, L.field,
                                                                                    prescale, pass, w, bad);
     k_gscale_op<<<std::max(1, std::min(1216, (N + 255) / 256)), 256, 0, s>>>(N, L.A.rp, L.A.ci, L.A.v, w, at);
-    count_launch(2);
+    count_launch(3);
     CSX_CUDA_GOTO(cudaGetLastError());
     CSX_CUDA_GOTO(cudaMemcpyAsync(&badh, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     CSX_CUDA_GOTO(cudaStreamSynchronize(s));
@@ -902,10 +1119,10 @@ static cs_status gsetup_level(const cs_ghier *h, int l, int kind, int nu, int pr
         goto done;
     }
     // E_0 = I: identity rows, no storage
-    E.u.assign((size_t)nb, 0);
-    E.coff.assign((size_t)nb, 0);
-    E.voff.assign((size_t)nb, 0);
-    E.ident.assign((size_t)nb, 1);
+    E.u.assign((size_t)ng, 0);
+    E.coff.assign((size_t)ng, 0);
+    E.voff.assign((size_t)ng, 0);
+    E.ident.assign((size_t)ng, 1);
     if ((rc = gehost_upload(E, s)) != CS_OK) goto done;
     for (int step = 0; step < nu; ++step)
         for (int k = 0; k < ncol; ++k) {
@@ -915,67 +1132,110 @@ static cs_status gsetup_level(const cs_ghier *h, int l, int kind, int nu, int pr
                 upd[b] = kind != CS_MULTIPLICATIVE || L.hcol[b] == k;
                 (upd[b] ? ulist : clist).push_back(b);
             }
-            // the new patterns: updated blocks take the union of the columns of
-            // their rows of A~ E and of E; the others keep theirs
-            En.u.assign((size_t)nb, 0);
-            En.coff.assign((size_t)nb, 0);
-            En.voff.assign((size_t)nb, 0);
-            En.ident.assign((size_t)nb, 0);
-            En.cols.clear();
-            En.nvals = 0;
+            // the updated blocks' new rows in block-row storage: the new E
+            // itself for a partition (the other blocks keep their rows), a
+            // staging pool fused into node rows when blocks overlap
+            GEHost &P = over ? B : En;
+            P.u.assign((size_t)nb, 0);
+            P.coff.assign((size_t)nb, 0);
+            P.voff.assign((size_t)nb, 0);
+            P.ident.assign((size_t)nb, 0);
+            P.cols.clear();
+            P.nvals = 0;
             for (int b = 0; b < nb; ++b) {
                 const int n = L.hbptr[b + 1] - L.hbptr[b];
-                En.coff[b] = (int64_t)En.cols.size();
-                En.voff[b] = En.nvals;
-                if (!upd[b]) {
-                    En.ident[b] = E.ident[b];
-                    En.u[b] = E.u[b];
-                    En.cols.insert(En.cols.end(), E.cols.begin() + E.coff[b], E.cols.begin() + E.coff[b] + E.u[b]);
-                } else {
+                P.coff[b] = (int64_t)P.cols.size();
+                P.voff[b] = P.nvals;
+                if (upd[b]) {
+                    gblock_pattern(L, b, E, grp, mark, ++stamp, row);
+                    P.u[b] = (int)row.size();
+                    P.cols.insert(P.cols.end(), row.begin(), row.end());
+                } else if (!over) {
+                    P.ident[b] = E.ident[b];
+                    P.u[b] = E.u[b];
+                    P.cols.insert(P.cols.end(), E.cols.begin() + E.coff[b], E.cols.begin() + E.coff[b] + E.u[b]);
+                }
+                P.nvals += (int64_t)n * P.u[b];
+            }
+            if ((rc = gehost_upload(P, s)) != CS_OK) goto done;
+            std::vector<int> fp, fb, fl;
+            if (over) {  // node rows: the union of the patterns of the updated blocks holding the node
+                fp.assign((size_t)N + 1, 0);
+                En.u.assign((size_t)N, 0);
+                En.coff.assign((size_t)N, 0);
+                En.voff.assign((size_t)N, 0);
+                En.ident.assign((size_t)N, 0);
+                En.cols.clear();
+                En.nvals = 0;
+                for (int i = 0; i < N; ++i) {
                     ++stamp;
                     row.clear();
-                    auto add = [&](int c) { if (mark[c] != stamp) { mark[c] = stamp; row.push_back(c); } };
-                    for (int p = L.hbptr[b]; p < L.hbptr[b + 1]; ++p) {
-                        const int r = L.hbidx[p];
-                        for (int64_t q = L.A.hrp[r]; q < L.A.hrp[r + 1]; ++q) {
-                            const int j = L.A.hci[q], c = blk[j];
-                            if (E.ident[c]) add(j);
-                            else for (int t = 0; t < E.u[c]; ++t) add(E.cols[E.coff[c] + t]);
+                    for (int u = L.hnptr[i]; u < L.hnptr[i + 1]; ++u) {
+                        const int b = L.hnblk[u];
+                        if (!upd[b]) continue;
+                        fb.push_back(b);
+                        fl.push_back(L.hnloc[u]);
+                        for (int t = 0; t < P.u[b]; ++t) {
+                            const int c = P.cols[P.coff[b] + t];
+                            if (mark[c] != stamp) { mark[c] = stamp; row.push_back(c); }
                         }
-                        if (E.ident[b]) add(r);
                     }
-                    if (!E.ident[b])
-                        for (int t = 0; t < E.u[b]; ++t) add(E.cols[E.coff[b] + t]);
-                    std::sort(row.begin(), row.end());
-                    En.u[b] = (int)row.size();
-                    En.cols.insert(En.cols.end(), row.begin(), row.end());
+                    fp[i + 1] = (int)fb.size();
+                    En.coff[i] = (int64_t)En.cols.size();
+                    En.voff[i] = En.nvals;
+                    if (fp[i + 1] == fp[i]) {
+                        En.ident[i] = E.ident[i];
+                        En.u[i] = E.u[i];
+                        En.cols.insert(En.cols.end(), E.cols.begin() + E.coff[i], E.cols.begin() + E.coff[i] + E.u[i]);
+                    } else {
+                        std::sort(row.begin(), row.end());
+                        En.u[i] = (int)row.size();
+                        En.cols.insert(En.cols.end(), row.begin(), row.end());
+                    }
+                    En.nvals += En.u[i];
                 }
-                En.nvals += (int64_t)n * En.u[b];
+                if ((rc = gehost_upload(En, s)) != CS_OK) goto done;
+                CSX_CUDA_GOTO(cudaMemcpyAsync(dfp, fp.data(), sizeof(int) * fp.size(), cudaMemcpyHostToDevice, s));
+                if (!fb.empty()) {
+                    CSX_CUDA_GOTO(cudaMemcpyAsync(dfb, fb.data(), sizeof(int) * fb.size(), cudaMemcpyHostToDevice, s));
+                    CSX_CUDA_GOTO(cudaMemcpyAsync(dfl, fl.data(), sizeof(int) * fl.size(), cudaMemcpyHostToDevice, s));
+                }
             }
-            if ((rc = gehost_upload(En, s)) != CS_OK) goto done;
-            if ((rc = dalloc_t(&R, (size_t)std::max<int64_t>(En.nvals, 1), nullptr, s)) != CS_OK) goto done;
+            if ((rc = dalloc_t(&R, (size_t)std::max<int64_t>(P.nvals, 1), nullptr, s)) != CS_OK) goto done;
             std::vector<int> lists(ulist);
             lists.insert(lists.end(), clist.begin(), clist.end());
             CSX_CUDA_GOTO(cudaMemcpyAsync(dlist, lists.data(), sizeof(int) * (size_t)nb, cudaMemcpyHostToDevice, s));
-            if (!ulist.empty())
-                k_gsetup_step<<<gwarp_blocks((int64_t)ulist.size()) * 2, 32 * GSETUP_WARPS, 0, s>>>(
-                    (int)ulist.size(), dlist, L.bptr, L.bidx, dblk, dloc, L.A.rp, L.A.ci, at, E.view(), En.dcoff,
-                    En.dvoff, En.du, En.dcols, En.dvals, R, dlamoff, w, lam + (int64_t)step * lamsize);
-            if (!clist.empty())
+            if (!ulist.empty()) {
+                const unsigned grid = spd ? std::min(gwarp_blocks((int64_t)ulist.size()) * 2, spd_grid)
+                                          : gwarp_blocks((int64_t)ulist.size()) * 2;
+                k_gsetup_step<<<grid, 32 * GSETUP_WARPS, 0, s>>>(
+                    (int)ulist.size(), dlist, L.bptr, L.bidx, dgrp, dgloc, L.A.rp, L.A.ci, at, E.view(), P.dcoff,
+                    P.dvoff, P.du, P.dcols, P.dvals, R, dlamoff, w, lam + (int64_t)step * lamsize, scr);
+                count_launch();
+            }
+            if (over) {
+                k_gfuse<<<gwarp_blocks(N), 256, 0, s>>>(N, dfp, dfb, dfl, P.view(), E.view(), En.dcoff, En.dvoff,
+                                                         En.du, En.dcols, En.dvals, kind == CS_ADDITIVE ? 1 : 0);
+                count_launch();
+            } else if (!clist.empty()) {
                 k_gsetup_copy<<<gwarp_blocks((int64_t)clist.size()), 256, 0, s>>>(
                     (int)clist.size(), dlist + ulist.size(), L.bptr, E.view(), En.dvoff, En.dvals);
-            count_launch(2);
+                count_launch();
+            }
             CSX_CUDA_GOTO(cudaGetLastError());
             CSX_CUDA_GOTO(cudaStreamSynchronize(s));
             dfree(R, s);
             R = nullptr;
+            B.release(s);
             E.release(s);
             std::swap(E, En);
         }
 done:
     E.release(s);
     En.release(s);
-    dfree(R, s); dfree(w, s); dfree(at, s); dfree(dblk, s); dfree(dloc, s); dfree(bad, s); dfree(dlist, s);
+    B.release(s);
+    dfree(R, s); dfree(w, s); dfree(at, s); dfree(dgrp, s); dfree(dgloc, s); dfree(bad, s); dfree(dlist, s);
+    dfree(scr, s); dfree(dfp, s); dfree(dfb, s); dfree(dfl, s);
     return rc;
 }
 
@@ -988,16 +1248,18 @@ void cs_gdestroy_cascade(cs_gcascade *c) {
     cudaDeviceSynchronize();
     for (double *p : c->lam) dfree(p);
     for (int64_t *p : c->lamoff) dfree(p);
-    dfree(c->gm_V); dfree(c->gm_Z); dfree(c->gm_h);
+    dfree(c->gm_V); dfree(c->gm_Z); dfree(c->gm_h); dfree(c->cg);
     delete c;
 }
 
-cs_status cs_gsetup_cascade(cs_ghier *h, int kind, int nu, int prescale, cs_stream stream, cs_gcascade **out) {
+cs_status cs_gsetup_cascade(cs_ghier *h, int kind, int nu, int prescale, int spd, cs_stream stream,
+                            cs_gcascade **out) {
     if (!h || !out) { set_error("null argument"); return CS_ERR_ARG; }
     *out = nullptr;
     if (kind != CS_ADDITIVE && kind != CS_MULTIPLICATIVE) { set_error("bad cascade kind"); return CS_ERR_ARG; }
     if (nu < 1 || nu > 8) { set_error("nu must be in 1..8"); return CS_ERR_ARG; }
     if (prescale < CS_PRESCALE_NONE || prescale > CS_PRESCALE_STOKES_LINF) { set_error("bad prescaling mode"); return CS_ERR_ARG; }
+    if (spd != 0 && spd != 1) { set_error("spd must be 0 or 1"); return CS_ERR_ARG; }
     if (prescale >= CS_PRESCALE_STOKES_L1 && h->lev[0].hfield.empty()) {
         set_error("Stokes prescaling needs the fields of the unknowns");
         return CS_ERR_ARG;
@@ -1029,7 +1291,7 @@ cs_status cs_gsetup_cascade(cs_ghier *h, int kind, int nu, int prescale, cs_stre
             rc = cuda_fail(cudaGetLastError(), "copy block offsets", __FILE__, __LINE__);
             break;
         }
-        rc = gsetup_level(h, l, kind, nu, prescale, c->lam[l], c->lamoff[l], c->lamsize[l], s);
+        rc = gsetup_level(h, l, kind, nu, prescale, spd, c->lam[l], c->lamoff[l], c->lamsize[l], s);
     }
     if (rc != CS_OK) {
         cudaStreamSynchronize(s);
@@ -1106,6 +1368,51 @@ __global__ void k_gsweep_block(int n, const int *__restrict__ sel, const int *__
     }
 }
 
+// Overlapping additive blocks (Sec. 3.6.2), first half: d_(b,p) =
+// sum_q Lambda_b[p][q] r_(rows_b[q]) (Lambda^T with transpose) for every
+// block, r = A x - b given; one warp per block, lane p for row p.
+__global__ void k_gblock_corr(int nb, const int *__restrict__ bptr, const int *__restrict__ bidx,
+                              const double *__restrict__ lam, const int64_t *__restrict__ lamoff,
+                              const double *__restrict__ r, double *__restrict__ d, int transpose) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = w0; b < nb; b += nw) {
+        const int b0 = bptr[b], nbk = bptr[b + 1] - b0;
+        const double *Lb = lam + lamoff[b];
+        const double rl = lane < nbk ? r[bidx[b0 + lane]] : 0.0;
+        double acc = 0.0;
+        for (int q = 0; q < nbk; ++q) {
+            const double rq = __shfl_sync(0xffffffffu, rl, q);
+            if (lane < nbk) acc = fma(transpose ? Lb[q * nbk + lane] : Lb[lane * nbk + q], rq, acc);
+        }
+        if (lane < nbk) d[b0 + lane] = acc;
+    }
+}
+// second half: out_i = x_i - (sum over the blocks holding i of d) / theta_i
+__global__ void k_gnode_avg(int N, const int *__restrict__ nptr, const int *__restrict__ nblk,
+                            const int *__restrict__ nloc, const int *__restrict__ bptr, const double *__restrict__ d,
+                            const double *__restrict__ x, double *__restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        double sacc = 0.0;
+        for (int u = nptr[i]; u < nptr[i + 1]; ++u) sacc += d[bptr[nblk[u]] + nloc[u]];
+        out[i] = x[i] - sacc / (double)(nptr[i + 1] - nptr[i]);
+    }
+}
+
+// PCG vector updates: x += alpha p, r -= alpha q; and p = z + beta p
+__global__ void k_gcg_update(int64_t n, double alpha, const double *__restrict__ p, const double *__restrict__ q,
+                             double *__restrict__ x, double *__restrict__ r) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] = fma(alpha, p[i], x[i]);
+        r[i] = fma(-alpha, q[i], r[i]);
+    }
+}
+__global__ void k_gcg_dir(int64_t n, double beta, const double *__restrict__ z, double *__restrict__ p) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = fma(beta, p[i], z[i]);
+}
+
 // r = A x - b (sign = 1) or b - A x (sign = -1)
 __global__ void k_gresid(int n, const int64_t *__restrict__ rp, const int *__restrict__ ci,
                          const double *__restrict__ v, const double *__restrict__ bv, const double *__restrict__ x,
@@ -1151,6 +1458,15 @@ static cs_status gstep(const cs_ghier *h, const cs_gcascade *c, int l, int step,
         if (out != x) CSX_CUDA(cudaMemcpyAsync(out, x, sizeof(double) * L.A.n, cudaMemcpyDeviceToDevice, s));
     }
     if (n == 0) return CS_OK;
+    if (L.overlap && c->kind == CS_ADDITIVE) {  // x - diag(theta)^{-1} Theta^T Lambda Theta (A x - b)
+        k_gresid<<<grows(L.A.n), 256, 0, s>>>(L.A.n, L.A.rp, L.A.ci, L.A.v, b, x, L.r, 1.0);
+        k_gblock_corr<<<gwarp_blocks(L.nb), 256, 0, s>>>(L.nb, L.bptr, L.bidx, lam, c->lamoff[l], L.r, L.dpool,
+                                                          transpose ? 1 : 0);
+        k_gnode_avg<<<grows(L.A.n), 256, 0, s>>>(L.A.n, L.nptr, L.nblk, L.nloc, L.bptr, L.dpool, x, out);
+        count_launch(3);
+        CSX_CUDA(cudaGetLastError());
+        return CS_OK;
+    }
     if (L.nbmax == 1)
         k_gsweep_point<<<grows(n), 256, 0, s>>>(n, sel, L.bptr, L.bidx, L.A.rp, L.A.ci, L.A.v, lam, c->lamoff[l], b,
                                                  x, out, L.ident);
@@ -1214,6 +1530,14 @@ static cs_status gcheck(const cs_ghier *h, const cs_gcascade *c, int level) {
     return CS_OK;
 }
 
+static cs_status gdot(const cs_ghier *h, int64_t n, const double *a, const double *b, double *out, cudaStream_t s) {
+    CSX_TRY(launch_dot(n, a, b, h->red, NRED, s));
+    CSX_CUDA(cudaMemcpyAsync(h->red_host, h->red + NRED, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CSX_CUDA(cudaStreamSynchronize(s));
+    *out = h->red_host[0];
+    return CS_OK;
+}
+
 static cs_status gnorm(const cs_ghier *h, int64_t n, const double *a, double *out, cudaStream_t s) {
     CSX_TRY(launch_dot(n, a, a, h->red, NRED, s));
     CSX_CUDA(cudaMemcpyAsync(h->red_host, h->red + NRED, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1256,10 +1580,12 @@ cs_status cs_gvcycle(const cs_ghier *h, cs_gcascade *c, const cs_vcycle_opts *o,
     return gvcycle_rec(h, c, 0, *o, b, x, (cudaStream_t)stream);
 }
 
-// Stationary x <- V(x, b), or right-preconditioned restarted GMRES in its
+// Stationary x <- V(x, b); right-preconditioned restarted GMRES in its
 // flexible form (Z_j = V0 v_j kept, x += Z y; modified Gram-Schmidt,
-// Givens rotations; the Hessenberg problem on the host); both stop on the
-// true relative residual.
+// Givens rotations; the Hessenberg problem on the host); or preconditioned
+// conjugate gradients with M = V(0, .) (SM "On preconditioned conjugate
+// gradient"), stopping on the recurrence residual and reporting the true
+// one.
 cs_status cs_gsolve(const cs_ghier *h, cs_gcascade *c, const cs_solve_opts *o_in, const double *b, double *x,
                     cs_solve_info *info, cs_stream stream) {
     CSX_TRY(gcheck(h, c, 0));
@@ -1268,8 +1594,8 @@ cs_status cs_gsolve(const cs_ghier *h, cs_gcascade *c, const cs_solve_opts *o_in
     if (o.maxit <= 0) o.maxit = 100;
     if (o.tol <= 0) o.tol = 1e-10;
     if (o.restart <= 0) o.restart = 30;
-    if (o.method != CS_STATIONARY && o.method != CS_GMRES_RIGHT) {
-        set_error("the general path solves with CS_STATIONARY or CS_GMRES_RIGHT");
+    if (o.method != CS_STATIONARY && o.method != CS_GMRES_RIGHT && o.method != CS_PCG) {
+        set_error("the general path solves with CS_STATIONARY, CS_GMRES_RIGHT or CS_PCG");
         return CS_ERR_ARG;
     }
     if (o.cycle.precision != CS_FP64 || o.host_buffers) { set_error("the general path takes FP64 device vectors"); return CS_ERR_ARG; }
@@ -1296,7 +1622,46 @@ cs_status cs_gsolve(const cs_ghier *h, cs_gcascade *c, const cs_solve_opts *o_in
         rel = nr / nb;
         return CS_OK;
     };
-    if (o.method == CS_STATIONARY) {
+    if (o.method == CS_PCG) {
+        if (!c->cg) CSX_TRY(dalloc_t(&c->cg, (size_t)4 * N, &c->bytes, s));
+        double *r = c->cg, *z = r + N, *p = z + N, *q = p + N;
+        const unsigned g = grows(N);
+        double rz = 0.0, pq = 0.0;
+        CSX_TRY(residual(r));
+        const double rel0 = rel;
+        if (o.hist && inf.nhist < o.hist_cap) o.hist[inf.nhist++] = rel;
+        CSX_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * N, s));
+        CSX_TRY(gvcycle_rec(h, c, 0, o.cycle, r, z, s));
+        CSX_TRY(gdot(h, N, r, z, &rz, s));
+        CSX_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        while (rel > o.tol && inf.iterations < o.maxit) {
+            k_gspmv<<<g, 256, 0, s>>>((int)N, L.A.rp, L.A.ci, L.A.v, p, q, 0);
+            count_launch();
+            CSX_TRY(gdot(h, N, p, q, &pq, s));
+            k_gcg_update<<<g, 256, 0, s>>>(N, rz / pq, p, q, x, r);
+            count_launch();
+            CSX_CUDA(cudaGetLastError());
+            ++inf.iterations;
+            double nr = 0.0;
+            CSX_TRY(gnorm(h, N, r, &nr, s));
+            rel = nr / nb;
+            if (o.hist && inf.nhist < o.hist_cap) o.hist[inf.nhist++] = rel;
+            if (!std::isfinite(rel) || rel > 1e3 * std::max(rel0, 1.0)) {
+                set_error("PCG diverged (relative residual %g)", rel);
+                rc = CS_ERR_DIVERGED;
+                break;
+            }
+            if (!(rel > o.tol)) break;
+            CSX_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * N, s));
+            CSX_TRY(gvcycle_rec(h, c, 0, o.cycle, r, z, s));
+            double rz1 = 0.0;
+            CSX_TRY(gdot(h, N, r, z, &rz1, s));
+            k_gcg_dir<<<g, 256, 0, s>>>(N, rz1 / rz, z, p);
+            count_launch();
+            rz = rz1;
+        }
+        if (rc == CS_OK) CSX_TRY(residual(L.r));  // the true residual decides
+    } else if (o.method == CS_STATIONARY) {
         CSX_TRY(residual(L.r));
         const double rel0 = rel;
         if (o.hist && inf.nhist < o.hist_cap) o.hist[inf.nhist++] = rel;
