@@ -64,6 +64,9 @@ def args_():
                    help="GMRES restart of the interface workload (the oracle needs 149 steps at 1023^2 without restart)")
     p.add_argument("--general-n", type=int, default=1535, help="interior nodes per side of the general-path mesh")
     p.add_argument("--stokes-n", type=int, default=256, help="cells per side of the MAC Stokes problem")
+    p.add_argument("--overlap-n", type=int, default=767, help="interior nodes per side of the overlapping-block mesh")
+    p.add_argument("--overlap-mult-n", type=int, default=255,
+                   help="mesh of the multiplicative overlapping-block line (its exact setup fills E along colour chains)")
     p.add_argument("--batch-count", type=int, default=512, help="problems of the batched workload timed")
     p.add_argument("--batch-fp64-count", type=int, default=32,
                    help="problems on which FP32 and FP64 cycles are compared")
@@ -73,7 +76,8 @@ def args_():
     p.add_argument("--batch-single", type=int, default=4, help="problems also solved on the single-problem path")
     p.add_argument("--batch-profile-count", type=int, default=16, help="problems in the batch profile case")
     p.add_argument("--profile", default="",
-                   choices=["", "setup", "step", "step16", "sweep", "multirhs", "blocksetup", "batch"],
+                   choices=["", "setup", "step", "step16", "sweep", "multirhs", "blocksetup", "batch", "general",
+                            "overlap", "sketch"],
                    help="run one untimed setup (or setup + solve) and exit: the case ncu captures")
     return p.parse_args()
 
@@ -633,6 +637,55 @@ def stokes_section(a, cmg, problems, dev):
     return out
 
 
+def overlap_section(a, cmg, problems, dev):
+    """Overlapping blocks (Sec. 3.6.2) and PCG (SM "On preconditioned
+    conjugate gradient") on the jittered Q1 mesh of --overlap-n interior
+    nodes per side: the nodes of every element form a block (an interior
+    node lies in 4), additive nu = 2 with theta-averaged fusion and right
+    GMRES, the same with the SPD projection and PCG, and the multiplicative
+    form (colours separate blocks sharing a node) with right GMRES on the
+    smaller --overlap-mult-n mesh (its 19 colours let a node's row of E grow
+    along chains of colour steps, so its exact setup costs far more than the
+    additive one); all V(1,1) RF to 1e-10."""
+    import torch
+    t0 = time.perf_counter()
+    u = problems.unstructured_q1(a.overlap_n, 7, renumber=False)
+    t_gen = time.perf_counter() - t0
+    s = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hg = cmg.gsetup_hierarchy(u["A"], u["Ps"], rscale=0.25, blocks=u["cells"], seed=3)
+    t_h = time.perf_counter() - t0
+    N = u["A"].shape[0]
+    bd = torch.tensor(problems.rhs(N, 5), dtype=torch.float64, device=dev)
+    out = {"workload": f"jittered Q1 {a.overlap_n}^2 interior nodes ({N} unknowns), element blocks of up to 4 "
+                       f"nodes overlapping ({hg.level(0)['nblocks']} blocks), Galerkin levels, V(1,1) RF to 1e-10",
+           "generate_s": t_gen, "hierarchy_s": t_h, "levels": hg.nlevels, "colours_level0": hg.level(0)["ncolours"]}
+    um = problems.unstructured_q1(a.overlap_mult_n, 7, renumber=False)
+    hm = cmg.gsetup_hierarchy(um["A"], um["Ps"], rscale=0.25, blocks=um["cells"], seed=3)
+    bm = torch.tensor(problems.rhs(um["A"].shape[0], 5), dtype=torch.float64, device=dev)
+    for name, kind, spd, method in (("additive_nu2_gmres_right", "additive", False, "gmres_right"),
+                                    ("additive_nu2_spd_pcg", "additive", True, "pcg"),
+                                    (f"multiplicative_nu2_gmres_right_{a.overlap_mult_n}", "multiplicative", False,
+                                     "gmres_right")):
+        if kind == "multiplicative":
+            hg, bd, N = hm, bm, um["A"].shape[0]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        ev[0].record(s)
+        cg = cmg.gsetup_cascade(hg, kind, nu=2, spd=spd)
+        ev[1].record(s)
+        x = torch.zeros(N, dtype=torch.float64, device=dev)
+        info = cmg.gsolve(hg, cg, bd, x, method=method, tol=1e-10, maxit=300, raise_on_error=False)
+        ev[2].record(s)
+        torch.cuda.synchronize()
+        out[name] = {"unknowns": N, "cascade_ms": ev[0].elapsed_time(ev[1]), "solve_ms": ev[1].elapsed_time(ev[2]),
+                     "iterations": info.iterations, "converged": bool(info.converged),
+                     "final_rel_residual": float(info.final_rel_residual)}
+        del cg
+    return out
+
+
 # ------------------------------------------------------------------- ours
 def main():
     a = args_()
@@ -683,6 +736,29 @@ def main():
         bt.solve(bs, xs, tol=1e-300, maxit=3, raise_on_error=False)
         torch.cuda.synchronize()
         print(json.dumps({"profile": a.profile, "problems": len(P), "launches": cmg.kernel_launches()}), flush=True)
+        return
+
+    if a.profile in ("general", "overlap"):  # general-path setup and five additive steps on a jittered Q1 mesh
+        nq = a.general_n if a.profile == "general" else a.overlap_n
+        u = problems.unstructured_q1(nq, 7, renumber=False)
+        hg = cmg.gsetup_hierarchy(u["A"], u["Ps"], rscale=0.25, blocks=u["cells"] if a.profile == "overlap" else None,
+                                  seed=3)
+        cg = cmg.gsetup_cascade(hg, "additive", nu=2)
+        N = hg.N(0)
+        bg = torch.rand(N, dtype=torch.float64, device=dev)
+        xg = [torch.rand(N, dtype=torch.float64, device=dev) for _ in range(2)]
+        for k in range(5):
+            cmg.gsweep(hg, cg, 0, k % 2, bg, xg[k % 2], xg[(k + 1) % 2])
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": a.profile, "n": nq, "launches": cmg.kernel_launches()}), flush=True)
+        return
+
+    if a.profile == "sketch":  # the sketched multiplicative setup (s = 32 columns) on the 3D Poisson problem
+        As, _ = problems.poisson3d(a.n)
+        hs = cmg.setup_hierarchy(As.dim, As.n, As.offsets, torch.tensor(As.coeff, dtype=torch.float64, device=dev))
+        cmg.setup_cascade(hs, "multiplicative", nu=a.nu, sketch=32, sketch_seed=2024, setup_precision="fp32")
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": a.profile, "n": a.n, "launches": cmg.kernel_launches()}), flush=True)
         return
 
     if a.profile == "blocksetup":  # the exact 3x3-block setup of the learned-setup workload (Q1, n^2)
@@ -899,6 +975,8 @@ def main():
         result["general_path"] = general_section(a, cmg, problems, dev)
         torch.cuda.empty_cache()
         result["stokes_prescaling"] = stokes_section(a, cmg, problems, dev)
+        torch.cuda.empty_cache()
+        result["overlapping_blocks"] = overlap_section(a, cmg, problems, dev)
         torch.cuda.empty_cache()
         # ---- plain FP64 path (stationary V-cycle iteration)
         pinfo = []
