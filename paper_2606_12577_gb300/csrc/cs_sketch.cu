@@ -98,16 +98,20 @@ __global__ void __launch_bounds__(256) k_sketch_step(Grid g, int nst, SkOff off,
                 if (t < s) z[u] = fma(a, Y[j * s + t], z[u]);
             }
         }
-        double gz = 0.0, cz = 0.0;
+        // <Z, Z> and <Y, Z>: each lane's columns in T, the lanes combined in
+        // FP64; with FP32 vectors the products and the update stay off the
+        // FP64 pipe (GB300 issues FP64 at a small fraction of the FP32 rate)
+        T gl = T(0), cl = T(0);
 #pragma unroll
         for (int u = 0; u < SPL; ++u) {
             const int t = lane + 32 * u;
             if (t < s) {
-                const double zd = (double)z[u], yd = (double)Y[i * s + t];
-                gz = fma(zd, zd, gz);
-                cz = fma(yd, zd, cz);
+                const T yv = Y[i * s + t];
+                gl = fma(z[u], z[u], gl);
+                cl = fma(yv, z[u], cl);
             }
         }
+        double gz = (double)gl, cz = (double)cl;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             gz += __shfl_xor_sync(0xffffffffu, gz, o);
@@ -115,10 +119,11 @@ __global__ void __launch_bounds__(256) k_sketch_step(Grid g, int nst, SkOff off,
         }
         const double G = exact ? rowsq : gz, C = exact ? aii : cz;
         const double lt = G > 0.0 ? C / G : 0.0;
+        const T ltt = (T)lt;
 #pragma unroll
         for (int u = 0; u < SPL; ++u) {
             const int t = lane + 32 * u;
-            if (t < s) Yn[i * s + t] = (T)((double)Y[i * s + t] - lt * (double)z[u]);
+            if (t < s) Yn[i * s + t] = fma(-ltt, z[u], Y[i * s + t]);
         }
         if (lane == 0) lam[i] = wi * lt * wi;
     }
