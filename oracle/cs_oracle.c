@@ -14,8 +14,18 @@
  *     eq. (fwdar) / (fwdmr) read as Lambda_{nu-l+1}^T (and colour chi-k+1),
  *     the order fixed by the reverse propagator of SM Sec. 3
  *   - V-cycle ......................... Algorithm 1
- *   - Galerkin coarse operator A_2h = R A_h P with R = 2^{-d} P^T (SM 4.1)
- *   - left-preconditioned GMRES driver .. Sec. 3.1
+ *   - Galerkin coarse operator A_2h = R A_h P with R = 2^{-d} P^T (SM 4.1),
+ *     or rscale P^T A P for a user CSR hierarchy with user blocks
+ *   - coarsest direct solve: Cholesky for a symmetric matrix, LU with
+ *     partial pivoting otherwise (Algorithm 1)
+ *   - outer solves: stationary, left-preconditioned GMRES (Sec. 3.1), the
+ *     same with the cycle on the right (flexible form), and PCG (SM "On
+ *     preconditioned conjugate gradient")
+ *   - greedy colouring of the block graph in hash-priority order (Sec. 3.4)
+ *   - sketched setup min ||(E - Lambda R) S||_F, Rademacher S (Sec. 4)
+ *   - Stokes prescaling (Sec. 2.3; SM "Prescaling Stokes problems")
+ *   - overlapping blocks with theta-averaged fusion (Sec. 3.6.2) and the
+ *     SPD projection of Lambda blocks bounded by block Jacobi (SM, PCG)
  *
  * No blocking, fusion or reordering beyond what those definitions state.
  *
