@@ -308,12 +308,21 @@ def learned_section(a, cmg, problems, dev):
         c, setup_ms, wall_ms = res[name]
         mu = 3 if name == "level1_repeated" else 1
         x = torch.zeros(A5.N, dtype=torch.float64, device=dev)
+        cmg.solve(h5, c, b5, x, method="gmres", tol=1e-10, maxit=300, mu_pre=mu, mu_post=mu,
+                  raise_on_error=False)  # warm-up (graph capture of the cycle)
+        x.zero_()
+        torch.cuda.synchronize()
+        e0.record(s)
         info = cmg.solve(h5, c, b5, x, method="gmres", tol=1e-10, maxit=300, mu_pre=mu, mu_post=mu,
                          raise_on_error=False)
+        e1.record(s)
+        torch.cuda.synchronize()
+        solve_ms = e0.elapsed_time(e1)
         x = torch.zeros(A5.N, dtype=torch.float64, device=dev)
         st = cmg.solve(h5, c, b5, x, method="stationary", tol=1e-10, maxit=40, mu_pre=mu, mu_post=mu,
                        raise_on_error=False)
-        out[name] = {"setup_ms": setup_ms, "gmres_iterations": info.iterations, "converged": info.converged,
+        out[name] = {"setup_ms": setup_ms, "gmres_solve_ms": solve_ms, "total_ms": setup_ms + solve_ms,
+                     "gmres_iterations": info.iterations, "converged": info.converged,
                      "rho_gmres": oracle.rho_from_history(info.history) if len(info.history) > 2 else None,
                      "rho_stationary": oracle.rho_from_history(st.history) if len(st.history) > 2 else None}
     return out

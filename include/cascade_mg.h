@@ -87,8 +87,11 @@ typedef struct {
  * with even 1-based index on every axis (so n -> floor(n/2)); interpolation
  * P is bilinear/trilinear on that node set and the coarse operator is the
  * Galerkin product A_2h = R A_h P with R = 2^-dim P^T (SM Sec. 4.1), a
- * 9-point (2D) / 27-point (3D) stencil.  The coarsest operator is factorised
- * densely in FP64 for the bottom-level direct solve (Algorithm 1).
+ * 9-point (2D) / 27-point (3D) stencil.  The coarsest operator, when it has
+ * at most 1024 unknowns, is factorised densely in FP64 for the bottom-level
+ * direct solve (Algorithm 1); a larger coarsest level (max_levels cutting
+ * the hierarchy short) is kept for cascade setups, and cycles on it return
+ * CS_ERR_UNSUPPORTED.
  * A0: the finest operator (its coefficients are copied).  opts may be NULL
  * (defaults).  On success *out receives a handle that cs_destroy_hierarchy
  * frees.  Errors: CS_ERR_ARG (bad stencil), CS_ERR_NOMEM, CS_ERR_SINGULAR,
@@ -417,8 +420,23 @@ cs_status cs_solve_batched(int nprob, cs_hierarchy *const *h, cs_cascade *const 
  * the fallback.  Weights are FP32 masters used in BF16 for every product,
  * with FP32 accumulation; parameters are [W1 (nhid x nin), b1, W2, b2, W3
  * (nout x nhid), b3], row-major.  max_batch: rows per forward/backward pass
- * (longer forward calls are chunked).  Weights are He-uniform from seed. */
+ * (longer forward calls are chunked).  Weights are He-uniform from seed.
+ * Every product of the forward and backward passes runs on the tensor cores
+ * (cs_tc_gemm_bf16's kernel): the BF16 weights enter as they are, FP32
+ * activations and gradients as BF16 pairs hi = bf16(x), lo = bf16(x - hi)
+ * (products of two FP32 factors as a_hi b_hi + a_lo b_hi + a_hi b_lo), so
+ * results agree with FP32 products of BF16 weights to about 2^-16.  A wait
+ * of the GEMM kernel that expires makes the next call that synchronises
+ * return CS_ERR_TIMEOUT. */
 cs_status cs_mlp_create(int nin, int nhid, int nout, int max_batch, uint64_t seed, cs_mlp **out);
+/* C[M x N] (FP32, row-major, DEVICE) = A[M x K] B[N x K]^T for DEVICE BF16
+ * matrices A and B, row-major with K contiguous, FP32 accumulation: the
+ * tcgen05 tensor-core GEMM of the learned setup (128 x 128 tiles, TMA-staged
+ * 128 x 64 operand tiles with the 128-byte swizzle, the accumulator in tensor
+ * memory).  K a multiple of 8 (16-byte rows), A and B 16-byte aligned.
+ * Synchronises the stream.  Errors: CS_ERR_ARG, CS_ERR_CUDA, CS_ERR_TIMEOUT
+ * (a bounded wait of the kernel expired; the context stays usable). */
+cs_status cs_tc_gemm_bf16(int M, int N, int K, const void *A, const void *B, float *C, cs_stream stream);
 void cs_mlp_destroy(cs_mlp *m);
 int64_t cs_mlp_nparam(const cs_mlp *m);
 cs_status cs_mlp_get_params(const cs_mlp *m, float *host_params);

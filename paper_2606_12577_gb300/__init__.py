@@ -21,7 +21,7 @@ from ._capi import CascadeError
 __all__ = ["setup_hierarchy", "setup_cascade", "vcycle", "solve", "smooth", "sweep", "sweep_rhs", "residual_restrict",
            "prolong_correct", "coarse_solve", "residual", "query_level", "export_operator", "export_colours",
            "export_lambda", "kernel_launches", "smooth_noalloc", "MLP", "block_features", "block_targets", "learned_status", "learned_stats", "setup_many", "Batch", "solve_batched", "Hierarchy", "Cascade", "SolveInfo",
-           "CascadeError", "GHierarchy", "GCascade", "gsetup_hierarchy", "gsetup_cascade", "gexport_lambda", "gsweep",
+           "CascadeError", "GHierarchy", "GCascade", "gsetup_hierarchy", "gsetup_cascade", "gexport_lambda", "tc_gemm_bf16", "gsweep",
            "gsmooth", "gvcycle", "gsolve", "residual_restrict_lowp", "prolong_correct_lowp"]
 
 
@@ -755,6 +755,23 @@ def gsetup_cascade(h, kind="additive", nu=3, prescale=True, spd=False, stream=No
     _capi.check(_capi.lib().cs_gsetup_cascade(h.ptr, k, nu, _capi.PRESCALE[prescale], int(bool(spd)),
                                               _stream(stream), C.byref(out)), "cs_gsetup_cascade")
     return GCascade(out.value, h, kind, nu)
+
+
+def tc_gemm_bf16(A, B, stream=None):
+    """C = A B^T (FP32) for CUDA bf16 tensors A [M, K] and B [N, K] (K a
+    multiple of 8, contiguous) on the tcgen05 tensor cores."""
+    import torch
+    if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16 or not A.is_cuda or not B.is_cuda:
+        raise TypeError("tc_gemm_bf16 takes CUDA bfloat16 tensors")
+    A, B = A.contiguous(), B.contiguous()
+    M, K = A.shape
+    N, K2 = B.shape
+    if K != K2:
+        raise ValueError("A and B need the same K")
+    out = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _capi.check(_capi.lib().cs_tc_gemm_bf16(M, N, K, A.data_ptr(), B.data_ptr(), out.data_ptr(), _stream(stream)),
+                "cs_tc_gemm_bf16")
+    return out
 
 
 def gexport_lambda(c, level):

@@ -102,6 +102,7 @@ _SIGS = {
     "cs_gsetup_hierarchy": (C.c_int, [C.POINTER(cs_csr), C.c_int, C.POINTER(cs_csr), C.c_double, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p,
                                       C.POINTER(C.c_void_p)]),
+    "cs_tc_gemm_bf16": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cs_gsetup_cascade": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                     C.POINTER(C.c_void_p)]),
     "cs_gsweep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,

@@ -410,7 +410,11 @@ cs_status cs_setup_hierarchy(const cs_stencil *A0, const cs_hierarchy_opts *opts
         if ((rc = dalloc_t(&h->hb, h->lev[0].g.N, &h->bytes, s)) != CS_OK) goto fail;
         if ((rc = dalloc_t(&h->hx, h->lev[0].g.N, &h->bytes, s)) != CS_OK) goto fail;
     }
-    if (!h->periodic && h->lev.back().g.N <= 4096) {
+    // the dense factorisation runs in one CTA (O(n^3) FP64 operations): up to
+    // 1024 unknowns; a larger coarsest level (a hierarchy cut short by
+    // max_levels, kept for its cascade setup) is not factorised and cycles on
+    // it report CS_ERR_UNSUPPORTED
+    if (!h->periodic && h->lev.back().g.N <= 1024) {
         if ((rc = coarse_factor(h, s)) != CS_OK) goto fail;
     }
     {

@@ -6,6 +6,8 @@
 // Network: in -> hid (ReLU) -> hid (ReLU) -> out, Y = H2 W3^T + b3.
 // Weights are kept as FP32 masters and rounded to BF16 for every product
 // (BF16 weights, FP32 accumulation); biases, activations and gradients FP32.
+// Every product runs on the tensor cores (cs_tcgemm.cu): BF16 weights enter
+// as they are, FP32 activations and gradients as BF16 hi + lo pairs along K.
 // Layout: activations row-major [batch][width]; W_l row-major [out][in].
 //
 // Features of a block of bs x bs nodes (2D): for each block node p its row
@@ -20,6 +22,7 @@
 #include <vector>
 
 #include "cs_internal.cuh"
+#include "cs_tcgemm.cuh"
 
 struct cs_mlp {
     int nin = 0, nhid = 0, nout = 0, max_batch = 0;
@@ -36,76 +39,19 @@ struct cs_mlp {
     int64_t bytes = 0;
     // offsets into p / g
     int64_t oW1, ob1, oW2, ob2, oW3, ob3, o16W1, o16W2, o16W3;
+    // tensor-core operands (K contiguous, K padded to 64 per segment): the
+    // forward pass, the input gradients, and the weight gradients (K = batch)
+    int kin = 0, khid = 0, kout = 0, kb = 0;
+    csx::TcOperand tX, tW1, tH1, tW2, tH2, tW3, tDY, tW3T, tD2, tW2T;
+    csx::TcOperand tDYT, tH2T, tD2T, tH1T, tD1T, tXT;
+    float *part = nullptr;  // split-K partials
+    int64_t part_cap = 0;
+    int *err = nullptr;     // bounded-wait expiry flag of the GEMM kernel
 };
 
 namespace csx {
 
-// ------------------------------------------------------------------ GEMM
-// C[M x N] = A_op[M x K] B_op[K x N] (+ bias[n]) (ReLU), FP32 accumulation.
-// A_op(m,k) = TA ? A[k*lda + m] : A[m*lda + k]; B_op(k,n) = TB ? B[n*ldb + k]
-// : B[k*ldb + n].  64 x 64 tile per 256-thread CTA, 4 x 4 outputs a thread.
-template <bool TA, bool TB, typename TBt>
-__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float *__restrict__ A, int lda,
-                                               const TBt *__restrict__ B, int ldb, float *__restrict__ C, int ldc,
-                                               const float *__restrict__ bias, int relu, float *__restrict__ Z) {
-    __shared__ float As[16][64 + 4];
-    __shared__ float Bs[16][64 + 4];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        for (int t = threadIdx.x; t < 16 * 64; t += 256) {
-            const int kk = t / 64, mm = t % 64;
-            const int gm = m0 + mm, gk = k0 + kk;
-            float va = 0.f;
-            if (gm < M && gk < K) va = TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
-            As[kk][mm] = va;
-            const int gn = n0 + mm;
-            float vb = 0.f;
-            if (gn < N && gk < K) vb = (float)(TB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn]);
-            Bs[kk][mm] = vb;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int gm = m0 + ty * 4 + i;
-        if (gm >= M) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int gn = n0 + tx * 4 + j;
-            if (gn >= N) continue;
-            float v = acc[i][j];
-            if (bias) v += bias[gn];
-            if (Z) Z[(int64_t)gm * ldc + gn] = v;  // pre-activation, kept for the backward pass
-            if (relu) v = fmaxf(v, 0.f);
-            C[(int64_t)gm * ldc + gn] = v;
-        }
-    }
-}
-
-template <bool TA, bool TB, typename TBt>
-static cs_status gemm(int M, int N, int K, const float *A, int lda, const TBt *B, int ldb, float *C, int ldc,
-                      const float *bias, bool relu, cudaStream_t s, float *Z = nullptr) {
-    dim3 gr((N + 63) / 64, (M + 63) / 64);
-    k_gemm<TA, TB, TBt><<<gr, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu ? 1 : 0, Z);
-    CSX_CUDA(cudaGetLastError());
-    count_launch();
-    return CS_OK;
-}
+static int64_t round64(int64_t n) { return (n + 63) / 64 * 64; }
 
 // h = relu(z) already fused; backward: d <- d * (z > 0)
 __global__ void k_relu_grad(int64_t n, const float *__restrict__ z, float *__restrict__ d) {
@@ -180,6 +126,10 @@ __global__ void k_to_bf16(int64_t n, const float *__restrict__ a, __nv_bfloat16 
         o[i] = __float2bfloat16_rn(a[i]);
 }
 
+// the BF16 weights (round to nearest even of the FP32 masters): the plain
+// copies and the tensor-core operands W_l (forward) and W_l^T (input
+// gradients), each entering two K segments so that it meets both halves of
+// the activations' hi + lo pairs
 static cs_status refresh_bf16(cs_mlp *M, cudaStream_t s) {
     const int64_t n1 = (int64_t)M->nhid * M->nin, n2 = (int64_t)M->nhid * M->nhid, n3 = (int64_t)M->nout * M->nhid;
     k_to_bf16<<<256, 256, 0, s>>>(n1, M->p + M->oW1, M->w16 + M->o16W1);
@@ -187,16 +137,38 @@ static cs_status refresh_bf16(cs_mlp *M, cudaStream_t s) {
     k_to_bf16<<<256, 256, 0, s>>>(n3, M->p + M->oW3, M->w16 + M->o16W3);
     count_launch(3);
     CSX_CUDA(cudaGetLastError());
+    CSX_TRY(tc_pack(M->tW1, M->nhid, M->nin, M->kin, "hh", M->p + M->oW1, M->nin, false, s));
+    CSX_TRY(tc_pack(M->tW2, M->nhid, M->nhid, M->khid, "hh", M->p + M->oW2, M->nhid, false, s));
+    CSX_TRY(tc_pack(M->tW3, M->nout, M->nhid, M->khid, "hh", M->p + M->oW3, M->nhid, false, s));
+    CSX_TRY(tc_pack(M->tW3T, M->nhid, M->nout, M->kout, "hh", M->p + M->oW3, M->nhid, true, s));
+    CSX_TRY(tc_pack(M->tW2T, M->nhid, M->nhid, M->khid, "hh", M->p + M->oW2, M->nhid, true, s));
+    return CS_OK;
+}
+
+static cs_status mlp_gemm(cs_mlp *M, const TcOperand &A, const TcOperand &B, int m, int n, int64_t k, float *C,
+                          int ldc, const float *bias, bool relu, float *Z, cudaStream_t s) {
+    return tc_gemm(A, B, m, n, k, C, ldc, bias, relu, Z, M->part, M->part_cap, M->err, s);
+}
+
+// the GEMM kernel's bounded waits: CS_ERR_TIMEOUT once one expired
+static cs_status mlp_check(cs_mlp *M, cudaStream_t s) {
+    int h = 0;
+    CSX_CUDA(cudaMemcpyAsync(&h, M->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CSX_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        set_error("a tensor-core GEMM wait expired");
+        return CS_ERR_TIMEOUT;
+    }
     return CS_OK;
 }
 
 static cs_status forward(cs_mlp *M, int B, const float *X, cudaStream_t s) {
-    CSX_TRY(gemm<false, true, __nv_bfloat16>(B, M->nhid, M->nin, X, M->nin, M->w16 + M->o16W1, M->nin, M->h1,
-                                             M->nhid, M->p + M->ob1, true, s, M->z1));
-    CSX_TRY(gemm<false, true, __nv_bfloat16>(B, M->nhid, M->nhid, M->h1, M->nhid, M->w16 + M->o16W2, M->nhid, M->h2,
-                                             M->nhid, M->p + M->ob2, true, s, M->z2));
-    CSX_TRY(gemm<false, true, __nv_bfloat16>(B, M->nout, M->nhid, M->h2, M->nhid, M->w16 + M->o16W3, M->nhid, M->y,
-                                             M->nout, M->p + M->ob3, false, s));
+    CSX_TRY(tc_pack(M->tX, B, M->nin, M->kin, "hl", X, M->nin, false, s));
+    CSX_TRY(mlp_gemm(M, M->tX, M->tW1, B, M->nhid, 2 * M->kin, M->h1, M->nhid, M->p + M->ob1, true, M->z1, s));
+    CSX_TRY(tc_pack(M->tH1, B, M->nhid, M->khid, "hl", M->h1, M->nhid, false, s));
+    CSX_TRY(mlp_gemm(M, M->tH1, M->tW2, B, M->nhid, 2 * M->khid, M->h2, M->nhid, M->p + M->ob2, true, M->z2, s));
+    CSX_TRY(tc_pack(M->tH2, B, M->nhid, M->khid, "hl", M->h2, M->nhid, false, s));
+    CSX_TRY(mlp_gemm(M, M->tH2, M->tW3, B, M->nout, 2 * M->khid, M->y, M->nout, M->p + M->ob3, false, nullptr, s));
     return CS_OK;
 }
 
@@ -209,27 +181,36 @@ static cs_status backward(cs_mlp *M, int B, const float *X, const float *T, cuda
     k_mse<<<nparts, 256, 0, s>>>(ny, M->y, T, M->dy, part);
     k_mse_finish<<<1, 256, 0, s>>>(nparts, ny, part, M->loss);
     count_launch(2);
+    // weight gradients contract over the batch: both factors FP32, as
+    // three K segments (a_hi b_hi + a_lo b_hi + a_hi b_lo)
+    const int kseg = (int)round64(B);
     // layer 3: dW3 = dY^T H2, db3 = colsum(dY), dH2 = dY W3
-    CSX_TRY(gemm<true, false, float>(M->nout, M->nhid, B, M->dy, M->nout, M->h2, M->nhid, M->g + M->oW3, M->nhid,
-                                     nullptr, false, s));
+    CSX_TRY(tc_pack(M->tDYT, M->nout, B, kseg, "hlh", M->dy, M->nout, true, s));
+    CSX_TRY(tc_pack(M->tH2T, M->nhid, B, kseg, "hhl", M->h2, M->nhid, true, s));
+    CSX_TRY(mlp_gemm(M, M->tDYT, M->tH2T, M->nout, M->nhid, 3 * kseg, M->g + M->oW3, M->nhid, nullptr, false, nullptr,
+                     s));
     k_colsum<<<M->nout, 256, 0, s>>>(B, M->nout, M->dy, M->g + M->ob3);
     count_launch();
-    CSX_TRY(gemm<false, false, __nv_bfloat16>(B, M->nhid, M->nout, M->dy, M->nout, M->w16 + M->o16W3, M->nhid, M->d2,
-                                              M->nhid, nullptr, false, s));
+    CSX_TRY(tc_pack(M->tDY, B, M->nout, M->kout, "hl", M->dy, M->nout, false, s));
+    CSX_TRY(mlp_gemm(M, M->tDY, M->tW3T, B, M->nhid, 2 * M->kout, M->d2, M->nhid, nullptr, false, nullptr, s));
     k_relu_grad<<<1024, 256, 0, s>>>((int64_t)B * M->nhid, M->z2, M->d2);
     count_launch();
     // layer 2
-    CSX_TRY(gemm<true, false, float>(M->nhid, M->nhid, B, M->d2, M->nhid, M->h1, M->nhid, M->g + M->oW2, M->nhid,
-                                     nullptr, false, s));
+    CSX_TRY(tc_pack(M->tD2T, M->nhid, B, kseg, "hlh", M->d2, M->nhid, true, s));
+    CSX_TRY(tc_pack(M->tH1T, M->nhid, B, kseg, "hhl", M->h1, M->nhid, true, s));
+    CSX_TRY(mlp_gemm(M, M->tD2T, M->tH1T, M->nhid, M->nhid, 3 * kseg, M->g + M->oW2, M->nhid, nullptr, false,
+                     nullptr, s));
     k_colsum<<<M->nhid, 256, 0, s>>>(B, M->nhid, M->d2, M->g + M->ob2);
     count_launch();
-    CSX_TRY(gemm<false, false, __nv_bfloat16>(B, M->nhid, M->nhid, M->d2, M->nhid, M->w16 + M->o16W2, M->nhid, M->d1,
-                                              M->nhid, nullptr, false, s));
+    CSX_TRY(tc_pack(M->tD2, B, M->nhid, M->khid, "hl", M->d2, M->nhid, false, s));
+    CSX_TRY(mlp_gemm(M, M->tD2, M->tW2T, B, M->nhid, 2 * M->khid, M->d1, M->nhid, nullptr, false, nullptr, s));
     k_relu_grad<<<1024, 256, 0, s>>>((int64_t)B * M->nhid, M->z1, M->d1);
     count_launch();
     // layer 1
-    CSX_TRY(gemm<true, false, float>(M->nhid, M->nin, B, M->d1, M->nhid, X, M->nin, M->g + M->oW1, M->nin, nullptr,
-                                     false, s));
+    CSX_TRY(tc_pack(M->tD1T, M->nhid, B, kseg, "hlh", M->d1, M->nhid, true, s));
+    CSX_TRY(tc_pack(M->tXT, M->nin, B, kseg, "hhl", X, M->nin, true, s));
+    CSX_TRY(mlp_gemm(M, M->tD1T, M->tXT, M->nhid, M->nin, 3 * kseg, M->g + M->oW1, M->nin, nullptr, false, nullptr,
+                     s));
     k_colsum<<<M->nhid, 256, 0, s>>>(B, M->nhid, M->d1, M->g + M->ob1);
     count_launch();
     CSX_CUDA(cudaGetLastError());
@@ -416,6 +397,30 @@ cs_status cs_mlp_create(int nin, int nhid, int nout, int max_batch, uint64_t see
     if ((rc = dalloc_t(&M->dy, B * nout, &M->bytes)) != CS_OK) goto fail;
     if ((rc = dalloc_t(&M->loss, 4, &M->bytes)) != CS_OK) goto fail;
     if (cudaMallocHost(&M->loss_host, sizeof(float) * 4) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "cudaMallocHost", __FILE__, __LINE__); goto fail; }
+    M->kin = (int)round64(nin);
+    M->khid = (int)round64(nhid);
+    M->kout = (int)round64(nout);
+    M->kb = (int)round64(B);
+    if ((rc = tc_operand_init(M->tX, B, 2 * M->kin, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tW1, nhid, 2 * M->kin, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tH1, B, 2 * M->khid, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tW2, nhid, 2 * M->khid, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tH2, B, 2 * M->khid, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tW3, nout, 2 * M->khid, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tDY, B, 2 * M->kout, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tW3T, nhid, 2 * M->kout, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tD2, B, 2 * M->khid, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tW2T, nhid, 2 * M->khid, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tDYT, nout, 3 * M->kb, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tH2T, nhid, 3 * M->kb, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tD2T, nhid, 3 * M->kb, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tH1T, nhid, 3 * M->kb, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tD1T, nhid, 3 * M->kb, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = tc_operand_init(M->tXT, nin, 3 * M->kb, &M->bytes)) != CS_OK) goto fail;
+    M->part_cap = (int64_t)4 << 20;
+    if ((rc = dalloc_t(&M->part, (size_t)M->part_cap, &M->bytes)) != CS_OK) goto fail;
+    if ((rc = dalloc_t(&M->err, 1, &M->bytes)) != CS_OK) goto fail;
+    if (cudaMemset(M->err, 0, sizeof(int)) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "MLP init", __FILE__, __LINE__); goto fail; }
     if (cudaMemcpy(M->p, h.data(), sizeof(float) * M->nparam, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(M->m, 0, sizeof(float) * M->nparam) != cudaSuccess ||
         cudaMemset(M->v, 0, sizeof(float) * M->nparam) != cudaSuccess) {
@@ -436,6 +441,10 @@ void cs_mlp_destroy(cs_mlp *M) {
     dfree(M->p); dfree(M->g); dfree(M->m); dfree(M->v); dfree(M->w16);
     dfree(M->z1); dfree(M->z2); dfree(M->h1); dfree(M->h2); dfree(M->d1); dfree(M->d2); dfree(M->y); dfree(M->dy);
     dfree(M->loss);
+    for (csx::TcOperand *o : {&M->tX, &M->tW1, &M->tH1, &M->tW2, &M->tH2, &M->tW3, &M->tDY, &M->tW3T, &M->tD2,
+                              &M->tW2T, &M->tDYT, &M->tH2T, &M->tD2T, &M->tH1T, &M->tD1T, &M->tXT})
+        dfree(o->p);
+    dfree(M->part); dfree(M->err);
     if (M->loss_host) cudaFreeHost(M->loss_host);
     delete M;
 }
@@ -466,7 +475,7 @@ cs_status cs_mlp_forward(cs_mlp *M, int batch, const float *X, float *Y, cs_stre
         CSX_CUDA(cudaMemcpyAsync(Y + (int64_t)b0 * M->nout, M->y, sizeof(float) * B * M->nout,
                                  cudaMemcpyDeviceToDevice, s));
     }
-    return CS_OK;
+    return mlp_check(M, s);
 }
 
 cs_status cs_mlp_gradients(cs_mlp *M, int batch, const float *X, const float *T, float *grad_host, float *loss,
@@ -477,7 +486,7 @@ cs_status cs_mlp_gradients(cs_mlp *M, int batch, const float *X, const float *T,
     CSX_TRY(forward(M, batch, X, s));
     CSX_TRY(backward(M, batch, X, T, s));
     CSX_CUDA(cudaMemcpyAsync(M->loss_host, M->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
-    CSX_CUDA(cudaStreamSynchronize(s));
+    CSX_TRY(mlp_check(M, s));
     if (loss) *loss = M->loss_host[0];
     if (grad_host) CSX_CUDA(cudaMemcpy(grad_host, M->g, sizeof(float) * M->nparam, cudaMemcpyDeviceToHost));
     return CS_OK;
@@ -499,7 +508,7 @@ cs_status cs_mlp_train_step(cs_mlp *M, int batch, const float *X, const float *T
     CSX_TRY(refresh_bf16(M, s));
     if (loss) {
         CSX_CUDA(cudaMemcpyAsync(M->loss_host, M->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
-        CSX_CUDA(cudaStreamSynchronize(s));
+        CSX_TRY(mlp_check(M, s));
         *loss = M->loss_host[0];
     }
     return CS_OK;
