@@ -53,9 +53,9 @@ def args_():
     p.add_argument("--order", default="RF")
     p.add_argument("--cpu-n", type=int, default=128, help="side of the oracle's one-thread sample")
     p.add_argument("--no-extras", action="store_true", help="time the chosen form only")
-    p.add_argument("--learned-meshes", type=int, default=128, help="training meshes of the learned setup")
-    p.add_argument("--learned-n", type=int, default=127, help="interior nodes per side of a training mesh")
-    p.add_argument("--learned-steps", type=int, default=6000, help="Adam steps")
+    p.add_argument("--learned-meshes", type=int, default=2000, help="training meshes of the learned setup")
+    p.add_argument("--learned-n", type=int, default=511, help="interior nodes per side of a training mesh")
+    p.add_argument("--learned-steps", type=int, default=20000, help="Adam steps")
     p.add_argument("--interface-maxit", type=int, default=300, help="GMRES steps allowed on the interface workload")
     p.add_argument("--interface-precision", default="fp64", choices=["fp32", "fp64"],
                    help="cycle and Krylov precision of the batched interface solve (FP32 Krylov vectors resolve "
@@ -77,7 +77,7 @@ def args_():
     p.add_argument("--batch-profile-count", type=int, default=16, help="problems in the batch profile case")
     p.add_argument("--profile", default="",
                    choices=["", "setup", "step", "step16", "sweep", "multirhs", "blocksetup", "batch", "general",
-                            "overlap", "sketch"],
+                            "overlap", "sketch", "mlp"],
                    help="run one untimed setup (or setup + solve) and exit: the case ncu captures")
     return p.parse_args()
 
@@ -265,12 +265,16 @@ def learned_section(a, cmg, problems, dev):
 
     import oracle
     from paper_2606_12577_gb300 import learned
-    t0 = time.perf_counter()
-    meshes = [problems.q1_jittered(a.learned_n, 50000 + k) for k in range(a.learned_meshes)]
-    t_gen = time.perf_counter() - t0
+    import multiprocessing as mpc
+    nb_side = -(-a.learned_n // 3)
+    nproc = max(1, min(16, os.cpu_count() or 1))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    X, T = learned.make_dataset(meshes)
+    # the meshes stream from a spawn pool of host processes (the parent holds
+    # a CUDA context) while the GPU labels the ones that have arrived
+    with mpc.get_context("spawn").Pool(nproc) as pool:
+        stream_in = pool.imap(_q1_mesh, [(a.learned_n, 50000 + k) for k in range(a.learned_meshes)], chunksize=2)
+        X, T = learned.make_dataset(stream_in, total=a.learned_meshes * nb_side * nb_side)
     torch.cuda.synchronize()
     t_label = time.perf_counter() - t0
     mdl = cmg.MLP(X.shape[1], 128, T.shape[1], max_batch=8192, seed=1)
@@ -285,9 +289,13 @@ def learned_section(a, cmg, problems, dev):
     out = {"workload": "Q1 FE, jittered 512^2-element mesh (511^2 unknowns), log-normal kappa (sigma 2, corr 16h), "
                        "3x3-node blocks (9x9 Lambda), additive nu=3, GMRES V(1,1) RF to 1e-10",
            "training": {"meshes": a.learned_meshes, "mesh_unknowns": a.learned_n ** 2, "samples": int(X.shape[0]),
-                        "steps": a.learned_steps, "batch": 4096, "loss_first": float(np.mean(hist[:10])),
-                        "loss_last": float(np.mean(hist[-50:])), "generate_s": t_gen, "label_s": t_label,
-                        "train_s": t_train}}
+                        "dataset_gb": (X.numel() + T.numel()) * 4 / 1e9, "steps": a.learned_steps, "batch": 4096,
+                        "epochs": a.learned_steps * 4096 / int(X.shape[0]), "loss_first": float(np.mean(hist[:10])),
+                        "loss_last": float(np.mean(hist[-50:])), "generate_and_label_s": t_label,
+                        "host_processes": nproc, "train_s": t_train,
+                        "gemm": "tcgen05 BF16 (FP32 factors as hi + lo pairs), FP32 accumulation in TMEM"}}
+    del X, T
+    torch.cuda.empty_cache()
     used, ratio = cmg.learned_status(res["learned"][0])
     out["predicted_blocks_in_use"] = bool(used == 1)
     out["level1_objective_ratio_predicted"] = ratio
@@ -326,6 +334,56 @@ def learned_section(a, cmg, problems, dev):
                      "rho_gmres": oracle.rho_from_history(info.history) if len(info.history) > 2 else None,
                      "rho_stationary": oracle.rho_from_history(st.history) if len(st.history) > 2 else None}
     return out
+
+
+def tensor_core_section(a, cmg, dev):
+    """The learned setup's tcgen05 BF16 GEMM (C = A B^T, FP32 accumulation in
+    tensor memory) on an 8192^3 problem, against the measured cuBLAS BF16
+    burst peak, and the network's training step at batch 4096 (nine GEMMs,
+    every FP32 factor as a BF16 hi + lo pair)."""
+    import torch
+    try:
+        with open(PEAKS) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+        src = "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    except Exception:
+        peak, src = 1900.0, "fallback"
+    n = 8192
+    g = torch.Generator(device=dev).manual_seed(3)
+    A = torch.randn(n, n, device=dev, generator=g).to(torch.bfloat16)
+    B = torch.randn(n, n, device=dev, generator=g).to(torch.bfloat16)
+    for _ in range(3):
+        cmg.tc_gemm_bf16(A, B)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        C = cmg.tc_gemm_bf16(A, B)
+    e1.record(s)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / reps * 1e-3
+    tf = 2.0 * n ** 3 / t / 1e12
+    ref = (A[:64].float() @ B[:64].float().T)
+    err = float((C[:64, :64] - ref).abs().max() / ref.abs().max())
+    del A, B, C
+    m = cmg.MLP(225, 128, 243, max_batch=4096, seed=1)
+    Xm = torch.randn(4096, 225, device=dev, generator=g) * 0.3
+    Tm = torch.randn(4096, 243, device=dev, generator=g) * 0.1
+    for _ in range(3):
+        m.train_step(Xm, Tm, 1e-3, with_loss=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for k in range(50):
+        m.train_step(Xm, Tm, 1e-3, with_loss=(k == 49))
+    e1.record(s)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return {"gemm_8192": {"bound": "tensor", "kernel": "k_tc_gemm (tcgen05.mma kind::f16, 128x128 tiles, TMA 128B swizzle, "
+                                                        "4 stages)", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                          "frac": tf / peak, "launch_ms": t * 1e3, "peak_source": src, "max_rel_err_64x64": err},
+            "mlp_train_step_ms_b4096": e0.elapsed_time(e1) / 50}
 
 
 def interface_section(a, cmg, problems, dev):
@@ -407,6 +465,13 @@ def stencil_rel_residual(A, x, b, m, dev):
 def _batch_problem(k):
     import problems
     return problems.batch_problem(k)
+
+
+def _q1_mesh(args):
+    """One training mesh of the learned setup (runs in a pool worker)."""
+    import problems as pr
+    n, seed = args
+    return pr.q1_jittered(n, seed)
 
 
 def make_batch_problems(K):
@@ -762,6 +827,17 @@ def main():
         print(json.dumps({"profile": a.profile, "n": nq, "launches": cmg.kernel_launches()}), flush=True)
         return
 
+    if a.profile == "mlp":  # five training steps of the learned-setup network at batch 4096 (tensor-core GEMMs)
+        m = cmg.MLP(225, 128, 243, max_batch=4096, seed=1)
+        g = torch.Generator(device=dev).manual_seed(5)
+        Xm = torch.randn(4096, 225, device=dev, generator=g) * 0.3
+        Tm = torch.randn(4096, 243, device=dev, generator=g) * 0.1
+        for k in range(5):
+            m.train_step(Xm, Tm, 1e-3, with_loss=(k == 4))
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": a.profile, "launches": cmg.kernel_launches()}), flush=True)
+        return
+
     if a.profile == "sketch":  # the sketched multiplicative setup (s = 32 columns) on the 3D Poisson problem
         As, _ = problems.poisson3d(a.n)
         hs = cmg.setup_hierarchy(As.dim, As.n, As.offsets, torch.tensor(As.coeff, dtype=torch.float64, device=dev))
@@ -973,6 +1049,7 @@ def main():
             "algorithmic_bytes_per_launch": bytes_m, "bound": "hbm"}
         del hb, cb, ci, Xb, Bb
         torch.cuda.empty_cache()
+        result["tensor_core_gemm"] = tensor_core_section(a, cmg, dev)
         result["learned_setup"] = learned_section(a, cmg, problems, dev)
         torch.cuda.empty_cache()
         result["interface_solve"] = interface_section(a, cmg, problems, dev)
