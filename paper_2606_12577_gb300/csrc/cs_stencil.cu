@@ -767,35 +767,82 @@ __device__ __forceinline__ int p1d(int f, int nc, int *c, float *w) {
     return k;
 }
 
-// xo_f = x_f - sum_I P_{f,I} xc_I
+// xo_f = x_f - sum_I P_{f,I} xc_I, one thread per coarse cell: cell j of an
+// axis holds the fine nodes 2j (between coarse nodes j - 1 and j, weights
+// 1/2, a node outside the grid dropped) and 2j + 1 (on coarse node j, weight
+// 1).  The thread loads the cell's up to 2^d coarse corners once, all at
+// once, and forms each of its up to 2^d fine nodes with the products in the
+// order of the per-node definition (z outer, then y, then x; weight
+// wx wy wz rounded once), so every fine value is the one a per-node loop
+// gives.  A per-node thread issued its up to 2^d coarse reads one after the
+// other and was latency bound.
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TBX *TBY) k_prolong(Grid gf, Grid gc, const T *__restrict__ xc, const T *x,
                                                        T *xo) {
-    int fx = blockIdx.x * TBX + threadIdx.x;
-    int fy = blockIdx.y * TBY + threadIdx.y;
-    int fz = blockIdx.z;
-    if (fx >= gf.nx || fy >= gf.ny) return;
-    int cxs[2], cys[2], czs[2];
-    float wx[2], wy[2], wz[2];
-    int kx = p1d(fx, gc.nx, cxs, wx);
-    int ky = p1d(fy, gc.ny, cys, wy);
-    int kz = 1;
-    czs[0] = 0; wz[0] = 1.f;
-    if (DIM == 3) kz = p1d(fz, gc.nz, czs, wz);
     using C = typename AccT<T>::type;
-    C acc = C(0);
-    for (int c = 0; c < kz; ++c)
-        for (int bb = 0; bb < ky; ++bb)
-            for (int a = 0; a < kx; ++a)
-                acc = fma(C(wx[a] * wy[bb] * wz[c]),
-                          ld<T>(xc[cxs[a] + (int64_t)gc.nx * (cys[bb] + (int64_t)gc.ny * czs[c])]), acc);
-    int64_t f = fx + (int64_t)gf.nx * (fy + (int64_t)gf.ny * fz);
-    xo[f] = st<T>(ld<T>(x[f]) - acc);
+    const int jx = blockIdx.x * TBX + threadIdx.x, jy = blockIdx.y * TBY + threadIdx.y, jz = blockIdx.z;
+    if (2 * jx >= gf.nx || 2 * jy >= gf.ny) return;
+    // corner d of an axis: coarse node j - 1 (d = 0) or j (d = 1)
+    const int cx[2] = {jx - 1, jx}, cy[2] = {jy - 1, jy}, cz[2] = {DIM == 3 ? jz - 1 : 0, DIM == 3 ? jz : 0};
+    auto okx = [&](int d) { return cx[d] >= 0 && cx[d] < gc.nx; };
+    auto oky = [&](int d) { return cy[d] >= 0 && cy[d] < gc.ny; };
+    auto okz = [&](int d) { return DIM == 3 ? (cz[d] >= 0 && cz[d] < gc.nz) : d == 1; };
+    C v[2][2][2];
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx)
+                v[dz][dy][dx] = (okx(dx) && oky(dy) && okz(dz))
+                                    ? ld<T>(xc[cx[dx] + (int64_t)gc.nx * (cy[dy] + (int64_t)gc.ny * cz[dz])])
+                                    : C(0);
+    // fine node e of an axis (0: 2j, 1: 2j + 1) takes corner d when
+    // e == 1 ? d == 1 : the corner is inside the grid, with weight 1 or 1/2;
+    // the corners run in ascending d, as in the per-node definition
+#pragma unroll
+    for (int ez = 0; ez < (DIM == 3 ? 2 : 1); ++ez) {
+        const int fz = DIM == 3 ? 2 * jz + ez : jz;
+        if (fz >= gf.nz) continue;
+#pragma unroll
+        for (int ey = 0; ey < 2; ++ey) {
+            const int fy = 2 * jy + ey;
+            if (fy >= gf.ny) continue;
+#pragma unroll
+            for (int ex = 0; ex < 2; ++ex) {
+                const int fx = 2 * jx + ex;
+                if (fx >= gf.nx) continue;
+                C acc = C(0);
+#pragma unroll
+                for (int dz = 0; dz < 2; ++dz) {
+                    const bool uz = DIM == 3 ? (ez == 1 ? dz == 1 : okz(dz)) : dz == 1;
+                    const float wz = (DIM == 3 && ez == 0) ? 0.5f : 1.f;
+                    if (!uz) continue;
+#pragma unroll
+                    for (int dy = 0; dy < 2; ++dy) {
+                        const bool uy = ey == 1 ? dy == 1 : oky(dy);
+                        const float wy = ey == 0 ? 0.5f : 1.f;
+                        if (!uy) continue;
+#pragma unroll
+                        for (int dx = 0; dx < 2; ++dx) {
+                            const bool ux = ex == 1 ? dx == 1 : okx(dx);
+                            const float wx = ex == 0 ? 0.5f : 1.f;
+                            if (!ux) continue;
+                            acc = fma(C(wx * wy * wz), v[dz][dy][dx], acc);
+                        }
+                    }
+                }
+                const int64_t f = fx + (int64_t)gf.nx * (fy + (int64_t)gf.ny * fz);
+                xo[f] = st<T>(ld<T>(x[f]) - acc);
+            }
+        }
+    }
 }
 
 template <typename T>
 cs_status launch_prolong_correct(const Level &f, const Level &c, const T *xc, const T *x, T *xo, cudaStream_t s) {
-    dim3 gr = node_grid(f.g), bl = node_block();
+    const int cxn = (f.g.nx + 1) / 2, cyn = (f.g.ny + 1) / 2, czn = f.g.dim == 3 ? (f.g.nz + 1) / 2 : f.g.nz;
+    dim3 gr((unsigned)((cxn + TBX - 1) / TBX), (unsigned)((cyn + TBY - 1) / TBY), (unsigned)czn), bl = node_block();
     if (f.g.dim == 2) k_prolong<2, T><<<gr, bl, 0, s>>>(f.g, c.g, xc, x, xo);
     else k_prolong<3, T><<<gr, bl, 0, s>>>(f.g, c.g, xc, x, xo);
     CSX_CUDA(cudaGetLastError());
