@@ -890,7 +890,8 @@ def main():
 
     if a.profile:
         h = cmg.setup_hierarchy(A.dim, A.n, A.offsets, coeff)
-        c = cmg.setup_cascade(h, a.kind, nu=a.nu, lowp=2 if a.profile == "step16" else True)
+        c = cmg.setup_cascade(h, a.kind, nu=a.nu, lowp=2 if a.profile == "step16" else True,
+                              setup_precision="fp32" if a.profile in ("setup", "step") else "fp64")
         if a.profile in ("step", "step16"):
             x = torch.zeros(A.N, dtype=torch.float64, device=dev)
             cmg.solve(h, c, bd, x, method="refine", precision="bf16" if a.profile == "step16" else "fp32",
