@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "cs_internal.cuh"
@@ -175,23 +176,48 @@ __global__ void k_gspgemm(int n, const int64_t *__restrict__ arp, const int *__r
     }
 }
 
+// Host symbolic work in parallel: fn(t, lo, hi) over T contiguous ranges
+// of [0, n) (T host threads, at most 16); callers write per-range parts and
+// join them in range order, so results do not depend on T.
+template <class F>
+static int gpar_ranges(int64_t n, F &&fn) {
+    const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw, 16), (n + 8191) / 8192));
+    if (T == 1) {
+        fn(0, (int64_t)0, n);
+        return 1;
+    }
+    std::vector<std::thread> th;
+    th.reserve((size_t)T);
+    for (int t = 0; t < T; ++t) th.emplace_back([&fn, t, T, n] { fn(t, n * t / T, n * (t + 1) / T); });
+    for (std::thread &x : th) x.join();
+    return T;
+}
+
 // the pattern of A B (sorted rows), host
 static void gspgemm_pattern(const GCsr &A, const GCsr &B, GCsr &C) {
     C.n = A.n; C.m = B.m;
     C.hrp.assign((size_t)A.n + 1, 0);
-    C.hci.clear();
-    std::vector<int> mark((size_t)B.m, -1), row;
-    for (int i = 0; i < A.n; ++i) {
-        row.clear();
-        for (int64_t p = A.hrp[i]; p < A.hrp[i + 1]; ++p) {
-            const int k = A.hci[p];
-            for (int64_t q = B.hrp[k]; q < B.hrp[k + 1]; ++q)
-                if (mark[B.hci[q]] != i) { mark[B.hci[q]] = i; row.push_back(B.hci[q]); }
+    std::vector<std::vector<int>> part(16);
+    const int T = gpar_ranges(A.n, [&](int t, int64_t lo, int64_t hi) {
+        std::vector<int> mark((size_t)B.m, -1), row;
+        std::vector<int> &out = part[t];
+        for (int64_t i = lo; i < hi; ++i) {
+            row.clear();
+            for (int64_t p = A.hrp[i]; p < A.hrp[i + 1]; ++p) {
+                const int k = A.hci[p];
+                for (int64_t q = B.hrp[k]; q < B.hrp[k + 1]; ++q)
+                    if (mark[B.hci[q]] != (int)i) { mark[B.hci[q]] = (int)i; row.push_back(B.hci[q]); }
+            }
+            std::sort(row.begin(), row.end());
+            out.insert(out.end(), row.begin(), row.end());
+            C.hrp[i + 1] = (int64_t)row.size();
         }
-        std::sort(row.begin(), row.end());
-        C.hci.insert(C.hci.end(), row.begin(), row.end());
-        C.hrp[i + 1] = (int64_t)C.hci.size();
-    }
+    });
+    for (int i = 0; i < A.n; ++i) C.hrp[i + 1] += C.hrp[i];
+    C.hci.clear();
+    C.hci.reserve((size_t)C.hrp[A.n]);
+    for (int t = 0; t < T; ++t) C.hci.insert(C.hci.end(), part[t].begin(), part[t].end());
 }
 
 static unsigned gwarp_blocks(int64_t items) {
@@ -314,26 +340,54 @@ static void gnode_blocks(GLevel &L) {
 static cs_status gcolour(GLevel &L, int l, uint64_t seed, cudaStream_t s) {
     const int nb = L.nb;
     // symmetrised block graph without duplicates: blocks b and c touch when a
-    // row of b couples to a node of c or they share a node
-    std::vector<std::vector<int>> nbr((size_t)nb);
-    for (int b = 0; b < nb; ++b)
-        for (int p = L.hbptr[b]; p < L.hbptr[b + 1]; ++p) {
-            const int i = L.hbidx[p];
-            for (int64_t q = L.A.hrp[i] - 1; q < L.A.hrp[i + 1]; ++q) {
-                const int j = q < L.A.hrp[i] ? i : L.A.hci[q];
-                for (int u = L.hnptr[j]; u < L.hnptr[j + 1]; ++u) {
-                    const int c = L.hnblk[u];
-                    if (c != b) { nbr[b].push_back(c); nbr[c].push_back(b); }
+    // row of b couples to a node of c or they share a node.  The directed
+    // lists (b -> c) are built in parallel, then merged with their reverse.
+    std::vector<std::vector<int>> out((size_t)nb);
+    gpar_ranges(nb, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t b = lo; b < hi; ++b) {
+            std::vector<int> &ob = out[b];
+            for (int p = L.hbptr[b]; p < L.hbptr[b + 1]; ++p) {
+                const int i = L.hbidx[p];
+                for (int64_t q = L.A.hrp[i] - 1; q < L.A.hrp[i + 1]; ++q) {
+                    const int j = q < L.A.hrp[i] ? i : L.A.hci[q];
+                    for (int u = L.hnptr[j]; u < L.hnptr[j + 1]; ++u)
+                        if (L.hnblk[u] != b) ob.push_back(L.hnblk[u]);
                 }
             }
+            std::sort(ob.begin(), ob.end());
+            ob.erase(std::unique(ob.begin(), ob.end()), ob.end());
         }
+    });
+    std::vector<int> rp((size_t)nb + 1, 0);
+    for (int b = 0; b < nb; ++b)
+        for (int c : out[b]) rp[c + 1]++;
+    for (int b = 0; b < nb; ++b) rp[b + 1] += rp[b];
+    std::vector<int> rin((size_t)rp[nb]), fillr(rp.begin(), rp.end() - 1);
+    for (int b = 0; b < nb; ++b)
+        for (int c : out[b]) rin[fillr[c]++] = b;  // reverse edges, ascending b per c
     std::vector<int> gp((size_t)nb + 1, 0), gi;
-    for (int b = 0; b < nb; ++b) {
-        std::sort(nbr[b].begin(), nbr[b].end());
-        nbr[b].erase(std::unique(nbr[b].begin(), nbr[b].end()), nbr[b].end());
-        gi.insert(gi.end(), nbr[b].begin(), nbr[b].end());
-        gp[b + 1] = (int)gi.size();
-    }
+    std::vector<std::vector<int>> part(16);
+    std::vector<int> deg((size_t)nb);
+    const int T = gpar_ranges(nb, [&](int t, int64_t lo, int64_t hi) {
+        std::vector<int> &pt = part[t];
+        for (int64_t b = lo; b < hi; ++b) {  // union of two ascending lists
+            const std::vector<int> &ob = out[b];
+            size_t x = 0;
+            int y = rp[b];
+            const size_t s0 = pt.size();
+            while (x < ob.size() || y < rp[b + 1]) {
+                int v;
+                if (y >= rp[b + 1] || (x < ob.size() && ob[x] < rin[y])) v = ob[x++];
+                else if (x >= ob.size() || rin[y] < ob[x]) v = rin[y++];
+                else { v = ob[x++]; ++y; }
+                pt.push_back(v);
+            }
+            deg[b] = (int)(pt.size() - s0);
+        }
+    });
+    for (int b = 0; b < nb; ++b) gp[b + 1] = gp[b] + deg[b];
+    gi.reserve((size_t)gp[nb]);
+    for (int t = 0; t < T; ++t) gi.insert(gi.end(), part[t].begin(), part[t].end());
     if (gi.empty()) gi.push_back(0);
     int *dgp = nullptr, *dgi = nullptr, *ca = nullptr, *cb = nullptr, *cnt = nullptr;
     uint64_t *prio = nullptr;
@@ -1085,8 +1139,9 @@ static cs_status gsetup_level(const cs_ghier *h, int l, int kind, int nu, int pr
     int badh = 0;
     GEHost E, En, B;
     cs_status rc = CS_OK;
-    std::vector<int> mark((size_t)N, -1), row;
-    int stamp = 0;
+    // per host thread: column marks (allocated on first use) and stamps
+    std::vector<std::vector<int>> marks(16);
+    std::vector<int> stamps(16, 0);
     const int ncol = kind == CS_MULTIPLICATIVE ? L.ncol : 1;
     const unsigned spd_grid = 152 * 4;
     if ((rc = dalloc_t(&w, (size_t)N, nullptr, s)) != CS_OK) goto done;
@@ -1142,20 +1197,33 @@ static cs_status gsetup_level(const cs_ghier *h, int l, int kind, int nu, int pr
             P.ident.assign((size_t)nb, 0);
             P.cols.clear();
             P.nvals = 0;
-            for (int b = 0; b < nb; ++b) {
-                const int n = L.hbptr[b + 1] - L.hbptr[b];
-                P.coff[b] = (int64_t)P.cols.size();
-                P.voff[b] = P.nvals;
-                if (upd[b]) {
-                    gblock_pattern(L, b, E, grp, mark, ++stamp, row);
-                    P.u[b] = (int)row.size();
-                    P.cols.insert(P.cols.end(), row.begin(), row.end());
-                } else if (!over) {
-                    P.ident[b] = E.ident[b];
-                    P.u[b] = E.u[b];
-                    P.cols.insert(P.cols.end(), E.cols.begin() + E.coff[b], E.cols.begin() + E.coff[b] + E.u[b]);
+            {
+                std::vector<std::vector<int>> part(16);
+                const int T = gpar_ranges(nb, [&](int t, int64_t lo, int64_t hi) {
+                    if (marks[t].empty()) marks[t].assign((size_t)N, -1);
+                    std::vector<int> rw;
+                    for (int64_t b = lo; b < hi; ++b) {
+                        if (upd[b]) {
+                            gblock_pattern(L, (int)b, E, grp, marks[t], ++stamps[t], rw);
+                            P.u[b] = (int)rw.size();
+                            part[t].insert(part[t].end(), rw.begin(), rw.end());
+                        } else if (!over) {
+                            P.ident[b] = E.ident[b];
+                            P.u[b] = E.u[b];
+                            part[t].insert(part[t].end(), E.cols.begin() + E.coff[b],
+                                           E.cols.begin() + E.coff[b] + E.u[b]);
+                        }
+                    }
+                });
+                int64_t nc = 0;
+                for (int b = 0; b < nb; ++b) {
+                    P.coff[b] = nc;
+                    P.voff[b] = P.nvals;
+                    nc += P.u[b];
+                    P.nvals += (int64_t)(L.hbptr[b + 1] - L.hbptr[b]) * P.u[b];
                 }
-                P.nvals += (int64_t)n * P.u[b];
+                P.cols.reserve((size_t)nc);
+                for (int t = 0; t < T; ++t) P.cols.insert(P.cols.end(), part[t].begin(), part[t].end());
             }
             if ((rc = gehost_upload(P, s)) != CS_OK) goto done;
             std::vector<int> fp, fb, fl;
@@ -1167,32 +1235,51 @@ static cs_status gsetup_level(const cs_ghier *h, int l, int kind, int nu, int pr
                 En.ident.assign((size_t)N, 0);
                 En.cols.clear();
                 En.nvals = 0;
-                for (int i = 0; i < N; ++i) {
-                    ++stamp;
-                    row.clear();
-                    for (int u = L.hnptr[i]; u < L.hnptr[i + 1]; ++u) {
-                        const int b = L.hnblk[u];
-                        if (!upd[b]) continue;
-                        fb.push_back(b);
-                        fl.push_back(L.hnloc[u]);
-                        for (int t = 0; t < P.u[b]; ++t) {
-                            const int c = P.cols[P.coff[b] + t];
-                            if (mark[c] != stamp) { mark[c] = stamp; row.push_back(c); }
+                std::vector<std::vector<int>> pcols(16), pfb(16), pfl(16);
+                std::vector<int> ncontrib((size_t)N, 0);
+                const int T = gpar_ranges(N, [&](int t, int64_t lo, int64_t hi) {
+                    if (marks[t].empty()) marks[t].assign((size_t)N, -1);
+                    std::vector<int> &mk = marks[t];
+                    std::vector<int> rw;
+                    for (int64_t i = lo; i < hi; ++i) {
+                        const int st = ++stamps[t];
+                        rw.clear();
+                        for (int u = L.hnptr[i]; u < L.hnptr[i + 1]; ++u) {
+                            const int b = L.hnblk[u];
+                            if (!upd[b]) continue;
+                            pfb[t].push_back(b);
+                            pfl[t].push_back(L.hnloc[u]);
+                            ++ncontrib[i];
+                            for (int q = 0; q < P.u[b]; ++q) {
+                                const int c = P.cols[P.coff[b] + q];
+                                if (mk[c] != st) { mk[c] = st; rw.push_back(c); }
+                            }
+                        }
+                        if (!ncontrib[i]) {
+                            En.ident[i] = E.ident[i];
+                            En.u[i] = E.u[i];
+                            pcols[t].insert(pcols[t].end(), E.cols.begin() + E.coff[i],
+                                            E.cols.begin() + E.coff[i] + E.u[i]);
+                        } else {
+                            std::sort(rw.begin(), rw.end());
+                            En.u[i] = (int)rw.size();
+                            pcols[t].insert(pcols[t].end(), rw.begin(), rw.end());
                         }
                     }
-                    fp[i + 1] = (int)fb.size();
-                    En.coff[i] = (int64_t)En.cols.size();
+                });
+                int64_t nc = 0;
+                for (int i = 0; i < N; ++i) {
+                    fp[i + 1] = fp[i] + ncontrib[i];
+                    En.coff[i] = nc;
                     En.voff[i] = En.nvals;
-                    if (fp[i + 1] == fp[i]) {
-                        En.ident[i] = E.ident[i];
-                        En.u[i] = E.u[i];
-                        En.cols.insert(En.cols.end(), E.cols.begin() + E.coff[i], E.cols.begin() + E.coff[i] + E.u[i]);
-                    } else {
-                        std::sort(row.begin(), row.end());
-                        En.u[i] = (int)row.size();
-                        En.cols.insert(En.cols.end(), row.begin(), row.end());
-                    }
+                    nc += En.u[i];
                     En.nvals += En.u[i];
+                }
+                En.cols.reserve((size_t)nc);
+                for (int t = 0; t < T; ++t) {
+                    En.cols.insert(En.cols.end(), pcols[t].begin(), pcols[t].end());
+                    fb.insert(fb.end(), pfb[t].begin(), pfb[t].end());
+                    fl.insert(fl.end(), pfl[t].begin(), pfl[t].end());
                 }
                 if ((rc = gehost_upload(En, s)) != CS_OK) goto done;
                 CSX_CUDA_GOTO(cudaMemcpyAsync(dfp, fp.data(), sizeof(int) * fp.size(), cudaMemcpyHostToDevice, s));
