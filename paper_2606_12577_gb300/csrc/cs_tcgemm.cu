@@ -3,12 +3,13 @@
 // BF16, K contiguous (row-major A and B, "TN"), FP32 accumulation in tensor
 // memory.
 //
-// One CTA computes a 128 x 128 tile of C (grid x: N tiles, y: M tiles, z: K
-// splits).  Operand tiles of 128 rows x 64 BF16 (128 B per row) are staged
-// by TMA into shared memory with the 128-byte swizzle, four stages deep; one
-// thread issues the TMA copies and the tcgen05.mma instructions (M = 128,
-// N = 128, K = 16 each) and commits each stage back to its "empty" barrier;
-// the accumulator lives in 128 TMEM columns; the four warps read it back with
+// One CTA computes a 128 x BN tile of C, BN = 128, or 256 when N > 128 (grid
+// x: N tiles, y: M tiles, z: K splits).  Operand boxes of 128 rows x 64 BF16
+// (128 B per row) are staged by TMA into shared memory with the 128-byte
+// swizzle, four stages deep; one thread issues the TMA copies and the
+// tcgen05.mma instructions (M = 128, N = BN, K = 16 each) and commits each
+// stage back to its "empty" barrier; the accumulator lives in BN TMEM
+// columns; the four warps read it back with
 // tcgen05.ld (warp w owns TMEM lanes 32w .. 32w + 31, i.e. rows of C) for the
 // epilogue (bias, pre-activation copy, ReLU) or for a split-K partial.
 //
@@ -35,10 +36,15 @@ namespace csx {
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;  // tile; BK: BF16 elements per 128-byte row
+constexpr int TC_BM = 128, TC_BK = 64;  // tile rows; BK: BF16 elements per 128-byte row
 constexpr int TC_STAGES = 4;
-constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;  // 16 KB per operand tile
-constexpr int TC_SMEM = 2 * TC_STAGES * TC_TILE_BYTES + 1024 /* alignment */ + 32768 /* slack */;
+constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;  // 16 KB: one 128-row operand box
+// dynamic shared memory for a tile of BN columns: per stage one A box and
+// BN / 128 B boxes, plus alignment and slack
+template <int BN>
+constexpr int tc_smem() {
+    return TC_STAGES * TC_TILE_BYTES * (1 + BN / 128) + 1024 + 8192;
+}
 constexpr long long TC_SPIN = 1ll << 24;  // try_wait rounds before a wait is declared expired
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -86,14 +92,17 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
 
 // instruction descriptor of kind::f16: D F32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9, 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in 24-28
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
-                              ((uint32_t)(TC_BM >> 4) << 24);
+template <int BN>
+constexpr uint32_t tc_idesc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-        "l"(da), "l"(db), "r"(TC_IDESC), "r"(accumulate)
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -120,9 +129,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
 
 // C (+ bias, ReLU, pre-activation copy Z) = A B^T over the K blocks
 // [z kps, min(nkb, (z + 1) kps)) of this CTA's split, or, with partial set,
-// the split's raw sum into C + z M N (row stride N).
+// the split's raw sum into C + z M N (row stride N).  BN = 128 or 256 columns
+// per tile: the B tile is BN / 128 stacked 128-row boxes, one MMA of N = BN
+// per 16-wide K step, BN TMEM columns.
+template <int BN>
 __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUtensorMap ma,
                                                     const __grid_constant__ CUtensorMap mb, TcArgs a) {
+    constexpr int NB = BN / 128;                         // B boxes per stage
+    constexpr int BTILE = NB * TC_TILE_BYTES;            // B bytes per stage
+    constexpr uint32_t IDESC = tc_idesc<BN>();
     extern __shared__ uint8_t tc_smem_raw[];
     __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
     __shared__ uint32_t tmem_slot;
@@ -131,7 +146,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     const uint32_t base = (raw + 1023u) & ~1023u;  // the 128-byte swizzle wants 1024-byte aligned tiles
     const uint32_t sA = base, sB = base + TC_STAGES * TC_TILE_BYTES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n0 = blockIdx.x * TC_BN, m0 = blockIdx.y * TC_BM;
+    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * TC_BM;
     const int kb0 = blockIdx.z * a.kps;
     const int nk = min(a.nkb, kb0 + a.kps) - kb0;
     if (threadIdx.x == 0) {
@@ -146,7 +161,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(TC_BN)
+                     "r"(BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -164,9 +179,11 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
         auto load = [&](int k) {
             const int s = k % TC_STAGES;
             const uint32_t fb = smem_u32(&full[s]);
-            mbar_expect_tx(fb, 2 * TC_TILE_BYTES);
+            mbar_expect_tx(fb, TC_TILE_BYTES + BTILE);
             tma_load_2d(sA + s * TC_TILE_BYTES, &ma, (kb0 + k) * TC_BK, m0, fb);
-            tma_load_2d(sB + s * TC_TILE_BYTES, &mb, (kb0 + k) * TC_BK, n0, fb);
+#pragma unroll
+            for (int h = 0; h < NB; ++h)  // 128-row boxes stacked: 8-row groups stay 1024 B apart
+                tma_load_2d(sB + s * BTILE + h * TC_TILE_BYTES, &mb, (kb0 + k) * TC_BK, n0 + 128 * h, fb);
         };
         for (int k = 0; k < nk && k < TC_STAGES; ++k) {
             load(k);
@@ -179,8 +196,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
             for (int j = 0; j < TC_BK / 16; ++j)  // K = 16 per instruction: 32 bytes along the swizzled row
-                mma_bf16(tmem, sw128_desc(sA + s * TC_TILE_BYTES + 32 * j), sw128_desc(sB + s * TC_TILE_BYTES + 32 * j),
-                         (k > 0 || j > 0) ? 1u : 0u);
+                mma_bf16(tmem, sw128_desc(sA + s * TC_TILE_BYTES + 32 * j), sw128_desc(sB + s * BTILE + 32 * j),
+                         IDESC, (k > 0 || j > 0) ? 1u : 0u);
             mma_commit(smem_u32(&empty[s]));
             // refill the stage of the previous K block once its products are done
             if (k >= 1 && k - 1 + TC_STAGES < nk) {
@@ -205,7 +222,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     if (!all_ok && threadIdx.x == 0) atomicExch(a.err, 1);
     if (all_ok && !failed && nk > 0) {
         const int row = m0 + warp * 32 + lane;
-        for (int c = 0; c < TC_BN; c += 32) {
+        for (int c = 0; c < BN; c += 32) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
             if (row >= a.M) continue;
@@ -235,7 +252,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
     }
 }
 
@@ -282,6 +299,11 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
 std::once_flag g_attr_once;
 cudaError_t g_attr_err = cudaSuccess;
+
+template <int BN>
+void tc_launch(const TcOperand &A, const TcOperand &B, const TcArgs &a, int tn, int tm, int splits, cudaStream_t s) {
+    k_tc_gemm<BN><<<dim3(tn, tm, splits), 128, tc_smem<BN>(), s>>>(A.map, B.map, a);
+}
 }  // namespace
 
 cs_status tc_map(CUtensorMap *map, const __nv_bfloat16 *ptr, int64_t rows, int64_t kw) {
@@ -349,11 +371,15 @@ cs_status tc_gemm(const TcOperand &A, const TcOperand &B, int M, int N, int64_t 
         return CS_ERR_ARG;
     }
     std::call_once(g_attr_once, [] {
-        g_attr_err = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        g_attr_err = cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<128>());
+        if (g_attr_err == cudaSuccess)
+            g_attr_err =
+                cudaFuncSetAttribute(k_tc_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<256>());
     });
     CSX_CUDA(g_attr_err);
+    const int bn = N > 128 ? 256 : 128;  // one MMA of N = 256 per K step when the columns need it
     const int nkb = (int)((K + TC_BK - 1) / TC_BK);
-    const int tn = (N + TC_BN - 1) / TC_BN, tm = (M + TC_BM - 1) / TC_BM;
+    const int tn = (N + bn - 1) / bn, tm = (M + TC_BM - 1) / TC_BM;
     int splits = tn * tm >= 76 ? 1 : std::min(nkb, (152 + tn * tm - 1) / (tn * tm));
     int kps = (nkb + splits - 1) / splits;
     splits = (nkb + kps - 1) / kps;  // every split gets at least one K block
@@ -368,7 +394,8 @@ cs_status tc_gemm(const TcOperand &A, const TcOperand &B, int M, int N, int64_t 
     a.ldc = ldc;
     a.bias = bias; a.relu = relu ? 1 : 0; a.Z = Z;
     a.err = err;
-    k_tc_gemm<<<dim3(tn, tm, splits), 128, TC_SMEM, s>>>(A.map, B.map, a);
+    if (bn == 256) tc_launch<256>(A, B, a, tn, tm, splits, s);
+    else tc_launch<128>(A, B, a, tn, tm, splits, s);
     count_launch();
     CSX_CUDA(cudaGetLastError());
     if (splits > 1) {
