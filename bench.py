@@ -336,6 +336,51 @@ def learned_section(a, cmg, problems, dev):
     return out
 
 
+def small_2d_section(a, cmg, problems, dev):
+    """The small latency-bound case: 2D Poisson 5-point 64^2, Dirichlet, point
+    blocks, additive nu = 3, V(1,1) RF, Galerkin levels to 4^2 and the dense
+    coarsest solve, FP64 throughout, RHS U[-1,1] (seed 1000): setup + solve
+    to 1e-10 per step (CUDA events, 20 steps after 3 warm-up), stationary and
+    right-preconditioned GMRES; the V-cycle is graph-captured."""
+    import torch
+    A = problems.poisson(2, 64)
+    coeff = torch.tensor(A.coeff, dtype=torch.float64, device=dev)
+    b = torch.tensor(problems.rhs(A.N, 1000), dtype=torch.float64, device=dev)
+    s = torch.cuda.current_stream()
+    out = {"workload": "2D Poisson 5-point 64^2, additive nu=3, V(1,1) RF, FP64 setup + solve to 1e-10"}
+    for method in ("stationary", "gmres_right"):
+        info = [None]
+
+        def one():
+            h = cmg.setup_hierarchy(A.dim, A.n, A.offsets, coeff)
+            c = cmg.setup_cascade(h, "additive", nu=3)
+            x = torch.zeros(A.N, dtype=torch.float64, device=dev)
+            info[0] = cmg.solve(h, c, b, x, method=method, tol=1e-10, mu_pre=1, mu_post=1, order="RF")
+            return h, c
+
+        for _ in range(3):
+            h, c = one()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(20):
+            one()
+        e1.record(s)
+        torch.cuda.synchronize()
+        step_ms = e0.elapsed_time(e1) / 20
+        x = torch.zeros(A.N, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(20):
+            x.zero_()
+            cmg.solve(h, c, b, x, method=method, tol=1e-10, mu_pre=1, mu_post=1, order="RF")
+        e1.record(s)
+        torch.cuda.synchronize()
+        out[method] = {"setup_plus_solve_ms": step_ms, "solve_ms": e0.elapsed_time(e1) / 20,
+                       "iterations": info[0].iterations, "final_rel_residual": float(info[0].final_rel_residual)}
+    return out
+
+
 def tensor_core_section(a, cmg, dev):
     """The learned setup's tcgen05 BF16 GEMM (C = A B^T, FP32 accumulation in
     tensor memory) on an 8192^3 problem, against the measured cuBLAS BF16
@@ -1053,6 +1098,7 @@ def main():
             "algorithmic_bytes_per_launch": bytes_m, "bound": "hbm"}
         del hb, cb, ci, Xb, Bb
         torch.cuda.empty_cache()
+        result["small_2d_poisson_64"] = small_2d_section(a, cmg, problems, dev)
         result["tensor_core_gemm"] = tensor_core_section(a, cmg, dev)
         result["learned_setup"] = learned_section(a, cmg, problems, dev)
         torch.cuda.empty_cache()
