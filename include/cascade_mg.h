@@ -108,8 +108,11 @@ typedef struct {
     int nu;        /* depth, 1..8 */
     int prescale;  /* 1: elliptic prescaling W = diag(A_ii^-1/2) (Sec. 2.3.1); 0: none */
     int alpha;     /* residual truncation (Algorithm 2): after each row update keep the alpha columns
-                      of largest magnitude (ties: smaller column index); 0 = none; point blocks
-                      only (CS_ERR_UNSUPPORTED for block levels or with a model) */
+                      of largest magnitude (ties: smaller column index), on block levels the alpha
+                      column blocks of largest Frobenius norm over the block's rows (ties: smaller
+                      block index); 0 = none.  Block levels take alpha <= 64 (or alpha at least the
+                      column blocks in reach, which truncates nothing), else CS_ERR_UNSUPPORTED;
+                      CS_ERR_UNSUPPORTED with a model */
     int lowp;      /* 1: also keep FP32 copies of the level operators and Lambda for
                       CS_FP32 cycles (iterative refinement); 2: FP32 and BF16 copies, the
                       latter for CS_BF16 cycles (BF16 storage, FP32 arithmetic; point-block

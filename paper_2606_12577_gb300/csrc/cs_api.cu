@@ -446,13 +446,9 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
     if (o->kind != CS_ADDITIVE && o->kind != CS_MULTIPLICATIVE) { set_error("bad cascade kind"); return CS_ERR_ARG; }
     if (o->nu < 1 || o->nu > 8) { set_error("nu must be in 1..8"); return CS_ERR_ARG; }
     if (o->alpha < 0) { set_error("alpha must be >= 0 (0: no truncation)"); return CS_ERR_ARG; }
-    if (o->alpha > 0) {
-        for (int l = 0; l + 1 < h->nlev; ++l)
-            if (h->lev[l].bs > 1) {
-                set_error("truncation (alpha > 0) is implemented for point blocks only");
-                return CS_ERR_UNSUPPORTED;
-            }
-        if (o->model) { set_error("truncation does not combine with the learned setup"); return CS_ERR_UNSUPPORTED; }
+    if (o->alpha > 0 && o->model) {
+        set_error("truncation does not combine with the learned setup");
+        return CS_ERR_UNSUPPORTED;
     }
     cudaStream_t s = (cudaStream_t)stream;
     cs_cascade *c = new cs_cascade();
@@ -512,7 +508,7 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
             if (o->sketch > 0)
                 return cascade_setup_level_sketch(h, l, c->kind, c->nu, o->prescale, o->sketch, o->sketch_seed,
                                                   o->sketch_exact_first, o->setup_precision == CS_FP32, c->lam[l], st);
-            if (L.bs > 1) return cascade_setup_level_blocks(h, l, c->kind, c->nu, o->prescale, c->lam[l], st);
+            if (L.bs > 1) return cascade_setup_level_blocks(h, l, c->kind, c->nu, o->prescale, o->alpha, c->lam[l], st);
             int64_t peak = 0;
             return cascade_setup_level(h, l, c->kind, c->nu, o->prescale, !o->no_reuse, o->alpha,
                                        o->setup_precision == CS_FP32, c->lam[l], st, &peak);
@@ -528,7 +524,7 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
                 double *lam1 = nullptr;
                 cs_status r = dalloc_t(&lam1, (size_t)lam_step(L), nullptr, s);
                 if (r != CS_OK) return r;
-                r = cascade_setup_level_blocks(h, 0, CS_ADDITIVE, 1, o->prescale, lam1, s);
+                r = cascade_setup_level_blocks(h, 0, CS_ADDITIVE, 1, o->prescale, 0, lam1, s);
                 if (r == CS_OK)
                     r = learned_setup_level0(h, c, const_cast<cs_mlp *>(o->model), o->model_tol > 0 ? o->model_tol : 0.05,
                                              c->lam[0], lam1, s);

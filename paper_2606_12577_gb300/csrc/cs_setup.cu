@@ -1628,8 +1628,113 @@ __global__ void __launch_bounds__(128) k_block_update(Grid g, int bs, int nbx, i
         }
 }
 
+// Truncation of the updated block rows (Algorithm 2's optional step, for
+// blocks): block b's rows keep the alpha column blocks of largest Frobenius
+// norm over the block's rows -- ties go to the smaller block index -- and
+// the others are set to zero.  Candidates are the blocks within reach of the
+// offsets (radius R) that hold an in-grid column of one of the rows; a
+// column block's squared norm adds, over its nodes in ascending index and
+// per node over the block's rows in ascending index, the squared entries
+// (unfused).  With no more candidates than alpha the rows are kept.  One
+// warp per block: lanes over candidates, alpha rounds of a warp arg-max,
+// then lanes over offsets zero what was not selected.  offidx maps an offset
+// (ox, oy, oz), |o| <= R per axis, to its index in the step's offsets, or -1.
+// err is set when the candidates exceed 32 TR_KC or alpha exceeds 64.
+constexpr int TR_KC = 32;  // candidates per lane
+template <int DIM, int NMAX>
+__global__ void __launch_bounds__(128) k_block_truncate(Grid g, int bs, int nbx, int nby, int nbz, int64_t nblocks,
+                                                         double *__restrict__ E, int nN, const int *__restrict__ off,
+                                                         const int *__restrict__ offidx, int R, int alpha,
+                                                         int colour, int *err) {
+    __shared__ int ssel[4][64];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t b = blockIdx.x * (int64_t)4 + wib;
+    if (b >= nblocks) return;
+    int node[NMAX], lpos[NMAX], bc;
+    const int np = block_nodes<DIM, NMAX>(g, bs, nbx, nby, b, node, lpos, nullptr, &bc);
+    if (colour >= 0 && bc != colour) return;
+    const int64_t N = g.N;
+    const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((int64_t)nbx * nby));
+    auto lo = [&](int c) { return bs * c - R >= 0 ? (bs * c - R) / bs : 0; };  // floor, clamped at 0
+    const int cx0 = lo(bx), cy0 = lo(by), cz0 = DIM == 3 ? lo(bz) : 0;
+    const int cx1 = min(nbx - 1, (bs * bx + bs - 1 + R) / bs), cy1 = min(nby - 1, (bs * by + bs - 1 + R) / bs);
+    const int cz1 = DIM == 3 ? min(nbz - 1, (bs * bz + bs - 1 + R) / bs) : 0;
+    const int ncx = cx1 - cx0 + 1, ncy = cy1 - cy0 + 1, ncz = cz1 - cz0 + 1;
+    const int ncand = ncx * ncy * ncz;
+    if (ncand > 32 * TR_KC || alpha > 64) {
+        if (lane == 0) atomicExch(err, 1);
+        return;
+    }
+    const int side = 2 * R + 1;
+    double nrm[TR_KC];
+    bool pres[TR_KC], sel[TR_KC];
+#pragma unroll
+    for (int k = 0; k < TR_KC; ++k) {
+        nrm[k] = 0.0;
+        pres[k] = false;
+        sel[k] = false;
+        const int c = lane + 32 * k;
+        if (c >= ncand) continue;
+        const int qx = cx0 + c % ncx, qy = cy0 + (c / ncx) % ncy, qz = cz0 + c / (ncx * ncy);
+        double acc = 0.0;
+        bool any = false;
+        for (int jz = (DIM == 3 ? bs * qz : 0); jz < (DIM == 3 ? min(g.nz, bs * qz + bs) : 1); ++jz)
+            for (int jy = bs * qy; jy < min(g.ny, bs * qy + bs); ++jy)
+                for (int jx = bs * qx; jx < min(g.nx, bs * qx + bs); ++jx)
+                    for (int p = 0; p < np; ++p) {
+                        const int ix = node[p] % g.nx, iy = (node[p] / g.nx) % g.ny, iz = node[p] / (g.nx * g.ny);
+                        const int ox = jx - ix, oy = jy - iy, oz = jz - iz;
+                        if (abs(ox) > R || abs(oy) > R || abs(oz) > R) continue;
+                        const int t = __ldg(offidx + (ox + R) + side * ((oy + R) + side * (DIM == 3 ? oz + R : 0)));
+                        if (t < 0) continue;
+                        const double v = E[(int64_t)t * N + node[p]];
+                        acc = __dadd_rn(acc, __dmul_rn(v, v));
+                        any = true;
+                    }
+        nrm[k] = acc;
+        pres[k] = any;
+    }
+    int npres = 0;
+#pragma unroll
+    for (int k = 0; k < TR_KC; ++k) npres += pres[k] ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) npres += __shfl_xor_sync(0xffffffffu, npres, o);
+    if (npres <= alpha) return;  // every candidate kept
+    for (int a = 0; a < alpha; ++a) {
+        double bn = -1.0;
+        int bcand = 1 << 30;
+#pragma unroll
+        for (int k = 0; k < TR_KC; ++k) {
+            const int c = lane + 32 * k;
+            if (!pres[k] || sel[k]) continue;
+            if (nrm[k] > bn || (nrm[k] == bn && c < bcand)) { bn = nrm[k]; bcand = c; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {  // arg-max: larger norm, then the smaller candidate (block index)
+            const double on = __shfl_xor_sync(0xffffffffu, bn, o);
+            const int oc = __shfl_xor_sync(0xffffffffu, bcand, o);
+            if (on > bn || (on == bn && oc < bcand)) { bn = on; bcand = oc; }
+        }
+#pragma unroll
+        for (int k = 0; k < TR_KC; ++k)
+            if (lane + 32 * k == bcand) sel[k] = true;
+        if (lane == 0) ssel[wib][a] = bcand;
+    }
+    __syncwarp();
+    for (int p = 0; p < np; ++p) {
+        const int ix = node[p] % g.nx, iy = (node[p] / g.nx) % g.ny, iz = node[p] / (g.nx * g.ny);
+        for (int t = lane; t < nN; t += 32) {
+            const int jx = ix + __ldg(off + 3 * t), jy = iy + __ldg(off + 3 * t + 1);
+            const int jz = DIM == 3 ? iz + __ldg(off + 3 * t + 2) : 0;
+            if (jx < 0 || jx >= g.nx || jy < 0 || jy >= g.ny || (DIM == 3 && (jz < 0 || jz >= g.nz))) continue;
+            const int c = (jx / bs - cx0) + ncx * ((jy / bs - cy0) + ncy * (DIM == 3 ? jz / bs - cz0 : 0));
+            bool keep = false;
+            for (int a = 0; a < alpha; ++a) keep = keep || ssel[wib][a] == c;
+            if (!keep) E[(int64_t)t * N + node[p]] = 0.0;
+        }
+    }
+}
+
 template <int DIM, int KIND>
-static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, int prescale, double *lam,
+static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, int prescale, int alpha, double *lam,
                                 cudaStream_t s) {
     using S = StenS<DIM, KIND>;
     constexpr int NST = S::NST;
@@ -1641,12 +1746,17 @@ static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, 
     dim3 gr = node_grid(g), bl = node_block();
     double *w = nullptr, *At = nullptr, *Ecur = nullptr, *Enxt = nullptr, *Rbuf = nullptr, *GC = nullptr, *Ltb = nullptr;
     int *bad = nullptr, *pstart = nullptr, *curR = nullptr, *shiftR = nullptr, *curN = nullptr, *shiftN = nullptr;
+    int *toff = nullptr, *tidx = nullptr, *terr = nullptr;  // truncation: offsets, offset lookup, error flag
     unsigned *pairs = nullptr;
     cs_status rc = CS_OK;
     int badh = 0;
     std::vector<Off3> Ocur{{0, 0, 0}};
     std::vector<Off3> D;
     const size_t smem = (size_t)NST * TBX * TBY * (sizeof(double) + sizeof(int));
+    if (alpha > 0) {
+        if ((rc = dalloc_t(&terr, 1, nullptr, s)) != CS_OK) goto done;
+        CSX_CUDA_GOTO(cudaMemsetAsync(terr, 0, sizeof(int), s));
+    }
     for (int dz = (DIM == 3 ? -(bs - 1) : 0); dz <= (DIM == 3 ? bs - 1 : 0); ++dz)
         for (int dy = -(bs - 1); dy <= bs - 1; ++dy)
             for (int dx = -(bs - 1); dx <= bs - 1; ++dx) D.push_back({dx, dy, dz});  // lexicographic = sidx order
@@ -1753,6 +1863,27 @@ static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, 
             }
             if ((rc = dalloc_t(&Rbuf, (size_t)nR * N, nullptr, s)) != CS_OK) goto done;
             if (!last && (rc = dalloc_t(&Enxt, (size_t)nN * N, nullptr, s)) != CS_OK) goto done;
+            int tR = 0;
+            for (const Off3 &o : ON) tR = std::max({tR, std::abs(o.x), std::abs(o.y), std::abs(o.z)});
+            // at most (2 ceil(R / bs) + 2)^d column blocks are in reach: alpha at
+            // least that truncates nothing
+            const int reach = 2 * ((tR + bs - 1) / bs) + 2;
+            const bool trunc = alpha > 0 && !last && (int64_t)alpha < (int64_t)reach * reach * (DIM == 3 ? reach : 1);
+            if (trunc) {  // the new offsets and their dense lookup over [-R, R]^d
+                const int side = 2 * tR + 1;
+                std::vector<int> ho(3 * (size_t)nN), hidx((size_t)side * side * (DIM == 3 ? side : 1), -1);
+                for (int o = 0; o < nN; ++o) {
+                    ho[3 * o] = ON[o].x; ho[3 * o + 1] = ON[o].y; ho[3 * o + 2] = ON[o].z;
+                    hidx[(ON[o].x + tR) + side * ((ON[o].y + tR) + side * (DIM == 3 ? ON[o].z + tR : 0))] = o;
+                }
+                dfree(toff, s); dfree(tidx, s);
+                toff = nullptr; tidx = nullptr;
+                if ((rc = dalloc_t(&toff, ho.size(), nullptr, s)) != CS_OK) goto done;
+                if ((rc = dalloc_t(&tidx, hidx.size(), nullptr, s)) != CS_OK) goto done;
+                CSX_CUDA_GOTO(cudaMemcpyAsync(toff, ho.data(), sizeof(int) * ho.size(), cudaMemcpyHostToDevice, s));
+                CSX_CUDA_GOTO(cudaMemcpyAsync(tidx, hidx.data(), sizeof(int) * hidx.size(), cudaMemcpyHostToDevice, s));
+                CSX_CUDA_GOTO(cudaStreamSynchronize(s));  // the host tables go out of scope
+            }
             {
                 const int colour = ncol == 2 ? k : -1;
                 k_block_R<DIM, KIND><<<gr, bl, smem, s>>>(g, h->periodic, At, Ecur, Rbuf, nR, pstart, pairs, bs, colour);
@@ -1777,6 +1908,11 @@ static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, 
             k_block_update<DIM, NM><<<nwarp, 128, 0, s>>>(g, bs, L.nbx, L.nby, L.nblocks, Ecur, Rbuf, Enxt, nN,   \
                                                           curN, shiftN, colour, Ltb);                               \
             count_launch();                                                                                         \
+            if (trunc) {                                                                                            \
+                k_block_truncate<DIM, NM><<<nwarp, 128, 0, s>>>(g, bs, L.nbx, L.nby, L.nbz, L.nblocks, Enxt, nN,  \
+                                                                toff, tidx, tR, alpha, colour, terr);              \
+                count_launch();                                                                                     \
+            }                                                                                                       \
         }                                                                                                           \
     }
                 if (nmax == 4) CSX_BLOCK_STEPS(4)
@@ -1786,6 +1922,17 @@ static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, 
 #undef CSX_BLOCK_STEPS
             }
             if (cudaGetLastError() != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "block setup", __FILE__, __LINE__); goto done; }
+            if (trunc) {
+                int th = 0;
+                CSX_CUDA_GOTO(cudaMemcpyAsync(&th, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
+                CSX_CUDA_GOTO(cudaStreamSynchronize(s));
+                if (th) {
+                    set_error("level %d: truncation needs alpha <= 64 and at most %d column blocks in reach", l,
+                              32 * TR_KC);
+                    rc = CS_ERR_UNSUPPORTED;
+                    goto done;
+                }
+            }
             dfree(Ecur, s);
             dfree(Rbuf, s);
             Rbuf = nullptr;
@@ -1798,18 +1945,19 @@ done:
     dfree(w, s); dfree(At, s); dfree(Ecur, s); dfree(Enxt, s); dfree(Rbuf, s); dfree(bad, s); dfree(pstart, s);
     dfree(GC, s); dfree(Ltb, s);
     dfree(pairs, s); dfree(curR, s); dfree(shiftR, s); dfree(curN, s); dfree(shiftN, s);
+    dfree(toff, s); dfree(tidx, s); dfree(terr, s);
     return rc;
 }
 
-cs_status cascade_setup_level_blocks(const cs_hierarchy *h, int l, int kind, int nu, int prescale, double *lam,
+cs_status cascade_setup_level_blocks(const cs_hierarchy *h, int l, int kind, int nu, int prescale, int alpha, double *lam,
                                      cudaStream_t s) {
     const Level &L = h->lev[l];
     if (L.g.dim == 2) {
-        if (L.kind == STAR) return setup_blocks_t<2, STAR>(h, l, kind, nu, prescale, lam, s);
-        return setup_blocks_t<2, BOX>(h, l, kind, nu, prescale, lam, s);
+        if (L.kind == STAR) return setup_blocks_t<2, STAR>(h, l, kind, nu, prescale, alpha, lam, s);
+        return setup_blocks_t<2, BOX>(h, l, kind, nu, prescale, alpha, lam, s);
     }
-    if (L.kind == STAR) return setup_blocks_t<3, STAR>(h, l, kind, nu, prescale, lam, s);
-    return setup_blocks_t<3, BOX>(h, l, kind, nu, prescale, lam, s);
+    if (L.kind == STAR) return setup_blocks_t<3, STAR>(h, l, kind, nu, prescale, alpha, lam, s);
+    return setup_blocks_t<3, BOX>(h, l, kind, nu, prescale, alpha, lam, s);
 }
 
 }  // namespace csx
