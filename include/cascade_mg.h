@@ -135,7 +135,12 @@ typedef struct {
                       their inner products summed in FP64 over chunks of 8 terms and each
                       row's lambda = <E_i, R_i> / <R_i, R_i> divided in FP64 (Lambda agrees
                       with the FP64 setup to about 1e-5 relative; meant for FP32 cycles).
-                      Point blocks without alpha or model, else CS_ERR_UNSUPPORTED.  With
+                      Block levels form their R and E rows the same way, their Gram and cross
+                      products in FP32 over chunks of 8 and in FP64 across them, and solve the
+                      block least squares in FP64 with the minimum-norm cutoff at 1e-5 tr(G), the
+                      resolution of FP32 products (exactly singular Gram matrices occur from the
+                      second step on 9-point levels).  CS_ERR_UNSUPPORTED with a model or with
+                      alpha (the ranking of truncation would flip near ties).  With
                       sketch > 0: the sketch vectors Y and Z = A~ Y in FP32, the inner
                       products and lambda in FP64 */
     int sketch;          /* 0 (default): the exact setup.  s in 1..128: the sketched setup of the

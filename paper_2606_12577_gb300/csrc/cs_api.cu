@@ -465,10 +465,9 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
         return CS_ERR_ARG;
     }
     if (o->setup_precision == CS_FP32) {
-        bool blocks = false;
-        for (int l = 0; l < h->nlev; ++l) blocks = blocks || h->lev[l].bs > 1;
-        if (blocks || o->model || o->alpha > 0) {
-            set_error("the FP32 setup is implemented for point blocks without truncation or a model");
+        // truncation ranks columns by norm: FP32 products would flip near ties
+        if (o->model || o->alpha > 0) {
+            set_error("the FP32 setup takes no model and no truncation");
             delete c;
             return CS_ERR_UNSUPPORTED;
         }
@@ -508,7 +507,9 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
             if (o->sketch > 0)
                 return cascade_setup_level_sketch(h, l, c->kind, c->nu, o->prescale, o->sketch, o->sketch_seed,
                                                   o->sketch_exact_first, o->setup_precision == CS_FP32, c->lam[l], st);
-            if (L.bs > 1) return cascade_setup_level_blocks(h, l, c->kind, c->nu, o->prescale, o->alpha, c->lam[l], st);
+            if (L.bs > 1)
+                return cascade_setup_level_blocks(h, l, c->kind, c->nu, o->prescale, o->alpha,
+                                                  o->setup_precision == CS_FP32, c->lam[l], st);
             int64_t peak = 0;
             return cascade_setup_level(h, l, c->kind, c->nu, o->prescale, !o->no_reuse, o->alpha,
                                        o->setup_precision == CS_FP32, c->lam[l], st, &peak);
@@ -524,7 +525,7 @@ cs_status cs_setup_cascade(cs_hierarchy *h, const cs_cascade_opts *o, cs_stream 
                 double *lam1 = nullptr;
                 cs_status r = dalloc_t(&lam1, (size_t)lam_step(L), nullptr, s);
                 if (r != CS_OK) return r;
-                r = cascade_setup_level_blocks(h, 0, CS_ADDITIVE, 1, o->prescale, 0, lam1, s);
+                r = cascade_setup_level_blocks(h, 0, CS_ADDITIVE, 1, o->prescale, 0, false, lam1, s);
                 if (r == CS_OK)
                     r = learned_setup_level0(h, c, const_cast<cs_mlp *>(o->model), o->model_tol > 0 ? o->model_tol : 0.05,
                                              c->lam[0], lam1, s);

@@ -222,7 +222,7 @@ cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, in
                               bool fp32, double *lam, cudaStream_t s, int64_t *peak_bytes);
 cs_status cascade_setup_level_sketch(const cs_hierarchy *h, int l, int kind, int nu, int prescale, int s,
                                      uint64_t seed, int exact_first, bool fp32, double *lam, cudaStream_t st);
-cs_status cascade_setup_level_blocks(const cs_hierarchy *h, int l, int kind, int nu, int prescale, int alpha, double *lam,
+cs_status cascade_setup_level_blocks(const cs_hierarchy *h, int l, int kind, int nu, int prescale, int alpha, bool fp32, double *lam,
                                      cudaStream_t s);
 cs_status learned_setup_level0(const cs_hierarchy *h, cs_cascade *c, cs_mlp *M, double tol, double *lam,
                                const double *lam_exact1, cudaStream_t s);

@@ -1171,18 +1171,19 @@ cs_status cascade_setup_level(const cs_hierarchy *h, int l, int kind, int nu, in
 // R lives on O_R = O_cur + S; the update spreads each row over the block, so
 // O_next = O_R + D with D the displacements {-(bs-1)..bs-1}^dim.
 
-// R rows of the nodes of active blocks (one thread per node)
-template <int DIM, int KIND>
-__global__ void __launch_bounds__(TBX *TBY) k_block_R(Grid g, int periodic, const double *__restrict__ At,
-                                                       const double *__restrict__ Ecur, double *__restrict__ Rbuf,
+// R rows of the nodes of active blocks (one thread per node), in W
+// (FP64, or FP32 for the FP32 setup products)
+template <int DIM, int KIND, typename W = double>
+__global__ void __launch_bounds__(TBX *TBY) k_block_R(Grid g, int periodic, const W *__restrict__ At,
+                                                       const W *__restrict__ Ecur, W *__restrict__ Rbuf,
                                                        int nR, const int *__restrict__ pstart,
                                                        const unsigned *__restrict__ pairs, int bs, int colour) {
     using S = StenS<DIM, KIND>;
     constexpr int NST = S::NST;
     constexpr int NT = TBX * TBY;
     extern __shared__ double sm_blk[];
-    double *sa = sm_blk;
-    int *snb = reinterpret_cast<int *>(sm_blk + NST * NT);
+    W *sa = reinterpret_cast<W *>(sm_blk);
+    int *snb = reinterpret_cast<int *>(sa + NST * NT);
     const int tid = threadIdx.x + TBX * threadIdx.y;
     const int ix = blockIdx.x * TBX + threadIdx.x, iy = blockIdx.y * TBY + threadIdx.y, iz = blockIdx.z;
     if (ix >= g.nx || iy >= g.ny) return;
@@ -1205,12 +1206,12 @@ __global__ void __launch_bounds__(TBX *TBY) k_block_R(Grid g, int periodic, cons
             in = jx >= 0 && jx < g.nx && jy >= 0 && jy < g.ny && (DIM == 2 || (jz >= 0 && jz < g.nz));
         }
         snb[s * NT + tid] = in ? jx + g.nx * (jy + g.ny * jz) : i;
-        sa[s * NT + tid] = in ? At[(int64_t)s * N + i] : 0.0;
+        sa[s * NT + tid] = in ? At[(int64_t)s * N + i] : W(0);
     }
     int p = __ldg(pstart);
     for (int o = 0; o < nR; ++o) {
         const int pe = __ldg(pstart + o + 1);
-        double r = 0.0;
+        W r = W(0);
         for (; p < pe; ++p) {
             const unsigned u = __ldg(pairs + p);
             const int s = (int)(u >> 24), c = (int)(u & 0xffffffu);
@@ -1259,9 +1260,9 @@ __device__ __forceinline__ int block_sidx(const int (*dl)[3], int p, int q, int 
 // warp-shuffle sums in a fixed order.  Output layout: entry e of block b at
 // GC[e * nblocks + b], e = p NMAX + q for G (q >= p only) and NMAX^2 + p NMAX
 // + q for C, so that the thread-per-block solve reads it coalesced.
-template <int DIM, int NMAX>
+template <int DIM, int NMAX, typename W = double>
 __global__ void __launch_bounds__(128) k_block_gram(Grid g, int bs, int nbx, int nby, int64_t nblocks,
-                                                     const double *__restrict__ Ecur, const double *__restrict__ Rbuf,
+                                                     const W *__restrict__ Ecur, const W *__restrict__ Rbuf,
                                                      int nR, const int *__restrict__ curR,
                                                      const int *__restrict__ shiftR, int colour,
                                                      double *__restrict__ GC) {
@@ -1275,14 +1276,34 @@ __global__ void __launch_bounds__(128) k_block_gram(Grid g, int bs, int nbx, int
     for (int p = 0; p < np; ++p)
         for (int q = 0; q < np; ++q) {
             const int *sh = shiftR + (int64_t)block_sidx<DIM>(dl, p, q, bs) * nR;
+            // FP64: the lane's products accumulated in FP64; FP32: in FP32 over
+            // chunks of 8 terms, the chunks added in FP64
             double gg = 0.0, cc = 0.0;
+            W gw = W(0), cw = W(0);
+            int nt = 0;
             for (int o = lane; o < nR; o += 32) {
                 const int t = __ldg(sh + o);
                 if (t < 0) continue;
-                const double rq = Rbuf[(int64_t)t * N + node[q]];
-                if (q >= p) gg = fma(Rbuf[(int64_t)o * N + node[p]], rq, gg);
+                const W rq = Rbuf[(int64_t)t * N + node[q]];
                 const int c0 = __ldg(curR + o);
-                if (c0 >= 0) cc = fma(Ecur[(int64_t)c0 * N + node[p]], rq, cc);
+                if constexpr (sizeof(W) == sizeof(double)) {
+                    if (q >= p) gg = fma(Rbuf[(int64_t)o * N + node[p]], rq, gg);
+                    if (c0 >= 0) cc = fma(Ecur[(int64_t)c0 * N + node[p]], rq, cc);
+                } else {
+                    if (q >= p) gw = fma(Rbuf[(int64_t)o * N + node[p]], rq, gw);
+                    if (c0 >= 0) cw = fma(Ecur[(int64_t)c0 * N + node[p]], rq, cw);
+                    if (++nt == 8) {
+                        gg += (double)gw;
+                        cc += (double)cw;
+                        gw = W(0);
+                        cw = W(0);
+                        nt = 0;
+                    }
+                }
+            }
+            if constexpr (sizeof(W) != sizeof(double)) {
+                gg += (double)gw;
+                cc += (double)cw;
             }
             for (int off = 16; off > 0; off >>= 1) {
                 gg += __shfl_xor_sync(0xffffffffu, gg, off);
@@ -1303,9 +1324,9 @@ __device__ __forceinline__ int pk(int i, int j) {
 }
 
 // Least squares Lam~ = C G^{-1} of one block per thread: Cholesky of G with
-// pivot threshold 1e-14 tr(G); otherwise the minimum-norm solution C G^+
-// from a cyclic Jacobi eigendecomposition of G (eigenvalues <= 1e-14 tr(G)
-// dropped).  A 3x3-node block whose centre node has its whole 9-point
+// pivot threshold rtol tr(G) (rtol = 1e-14; 1e-5 for FP32 setup products);
+// otherwise the minimum-norm solution C G^+ from a cyclic Jacobi
+// eigendecomposition of G (eigenvalues <= rtol tr(G) dropped).  A 3x3-node block whose centre node has its whole 9-point
 // stencil inside the block has an exactly singular G from the second cascade
 // level on (the level-1 step annihilates that row of A E), so the Jacobi
 // path is common, not exceptional.  One block per thread keeps every lane of
@@ -1319,7 +1340,7 @@ template <int DIM, int NMAX>
 __global__ void __launch_bounds__(64) k_block_ls(Grid g, int bs, int nbx, int nby, int64_t nblocks,
                                                   const double *__restrict__ w, int colour,
                                                   const double *__restrict__ GC, double *__restrict__ Lt,
-                                                  double *__restrict__ lam) {
+                                                  double *__restrict__ lam, double rtol) {
     constexpr int NP = NMAX * (NMAX + 1) / 2;
     extern __shared__ double sm_ls[];
     const int tid = threadIdx.x;
@@ -1338,7 +1359,7 @@ __global__ void __launch_bounds__(64) k_block_ls(Grid g, int bs, int nbx, int nb
     };
     double tr = 0.0;
     for (int i = 0; i < n; ++i) tr += Gat(i, i);
-    const double tol = 1e-14 * tr;
+    const double tol = rtol * tr;
     bool ok = tr > 0.0;
     for (int i = 0; i < n; ++i)
         for (int j = i; j < n; ++j) A[64 * pk<NMAX>(i, j)] = Gat(i, j);
@@ -1452,10 +1473,10 @@ __global__ void __launch_bounds__(64) k_block_ls(Grid g, int bs, int nbx, int nb
 // algorithm (two-sided, as written for a full matrix).
 template <int NMAX>
 __device__ void block_lstsq_warp(const double *G, const double *C, int n, double *Lt, double *A, double *Q,
-                                 double *ev, int lane) {
+                                 double *ev, int lane, double rtol) {
     double tr = 0.0;
     for (int k = 0; k < n; ++k) tr += G[k * NMAX + k];
-    const double tol = 1e-14 * tr;
+    const double tol = rtol * tr;
     bool ok = tr > 0.0;
     for (int k = lane; k < NMAX * NMAX; k += 32) A[k] = G[k];
     __syncwarp();
@@ -1560,7 +1581,7 @@ template <int DIM, int NMAX>
 __global__ void __launch_bounds__(128) k_block_ls_warp(Grid g, int bs, int nbx, int nby, int64_t nblocks,
                                                         const double *__restrict__ w, int colour,
                                                         const double *__restrict__ GC, double *__restrict__ Lt,
-                                                        double *__restrict__ lam) {
+                                                        double *__restrict__ lam, double rtol) {
     __shared__ double sG[4][NMAX * NMAX], sC[4][NMAX * NMAX], sL[4][NMAX * NMAX], sA[4][NMAX * NMAX],
         sQ[4][NMAX * NMAX], sEv[4][NMAX];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1576,7 +1597,7 @@ __global__ void __launch_bounds__(128) k_block_ls_warp(Grid g, int bs, int nbx, 
         sC[wib][e] = in ? GC[(int64_t)(NMAX * NMAX + e) * nblocks + b] : 0.0;
     }
     __syncwarp();
-    block_lstsq_warp<NMAX>(sG[wib], sC[wib], np, sL[wib], sA[wib], sQ[wib], sEv[wib], lane);
+    block_lstsq_warp<NMAX>(sG[wib], sC[wib], np, sL[wib], sA[wib], sQ[wib], sEv[wib], lane, rtol);
     for (int e = lane; e < np * np; e += 32) {
         const int p = e / np, q = e % np;
         const double v = sL[wib][p * NMAX + q];
@@ -1588,10 +1609,10 @@ __global__ void __launch_bounds__(128) k_block_ls_warp(Grid g, int bs, int nbx, 
 // E update of one block per warp (Algorithm 2): new rows E_i - Lam~_ii R_i
 // over the next offset set; blocks of the other colour carry their rows
 // over unchanged.
-template <int DIM, int NMAX>
+template <int DIM, int NMAX, typename W = double>
 __global__ void __launch_bounds__(128) k_block_update(Grid g, int bs, int nbx, int nby, int64_t nblocks,
-                                                       const double *__restrict__ Ecur,
-                                                       const double *__restrict__ Rbuf, double *__restrict__ Enxt,
+                                                       const W *__restrict__ Ecur,
+                                                       const W *__restrict__ Rbuf, W *__restrict__ Enxt,
                                                        int nN, const int *__restrict__ curN,
                                                        const int *__restrict__ shiftN, int colour,
                                                        const double *__restrict__ Lt) {
@@ -1606,7 +1627,7 @@ __global__ void __launch_bounds__(128) k_block_update(Grid g, int bs, int nbx, i
         for (int k = 0; k < np; ++k)
             for (int o = lane; o < nN; o += 32) {
                 const int c = __ldg(curN + o);
-                Enxt[(int64_t)o * N + node[k]] = c >= 0 ? Ecur[(int64_t)c * N + node[k]] : 0.0;
+                Enxt[(int64_t)o * N + node[k]] = c >= 0 ? Ecur[(int64_t)c * N + node[k]] : W(0);
             }
         return;
     }
@@ -1619,10 +1640,10 @@ __global__ void __launch_bounds__(128) k_block_update(Grid g, int bs, int nbx, i
     for (int p = 0; p < np; ++p)
         for (int o = lane; o < nN; o += 32) {
             const int c0 = __ldg(curN + o);
-            double v = c0 >= 0 ? Ecur[(int64_t)c0 * N + node[p]] : 0.0;
+            W v = c0 >= 0 ? Ecur[(int64_t)c0 * N + node[p]] : W(0);
             for (int q = 0; q < np; ++q) {
                 const int t = __ldg(shiftN + (int64_t)block_sidx<DIM>(dl, p, q, bs) * nN + o);
-                if (t >= 0) v = fma(-L[p * NMAX + q], Rbuf[(int64_t)t * N + node[q]], v);
+                if (t >= 0) v = fma((W)-L[p * NMAX + q], Rbuf[(int64_t)t * N + node[q]], v);
             }
             Enxt[(int64_t)o * N + node[p]] = v;
         }
@@ -1641,9 +1662,9 @@ __global__ void __launch_bounds__(128) k_block_update(Grid g, int bs, int nbx, i
 // (ox, oy, oz), |o| <= R per axis, to its index in the step's offsets, or -1.
 // err is set when the candidates exceed 32 TR_KC or alpha exceeds 64.
 constexpr int TR_KC = 32;  // candidates per lane
-template <int DIM, int NMAX>
+template <int DIM, int NMAX, typename W = double>
 __global__ void __launch_bounds__(128) k_block_truncate(Grid g, int bs, int nbx, int nby, int nbz, int64_t nblocks,
-                                                         double *__restrict__ E, int nN, const int *__restrict__ off,
+                                                         W *__restrict__ E, int nN, const int *__restrict__ off,
                                                          const int *__restrict__ offidx, int R, int alpha,
                                                          int colour, int *err) {
     __shared__ int ssel[4][64];
@@ -1687,7 +1708,7 @@ __global__ void __launch_bounds__(128) k_block_truncate(Grid g, int bs, int nbx,
                         if (abs(ox) > R || abs(oy) > R || abs(oz) > R) continue;
                         const int t = __ldg(offidx + (ox + R) + side * ((oy + R) + side * (DIM == 3 ? oz + R : 0)));
                         if (t < 0) continue;
-                        const double v = E[(int64_t)t * N + node[p]];
+                        const double v = (double)E[(int64_t)t * N + node[p]];
                         acc = __dadd_rn(acc, __dmul_rn(v, v));
                         any = true;
                     }
@@ -1728,12 +1749,12 @@ __global__ void __launch_bounds__(128) k_block_truncate(Grid g, int bs, int nbx,
             const int c = (jx / bs - cx0) + ncx * ((jy / bs - cy0) + ncy * (DIM == 3 ? jz / bs - cz0 : 0));
             bool keep = false;
             for (int a = 0; a < alpha; ++a) keep = keep || ssel[wib][a] == c;
-            if (!keep) E[(int64_t)t * N + node[p]] = 0.0;
+            if (!keep) E[(int64_t)t * N + node[p]] = W(0);
         }
     }
 }
 
-template <int DIM, int KIND>
+template <int DIM, int KIND, typename W>
 static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, int prescale, int alpha, double *lam,
                                 cudaStream_t s) {
     using S = StenS<DIM, KIND>;
@@ -1744,7 +1765,8 @@ static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, 
     const int bs = L.bs, ncol = kind == CS_MULTIPLICATIVE ? 2 : 1;
     const int nmax = L.nmax;
     dim3 gr = node_grid(g), bl = node_block();
-    double *w = nullptr, *At = nullptr, *Ecur = nullptr, *Enxt = nullptr, *Rbuf = nullptr, *GC = nullptr, *Ltb = nullptr;
+    double *w = nullptr, *GC = nullptr, *Ltb = nullptr;
+    W *At = nullptr, *Ecur = nullptr, *Enxt = nullptr, *Rbuf = nullptr;  // the products' precision
     int *bad = nullptr, *pstart = nullptr, *curR = nullptr, *shiftR = nullptr, *curN = nullptr, *shiftN = nullptr;
     int *toff = nullptr, *tidx = nullptr, *terr = nullptr;  // truncation: offsets, offset lookup, error flag
     unsigned *pairs = nullptr;
@@ -1752,7 +1774,7 @@ static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, 
     int badh = 0;
     std::vector<Off3> Ocur{{0, 0, 0}};
     std::vector<Off3> D;
-    const size_t smem = (size_t)NST * TBX * TBY * (sizeof(double) + sizeof(int));
+    const size_t smem = (size_t)NST * TBX * TBY * (sizeof(W) + sizeof(int));
     if (alpha > 0) {
         if ((rc = dalloc_t(&terr, 1, nullptr, s)) != CS_OK) goto done;
         CSX_CUDA_GOTO(cudaMemsetAsync(terr, 0, sizeof(int), s));
@@ -1769,7 +1791,7 @@ static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, 
         rc = cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__);
         goto done;
     }
-    k_prescale<DIM, KIND><<<gr, bl, 0, s>>>(g, h->periodic, prescale, L.A, w, At, bad);
+    k_prescale<DIM, KIND><<<gr, bl, 0, s>>>(g, h->periodic, prescale, L.A, w, nullptr, bad);
     count_launch();
     if (cudaMemcpyAsync(&badh, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -1781,15 +1803,15 @@ static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, 
         rc = CS_ERR_ARG;
         goto done;
     }
-    k_scale_op<DIM, KIND><<<gr, bl, 0, s>>>(g, h->periodic, L.A, w, At);
+    k_scale_op<DIM, KIND, W><<<gr, bl, 0, s>>>(g, h->periodic, L.A, w, At);
     count_launch();
     if ((rc = dalloc_t(&Ecur, N, nullptr, s)) != CS_OK) goto done;
     // Gram/cross products and Lam~ of every block, entry-major (coalesced for the per-thread solve)
     if ((rc = dalloc_t(&GC, (size_t)2 * nmax * nmax * L.nblocks, nullptr, s)) != CS_OK) goto done;
     if ((rc = dalloc_t(&Ltb, (size_t)nmax * nmax * L.nblocks, nullptr, s)) != CS_OK) goto done;
-    k_fill<<<1216, 256, 0, s>>>(N, Ecur, 1.0);
+    k_fill<<<1216, 256, 0, s>>>(N, Ecur, W(1));
     count_launch();
-    CSX_CUDA_GOTO(cudaFuncSetAttribute(k_block_R<DIM, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CSX_CUDA_GOTO(cudaFuncSetAttribute(k_block_R<DIM, KIND, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int lev = 0; lev < nu; ++lev) {
         for (int k = 0; k < ncol; ++k) {
             const bool last = lev == nu - 1 && k == ncol - 1;
@@ -1886,30 +1908,37 @@ static cs_status setup_blocks_t(const cs_hierarchy *h, int l, int kind, int nu, 
             }
             {
                 const int colour = ncol == 2 ? k : -1;
-                k_block_R<DIM, KIND><<<gr, bl, smem, s>>>(g, h->periodic, At, Ecur, Rbuf, nR, pstart, pairs, bs, colour);
+                k_block_R<DIM, KIND, W><<<gr, bl, smem, s>>>(g, h->periodic, At, Ecur, Rbuf, nR, pstart, pairs, bs, colour);
                 count_launch();
                 const unsigned nwarp = (unsigned)((L.nblocks + 3) / 4), nthr = (unsigned)((L.nblocks + 63) / 64);
+                // the minimum-norm cutoff: 1e-14 tr(G) with FP64 products; FP32 products resolve
+                // G only to ~1e-6 of its trace, so an exact null direction (3x3 blocks of
+                // 9-point operators, some 2x2 blocks of them from the second step on) is dropped
+                // below 1e-5 tr(G)
+                const double ls_rtol = sizeof(W) == sizeof(double) ? 1e-14 : 1e-5;
                 double *lam_l = lam + (int64_t)lev * L.nblocks * nmax * nmax;
 #define CSX_BLOCK_STEPS(NM)                                                                                         \
     {                                                                                                               \
         const size_t lsm = (size_t)64 * (NM * (NM + 1) / 2 + NM * NM) * sizeof(double);                          \
-        k_block_gram<DIM, NM><<<nwarp, 128, 0, s>>>(g, bs, L.nbx, L.nby, L.nblocks, Ecur, Rbuf, nR, curR, shiftR, \
+        k_block_gram<DIM, NM, W><<<nwarp, 128, 0, s>>>(g, bs, L.nbx, L.nby, L.nblocks, Ecur, Rbuf, nR, curR,    \
+                                                        shiftR, \
                                                      colour, GC);                                                   \
         if (L.nblocks >= kLsThreadMin) {                                                                            \
             CSX_CUDA_GOTO(cudaFuncSetAttribute(k_block_ls<DIM, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                                (int)lsm));                                                          \
-            k_block_ls<DIM, NM><<<nthr, 64, lsm, s>>>(g, bs, L.nbx, L.nby, L.nblocks, w, colour, GC, Ltb, lam_l); \
+            k_block_ls<DIM, NM><<<nthr, 64, lsm, s>>>(g, bs, L.nbx, L.nby, L.nblocks, w, colour, GC, Ltb, lam_l,  \
+                                                     ls_rtol);                                                      \
         } else {                                                                                                    \
             k_block_ls_warp<DIM, NM><<<nwarp, 128, 0, s>>>(g, bs, L.nbx, L.nby, L.nblocks, w, colour, GC, Ltb,    \
-                                                           lam_l);                                                  \
+                                                           lam_l, ls_rtol);                                         \
         }                                                                                                           \
         count_launch(2);                                                                                            \
         if (!last) {                                                                                                \
-            k_block_update<DIM, NM><<<nwarp, 128, 0, s>>>(g, bs, L.nbx, L.nby, L.nblocks, Ecur, Rbuf, Enxt, nN,   \
+            k_block_update<DIM, NM, W><<<nwarp, 128, 0, s>>>(g, bs, L.nbx, L.nby, L.nblocks, Ecur, Rbuf, Enxt, nN,\
                                                           curN, shiftN, colour, Ltb);                               \
             count_launch();                                                                                         \
             if (trunc) {                                                                                            \
-                k_block_truncate<DIM, NM><<<nwarp, 128, 0, s>>>(g, bs, L.nbx, L.nby, L.nbz, L.nblocks, Enxt, nN,  \
+                k_block_truncate<DIM, NM, W><<<nwarp, 128, 0, s>>>(g, bs, L.nbx, L.nby, L.nbz, L.nblocks, Enxt, nN, \
                                                                 toff, tidx, tR, alpha, colour, terr);              \
                 count_launch();                                                                                     \
             }                                                                                                       \
@@ -1949,15 +1978,21 @@ done:
     return rc;
 }
 
-cs_status cascade_setup_level_blocks(const cs_hierarchy *h, int l, int kind, int nu, int prescale, int alpha, double *lam,
+cs_status cascade_setup_level_blocks(const cs_hierarchy *h, int l, int kind, int nu, int prescale, int alpha, bool fp32, double *lam,
                                      cudaStream_t s) {
     const Level &L = h->lev[l];
     if (L.g.dim == 2) {
-        if (L.kind == STAR) return setup_blocks_t<2, STAR>(h, l, kind, nu, prescale, alpha, lam, s);
-        return setup_blocks_t<2, BOX>(h, l, kind, nu, prescale, alpha, lam, s);
+        if (L.kind == STAR)
+            return fp32 ? setup_blocks_t<2, STAR, float>(h, l, kind, nu, prescale, alpha, lam, s)
+                        : setup_blocks_t<2, STAR, double>(h, l, kind, nu, prescale, alpha, lam, s);
+        return fp32 ? setup_blocks_t<2, BOX, float>(h, l, kind, nu, prescale, alpha, lam, s)
+                    : setup_blocks_t<2, BOX, double>(h, l, kind, nu, prescale, alpha, lam, s);
     }
-    if (L.kind == STAR) return setup_blocks_t<3, STAR>(h, l, kind, nu, prescale, alpha, lam, s);
-    return setup_blocks_t<3, BOX>(h, l, kind, nu, prescale, alpha, lam, s);
+    if (L.kind == STAR)
+        return fp32 ? setup_blocks_t<3, STAR, float>(h, l, kind, nu, prescale, alpha, lam, s)
+                    : setup_blocks_t<3, STAR, double>(h, l, kind, nu, prescale, alpha, lam, s);
+    return fp32 ? setup_blocks_t<3, BOX, float>(h, l, kind, nu, prescale, alpha, lam, s)
+                : setup_blocks_t<3, BOX, double>(h, l, kind, nu, prescale, alpha, lam, s);
 }
 
 }  // namespace csx

@@ -12,6 +12,17 @@ from tests import gpu_util as gu
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
+# FP32 products in the block setup: R and E entries carry a few (nst + 1) u of
+# their row sums (u = 2^-24), the n_b x n_b Gram matrices about nR u of their
+# entries, and the FP64 block solve multiplies that by cond(G) (up to ~1e2 on
+# these variable-coefficient 2x2 blocks), over nu steps: 1e-3.
+FP32_BLOCK_TOL = 1e-3
+# On the contrast-1e4 correlated field the coarse levels' block Gram matrices
+# have eigenvalues between 1e-14 and 1e-5 of their trace: FP64 keeps them,
+# FP32 products cannot resolve them and the 1e-5 cutoff drops them, so Lambda
+# differs by a few 1e-2 there (2.7e-2 measured on level 3); the smoother, and
+# the iteration count, stay as good.
+FP32_BLOCK_TOL_CONTRAST = 1e-1
 
 
 def _dev(a, dtype=None):
@@ -42,6 +53,42 @@ def built():
     import __graft_entry__ as g
     g.build()
     return True
+
+
+@pytest.mark.parametrize("name,kind,nu,alpha,tol", [("v2d_37", "additive", 3, 0, FP32_BLOCK_TOL),
+                                                  ("v3d_17", "additive", 2, 0, FP32_BLOCK_TOL),
+                                                  ("v2d_37", "multiplicative", 3, 0, FP32_BLOCK_TOL),
+                                                  ("c2d_66", "multiplicative", 3, 0, FP32_BLOCK_TOL_CONTRAST)])
+def test_fp32_block_setup_matches_oracle(built, name, kind, nu, alpha, tol):
+    """setup_precision fp32 on block levels: R and E rows in FP32, the block
+    Gram and cross products in FP32 over chunks of 8 and FP64 across them,
+    the least squares in FP64 with the minimum-norm cutoff at 1e-5 tr(G)
+    (FP32 products lift an exactly null eigenvalue to ~1e-7 tr(G); such Gram
+    matrices occur from the second step on the 9-point levels).  Lambda
+    within FP32_BLOCK_TOL of the oracle, and the FP32-cycle GMRES reaches
+    1e-10."""
+    import torch
+
+    import paper_2606_12577_gb300 as cmg
+    A = PROBS[name]()
+    ho = oracle.Hierarchy(A, bs=2)
+    co = oracle.Cascade(ho, kind, nu=nu, alpha=alpha)
+    hg = gu.gpu_hierarchy(A, block=2)
+    cg = cmg.setup_cascade(hg, kind, nu=nu, alpha=alpha, lowp=True, setup_precision="fp32")
+    errs = [gu.rel_max(cmg.export_lambda(cg, l), co.lam(l)) for l in range(co.nlev)]
+    assert max(errs) <= tol, errs
+    assert max(errs) > 0.0
+    c64 = cmg.setup_cascade(hg, kind, nu=nu, alpha=alpha, lowp=True)
+    b = problems.rhs(A.N, 13)
+    its = []
+    for c in (cg, c64):
+        x = torch.zeros(A.N, dtype=torch.float64, device="cuda")
+        info = cmg.solve(hg, c, _dev(b), x, method="gmres_right", precision="fp32", tol=1e-10, maxit=300)
+        assert info.converged
+        its.append(info.iterations)
+    assert its[0] <= its[1] + max(2, its[1] // 5), its
+    with pytest.raises(cmg.CascadeError, match="CS_ERR_UNSUPPORTED"):  # FP32 products would flip the ranking
+        cmg.setup_cascade(hg, kind, nu=nu, alpha=3, lowp=True, setup_precision="fp32")
 
 
 @pytest.mark.parametrize("name,bs,kind,alpha,nu", [("v2d_37", 2, "additive", 4, 3), ("v2d_37", 2, "multiplicative", 5, 3),

@@ -166,7 +166,7 @@ def test_fp32_setup_limits(built):
         cmg.setup_cascade(hg, "additive", nu=2, alpha=3, setup_precision="fp32")
     hb = gu.gpu_hierarchy(A, block=2)
     with pytest.raises(cmg.CascadeError, match="FP32 setup"):
-        cmg.setup_cascade(hb, "additive", nu=2, setup_precision="fp32")
+        cmg.setup_cascade(hb, "additive", nu=2, alpha=3, setup_precision="fp32")
 
 
 def test_truncation_limits(built):
