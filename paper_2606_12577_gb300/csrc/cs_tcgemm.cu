@@ -256,6 +256,149 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     }
 }
 
+// Persistent form for large products (no K split): one CTA per SM walks the
+// 128 x BN tiles (tile t: M block t / tn, N block t % tn) in a grid-stride
+// loop, with three roles.  Warp 0 lane 0 streams the operand boxes of every
+// (tile, K block) through the 4-stage ring; warp 1 lane 0 issues the MMAs
+// into one of two TMEM accumulators (2 BN columns) and commits each stage
+// to its "empty" barrier and each finished tile to its accumulator's "full"
+// barrier; warps 2-5 read a finished accumulator back (warp w owns TMEM
+// lanes 32 (w mod 4) ..), apply the epilogue and release the accumulator, so
+// the epilogue of one tile overlaps the products of the next.  Every wait is
+// bounded: on expiry *err is raised and the role stops, and all roles reach
+// the final barrier.
+template <int BN>
+__global__ void __launch_bounds__(192, 1) k_tc_gemm_persistent(const __grid_constant__ CUtensorMap ma,
+                                                               const __grid_constant__ CUtensorMap mb, TcArgs a,
+                                                               int tn, int ntiles) {
+    constexpr int NB = BN / 128;
+    constexpr int BTILE = NB * TC_TILE_BYTES;
+    constexpr uint32_t IDESC = tc_idesc<BN>();
+    extern __shared__ uint8_t tc_smem_raw[];
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2], done;
+    __shared__ uint32_t tmem_slot;
+    const uint32_t raw = smem_u32(tc_smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t sA = base, sB = base + TC_STAGES * TC_TILE_BYTES;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int c = 0; c < 2; ++c) {
+            mbar_init(smem_u32(&tfull[c]), 1);
+            mbar_init(smem_u32(&tempty[c]), 4);  // one arrival per epilogue warp
+        }
+        mbar_init(smem_u32(&done), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(2 * BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const int nkb = a.nkb;
+    if (warp == 0) {
+        if (lane == 0) {  // producer
+            int64_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int m0 = (t / tn) * TC_BM, n0 = (t % tn) * BN;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = (int)(it % TC_STAGES);
+                    if (it >= TC_STAGES &&
+                        !mbar_wait(smem_u32(&empty[s]), (uint32_t)((it / TC_STAGES - 1) & 1))) { ok = false; break; }
+                    const uint32_t fb = smem_u32(&full[s]);
+                    mbar_expect_tx(fb, TC_TILE_BYTES + BTILE);
+                    tma_load_2d(sA + s * TC_TILE_BYTES, &ma, kb * TC_BK, m0, fb);
+#pragma unroll
+                    for (int h = 0; h < NB; ++h)
+                        tma_load_2d(sB + s * BTILE + h * TC_TILE_BYTES, &mb, kb * TC_BK, n0 + 128 * h, fb);
+                }
+            }
+            if (!ok) atomicExch(a.err, 1);
+            // the copies of the last stages land before the CTA exits
+            for (int64_t k = std::max<int64_t>(0, it - TC_STAGES); k < it; ++k)
+                mbar_wait(smem_u32(&full[k % TC_STAGES]), (uint32_t)((k / TC_STAGES) & 1));
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issue
+            int64_t it = 0;
+            int tc = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tc) {
+                const int c = tc & 1;
+                if (tc >= 2 && !mbar_wait(smem_u32(&tempty[c]), (uint32_t)(((tc >> 1) - 1) & 1))) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc = tmem + (uint32_t)(c * BN);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = (int)(it % TC_STAGES);
+                    if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((it / TC_STAGES) & 1))) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < TC_BK / 16; ++j)
+                        mma_bf16(acc, sw128_desc(sA + s * TC_TILE_BYTES + 32 * j), sw128_desc(sB + s * BTILE + 32 * j),
+                                 IDESC, (kb > 0 || j > 0) ? 1u : 0u);
+                    mma_commit(smem_u32(&empty[s]));
+                }
+                mma_commit(smem_u32(&tfull[c]));
+            }
+            if (!ok) atomicExch(a.err, 1);
+            // every product issued has completed before the accumulators are freed
+            mma_commit(smem_u32(&done));
+            if (!mbar_wait(smem_u32(&done), 0u)) atomicExch(a.err, 1);
+        }
+        __syncwarp();
+    } else {  // epilogue warps 2..5
+        const int quad = warp & 3;
+        int tc = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc) {
+            const int c = tc & 1;
+            const bool got = mbar_wait(smem_u32(&tfull[c]), (uint32_t)((tc >> 1) & 1));
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) atomicExch(a.err, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m0 = (t / tn) * TC_BM, n0 = (t % tn) * BN;
+            const int row = m0 + quad * 32 + lane;
+            for (int cc = 0; cc < BN; cc += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * BN + cc), v);
+                if (row >= a.M) continue;
+                float *out = a.C + (int64_t)row * a.ldc;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int n = n0 + cc + i;
+                    if (n >= a.N) continue;
+                    float x = v[i];
+                    if (a.bias) x += a.bias[n];
+                    if (a.Z) a.Z[(int64_t)row * a.ldc + n] = x;
+                    if (a.relu) x = fmaxf(x, 0.f);
+                    out[n] = x;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[c])) : "memory");
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+    }
+}
+
 // sum of the split partials in split order, then the epilogue
 __global__ void k_tc_reduce(int M, int N, int splits, const float *__restrict__ P, float *__restrict__ C, int ldc,
                             const float *__restrict__ bias, int relu, float *__restrict__ Z) {
@@ -302,7 +445,11 @@ cudaError_t g_attr_err = cudaSuccess;
 
 template <int BN>
 void tc_launch(const TcOperand &A, const TcOperand &B, const TcArgs &a, int tn, int tm, int splits, cudaStream_t s) {
-    k_tc_gemm<BN><<<dim3(tn, tm, splits), 128, tc_smem<BN>(), s>>>(A.map, B.map, a);
+    const int ntiles = tn * tm;
+    if (splits == 1 && ntiles >= 2 * 152)  // enough tiles that a CTA per SM overlaps its epilogues
+        k_tc_gemm_persistent<BN><<<152, 192, tc_smem<BN>(), s>>>(A.map, B.map, a, tn, ntiles);
+    else
+        k_tc_gemm<BN><<<dim3(tn, tm, splits), 128, tc_smem<BN>(), s>>>(A.map, B.map, a);
 }
 }  // namespace
 
@@ -375,6 +522,12 @@ cs_status tc_gemm(const TcOperand &A, const TcOperand &B, int M, int N, int64_t 
         if (g_attr_err == cudaSuccess)
             g_attr_err =
                 cudaFuncSetAttribute(k_tc_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem<256>());
+        if (g_attr_err == cudaSuccess)
+            g_attr_err = cudaFuncSetAttribute(k_tc_gemm_persistent<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              tc_smem<128>());
+        if (g_attr_err == cudaSuccess)
+            g_attr_err = cudaFuncSetAttribute(k_tc_gemm_persistent<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              tc_smem<256>());
     });
     CSX_CUDA(g_attr_err);
     const int bn = N > 128 ? 256 : 128;  // one MMA of N = 256 per K step when the columns need it

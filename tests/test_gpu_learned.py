@@ -26,14 +26,16 @@ def built():
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 243, 232), (4096, 128, 512), (130, 20, 8), (256, 256, 1024),
-                                   (1000, 300, 200), (640, 512, 4096)])
+                                   (1000, 300, 200), (640, 512, 4096), (4096, 2560, 256), (39000, 100, 72)])
 def test_tc_gemm_matches_bf16_products(built, M, N, K):
     """The tcgen05 GEMM (TMA-staged 128 x 64 boxes, 128-byte swizzle, FP32
     accumulator in tensor memory; 128 x 128 tiles, or 128 x 256 when N > 128)
     against the exact products of the same BF16 values in FP64: every entry
     within the FP32 accumulation bound K 2^-24 sum_k |a_ik| |b_jk| (ragged M,
     N and K exercise the zero-filled tile edges, N = 300 a second 256-wide
-    tile whose upper box starts past the last row)."""
+    tile whose upper box starts past the last row; the last two shapes have
+    enough tiles for the persistent kernel, with two TMEM accumulators, in
+    128 x 256 and ragged 128 x 128 tiles)."""
     import torch
 
     import paper_2606_12577_gb300 as cmg
