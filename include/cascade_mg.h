@@ -441,9 +441,12 @@ cs_status cs_mlp_create(int nin, int nhid, int nout, int max_batch, uint64_t see
  * matrices A and B, row-major with K contiguous, FP32 accumulation: the
  * tcgen05 tensor-core GEMM of the learned setup (128 x 128 tiles, TMA-staged
  * 128 x 64 operand tiles with the 128-byte swizzle, the accumulator in tensor
- * memory).  K a multiple of 8 (16-byte rows), A and B 16-byte aligned.
- * Synchronises the stream.  Errors: CS_ERR_ARG, CS_ERR_CUDA, CS_ERR_TIMEOUT
- * (a bounded wait of the kernel expired; the context stays usable). */
+ * memory).  K a multiple of 8 (16-byte rows), A and B 16-byte aligned, all
+ * three on the current device.  Products with at least two tiles per SM run
+ * persistent (one CTA per SM, two TMEM accumulators).  Synchronises the
+ * stream.  Errors: CS_ERR_ARG (shapes, alignment, memory not of the current
+ * device), CS_ERR_CUDA, CS_ERR_TIMEOUT (a bounded wait of the kernel expired;
+ * the context stays usable). */
 cs_status cs_tc_gemm_bf16(int M, int N, int K, const void *A, const void *B, float *C, cs_stream stream);
 void cs_mlp_destroy(cs_mlp *m);
 int64_t cs_mlp_nparam(const cs_mlp *m);

@@ -572,11 +572,32 @@ cs_status cs_tc_gemm_bf16(int M, int N, int K, const void *A, const void *B, flo
         return CS_ERR_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    static int *err = nullptr;
-    static std::once_flag once;
-    static cudaError_t alloc_err = cudaSuccess;
-    std::call_once(once, [] { alloc_err = cudaMalloc(&err, sizeof(int)); });
-    CSX_CUDA(alloc_err);
+    int dev = 0;
+    CSX_CUDA(cudaGetDevice(&dev));
+    const void *ptrs[3] = {A, B, C};
+    const char *names[3] = {"A", "B", "C"};
+    for (int k = 0; k < 3; ++k) {  // the operands must be memory of the current device
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, ptrs[k]) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cs_tc_gemm_bf16: %s is not a CUDA device pointer", names[k]);
+            return CS_ERR_ARG;
+        }
+        if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev) {
+            set_error("cs_tc_gemm_bf16: %s must be device memory of the current device %d", names[k], dev);
+            return CS_ERR_ARG;
+        }
+    }
+    // one wait-expiry flag per device, allocated on first use there
+    static int *errs[64] = {};
+    static std::mutex mu;
+    if (dev < 0 || dev >= 64) { set_error("device ordinal %d unsupported", dev); return CS_ERR_UNSUPPORTED; }
+    int *err = nullptr;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        if (!errs[dev]) CSX_CUDA(cudaMalloc(&errs[dev], sizeof(int)));
+        err = errs[dev];
+    }
     TcOperand a, b;
     a.p = (__nv_bfloat16 *)A; a.rows = M; a.kw = K;
     b.p = (__nv_bfloat16 *)B; b.rows = N; b.kw = K;

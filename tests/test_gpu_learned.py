@@ -50,6 +50,16 @@ def test_tc_gemm_matches_bf16_products(built, M, N, K):
     assert np.all(np.abs(C - ref) <= bound), float(np.max(np.abs(C - ref) / bound))
 
 
+def test_tc_gemm_rejects_memory_off_the_device(built):
+    """The C entry checks its operands before any launch: host memory is
+    refused with CS_ERR_ARG."""
+    from paper_2606_12577_gb300 import _capi
+    a = np.zeros((128, 64), dtype=np.uint16)
+    c = np.zeros((128, 128), dtype=np.float32)
+    st = _capi.lib().cs_tc_gemm_bf16(128, 128, 64, a.ctypes.data, a.ctypes.data, c.ctypes.data, None)
+    assert st == _capi.CS_ERR_ARG
+
+
 def test_features_and_targets_match_oracle(built):
     import paper_2606_12577_gb300 as cmg
     A = problems.q1_jittered(23, 4)
