@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
     __shared__ uint32_t tmem_slot;
     __shared__ int failed;
+    __shared__ float stile[4][32][33];  // per warp: a 32 x 32 chunk of C, padded against bank conflicts
     const uint32_t raw = smem_u32(tc_smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // the 128-byte swizzle wants 1024-byte aligned tiles
     const uint32_t sA = base, sB = base + TC_STAGES * TC_TILE_BYTES;
@@ -221,31 +222,31 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     const int all_ok = __syncthreads_and(got ? 1 : 0);
     if (!all_ok && threadIdx.x == 0) atomicExch(a.err, 1);
     if (all_ok && !failed && nk > 0) {
-        const int row = m0 + warp * 32 + lane;
+        // each 32 x 32 chunk goes through shared memory, so that every row of
+        // it leaves as one 128-byte segment (lane = column)
+        float(*tile)[33] = stile[warp];
         for (int c = 0; c < BN; c += 32) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            if (row >= a.M) continue;
-            if (a.partial) {
-                float *out = a.C + ((int64_t)blockIdx.z * a.M + row) * a.N;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int n = n0 + c + i;
-                    if (n < a.N) out[n] = v[i];
-                }
-            } else {
-                float *out = a.C + (int64_t)row * a.ldc;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int n = n0 + c + i;
-                    if (n >= a.N) continue;
-                    float x = v[i];
-                    if (a.bias) x += a.bias[n];
+            for (int i = 0; i < 32; ++i) tile[lane][i] = v[i];
+            __syncwarp();
+            const int n = n0 + c + lane;
+            const float bn = (!a.partial && a.bias && n < a.N) ? a.bias[n] : 0.f;
+            for (int r = 0; r < 32; ++r) {
+                const int row = m0 + warp * 32 + r;
+                if (row >= a.M || n >= a.N) continue;
+                float x = tile[r][lane];
+                if (a.partial) {
+                    a.C[((int64_t)blockIdx.z * a.M + row) * a.N + n] = x;
+                } else {
+                    if (a.bias) x += bn;
                     if (a.Z) a.Z[(int64_t)row * a.ldc + n] = x;
                     if (a.relu) x = fmaxf(x, 0.f);
-                    out[n] = x;
+                    a.C[(int64_t)row * a.ldc + n] = x;
                 }
             }
+            __syncwarp();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -277,6 +278,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_persistent(const __grid_cons
     extern __shared__ uint8_t tc_smem_raw[];
     __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2], done;
     __shared__ uint32_t tmem_slot;
+    __shared__ float stile[4][32][33];  // per epilogue warp: a 32 x 32 chunk, padded against bank conflicts
     const uint32_t raw = smem_u32(tc_smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const uint32_t sA = base, sB = base + TC_STAGES * TC_TILE_BYTES;
@@ -369,22 +371,25 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_persistent(const __grid_cons
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int m0 = (t / tn) * TC_BM, n0 = (t % tn) * BN;
-            const int row = m0 + quad * 32 + lane;
+            float(*tile)[33] = stile[warp - 2];
             for (int cc = 0; cc < BN; cc += 32) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * BN + cc), v);
-                if (row >= a.M) continue;
-                float *out = a.C + (int64_t)row * a.ldc;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int n = n0 + cc + i;
-                    if (n >= a.N) continue;
-                    float x = v[i];
-                    if (a.bias) x += a.bias[n];
+                for (int i = 0; i < 32; ++i) tile[lane][i] = v[i];  // lane = row of the chunk
+                __syncwarp();
+                const int n = n0 + cc + lane;  // lane = column: every row goes out as one 128-byte segment
+                const float bn = (a.bias && n < a.N) ? a.bias[n] : 0.f;
+                for (int r = 0; r < 32; ++r) {
+                    const int row = m0 + quad * 32 + r;
+                    if (row >= a.M || n >= a.N) continue;
+                    float x = tile[r][lane];
+                    if (a.bias) x += bn;
                     if (a.Z) a.Z[(int64_t)row * a.ldc + n] = x;
                     if (a.relu) x = fmaxf(x, 0.f);
-                    out[n] = x;
+                    a.C[(int64_t)row * a.ldc + n] = x;
                 }
+                __syncwarp();
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
