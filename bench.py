@@ -77,7 +77,7 @@ def args_():
     p.add_argument("--batch-profile-count", type=int, default=16, help="problems in the batch profile case")
     p.add_argument("--profile", default="",
                    choices=["", "setup", "step", "step16", "sweep", "multirhs", "blocksetup", "batch", "general",
-                            "overlap", "sketch", "mlp"],
+                            "overlap", "sketch", "mlp", "tcgemm"],
                    help="run one untimed setup (or setup + solve) and exit: the case ncu captures")
     return p.parse_args()
 
@@ -870,6 +870,16 @@ def main():
             cmg.gsweep(hg, cg, 0, k % 2, bg, xg[k % 2], xg[(k + 1) % 2])
         torch.cuda.synchronize()
         print(json.dumps({"profile": a.profile, "n": nq, "launches": cmg.kernel_launches()}), flush=True)
+        return
+
+    if a.profile == "tcgemm":  # three 8192^3 BF16 products on the tensor cores (the persistent kernel)
+        g = torch.Generator(device=dev).manual_seed(3)
+        At = torch.randn(8192, 8192, device=dev, generator=g).to(torch.bfloat16)
+        Bt = torch.randn(8192, 8192, device=dev, generator=g).to(torch.bfloat16)
+        for _ in range(3):
+            cmg.tc_gemm_bf16(At, Bt)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": a.profile, "launches": cmg.kernel_launches()}), flush=True)
         return
 
     if a.profile == "mlp":  # five training steps of the learned-setup network at batch 4096 (tensor-core GEMMs)
