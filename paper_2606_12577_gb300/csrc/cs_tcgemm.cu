@@ -258,8 +258,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
 }
 
 // Persistent form for large products (no K split): one CTA per SM walks the
-// 128 x BN tiles (tile t: M block t / tn, N block t % tn) in a grid-stride
-// loop, with three roles.  Warp 0 lane 0 streams the operand boxes of every
+// 128 x BN tiles in a grid-stride loop, in groups of 16 M blocks with the M
+// block fastest inside a group (the tiles in flight share their A and B panels
+// in L2), with three roles.  Warp 0 lane 0 streams the operand boxes of every
 // (tile, K block) through the 4-stage ring; warp 1 lane 0 issues the MMAs
 // into one of two TMEM accumulators (2 BN columns) and commits each stage
 // to its "empty" barrier and each finished tile to its accumulator's "full"
@@ -268,6 +269,15 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
 // the epilogue of one tile overlaps the products of the next.  Every wait is
 // bounded: on expiry *err is raised and the role stops, and all roles reach
 // the final barrier.
+// tile t -> (M block, N block) in groups of TC_GROUP M blocks
+constexpr int TC_GROUP = 16;
+__device__ __forceinline__ void tc_tile(int t, int tn, int tm, int &mb, int &nb) {
+    const int per = TC_GROUP * tn, grp = t / per, first = grp * TC_GROUP;
+    const int gsize = min(TC_GROUP, tm - first), r = t - grp * per;
+    mb = first + r % gsize;
+    nb = r / gsize;
+}
+
 template <int BN>
 __global__ void __launch_bounds__(192, 1) k_tc_gemm_persistent(const __grid_constant__ CUtensorMap ma,
                                                                const __grid_constant__ CUtensorMap mb, TcArgs a,
@@ -312,7 +322,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_persistent(const __grid_cons
             int64_t it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const int m0 = (t / tn) * TC_BM, n0 = (t % tn) * BN;
+                int mbk, nbk;
+                tc_tile(t, tn, ntiles / tn, mbk, nbk);
+                const int m0 = mbk * TC_BM, n0 = nbk * BN;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = (int)(it % TC_STAGES);
                     if (it >= TC_STAGES &&
@@ -370,7 +382,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_persistent(const __grid_cons
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int m0 = (t / tn) * TC_BM, n0 = (t % tn) * BN;
+            int mbk, nbk;
+            tc_tile(t, tn, ntiles / tn, mbk, nbk);
+            const int m0 = mbk * TC_BM, n0 = nbk * BN;
             float(*tile)[33] = stile[warp - 2];
             for (int cc = 0; cc < BN; cc += 32) {
                 float v[32];
