@@ -28,7 +28,6 @@ struct cs_mlp {
     int nin = 0, nhid = 0, nout = 0, max_batch = 0;
     int64_t nparam = 0;
     float *p = nullptr;          // FP32 master parameters: W1 b1 W2 b2 W3 b3
-    __nv_bfloat16 *w16 = nullptr;  // BF16 copies of W1, W2, W3
     float *g = nullptr;          // gradients (same layout as p)
     float *m = nullptr, *v = nullptr;  // Adam moments
     float *z1 = nullptr, *z2 = nullptr, *h1 = nullptr, *h2 = nullptr, *y = nullptr;  // activations
@@ -38,7 +37,7 @@ struct cs_mlp {
     int64_t step = 0;
     int64_t bytes = 0;
     // offsets into p / g
-    int64_t oW1, ob1, oW2, ob2, oW3, ob3, o16W1, o16W2, o16W3;
+    int64_t oW1, ob1, oW2, ob2, oW3, ob3;
     // tensor-core operands (K contiguous, K padded to 64 per segment): the
     // forward pass, the input gradients, and the weight gradients (K = batch)
     int kin = 0, khid = 0, kout = 0, kb = 0;
@@ -121,22 +120,11 @@ __global__ void k_adam(int64_t n, float *__restrict__ p, const float *__restrict
     }
 }
 
-__global__ void k_to_bf16(int64_t n, const float *__restrict__ a, __nv_bfloat16 *__restrict__ o) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        o[i] = __float2bfloat16_rn(a[i]);
-}
-
-// the BF16 weights (round to nearest even of the FP32 masters): the plain
-// copies and the tensor-core operands W_l (forward) and W_l^T (input
-// gradients), each entering two K segments so that it meets both halves of
-// the activations' hi + lo pairs
+// the BF16 weights (round to nearest even of the FP32 masters) as the
+// tensor-core operands W_l (forward) and W_l^T (input gradients), each
+// entering two K segments so that it meets both halves of the activations'
+// hi + lo pairs
 static cs_status refresh_bf16(cs_mlp *M, cudaStream_t s) {
-    const int64_t n1 = (int64_t)M->nhid * M->nin, n2 = (int64_t)M->nhid * M->nhid, n3 = (int64_t)M->nout * M->nhid;
-    k_to_bf16<<<256, 256, 0, s>>>(n1, M->p + M->oW1, M->w16 + M->o16W1);
-    k_to_bf16<<<256, 256, 0, s>>>(n2, M->p + M->oW2, M->w16 + M->o16W2);
-    k_to_bf16<<<256, 256, 0, s>>>(n3, M->p + M->oW3, M->w16 + M->o16W3);
-    count_launch(3);
-    CSX_CUDA(cudaGetLastError());
     CSX_TRY(tc_pack(M->tW1, M->nhid, M->nin, M->kin, "hh", M->p + M->oW1, M->nin, false, s));
     CSX_TRY(tc_pack(M->tW2, M->nhid, M->nhid, M->khid, "hh", M->p + M->oW2, M->nhid, false, s));
     CSX_TRY(tc_pack(M->tW3, M->nout, M->nhid, M->khid, "hh", M->p + M->oW3, M->nhid, false, s));
@@ -367,8 +355,6 @@ cs_status cs_mlp_create(int nin, int nhid, int nout, int max_batch, uint64_t see
     M->oW2 = M->ob1 + nhid; M->ob2 = M->oW2 + (int64_t)nhid * nhid;
     M->oW3 = M->ob2 + nhid; M->ob3 = M->oW3 + (int64_t)nout * nhid;
     M->nparam = M->ob3 + nout;
-    M->o16W1 = 0; M->o16W2 = (int64_t)nhid * nin; M->o16W3 = M->o16W2 + (int64_t)nhid * nhid;
-    const int64_t nw16 = M->o16W3 + (int64_t)nout * nhid;
     cudaStream_t s = 0;
     cs_status rc = CS_OK;
     const int64_t B = max_batch;
@@ -386,7 +372,6 @@ cs_status cs_mlp_create(int nin, int nhid, int nout, int max_batch, uint64_t see
     if ((rc = dalloc_t(&M->g, M->nparam, &M->bytes)) != CS_OK) goto fail;
     if ((rc = dalloc_t(&M->m, M->nparam, &M->bytes)) != CS_OK) goto fail;
     if ((rc = dalloc_t(&M->v, M->nparam, &M->bytes)) != CS_OK) goto fail;
-    if ((rc = dalloc_t(&M->w16, nw16, &M->bytes)) != CS_OK) goto fail;
     if ((rc = dalloc_t(&M->z1, B * nhid, &M->bytes)) != CS_OK) goto fail;
     if ((rc = dalloc_t(&M->z2, B * nhid, &M->bytes)) != CS_OK) goto fail;
     if ((rc = dalloc_t(&M->h1, B * nhid, &M->bytes)) != CS_OK) goto fail;
@@ -438,7 +423,7 @@ fail:
 
 void cs_mlp_destroy(cs_mlp *M) {
     if (!M) return;
-    dfree(M->p); dfree(M->g); dfree(M->m); dfree(M->v); dfree(M->w16);
+    dfree(M->p); dfree(M->g); dfree(M->m); dfree(M->v);
     dfree(M->z1); dfree(M->z2); dfree(M->h1); dfree(M->h2); dfree(M->d1); dfree(M->d2); dfree(M->y); dfree(M->dy);
     dfree(M->loss);
     for (csx::TcOperand *o : {&M->tX, &M->tW1, &M->tH1, &M->tW2, &M->tH2, &M->tW3, &M->tDY, &M->tW3T, &M->tD2,
