@@ -16,6 +16,7 @@ symmetry, Galerkin stencils, special cases, convergence).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -92,6 +93,7 @@ def _load():
             "ora_casc_create_sketch": (P, [P, I, I, I, I, C.c_uint64, I]),
             "ora_rademacher": (D, [C.c_uint64, I, L, I, I]),
             "ora_max_threads": (I, []),
+            "ora_plant": (None, [I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -111,6 +113,25 @@ def block_priority(seed: int, level: int, b: int) -> int:
     """Priority of block b of a level in the greedy colouring (SplitMix64
     output at counter level 2^40 + b of the stream seeded with `seed`)."""
     return int(_load().ora_block_prio(int(seed) & 0xFFFFFFFFFFFFFFFF, level, b))
+
+
+# the planted mistakes of cs_oracle.c, in the order of its enum (ids 1, 2, ...)
+PLANTS = ("prescale_off", "update_sign", "lambda_t", "smooth_t", "colour_order", "reverse_order",
+          "smooth_sign", "interp_one_sided", "restrict_unscaled", "coarse_chol", "trunc_smallest",
+          "minnorm_off", "overlap_sum", "stokes_q2", "spd_no_upper", "pcg_beta", "greedy_ascending",
+          "sketch_stale")
+
+
+@contextlib.contextmanager
+def planted(name: str):
+    """Inside the block the oracle takes one known-wrong step (tests only,
+    to show that the pins reject it); outside it every step is as stated."""
+    lib = _load()
+    lib.ora_plant(PLANTS.index(name) + 1)
+    try:
+        yield
+    finally:
+        lib.ora_plant(0)
 
 
 def set_threads(n: int) -> None:

@@ -29,6 +29,10 @@
  *
  * No blocking, fusion or reordering beyond what those definitions state.
  *
+ * Planted mistakes (ora_plant, tests only): each id makes one step take a
+ * known-wrong form, so that the tests can show that the pins reject it; id
+ * 0, the default, runs every step as stated above.
+ *
  * Threads (OpenMP, optional): loops over independent rows or blocks carry a
  * parallel-for pragma and nothing else changes; every row or block is
  * computed by the same statements in the same order whatever the thread
@@ -60,6 +64,31 @@ int ora_max_threads(void) {
 }
 
 #define ORA_MAXLEV 24
+
+/* planted mistakes (see the header) */
+enum {
+    PL_NONE = 0,
+    PL_PRESCALE_OFF,      /* the setup without W (Sec. 2.3.1) */
+    PL_UPDATE_SIGN,       /* E_b + Lambda R_b instead of E_b - Lambda R_b (Alg. 2) */
+    PL_LAMBDA_T,          /* every block stores Lambda_b^T */
+    PL_SMOOTH_T,          /* the forward application takes Lambda^T */
+    PL_COLOUR_ORDER,      /* the forward application runs its colours backwards */
+    PL_REVERSE_ORDER,     /* the reverse application keeps the forward step order */
+    PL_SMOOTH_SIGN,       /* the smoother adds Lambda (A x - b) */
+    PL_INTERP_ONE_SIDED,  /* an even fine node interpolates from one coarse node */
+    PL_RESTRICT_UNSCALED, /* R = P^T beside a Galerkin product scaled 2^{-d} */
+    PL_COARSE_CHOL,       /* the coarsest solve takes Cholesky of a nonsymmetric A_c */
+    PL_TRUNC_SMALLEST,    /* truncation keeps the alpha smallest column blocks */
+    PL_MINNORM_OFF,       /* the block least squares without the minimum-norm cutoff */
+    PL_OVERLAP_SUM,       /* overlapping rows summed instead of averaged over theta */
+    PL_STOKES_Q2,         /* the L^2 pressure weight sums |a| w without squaring */
+    PL_SPD_NO_UPPER,      /* the SPD projection clips at 0 only, not at D^{-1} */
+    PL_PCG_BETA,          /* PCG with beta = rz_k / rz_{k+1} */
+    PL_GREEDY_ASCENDING,  /* the greedy colouring visits blocks in ascending priority */
+    PL_SKETCH_STALE,      /* the sketched setup never advances E S */
+};
+static int planted = PL_NONE;
+void ora_plant(int id) { planted = id; }
 
 /* ------------------------------------------------------------------ CSR */
 typedef struct {
@@ -228,7 +257,7 @@ static int p1d_entries(int f, int nc, int *c, double *w) {
     if (f % 2 == 1) { c[0] = (f - 1) / 2; w[0] = 1.0; return 1; }
     int k = 0;
     int lo = f / 2 - 1, hi = f / 2;
-    if (lo >= 0 && lo < nc) { c[k] = lo; w[k] = 0.5; ++k; }
+    if (lo >= 0 && lo < nc && planted != PL_INTERP_ONE_SIDED) { c[k] = lo; w[k] = 0.5; ++k; }
     if (hi >= 0 && hi < nc) { c[k] = hi; w[k] = 0.5; ++k; }
     return k;
 }
@@ -363,7 +392,7 @@ static void sym_eig(double *a, int n, double *ev, double *q) {
 static void ls_solve_block(const double *G, const double *C, int n, double *Lam) {
     double tr = 0.0;
     for (int i = 0; i < n; ++i) tr += G[i * n + i];
-    double tol = 1e-14 * tr;
+    double tol = planted == PL_MINNORM_OFF ? 0.0 : 1e-14 * tr;
     double *L = xmalloc(sizeof(double) * (size_t)n * n);
     memcpy(L, G, sizeof(double) * (size_t)n * n);
     double *y = xmalloc(sizeof(double) * (size_t)n);
@@ -436,7 +465,8 @@ static void project_spd_block(double *L, const double *D, int n) {
                 T[p * n + q] = a;
             }
         sym_eig(T, n, ev, Q);
-        for (int k = 0; k < n; ++k) ev[k] = ev[k] < 0.0 ? 0.0 : (ev[k] > 1.0 ? 1.0 : ev[k]);
+        for (int k = 0; k < n; ++k)
+            ev[k] = ev[k] < 0.0 ? 0.0 : (ev[k] > 1.0 && planted != PL_SPD_NO_UPPER ? 1.0 : ev[k]);
         /* S = Q diag(ev) Q^T, then L = Di S Di */
         for (int p = 0; p < n; ++p)
             for (int q = 0; q < n; ++q) {
@@ -541,7 +571,7 @@ static void factor_coarsest(ora_hier *h) {
         }
     double *tmp = xmalloc(sizeof(double) * (size_t)n * n);
     memcpy(tmp, h->cfac, sizeof(double) * (size_t)n * n);
-    if (asym <= 1e-14 * amax && chol(tmp, n, 0.0) == 0) {
+    if ((asym <= 1e-14 * amax || planted == PL_COARSE_CHOL) && chol(tmp, n, 0.0) == 0) {
         h->cspd = 1;
         memcpy(h->cfac, tmp, sizeof(double) * (size_t)n * n);
     } else {
@@ -577,7 +607,8 @@ ora_hier *ora_hier_create(int dim, const int *n3, int nst, const int *off, const
         csr_spgemm(&h->A[l], &h->P[l], 1.0, &AP);
         csr_spgemm(&Pt, &AP, h->rscale, &h->A[l + 1]);
         csr_transpose(&h->P[l], &h->R[l]);
-        for (int64_t p = 0; p < h->R[l].rp[h->R[l].n]; ++p) h->R[l].v[p] *= h->rscale;
+        if (planted != PL_RESTRICT_UNSCALED)
+            for (int64_t p = 0; p < h->R[l].rp[h->R[l].n]; ++p) h->R[l].v[p] *= h->rscale;
         csr_free(&Pt); csr_free(&AP);
         ++l;
         h->n3[l][0] = nc[0]; h->n3[l][1] = nc[1]; h->n3[l][2] = nc[2];
@@ -736,7 +767,7 @@ void ora_ghier_set_fields(ora_hier *h, const int *field) {
 typedef struct { uint64_t p; int b; } prio_t;
 static int cmp_prio(const void *a, const void *b) {
     const prio_t *x = a, *y = b;
-    if (x->p != y->p) return x->p > y->p ? -1 : 1; /* larger priority first */
+    if (x->p != y->p) return (x->p > y->p) != (planted == PL_GREEDY_ASCENDING) ? -1 : 1; /* larger priority first */
     return (x->b > y->b) - (x->b < y->b);          /* then smaller index */
 }
 
@@ -884,7 +915,7 @@ static int prescale_weights(const ora_hier *h, int l, int mode, double *w) {
                 if (fld[j] != 0) continue;
                 double a = fabs(A->v[p]) * w[j];
                 if (mode == 2) nrm += a;
-                else if (mode == 3) nrm += a * a;
+                else if (mode == 3) nrm += planted == PL_STOKES_Q2 ? a : a * a;
                 else if (a > nrm) nrm = a;
             }
             if (mode == 3) nrm = sqrt(nrm);
@@ -907,6 +938,7 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
     /* the prescaling W (Sec. 2.3) */
     double *w = xmalloc(sizeof(double) * (size_t)N);
     if (prescale_weights(h, l, prescale, w) != 0) { free(w); return -1; }
+    if (planted == PL_PRESCALE_OFF) for (int i = 0; i < N; ++i) w[i] = 1.0;
     const int over = h->overlap[l];
     if (over && alpha > 0) { free(w); return -1; }
     csr A;
@@ -1004,6 +1036,9 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
                     }
                 double *Lb = lam + (size_t)lev * lamsize + lamoff[b];
                 ls_solve_block(G, C, nbk, Lb);
+                if (planted == PL_LAMBDA_T)
+                    for (int p = 0; p < nbk; ++p)
+                        for (int q = p + 1; q < nbk; ++q) { double t = Lb[p * nbk + q]; Lb[p * nbk + q] = Lb[q * nbk + p]; Lb[q * nbk + p] = t; }
                 if (spd) {
                     double *Dbb = xcalloc((size_t)nbk * nbk, sizeof(double));
                     for (int p = 0; p < nbk; ++p)
@@ -1018,6 +1053,7 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
                     for (int t = 0; t < nu_cols; ++t) {
                         double s = Eb[(size_t)p * nu_cols + t];
                         for (int q = 0; q < nbk; ++q) s -= Lb[p * nbk + q] * Rb[(size_t)q * nu_cols + t];
+                        if (planted == PL_UPDATE_SIGN) s = 2.0 * Eb[(size_t)p * nu_cols + t] - s;
                         Eb[(size_t)p * nu_cols + t] = s;
                     }
                 /* optional truncation: keep the alpha column blocks of largest
@@ -1040,7 +1076,9 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
                             int best = -1;
                             for (int u = 0; u < nbl; ++u) {
                                 if (sel[u]) continue;
-                                if (best < 0 || bn[u] > bn[best] || (bn[u] == bn[best] && bl[u] < bl[best])) best = u;
+                                if (best < 0) { best = u; continue; }
+                                const int larger = planted == PL_TRUNC_SMALLEST ? bn[u] < bn[best] : bn[u] > bn[best];
+                                if (larger || (bn[u] == bn[best] && bl[u] < bl[best])) best = u;
                             }
                             sel[best] = 1;
                         }
@@ -1092,7 +1130,7 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
                         const srow *br = &bnew[bptr[nblk[u]] + nloc[u]];
                         for (int t = 0; t < br->nnz; ++t) o->v[ps[br->c[t]]] += br->v[t];
                     }
-                    const double th = (double)(nptr[i + 1] - nptr[i]);
+                    const double th = planted == PL_OVERLAP_SUM ? 1.0 : (double)(nptr[i + 1] - nptr[i]);
                     for (int t = 0; t < nc; ++t) o->v[t] /= th;
                 }
                 free(mk); free(ps); free(ul);
@@ -1284,7 +1322,7 @@ static int sketch_level(const ora_hier *h, int l, int kind, int nu, int prescale
                     }
                 free(G); free(C);
             }
-            double *tmp = Y; Y = Yn; Yn = tmp;
+            if (planted != PL_SKETCH_STALE) { double *tmp = Y; Y = Yn; Yn = tmp; }
         }
     }
     for (int step = 0; step < nu; ++step)
@@ -1351,9 +1389,9 @@ void ora_smooth(const ora_hier *h, const ora_casc *c, int l, int reverse, const 
     const int *bptr = h->bptr[l], *bidx = h->bidx[l];
     double *r = xmalloc(sizeof(double) * (size_t)N);
     for (int step = 0; step < c->nu; ++step) {
-        int L = reverse ? c->nu - 1 - step : step;
+        int L = reverse && planted != PL_REVERSE_ORDER ? c->nu - 1 - step : step;
         for (int kk = 0; kk < c->ncl[l]; ++kk) {
-            int K = reverse ? c->ncl[l] - 1 - kk : kk;
+            int K = reverse != (planted == PL_COLOUR_ORDER) ? c->ncl[l] - 1 - kk : kk;
             ora_residual(h, l, b, x, r);
             if (h->overlap[l] && c->kind == 0) {
                 /* x -= diag(theta)^{-1} Theta^T Lambda Theta r (Sec. 3.6.2): the
@@ -1388,11 +1426,13 @@ void ora_smooth(const ora_hier *h, const ora_casc *c, int l, int reverse, const 
                 int nbk = bptr[bk + 1] - bptr[bk];
                 const int *rows = bidx + bptr[bk];
                 const double *Lb = c->lam[l] + (size_t)L * c->lamsize[l] + c->lamoff[l][bk];
+                const int tr = reverse != (planted == PL_SMOOTH_T);
                 for (int p = 0; p < nbk; ++p) {
                     double s = 0.0;
                     for (int q = 0; q < nbk; ++q)
-                        s += (reverse ? Lb[q * nbk + p] : Lb[p * nbk + q]) * r[rows[q]];
-                    x[rows[p]] -= s;
+                        s += (tr ? Lb[q * nbk + p] : Lb[p * nbk + q]) * r[rows[q]];
+                    if (planted == PL_SMOOTH_SIGN) x[rows[p]] += s;
+                    else x[rows[p]] -= s;
                 }
             }
         }
@@ -1506,7 +1546,7 @@ int ora_solve(const ora_hier *h, const ora_casc *c, int method, int mu_pre, int 
             ora_vcycle(h, c, mu_pre, mu_post, rf, r, z);
             double rz1 = 0.0;
             for (int i = 0; i < N; ++i) rz1 += r[i] * z[i];
-            double beta = rz1 / rz;
+            double beta = planted == PL_PCG_BETA ? rz / rz1 : rz1 / rz;
             rz = rz1;
             for (int i = 0; i < N; ++i) pv[i] = z[i] + beta * pv[i];
         }

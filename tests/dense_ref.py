@@ -134,7 +134,8 @@ def dense_overlap_cascade(Ad, blocks, nu, w=None):
     ||(Theta - Lambda Theta A~) E_{l-1}||_F (per block lstsq with the
     method's rank rule) and E_l = diag(theta)^-1 Theta^T (Theta - Lambda_l
     Theta A~) E_{l-1}.  Returns the unscaled per-block Lambda per step (list
-    over steps of lists over blocks) and the dense Theta."""
+    over steps of lists over blocks), the dense Theta, and ||E_l||_F for
+    l = 0..nu."""
     N = Ad.shape[0]
     if w is None:
         w = 1.0 / np.sqrt(np.diag(Ad))
@@ -148,7 +149,7 @@ def dense_overlap_cascade(Ad, blocks, nu, w=None):
             r += 1
     theta = Th.sum(axis=0)
     E = np.eye(N)
-    out = []
+    out, norms = [], [np.linalg.norm(E)]
     for _ in range(nu):
         AE = At @ E
         new = np.zeros((M, N))
@@ -164,4 +165,5 @@ def dense_overlap_cascade(Ad, blocks, nu, w=None):
             r += len(b)
         E = (Th.T @ new) / theta[:, None]
         out.append(lams)
-    return out, Th
+        norms.append(np.linalg.norm(E))
+    return out, Th, np.array(norms)

@@ -955,25 +955,44 @@ def _cells_problem(n=9, seed=5):
     return u, oracle.Hierarchy.from_csr(u["A"], u["Ps"], rscale=0.25, blocks=u["cells"], seed=3)
 
 
-def test_overlapping_additive_cascade_matches_dense_definition():
+def _with_singletons(cells, every):
+    """The cell blocks plus a one-node block on every `every`-th unknown, so
+    that the overlap count theta differs between nodes."""
+    cptr, cidx = cells
+    extra = np.arange(0, int(cidx.max()) + 1, every, dtype=np.int32)
+    bptr = np.concatenate([cptr, cptr[-1] + 1 + np.arange(len(extra), dtype=np.int32)]).astype(np.int32)
+    return bptr, np.concatenate([cidx, extra]).astype(np.int32)
+
+
+@pytest.mark.parametrize("singletons", [0, 3])
+def test_overlapping_additive_cascade_matches_dense_definition(singletons):
     """Sec. 3.6.2: the overlapping-block additive cascade (the interior nodes
-    of every element as a block, an interior node in 4 blocks) against the
-    dense definition with Theta, and one application of the smoother
-    against x - diag(theta)^-1 Theta^T Lambda Theta (A x - b) step by step."""
-    u, h = _cells_problem()
+    of every element as a block, an interior node in 4 blocks; with
+    `singletons`, one-node blocks on some nodes as well, so theta varies)
+    against the dense definition with Theta, Lambda and ||E_l||_F after
+    every step, and one application of the smoother against
+    x - diag(theta)^-1 Theta^T Lambda Theta (A x - b) step by step.  Lambda
+    alone cannot see a wrong theta where theta is the same at every node (a
+    uniform scale of E leaves the least squares unchanged); ||E_l||_F and
+    the varying theta do."""
+    u = problems.unstructured_q1(9, 5)
+    cells = _with_singletons(u["cells"], singletons) if singletons else u["cells"]
+    h = oracle.Hierarchy.from_csr(u["A"], u["Ps"], rscale=0.25, blocks=cells, seed=3)
     assert h.overlapping(0)
     c = oracle.Cascade(h, "additive", nu=2)
     bptr, bidx, _ = h.blocks(0)
     blist = [bidx[bptr[b]:bptr[b + 1]] for b in range(len(bptr) - 1)]
-    lams, Th = dense_ref.dense_overlap_cascade(u["A"].toarray(), blist, 2)
+    lams, Th, norms = dense_ref.dense_overlap_cascade(u["A"].toarray(), blist, 2)
+    theta = Th.sum(axis=0)
+    assert (theta.min() < theta.max()) == bool(singletons)
     lam = c.lam(0)
     offs = np.cumsum([0] + [len(b) ** 2 for b in blist])
     for step in range(2):
         for k, b in enumerate(blist):
             got = lam[step, offs[k]:offs[k + 1]].reshape(len(b), len(b))
             assert np.abs(got - lams[step][k]).max() <= 1e-10 * np.abs(lams[step][k]).max(), (step, k)
+    np.testing.assert_allclose(c.efrob(0), norms, rtol=1e-10)
     A = u["A"].toarray()
-    theta = Th.sum(axis=0)
     b = problems.uniform(3, A.shape[0])
     x0 = problems.uniform(4, A.shape[0])
     x = x0.copy()
