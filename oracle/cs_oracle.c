@@ -86,6 +86,10 @@ enum {
     PL_PCG_BETA,          /* PCG with beta = rz_k / rz_{k+1} */
     PL_GREEDY_ASCENDING,  /* the greedy colouring visits blocks in ascending priority */
     PL_SKETCH_STALE,      /* the sketched setup never advances E S */
+    PL_PRESCALE_POWER,    /* the elliptic weight 1 / A_ii instead of A_ii^{-1/2} */
+    PL_OVERLAP_SMOOTH_SUM,/* the overlapping smoother sums its block corrections */
+    PL_GALERKIN_RSCALE,   /* a user hierarchy's coarse operator without rscale */
+    PL_PARITY,            /* red-black parity from the x block index alone */
 };
 static int planted = PL_NONE;
 void ora_plant(int id) { planted = id; }
@@ -542,7 +546,7 @@ static void make_blocks(ora_hier *h, int l) {
     for (int bz = 0; bz < nbz; ++bz)
         for (int by = 0; by < nby; ++by)
             for (int bx = 0; bx < nbx; ++bx) {
-                int s = (bx + 1) + (by + 1) + (h->dim == 3 ? bz + 1 : 0);
+                int s = planted == PL_PARITY ? bx : (bx + 1) + (by + 1) + (h->dim == 3 ? bz + 1 : 0);
                 h->bpar[l][bx + nbx * (by + nby * bz)] = s & 1;
             }
     free(fill); free(blk);
@@ -691,7 +695,7 @@ int ora_ghier_add_level(ora_hier *h, int Nc, const int64_t *prp, const int *pci,
     csr Pt, AP;
     csr_transpose(&h->P[l], &Pt);
     csr_spgemm(&h->A[l], &h->P[l], 1.0, &AP);
-    csr_spgemm(&Pt, &AP, h->rscale, &h->A[l + 1]);
+    csr_spgemm(&Pt, &AP, planted == PL_GALERKIN_RSCALE ? 1.0 : h->rscale, &h->A[l + 1]);
     csr_transpose(&h->P[l], &h->R[l]);
     for (int64_t p = 0; p < h->R[l].rp[h->R[l].n]; ++p) h->R[l].v[p] *= h->rscale;
     csr_free(&Pt); csr_free(&AP);
@@ -897,7 +901,7 @@ static int prescale_weights(const ora_hier *h, int l, int mode, double *w) {
         if (mode == 0) w[i] = 1.0;
         else if (mode == 1) {
             if (!(d > 0.0)) return -1;
-            w[i] = 1.0 / sqrt(d);
+            w[i] = planted == PL_PRESCALE_POWER ? 1.0 / d : 1.0 / sqrt(d);
         } else if (!fld || fld[i] == 0) {
             double l1 = 0.0;
             for (int64_t p = A->rp[i]; p < A->rp[i + 1]; ++p)
@@ -1415,7 +1419,7 @@ void ora_smooth(const ora_hier *h, const ora_casc *c, int l, int reverse, const 
                 for (int i = 0; i < N; ++i) {
                     double s = 0.0;
                     for (int u = nptr[i]; u < nptr[i + 1]; ++u) s += d[bptr[nblk[u]] + nloc[u]];
-                    x[i] -= s / (double)(nptr[i + 1] - nptr[i]);
+                    x[i] -= planted == PL_OVERLAP_SMOOTH_SUM ? s : s / (double)(nptr[i + 1] - nptr[i]);
                 }
                 free(d); free(nptr); free(nblk); free(nloc);
                 continue;

@@ -39,6 +39,10 @@ MUTANTS = {
     "greedy_ascending": [(pins.test_csr_hierarchy_galerkin_and_greedy_colouring, {})],
     "sketch_stale": [(pins.test_sketched_setup_matches_dense_lstsq,
                       dict(kind="additive", bs=1, exact_first=False, s=6))],
+    "prescale_power": [(pins.test_scale_invariance_of_setup, {})],
+    "overlap_smooth_sum": [(pins.test_overlapping_additive_cascade_matches_dense_definition, dict(singletons=0))],
+    "galerkin_rscale": [(pins.test_csr_hierarchy_galerkin_and_greedy_colouring, {})],
+    "parity": [(pins.test_setup_matches_dense_lstsq, dict(dim=2, n=7, bs=1, kind="multiplicative", nu=3))],
 }
 
 
