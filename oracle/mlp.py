@@ -13,11 +13,32 @@ module restates, in plain numpy:
   * the features (prescaled operator rows over the (bs+2)^2 window of a
     block) and targets (prescaled Lambda~ blocks of an oracle cascade).
 
-Pinned in tests/test_oracle_mlp.py by central finite differences.
+Pinned in tests/test_oracle_mlp.py by central finite differences and by
+the definitions of the features, targets, rounding and loss.  ``planted``
+(tests only) makes one step take a known-wrong form, so that a test can show
+that the pins reject it.
 """
 from __future__ import annotations
 
+import contextlib
+
 import numpy as np
+
+# planted mistakes (tests only): None runs every step as stated
+PLANTS = ("weights_unrounded", "loss_sum", "relu_grad_open", "window_mirror", "target_unscaled")
+_planted = None
+
+
+@contextlib.contextmanager
+def planted(name: str):
+    """Inside the block one step takes the named known-wrong form."""
+    global _planted
+    assert name in PLANTS
+    _planted = name
+    try:
+        yield
+    finally:
+        _planted = None
 
 
 def bf16_round(x: np.ndarray) -> np.ndarray:
@@ -40,7 +61,7 @@ def unpack(p, nin, nhid, nout):
 
 def _rounder(bf16):
     """Weights as used in the products: BF16-rounded FP32 masters, or exact."""
-    if bf16:
+    if bf16 and _planted != "weights_unrounded":
         return lambda w: bf16_round(np.asarray(w, dtype=np.float32))
     return lambda w: np.asarray(w, dtype=np.float64)
 
@@ -66,12 +87,14 @@ def loss_and_grad(p, X, T, nin, nhid, nout, bf16=True):
     Y, (Z1, H1, Z2, H2) = forward(p, X, nin, nhid, nout, bf16)
     n = Y.size
     E = Y - T
+    if _planted == "loss_sum":
+        n = 1
     loss = float(np.sum(E * E) / n)
     dY = 2.0 * E / n
     dW3 = dY.T @ H2
     db3 = dY.sum(axis=0)
     dH2 = dY @ q(W3)
-    dZ2 = dH2 * (Z2 > 0)
+    dZ2 = dH2 * (Z2 > 0) if _planted != "relu_grad_open" else dH2
     dW2 = dZ2.T @ H1
     db2 = dZ2.sum(axis=0)
     dH1 = dZ2 @ q(W2)
@@ -94,6 +117,7 @@ def block_features(A, bs: int) -> np.ndarray:
     w = 1.0 / np.sqrt(d)
     nbx, nby = -(-nx // bs), -(-ny // bs)
     win = bs + 2
+    sx = -1 if _planted == "window_mirror" else 1
     F = np.zeros((nbx * nby, bs * bs * win * win))
     for by in range(nby):
         for bx in range(nbx):
@@ -109,7 +133,7 @@ def block_features(A, bs: int) -> np.ndarray:
                     if not (0 <= jx < nx and 0 <= jy < ny):
                         continue
                     j = jx + nx * jy
-                    F[b, p * win * win + (lx + dx + 1) + win * (ly + dy + 1)] += w[i] * A.coeff[s, i] * w[j]
+                    F[b, p * win * win + (lx + sx * dx + 1) + win * (ly + sx * dy + 1)] += w[i] * A.coeff[s, i] * w[j]
     return F
 
 
@@ -140,5 +164,6 @@ def block_targets(lam_blocks: np.ndarray, A, bs: int, nu: int) -> np.ndarray:
                 off += k * k
                 for a, (p, i) in enumerate(pres):
                     for c, (qq, j) in enumerate(pres):
-                        T[b, (l * nm + p) * nm + qq] = blk[a, c] * np.sqrt(d[i] * d[j])
+                        sc = 1.0 if _planted == "target_unscaled" else np.sqrt(d[i] * d[j])
+                        T[b, (l * nm + p) * nm + qq] = blk[a, c] * sc
     return T

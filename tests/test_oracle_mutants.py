@@ -13,6 +13,8 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import mlp as om
+from tests import test_oracle_mlp as mpins
 from tests import test_oracle_pins as pins
 
 # mistake -> the pins (function, arguments) expected to reject it
@@ -68,4 +70,32 @@ def test_pins_reject_the_planted_mistake(mistake):
     assert failed, f"no pin rejects the planted mistake '{mistake}'"
     # and without the mistake the same pins pass
     for fn, kw in MUTANTS[mistake]:
+        fn(**kw)
+
+
+# the network's oracle (oracle/mlp.py): mistake -> the pins expected to reject it
+MLP_MUTANTS = {
+    "weights_unrounded": [(mpins.test_forward_rounds_the_weights_to_bf16, {})],
+    "loss_sum": [(mpins.test_loss_is_the_mean_squared_error, {})],
+    "relu_grad_open": [(mpins.test_backprop_matches_finite_differences, {})],
+    "window_mirror": [(mpins.test_features_are_the_prescaled_rows_over_every_window, dict(n=10, bs=3))],
+    "target_unscaled": [(mpins.test_targets_are_the_prescaled_blocks_of_every_block, dict(n=10, bs=3))],
+}
+
+
+def test_every_planted_network_mistake_has_a_case():
+    assert set(MLP_MUTANTS) == set(om.PLANTS)
+
+
+@pytest.mark.parametrize("mistake", list(MLP_MUTANTS))
+def test_network_pins_reject_the_planted_mistake(mistake):
+    failed = []
+    with om.planted(mistake):
+        for fn, kw in MLP_MUTANTS[mistake]:
+            try:
+                fn(**kw)
+            except AssertionError:
+                failed.append(fn.__name__)
+    assert failed, f"no pin rejects the planted network mistake '{mistake}'"
+    for fn, kw in MLP_MUTANTS[mistake]:
         fn(**kw)
