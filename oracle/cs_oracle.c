@@ -90,6 +90,8 @@ enum {
     PL_OVERLAP_SMOOTH_SUM,/* the overlapping smoother sums its block corrections */
     PL_GALERKIN_RSCALE,   /* a user hierarchy's coarse operator without rscale */
     PL_PARITY,            /* red-black parity from the x block index alone */
+    PL_GIVENS_SIGN,       /* left GMRES rotates H with the sign of s flipped */
+    PL_RIGHT_UPDATE_V,    /* right GMRES updates x from V y instead of Z y */
 };
 static int planted = PL_NONE;
 void ora_plant(int id) { planted = id; }
@@ -1621,8 +1623,9 @@ int ora_solve(const ora_hier *h, const ora_casc *c, int method, int mu_pre, int 
                 for (int k = i + 1; k < j; ++k) s -= H[i * m + k] * y[k];
                 y[i] = s / H[i * m + i];
             }
+            const double *U = planted == PL_RIGHT_UPDATE_V ? V : Z;
             for (int i = 0; i < j; ++i)
-                for (int q = 0; q < N; ++q) x[q] += y[i] * Z[(size_t)i * N + q];
+                for (int q = 0; q < N; ++q) x[q] += y[i] * U[(size_t)i * N + q];
         }
         conv = rel <= tol;
         if (final_rel) *final_rel = rel;
@@ -1675,7 +1678,7 @@ int ora_solve(const ora_hier *h, const ora_casc *c, int method, int mu_pre, int 
                 for (int i = 0; i < j; ++i) {
                     double a = H[i * m + j], bb = H[(i + 1) * m + j];
                     H[i * m + j] = cs[i] * a + sn[i] * bb;
-                    H[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+                    H[(i + 1) * m + j] = (planted == PL_GIVENS_SIGN ? sn[i] : -sn[i]) * a + cs[i] * bb;
                 }
                 double a = H[j * m + j], bb = H[(j + 1) * m + j];
                 double d = sqrt(a * a + bb * bb);

@@ -45,6 +45,10 @@ MUTANTS = {
     "overlap_smooth_sum": [(pins.test_overlapping_additive_cascade_matches_dense_definition, dict(singletons=0))],
     "galerkin_rscale": [(pins.test_csr_hierarchy_galerkin_and_greedy_colouring, {})],
     "parity": [(pins.test_setup_matches_dense_lstsq, dict(dim=2, n=7, bs=1, kind="multiplicative", nu=3))],
+    "givens_sign": [(pins.test_gmres_residuals_are_minimal, dict(method="gmres"))],
+    "right_update_v": [(pins.test_manufactured_convergence,
+                        dict(dim=2, n=31, kind="additive", method="gmres_right")),
+                       (pins.test_gmres_residuals_are_minimal, dict(method="gmres_right"))],
 }
 
 

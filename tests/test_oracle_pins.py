@@ -516,7 +516,8 @@ def test_restriction_scale_invariance():
 
 @pytest.mark.parametrize("dim,n,kind,method", [
     (2, 31, "additive", "stationary"), (2, 31, "multiplicative", "gmres"),
-    (3, 15, "additive", "gmres"), (3, 15, "multiplicative", "stationary")])
+    (3, 15, "additive", "gmres"), (3, 15, "multiplicative", "stationary"),
+    (2, 31, "additive", "gmres_right"), (3, 15, "multiplicative", "gmres_right")])
 def test_manufactured_convergence(dim, n, kind, method):
     A = problems.poisson(dim, n)
     h = oracle.Hierarchy(A)
@@ -548,6 +549,51 @@ def test_gmres_finite_termination():
     # single-level hierarchy: V is the direct solve, so GMRES ends after one step
     x, it, hist, fin = oracle.solve(h, c, b, method="gmres", tol=1e-12)
     assert it == 1 and fin < 1e-12
+
+
+def _krylov_min_residuals(K, r0, k_max):
+    """min over y of ||r0 - K Q_k y|| for k = 0..k_max, Q_k an orthonormal
+    basis of span{r0, K r0, ..., K^{k-1} r0} (Arnoldi with a second
+    Gram-Schmidt pass), the minimum by numpy's least squares."""
+    Q = np.zeros((len(r0), 0))
+    out = [np.linalg.norm(r0)]
+    v = r0 / np.linalg.norm(r0)
+    for _ in range(k_max):
+        Q = np.column_stack([Q, v])
+        KQ = K @ Q
+        y = np.linalg.lstsq(KQ, r0, rcond=None)[0]
+        out.append(np.linalg.norm(r0 - KQ @ y))
+        w = K @ v
+        for _ in range(2):
+            w = w - Q @ (Q.T @ w)
+        v = w / np.linalg.norm(w)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("method", ["gmres", "gmres_right"])
+def test_gmres_residuals_are_minimal(method):
+    """GMRES (Sec. 3.1) is the minimal-residual method: left-preconditioned,
+    its k-th estimate is min ||M b - M A x|| over x in K_k(M A, M b);
+    right-preconditioned, min ||b - A x|| over x in M K_k(A M, b).  M is
+    the oracle's V-cycle, assembled column by column; the minima come from
+    dense least squares, independent of the oracle's Arnoldi and Givens
+    steps."""
+    A = _small_problem(2, 15, seed=95)
+    h = oracle.Hierarchy(A)
+    c = oracle.Cascade(h, "additive", nu=1)
+    N = A.N
+    M = np.column_stack([oracle.vcycle(h, c, np.eye(N)[:, j], rf=True) for j in range(N)])
+    Ad = dense_ref.dense_from_stencil(A)
+    b = problems.uniform(17, N)
+    x, it, hist, fin = oracle.solve(h, c, b, method=method, tol=1e-11, restart=50, maxit=50)
+    assert it > 4 and fin <= 1e-11
+    if method == "gmres":
+        K, r0, scale = M @ Ad, M @ b, np.linalg.norm(M @ b)
+    else:
+        K, r0, scale = Ad @ M, b, np.linalg.norm(b)
+    ref = _krylov_min_residuals(K, r0, len(hist) - 1) / scale
+    keep = ref > 1e-9
+    np.testing.assert_allclose(hist[keep], ref[keep], rtol=1e-6)
 
 
 def test_metrics():
