@@ -92,6 +92,7 @@ enum {
     PL_PARITY,            /* red-black parity from the x block index alone */
     PL_GIVENS_SIGN,       /* left GMRES rotates H with the sign of s flipped */
     PL_RIGHT_UPDATE_V,    /* right GMRES updates x from V y instead of Z y */
+    PL_INPLACE_COLOUR,    /* a setup step's blocks see the rows updated before them (serial) */
 };
 static int planted = PL_NONE;
 void ora_plant(int id) { planted = id; }
@@ -986,7 +987,7 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
 
     for (int lev = 0; lev < nu; ++lev) {
         for (int k = 0; k < ncol; ++k) {
-#pragma omp parallel
+#pragma omp parallel if (planted != PL_INPLACE_COLOUR)
           {
             /* per-thread scratch: column marks and positions, block marks */
             int *mark = xmalloc(sizeof(int) * (size_t)N);
@@ -1104,6 +1105,15 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
                     int u = 0;
                     for (int t = 0; t < nu_cols; ++t)
                         if (keep[t]) { o->c[u] = ulist[t]; o->v[u] = Eb[(size_t)p * nu_cols + t]; ++u; }
+                    if (planted == PL_INPLACE_COLOUR && o == &Enew[rows[p]]) {
+                        srow *e = &E[rows[p]];
+                        free(e->c); free(e->v);
+                        e->nnz = cnt;
+                        e->c = xmalloc(sizeof(int) * (size_t)(cnt ? cnt : 1));
+                        e->v = xmalloc(sizeof(double) * (size_t)(cnt ? cnt : 1));
+                        memcpy(e->c, o->c, sizeof(int) * (size_t)cnt);
+                        memcpy(e->v, o->v, sizeof(double) * (size_t)cnt);
+                    }
                 }
                 free(keep); free(Rb); free(Eb); free(G); free(C);
             }

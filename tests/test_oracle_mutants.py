@@ -49,6 +49,8 @@ MUTANTS = {
     "right_update_v": [(pins.test_manufactured_convergence,
                         dict(dim=2, n=31, kind="additive", method="gmres_right")),
                        (pins.test_gmres_residuals_are_minimal, dict(method="gmres_right"))],
+    "inplace_colour": [(pins.test_coarse_level_setup_matches_dense_lstsq,
+                        dict(dim=2, n=14, bs=1, kind="multiplicative"))],
 }
 
 

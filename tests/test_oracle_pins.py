@@ -139,6 +139,37 @@ def test_setup_matches_dense_lstsq(dim, n, bs, kind, nu):
     assert np.all(np.diff(ef) <= 1e-12 * ef[:-1])
 
 
+@pytest.mark.parametrize("dim,n,bs,kind", [(2, 14, 1, "multiplicative"), (2, 14, 2, "multiplicative"),
+                                          (2, 14, 2, "additive"), (3, 10, 1, "multiplicative")])
+def test_coarse_level_setup_matches_dense_lstsq(dim, n, bs, kind):
+    """Algorithm 2 on the Galerkin level 1 (9- or 27-point operators):
+    there red-black is not a graph colouring, so the multiplicative form
+    depends on each colour reading the residual of the state before it
+    (the snapshot per colour); Lambda and ||E||_F against the dense
+    cascade on the dense coarse operator."""
+    A = _small_problem(dim, n, seed=13 + n + bs)
+    h = oracle.Hierarchy(A, bs=bs, max_levels=3)
+    assert h.nlev == 3  # level 1 is smoothed, level 2 solved directly
+    c = oracle.Cascade(h, kind, nu=2)
+    Ac = h.dense(1)
+    nc = tuple(h.dims(1))
+    blocks, par = dense_ref.block_partition(nc, dim, bs)
+    # red-black blocks of one colour are coupled here
+    assert any(par[a] == par[b] and np.any(Ac[np.ix_(blocks[a], blocks[b])] != 0)
+               for a in range(len(blocks)) for b in range(a + 1, len(blocks)))
+    lam_t, lam_u, Es = dense_ref.dense_cascade(Ac, blocks, par, kind, 2)
+    lam = c.lam(1)
+    offs = np.cumsum([0] + [len(r) ** 2 for r in blocks])
+    for l in range(2):
+        for b, rows in enumerate(blocks):
+            k = par[b] if kind == "multiplicative" else 0
+            nb = len(rows)
+            ref = lam_u[l][k][np.ix_(rows, rows)]
+            got = lam[l, offs[b]:offs[b + 1]].reshape(nb, nb)
+            np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
+    np.testing.assert_allclose(c.efrob(1), [np.linalg.norm(E) for E in Es], rtol=1e-10)
+
+
 @pytest.mark.parametrize("kind", ["additive", "multiplicative"])
 def test_first_order_optimality_and_perturbation(kind):
     """(E_b - Lam_b R_b) R_b^T = 0, and random perturbations of any block
