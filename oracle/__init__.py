@@ -120,7 +120,8 @@ PLANTS = ("prescale_off", "update_sign", "lambda_t", "smooth_t", "colour_order",
           "smooth_sign", "interp_one_sided", "restrict_unscaled", "coarse_chol", "trunc_smallest",
           "minnorm_off", "overlap_sum", "stokes_q2", "spd_no_upper", "pcg_beta", "greedy_ascending",
           "sketch_stale", "prescale_power", "overlap_smooth_sum", "galerkin_rscale", "parity",
-          "givens_sign", "right_update_v", "inplace_colour")
+          "givens_sign", "right_update_v", "inplace_colour",
+          "sketch_first_t")
 
 
 @contextlib.contextmanager

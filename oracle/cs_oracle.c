@@ -93,6 +93,7 @@ enum {
     PL_GIVENS_SIGN,       /* left GMRES rotates H with the sign of s flipped */
     PL_RIGHT_UPDATE_V,    /* right GMRES updates x from V y instead of Z y */
     PL_INPLACE_COLOUR,    /* a setup step's blocks see the rows updated before them (serial) */
+    PL_SKETCH_FIRST_T,    /* the sketch's exact first step takes C = A~_bb instead of A~_bb^T */
 };
 static int planted = PL_NONE;
 void ora_plant(int id) { planted = id; }
@@ -1313,8 +1314,12 @@ static int sketch_level(const ora_hier *h, int l, int kind, int nu, int prescale
                             for (int64_t u = A.rp[rp_]; u < A.rp[rp_ + 1]; ++u)
                                 for (int64_t v = A.rp[rq]; v < A.rp[rq + 1]; ++v)
                                     if (A.ci[u] == A.ci[v]) g += A.v[u] * A.v[v];
-                            for (int64_t v = A.rp[rq]; v < A.rp[rq + 1]; ++v)
-                                if (A.ci[v] == rp_) c += A.v[v];
+                            if (planted == PL_SKETCH_FIRST_T) {
+                                for (int64_t v = A.rp[rp_]; v < A.rp[rp_ + 1]; ++v)
+                                    if (A.ci[v] == rq) c += A.v[v];
+                            } else
+                                for (int64_t v = A.rp[rq]; v < A.rp[rq + 1]; ++v)
+                                    if (A.ci[v] == rp_) c += A.v[v];
                             G[p * nbk + q] = g; C[p * nbk + q] = c;
                         }
                 } else {

@@ -40,7 +40,7 @@ MUTANTS = {
     "pcg_beta": [(pins.test_pcg_matches_a_plain_pcg_around_the_oracle_cycle, dict(blocks="points"))],
     "greedy_ascending": [(pins.test_csr_hierarchy_galerkin_and_greedy_colouring, {})],
     "sketch_stale": [(pins.test_sketched_setup_matches_dense_lstsq,
-                      dict(kind="additive", bs=1, exact_first=False, s=6))],
+                      dict(kind="additive", bs=1, exact_first=False, s=6, prob="sym"))],
     "prescale_power": [(pins.test_scale_invariance_of_setup, {})],
     "overlap_smooth_sum": [(pins.test_overlapping_additive_cascade_matches_dense_definition, dict(singletons=0))],
     "galerkin_rscale": [(pins.test_csr_hierarchy_galerkin_and_greedy_colouring, {})],
@@ -51,6 +51,8 @@ MUTANTS = {
                        (pins.test_gmres_residuals_are_minimal, dict(method="gmres_right"))],
     "inplace_colour": [(pins.test_coarse_level_setup_matches_dense_lstsq,
                         dict(dim=2, n=14, bs=1, kind="multiplicative"))],
+    "sketch_first_t": [(pins.test_sketched_setup_matches_dense_lstsq,
+                        dict(kind="multiplicative", bs=2, exact_first=True, s=16, prob="nonsym"))],
 }
 
 

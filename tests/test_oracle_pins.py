@@ -810,16 +810,19 @@ def _sketch_dense(h, l, kind, nu, s, seed, exact_first):
     return lam, Y
 
 
-@pytest.mark.parametrize("kind,bs,exact_first,s", [("additive", 1, False, 6), ("multiplicative", 1, False, 5),
-                                                   ("additive", 2, False, 16), ("additive", 1, True, 4),
-                                                   ("multiplicative", 2, True, 16), ("multiplicative", 3, False, 32)])
-def test_sketched_setup_matches_dense_lstsq(kind, bs, exact_first, s):
+@pytest.mark.parametrize("kind,bs,exact_first,s,prob", [
+    ("additive", 1, False, 6, "sym"), ("multiplicative", 1, False, 5, "sym"), ("additive", 2, False, 16, "sym"),
+    ("additive", 1, True, 4, "sym"), ("multiplicative", 2, True, 16, "sym"), ("multiplicative", 3, False, 32, "sym"),
+    ("additive", 1, True, 8, "nonsym"), ("multiplicative", 2, True, 16, "nonsym")])
+def test_sketched_setup_matches_dense_lstsq(kind, bs, exact_first, s, prob):
     """The sketched cascade (Sec. 4, concluding remarks) on every smoothing
     level equals the dense brute force above (lstsq per block, the same
     sketch) to 1e-10: the oracle's normal equations and lstsq's orthogonal
     factorisation agree to about kappa(Z_b)^2 u, and later steps see blocks
-    with kappa(Z_b) ~ 1e2..1e3 (1.7e-11 measured for 3x3 blocks)."""
-    A = _small_problem(2, 9, seed=95)
+    with kappa(Z_b) ~ 1e2..1e3 (1.7e-11 measured for 3x3 blocks).  The
+    nonsymmetric operator tells the exact first step's C = E~ R^T = A~^T
+    restricted to the block from its transpose."""
+    A = _small_problem(2, 9, seed=95) if prob == "sym" else problems.nonsymmetric_3d(6, 2)
     h = oracle.Hierarchy(A, bs=bs)
     seed = 123
     c = oracle.Cascade(h, kind, nu=3, sketch=s, seed=seed, exact_first=exact_first)
