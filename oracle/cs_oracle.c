@@ -94,6 +94,10 @@ enum {
     PL_RIGHT_UPDATE_V,    /* right GMRES updates x from V y instead of Z y */
     PL_INPLACE_COLOUR,    /* a setup step's blocks see the rows updated before them (serial) */
     PL_SKETCH_FIRST_T,    /* the sketch's exact first step takes C = A~_bb instead of A~_bb^T */
+    PL_BOUNDARY_WRAP,     /* a Dirichlet grid wraps its stencil like a periodic one */
+    PL_PROLONG_SIGN,      /* the V-cycle adds P x_c with the wrong sign */
+    PL_RF_FORWARD,        /* the RF cycle pre-smooths with the forward application */
+    PL_STOKES_VEL_L1,     /* the velocity weight ||a_i||_1 / a_ii instead of its square root */
 };
 static int planted = PL_NONE;
 void ora_plant(int id) { planted = id; }
@@ -232,7 +236,7 @@ static void csr_from_stencil(const int n3[3], int nst, const int *off, const dou
                 int cnt = 0;
                 for (int s = 0; s < nst; ++s) {
                     int jx = ix + off[3 * s], jy = iy + off[3 * s + 1], jz = iz + off[3 * s + 2];
-                    if (periodic) {
+                    if (periodic || planted == PL_BOUNDARY_WRAP) {
                         jx = (jx % nx + nx) % nx; jy = (jy % ny + ny) % ny; jz = (jz % nz + nz) % nz;
                     } else if (jx < 0 || jx >= nx || jy < 0 || jy >= ny || jz < 0 || jz >= nz) {
                         continue;
@@ -911,7 +915,7 @@ static int prescale_weights(const ora_hier *h, int l, int mode, double *w) {
             for (int64_t p = A->rp[i]; p < A->rp[i + 1]; ++p)
                 if (!fld || fld[A->ci[p]] == 0) l1 += fabs(A->v[p]);
             if (!(d > 0.0) || !(l1 > 0.0)) return -1;
-            w[i] = sqrt(l1) / d;
+            w[i] = planted == PL_STOKES_VEL_L1 ? l1 / d : sqrt(l1) / d;
         }
     }
     if (mode >= 2 && fld)
@@ -1470,7 +1474,8 @@ void ora_prolong_correct(const ora_hier *h, int l, const double *xc, double *x) 
     for (int i = 0; i < P->n; ++i) {
         double s = 0.0;
         for (int64_t p = P->rp[i]; p < P->rp[i + 1]; ++p) s += P->v[p] * xc[P->ci[p]];
-        x[i] -= s;
+        if (planted == PL_PROLONG_SIGN) x[i] += s;
+        else x[i] -= s;
     }
 }
 /* x = A_c^{-1} b on the coarsest level (dense Cholesky, LU if not SPD). */
@@ -1486,7 +1491,7 @@ static void vcycle_rec(const ora_hier *h, const ora_casc *c, int l, int mu_pre, 
                        const double *b, double *x) {
     if (l == h->nlev - 1) { ora_coarse_solve(h, b, x); return; }
     int N = h->A[l].n, Nc = h->A[l + 1].n;
-    for (int m = 0; m < mu_pre; ++m) ora_smooth(h, c, l, rf ? 1 : 0, b, x);
+    for (int m = 0; m < mu_pre; ++m) ora_smooth(h, c, l, rf && planted != PL_RF_FORWARD ? 1 : 0, b, x);
     double *r = xmalloc(sizeof(double) * (size_t)N);
     double *rc = xmalloc(sizeof(double) * (size_t)Nc);
     double *xc = xcalloc((size_t)Nc, sizeof(double));

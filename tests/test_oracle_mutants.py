@@ -53,6 +53,11 @@ MUTANTS = {
                         dict(dim=2, n=14, bs=1, kind="multiplicative"))],
     "sketch_first_t": [(pins.test_sketched_setup_matches_dense_lstsq,
                         dict(kind="multiplicative", bs=2, exact_first=True, s=16, prob="nonsym"))],
+    "boundary_wrap": [(pins.test_couplings_to_boundary_nodes_are_ignored, {}),
+                      (pins.test_galerkin_matches_dense_rap, dict(dim=2, n=8))],
+    "prolong_sign": [(pins.test_manufactured_convergence, dict(dim=2, n=31, kind="additive", method="stationary"))],
+    "rf_forward": [(pins.test_vcycle_symmetry_rf, dict(kind="additive"))],
+    "stokes_vel_l1": [(pins.test_stokes_prescaling_has_its_defining_properties, dict(q=1, mode="stokes1"))],
 }
 
 
