@@ -1246,3 +1246,36 @@ def test_pcg_matches_a_plain_pcg_around_the_oracle_cycle(blocks):
         rz = rz1
     assert k == it
     assert np.abs(x - y).max() <= 1e-10 * np.abs(y).max()
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    """The oracle's parallel loops run over independent rows or blocks with
+    serial reductions, so every result is bitwise that of one thread: the
+    structured cascades (both kinds, truncation, a sketch), the overlapping
+    CSR cascade and a solve, each at 1 and 4 threads."""
+    lib = oracle._load()
+    if lib.ora_max_threads() < 1:
+        pytest.skip("oracle built without threads")
+    A = _small_problem(3, 11, seed=33)
+    b = problems.uniform(2, A.N, -1.0, 1.0)
+    u = problems.unstructured_q1(9, 5)
+
+    def run():
+        h = oracle.Hierarchy(A, bs=2)
+        out = [oracle.Cascade(h, "additive", nu=3).lam(0), oracle.Cascade(h, "multiplicative", nu=2, alpha=5).lam(0),
+               oracle.Cascade(h, "additive", nu=2, sketch=8, seed=3).lam(0)]
+        c = oracle.Cascade(h, "multiplicative", nu=2)
+        out.append(oracle.solve(h, c, b, method="gmres_right", tol=1e-10)[0])
+        hc = oracle.Hierarchy.from_csr(u["A"], u["Ps"], rscale=0.25, blocks=u["cells"], seed=3)
+        out.append(oracle.Cascade(hc, "additive", nu=2).lam(0))
+        return out
+
+    try:
+        oracle.set_threads(1)
+        one = run()
+        oracle.set_threads(4)
+        four = run()
+    finally:
+        oracle.set_threads(os.cpu_count() or 1)
+    for a, c in zip(one, four):
+        assert np.array_equal(a, c)
