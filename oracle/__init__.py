@@ -121,7 +121,8 @@ PLANTS = ("prescale_off", "update_sign", "lambda_t", "smooth_t", "colour_order",
           "minnorm_off", "overlap_sum", "stokes_q2", "spd_no_upper", "pcg_beta", "greedy_ascending",
           "sketch_stale", "prescale_power", "overlap_smooth_sum", "galerkin_rscale", "parity",
           "givens_sign", "right_update_v", "inplace_colour",
-          "sketch_first_t", "boundary_wrap", "prolong_sign", "rf_forward", "stokes_vel_l1")
+          "sketch_first_t", "boundary_wrap", "prolong_sign", "rf_forward", "stokes_vel_l1",
+          "sketch_z_once", "spd_unweighted")
 
 
 @contextlib.contextmanager

@@ -98,6 +98,8 @@ enum {
     PL_PROLONG_SIGN,      /* the V-cycle adds P x_c with the wrong sign */
     PL_RF_FORWARD,        /* the RF cycle pre-smooths with the forward application */
     PL_STOKES_VEL_L1,     /* the velocity weight ||a_i||_1 / a_ii instead of its square root */
+    PL_SKETCH_Z_ONCE,     /* the multiplicative sketch forms A~ Y once per step, not per colour */
+    PL_SPD_UNWEIGHTED,    /* the SPD projection takes D = I instead of A~_bb */
 };
 static int planted = PL_NONE;
 void ora_plant(int id) { planted = id; }
@@ -1057,6 +1059,9 @@ static int cascade_level(const ora_hier *h, int l, int kind, int nu, int prescal
                         for (int64_t q = A.rp[rows[p]]; q < A.rp[rows[p] + 1]; ++q)
                             for (int t = 0; t < nbk; ++t)
                                 if (A.ci[q] == rows[t]) Dbb[p * nbk + t] += A.v[q];
+                    if (planted == PL_SPD_UNWEIGHTED)
+                        for (int p = 0; p < nbk; ++p)
+                            for (int t = 0; t < nbk; ++t) Dbb[p * nbk + t] = p == t ? 1.0 : 0.0;
                     project_spd_block(Lb, Dbb, nbk);
                     free(Dbb);
                 }
@@ -1294,6 +1299,7 @@ static int sketch_level(const ora_hier *h, int l, int kind, int nu, int prescale
     for (int step = 0; step < nu; ++step) {
         for (int k = 0; k < ncol; ++k) {
             /* Z = A~ Y */
+            if (!(planted == PL_SKETCH_Z_ONCE && k > 0)) {
 #pragma omp parallel for schedule(static)
             for (int i = 0; i < N; ++i)
                 for (int t = 0; t < s; ++t) {
@@ -1301,6 +1307,7 @@ static int sketch_level(const ora_hier *h, int l, int kind, int nu, int prescale
                     for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) z += A.v[p] * Y[(int64_t)A.ci[p] * s + t];
                     Z[(int64_t)i * s + t] = z;
                 }
+            }
             memcpy(Yn, Y, sizeof(double) * (size_t)N * s);
 #pragma omp parallel for schedule(dynamic, 64)
             for (int b = 0; b < nb; ++b) {

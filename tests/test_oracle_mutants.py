@@ -58,6 +58,9 @@ MUTANTS = {
     "prolong_sign": [(pins.test_manufactured_convergence, dict(dim=2, n=31, kind="additive", method="stationary"))],
     "rf_forward": [(pins.test_vcycle_symmetry_rf, dict(kind="additive"))],
     "stokes_vel_l1": [(pins.test_stokes_prescaling_has_its_defining_properties, dict(q=1, mode="stokes1"))],
+    "sketch_z_once": [(pins.test_sketched_setup_matches_dense_lstsq,
+                       dict(kind="multiplicative", bs=1, exact_first=False, s=5, prob="sym"))],
+    "spd_unweighted": [(pins.test_spd_projection_is_bounded_by_block_jacobi, {})],
 }
 
 
